@@ -1,0 +1,479 @@
+/*
+ * lbm_oracle.c -- FP64 CPU oracle for the entropy-limited LBGK step.
+ *
+ * TEST INFRASTRUCTURE ONLY: see lbm_oracle.h.  Plain, slow, single-threaded
+ * C.  Every floating-point expression is written in the order it is meant to
+ * be evaluated (left to right) and the file is built with -ffp-contract=off,
+ * so no product is fused into an FMA.
+ *
+ * One step (Eq. lbgkLB with the limiter as a post-processing routine after
+ * the collision, Sec. 4.3.2), in the order the paper applies it:
+ *   1. free flight, pull form:  f_in_k(x) = f_k(x - v_k)                Sec. 2
+ *      a link that leaves the lattice is reflected (halfway bounce-back,
+ *      Sec. 4.4.1); a link through the moving lid gains 6 W_k rho_w (v_k . u_w)
+ *   2. moments rho, u                                                   Eq. macro_dis
+ *   3. polynomial quasiequilibrium f*                                   Eq. polyeq1d / polyeq2d
+ *   4. LBGK collision  f' = f* + (2 beta - 1)(f* - f_in)                Eq. collLBGK, lbgkLB
+ *   5. dS(f') = sum_k (f'_k - f*_k)^2 / f*_k                            Sec. 3.6, quadratic form of Eq. DelS
+ *   6. phi_pos: positivity rule, closest nonnegative point of the line
+ *      through f' and f*                                                Sec. 3.1
+ *   7. phi_med: median of dS over the stencil, homothety sqrt(dS_t/dS)  Sec. 3.5, Eq. entrHom
+ *   8. phi = min(phi_pos, phi_med);  f_out = f* + phi (f' - f*)         Eq. LimGenF
+ *   9. Ehrenfests' step f -> f* at the (at most k) sites of largest
+ *      dS > delta, ties broken by lower site index                      Sec. 3.2, Sec. 4.3.2
+ *  10. sums: mass, sum dS, LBGK and limiter entropy production          Sec. 3.4, Sec. 4.3.1
+ */
+#include "lbm_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* D2Q9 (Sec. 4.1): 0 rest, 1 east, 2 north, 3 west, 4 south, 5 NE, 6 NW, 7 SW, 8 SE. */
+static const int cx9[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+static const int cy9[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+static const int opp9[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+
+/* D2Q9 lattice weights W_0 = 4/9, W_1..4 = 1/9, W_5..8 = 1/36 (Sec. 4.1). */
+static double w9(int k)
+{
+    if (k == 0) return 4.0 / 9.0;
+    if (k < 5) return 1.0 / 9.0;
+    return 1.0 / 36.0;
+}
+
+/* D1Q3 (Sec. 4.1): the paper's f1 (rest), f2 (left, v = -1), f3 (right, v = +1) as 0, 1, 2. */
+static const int cx3[3] = {0, -1, 1};
+static const int opp3[3] = {0, 2, 1};
+
+static int nq(int lattice) { return lattice == ORC_D1Q3 ? 3 : 9; }
+
+void orc_feq(int lattice, double rho, double ux, double uy, double *feq)
+{
+    if (lattice == ORC_D1Q3) {
+        /* Eq. polyeq1d, term by term as printed. */
+        double u = ux;
+        double uu = u * u;
+        feq[0] = ((2.0 * rho) / 3.0) * (1.0 - (3.0 * uu) / 2.0);
+        feq[1] = (rho / 6.0) * ((1.0 - 3.0 * u) + 3.0 * uu);
+        feq[2] = (rho / 6.0) * ((1.0 + 3.0 * u) + 3.0 * uu);
+        return;
+    }
+    /* Eq. polyeq2d: f*_k = rho W_k (1 + 3 v.u + 9 (v.u)^2 / 2 - 3 u^2 / 2). */
+    double usq = ux * ux + uy * uy;
+    for (int k = 0; k < 9; ++k) {
+        double c = (double)cx9[k] * ux + (double)cy9[k] * uy;
+        feq[k] = (rho * w9(k)) * (((1.0 + 3.0 * c) + (9.0 * (c * c)) / 2.0) - (3.0 * usq) / 2.0);
+    }
+}
+
+void orc_site_moments(int lattice, const double *f, double *rho, double *ux, double *uy)
+{
+    /* Eq. macro_dis: rho = sum_k f_k, rho u = sum_k v_k f_k, summed in k order. */
+    double r = 0.0, jx = 0.0, jy = 0.0;
+    if (lattice == ORC_D1Q3) {
+        for (int k = 0; k < 3; ++k) {
+            r += f[k];
+            jx += (double)cx3[k] * f[k];
+        }
+    } else {
+        for (int k = 0; k < 9; ++k) {
+            r += f[k];
+            jx += (double)cx9[k] * f[k];
+            jy += (double)cy9[k] * f[k];
+        }
+    }
+    *rho = r;
+    *ux = jx / r;
+    *uy = (lattice == ORC_D1Q3) ? 0.0 : jy / r;
+}
+
+void orc_init(const orc_config *cfg, const double *rho, const double *ux, const double *uy, double *f)
+{
+    int q = nq(cfg->lattice);
+    long long n = (long long)cfg->nx * cfg->ny;
+    double feq[9];
+    for (long long s = 0; s < n; ++s) {
+        orc_feq(cfg->lattice, rho[s], ux[s], uy ? uy[s] : 0.0, feq);
+        for (int k = 0; k < q; ++k) f[k * n + s] = feq[k];
+    }
+}
+
+void orc_moments(const orc_config *cfg, const double *f, double *rho, double *ux, double *uy)
+{
+    int q = nq(cfg->lattice);
+    long long n = (long long)cfg->nx * cfg->ny;
+    double fl[9], r, a, b;
+    for (long long s = 0; s < n; ++s) {
+        for (int k = 0; k < q; ++k) fl[k] = f[k * n + s];
+        orc_site_moments(cfg->lattice, fl, &r, &a, &b);
+        rho[s] = r;
+        ux[s] = a;
+        if (uy) uy[s] = b;
+    }
+}
+
+/* Step 1: the populations that arrive at site (i, j) after free flight. */
+static void pull(const orc_config *cfg, const double *f, int i, int j, double *fin)
+{
+    int nx = cfg->nx, ny = cfg->ny;
+    long long n = (long long)nx * ny;
+    if (cfg->lattice == ORC_D1Q3) {
+        for (int k = 0; k < 3; ++k) {
+            int si = i - cx3[k];
+            if (cfg->boundary == ORC_BC_PERIODIC) si = (si + nx) % nx;
+            if (si < 0 || si >= nx)
+                fin[k] = f[opp3[k] * n + i]; /* closed end: halfway bounce-back */
+            else
+                fin[k] = f[k * n + si];
+        }
+        return;
+    }
+    int wrapx = cfg->boundary == ORC_BC_PERIODIC || cfg->boundary == ORC_BC_CHANNEL;
+    int wrapy = cfg->boundary == ORC_BC_PERIODIC;
+    for (int k = 0; k < 9; ++k) {
+        int si = i - cx9[k], sj = j - cy9[k];
+        if (wrapx) si = (si + nx) % nx;
+        if (wrapy) sj = (sj + ny) % ny;
+        if (si >= 0 && si < nx && sj >= 0 && sj < ny) {
+            fin[k] = f[k * n + (long long)sj * nx + si];
+        } else {
+            /* Halfway bounce-back: the population that left (i, j) towards the
+             * wall in direction opp(k) comes back as direction k.  A link
+             * through the lid (source above the top row) also picks up the
+             * moving-wall momentum 6 W_k rho_w (v_k . u_w) with u_w = (u_lid, 0). */
+            double v = f[opp9[k] * n + (long long)j * nx + i];
+            if (sj > ny - 1) v += ((6.0 * w9(k)) * cfg->rho_wall) * ((double)cx9[k] * cfg->u_lid);
+            fin[k] = v;
+        }
+    }
+}
+
+/*
+ * Steps 2-5 at one site.  Writes f* and f' (q values each), dS(f') and
+ * dS(f_in); returns 1 if the site cannot be limited (rho <= 0, f*_k <= 0 for
+ * some k, or a nonfinite value), in which case *dS = +inf.
+ */
+static int site_collide(const orc_config *cfg, const double *fin, double *fs, double *fp,
+                        double *dS, double *dS_in, double *rho_out)
+{
+    int q = nq(cfg->lattice);
+    double rho, ux, uy;
+    orc_site_moments(cfg->lattice, fin, &rho, &ux, &uy);
+    orc_feq(cfg->lattice, rho, ux, uy, fs);
+    double a = 2.0 * cfg->beta - 1.0;
+    for (int k = 0; k < q; ++k) fp[k] = fs[k] + a * (fs[k] - fin[k]);
+    int bad = !(rho > 0.0) || !isfinite(rho) || !isfinite(ux) || !isfinite(uy);
+    for (int k = 0; k < q; ++k)
+        if (!(fs[k] > 0.0) || !isfinite(fin[k])) bad = 1;
+    double s = 0.0, si = 0.0;
+    for (int k = 0; k < q; ++k) {
+        double d = fp[k] - fs[k];
+        s += (d * d) / fs[k];
+    }
+    for (int k = 0; k < q; ++k) {
+        double d = fin[k] - fs[k];
+        si += (d * d) / fs[k];
+    }
+    if (!isfinite(s) || !isfinite(si)) bad = 1;
+    *rho_out = rho;
+    *dS = bad ? INFINITY : s;
+    *dS_in = bad ? 0.0 : si;
+    return bad;
+}
+
+static void sort_small(double *v, int m)
+{
+    for (int a = 1; a < m; ++a) {
+        double x = v[a];
+        int b = a - 1;
+        while (b >= 0 && v[b] > x) {
+            v[b + 1] = v[b];
+            --b;
+        }
+        v[b + 1] = x;
+    }
+}
+
+/*
+ * Median-filter stencil at site (i, j) (Sec. 3.5; wall rules of Sec. 4.4):
+ * boundary nodes are not filtered; a node next to a wall uses itself and its
+ * two neighbours along that wall; a node next to two walls (next to a corner)
+ * uses itself and its inward neighbour along x and along y; all other nodes
+ * use the 3x3 block.  D1Q3: three points, the end sites not filtered.
+ * Returns the stencil size (0 = not filtered) and the values in v.
+ */
+static int median_stencil(const orc_config *cfg, const double *dS, int i, int j, double *v)
+{
+    int nx = cfg->nx, ny = cfg->ny;
+    if (cfg->lattice == ORC_D1Q3) {
+        if (cfg->boundary == ORC_BC_PERIODIC) {
+            v[0] = dS[(i - 1 + nx) % nx];
+            v[1] = dS[i];
+            v[2] = dS[(i + 1) % nx];
+            return 3;
+        }
+        if (i == 0 || i == nx - 1) return 0;
+        v[0] = dS[i - 1];
+        v[1] = dS[i];
+        v[2] = dS[i + 1];
+        return 3;
+    }
+#define DS(a, b) dS[(long long)(b) * nx + (a)]
+    int wallx = cfg->boundary == ORC_BC_WALLS;
+    int wally = cfg->boundary != ORC_BC_PERIODIC;
+    if ((wallx && (i == 0 || i == nx - 1)) || (wally && (j == 0 || j == ny - 1))) return 0;
+    int nearx = wallx && (i == 1 || i == nx - 2);
+    int neary = wally && (j == 1 || j == ny - 2);
+    if (nearx && neary) {
+        int ii = (i == 1) ? 2 : nx - 3;
+        int jj = (j == 1) ? 2 : ny - 3;
+        v[0] = DS(i, j);
+        v[1] = DS(ii, j);
+        v[2] = DS(i, jj);
+        return 3;
+    }
+    if (neary) {
+        v[0] = DS((i - 1 + nx) % nx, j);
+        v[1] = DS(i, j);
+        v[2] = DS((i + 1) % nx, j);
+        return 3;
+    }
+    if (nearx) {
+        v[0] = DS(i, j - 1);
+        v[1] = DS(i, j);
+        v[2] = DS(i, j + 1);
+        return 3;
+    }
+    int m = 0;
+    for (int b = -1; b <= 1; ++b)
+        for (int a = -1; a <= 1; ++a) v[m++] = DS((i + a + nx) % nx, (j + b + ny) % ny);
+    return 9;
+#undef DS
+}
+
+typedef struct {
+    double dS;
+    long long s;
+} cand_t;
+
+static int cand_cmp(const void *pa, const void *pb)
+{
+    const cand_t *a = (const cand_t *)pa, *b = (const cand_t *)pb;
+    if (a->dS > b->dS) return -1;
+    if (a->dS < b->dS) return 1;
+    return (a->s < b->s) ? -1 : (a->s > b->s);
+}
+
+/*
+ * Steps 6-9 on per-site fields fs (f*), fp (f'), dS (dS(f')) and the bad-site
+ * flags; writes f_out and accumulates the limiter sums into st.
+ */
+static void limit_core(const orc_config *cfg, unsigned limiters, const double *fs,
+                       const double *fp, const double *dS, const unsigned char *bad,
+                       double *f_out, double *phi_field, long long *sel, long long *n_sel,
+                       orc_stats *st)
+{
+    int q = nq(cfg->lattice);
+    int nx = cfg->nx;
+    long long n = (long long)cfg->nx * cfg->ny;
+    double *phi = (double *)malloc(sizeof(double) * (size_t)n);
+    double v[9];
+    for (long long s = 0; s < n; ++s) {
+        double phi_pos = 1.0, phi_med = 1.0;
+        if (!bad[s]) {
+            if (limiters & ORC_LIM_POSITIVITY) {
+                /* Sec. 3.1: move along {f* + lambda (f' - f*)} to the positivity boundary. */
+                for (int k = 0; k < q; ++k) {
+                    double fpk = fp[k * n + s], fsk = fs[k * n + s];
+                    if (fpk < 0.0) {
+                        double r = fsk / (fsk - fpk);
+                        if (r < phi_pos) phi_pos = r;
+                    }
+                }
+            }
+            if (limiters & ORC_LIM_MEDIAN) {
+                int m = median_stencil(cfg, dS, (int)(s % nx), (int)(s / nx), v);
+                if (m > 0) {
+                    sort_small(v, m);
+                    double med = v[m / 2];
+                    double x = dS[s];
+                    if (cfg->median_mode == ORC_MEDIAN_GATE) {
+                        if (x > cfg->delta_median && med < x) phi_med = sqrt(med / x);
+                    } else {
+                        double t = med > cfg->delta_median ? med : cfg->delta_median;
+                        if (x > t) phi_med = sqrt(t / x);
+                    }
+                }
+            }
+        }
+        double p = phi_pos < phi_med ? phi_pos : phi_med;
+        phi[s] = p;
+        if (phi_pos < 1.0) st->n_pos++;
+        if (phi_med < 1.0) st->n_med++;
+        if (p < 1.0) {
+            for (int k = 0; k < q; ++k) {
+                double fsk = fs[k * n + s];
+                f_out[k * n + s] = fsk + p * (fp[k * n + s] - fsk);
+            }
+            st->dS_lim += (1.0 - p * p) * dS[s];
+        } else {
+            /* phi = 1 is the identity: the post-collision state is stored as is. */
+            for (int k = 0; k < q; ++k) f_out[k * n + s] = fp[k * n + s];
+        }
+    }
+    if (phi_field)
+        for (long long s = 0; s < n; ++s) phi_field[s] = phi[s];
+
+    long long m_sel = 0;
+    if (limiters & ORC_LIM_EHRENFEST) {
+        cand_t *c = (cand_t *)malloc(sizeof(cand_t) * (size_t)(n > 0 ? n : 1));
+        long long nc = 0;
+        for (long long s = 0; s < n; ++s) {
+            if (!bad[s] && dS[s] > cfg->delta_ehrenfest) {
+                c[nc].dS = dS[s];
+                c[nc].s = s;
+                nc++;
+            }
+        }
+        st->n_cand += nc;
+        qsort(c, (size_t)nc, sizeof(cand_t), cand_cmp);
+        m_sel = nc < cfg->k_max ? nc : cfg->k_max;
+        if (m_sel < 0) m_sel = 0;
+        double fl[9], feq[9], r, a, b;
+        for (long long t = 0; t < m_sel; ++t) {
+            long long s = c[t].s;
+            /* Ehrenfests' step: equilibrate the limited state at s, f -> f*(m(f)). */
+            for (int k = 0; k < q; ++k) fl[k] = f_out[k * n + s];
+            orc_site_moments(cfg->lattice, fl, &r, &a, &b);
+            orc_feq(cfg->lattice, r, a, b, feq);
+            for (int k = 0; k < q; ++k) f_out[k * n + s] = feq[k];
+            st->dS_lim += (phi[s] * phi[s]) * dS[s];
+            st->n_ehr++;
+            if (sel) sel[t] = s;
+        }
+        free(c);
+    }
+    if (n_sel) *n_sel = m_sel;
+    free(phi);
+}
+
+static int run_collide_and_limit(const orc_config *cfg, unsigned limiters, int do_stream,
+                                 const double *f_st, double *f_out, double *dS_field,
+                                 double *phi_field, long long *sel, long long *n_sel,
+                                 orc_stats *stats)
+{
+    int q = nq(cfg->lattice);
+    int nx = cfg->nx, ny = cfg->ny;
+    long long n = (long long)nx * ny;
+    double *fs = (double *)malloc(sizeof(double) * (size_t)(q * n));
+    double *fp = (double *)malloc(sizeof(double) * (size_t)(q * n));
+    double *dS = (double *)malloc(sizeof(double) * (size_t)n);
+    unsigned char *bad = (unsigned char *)malloc((size_t)n);
+    orc_stats st;
+    memset(&st, 0, sizeof(st));
+    double a = 2.0 * cfg->beta - 1.0;
+    double sum_in = 0.0;
+    double fin[9], fsl[9], fpl[9];
+    for (int j = 0; j < ny; ++j) {
+        for (int i = 0; i < nx; ++i) {
+            long long s = (long long)j * nx + i;
+            double rho, ds, dsi;
+            int b;
+            if (do_stream) {
+                pull(cfg, f_st, i, j, fin);
+                b = site_collide(cfg, fin, fsl, fpl, &ds, &dsi, &rho);
+            } else {
+                /* Limiter pass on the stored state: f' := f, f* := f*(m(f)). */
+                double ux, uy;
+                for (int k = 0; k < q; ++k) fin[k] = f_st[k * n + s];
+                orc_site_moments(cfg->lattice, fin, &rho, &ux, &uy);
+                orc_feq(cfg->lattice, rho, ux, uy, fsl);
+                b = !(rho > 0.0) || !isfinite(rho) || !isfinite(ux) || !isfinite(uy);
+                for (int k = 0; k < q; ++k) {
+                    fpl[k] = fin[k];
+                    if (!(fsl[k] > 0.0) || !isfinite(fin[k])) b = 1;
+                }
+                ds = 0.0;
+                for (int k = 0; k < q; ++k) {
+                    double d = fpl[k] - fsl[k];
+                    ds += (d * d) / fsl[k];
+                }
+                if (!isfinite(ds)) b = 1;
+                if (b) ds = INFINITY;
+                dsi = 0.0;
+            }
+            for (int k = 0; k < q; ++k) {
+                fs[k * n + s] = fsl[k];
+                fp[k * n + s] = fpl[k];
+            }
+            dS[s] = ds;
+            bad[s] = (unsigned char)b;
+            st.mass += rho;
+            if (!b) {
+                st.sum_dS += ds;
+                sum_in += dsi;
+            } else {
+                st.n_bad++;
+            }
+        }
+    }
+    st.dS_lbgk = do_stream ? (1.0 - a * a) * sum_in : 0.0;
+    limit_core(cfg, limiters, fs, fp, dS, bad, f_out, phi_field, sel, n_sel, &st);
+    if (dS_field) memcpy(dS_field, dS, sizeof(double) * (size_t)n);
+    if (stats) *stats = st;
+    free(fs);
+    free(fp);
+    free(dS);
+    free(bad);
+    return st.n_bad > 0;
+}
+
+int orc_step(const orc_config *cfg, const double *f_st, double *f_out, double *dS_field,
+             double *phi_field, long long *sel, long long *n_sel, orc_stats *stats)
+{
+    return run_collide_and_limit(cfg, cfg->limiters, 1, f_st, f_out, dS_field, phi_field, sel,
+                                 n_sel, stats);
+}
+
+int orc_limit(const orc_config *cfg, unsigned limiters, const double *f_st, double *f_out,
+              double *dS_field, double *phi_field, long long *sel, long long *n_sel,
+              orc_stats *stats)
+{
+    return run_collide_and_limit(cfg, limiters, 0, f_st, f_out, dS_field, phi_field, sel, n_sel,
+                                 stats);
+}
+
+int orc_run(const orc_config *cfg, double *f, long long nsteps, orc_stats *stats)
+{
+    int q = nq(cfg->lattice);
+    long long n = (long long)cfg->nx * cfg->ny;
+    double *g = (double *)malloc(sizeof(double) * (size_t)(q * n));
+    double *cur = f, *nxt = g;
+    int rc = 0;
+    for (long long t = 0; t < nsteps; ++t) {
+        rc |= orc_step(cfg, cur, nxt, NULL, NULL, NULL, NULL, stats);
+        double *tmp = cur;
+        cur = nxt;
+        nxt = tmp;
+    }
+    if (cur != f) memcpy(f, cur, sizeof(double) * (size_t)(q * n));
+    free(g);
+    return rc;
+}
+
+int orc_delta_s(const orc_config *cfg, const double *f_st, double *dS_field)
+{
+    int q = nq(cfg->lattice);
+    int nx = cfg->nx, ny = cfg->ny;
+    double fin[9], fs[9], fp[9], rho, ds, dsi;
+    int rc = 0;
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            pull(cfg, f_st, i, j, fin);
+            rc |= site_collide(cfg, fin, fs, fp, &ds, &dsi, &rho);
+            dS_field[(long long)j * nx + i] = ds;
+        }
+    (void)q;
+    return rc;
+}

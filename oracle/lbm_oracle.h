@@ -1,0 +1,117 @@
+/*
+ * lbm_oracle.h -- FP64 CPU oracle for the entropy-limited LBGK step.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference leg of bench.py may load or call this code.  It
+ * shares no source, header, table or constant with the CUDA library
+ * (include/lbm.h, paper_0704_0043_gb300/csrc/); neither side includes or
+ * links the other.
+ *
+ * What it computes (Brownlee, Gorban, Levesley, "Nonequilibrium entropy
+ * limiters in lattice Boltzmann methods", Physica A 2007):
+ *   - free flight (Sec. 2) in pull form with halfway bounce-back walls and a
+ *     moving lid (Sec. 4.4.1),
+ *   - moments (Eq. macro_dis), polynomial quasiequilibria (Eq. polyeq1d,
+ *     Eq. polyeq2d),
+ *   - the LBGK collision with over-relaxation (Eq. collLBGK, Eq. lbgkLB),
+ *   - the nonequilibrium entropy in its quadratic Kullback form (Eq. DelS
+ *     and the quadratic approximation that follows it in Sec. 3.6),
+ *   - the limiters f -> f* + phi (f - f*) (Eq. LimGenF): the positivity rule
+ *     (Sec. 3.1), the entropic median filter (Sec. 3.5, Sec. 4.3.2, Sec. 4.4)
+ *     and Ehrenfests' trimming with at most k sites per step (Sec. 3.2),
+ *   - the dissipation monitors of Sec. 3.4 and Sec. 4.3.1.
+ * Every operation is plain IEEE double arithmetic, evaluated left to right,
+ * with no contraction into FMA (build with -ffp-contract=off).
+ *
+ * Population layout: plane-major, f[k * ny * nx + j * nx + i] for direction
+ * k, row j (y, upward) and column i (x).  D1Q3 uses ny = 1.
+ */
+#ifndef LBM_ORACLE_H
+#define LBM_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORC_D1Q3 1
+#define ORC_D2Q9 2
+
+#define ORC_BC_WALLS 0    /* D2Q9: cavity (three still walls, lid on top); D1Q3: closed tube ends */
+#define ORC_BC_PERIODIC 1 /* periodic in every direction */
+#define ORC_BC_CHANNEL 2  /* D2Q9: periodic in x, still wall at the bottom, lid on top */
+
+#define ORC_LIM_POSITIVITY 1u
+#define ORC_LIM_EHRENFEST 2u
+#define ORC_LIM_MEDIAN 4u
+
+#define ORC_MEDIAN_THRESHOLD 0 /* dS_t = max(dS_med, delta); phi = sqrt(dS_t/dS) where dS > dS_t */
+#define ORC_MEDIAN_GATE 1      /* phi = sqrt(dS_med/dS) where dS > delta and dS_med < dS */
+
+typedef struct {
+    int lattice;            /* ORC_D1Q3 or ORC_D2Q9 */
+    int nx, ny;             /* lattice size; ny = 1 for D1Q3 */
+    int boundary;           /* ORC_BC_* */
+    double beta;            /* LBGK over-relaxation parameter, Eq. collLBGK */
+    double u_lid;           /* lid x-velocity (D2Q9 top wall) */
+    double rho_wall;        /* density used in the moving-wall term */
+    unsigned limiters;      /* ORC_LIM_* bit set */
+    double delta_median;    /* median-filter tolerance */
+    double delta_ehrenfest; /* Ehrenfests' threshold */
+    long long k_max;        /* at most this many Ehrenfests' sites per step */
+    int median_mode;        /* ORC_MEDIAN_* */
+} orc_config;
+
+typedef struct {
+    double mass;      /* sum of rho over sites (after free flight) */
+    double sum_dS;    /* sum of dS(f') over sites, f' = post-collision, pre-limiter */
+    double dS_lbgk;   /* [1 - (2 beta - 1)^2] * sum of dS(f_in), Sec. 3.4 */
+    double dS_lim;    /* entropy added by the limiters, quadratic approximation */
+    long long n_pos;  /* sites where the positivity rule acted (phi_pos < 1) */
+    long long n_med;  /* sites where the median filter acted (phi_med < 1) */
+    long long n_ehr;  /* sites equilibrated by Ehrenfests' step */
+    long long n_cand; /* sites with dS(f') > delta_ehrenfest */
+    long long n_bad;  /* sites with rho <= 0, a nonpositive f*_i or a nonfinite value */
+} orc_stats;
+
+/* Polynomial quasiequilibrium f*(rho, u) at one site (Eq. polyeq1d / Eq. polyeq2d). */
+void orc_feq(int lattice, double rho, double ux, double uy, double *feq);
+
+/* Moments rho, u of one site's populations (Eq. macro_dis). */
+void orc_site_moments(int lattice, const double *f, double *rho, double *ux, double *uy);
+
+/* f = f*(rho(x), u(x)) for every site.  uy may be NULL for D1Q3. */
+void orc_init(const orc_config *cfg, const double *rho, const double *ux, const double *uy, double *f);
+
+/* Moments of every site of a stored field.  uy may be NULL for D1Q3. */
+void orc_moments(const orc_config *cfg, const double *f, double *rho, double *ux, double *uy);
+
+/*
+ * One limited LBGK step: free flight, collision, limiters, store.
+ * f_st: stored field (input), f_out: next stored field (may not alias f_st).
+ * Optional outputs (NULL to skip): dS_field = dS(f') per site (pre-limiter),
+ * phi_field = final phi per site before Ehrenfests' step, sel / n_sel = the
+ * sites Ehrenfests' step equilibrated, in selection order (sel needs room for
+ * min(k_max, sites) entries), stats.
+ * Returns 0, or 1 if any site was flagged (n_bad > 0).
+ */
+int orc_step(const orc_config *cfg, const double *f_st, double *f_out, double *dS_field,
+             double *phi_field, long long *sel, long long *n_sel, orc_stats *stats);
+
+/* nsteps steps in place (ping-pong through an internal buffer); stats of the last step. */
+int orc_run(const orc_config *cfg, double *f, long long nsteps, orc_stats *stats);
+
+/* dS(f') of the collision the next step would perform, without limiters. */
+int orc_delta_s(const orc_config *cfg, const double *f_st, double *dS_field);
+
+/*
+ * Limiters applied to the stored field itself (no free flight, no collision):
+ * f' := f_st, f* := f*(m(f_st)).  Same optional outputs as orc_step.
+ */
+int orc_limit(const orc_config *cfg, unsigned limiters, const double *f_st, double *f_out,
+              double *dS_field, double *phi_field, long long *sel, long long *n_sel,
+              orc_stats *stats);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
