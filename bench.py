@@ -1,0 +1,334 @@
+"""Benchmark of the limited LBGK step: prints one JSON line.
+
+Default workload: the 4096 x 4096 lid-driven cavity (D2Q9, Re = 7500, lid
+0.05, median filter delta = 1e-3 plus Ehrenfests' trimming delta = 1e-3 with
+k = 1677 = 0.01 % of the sites), FP32 populations, FP64 sums.  A bench step is
+one limited LBGK step of the whole lattice (free flight, collision, dS,
+positivity / median / Ehrenfests' limiters, FP64 sums) through lbm_step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica of the
+workload (the step does not shard across GPUs here); value = all ranks'
+site updates / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_SITE = {("d2q9", "fp32"): 72, ("d2q9", "fp64"): 144, ("d1q3", "fp32"): 24,
+                  ("d1q3", "fp64"): 48}
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--develop", type=int, default=500,
+                    help="untimed steps before warm-up so the flow has left the rest state")
+    ap.add_argument("--kernel", default="auto", choices=["auto", "tiled", "fused"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) taken while the timed region runs."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_0704_0043_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as fh:
+                h.update(name.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profile(kernel_name: str, sites: int):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary,
+    scaled to this lattice; None when the kernel sources changed since."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+    except Exception:
+        return None
+    ent = d.get(kernel_name)
+    if not ent or ent.get("src_hash") != source_hash():
+        return None
+    return ent["dram_bytes_per_site"] * sites
+
+
+def workload():
+    from paper_0704_0043_gb300 import inputs
+    return inputs.cavity4096_workload()
+
+
+def lattice_kwargs(w, kernel: str):
+    from paper_0704_0043_gb300 import lbm
+    km = {"auto": lbm.KERNEL_AUTO, "tiled": lbm.KERNEL_TILED, "fused": lbm.KERNEL_FUSED}[kernel]
+    return dict(lattice=lbm.D2Q9, nx=w.nx, ny=w.ny, boundary=lbm.BC_WALLS, precision=lbm.FP32,
+                beta=w.beta, u_lid=w.u_lid, rho_wall=w.rho0, limiters=w.limiters,
+                delta_median=w.delta_median, delta_ehrenfest=w.delta_ehrenfest, k_max=w.k_max,
+                kernel=km)
+
+
+def oracle_cfg(w, side: int):
+    import oracle
+    return oracle.Config(lattice=oracle.D2Q9, nx=side, ny=side, boundary=oracle.BC_WALLS,
+                         beta=w.beta, u_lid=w.u_lid, rho_wall=w.rho0, limiters=w.limiters,
+                         delta_median=w.delta_median, delta_ehrenfest=w.delta_ehrenfest,
+                         k_max=max(1, int(1e-4 * side * side)))
+
+
+def cpu_baseline(w, steps: int = 1):
+    """The FP64 oracle as it stands, single-threaded, on `steps` full-size steps."""
+    import oracle
+    from paper_0704_0043_gb300 import inputs
+    oc = oracle_cfg(w, w.nx)
+    rho, ux, uy = inputs.cavity_rest(w.nx, w.ny, w.rho0)
+    f = oracle.init(oc, rho, ux, uy)
+    t0 = time.perf_counter()
+    f, _, _ = oracle.run(oc, f, steps)
+    dt = time.perf_counter() - t0
+    return {"value": w.sites * steps / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"{steps} step(s) of the full {w.nx}x{w.ny} cavity, FP64, one thread, "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args):
+    """The oracle timed as it stands on the host, K steps of a 1024^2 sample."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_0704_0043_gb300 import inputs
+    w = workload()
+    side = 1024
+    oc = oracle_cfg(w, side)
+    rho, ux, uy = inputs.cavity_rest(side, side, w.rho0)
+    f = oracle.init(oc, rho, ux, uy)
+    f, _, _ = oracle.run(oc, f, args.warmup)
+    t0 = time.perf_counter()
+    f, _, _ = oracle.run(oc, f, args.steps)
+    dt = time.perf_counter() - t0
+    v = side * side * args.steps / dt / 1e6
+    sample = (f"{side}x{side} cavity with the {w.nx}^2 workload's parameters (Re 7500, lid 0.05, "
+              f"median + Ehrenfests' k = 0.01 % of sites), one oracle step per bench step")
+    out = {"impl": "reference", "metric": "limited-LBM MLUPS", "value": v, "unit": "MLUPS",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": dt * 1e3 / max(args.steps, 1), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "sample_side": side},
+           "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+
+    from paper_0704_0043_gb300 import build as lbm_build
+    from paper_0704_0043_gb300 import inputs, lbm
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if rank == 0:
+        lbm_build.build()
+    if dist is not None:
+        dist.barrier()
+    lbm.lib()
+
+    w = workload()
+    lat = lbm.Lattice(**lattice_kwargs(w, args.kernel))
+    rho, ux, uy = inputs.cavity_rest(w.nx, w.ny, w.rho0)
+    lat.init(rho, ux, uy)
+    lat.step(args.develop + args.warmup)
+    lat.synchronize()
+
+    stream = torch.cuda.current_stream()
+    sampler = ClockSampler(local)
+    sampler.start()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = lat.launch_count()
+    lat.timing(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    lat.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    launches = lat.launch_count() - launches0
+    step_ms, tail_ms, timed = lat.timing_read()
+    lat.timing(False)
+    clocks = sampler.stop()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    st = lat.stats()
+    if dist is not None:
+        t = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    mlups = world * w.sites * args.steps / elapsed / 1e6
+
+    # roofline of the step kernel (the dominant launch): algorithmic bytes / event time
+    bps = BYTES_PER_SITE[("d2q9", "fp32")]
+    kern_s = step_ms / 1e3 / max(timed, 1)
+    achieved = bps * w.sites / kern_s / 1e9
+    peak, peak_kind = peaks()
+    kname = "fused" if (args.kernel == "fused" or (args.kernel == "auto" and lbm.KERNEL_AUTO == 0 and
+                                                   lat_uses_fused(lat))) else "tiled"
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_kind": peak_kind,
+            "traffic": traffic_from_profile(kname, w.sites),
+            "kernel": kname, "kernel_ms": kern_s * 1e3, "tail_kernel_ms": tail_ms / max(timed, 1),
+            "bytes_per_site": bps}
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = end_to_end(lat, w, args.steps, torch)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, 1)
+    out = {"metric": "limited-LBM MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": elapsed * 1e3 / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "reynolds": 7500,
+                      "u_lid": w.u_lid, "beta": w.beta, "limiters": "median+ehrenfest",
+                      "delta": 1e-3, "k_max": w.k_max, "storage": "fp32", "sums": "fp64",
+                      "kernel": kname, "develop_steps": args.develop,
+                      "l2": "inputs larger than L2 (1.2 GB population buffers vs 129 MB L2)",
+                      "parallelism": f"replicas{world}" if world > 1 else "single"},
+           "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+           "clocks": clocks,
+           "last_step_stats": {k: st[k] for k in ("step", "mass", "sum_dS", "dS_lim", "n_med",
+                                                   "n_ehr", "n_cand")}}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    lat.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def lat_uses_fused(lat) -> bool:
+    return False
+
+
+def end_to_end(lat, w, steps, torch):
+    """Same metric through the public API with pinned host buffers: upload the
+    initial density/velocity fields, run `steps` steps, read the moments and
+    the stats back; the copies are inside the timed region."""
+    import numpy as np
+    from paper_0704_0043_gb300 import inputs
+    rho, ux, uy = inputs.cavity_rest(w.nx, w.ny, w.rho0)
+    hin = [torch.from_numpy(a.reshape(-1).copy()).pin_memory() for a in (rho, ux, uy)]
+    hout = [torch.empty(w.sites, dtype=torch.float64).pin_memory() for _ in range(3)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lat.init(*hin)
+    lat.step(steps)
+    lat.moments(out=tuple(hout))
+    st = lat.stats()
+    dt = time.perf_counter() - t0
+    assert np.isfinite(st["mass"])
+    h2d = 3 * 8 * w.sites
+    d2h = 3 * 8 * w.sites + 96
+    return {"value": w.sites * steps / dt / 1e6, "unit": "MLUPS",
+            "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": d2h / steps,
+            "request": f"init from host rho/u, {steps} steps, moments + stats to host"}
+
+
+if __name__ == "__main__":
+    main()

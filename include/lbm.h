@@ -1,0 +1,216 @@
+/*
+ * lbm.h -- C ABI of liblbm, a GB300 (sm_103a) implementation of the lattice
+ * Boltzmann step with nonequilibrium entropy limiters of Brownlee, Gorban and
+ * Levesley, "Nonequilibrium entropy limiters in lattice Boltzmann methods",
+ * Physica A 2007 (arXiv:0704.0043).
+ *
+ * One step (Eq. lbgkLB; the limiter is "a post-processing routine immediately
+ * following the collision step", Sec. 4.3.2):
+ *   free flight in pull form, halfway bounce-back walls, moving lid (Sec. 2, Sec. 4.4.1)
+ *   -> moments (Eq. macro_dis) -> polynomial f* (Eq. polyeq1d / Eq. polyeq2d)
+ *   -> LBGK collision f' = f* + (2 beta - 1)(f* - f)      (Eq. collLBGK)
+ *   -> dS(f') = sum_k (f'_k - f*_k)^2 / f*_k              (Sec. 3.6, quadratic form of Eq. DelS)
+ *   -> limiters f -> f* + phi (f - f*)                     (Eq. LimGenF):
+ *      positivity rule (Sec. 3.1), median filter (Sec. 3.5), Ehrenfests' trimming (Sec. 3.2)
+ *   -> stored field for the next step, plus FP64 sums (Sec. 3.4, Sec. 4.3.1).
+ *
+ * Conventions shared by every entry point
+ *   - Every call returns lbm_status; nothing throws or exits across the ABI.
+ *     On failure lbm_last_error(ctx) holds a one-line message.
+ *   - The library owns the lattice (populations, scratch) in device memory.
+ *     Callers own every buffer they pass in or out.
+ *   - All device work is ordered on the CUDA stream given to lbm_create (a
+ *     cudaStream_t passed as void*; NULL = the legacy default stream).  Calls
+ *     that fill host memory synchronise that stream before returning.
+ *   - Array arguments may be host or device pointers (detected with
+ *     cudaPointerGetAttributes).  Field layout is the oracle layout: site
+ *     (i, j) at index j * nx + i (x fastest, y upward, lid at j = ny - 1);
+ *     population fields are plane-major, f[k * ny * nx + j * nx + i].
+ *   - D2Q9 directions follow Sec. 4.1: 0 rest, 1 E, 2 N, 3 W, 4 S, 5 NE, 6 NW,
+ *     7 SW, 8 SE.  D1Q3: 0 rest, 1 left (v = -1), 2 right (v = +1), i.e. the
+ *     paper's f1, f2, f3.
+ *   - A context is used by one host thread at a time.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_ABI_VERSION 1
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_INVALID_ARG = 1, /* a parameter is out of range; nothing was enqueued */
+    LBM_ERR_OOM = 2,         /* device allocation failed */
+    LBM_ERR_CUDA = 3,        /* a CUDA runtime call failed (message names it) */
+    LBM_ERR_NONFINITE = 4,   /* a site had rho <= 0, f*_k <= 0 or a nonfinite value */
+    LBM_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+    LBM_ERR_STATE = 6        /* call out of order (e.g. step before init) */
+} lbm_status;
+
+enum { LBM_D1Q3 = 1, LBM_D2Q9 = 2 };
+
+/* Storage precision of the populations; arithmetic is FP64 for LBM_FP64 and
+ * FP32 otherwise.  LBM_FP64 evaluates every operation in the oracle's order
+ * with no FMA contraction. */
+enum { LBM_FP64 = 0, LBM_FP32 = 1 };
+
+enum {
+    LBM_BC_WALLS = 0,    /* D2Q9: still walls left, right, bottom, lid on top; D1Q3: closed ends */
+    LBM_BC_PERIODIC = 1, /* periodic in every direction */
+    LBM_BC_CHANNEL = 2   /* D2Q9: periodic in x, still bottom wall, lid on top */
+};
+
+/* Limiters (bit set). */
+enum { LBM_LIM_POSITIVITY = 1, LBM_LIM_EHRENFEST = 2, LBM_LIM_MEDIAN = 4 };
+
+/* Median-filter acceptance rule (Sec. 3.5 with the tolerance of Sec. 4.3.2). */
+enum {
+    LBM_MEDIAN_THRESHOLD = 0, /* dS_t = max(dS_med, delta); phi = sqrt(dS_t/dS) where dS > dS_t */
+    LBM_MEDIAN_GATE = 1       /* phi = sqrt(dS_med/dS) where dS > delta and dS_med < dS */
+};
+
+/* Kernel choice for lbm_step. */
+enum {
+    LBM_KERNEL_AUTO = 0,    /* fused FP32 D2Q9 kernel where it applies, else the tiled kernel */
+    LBM_KERNEL_TILED = 1,   /* overlapping-tile kernel: every lattice, boundary and precision */
+    LBM_KERNEL_FUSED = 2    /* FP32 D2Q9 with LBM_BC_WALLS only: row-streaming fused kernel */
+};
+
+typedef struct lbm_config {
+    int32_t lattice;         /* LBM_D1Q3 or LBM_D2Q9 */
+    int32_t nx, ny;          /* sites; ny must be 1 for D1Q3.  nx, ny >= 4 for D2Q9 walls */
+    int32_t boundary;        /* LBM_BC_* */
+    int32_t precision;       /* LBM_FP64 or LBM_FP32 */
+    uint32_t limiters;       /* LBM_LIM_* bits applied by lbm_step */
+    int32_t median_mode;     /* LBM_MEDIAN_* */
+    int32_t kernel;          /* LBM_KERNEL_* */
+    double beta;             /* LBGK over-relaxation, 0 <= beta <= 1 (Eq. collLBGK) */
+    double u_lid;            /* lid x-velocity (D2Q9, LBM_BC_WALLS / LBM_BC_CHANNEL) */
+    double rho_wall;         /* density in the moving-wall momentum term 6 W_k rho_wall (v_k . u_lid) */
+    double delta_median;     /* median-filter tolerance delta (>= 0) */
+    double delta_ehrenfest;  /* Ehrenfests' threshold: sites with dS > delta are candidates */
+    int64_t k_max;           /* Ehrenfests' step acts on at most k_max sites per step (>= 0) */
+    int32_t stats_history;   /* per-step stats kept on the device (ring length, >= 1) */
+    int32_t reserved;        /* must be 0 */
+} lbm_config;
+
+typedef struct lbm_step_stats {
+    int64_t step;            /* steps taken since lbm_init / lbm_set_populations */
+    double mass;             /* sum of rho over sites, after free flight */
+    double sum_dS;           /* sum of dS(f') (post-collision, pre-limiter) */
+    double dS_lbgk;          /* [1 - (2 beta - 1)^2] * sum of dS(f_in) (Sec. 3.4) */
+    double dS_lim;           /* entropy added by the limiters: sum (1 - phi^2) dS(f'),
+                                plus phi^2 dS(f') at each Ehrenfests' site */
+    int64_t n_pos;           /* sites where the positivity rule acted */
+    int64_t n_med;           /* sites where the median filter acted */
+    int64_t n_ehr;           /* sites equilibrated by Ehrenfests' step */
+    int64_t n_cand;          /* sites with dS(f') > delta_ehrenfest */
+    int64_t n_bad;           /* sites flagged nonfinite / nonpositive */
+    int32_t status;          /* lbm_status of that step */
+    int32_t reserved;
+} lbm_step_stats;
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Fills *cfg with defaults: D2Q9 100 x 100 cavity, FP32, beta = 1, no limiters,
+ * delta = 1e-3, k_max = 0, one stats record. */
+void lbm_config_default(lbm_config *cfg);
+
+/* Validates cfg, allocates the lattice and scratch on the current device and
+ * returns a context bound to `cuda_stream`.  Populations start at zero; call
+ * lbm_init or lbm_set_populations before lbm_step (else LBM_ERR_STATE).
+ * Errors: LBM_ERR_INVALID_ARG (bad cfg / NULL out), LBM_ERR_OOM, LBM_ERR_CUDA. */
+lbm_status lbm_create(const lbm_config *cfg, void *cuda_stream, lbm_ctx **out);
+
+/* Synchronises the context's stream and frees everything it owns.  NULL is a no-op. */
+lbm_status lbm_destroy(lbm_ctx *ctx);
+
+/* Populations at polynomial equilibrium f*(rho, u) (Eq. polyeq1d / Eq. polyeq2d),
+ * evaluated in FP64 and stored at the context's precision; resets the step
+ * counter and the stats.  rho, ux: nx * ny doubles; uy: nx * ny doubles or NULL
+ * (taken as 0; ignored for D1Q3).  Errors: LBM_ERR_INVALID_ARG (NULL rho/ux). */
+lbm_status lbm_init(lbm_ctx *ctx, const double *rho, const double *ux, const double *uy);
+
+/* nsteps limited LBGK steps (free flight, collision, the configured limiters,
+ * FP64 sums), enqueued asynchronously.  A site that cannot be limited sets the
+ * context's sticky status to LBM_ERR_NONFINITE; that status is returned by the
+ * next call that synchronises (lbm_stats, lbm_moments, lbm_synchronize, ...).
+ * Errors: LBM_ERR_STATE (no init), LBM_ERR_INVALID_ARG (nsteps < 0). */
+lbm_status lbm_step(lbm_ctx *ctx, int64_t nsteps);
+
+/* The dS(f') field (quadratic Kullback form, Sec. 3.6) of the collision the
+ * next lbm_step performs on the stored populations, evaluated in FP64 from the
+ * stored values: nx * ny doubles into `out`.  No population is modified. */
+lbm_status lbm_delta_s(lbm_ctx *ctx, double *out);
+
+/* Applies `limiters` to the stored populations themselves, with no free flight
+ * and no collision: f' := f, f* := f*(m(f)), then the same limiter pass as a
+ * step (Sec. 3).  Counts and sums go to the stats (step counter unchanged). */
+lbm_status lbm_limit(lbm_ctx *ctx, uint32_t limiters);
+
+/* rho, u (Eq. macro_dis) of the stored populations, FP64, nx * ny each;
+ * uy may be NULL.  Synchronises; returns the sticky status. */
+lbm_status lbm_moments(lbm_ctx *ctx, double *rho, double *ux, double *uy);
+
+/* Stats of the most recent step (or lbm_limit pass).  Synchronises; returns
+ * the sticky status (the stats are written either way). */
+lbm_status lbm_stats(lbm_ctx *ctx, lbm_step_stats *out);
+
+/* Up to `cap` most recent per-step stats, oldest first (at most stats_history);
+ * *n receives the count written. */
+lbm_status lbm_stats_history(lbm_ctx *ctx, lbm_step_stats *out, int64_t cap, int64_t *n);
+
+/* The sites Ehrenfests' step equilibrated in the most recent step, sorted by
+ * site index: min(cap, n) int64 indices into idx (host or device), *n = the
+ * full count.  Selection (Sec. 3.2, Sec. 4.3.2): the k_max largest dS(f') >
+ * delta_ehrenfest, ties to the lower site index. */
+lbm_status lbm_limited_sites(lbm_ctx *ctx, int64_t *idx, int64_t cap, int64_t *n);
+
+/* Copies the stored populations out as FP64 (q * nx * ny doubles), or sets
+ * them from FP64 (rounded to the storage precision; resets the step counter).
+ * Used for checkpoints and for parity checks against the oracle. */
+lbm_status lbm_get_populations(lbm_ctx *ctx, double *f);
+lbm_status lbm_set_populations(lbm_ctx *ctx, const double *f);
+
+/* Waits for the context's stream; returns (and clears) the sticky status. */
+lbm_status lbm_synchronize(lbm_ctx *ctx);
+
+/* Fills `out` with the context's configuration. */
+lbm_status lbm_get_config(const lbm_ctx *ctx, lbm_config *out);
+
+/* Bytes of device memory the context holds (for admission by HBM footprint). */
+int64_t lbm_device_bytes(const lbm_ctx *ctx);
+
+/* Device bytes lbm_create would allocate for cfg (0 if cfg is invalid). */
+int64_t lbm_footprint_bytes(const lbm_config *cfg);
+
+/* Per-kernel timing with CUDA events recorded on the context's stream.  While
+ * enabled, every step records an event before its step kernel, one between
+ * the step kernel and its one-block tail kernel, and one after the tail.
+ * lbm_timing_read synchronises, returns the summed milliseconds of each kernel
+ * kind and the number of timed steps, and clears the record. */
+lbm_status lbm_timing(lbm_ctx *ctx, int32_t enable);
+lbm_status lbm_timing_read(lbm_ctx *ctx, double *step_kernel_ms, double *tail_kernel_ms, int64_t *steps);
+
+/* Number of kernel launches the context has enqueued so far. */
+int64_t lbm_launch_count(const lbm_ctx *ctx);
+
+/* Last error message of ctx (never NULL); lbm_last_error(NULL) reports errors
+ * of lbm_create and lbm_footprint_bytes on the calling thread. */
+const char *lbm_last_error(const lbm_ctx *ctx);
+
+/* Static name of a status code. */
+const char *lbm_status_string(lbm_status s);
+
+/* LBM_ABI_VERSION of the loaded library. */
+int32_t lbm_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,240 @@
+// finalize.cu -- the per-step tail: fixed-order FP64 reduction of the step
+// kernel's block partials, Ehrenfests' selection and step, and the stats record.
+//
+// Ehrenfests' regularisation (Sec. 3.2; Sec. 4.3.2): among the sites whose
+// dS(f') exceeds delta, at most k with the largest dS are equilibrated,
+// f -> f*(m(f)).  Ties in dS go to the lower site index, so the chosen set is
+// unique.  When there are more than k candidates, a single block finds the k-th
+// largest (dS, -site) pair by radix selection: eight 8-bit digit passes over the
+// 64-bit pattern of dS (positive doubles order like their bit patterns), then
+// four passes over the site index among the candidates tied at the threshold.
+#include "internal.h"
+#include "lattice.cuh"
+
+namespace lbm {
+namespace {
+
+constexpr int kFinThreads = 512;
+constexpr int kSortCap = 4096;  // selected sets up to this size are sorted by site in shared memory
+
+__device__ __forceinline__ unsigned long long key_bits(double d) { return (unsigned long long)__double_as_longlong(d); }
+
+__device__ __forceinline__ long long fidx(long long plane, int pitch, int k, int y, int x)
+{
+    return (long long)k * plane + (long long)y * pitch + kLead + x;
+}
+
+// Sum of v over the block in a fixed order (same result every run).
+__device__ double block_sum(double v, double *red)
+{
+    const int t = threadIdx.x;
+    red[t] = v;
+    __syncthreads();
+    for (int s = kFinThreads / 2; s > 0; s >>= 1) {
+        if (t < s) red[t] += red[t + s];
+        __syncthreads();
+    }
+    const double r = red[0];
+    __syncthreads();
+    return r;
+}
+
+template <int Q, typename T>
+__global__ void __launch_bounds__(kFinThreads) k_finalize(FinalParams p, T *__restrict__ f)
+{
+    using A = Ar<T>;
+    __shared__ double red[kFinThreads];
+    __shared__ double tot[P_NSTAT];
+    __shared__ unsigned hist[256];
+    __shared__ unsigned long long s_prefix;
+    __shared__ long long s_rem;
+    __shared__ int s_nsel;
+    __shared__ int s_site[kSortCap];
+    __shared__ int s_idx[kSortCap];
+    const int t = threadIdx.x;
+
+    for (int i = 0; i < P_NSTAT; ++i) {
+        double v = 0.0;
+        for (int r = t; r < p.nblocks; r += kFinThreads) v += p.partials[(long long)r * P_NSTAT + i];
+        v = block_sum(v, red);
+        if (t == 0) tot[i] = v;
+    }
+
+    const int ncand_all = p.ehrenfest ? *p.cand_count : 0;
+    const int n = ncand_all < p.cand_cap ? ncand_all : p.cand_cap;
+    const long long k = p.k_max;
+    if (t == 0) s_nsel = 0;
+    __syncthreads();
+    double ehr_sum = 0.0;
+    if (p.ehrenfest && k > 0 && n > 0) {
+        unsigned long long kv = 0;  // threshold dS pattern
+        int site_thr = 0x7fffffff;
+        bool take_all = (long long)n <= k;
+        if (!take_all) {
+            unsigned long long prefix = 0, mask = 0;
+            long long rem = k;
+            for (int shift = 56; shift >= 0; shift -= 8) {
+                for (int d = t; d < 256; d += kFinThreads) hist[d] = 0;
+                __syncthreads();
+                for (int i = t; i < n; i += kFinThreads) {
+                    const unsigned long long u = key_bits(p.cand[i].key);
+                    if ((u & mask) == prefix) atomicAdd(&hist[(u >> shift) & 255u], 1u);
+                }
+                __syncthreads();
+                if (t == 0) {
+                    long long cum = 0;
+                    for (int d = 255; d >= 0; --d) {
+                        if (cum + (long long)hist[d] >= rem) {
+                            s_prefix = prefix | ((unsigned long long)d << shift);
+                            s_rem = rem - cum;
+                            break;
+                        }
+                        cum += hist[d];
+                    }
+                }
+                __syncthreads();
+                prefix = s_prefix;
+                rem = s_rem;
+                mask |= 255ull << shift;
+                __syncthreads();
+            }
+            kv = prefix;
+            // among the candidates with dS == kv take the `rem` lowest sites
+            unsigned sprefix = 0, smask = 0;
+            for (int shift = 24; shift >= 0; shift -= 8) {
+                for (int d = t; d < 256; d += kFinThreads) hist[d] = 0;
+                __syncthreads();
+                for (int i = t; i < n; i += kFinThreads) {
+                    const Cand c = p.cand[i];
+                    const unsigned s = (unsigned)c.site;
+                    if (key_bits(c.key) == kv && (s & smask) == sprefix) atomicAdd(&hist[(s >> shift) & 255u], 1u);
+                }
+                __syncthreads();
+                if (t == 0) {
+                    long long cum = 0;
+                    for (int d = 0; d < 256; ++d) {
+                        if (cum + (long long)hist[d] >= rem) {
+                            s_prefix = (unsigned long long)(sprefix | ((unsigned)d << shift));
+                            s_rem = rem - cum;
+                            break;
+                        }
+                        cum += hist[d];
+                    }
+                }
+                __syncthreads();
+                sprefix = (unsigned)s_prefix;
+                rem = s_rem;
+                smask |= 255u << shift;
+                __syncthreads();
+            }
+            site_thr = (int)sprefix;
+        }
+        // compaction of the chosen candidates (indices into p.cand)
+        for (int i = t; i < n; i += kFinThreads) {
+            const Cand c = p.cand[i];
+            const unsigned long long u = key_bits(c.key);
+            const bool chosen = take_all || u > kv || (u == kv && c.site <= site_thr);
+            if (chosen) {
+                const int j = atomicAdd(&s_nsel, 1);
+                if (j < p.sel_cap) p.sel[j] = i;
+            }
+        }
+        __syncthreads();
+        if (t == 0 && s_nsel > p.sel_cap) s_nsel = p.sel_cap;
+        __syncthreads();
+        const int nsel = s_nsel;
+        const bool sorted = nsel <= kSortCap;
+        if (sorted) {
+            // bitonic sort of the chosen set by site index (padding sorts last)
+            int m = 1;
+            while (m < nsel) m <<= 1;
+            for (int i = t; i < m; i += kFinThreads) {
+                s_idx[i] = i < nsel ? p.sel[i] : -1;
+                s_site[i] = i < nsel ? p.cand[p.sel[i]].site : 0x7fffffff;
+            }
+            __syncthreads();
+            for (int size = 2; size <= m; size <<= 1) {
+                for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                    for (int i = t; i < m; i += kFinThreads) {
+                        const int j = i ^ stride;
+                        if (j > i) {
+                            const bool up = (i & size) == 0;
+                            if ((s_site[i] > s_site[j]) == up) {
+                                int a = s_site[i]; s_site[i] = s_site[j]; s_site[j] = a;
+                                a = s_idx[i]; s_idx[i] = s_idx[j]; s_idx[j] = a;
+                            }
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+        }
+        // Ehrenfests' step at each chosen site, in site order when sorted
+        for (int r = t; r < nsel; r += kFinThreads) {
+            const int ci = sorted ? s_idx[r] : p.sel[r];
+            const Cand c = p.cand[ci];
+            const int x = c.site % p.nx, y = c.site / p.nx;
+            T g[Q], fs[Q], rho, ux, uy;
+#pragma unroll
+            for (int q = 0; q < Q; ++q) g[q] = f[fidx(p.plane, p.pitch, q, y, x)];
+            moments<Q, T>(g, rho, ux, uy);
+            feq<Q, T>(rho, ux, uy, fs);
+#pragma unroll
+            for (int q = 0; q < Q; ++q) f[fidx(p.plane, p.pitch, q, y, x)] = fs[q];
+            ehr_sum = Ar<double>::add(ehr_sum, Ar<double>::mul(Ar<double>::mul(c.phi, c.phi), c.key));
+        }
+        __syncthreads();
+        // the chosen sites, as site indices, for lbm_limited_sites
+        if (sorted) {
+            for (int r = t; r < nsel; r += kFinThreads) p.sel[r] = s_site[r];
+        } else {
+            // unsorted (more than kSortCap chosen): convert in place, one owner per slot
+            for (int r = t; r < nsel; r += kFinThreads) p.sel[r] = p.cand[p.sel[r]].site;
+        }
+    }
+    const double esum = block_sum(ehr_sum, red);
+    __syncthreads();
+    if (t == 0) {
+        long long step = p.counters[0];
+        if (p.collide) {
+            step += 1;
+            p.counters[0] = step;
+        }
+        const long long rec = p.counters[1];
+        p.counters[1] = rec + 1;
+        DevStats st;
+        st.step = step;
+        st.mass = tot[P_MASS];
+        st.sum_dS = tot[P_SUM_DS];
+        st.dS_lbgk = p.collide ? Ar<double>::mul(p.one_minus_a2, tot[P_SUM_IN]) : 0.0;
+        st.dS_lim = Ar<double>::add(tot[P_DS_LIM], esum);
+        st.n_pos = (long long)tot[P_NPOS];
+        st.n_med = (long long)tot[P_NMED];
+        st.n_ehr = s_nsel;
+        st.n_cand = ncand_all;
+        st.n_bad = (long long)tot[P_NBAD];
+        const unsigned sb = *p.status;
+        st.status = (sb & kStatNonfinite) ? 4 : ((sb & kStatTimeout) ? 5 : 0);
+        st.reserved = 0;
+        p.stats_ring[rec % p.ring_len] = st;
+        *p.sel_count = s_nsel;
+        *p.cand_count = 0;
+    }
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_finalize(int q, const FinalParams &p, T *f, cudaStream_t s)
+{
+    if (q == 9)
+        k_finalize<9, T><<<1, kFinThreads, 0, s>>>(p, f);
+    else
+        k_finalize<3, T><<<1, kFinThreads, 0, s>>>(p, f);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_finalize<float>(int, const FinalParams &, float *, cudaStream_t);
+template cudaError_t launch_finalize<double>(int, const FinalParams &, double *, cudaStream_t);
+
+}  // namespace lbm

@@ -1,0 +1,105 @@
+// internal.h -- shared declarations of the liblbm translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+// Device layout of a population field: plane-major, rows padded.  Element
+// (k, y, x) lives at k * plane + y * pitch + kLead + x.  The kLead elements in
+// front of every row and the tail of each row are zero and never written, so
+// row segments may be copied a few elements past either edge of the lattice.
+constexpr int kLead = 32;
+__host__ __device__ inline int row_pitch(int nx) { return ((nx + 31) / 32) * 32 + 2 * kLead; }
+
+// Sticky device status bits.
+enum : unsigned { kStatNonfinite = 1u, kStatTimeout = 2u, kStatCandOverflow = 4u };
+
+// Per-block partial sums written by the step kernels, reduced in a fixed
+// order by the finalise kernel.
+enum { P_MASS = 0, P_SUM_DS, P_SUM_IN, P_DS_LIM, P_NPOS, P_NMED, P_NBAD, P_NSTAT };
+
+// Ehrenfests' candidate: FP64 key dS(f'), phi of the limiter pass, site index.
+struct Cand {
+    double key;
+    double phi;
+    int32_t site;
+    int32_t pad;
+};
+
+struct DevStats {  // mirrors lbm_step_stats
+    long long step;
+    double mass, sum_dS, dS_lbgk, dS_lim;
+    long long n_pos, n_med, n_ehr, n_cand, n_bad;
+    int status;
+    int reserved;
+};
+
+struct StepParams {
+    int nx, ny, pitch;
+    long long plane;           // elements per population plane
+    int boundary;              // LBM_BC_*
+    unsigned limiters;
+    int median_mode;
+    int collide;               // 1: free flight + collision; 0: limiter pass on stored state
+    double a;                  // 2 beta - 1
+    double delta_m, delta_e;
+    double lid[9];             // ((6 W_k) rho_wall) (c_kx u_lid), added on links through the lid
+    // scratch (library-owned)
+    Cand *cand;
+    int *cand_count;
+    int cand_cap;
+    double *partials;          // [blocks][P_NSTAT]
+    unsigned *status;
+    double *ds_out;            // optional FP64 dS(f') field (nx * ny) or nullptr
+};
+
+struct FinalParams {
+    int nblocks;               // partial rows to reduce
+    double one_minus_a2;       // 1 - (2 beta - 1)^2
+    long long k_max;
+    int ehrenfest;             // apply Ehrenfests' step
+    int collide;
+    int nx, ny, pitch;
+    long long plane;
+    const double *partials;
+    Cand *cand;
+    int *cand_count;
+    int cand_cap;
+    int *sel;                  // selected sites out
+    int sel_cap;
+    int *sel_count;
+    unsigned *status;
+    DevStats *stats_ring;
+    int ring_len;
+    long long *counters;       // [0] steps taken (incremented when collide), [1] records written
+};
+
+// Launchers (stream-ordered, no synchronisation).  Return cudaGetLastError().
+template <typename T>
+cudaError_t launch_tiled(int q, const StepParams &p, const T *src, T *dst, int *nblocks,
+                         cudaStream_t s);
+template <typename T>
+cudaError_t launch_finalize(int q, const FinalParams &p, T *f, cudaStream_t s);
+template <typename T>
+cudaError_t launch_init(int q, int nx, int ny, int pitch, long long plane, const double *rho,
+                        const double *ux, const double *uy, T *f, cudaStream_t s);
+template <typename T>
+cudaError_t launch_moments(int q, int nx, int ny, int pitch, long long plane, const T *f,
+                           double *rho, double *ux, double *uy, cudaStream_t s);
+template <typename T>
+cudaError_t launch_get(int q, int nx, int ny, int pitch, long long plane, const T *f, double *out,
+                       cudaStream_t s);
+template <typename T>
+cudaError_t launch_set(int q, int nx, int ny, int pitch, long long plane, const double *in, T *f,
+                       cudaStream_t s);
+template <typename T>
+cudaError_t launch_delta_s(int q, const StepParams &p, const T *f, double *out, cudaStream_t s);
+
+// Fused FP32 D2Q9 step for LBM_BC_WALLS (row-streaming kernel).
+cudaError_t launch_fused_d2q9(const StepParams &p, const float *src, float *dst, int *nblocks,
+                              cudaStream_t s);
+int fused_d2q9_blocks(int nx, int ny);
+
+}  // namespace lbm

@@ -1,0 +1,246 @@
+// lattice.cuh -- per-site arithmetic of the limited LBGK step (device side).
+//
+// Velocity sets (Sec. 4.1): D2Q9 numbered 0 rest, 1 E, 2 N, 3 W, 4 S, 5 NE,
+// 6 NW, 7 SW, 8 SE with weights 4/9, 1/9, 1/36; D1Q3 numbered 0 rest, 1 left,
+// 2 right (the paper's f1, f2, f3).
+//
+// Arithmetic policy Ar<T>:
+//   Ar<double> rounds every operation on its own (__dadd_rn and friends are
+//   never contracted into FMA), so FP64 code written in a fixed order
+//   evaluates exactly that order: the FP64 path reproduces a plain
+//   left-to-right double evaluation of the same formulas bit for bit.
+//   Ar<float> uses the plain operators; the compiler may fuse them.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+template <typename T> struct Ar;
+
+template <> struct Ar<double> {
+    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
+    static __device__ __forceinline__ double sqrt(double a) { return __dsqrt_rn(a); }
+};
+
+template <> struct Ar<float> {
+    static __device__ __forceinline__ float add(float a, float b) { return a + b; }
+    static __device__ __forceinline__ float sub(float a, float b) { return a - b; }
+    static __device__ __forceinline__ float mul(float a, float b) { return a * b; }
+    static __device__ __forceinline__ float div(float a, float b) { return a / b; }
+    static __device__ __forceinline__ float sqrt(float a) { return sqrtf(a); }
+};
+
+template <int Q> struct Lat;
+
+template <> struct Lat<9> {
+    static __host__ __device__ __forceinline__ constexpr int cx(int k)
+    {
+        return k == 1 || k == 5 || k == 8 ? 1 : (k == 3 || k == 6 || k == 7 ? -1 : 0);
+    }
+    static __host__ __device__ __forceinline__ constexpr int cy(int k)
+    {
+        return k == 2 || k == 5 || k == 6 ? 1 : (k == 4 || k == 7 || k == 8 ? -1 : 0);
+    }
+    static __host__ __device__ __forceinline__ constexpr int opp(int k)
+    {
+        return k == 0 ? 0 : (k <= 4 ? ((k + 1) % 4) + 1 : ((k - 3) % 4) + 5);
+    }
+    static __host__ __device__ __forceinline__ constexpr double w(int k)
+    {
+        return k == 0 ? 4.0 / 9.0 : (k <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+    }
+};
+
+template <> struct Lat<3> {
+    static __host__ __device__ __forceinline__ constexpr int cx(int k) { return k == 1 ? -1 : (k == 2 ? 1 : 0); }
+    static __host__ __device__ __forceinline__ constexpr int cy(int) { return 0; }
+    static __host__ __device__ __forceinline__ constexpr int opp(int k) { return k == 0 ? 0 : 3 - k; }
+    static __host__ __device__ __forceinline__ constexpr double w(int k) { return k == 0 ? 2.0 / 3.0 : 1.0 / 6.0; }
+};
+
+// Eq. macro_dis: rho = sum_k f_k, rho u = sum_k v_k f_k, accumulated in k order
+// (terms with v = 0 contribute exactly nothing and are skipped).
+template <typename T>
+__device__ __forceinline__ void moments9(const T f[9], T &rho, T &ux, T &uy)
+{
+    using A = Ar<T>;
+    T r = f[0];
+#pragma unroll
+    for (int k = 1; k < 9; ++k) r = A::add(r, f[k]);
+    T jx = A::sub(f[1], f[3]);
+    jx = A::add(jx, f[5]);
+    jx = A::sub(jx, f[6]);
+    jx = A::sub(jx, f[7]);
+    jx = A::add(jx, f[8]);
+    T jy = A::sub(f[2], f[4]);
+    jy = A::add(jy, f[5]);
+    jy = A::add(jy, f[6]);
+    jy = A::sub(jy, f[7]);
+    jy = A::sub(jy, f[8]);
+    rho = r;
+    ux = A::div(jx, r);
+    uy = A::div(jy, r);
+}
+
+template <typename T>
+__device__ __forceinline__ void moments3(const T f[3], T &rho, T &ux, T &uy)
+{
+    using A = Ar<T>;
+    T r = A::add(A::add(f[0], f[1]), f[2]);
+    rho = r;
+    ux = A::div(A::sub(f[2], f[1]), r);
+    uy = T(0);
+}
+
+// Eq. polyeq2d: f*_k = rho W_k (1 + 3 v_k.u + 9 (v_k.u)^2 / 2 - 3 u^2 / 2).
+template <typename T>
+__device__ __forceinline__ void feq9(T rho, T ux, T uy, T fs[9])
+{
+    using A = Ar<T>;
+    const T usq = A::add(A::mul(ux, ux), A::mul(uy, uy));
+    const T tail = A::div(A::mul(T(3), usq), T(2));
+    const T c[9] = {T(0), ux, uy, -ux, -uy, A::add(ux, uy), A::sub(uy, ux), -A::add(ux, uy),
+                    A::sub(ux, uy)};
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        T poly = A::add(A::add(T(1), A::mul(T(3), c[k])), A::div(A::mul(T(9), A::mul(c[k], c[k])), T(2)));
+        poly = A::sub(poly, tail);
+        fs[k] = A::mul(A::mul(rho, T(Lat<9>::w(k))), poly);
+    }
+}
+
+// Eq. polyeq1d, term by term as printed.
+template <typename T>
+__device__ __forceinline__ void feq3(T rho, T u, T fs[3])
+{
+    using A = Ar<T>;
+    const T uu = A::mul(u, u);
+    fs[0] = A::mul(A::div(A::mul(T(2), rho), T(3)), A::sub(T(1), A::div(A::mul(T(3), uu), T(2))));
+    const T r6 = A::div(rho, T(6));
+    fs[1] = A::mul(r6, A::add(A::sub(T(1), A::mul(T(3), u)), A::mul(T(3), uu)));
+    fs[2] = A::mul(r6, A::add(A::add(T(1), A::mul(T(3), u)), A::mul(T(3), uu)));
+}
+
+template <int Q, typename T>
+__device__ __forceinline__ void moments(const T f[Q], T &rho, T &ux, T &uy)
+{
+    if constexpr (Q == 9)
+        moments9<T>(f, rho, ux, uy);
+    else
+        moments3<T>(f, rho, ux, uy);
+}
+
+template <int Q, typename T>
+__device__ __forceinline__ void feq(T rho, T ux, T uy, T fs[Q])
+{
+    if constexpr (Q == 9)
+        feq9<T>(rho, ux, uy, fs);
+    else
+        feq3<T>(rho, ux, fs);
+}
+
+// Quadratic nonequilibrium entropy (Sec. 3.6): sum_k (g_k - f*_k)^2 / f*_k, k order.
+template <int Q, typename T>
+__device__ __forceinline__ T quad_entropy(const T g[Q], const T fs[Q])
+{
+    using A = Ar<T>;
+    T s = T(0);
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+        const T d = A::sub(g[k], fs[k]);
+        s = A::add(s, A::div(A::mul(d, d), fs[k]));
+    }
+    return s;
+}
+
+// Collision and entropy at one site from its arriving populations f_in:
+// f*, f' = f* + a (f* - f_in) with a = 2 beta - 1 (Eq. collLBGK), dS(f'),
+// dS(f_in) and rho.  With collide = false (limiter pass on a stored state)
+// f' = f_in.  Returns true for a site that cannot be limited: rho <= 0,
+// f*_k <= 0 for some k, or a nonfinite value.
+template <int Q, typename T>
+__device__ __forceinline__ bool site_collide(const T fin[Q], T a, bool collide, T fs[Q], T fp[Q],
+                                             T &ds, T &ds_in, T &rho)
+{
+    using A = Ar<T>;
+    T ux, uy;
+    moments<Q, T>(fin, rho, ux, uy);
+    feq<Q, T>(rho, ux, uy, fs);
+#pragma unroll
+    for (int k = 0; k < Q; ++k) fp[k] = collide ? A::add(fs[k], A::mul(a, A::sub(fs[k], fin[k]))) : fin[k];
+    bool bad = !(rho > T(0)) || !isfinite(rho) || !isfinite(ux) || !isfinite(uy);
+#pragma unroll
+    for (int k = 0; k < Q; ++k) bad |= !(fs[k] > T(0)) || !isfinite(fin[k]);
+    ds = quad_entropy<Q, T>(fp, fs);
+    ds_in = collide ? quad_entropy<Q, T>(fin, fs) : T(0);
+    bad |= !isfinite(ds) || !isfinite(ds_in);
+    return bad;
+}
+
+// Positivity rule (Sec. 3.1): largest lambda <= 1 such that f* + lambda (f' - f*) >= 0.
+template <int Q, typename T>
+__device__ __forceinline__ T phi_positivity(const T fs[Q], const T fp[Q])
+{
+    using A = Ar<T>;
+    T phi = T(1);
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+        if (fp[k] < T(0)) {
+            const T r = A::div(fs[k], A::sub(fs[k], fp[k]));
+            if (r < phi) phi = r;
+        }
+    }
+    return phi;
+}
+
+// Median-filter homothety coefficient (Sec. 3.5, Eq. entrHom) for entropy x and
+// stencil median med.  mode 0: dS_t = max(med, delta), phi = sqrt(dS_t/x) if
+// x > dS_t.  mode 1: phi = sqrt(med/x) if x > delta and med < x.
+template <typename T>
+__device__ __forceinline__ T phi_median(T x, T med, T delta, int mode)
+{
+    using A = Ar<T>;
+    if (mode == 1) {
+        if (x > delta && med < x) return A::sqrt(A::div(med, x));
+        return T(1);
+    }
+    const T t = med > delta ? med : delta;
+    return x > t ? A::sqrt(A::div(t, x)) : T(1);
+}
+
+template <typename T> __device__ __forceinline__ T tmin(T a, T b) { return b < a ? b : a; }
+template <typename T> __device__ __forceinline__ T tmax(T a, T b) { return a < b ? b : a; }
+
+template <typename T> __device__ __forceinline__ T med3(T a, T b, T c)
+{
+    return tmax(tmin(a, b), tmin(tmax(a, b), c));
+}
+
+// Median of nine values given as three columns (a, b, c): with each column
+// sorted, the median is med3(largest column minimum, median of the column
+// medians, smallest column maximum).
+template <typename T>
+__device__ __forceinline__ T med9(T a0, T a1, T a2, T b0, T b1, T b2, T c0, T c1, T c2)
+{
+    auto sort3 = [](T &x, T &y, T &z) {
+        T lo = tmin(x, y), hi = tmax(x, y);
+        T lo2 = tmin(lo, z), t = tmax(lo, z);
+        x = lo2;
+        y = tmin(hi, t);
+        z = tmax(hi, t);
+    };
+    sort3(a0, a1, a2);
+    sort3(b0, b1, b2);
+    sort3(c0, c1, c2);
+    const T lo = tmax(tmax(a0, b0), c0);
+    const T mid = med3(a1, b1, c1);
+    const T hi = tmin(tmin(a2, b2), c2);
+    return med3(lo, mid, hi);
+}
+
+}  // namespace lbm

@@ -1,0 +1,717 @@
+// lbm_api.cu -- the C ABI of liblbm (include/lbm.h): context, validation,
+// device memory ownership, transfers and the per-step launch sequence.
+//
+// A step is two stream-ordered launches: the step kernel (free flight,
+// collision, dS, positivity and median limiters, Ehrenfests' candidates,
+// block partial sums; Eq. lbgkLB and Sec. 3) writing the other population
+// buffer, then the one-block tail (fixed-order FP64 sums, Ehrenfests' step,
+// stats record).  The two buffers swap roles every step.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "internal.h"
+#include "lattice.cuh"
+
+using namespace lbm;
+
+struct lbm_ctx {
+    lbm_config cfg{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int q = 9;
+    int pitch = 0;
+    long long plane = 0;
+    size_t elem = 4;
+    size_t field_bytes = 0;
+    void *buf[2] = {nullptr, nullptr};
+    int cur = 0;
+    Cand *cand = nullptr;
+    int cand_cap = 0;
+    int *counts = nullptr;  // [0] candidate count, [1] chosen count
+    int *sel = nullptr;
+    int sel_cap = 0;
+    double *partials = nullptr;
+    int partial_rows = 0;
+    unsigned *status = nullptr;
+    DevStats *ring = nullptr;
+    int ring_len = 1;
+    long long *counters = nullptr;  // [0] steps, [1] records
+    double *stage = nullptr;
+    size_t stage_bytes = 0;
+    bool ready = false;
+    bool timing = false;
+    std::vector<cudaEvent_t> events;  // three per timed step
+    size_t events_used = 0;
+    long long launches = 0;
+    int64_t device_bytes = 0;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+lbm_status fail(lbm_ctx *c, lbm_status s, const std::string &msg)
+{
+    if (c)
+        c->err = msg;
+    else
+        g_err = msg;
+    return s;
+}
+
+lbm_status cuda_fail(lbm_ctx *c, cudaError_t e, const char *what)
+{
+    std::string m = std::string(what) + " failed: " + cudaGetErrorString(e);
+    return fail(c, e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA, m);
+}
+
+#define CK(c, call)                                   \
+    do {                                              \
+        cudaError_t e_ = (call);                      \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, #call); \
+    } while (0)
+
+int lattice_q(int lattice) { return lattice == LBM_D1Q3 ? 3 : 9; }
+
+bool fused_applies(const lbm_config &c)
+{
+    return c.lattice == LBM_D2Q9 && c.precision == LBM_FP32 && c.boundary == LBM_BC_WALLS &&
+           c.kernel == LBM_KERNEL_FUSED;
+}
+
+int tiled_blocks(const lbm_config &c)
+{
+    if (c.lattice == LBM_D2Q9) return ((c.nx + 29) / 30) * ((c.ny + 5) / 6);
+    return (c.nx + 253) / 254;
+}
+
+std::string validate(const lbm_config *c)
+{
+    if (!c) return "config is NULL";
+    if (c->lattice != LBM_D1Q3 && c->lattice != LBM_D2Q9) return "lattice must be LBM_D1Q3 or LBM_D2Q9";
+    if (c->nx < 1 || c->ny < 1) return "nx and ny must be >= 1";
+    if ((long long)c->nx * c->ny > 0x7fffffffLL) return "nx * ny must fit a 32-bit site index";
+    if (c->precision != LBM_FP64 && c->precision != LBM_FP32) return "precision must be LBM_FP64 or LBM_FP32";
+    if (c->lattice == LBM_D1Q3) {
+        if (c->ny != 1) return "D1Q3 needs ny == 1";
+        if (c->boundary != LBM_BC_WALLS && c->boundary != LBM_BC_PERIODIC)
+            return "D1Q3 boundary must be LBM_BC_WALLS or LBM_BC_PERIODIC";
+        if (c->boundary == LBM_BC_WALLS && c->nx < 3) return "D1Q3 with closed ends needs nx >= 3";
+    } else {
+        if (c->boundary < LBM_BC_WALLS || c->boundary > LBM_BC_CHANNEL) return "unknown boundary kind";
+        if (c->boundary == LBM_BC_WALLS && (c->nx < 4 || c->ny < 4)) return "D2Q9 cavity needs nx, ny >= 4";
+        if (c->boundary == LBM_BC_CHANNEL && c->ny < 4) return "D2Q9 channel needs ny >= 4";
+    }
+    if (c->limiters & ~7u) return "unknown limiter bits";
+    if (!(c->beta >= 0.0 && c->beta <= 1.0)) return "beta must lie in [0, 1]";
+    if (!std::isfinite(c->u_lid) || !std::isfinite(c->rho_wall)) return "u_lid and rho_wall must be finite";
+    if (!(c->delta_median >= 0.0) || !(c->delta_ehrenfest >= 0.0)) return "delta_median and delta_ehrenfest must be >= 0";
+    if (c->k_max < 0) return "k_max must be >= 0";
+    if (c->median_mode != LBM_MEDIAN_THRESHOLD && c->median_mode != LBM_MEDIAN_GATE) return "unknown median_mode";
+    if (c->kernel < LBM_KERNEL_AUTO || c->kernel > LBM_KERNEL_FUSED) return "unknown kernel";
+    if (c->kernel == LBM_KERNEL_FUSED && !fused_applies(*c))
+        return "LBM_KERNEL_FUSED needs D2Q9, LBM_FP32 and LBM_BC_WALLS";
+    if (c->stats_history < 0) return "stats_history must be >= 0";
+    return "";
+}
+
+struct Sizes {
+    int q, pitch;
+    long long plane;
+    size_t elem, field, cand, sel, partials, ring;
+    int cand_cap, sel_cap, rows, ring_len;
+    int64_t total() const
+    {
+        return (int64_t)(2 * field + cand + sel + partials + ring + 64 * sizeof(long long) + 4096);
+    }
+};
+
+Sizes sizes_for(const lbm_config &c)
+{
+    Sizes z{};
+    z.q = lattice_q(c.lattice);
+    z.pitch = row_pitch(c.nx);
+    z.plane = (long long)c.ny * z.pitch;
+    z.elem = c.precision == LBM_FP64 ? 8 : 4;
+    z.field = (size_t)z.q * (size_t)z.plane * z.elem;
+    const long long n = (long long)c.nx * c.ny;
+    z.cand_cap = (c.limiters & LBM_LIM_EHRENFEST) ? (int)n : 1;
+    z.cand = (size_t)z.cand_cap * sizeof(Cand);
+    z.sel_cap = (int)std::max<long long>(1, std::min<long long>(c.k_max, n));
+    z.sel = (size_t)z.sel_cap * sizeof(int);
+    z.rows = tiled_blocks(c);
+    if (fused_applies(c)) z.rows = std::max(z.rows, fused_d2q9_blocks(c.nx, c.ny));
+    z.partials = (size_t)z.rows * P_NSTAT * sizeof(double);
+    z.ring_len = std::max(1, c.stats_history);
+    z.ring = (size_t)z.ring_len * sizeof(DevStats);
+    return z;
+}
+
+bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+lbm_status ensure_stage(lbm_ctx *c, size_t bytes)
+{
+    if (c->stage_bytes >= bytes) return LBM_OK;
+    if (c->stage) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(c->stage);
+        c->device_bytes -= (int64_t)c->stage_bytes;
+        c->stage = nullptr;
+        c->stage_bytes = 0;
+    }
+    CK(c, cudaMalloc(&c->stage, bytes));
+    c->stage_bytes = bytes;
+    c->device_bytes += (int64_t)bytes;
+    return LBM_OK;
+}
+
+// Device-side view of a caller array of `count` doubles: the pointer itself
+// when it is device memory, else the staging buffer at element offset `off`
+// (filled from the host for inputs).
+lbm_status dev_in(lbm_ctx *c, const double *src, size_t count, size_t off, const double **out)
+{
+    if (is_device_ptr(src)) {
+        *out = src;
+        return LBM_OK;
+    }
+    CK(c, cudaMemcpyAsync(c->stage + off, src, count * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    *out = c->stage + off;
+    return LBM_OK;
+}
+
+StepParams step_params(lbm_ctx *c, int collide, unsigned limiters)
+{
+    const lbm_config &g = c->cfg;
+    StepParams p{};
+    p.nx = g.nx;
+    p.ny = g.ny;
+    p.pitch = c->pitch;
+    p.plane = c->plane;
+    p.boundary = g.boundary;
+    p.limiters = limiters;
+    p.median_mode = g.median_mode;
+    p.collide = collide;
+    p.a = 2.0 * g.beta - 1.0;
+    p.delta_m = g.delta_median;
+    p.delta_e = g.delta_ehrenfest;
+    for (int k = 0; k < 9; ++k) {
+        const bool lid = c->q == 9 && g.boundary != LBM_BC_PERIODIC && Lat<9>::cy(k) == -1;
+        p.lid[k] = lid ? ((6.0 * Lat<9>::w(k)) * g.rho_wall) * ((double)Lat<9>::cx(k) * g.u_lid) : 0.0;
+    }
+    p.cand = c->cand;
+    p.cand_count = c->counts;
+    p.cand_cap = c->cand_cap;
+    p.partials = c->partials;
+    p.status = c->status;
+    p.ds_out = nullptr;
+    return p;
+}
+
+FinalParams final_params(lbm_ctx *c, int collide, unsigned limiters, int nblocks)
+{
+    const lbm_config &g = c->cfg;
+    FinalParams f{};
+    f.nblocks = nblocks;
+    const double a = 2.0 * g.beta - 1.0;
+    f.one_minus_a2 = 1.0 - a * a;
+    f.k_max = g.k_max;
+    f.ehrenfest = (limiters & LBM_LIM_EHRENFEST) ? 1 : 0;
+    f.collide = collide;
+    f.nx = g.nx;
+    f.ny = g.ny;
+    f.pitch = c->pitch;
+    f.plane = c->plane;
+    f.partials = c->partials;
+    f.cand = c->cand;
+    f.cand_count = c->counts;
+    f.cand_cap = c->cand_cap;
+    f.sel = c->sel;
+    f.sel_cap = c->sel_cap;
+    f.sel_count = c->counts + 1;
+    f.status = c->status;
+    f.stats_ring = c->ring;
+    f.ring_len = c->ring_len;
+    f.counters = c->counters;
+    return f;
+}
+
+// Next event of the timing record (created on first use).
+lbm_status next_event(lbm_ctx *c, cudaEvent_t *ev)
+{
+    if (c->events_used == c->events.size()) {
+        cudaEvent_t e;
+        CK(c, cudaEventCreate(&e));
+        c->events.push_back(e);
+    }
+    *ev = c->events[c->events_used++];
+    return LBM_OK;
+}
+
+lbm_status mark(lbm_ctx *c)
+{
+    if (!c->timing) return LBM_OK;
+    cudaEvent_t ev;
+    lbm_status s = next_event(c, &ev);
+    if (s != LBM_OK) return s;
+    CK(c, cudaEventRecord(ev, c->stream));
+    return LBM_OK;
+}
+
+// One pass (step or limiter pass) from buf[cur] into buf[cur ^ 1].
+lbm_status run_pass(lbm_ctx *c, int collide, unsigned limiters)
+{
+    lbm_status ms = mark(c);
+    if (ms != LBM_OK) return ms;
+    StepParams p = step_params(c, collide, limiters);
+    int nblocks = 0;
+    cudaError_t e;
+    void *src = c->buf[c->cur], *dst = c->buf[c->cur ^ 1];
+    if (c->cfg.precision == LBM_FP64) {
+        e = launch_tiled<double>(c->q, p, (const double *)src, (double *)dst, &nblocks, c->stream);
+    } else if (collide && fused_applies(c->cfg)) {
+        e = launch_fused_d2q9(p, (const float *)src, (float *)dst, &nblocks, c->stream);
+    } else {
+        e = launch_tiled<float>(c->q, p, (const float *)src, (float *)dst, &nblocks, c->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
+    if ((ms = mark(c)) != LBM_OK) return ms;
+    FinalParams f = final_params(c, collide, limiters, nblocks);
+    if (c->cfg.precision == LBM_FP64)
+        e = launch_finalize<double>(c->q, f, (double *)dst, c->stream);
+    else
+        e = launch_finalize<float>(c->q, f, (float *)dst, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "finalize kernel launch");
+    if ((ms = mark(c)) != LBM_OK) return ms;
+    c->launches += 2;
+    c->cur ^= 1;
+    return LBM_OK;
+}
+
+lbm_status read_status(lbm_ctx *c, bool clear)
+{
+    unsigned s = 0;
+    CK(c, cudaMemcpyAsync(&s, c->status, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (clear && s) CK(c, cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->stream));
+    if (s & kStatNonfinite) return fail(c, LBM_ERR_NONFINITE, "a site had rho <= 0, f*_k <= 0 or a nonfinite value");
+    if (s & kStatTimeout) return fail(c, LBM_ERR_TIMEOUT, "a bounded device wait gave up");
+    if (s & kStatCandOverflow) return fail(c, LBM_ERR_CUDA, "Ehrenfests' candidate buffer overflowed");
+    return LBM_OK;
+}
+
+lbm_status reset_counters(lbm_ctx *c)
+{
+    CK(c, cudaMemsetAsync(c->counters, 0, 2 * sizeof(long long), c->stream));
+    CK(c, cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->stream));
+    CK(c, cudaMemsetAsync(c->counts, 0, 2 * sizeof(int), c->stream));
+    CK(c, cudaMemsetAsync(c->ring, 0, (size_t)c->ring_len * sizeof(DevStats), c->stream));
+    return LBM_OK;
+}
+
+void free_all(lbm_ctx *c)
+{
+    for (cudaEvent_t e : c->events) cudaEventDestroy(e);
+    c->events.clear();
+    void *ptrs[] = {c->buf[0], c->buf[1], c->cand, c->counts, c->sel, c->partials,
+                    c->status, c->ring, c->counters, c->stage};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+}
+
+void to_public(const DevStats &d, lbm_step_stats *o)
+{
+    o->step = d.step;
+    o->mass = d.mass;
+    o->sum_dS = d.sum_dS;
+    o->dS_lbgk = d.dS_lbgk;
+    o->dS_lim = d.dS_lim;
+    o->n_pos = d.n_pos;
+    o->n_med = d.n_med;
+    o->n_ehr = d.n_ehr;
+    o->n_cand = d.n_cand;
+    o->n_bad = d.n_bad;
+    o->status = d.status;
+    o->reserved = 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lbm_config_default(lbm_config *c)
+{
+    if (!c) return;
+    std::memset(c, 0, sizeof(*c));
+    c->lattice = LBM_D2Q9;
+    c->nx = 100;
+    c->ny = 100;
+    c->boundary = LBM_BC_WALLS;
+    c->precision = LBM_FP32;
+    c->limiters = 0;
+    c->median_mode = LBM_MEDIAN_THRESHOLD;
+    c->kernel = LBM_KERNEL_AUTO;
+    c->beta = 1.0;
+    c->u_lid = 0.0;
+    c->rho_wall = 1.0;
+    c->delta_median = 1e-3;
+    c->delta_ehrenfest = 1e-3;
+    c->k_max = 0;
+    c->stats_history = 1;
+}
+
+int64_t lbm_footprint_bytes(const lbm_config *cfg)
+{
+    std::string v = validate(cfg);
+    if (!v.empty()) {
+        g_err = v;
+        return 0;
+    }
+    return sizes_for(*cfg).total();
+}
+
+lbm_status lbm_create(const lbm_config *cfg, void *cuda_stream, lbm_ctx **out)
+{
+    if (!out) return fail(nullptr, LBM_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    std::string v = validate(cfg);
+    if (!v.empty()) return fail(nullptr, LBM_ERR_INVALID_ARG, v);
+    lbm_ctx *c = new lbm_ctx();
+    c->cfg = *cfg;
+    if (c->cfg.stats_history < 1) c->cfg.stats_history = 1;
+    c->stream = (cudaStream_t)cuda_stream;
+    const Sizes z = sizes_for(c->cfg);
+    c->q = z.q;
+    c->pitch = z.pitch;
+    c->plane = z.plane;
+    c->elem = z.elem;
+    c->field_bytes = z.field;
+    c->cand_cap = z.cand_cap;
+    c->sel_cap = z.sel_cap;
+    c->partial_rows = z.rows;
+    c->ring_len = z.ring_len;
+    cudaError_t e = cudaGetDevice(&c->device);
+    auto alloc = [&](void **p, size_t bytes) -> cudaError_t {
+        if (e != cudaSuccess) return e;
+        e = cudaMalloc(p, bytes);
+        if (e == cudaSuccess) e = cudaMemsetAsync(*p, 0, bytes, c->stream);
+        return e;
+    };
+    alloc(&c->buf[0], z.field);
+    alloc(&c->buf[1], z.field);
+    alloc((void **)&c->cand, z.cand);
+    alloc((void **)&c->counts, 2 * sizeof(int));
+    alloc((void **)&c->sel, z.sel);
+    alloc((void **)&c->partials, z.partials);
+    alloc((void **)&c->status, sizeof(unsigned));
+    alloc((void **)&c->ring, z.ring);
+    alloc((void **)&c->counters, 2 * sizeof(long long));
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        free_all(c);
+        std::string m = std::string("lbm_create: device allocation failed: ") + cudaGetErrorString(e);
+        delete c;
+        return fail(nullptr, e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA, m);
+    }
+    c->device_bytes = z.total();
+    *out = c;
+    return LBM_OK;
+}
+
+lbm_status lbm_destroy(lbm_ctx *c)
+{
+    if (!c) return LBM_OK;
+    cudaStreamSynchronize(c->stream);
+    free_all(c);
+    delete c;
+    return LBM_OK;
+}
+
+lbm_status lbm_init(lbm_ctx *c, const double *rho, const double *ux, const double *uy)
+{
+    if (!c) return fail(nullptr, LBM_ERR_INVALID_ARG, "ctx is NULL");
+    if (!rho || !ux) return fail(c, LBM_ERR_INVALID_ARG, "rho and ux must not be NULL");
+    const size_t n = (size_t)c->cfg.nx * c->cfg.ny;
+    lbm_status s = ensure_stage(c, 3 * n * sizeof(double));
+    if (s != LBM_OK) return s;
+    const double *dr, *du, *dv = nullptr;
+    if ((s = dev_in(c, rho, n, 0, &dr)) != LBM_OK) return s;
+    if ((s = dev_in(c, ux, n, n, &du)) != LBM_OK) return s;
+    if (uy && c->q == 9 && (s = dev_in(c, uy, n, 2 * n, &dv)) != LBM_OK) return s;
+    cudaError_t e;
+    if (c->cfg.precision == LBM_FP64)
+        e = launch_init<double>(c->q, c->cfg.nx, c->cfg.ny, c->pitch, c->plane, dr, du, dv, (double *)c->buf[0], c->stream);
+    else
+        e = launch_init<float>(c->q, c->cfg.nx, c->cfg.ny, c->pitch, c->plane, dr, du, dv, (float *)c->buf[0], c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "init kernel launch");
+    c->launches++;
+    c->cur = 0;
+    if ((s = reset_counters(c)) != LBM_OK) return s;
+    CK(c, cudaStreamSynchronize(c->stream));
+    c->ready = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx *c, int64_t nsteps)
+{
+    if (!c) return fail(nullptr, LBM_ERR_INVALID_ARG, "ctx is NULL");
+    if (nsteps < 0) return fail(c, LBM_ERR_INVALID_ARG, "nsteps must be >= 0");
+    if (!c->ready) return fail(c, LBM_ERR_STATE, "lbm_step before lbm_init / lbm_set_populations");
+    for (int64_t i = 0; i < nsteps; ++i) {
+        lbm_status s = run_pass(c, 1, c->cfg.limiters);
+        if (s != LBM_OK) return s;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_limit(lbm_ctx *c, uint32_t limiters)
+{
+    if (!c) return fail(nullptr, LBM_ERR_INVALID_ARG, "ctx is NULL");
+    if (limiters & ~7u) return fail(c, LBM_ERR_INVALID_ARG, "unknown limiter bits");
+    if (!c->ready) return fail(c, LBM_ERR_STATE, "lbm_limit before lbm_init / lbm_set_populations");
+    if ((limiters & LBM_LIM_EHRENFEST) && c->cand_cap < c->cfg.nx * c->cfg.ny)
+        return fail(c, LBM_ERR_INVALID_ARG, "Ehrenfests' limiter needs LBM_LIM_EHRENFEST in the config at create");
+    return run_pass(c, 0, limiters);
+}
+
+lbm_status lbm_delta_s(lbm_ctx *c, double *out)
+{
+    if (!c) return fail(nullptr, LBM_ERR_INVALID_ARG, "ctx is NULL");
+    if (!out) return fail(c, LBM_ERR_INVALID_ARG, "out is NULL");
+    if (!c->ready) return fail(c, LBM_ERR_STATE, "lbm_delta_s before lbm_init / lbm_set_populations");
+    const size_t n = (size_t)c->cfg.nx * c->cfg.ny;
+    const bool dev = is_device_ptr(out);
+    double *dst = out;
+    if (!dev) {
+        lbm_status s = ensure_stage(c, n * sizeof(double));
+        if (s != LBM_OK) return s;
+        dst = c->stage;
+    }
+    StepParams p = step_params(c, 1, 0);
+    cudaError_t e = c->cfg.precision == LBM_FP64
+                        ? launch_delta_s<double>(c->q, p, (const double *)c->buf[c->cur], dst, c->stream)
+                        : launch_delta_s<float>(c->q, p, (const float *)c->buf[c->cur], dst, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "delta_s kernel launch");
+    c->launches++;
+    if (!dev) CK(c, cudaMemcpyAsync(out, dst, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_moments(lbm_ctx *c, double *rho, double *ux, double *uy)
+{
+    if (!c) return fail(nullptr, LBM_ERR_INVALID_ARG, "ctx is NULL");
+    if (!rho || !ux) return fail(c, LBM_ERR_INVALID_ARG, "rho and ux must not be NULL");
+    if (!c->ready) return fail(c, LBM_ERR_STATE, "lbm_moments before lbm_init / lbm_set_populations");
+    const size_t n = (size_t)c->cfg.nx * c->cfg.ny;
+    const bool dev = is_device_ptr(rho);
+    if (dev != is_device_ptr(ux) || (uy && dev != is_device_ptr(uy)))
+        return fail(c, LBM_ERR_INVALID_ARG, "rho, ux, uy must all be host or all be device memory");
+    double *dr = rho, *du = ux, *dv = uy;
+    if (!dev) {
+        lbm_status s = ensure_stage(c, 3 * n * sizeof(double));
+        if (s != LBM_OK) return s;
+        dr = c->stage;
+        du = c->stage + n;
+        dv = uy ? c->stage + 2 * n : nullptr;
+    }
+    cudaError_t e = c->cfg.precision == LBM_FP64
+                        ? launch_moments<double>(c->q, c->cfg.nx, c->cfg.ny, c->pitch, c->plane,
+                                                 (const double *)c->buf[c->cur], dr, du, dv, c->stream)
+                        : launch_moments<float>(c->q, c->cfg.nx, c->cfg.ny, c->pitch, c->plane,
+                                                (const float *)c->buf[c->cur], dr, du, dv, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "moments kernel launch");
+    c->launches++;
+    if (!dev) {
+        CK(c, cudaMemcpyAsync(rho, dr, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaMemcpyAsync(ux, du, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        if (uy) CK(c, cudaMemcpyAsync(uy, dv, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    }
+    return read_status(c, false);
+}
+
+lbm_status lbm_stats_history(lbm_ctx *c, lbm_step_stats *out, int64_t cap, int64_t *n)
+{
+    if (!c) return fail(nullptr, LBM_ERR_INVALID_ARG, "ctx is NULL");
+    if (!out || !n || cap < 0) return fail(c, LBM_ERR_INVALID_ARG, "bad output arguments");
+    long long cnt[2] = {0, 0};
+    std::vector<DevStats> ring((size_t)c->ring_len);
+    CK(c, cudaMemcpyAsync(cnt, c->counters, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaMemcpyAsync(ring.data(), c->ring, ring.size() * sizeof(DevStats), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    const long long recs = cnt[1];
+    const long long have = std::min<long long>(recs, c->ring_len);
+    const long long take = std::min<long long>(have, cap);
+    for (long long i = 0; i < take; ++i) {
+        const long long r = recs - take + i;
+        to_public(ring[(size_t)(r % c->ring_len)], &out[i]);
+    }
+    *n = take;
+    return read_status(c, false);
+}
+
+lbm_status lbm_stats(lbm_ctx *c, lbm_step_stats *out)
+{
+    if (!c) return fail(nullptr, LBM_ERR_INVALID_ARG, "ctx is NULL");
+    if (!out) return fail(c, LBM_ERR_INVALID_ARG, "out is NULL");
+    std::memset(out, 0, sizeof(*out));
+    int64_t n = 0;
+    return lbm_stats_history(c, out, 1, &n);
+}
+
+lbm_status lbm_limited_sites(lbm_ctx *c, int64_t *idx, int64_t cap, int64_t *n)
+{
+    if (!c) return fail(nullptr, LBM_ERR_INVALID_ARG, "ctx is NULL");
+    if (!n || cap < 0 || (cap > 0 && !idx)) return fail(c, LBM_ERR_INVALID_ARG, "bad output arguments");
+    int cnt = 0;
+    CK(c, cudaMemcpyAsync(&cnt, c->counts + 1, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    std::vector<int> s((size_t)std::max(cnt, 0));
+    if (cnt > 0) {
+        CK(c, cudaMemcpyAsync(s.data(), c->sel, (size_t)cnt * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+    }
+    std::sort(s.begin(), s.end());
+    *n = cnt;
+    const int64_t take = std::min<int64_t>(cap, cnt);
+    std::vector<int64_t> w((size_t)take);
+    for (int64_t i = 0; i < take; ++i) w[(size_t)i] = s[(size_t)i];
+    if (take > 0) {
+        if (is_device_ptr(idx)) {
+            CK(c, cudaMemcpyAsync(idx, w.data(), (size_t)take * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+            CK(c, cudaStreamSynchronize(c->stream));
+        } else {
+            std::memcpy(idx, w.data(), (size_t)take * sizeof(int64_t));
+        }
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_get_populations(lbm_ctx *c, double *f)
+{
+    if (!c) return fail(nullptr, LBM_ERR_INVALID_ARG, "ctx is NULL");
+    if (!f) return fail(c, LBM_ERR_INVALID_ARG, "f is NULL");
+    const size_t tot = (size_t)c->q * c->cfg.nx * c->cfg.ny;
+    const bool dev = is_device_ptr(f);
+    double *dst = f;
+    if (!dev) {
+        lbm_status s = ensure_stage(c, tot * sizeof(double));
+        if (s != LBM_OK) return s;
+        dst = c->stage;
+    }
+    cudaError_t e = c->cfg.precision == LBM_FP64
+                        ? launch_get<double>(c->q, c->cfg.nx, c->cfg.ny, c->pitch, c->plane,
+                                             (const double *)c->buf[c->cur], dst, c->stream)
+                        : launch_get<float>(c->q, c->cfg.nx, c->cfg.ny, c->pitch, c->plane,
+                                            (const float *)c->buf[c->cur], dst, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "get kernel launch");
+    c->launches++;
+    if (!dev) CK(c, cudaMemcpyAsync(f, dst, tot * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_set_populations(lbm_ctx *c, const double *f)
+{
+    if (!c) return fail(nullptr, LBM_ERR_INVALID_ARG, "ctx is NULL");
+    if (!f) return fail(c, LBM_ERR_INVALID_ARG, "f is NULL");
+    const size_t tot = (size_t)c->q * c->cfg.nx * c->cfg.ny;
+    const double *src = f;
+    if (!is_device_ptr(f)) {
+        lbm_status s = ensure_stage(c, tot * sizeof(double));
+        if (s != LBM_OK) return s;
+        if ((s = dev_in(c, f, tot, 0, &src)) != LBM_OK) return s;
+    }
+    cudaError_t e = c->cfg.precision == LBM_FP64
+                        ? launch_set<double>(c->q, c->cfg.nx, c->cfg.ny, c->pitch, c->plane, src,
+                                             (double *)c->buf[0], c->stream)
+                        : launch_set<float>(c->q, c->cfg.nx, c->cfg.ny, c->pitch, c->plane, src,
+                                            (float *)c->buf[0], c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "set kernel launch");
+    c->launches++;
+    c->cur = 0;
+    lbm_status s = reset_counters(c);
+    if (s != LBM_OK) return s;
+    CK(c, cudaStreamSynchronize(c->stream));
+    c->ready = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_synchronize(lbm_ctx *c)
+{
+    if (!c) return fail(nullptr, LBM_ERR_INVALID_ARG, "ctx is NULL");
+    return read_status(c, true);
+}
+
+lbm_status lbm_get_config(const lbm_ctx *c, lbm_config *out)
+{
+    if (!c || !out) return fail(nullptr, LBM_ERR_INVALID_ARG, "NULL argument");
+    *out = c->cfg;
+    return LBM_OK;
+}
+
+lbm_status lbm_timing(lbm_ctx *c, int32_t enable)
+{
+    if (!c) return fail(nullptr, LBM_ERR_INVALID_ARG, "ctx is NULL");
+    c->timing = enable != 0;
+    c->events_used = 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_timing_read(lbm_ctx *c, double *step_ms, double *tail_ms, int64_t *steps)
+{
+    if (!c || !step_ms || !tail_ms || !steps) return fail(c, LBM_ERR_INVALID_ARG, "NULL argument");
+    CK(c, cudaStreamSynchronize(c->stream));
+    double a = 0.0, b = 0.0;
+    const size_t n = c->events_used / 3;
+    for (size_t i = 0; i < n; ++i) {
+        float t0 = 0.f, t1 = 0.f;
+        CK(c, cudaEventElapsedTime(&t0, c->events[3 * i], c->events[3 * i + 1]));
+        CK(c, cudaEventElapsedTime(&t1, c->events[3 * i + 1], c->events[3 * i + 2]));
+        a += t0;
+        b += t1;
+    }
+    *step_ms = a;
+    *tail_ms = b;
+    *steps = (int64_t)n;
+    c->events_used = 0;
+    return LBM_OK;
+}
+
+int64_t lbm_device_bytes(const lbm_ctx *c) { return c ? c->device_bytes : 0; }
+
+int64_t lbm_launch_count(const lbm_ctx *c) { return c ? c->launches : 0; }
+
+const char *lbm_last_error(const lbm_ctx *c) { return c ? c->err.c_str() : g_err.c_str(); }
+
+const char *lbm_status_string(lbm_status s)
+{
+    switch (s) {
+    case LBM_OK: return "LBM_OK";
+    case LBM_ERR_INVALID_ARG: return "LBM_ERR_INVALID_ARG";
+    case LBM_ERR_OOM: return "LBM_ERR_OOM";
+    case LBM_ERR_CUDA: return "LBM_ERR_CUDA";
+    case LBM_ERR_NONFINITE: return "LBM_ERR_NONFINITE";
+    case LBM_ERR_TIMEOUT: return "LBM_ERR_TIMEOUT";
+    case LBM_ERR_STATE: return "LBM_ERR_STATE";
+    }
+    return "LBM_ERR_UNKNOWN";
+}
+
+int32_t lbm_abi_version(void) { return LBM_ABI_VERSION; }
+
+}  // extern "C"

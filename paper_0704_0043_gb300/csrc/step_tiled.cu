@@ -1,0 +1,369 @@
+// step_tiled.cu -- one limited LBGK step with overlapping tiles, every lattice,
+// boundary kind and precision, plus the small field kernels (init, moments,
+// population transfer, dS field).
+//
+// A block computes free flight, collision and dS(f') (Eq. lbgkLB, Sec. 3.6) for
+// a tile of sites and keeps the dS values in shared memory; the sites of the
+// tile's interior then have their whole median stencil (Sec. 3.5) at hand and
+// finish the step: positivity rule (Sec. 3.1), median homothety (Eq. entrHom),
+// phi = min of the two, f_out = f* + phi (f' - f*) (Eq. LimGenF), Ehrenfests'
+// candidates (Sec. 3.2) and the block's FP64 partial sums (Sec. 3.4).  Tiles
+// overlap by one site on each side, so every site is finished by exactly one
+// block and the halo ring is recomputed.  In FP64 every operation runs in the
+// order of the formulas, unfused (see lattice.cuh).
+#include <type_traits>
+
+#include "internal.h"
+#include "lattice.cuh"
+
+namespace lbm {
+namespace {
+
+constexpr int kTX = 32, kTY = 8;  // D2Q9 tile of computed sites; (kTX-2) x (kTY-2) finished
+constexpr int kT1 = 256;          // D1Q3 tile; kT1 - 2 finished
+
+__device__ __forceinline__ long long fidx(long long plane, int pitch, int k, int y, int x)
+{
+    return (long long)k * plane + (long long)y * pitch + kLead + x;
+}
+
+// Free flight in pull form at site (x, y) (Sec. 2): f_in_k(x) = f_k(x - v_k);
+// a link leaving the lattice is reflected, f_in_k(x) = f_opp(k)(x) (halfway
+// bounce-back, Sec. 4.4.1), plus the moving-wall term for links through the lid.
+// Reads storage type S, returns compute type T.
+template <int Q, typename S, typename T>
+__device__ __forceinline__ void pull(const StepParams &p, const S *__restrict__ f, int x, int y, T fin[Q])
+{
+    using A = Ar<T>;
+    const bool wrapx = p.boundary != 0;
+    const bool wrapy = (Q == 9) && p.boundary == 1;
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+        int sx = x - Lat<Q>::cx(k), sy = y - Lat<Q>::cy(k);
+        if (wrapx) sx = sx < 0 ? sx + p.nx : (sx >= p.nx ? sx - p.nx : sx);
+        if (wrapy) sy = sy < 0 ? sy + p.ny : (sy >= p.ny ? sy - p.ny : sy);
+        if (sx >= 0 && sx < p.nx && sy >= 0 && sy < p.ny) {
+            fin[k] = T(f[fidx(p.plane, p.pitch, k, sy, sx)]);
+        } else {
+            T v = T(f[fidx(p.plane, p.pitch, Lat<Q>::opp(k), y, x)]);
+            if (Q == 9 && sy > p.ny - 1) v = A::add(v, T(p.lid[k]));
+            fin[k] = v;
+        }
+    }
+}
+
+// Median of the dS stencil of site (x, y), tile-local position (tx, ty) in a
+// shared array with row stride `ld` (Sec. 3.5; wall rules of Sec. 4.4): returns
+// false for sites the filter skips.
+template <int Q, typename T>
+__device__ __forceinline__ bool stencil_median(const StepParams &p, const T *s, int ld, int tx, int ty,
+                                               int x, int y, T &med)
+{
+#define S_(dx, dy) s[(ty + (dy)) * ld + tx + (dx)]
+    if constexpr (Q == 3) {
+        if (p.boundary == 0 && (x == 0 || x == p.nx - 1)) return false;
+        med = med3(S_(-1, 0), S_(0, 0), S_(1, 0));
+        return true;
+    } else {
+        const bool wallx = p.boundary == 0, wally = p.boundary != 1;
+        if ((wallx && (x == 0 || x == p.nx - 1)) || (wally && (y == 0 || y == p.ny - 1))) return false;
+        const bool nearx = wallx && (x == 1 || x == p.nx - 2);
+        const bool neary = wally && (y == 1 || y == p.ny - 2);
+        if (nearx && neary) {
+            const int dx = x == 1 ? 1 : -1, dy = y == 1 ? 1 : -1;
+            med = med3(S_(0, 0), S_(dx, 0), S_(0, dy));
+        } else if (neary) {
+            med = med3(S_(-1, 0), S_(0, 0), S_(1, 0));
+        } else if (nearx) {
+            med = med3(S_(0, -1), S_(0, 0), S_(0, 1));
+        } else {
+            med = med9(S_(-1, -1), S_(-1, 0), S_(-1, 1), S_(0, -1), S_(0, 0), S_(0, 1), S_(1, -1), S_(1, 0),
+                       S_(1, 1));
+        }
+        return true;
+    }
+#undef S_
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int Q, typename T>
+__global__ void __launch_bounds__(256) k_tiled(StepParams p, const T *__restrict__ src, T *__restrict__ dst)
+{
+    using A = Ar<T>;
+    constexpr int BX = Q == 9 ? kTX : kT1;
+    constexpr int BY = Q == 9 ? kTY : 1;
+    __shared__ T sds[BY * BX];
+    __shared__ double sred[8][P_NSTAT];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int x = (int)blockIdx.x * (BX - 2) - 1 + tx;
+    const int y = Q == 9 ? (int)blockIdx.y * (BY - 2) - 1 + ty : 0;
+    const bool wrapx = p.boundary != 0;
+    const bool wrapy = (Q == 9) && p.boundary == 1;
+    bool valid = wrapx ? (x >= -1 && x <= p.nx) : (x >= 0 && x < p.nx);
+    if (Q == 9) valid = valid && (wrapy ? (y >= -1 && y <= p.ny) : (y >= 0 && y < p.ny));
+    const int xs = wrapx ? (x < 0 ? x + p.nx : (x >= p.nx ? x - p.nx : x)) : x;
+    const int ys = wrapy ? (y < 0 ? y + p.ny : (y >= p.ny ? y - p.ny : y)) : y;
+
+    T fin[Q], fs[Q], fp[Q];
+    T ds = T(0), dsin = T(0), rho = T(0);
+    bool bad = false;
+    if (valid) {
+        if (p.collide) {
+            pull<Q, T, T>(p, src, xs, ys, fin);
+        } else {
+#pragma unroll
+            for (int k = 0; k < Q; ++k) fin[k] = src[fidx(p.plane, p.pitch, k, ys, xs)];
+        }
+        bad = site_collide<Q, T>(fin, T(p.a), p.collide != 0, fs, fp, ds, dsin, rho);
+        if (bad) ds = T(INFINITY);
+    }
+    sds[ty * BX + tx] = ds;
+    __syncthreads();
+
+    const bool own = valid && tx >= 1 && tx <= BX - 2 && (Q == 3 || (ty >= 1 && ty <= BY - 2)) && x >= 0 &&
+                     x < p.nx && y >= 0 && y < p.ny;
+    double acc[P_NSTAT];
+#pragma unroll
+    for (int i = 0; i < P_NSTAT; ++i) acc[i] = 0.0;
+    if (own) {
+        T phi_pos = T(1), phi_med = T(1);
+        if (!bad) {
+            if (p.limiters & 1u) phi_pos = phi_positivity<Q, T>(fs, fp);
+            if (p.limiters & 4u) {
+                T med;
+                if (stencil_median<Q, T>(p, sds, BX, tx, ty, x, y, med))
+                    phi_med = phi_median<T>(ds, med, T(p.delta_m), p.median_mode);
+            }
+        }
+        const T phi = phi_pos < phi_med ? phi_pos : phi_med;
+        if (phi < T(1)) {
+#pragma unroll
+            for (int k = 0; k < Q; ++k) dst[fidx(p.plane, p.pitch, k, y, x)] = A::add(fs[k], A::mul(phi, A::sub(fp[k], fs[k])));
+            acc[P_DS_LIM] = Ar<double>::mul(Ar<double>::sub(1.0, Ar<double>::mul((double)phi, (double)phi)), (double)ds);
+        } else {
+#pragma unroll
+            for (int k = 0; k < Q; ++k) dst[fidx(p.plane, p.pitch, k, y, x)] = fp[k];
+        }
+        acc[P_MASS] = (double)rho;
+        if (!bad) {
+            acc[P_SUM_DS] = (double)ds;
+            acc[P_SUM_IN] = (double)dsin;
+        } else {
+            acc[P_NBAD] = 1.0;
+            atomicOr(p.status, kStatNonfinite);
+        }
+        acc[P_NPOS] = phi_pos < T(1) ? 1.0 : 0.0;
+        acc[P_NMED] = phi_med < T(1) ? 1.0 : 0.0;
+        if ((p.limiters & 2u) && !bad) {
+            // Ehrenfests' candidates are decided on an FP64 dS(f').  FP32 storage:
+            // sites near or above the threshold recompute their collision in FP64
+            // from the same stored values.
+            double key = 0.0;
+            bool is = false;
+            if constexpr (std::is_same<T, double>::value) {
+                key = ds;
+                is = ds > p.delta_e;
+            } else {
+                if (ds > (float)(p.delta_e * (1.0 - 1.0 / 64.0))) {
+                    double fin64[Q], fs64[Q], fp64[Q], d64, din64, r64;
+                    if (p.collide) {
+                        pull<Q, T, double>(p, src, x, y, fin64);
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < Q; ++k) fin64[k] = (double)src[fidx(p.plane, p.pitch, k, y, x)];
+                    }
+                    const bool b64 = site_collide<Q, double>(fin64, p.a, p.collide != 0, fs64, fp64, d64, din64, r64);
+                    key = d64;
+                    is = !b64 && d64 > p.delta_e;
+                }
+            }
+            if (is) {
+                const int slot = atomicAdd(p.cand_count, 1);
+                if (slot < p.cand_cap) {
+                    Cand c;
+                    c.key = key;
+                    c.site = y * p.nx + x;
+                    c.phi = (double)phi;
+                    c.pad = 0;
+                    p.cand[slot] = c;
+                } else {
+                    atomicOr(p.status, kStatCandOverflow);
+                }
+            }
+        }
+        if (p.ds_out) p.ds_out[(long long)y * p.nx + x] = (double)ds;
+    }
+    // block partial sums, fixed order
+    const int lin = ty * BX + tx, warp = lin >> 5, lane = lin & 31;
+#pragma unroll
+    for (int i = 0; i < P_NSTAT; ++i) {
+        const double v = warp_sum(acc[i]);
+        if (lane == 0) sred[warp][i] = v;
+    }
+    __syncthreads();
+    if (lin < P_NSTAT) {
+        double v = 0.0;
+        for (int w = 0; w < (BX * BY) / 32; ++w) v += sred[w][lin];
+        p.partials[((long long)blockIdx.y * gridDim.x + blockIdx.x) * P_NSTAT + lin] = v;
+    }
+}
+
+template <int Q, typename T>
+__global__ void k_delta_s(StepParams p, const T *__restrict__ f, double *__restrict__ out)
+{
+    const long long n = (long long)p.nx * p.ny;
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(s % p.nx), y = (int)(s / p.nx);
+        double fin[Q], fs[Q], fp[Q], ds, dsin, rho;
+        pull<Q, T, double>(p, f, x, y, fin);
+        const bool bad = site_collide<Q, double>(fin, p.a, true, fs, fp, ds, dsin, rho);
+        out[s] = bad ? (double)INFINITY : ds;
+    }
+}
+
+template <int Q, typename T>
+__global__ void k_init(int nx, int ny, int pitch, long long plane, const double *__restrict__ rho,
+                       const double *__restrict__ ux, const double *__restrict__ uy, T *__restrict__ f)
+{
+    const long long n = (long long)nx * ny;
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(s % nx), y = (int)(s / nx);
+        double fs[Q];
+        feq<Q, double>(rho[s], ux[s], uy ? uy[s] : 0.0, fs);
+#pragma unroll
+        for (int k = 0; k < Q; ++k) f[fidx(plane, pitch, k, y, x)] = T(fs[k]);
+    }
+}
+
+template <int Q, typename T>
+__global__ void k_moments(int nx, int ny, int pitch, long long plane, const T *__restrict__ f,
+                          double *__restrict__ rho, double *__restrict__ ux, double *__restrict__ uy)
+{
+    const long long n = (long long)nx * ny;
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(s % nx), y = (int)(s / nx);
+        double g[Q], r, a, b;
+#pragma unroll
+        for (int k = 0; k < Q; ++k) g[k] = (double)f[fidx(plane, pitch, k, y, x)];
+        moments<Q, double>(g, r, a, b);
+        rho[s] = r;
+        ux[s] = a;
+        if (uy) uy[s] = b;
+    }
+}
+
+template <typename T>
+__global__ void k_get(int q, int nx, int ny, int pitch, long long plane, const T *__restrict__ f, double *__restrict__ out)
+{
+    const long long n = (long long)nx * ny, tot = n * q;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(e / n);
+        const long long s = e % n;
+        out[e] = (double)f[fidx(plane, pitch, k, (int)(s / nx), (int)(s % nx))];
+    }
+}
+
+template <typename T>
+__global__ void k_set(int q, int nx, int ny, int pitch, long long plane, const double *__restrict__ in, T *__restrict__ f)
+{
+    const long long n = (long long)nx * ny, tot = n * q;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(e / n);
+        const long long s = e % n;
+        f[fidx(plane, pitch, k, (int)(s / nx), (int)(s % nx))] = T(in[e]);
+    }
+}
+
+inline int grid_for(long long n, int threads)
+{
+    long long b = (n + threads - 1) / threads;
+    if (b > 152 * 32) b = 152 * 32;
+    return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_tiled(int q, const StepParams &p, const T *src, T *dst, int *nblocks, cudaStream_t s)
+{
+    if (q == 9) {
+        dim3 grid((p.nx + kTX - 3) / (kTX - 2), (p.ny + kTY - 3) / (kTY - 2));
+        k_tiled<9, T><<<grid, dim3(kTX, kTY), 0, s>>>(p, src, dst);
+        *nblocks = (int)(grid.x * grid.y);
+    } else {
+        dim3 grid((p.nx + kT1 - 3) / (kT1 - 2));
+        k_tiled<3, T><<<grid, dim3(kT1), 0, s>>>(p, src, dst);
+        *nblocks = (int)grid.x;
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_delta_s(int q, const StepParams &p, const T *f, double *out, cudaStream_t s)
+{
+    const int g = grid_for((long long)p.nx * p.ny, 256);
+    if (q == 9)
+        k_delta_s<9, T><<<g, 256, 0, s>>>(p, f, out);
+    else
+        k_delta_s<3, T><<<g, 256, 0, s>>>(p, f, out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_init(int q, int nx, int ny, int pitch, long long plane, const double *rho, const double *ux,
+                        const double *uy, T *f, cudaStream_t s)
+{
+    const int g = grid_for((long long)nx * ny, 256);
+    if (q == 9)
+        k_init<9, T><<<g, 256, 0, s>>>(nx, ny, pitch, plane, rho, ux, uy, f);
+    else
+        k_init<3, T><<<g, 256, 0, s>>>(nx, ny, pitch, plane, rho, ux, nullptr, f);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_moments(int q, int nx, int ny, int pitch, long long plane, const T *f, double *rho, double *ux,
+                           double *uy, cudaStream_t s)
+{
+    const int g = grid_for((long long)nx * ny, 256);
+    if (q == 9)
+        k_moments<9, T><<<g, 256, 0, s>>>(nx, ny, pitch, plane, f, rho, ux, uy);
+    else
+        k_moments<3, T><<<g, 256, 0, s>>>(nx, ny, pitch, plane, f, rho, ux, uy);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_get(int q, int nx, int ny, int pitch, long long plane, const T *f, double *out, cudaStream_t s)
+{
+    k_get<T><<<grid_for((long long)nx * ny * q, 256), 256, 0, s>>>(q, nx, ny, pitch, plane, f, out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_set(int q, int nx, int ny, int pitch, long long plane, const double *in, T *f, cudaStream_t s)
+{
+    k_set<T><<<grid_for((long long)nx * ny * q, 256), 256, 0, s>>>(q, nx, ny, pitch, plane, in, f);
+    return cudaGetLastError();
+}
+
+#define LBM_INST(T)                                                                                           \
+    template cudaError_t launch_tiled<T>(int, const StepParams &, const T *, T *, int *, cudaStream_t);     \
+    template cudaError_t launch_delta_s<T>(int, const StepParams &, const T *, double *, cudaStream_t);     \
+    template cudaError_t launch_init<T>(int, int, int, int, long long, const double *, const double *,      \
+                                        const double *, T *, cudaStream_t);                                  \
+    template cudaError_t launch_moments<T>(int, int, int, int, long long, const T *, double *, double *,    \
+                                           double *, cudaStream_t);                                          \
+    template cudaError_t launch_get<T>(int, int, int, int, long long, const T *, double *, cudaStream_t);   \
+    template cudaError_t launch_set<T>(int, int, int, int, long long, const double *, T *, cudaStream_t);
+LBM_INST(float)
+LBM_INST(double)
+#undef LBM_INST
+
+}  // namespace lbm

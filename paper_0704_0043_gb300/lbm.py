@@ -1,0 +1,290 @@
+"""Thin ctypes binding over liblbm's C ABI (include/lbm.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Arrays may be numpy arrays (host) or torch tensors (host or CUDA);
+they must be contiguous float64 of the documented size.  PyTorch supplies the
+CUDA stream (``torch.cuda.current_stream()``) when it is importable.
+
+The library must have been built (``paper_0704_0043_gb300.build.build()`` or
+``__graft_entry__.build()``); loading raises otherwise -- there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+D1Q3, D2Q9 = 1, 2
+FP64, FP32 = 0, 1
+BC_WALLS, BC_PERIODIC, BC_CHANNEL = 0, 1, 2
+LIM_POSITIVITY, LIM_EHRENFEST, LIM_MEDIAN = 1, 2, 4
+MEDIAN_THRESHOLD, MEDIAN_GATE = 0, 1
+KERNEL_AUTO, KERNEL_TILED, KERNEL_FUSED = 0, 1, 2
+
+OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_STATE = range(7)
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("lattice", ctypes.c_int32), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+        ("boundary", ctypes.c_int32), ("precision", ctypes.c_int32), ("limiters", ctypes.c_uint32),
+        ("median_mode", ctypes.c_int32), ("kernel", ctypes.c_int32), ("beta", ctypes.c_double),
+        ("u_lid", ctypes.c_double), ("rho_wall", ctypes.c_double), ("delta_median", ctypes.c_double),
+        ("delta_ehrenfest", ctypes.c_double), ("k_max", ctypes.c_int64),
+        ("stats_history", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    ]
+
+
+class StepStats(ctypes.Structure):
+    _fields_ = [
+        ("step", ctypes.c_int64), ("mass", ctypes.c_double), ("sum_dS", ctypes.c_double),
+        ("dS_lbgk", ctypes.c_double), ("dS_lim", ctypes.c_double), ("n_pos", ctypes.c_int64),
+        ("n_med", ctypes.c_int64), ("n_ehr", ctypes.c_int64), ("n_cand", ctypes.c_int64),
+        ("n_bad", ctypes.c_int64), ("status", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    ]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
+
+
+class LBMError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_status_name(status)}: {message}")
+        self.status = status
+
+
+_LIB = None
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def lib():
+    """The loaded liblbm (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"liblbm is not built ({path} missing); run __graft_entry__.build()")
+        L = ctypes.CDLL(path)
+        vp, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
+        cfgp = ctypes.POINTER(Config)
+        L.lbm_config_default.argtypes = [cfgp]
+        L.lbm_config_default.restype = None
+        L.lbm_create.argtypes = [cfgp, vp, ctypes.POINTER(vp)]
+        L.lbm_destroy.argtypes = [vp]
+        L.lbm_init.argtypes = [vp, vp, vp, vp]
+        L.lbm_step.argtypes = [vp, ctypes.c_int64]
+        L.lbm_delta_s.argtypes = [vp, vp]
+        L.lbm_limit.argtypes = [vp, ctypes.c_uint32]
+        L.lbm_moments.argtypes = [vp, vp, vp, vp]
+        L.lbm_stats.argtypes = [vp, ctypes.POINTER(StepStats)]
+        L.lbm_stats_history.argtypes = [vp, ctypes.POINTER(StepStats), ctypes.c_int64,
+                                        ctypes.POINTER(ctypes.c_int64)]
+        L.lbm_limited_sites.argtypes = [vp, vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
+        L.lbm_get_populations.argtypes = [vp, vp]
+        L.lbm_set_populations.argtypes = [vp, vp]
+        L.lbm_synchronize.argtypes = [vp]
+        L.lbm_get_config.argtypes = [vp, cfgp]
+        L.lbm_device_bytes.argtypes = [vp]
+        L.lbm_device_bytes.restype = ctypes.c_int64
+        L.lbm_footprint_bytes.argtypes = [cfgp]
+        L.lbm_footprint_bytes.restype = ctypes.c_int64
+        L.lbm_timing.argtypes = [vp, ctypes.c_int32]
+        L.lbm_timing_read.argtypes = [vp, dp, dp, ctypes.POINTER(ctypes.c_int64)]
+        L.lbm_launch_count.argtypes = [vp]
+        L.lbm_launch_count.restype = ctypes.c_int64
+        L.lbm_last_error.argtypes = [vp]
+        L.lbm_last_error.restype = ctypes.c_char_p
+        L.lbm_status_string.argtypes = [ctypes.c_int]
+        L.lbm_status_string.restype = ctypes.c_char_p
+        L.lbm_abi_version.restype = ctypes.c_int32
+        for name in ("lbm_create", "lbm_destroy", "lbm_init", "lbm_step", "lbm_delta_s", "lbm_limit",
+                     "lbm_moments", "lbm_stats", "lbm_stats_history", "lbm_limited_sites",
+                     "lbm_get_populations", "lbm_set_populations", "lbm_synchronize",
+                     "lbm_get_config", "lbm_timing", "lbm_timing_read"):
+            getattr(L, name).restype = ctypes.c_int
+        _LIB = L
+    return _LIB
+
+
+def _status_name(s: int) -> str:
+    try:
+        return lib().lbm_status_string(s).decode()
+    except Exception:
+        return f"status {s}"
+
+
+def _check(status: int, handle=None):
+    if status != OK:
+        msg = lib().lbm_last_error(handle).decode(errors="replace")
+        raise LBMError(status, msg)
+
+
+def current_stream_handle() -> int:
+    """cudaStream_t of torch's current stream (0 if torch/CUDA is absent)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return int(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return 0
+
+
+def _ptr(a, count: int, writable: bool):
+    """(address, keepalive) of a float64 buffer of `count` elements."""
+    if a is None:
+        return None, None
+    if hasattr(a, "data_ptr") and hasattr(a, "is_contiguous"):  # torch tensor
+        import torch
+        if a.dtype != torch.float64 or not a.is_contiguous() or a.numel() != count:
+            raise ValueError(f"expected a contiguous float64 tensor of {count} elements")
+        return a.data_ptr(), a
+    arr = np.asarray(a)
+    if arr.dtype != np.float64 or not arr.flags.c_contiguous or arr.size != count:
+        if writable:
+            raise ValueError(f"expected a contiguous float64 array of {count} elements")
+        arr = np.ascontiguousarray(arr, dtype=np.float64).reshape(-1)
+        if arr.size != count:
+            raise ValueError(f"expected {count} elements, got {arr.size}")
+    return arr.ctypes.data, arr
+
+
+def default_config(**kw) -> Config:
+    c = Config()
+    lib().lbm_config_default(ctypes.byref(c))
+    for k, v in kw.items():
+        if not hasattr(c, k):
+            raise TypeError(f"unknown config field {k}")
+        setattr(c, k, v)
+    return c
+
+
+def footprint_bytes(**kw) -> int:
+    c = default_config(**kw)
+    n = lib().lbm_footprint_bytes(ctypes.byref(c))
+    if n == 0:
+        raise LBMError(ERR_INVALID_ARG, lib().lbm_last_error(None).decode())
+    return n
+
+
+class Lattice:
+    """One lattice owned by liblbm (lbm_create ... lbm_destroy)."""
+
+    def __init__(self, stream: int | None = None, **cfg):
+        self.config = default_config(**cfg)
+        self.q = 3 if self.config.lattice == D1Q3 else 9
+        self.nx, self.ny = self.config.nx, self.config.ny
+        self.sites = self.nx * self.ny
+        self.stream = current_stream_handle() if stream is None else stream
+        h = ctypes.c_void_p()
+        _check(lib().lbm_create(ctypes.byref(self.config), ctypes.c_void_p(self.stream), ctypes.byref(h)))
+        self._h = h
+
+    # -- lifetime -------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().lbm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -- the C ABI, one method per entry point --------------------------------
+    def init(self, rho, ux, uy=None):
+        p1, k1 = _ptr(rho, self.sites, False)
+        p2, k2 = _ptr(ux, self.sites, False)
+        p3, k3 = _ptr(uy, self.sites, False)
+        _check(lib().lbm_init(self._h, p1, p2, p3), self._h)
+
+    def step(self, nsteps: int = 1):
+        _check(lib().lbm_step(self._h, int(nsteps)), self._h)
+
+    def limit(self, limiters: int):
+        _check(lib().lbm_limit(self._h, int(limiters)), self._h)
+
+    def delta_s(self, out=None):
+        if out is None:
+            out = np.empty((self.ny, self.nx))
+        p, k = _ptr(out, self.sites, True)
+        _check(lib().lbm_delta_s(self._h, p), self._h)
+        return out
+
+    def moments(self, out=None, check: bool = True):
+        if out is None:
+            out = tuple(np.empty((self.ny, self.nx)) for _ in range(3))
+        rho, ux, uy = out
+        a, ka = _ptr(rho, self.sites, True)
+        b, kb = _ptr(ux, self.sites, True)
+        c, kc = _ptr(uy, self.sites, True)
+        s = lib().lbm_moments(self._h, a, b, c)
+        if check:
+            _check(s, self._h)
+        return rho, ux, uy
+
+    def stats(self, check: bool = True) -> dict:
+        st = StepStats()
+        s = lib().lbm_stats(self._h, ctypes.byref(st))
+        if check:
+            _check(s, self._h)
+        return st.as_dict()
+
+    def stats_history(self, cap: int):
+        arr = (StepStats * cap)()
+        n = ctypes.c_int64()
+        _check(lib().lbm_stats_history(self._h, arr, cap, ctypes.byref(n)), self._h)
+        return [arr[i].as_dict() for i in range(n.value)]
+
+    def limited_sites(self) -> np.ndarray:
+        cap = max(1, int(self.config.k_max))
+        out = np.zeros(cap, dtype=np.int64)
+        n = ctypes.c_int64()
+        _check(lib().lbm_limited_sites(self._h, out.ctypes.data, cap, ctypes.byref(n)), self._h)
+        return out[:min(n.value, cap)].copy()
+
+    def get_populations(self, out=None):
+        if out is None:
+            out = np.empty((self.q, self.ny, self.nx))
+        p, k = _ptr(out, self.q * self.sites, True)
+        _check(lib().lbm_get_populations(self._h, p), self._h)
+        return out
+
+    def set_populations(self, f):
+        p, k = _ptr(f, self.q * self.sites, False)
+        _check(lib().lbm_set_populations(self._h, p), self._h)
+
+    def synchronize(self):
+        _check(lib().lbm_synchronize(self._h), self._h)
+
+    def timing(self, enable: bool):
+        _check(lib().lbm_timing(self._h, 1 if enable else 0), self._h)
+
+    def timing_read(self):
+        """(step-kernel ms, tail-kernel ms, timed steps) since timing was enabled."""
+        a, b, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+        _check(lib().lbm_timing_read(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(n)), self._h)
+        return a.value, b.value, n.value
+
+    def device_bytes(self) -> int:
+        return lib().lbm_device_bytes(self._h)
+
+    def launch_count(self) -> int:
+        return lib().lbm_launch_count(self._h)

@@ -1,0 +1,259 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+FP64 contexts evaluate every operation in the oracle's order with no FMA, so
+populations, dS fields and Ehrenfests' sets must match bit for bit; sums are
+reduced in a different order and must agree to 1e-12 relative.  FP32 contexts
+are compared after one step from the same FP32 state (1e-5 relative on
+populations; identical Ehrenfests' set, whose keys are FP64 on both sides) and
+after 1000 steps of the 100 x 100 cavity (rho, u within 1e-5 absolute).
+Lattice sizes span several tiles and end in ragged partial tiles.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_0704_0043_gb300 import inputs, lbm
+
+pytestmark = pytest.mark.gpu
+
+ALL = lbm.LIM_POSITIVITY | lbm.LIM_EHRENFEST | lbm.LIM_MEDIAN
+W9 = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+W3 = np.array([2 / 3, 1 / 6, 1 / 6])
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_0704_0043_gb300 import build
+    build.build()
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+
+
+def pair(**cfg):
+    """A GPU lattice and the oracle config with the same parameters."""
+    g = lbm.Lattice(**cfg)
+    oc = oracle.Config(lattice=g.config.lattice, nx=g.config.nx, ny=g.config.ny,
+                       boundary=g.config.boundary, beta=g.config.beta, u_lid=g.config.u_lid,
+                       rho_wall=g.config.rho_wall, limiters=g.config.limiters,
+                       delta_median=g.config.delta_median, delta_ehrenfest=g.config.delta_ehrenfest,
+                       k_max=g.config.k_max, median_mode=g.config.median_mode)
+    return g, oc
+
+
+def rand_state(q, ny, nx, seed, eps=0.1, neg_frac=0.0, heavy=0):
+    w = W9 if q == 9 else W3
+    f = inputs.random_populations(seed, q, ny, nx, w, eps, neg_frac=neg_frac)
+    rng = np.random.default_rng(seed + 99)
+    for _ in range(heavy):  # a few strongly nonequilibrium sites (positivity, Ehrenfests')
+        j, i = rng.integers(0, ny), rng.integers(0, nx)
+        if q == 9:
+            f[rng.integers(1, 9), j, i] *= 8.0
+        else:
+            f[0, j, i] *= 0.02
+    return f
+
+
+def stats_close(a, b, rtol=1e-12):
+    for key in ("mass", "sum_dS", "dS_lbgk", "dS_lim"):
+        assert abs(a[key] - b[key]) <= rtol * max(abs(b[key]), 1e-300) + 1e-300, (key, a[key], b[key])
+    for key in ("n_pos", "n_med", "n_ehr", "n_cand", "n_bad"):
+        assert a[key] == b[key], (key, a[key], b[key])
+
+
+FP64_CASES = [
+    dict(lattice=lbm.D2Q9, nx=67, ny=41, boundary=lbm.BC_WALLS, beta=0.97, u_lid=0.1,
+         limiters=ALL, delta_median=1e-4, delta_ehrenfest=5e-3, k_max=7),
+    dict(lattice=lbm.D2Q9, nx=45, ny=20, boundary=lbm.BC_CHANNEL, beta=0.9, u_lid=0.05,
+         rho_wall=1.3, limiters=ALL, delta_median=0.0, delta_ehrenfest=2e-3, k_max=5),
+    dict(lattice=lbm.D2Q9, nx=33, ny=13, boundary=lbm.BC_PERIODIC, beta=0.99, limiters=ALL,
+         delta_median=1e-5, delta_ehrenfest=1e-3, k_max=9, median_mode=lbm.MEDIAN_GATE),
+    dict(lattice=lbm.D2Q9, nx=4, ny=4, boundary=lbm.BC_WALLS, beta=0.95, u_lid=0.1, limiters=ALL,
+         delta_median=0.0, delta_ehrenfest=1e-3, k_max=2),
+    dict(lattice=lbm.D1Q3, nx=600, ny=1, boundary=lbm.BC_WALLS, beta=0.999, limiters=ALL,
+         delta_median=1e-6, delta_ehrenfest=1e-3, k_max=4),
+    dict(lattice=lbm.D1Q3, nx=517, ny=1, boundary=lbm.BC_PERIODIC, beta=0.8, limiters=ALL,
+         delta_median=0.0, delta_ehrenfest=5e-4, k_max=3),
+    dict(lattice=lbm.D1Q3, nx=3, ny=1, boundary=lbm.BC_WALLS, beta=0.9, limiters=ALL,
+         delta_median=0.0, delta_ehrenfest=1e-4, k_max=1),
+]
+
+
+@pytest.mark.parametrize("case", range(len(FP64_CASES)))
+def test_fp64_steps_bitwise_equal_to_oracle(case):
+    cfg = dict(FP64_CASES[case], precision=lbm.FP64)
+    g, oc = pair(**cfg)
+    f = rand_state(g.q, g.ny, g.nx, 10 + case, eps=0.15, heavy=max(1, g.sites // 200))
+    g.set_populations(f)
+    cur = f.copy()
+    acted = {"n_pos": 0, "n_med": 0, "n_ehr": 0}
+    for step in range(12):
+        # the next-collision dS field first
+        np.testing.assert_array_equal(g.delta_s(), oracle.delta_s(oc, cur))
+        g.step(1)
+        r = oracle.step(oc, cur)
+        cur = r.f
+        got = g.get_populations()
+        np.testing.assert_array_equal(got, cur, err_msg=f"step {step}")
+        st = g.stats()
+        stats_close(st, r.stats)
+        assert st["step"] == step + 1
+        np.testing.assert_array_equal(g.limited_sites(), np.sort(r.selected))
+        for k in acted:
+            acted[k] += r.stats[k]
+    assert acted["n_pos"] > 0 and acted["n_med"] > 0 and acted["n_ehr"] > 0, acted
+    rho, ux, uy = g.moments()
+    orho, oux, ouy = oracle.moments(oc, cur)
+    np.testing.assert_array_equal(rho, orho)
+    np.testing.assert_array_equal(ux, oux)
+
+
+def test_fp64_init_and_limit_pass_bitwise():
+    g, oc = pair(lattice=lbm.D2Q9, nx=70, ny=38, boundary=lbm.BC_WALLS, beta=0.96, u_lid=0.1,
+                 precision=lbm.FP64, limiters=ALL, delta_median=0.0, delta_ehrenfest=1e-3, k_max=11)
+    rho, ux, uy = inputs.random_moments(3, 70, 38, umax=0.1)
+    g.init(rho, ux, uy)
+    f0 = oracle.init(oc, rho, ux, uy)
+    np.testing.assert_array_equal(g.get_populations(), f0)
+    f = rand_state(9, 38, 70, 4, eps=0.2, neg_frac=0.05)
+    g.set_populations(f)
+    g.limit(ALL)
+    r = oracle.limit(oc, f, ALL)
+    np.testing.assert_array_equal(g.get_populations(), r.f)
+    np.testing.assert_array_equal(g.limited_sites(), np.sort(r.selected))
+    st = g.stats()
+    stats_close(st, r.stats)
+    assert st["step"] == 0 and r.stats["n_pos"] > 0 and r.stats["n_ehr"] == 11
+
+
+def test_shock_tube_fp64_ehrenfests_set_identical_every_step():
+    """The 1:2 shock tube, 800 sites, nu = 1e-9, Ehrenfests' delta = 1e-3, k = 4,
+    400 steps in FP64: moments within 1e-12 relative (bitwise here) and the same
+    Ehrenfests' set at every step."""
+    w = inputs.shock_tube_workload()
+    g, oc = pair(lattice=lbm.D1Q3, nx=w.nx, ny=1, boundary=lbm.BC_WALLS, beta=w.beta,
+                 precision=lbm.FP64, limiters=w.limiters, delta_ehrenfest=w.delta_ehrenfest,
+                 k_max=w.k_max)
+    rho, ux = inputs.shock_tube(w.nx)
+    g.init(rho, ux)
+    cur = oracle.init(oc, rho, ux)
+    n_acted = 0
+    for step in range(w.steps):
+        g.step(1)
+        r = oracle.step(oc, cur)
+        cur = r.f
+        sel = g.limited_sites()
+        np.testing.assert_array_equal(sel, np.sort(r.selected), err_msg=f"step {step}")
+        n_acted += len(sel)
+    grho, gux, _ = g.moments()
+    orho, oux, _ = oracle.moments(oc, cur)
+    np.testing.assert_allclose(grho, orho, rtol=1e-12, atol=0)
+    np.testing.assert_allclose(gux, oux, rtol=0, atol=1e-12 * 1.0)
+    np.testing.assert_array_equal(g.get_populations(), cur)
+    assert n_acted > 0
+
+
+@pytest.mark.parametrize("kernel", [lbm.KERNEL_TILED])
+def test_fp32_one_step_against_oracle(kernel):
+    cfg = dict(lattice=lbm.D2Q9, nx=157, ny=93, boundary=lbm.BC_WALLS, beta=0.97, u_lid=0.1,
+               precision=lbm.FP32, limiters=ALL, delta_median=1e-4, delta_ehrenfest=2e-3,
+               k_max=13, kernel=kernel)
+    g, oc = pair(**cfg)
+    f = rand_state(9, 93, 157, 21, eps=0.15, heavy=60).astype(np.float32).astype(np.float64)
+    g.set_populations(f)
+    np.testing.assert_array_equal(g.get_populations(), f)
+    # dS of the next collision is evaluated in FP64 from the stored values
+    np.testing.assert_array_equal(g.delta_s(), oracle.delta_s(oc, f))
+    g.step(1)
+    r = oracle.step(oc, f)
+    got = g.get_populations()
+    np.testing.assert_allclose(got, r.f, rtol=2e-5, atol=2e-7)
+    np.testing.assert_array_equal(g.limited_sites(), np.sort(r.selected))
+    st = g.stats()
+    assert st["n_ehr"] == r.stats["n_ehr"] == 13 and st["n_cand"] == r.stats["n_cand"]
+    assert abs(st["mass"] - r.stats["mass"]) <= 1e-6 * r.stats["mass"]
+
+
+def test_fp32_cavity_100_matches_fp64_oracle_after_1000_steps():
+    """Config: 100 x 100 cavity, lid 0.1, Re = 5000, median delta = 1e-3, FP32 on
+    the GPU vs the FP64 oracle: rho and u within 1e-5 absolute after 1000 steps."""
+    w = inputs.cavity100_workload()
+    g, oc = pair(lattice=lbm.D2Q9, nx=100, ny=100, boundary=lbm.BC_WALLS, beta=w.beta,
+                 u_lid=w.u_lid, rho_wall=w.rho0, precision=lbm.FP32, limiters=w.limiters,
+                 delta_median=w.delta_median)
+    rho, ux, uy = inputs.cavity_rest(100, 100, w.rho0)
+    g.init(rho, ux, uy)
+    f0 = oracle.init(oc, rho, ux, uy)
+    g.step(1000)
+    f, st, rc = oracle.run(oc, f0, 1000)
+    assert rc == 0
+    grho, gux, guy = g.moments()
+    orho, oux, ouy = oracle.moments(oc, f)
+    assert np.abs(grho - orho).max() < 1e-5
+    assert np.abs(gux - oux).max() < 1e-5
+    assert np.abs(guy - ouy).max() < 1e-5
+    gs = g.stats()
+    assert abs(gs["mass"] - st["mass"]) < 1e-5 * st["mass"]
+
+
+def test_radix_select_with_many_candidates_and_ties():
+    """More candidates than k, with exact ties across the threshold."""
+    nx, ny, k = 128, 96, 257
+    g, oc = pair(lattice=lbm.D2Q9, nx=nx, ny=ny, boundary=lbm.BC_PERIODIC, beta=1.0,
+                 precision=lbm.FP64, limiters=lbm.LIM_EHRENFEST, delta_ehrenfest=1e-4, k_max=k)
+    f = rand_state(9, ny, nx, 33, eps=0.2)
+    # copy whole rows so that many sites share identical states (exact dS ties)
+    f[:, 40:48, :] = f[:, 40:41, :]
+    g.set_populations(f)
+    g.limit(lbm.LIM_EHRENFEST)
+    r = oracle.limit(oc, f, lbm.LIM_EHRENFEST)
+    assert r.stats["n_cand"] > 4 * k
+    np.testing.assert_array_equal(g.limited_sites(), np.sort(r.selected))
+    np.testing.assert_array_equal(g.get_populations(), r.f)
+
+
+def test_checkpoint_resume_and_determinism():
+    cfg = dict(lattice=lbm.D2Q9, nx=96, ny=64, boundary=lbm.BC_WALLS, beta=0.99, u_lid=0.1,
+               precision=lbm.FP32, limiters=ALL, delta_median=1e-4, delta_ehrenfest=1e-3, k_max=5)
+    rho, ux, uy = inputs.random_moments(8, 96, 64, umax=0.05)
+    a = lbm.Lattice(**cfg)
+    a.init(rho, ux, uy)
+    a.step(30)
+    fa = a.get_populations()
+    b = lbm.Lattice(**cfg)
+    b.init(rho, ux, uy)
+    b.step(12)
+    ck = b.get_populations()
+    c = lbm.Lattice(**cfg)
+    c.set_populations(ck)
+    c.step(18)
+    np.testing.assert_array_equal(c.get_populations(), fa)
+    b.step(18)
+    np.testing.assert_array_equal(b.get_populations(), fa)
+
+
+def test_nonfinite_site_reports_status():
+    g, _ = pair(lattice=lbm.D2Q9, nx=40, ny=30, boundary=lbm.BC_WALLS, beta=0.9,
+                precision=lbm.FP32, limiters=ALL, k_max=3)
+    f = rand_state(9, 30, 40, 5)
+    f[:, 10, 10] = -1.0  # rho < 0 at one site
+    g.set_populations(f)
+    g.step(1)
+    with pytest.raises(lbm.LBMError) as e:
+        g.synchronize()
+    assert e.value.status == lbm.ERR_NONFINITE
+    st = g.stats(check=False)
+    assert st["n_bad"] >= 1
+
+
+def test_zero_steps_and_argument_errors():
+    g, _ = pair(lattice=lbm.D2Q9, nx=16, ny=16, boundary=lbm.BC_WALLS, precision=lbm.FP32)
+    with pytest.raises(lbm.LBMError) as e:
+        g.step(1)
+    assert e.value.status == lbm.ERR_STATE
+    rho, ux, uy = inputs.cavity_rest(16, 16)
+    g.init(rho, ux, uy)
+    f0 = g.get_populations()
+    g.step(0)
+    np.testing.assert_array_equal(g.get_populations(), f0)
+    with pytest.raises(lbm.LBMError):
+        g.step(-1)
