@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--develop", type=int, default=500,
                     help="untimed steps before warm-up so the flow has left the rest state")
     ap.add_argument("--kernel", default="auto", choices=["auto", "tiled", "fused"])
+    ap.add_argument("--side", type=int, default=4096,
+                    help="cavity side (4096 is the workload; smaller sides are for profiling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -137,9 +139,14 @@ def traffic_from_profile(kernel_name: str, sites: int):
     return ent["dram_bytes_per_site"] * sites
 
 
-def workload():
+def workload(side: int = 4096):
     from paper_0704_0043_gb300 import inputs
-    return inputs.cavity4096_workload()
+    w = inputs.cavity4096_workload()
+    if side != w.nx:
+        w.nx = w.ny = side
+        w.name = f"cavity_d2q9_{side}_re7500"
+        w.k_max = int(1e-4 * side * side)
+    return w
 
 
 def lattice_kwargs(w, kernel: str):
@@ -229,7 +236,7 @@ def main():
         dist.barrier()
     lbm.lib()
 
-    w = workload()
+    w = workload(args.side)
     lat = lbm.Lattice(**lattice_kwargs(w, args.kernel))
     rho, ux, uy = inputs.cavity_rest(w.nx, w.ny, w.rho0)
     lat.init(rho, ux, uy)

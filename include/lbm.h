@@ -54,9 +54,11 @@ typedef enum {
 
 enum { LBM_D1Q3 = 1, LBM_D2Q9 = 2 };
 
-/* Storage precision of the populations; arithmetic is FP64 for LBM_FP64 and
- * FP32 otherwise.  LBM_FP64 evaluates every operation in the oracle's order
- * with no FMA contraction. */
+/* Storage precision of the populations.  LBM_FP64 stores f and evaluates
+ * every operation in the oracle's order with no FMA contraction.  LBM_FP32
+ * stores the deviations g_k = f_k - rho_ref W_k from a uniform rest state and
+ * computes in FP32 on them (FP64 for the global sums and the Ehrenfests' keys);
+ * every transfer in or out of the library converts to and from f in FP64. */
 enum { LBM_FP64 = 0, LBM_FP32 = 1 };
 
 enum {
@@ -83,7 +85,7 @@ enum {
 
 typedef struct lbm_config {
     int32_t lattice;         /* LBM_D1Q3 or LBM_D2Q9 */
-    int32_t nx, ny;          /* sites; ny must be 1 for D1Q3.  nx, ny >= 4 for D2Q9 walls */
+    int32_t nx, ny;          /* sites; ny must be 1 for D1Q3; nx, ny >= 2 for D2Q9 walls */
     int32_t boundary;        /* LBM_BC_* */
     int32_t precision;       /* LBM_FP64 or LBM_FP32 */
     uint32_t limiters;       /* LBM_LIM_* bits applied by lbm_step */
@@ -97,6 +99,7 @@ typedef struct lbm_config {
     int64_t k_max;           /* Ehrenfests' step acts on at most k_max sites per step (>= 0) */
     int32_t stats_history;   /* per-step stats kept on the device (ring length, >= 1) */
     int32_t reserved;        /* must be 0 */
+    double rho_ref;          /* reference density of the FP32 deviation storage (> 0, default 1) */
 } lbm_config;
 
 typedef struct lbm_step_stats {
@@ -118,7 +121,7 @@ typedef struct lbm_step_stats {
 typedef struct lbm_ctx lbm_ctx;
 
 /* Fills *cfg with defaults: D2Q9 100 x 100 cavity, FP32, beta = 1, no limiters,
- * delta = 1e-3, k_max = 0, one stats record. */
+ * delta = 1e-3, k_max = 0, one stats record, rho_wall = rho_ref = 1. */
 void lbm_config_default(lbm_config *cfg);
 
 /* Validates cfg, allocates the lattice and scratch on the current device and

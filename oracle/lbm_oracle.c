@@ -196,11 +196,13 @@ static void sort_small(double *v, int m)
 }
 
 /*
- * Median-filter stencil at site (i, j) (Sec. 3.5; wall rules of Sec. 4.4):
- * boundary nodes are not filtered; a node next to a wall uses itself and its
- * two neighbours along that wall; a node next to two walls (next to a corner)
- * uses itself and its inward neighbour along x and along y; all other nodes
- * use the 3x3 block.  D1Q3: three points, the end sites not filtered.
+ * Median-filter stencil at site (i, j) (Sec. 3.5; wall rules of Sec. 4.4).
+ * The paper's boundary nodes sit on the walls and are not filtered; here the
+ * walls lie half a link outside the lattice, so every lattice node is a fluid
+ * node.  A node next to one wall uses itself and its two neighbours along that
+ * wall; a node next to two walls (a corner node) uses itself and its inward
+ * neighbour along x and along y; all other nodes use the 3x3 block.  D1Q3:
+ * three points; the two end sites are not filtered.
  * Returns the stencil size (0 = not filtered) and the values in v.
  */
 static int median_stencil(const orc_config *cfg, const double *dS, int i, int j, double *v)
@@ -222,12 +224,11 @@ static int median_stencil(const orc_config *cfg, const double *dS, int i, int j,
 #define DS(a, b) dS[(long long)(b) * nx + (a)]
     int wallx = cfg->boundary == ORC_BC_WALLS;
     int wally = cfg->boundary != ORC_BC_PERIODIC;
-    if ((wallx && (i == 0 || i == nx - 1)) || (wally && (j == 0 || j == ny - 1))) return 0;
-    int nearx = wallx && (i == 1 || i == nx - 2);
-    int neary = wally && (j == 1 || j == ny - 2);
+    int nearx = wallx && (i == 0 || i == nx - 1);
+    int neary = wally && (j == 0 || j == ny - 1);
     if (nearx && neary) {
-        int ii = (i == 1) ? 2 : nx - 3;
-        int jj = (j == 1) ? 2 : ny - 3;
+        int ii = (i == 0) ? 1 : nx - 2;
+        int jj = (j == 0) ? 1 : ny - 2;
         v[0] = DS(i, j);
         v[1] = DS(ii, j);
         v[2] = DS(i, jj);

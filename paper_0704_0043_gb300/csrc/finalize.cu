@@ -8,6 +8,8 @@
 // largest (dS, -site) pair by radix selection: eight 8-bit digit passes over the
 // 64-bit pattern of dS (positive doubles order like their bit patterns), then
 // four passes over the site index among the candidates tied at the threshold.
+#include <type_traits>
+
 #include "internal.h"
 #include "lattice.cuh"
 
@@ -22,6 +24,28 @@ __device__ __forceinline__ unsigned long long key_bits(double d) { return (unsig
 __device__ __forceinline__ long long fidx(long long plane, int pitch, int k, int y, int x)
 {
     return (long long)k * plane + (long long)y * pitch + kLead + x;
+}
+
+// Free flight into site (x, y) of a D2Q9 cavity / channel / periodic lattice,
+// evaluated in FP64 from FP32 storage exactly as the FP64 path evaluates it.
+__device__ void pull_d2q9_f64(const FinalParams &p, int x, int y, double fin[9])
+{
+    const bool wrapx = p.boundary != 0, wrapy = p.boundary == 1;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        int sx = x - Lat<9>::cx(k), sy = y - Lat<9>::cy(k);
+        if (wrapx) sx = sx < 0 ? sx + p.nx : (sx >= p.nx ? sx - p.nx : sx);
+        if (wrapy) sy = sy < 0 ? sy + p.ny : (sy >= p.ny ? sy - p.ny : sy);
+        // FP32 storage holds g = f - rho_ref W; the absolute value is (double) g + rw
+        if (sx >= 0 && sx < p.nx && sy >= 0 && sy < p.ny) {
+            fin[k] = Ar<double>::add((double)p.src[fidx(p.plane, p.pitch, k, sy, sx)], p.rw[k]);
+        } else {
+            const int q = Lat<9>::opp(k);
+            double v = Ar<double>::add((double)p.src[fidx(p.plane, p.pitch, q, y, x)], p.rw[q]);
+            if (sy > p.ny - 1) v = Ar<double>::add(v, p.lid[k]);
+            fin[k] = v;
+        }
+    }
 }
 
 // Sum of v over the block in a fixed order (same result every run).
@@ -60,16 +84,30 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(FinalParams p, T *__re
         if (t == 0) tot[i] = v;
     }
 
-    const int ncand_all = p.ehrenfest ? *p.cand_count : 0;
-    const int n = ncand_all < p.cand_cap ? ncand_all : p.cand_cap;
+    const int nrec = p.ehrenfest ? *p.cand_count : 0;
+    const int n = nrec < p.cand_cap ? nrec : p.cand_cap;
     const long long k = p.k_max;
     if (t == 0) s_nsel = 0;
+    if (Q == 9 && p.recompute) {
+        // FP64 key of each recorded site from the pre-step populations; sites at
+        // or below the threshold drop out (key -1)
+        for (int i = t; i < n; i += kFinThreads) {
+            const int site = p.cand[i].site;
+            double g[9], gs[9], gp[9], d64, din64, r64;
+            pull_d2q9_f64(p, site % p.nx, site / p.nx, g);
+            const bool bad = site_collide<9, double>(g, p.a, true, gs, gp, d64, din64, r64);
+            p.cand[i].key = (!bad && d64 > p.delta_e) ? d64 : -1.0;
+        }
+    }
     __syncthreads();
+    int nv = 0;
+    for (int i = t; i < n; i += kFinThreads) nv += p.cand[i].key > p.delta_e;
+    const int n_valid = (int)block_sum((double)nv, red);
     double ehr_sum = 0.0;
-    if (p.ehrenfest && k > 0 && n > 0) {
+    if (p.ehrenfest && k > 0 && n_valid > 0) {
         unsigned long long kv = 0;  // threshold dS pattern
         int site_thr = 0x7fffffff;
-        bool take_all = (long long)n <= k;
+        bool take_all = (long long)n_valid <= k;
         if (!take_all) {
             unsigned long long prefix = 0, mask = 0;
             long long rem = k;
@@ -77,8 +115,9 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(FinalParams p, T *__re
                 for (int d = t; d < 256; d += kFinThreads) hist[d] = 0;
                 __syncthreads();
                 for (int i = t; i < n; i += kFinThreads) {
-                    const unsigned long long u = key_bits(p.cand[i].key);
-                    if ((u & mask) == prefix) atomicAdd(&hist[(u >> shift) & 255u], 1u);
+                    const double key = p.cand[i].key;
+                    const unsigned long long u = key_bits(key);
+                    if (key > p.delta_e && (u & mask) == prefix) atomicAdd(&hist[(u >> shift) & 255u], 1u);
                 }
                 __syncthreads();
                 if (t == 0) {
@@ -107,7 +146,8 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(FinalParams p, T *__re
                 for (int i = t; i < n; i += kFinThreads) {
                     const Cand c = p.cand[i];
                     const unsigned s = (unsigned)c.site;
-                    if (key_bits(c.key) == kv && (s & smask) == sprefix) atomicAdd(&hist[(s >> shift) & 255u], 1u);
+                    if (c.key > p.delta_e && key_bits(c.key) == kv && (s & smask) == sprefix)
+                        atomicAdd(&hist[(s >> shift) & 255u], 1u);
                 }
                 __syncthreads();
                 if (t == 0) {
@@ -133,7 +173,7 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(FinalParams p, T *__re
         for (int i = t; i < n; i += kFinThreads) {
             const Cand c = p.cand[i];
             const unsigned long long u = key_bits(c.key);
-            const bool chosen = take_all || u > kv || (u == kv && c.site <= site_thr);
+            const bool chosen = c.key > p.delta_e && (take_all || u > kv || (u == kv && c.site <= site_thr));
             if (chosen) {
                 const int j = atomicAdd(&s_nsel, 1);
                 if (j < p.sel_cap) p.sel[j] = i;
@@ -177,8 +217,14 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(FinalParams p, T *__re
             T g[Q], fs[Q], rho, ux, uy;
 #pragma unroll
             for (int q = 0; q < Q; ++q) g[q] = f[fidx(p.plane, p.pitch, q, y, x)];
-            moments<Q, T>(g, rho, ux, uy);
-            feq<Q, T>(rho, ux, uy, fs);
+            if constexpr (std::is_same<T, float>::value) {
+                float drho;  // FP32 storage: deviations, equilibrium in deviation form
+                moments_dev<Q>(g, p.rho_ref, drho, rho, ux, uy);
+                feq_dev<Q>(drho, rho, ux, uy, fs);
+            } else {
+                moments<Q, T>(g, rho, ux, uy);
+                feq<Q, T>(rho, ux, uy, fs);
+            }
 #pragma unroll
             for (int q = 0; q < Q; ++q) f[fidx(p.plane, p.pitch, q, y, x)] = fs[q];
             ehr_sum = Ar<double>::add(ehr_sum, Ar<double>::mul(Ar<double>::mul(c.phi, c.phi), c.key));
@@ -211,7 +257,7 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(FinalParams p, T *__re
         st.n_pos = (long long)tot[P_NPOS];
         st.n_med = (long long)tot[P_NMED];
         st.n_ehr = s_nsel;
-        st.n_cand = ncand_all;
+        st.n_cand = n_valid;
         st.n_bad = (long long)tot[P_NBAD];
         const unsigned sb = *p.status;
         st.status = (sb & kStatNonfinite) ? 4 : ((sb & kStatTimeout) ? 5 : 0);

@@ -46,6 +46,9 @@ struct StepParams {
     double a;                  // 2 beta - 1
     double delta_m, delta_e;
     double lid[9];             // ((6 W_k) rho_wall) (c_kx u_lid), added on links through the lid
+    float rho_ref;             // FP32 storage holds g_k = f_k - rho_ref W_k
+    double rw[9];              // rho_ref W_k in FP64 (absolute value of FP32 storage: (double) g + rw)
+    float rwf[9];              // rho_ref W_k in FP32
     // scratch (library-owned)
     Cand *cand;
     int *cand_count;
@@ -74,6 +77,15 @@ struct FinalParams {
     DevStats *stats_ring;
     int ring_len;
     long long *counters;       // [0] steps taken (incremented when collide), [1] records written
+    // candidates recorded without an FP64 key (fused kernel): the key dS(f') is
+    // recomputed in FP64 from the pre-step populations `src` before selection
+    int recompute;
+    const float *src;
+    int boundary;
+    double a, delta_e;
+    double lid[9];
+    float rho_ref;
+    double rw[9];
 };
 
 // Launchers (stream-ordered, no synchronisation).  Return cudaGetLastError().
@@ -82,18 +94,18 @@ cudaError_t launch_tiled(int q, const StepParams &p, const T *src, T *dst, int *
                          cudaStream_t s);
 template <typename T>
 cudaError_t launch_finalize(int q, const FinalParams &p, T *f, cudaStream_t s);
+// Field kernels take the StepParams of the context for the layout (nx, ny,
+// pitch, plane) and the FP32 storage offsets (rw).
 template <typename T>
-cudaError_t launch_init(int q, int nx, int ny, int pitch, long long plane, const double *rho,
-                        const double *ux, const double *uy, T *f, cudaStream_t s);
+cudaError_t launch_init(int q, const StepParams &p, const double *rho, const double *ux, const double *uy, T *f,
+                        cudaStream_t s);
 template <typename T>
-cudaError_t launch_moments(int q, int nx, int ny, int pitch, long long plane, const T *f,
-                           double *rho, double *ux, double *uy, cudaStream_t s);
+cudaError_t launch_moments(int q, const StepParams &p, const T *f, double *rho, double *ux, double *uy,
+                           cudaStream_t s);
 template <typename T>
-cudaError_t launch_get(int q, int nx, int ny, int pitch, long long plane, const T *f, double *out,
-                       cudaStream_t s);
+cudaError_t launch_get(int q, const StepParams &p, const T *f, double *out, cudaStream_t s);
 template <typename T>
-cudaError_t launch_set(int q, int nx, int ny, int pitch, long long plane, const double *in, T *f,
-                       cudaStream_t s);
+cudaError_t launch_set(int q, const StepParams &p, const double *in, T *f, cudaStream_t s);
 template <typename T>
 cudaError_t launch_delta_s(int q, const StepParams &p, const T *f, double *out, cudaStream_t s);
 
@@ -101,5 +113,6 @@ cudaError_t launch_delta_s(int q, const StepParams &p, const T *f, double *out, 
 cudaError_t launch_fused_d2q9(const StepParams &p, const float *src, float *dst, int *nblocks,
                               cudaStream_t s);
 int fused_d2q9_blocks(int nx, int ny);
+bool fused_d2q9_fits(long long plane);  // 32-bit plane offsets inside the kernel
 
 }  // namespace lbm

@@ -15,6 +15,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace lbm {
 
 template <typename T> struct Ar;
@@ -98,6 +100,9 @@ __device__ __forceinline__ void moments3(const T f[3], T &rho, T &ux, T &uy)
 }
 
 // Eq. polyeq2d: f*_k = rho W_k (1 + 3 v_k.u + 9 (v_k.u)^2 / 2 - 3 u^2 / 2).
+// FP32: the rest population is taken as rho minus the other eight, which is
+// the same value in exact arithmetic and keeps sum_k f*_k = rho up to unbiased
+// rounding (the FP32 weights alone sum to 1 + 7.5e-9, a steady mass gain).
 template <typename T>
 __device__ __forceinline__ void feq9(T rho, T ux, T uy, T fs[9])
 {
@@ -112,6 +117,10 @@ __device__ __forceinline__ void feq9(T rho, T ux, T uy, T fs[9])
         poly = A::sub(poly, tail);
         fs[k] = A::mul(A::mul(rho, T(Lat<9>::w(k))), poly);
     }
+    if constexpr (std::is_same<T, float>::value) {
+        T rest = ((fs[1] + fs[2]) + (fs[3] + fs[4])) + ((fs[5] + fs[6]) + (fs[7] + fs[8]));
+        fs[0] = rho - rest;
+    }
 }
 
 // Eq. polyeq1d, term by term as printed.
@@ -124,6 +133,7 @@ __device__ __forceinline__ void feq3(T rho, T u, T fs[3])
     const T r6 = A::div(rho, T(6));
     fs[1] = A::mul(r6, A::add(A::sub(T(1), A::mul(T(3), u)), A::mul(T(3), uu)));
     fs[2] = A::mul(r6, A::add(A::add(T(1), A::mul(T(3), u)), A::mul(T(3), uu)));
+    if constexpr (std::is_same<T, float>::value) fs[0] = rho - (fs[1] + fs[2]);  // see feq9
 }
 
 template <int Q, typename T>
@@ -211,6 +221,118 @@ __device__ __forceinline__ T phi_median(T x, T med, T delta, int mode)
     }
     const T t = med > delta ? med : delta;
     return x > t ? A::sqrt(A::div(t, x)) : T(1);
+}
+
+// ---------------------------------------------------------------------------
+// FP32 storage holds deviations g_k = f_k - rho_ref W_k from a uniform rest
+// state (the D2Q9 and D1Q3 weights are symmetric under k -> opp(k), so
+// bounce-back and the lid term act on g exactly as on f).  Moments, f* and
+// the collision are evaluated on the deviations, which keeps three to four
+// more significant bits than storing f itself:
+//   rho = rho_ref + sum_k g_k,  rho u = sum_k v_k g_k,
+//   g*_k = f*_k - rho_ref W_k = W_k (drho + rho e_k) + 3 W_k rho (v_k . u)
+// with e_k = 9 (v_k.u)^2 / 2 - 3 u^2 / 2 (Eq. polyeq2d).  The rest deviation
+// closes the mass: g*_0 = drho - sum_{k>0} g*_k.
+
+__device__ __forceinline__ void moments9_dev(const float g[9], float rho_ref, float &drho, float &rho, float &ux,
+                                             float &uy)
+{
+    drho = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
+    rho = rho_ref + drho;
+    const float jx = ((g[1] - g[3]) + (g[5] - g[6])) + (g[8] - g[7]);
+    const float jy = ((g[2] - g[4]) + (g[5] + g[6])) - (g[7] + g[8]);
+    const float inv = __fdividef(1.0f, rho);
+    ux = jx * inv;
+    uy = jy * inv;
+}
+
+__device__ __forceinline__ void feq9_dev(float drho, float rho, float ux, float uy, float gs[9])
+{
+    const float w1 = 1.0f / 9.0f, w5 = 1.0f / 36.0f;
+    const float m = -1.5f * fmaf(ux, ux, uy * uy);
+    const float b1 = 3.0f * w1 * rho, b5 = 3.0f * w5 * rho;
+    const float cp = ux + uy, cm = uy - ux;
+    float e = fmaf(4.5f * ux, ux, m), A = w1 * fmaf(rho, e, drho), B = b1 * ux;
+    gs[1] = A + B;
+    gs[3] = A - B;
+    e = fmaf(4.5f * uy, uy, m);
+    A = w1 * fmaf(rho, e, drho);
+    B = b1 * uy;
+    gs[2] = A + B;
+    gs[4] = A - B;
+    e = fmaf(4.5f * cp, cp, m);
+    A = w5 * fmaf(rho, e, drho);
+    B = b5 * cp;
+    gs[5] = A + B;
+    gs[7] = A - B;
+    e = fmaf(4.5f * cm, cm, m);
+    A = w5 * fmaf(rho, e, drho);
+    B = b5 * cm;
+    gs[6] = A + B;
+    gs[8] = A - B;
+    gs[0] = drho - (((gs[1] + gs[2]) + (gs[3] + gs[4])) + ((gs[5] + gs[6]) + (gs[7] + gs[8])));
+}
+
+// D1Q3 (Eq. polyeq1d): g*_{1,2} = (drho + 3 rho u^2)/6 -/+ rho u / 2.
+__device__ __forceinline__ void moments3_dev(const float g[3], float rho_ref, float &drho, float &rho, float &ux,
+                                             float &uy)
+{
+    drho = (g[0] + g[1]) + g[2];
+    rho = rho_ref + drho;
+    ux = __fdividef(g[2] - g[1], rho);
+    uy = 0.0f;
+}
+
+__device__ __forceinline__ void feq3_dev(float drho, float rho, float u, float gs[3])
+{
+    const float A = (1.0f / 6.0f) * fmaf(3.0f * rho * u, u, drho), B = 0.5f * rho * u;
+    gs[1] = A - B;
+    gs[2] = A + B;
+    gs[0] = drho - (gs[1] + gs[2]);
+}
+
+template <int Q>
+__device__ __forceinline__ void moments_dev(const float g[Q], float rho_ref, float &drho, float &rho, float &ux,
+                                            float &uy)
+{
+    if constexpr (Q == 9)
+        moments9_dev(g, rho_ref, drho, rho, ux, uy);
+    else
+        moments3_dev(g, rho_ref, drho, rho, ux, uy);
+}
+
+template <int Q>
+__device__ __forceinline__ void feq_dev(float drho, float rho, float ux, float uy, float gs[Q])
+{
+    if constexpr (Q == 9)
+        feq9_dev(drho, rho, ux, uy, gs);
+    else
+        feq3_dev(drho, rho, ux, gs);
+}
+
+// FP32 counterpart of site_collide on deviations: g* and g' (deviations of f*
+// and f'), the absolute f* (rw_k + g*_k, for the entropy denominators and the
+// positivity rule), dS(f') = (2 beta - 1)^2 dS(f_in), dS(f_in), rho.
+template <int Q>
+__device__ __forceinline__ bool site_collide_dev(const float g[Q], float a, bool collide, float rho_ref,
+                                                 const float rw[Q], float gs[Q], float gp[Q], float fsa[Q],
+                                                 float &ds, float &ds_in, float &rho)
+{
+    float drho, ux, uy;
+    moments_dev<Q>(g, rho_ref, drho, rho, ux, uy);
+    feq_dev<Q>(drho, rho, ux, uy, gs);
+    float din = 0.f, fmin = 3.4e38f;
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+        const float d = gs[k] - g[k];
+        fsa[k] = rw[k] + gs[k];
+        din = fmaf(d, __fdividef(d, fsa[k]), din);
+        gp[k] = collide ? fmaf(a, d, gs[k]) : g[k];
+        fmin = fminf(fmin, fsa[k]);
+    }
+    ds_in = collide ? din : 0.f;
+    ds = collide ? a * a * din : din;
+    return !(rho > 0.f) || !(fmin > 0.f) || !isfinite(ds);
 }
 
 template <typename T> __device__ __forceinline__ T tmin(T a, T b) { return b < a ? b : a; }

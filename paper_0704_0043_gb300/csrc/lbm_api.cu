@@ -82,7 +82,7 @@ int lattice_q(int lattice) { return lattice == LBM_D1Q3 ? 3 : 9; }
 bool fused_applies(const lbm_config &c)
 {
     return c.lattice == LBM_D2Q9 && c.precision == LBM_FP32 && c.boundary == LBM_BC_WALLS &&
-           c.kernel == LBM_KERNEL_FUSED;
+           c.kernel != LBM_KERNEL_TILED && fused_d2q9_fits((long long)c.ny * row_pitch(c.nx));
 }
 
 int tiled_blocks(const lbm_config &c)
@@ -105,8 +105,8 @@ std::string validate(const lbm_config *c)
         if (c->boundary == LBM_BC_WALLS && c->nx < 3) return "D1Q3 with closed ends needs nx >= 3";
     } else {
         if (c->boundary < LBM_BC_WALLS || c->boundary > LBM_BC_CHANNEL) return "unknown boundary kind";
-        if (c->boundary == LBM_BC_WALLS && (c->nx < 4 || c->ny < 4)) return "D2Q9 cavity needs nx, ny >= 4";
-        if (c->boundary == LBM_BC_CHANNEL && c->ny < 4) return "D2Q9 channel needs ny >= 4";
+        if (c->boundary == LBM_BC_WALLS && (c->nx < 2 || c->ny < 2)) return "D2Q9 cavity needs nx, ny >= 2";
+        if (c->boundary == LBM_BC_CHANNEL && c->ny < 2) return "D2Q9 channel needs ny >= 2";
     }
     if (c->limiters & ~7u) return "unknown limiter bits";
     if (!(c->beta >= 0.0 && c->beta <= 1.0)) return "beta must lie in [0, 1]";
@@ -118,6 +118,7 @@ std::string validate(const lbm_config *c)
     if (c->kernel == LBM_KERNEL_FUSED && !fused_applies(*c))
         return "LBM_KERNEL_FUSED needs D2Q9, LBM_FP32 and LBM_BC_WALLS";
     if (c->stats_history < 0) return "stats_history must be >= 0";
+    if (!(c->rho_ref > 0.0) || !std::isfinite(c->rho_ref)) return "rho_ref must be finite and > 0";
     return "";
 }
 
@@ -212,6 +213,12 @@ StepParams step_params(lbm_ctx *c, int collide, unsigned limiters)
         const bool lid = c->q == 9 && g.boundary != LBM_BC_PERIODIC && Lat<9>::cy(k) == -1;
         p.lid[k] = lid ? ((6.0 * Lat<9>::w(k)) * g.rho_wall) * ((double)Lat<9>::cx(k) * g.u_lid) : 0.0;
     }
+    p.rho_ref = (float)g.rho_ref;
+    for (int k = 0; k < 9; ++k) {
+        const double w = c->q == 9 ? Lat<9>::w(k) : (k < 3 ? Lat<3>::w(k) : 0.0);
+        p.rw[k] = g.rho_ref * w;
+        p.rwf[k] = (float)p.rw[k];
+    }
     p.cand = c->cand;
     p.cand_count = c->counts;
     p.cand_cap = c->cand_cap;
@@ -290,6 +297,16 @@ lbm_status run_pass(lbm_ctx *c, int collide, unsigned limiters)
     if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
     if ((ms = mark(c)) != LBM_OK) return ms;
     FinalParams f = final_params(c, collide, limiters, nblocks);
+    if (collide && c->cfg.precision == LBM_FP32 && fused_applies(c->cfg)) {
+        f.recompute = 1;
+        f.src = (const float *)src;
+        f.boundary = c->cfg.boundary;
+        f.a = p.a;
+        f.delta_e = p.delta_e;
+        for (int k = 0; k < 9; ++k) f.lid[k] = p.lid[k];
+    }
+    f.rho_ref = p.rho_ref;
+    for (int k = 0; k < 9; ++k) f.rw[k] = p.rw[k];
     if (c->cfg.precision == LBM_FP64)
         e = launch_finalize<double>(c->q, f, (double *)dst, c->stream);
     else
@@ -371,6 +388,7 @@ void lbm_config_default(lbm_config *c)
     c->delta_ehrenfest = 1e-3;
     c->k_max = 0;
     c->stats_history = 1;
+    c->rho_ref = 1.0;
 }
 
 int64_t lbm_footprint_bytes(const lbm_config *cfg)
@@ -453,10 +471,11 @@ lbm_status lbm_init(lbm_ctx *c, const double *rho, const double *ux, const doubl
     if ((s = dev_in(c, ux, n, n, &du)) != LBM_OK) return s;
     if (uy && c->q == 9 && (s = dev_in(c, uy, n, 2 * n, &dv)) != LBM_OK) return s;
     cudaError_t e;
+    const StepParams sp = step_params(c, 1, 0);
     if (c->cfg.precision == LBM_FP64)
-        e = launch_init<double>(c->q, c->cfg.nx, c->cfg.ny, c->pitch, c->plane, dr, du, dv, (double *)c->buf[0], c->stream);
+        e = launch_init<double>(c->q, sp, dr, du, dv, (double *)c->buf[0], c->stream);
     else
-        e = launch_init<float>(c->q, c->cfg.nx, c->cfg.ny, c->pitch, c->plane, dr, du, dv, (float *)c->buf[0], c->stream);
+        e = launch_init<float>(c->q, sp, dr, du, dv, (float *)c->buf[0], c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "init kernel launch");
     c->launches++;
     c->cur = 0;
@@ -529,11 +548,10 @@ lbm_status lbm_moments(lbm_ctx *c, double *rho, double *ux, double *uy)
         du = c->stage + n;
         dv = uy ? c->stage + 2 * n : nullptr;
     }
+    const StepParams sp = step_params(c, 1, 0);
     cudaError_t e = c->cfg.precision == LBM_FP64
-                        ? launch_moments<double>(c->q, c->cfg.nx, c->cfg.ny, c->pitch, c->plane,
-                                                 (const double *)c->buf[c->cur], dr, du, dv, c->stream)
-                        : launch_moments<float>(c->q, c->cfg.nx, c->cfg.ny, c->pitch, c->plane,
-                                                (const float *)c->buf[c->cur], dr, du, dv, c->stream);
+                        ? launch_moments<double>(c->q, sp, (const double *)c->buf[c->cur], dr, du, dv, c->stream)
+                        : launch_moments<float>(c->q, sp, (const float *)c->buf[c->cur], dr, du, dv, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "moments kernel launch");
     c->launches++;
     if (!dev) {
@@ -613,11 +631,10 @@ lbm_status lbm_get_populations(lbm_ctx *c, double *f)
         if (s != LBM_OK) return s;
         dst = c->stage;
     }
+    const StepParams sp = step_params(c, 1, 0);
     cudaError_t e = c->cfg.precision == LBM_FP64
-                        ? launch_get<double>(c->q, c->cfg.nx, c->cfg.ny, c->pitch, c->plane,
-                                             (const double *)c->buf[c->cur], dst, c->stream)
-                        : launch_get<float>(c->q, c->cfg.nx, c->cfg.ny, c->pitch, c->plane,
-                                            (const float *)c->buf[c->cur], dst, c->stream);
+                        ? launch_get<double>(c->q, sp, (const double *)c->buf[c->cur], dst, c->stream)
+                        : launch_get<float>(c->q, sp, (const float *)c->buf[c->cur], dst, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "get kernel launch");
     c->launches++;
     if (!dev) CK(c, cudaMemcpyAsync(f, dst, tot * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -636,11 +653,10 @@ lbm_status lbm_set_populations(lbm_ctx *c, const double *f)
         if (s != LBM_OK) return s;
         if ((s = dev_in(c, f, tot, 0, &src)) != LBM_OK) return s;
     }
+    const StepParams sp = step_params(c, 1, 0);
     cudaError_t e = c->cfg.precision == LBM_FP64
-                        ? launch_set<double>(c->q, c->cfg.nx, c->cfg.ny, c->pitch, c->plane, src,
-                                             (double *)c->buf[0], c->stream)
-                        : launch_set<float>(c->q, c->cfg.nx, c->cfg.ny, c->pitch, c->plane, src,
-                                            (float *)c->buf[0], c->stream);
+                        ? launch_set<double>(c->q, sp, src, (double *)c->buf[0], c->stream)
+                        : launch_set<float>(c->q, sp, src, (float *)c->buf[0], c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "set kernel launch");
     c->launches++;
     c->cur = 0;

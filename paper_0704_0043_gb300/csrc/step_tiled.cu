@@ -10,7 +10,8 @@
 // candidates (Sec. 3.2) and the block's FP64 partial sums (Sec. 3.4).  Tiles
 // overlap by one site on each side, so every site is finished by exactly one
 // block and the halo ring is recomputed.  In FP64 every operation runs in the
-// order of the formulas, unfused (see lattice.cuh).
+// order of the formulas, unfused (see lattice.cuh).  FP32 storage holds the
+// deviations g = f - rho_ref W and the FP32 arithmetic runs on them.
 #include <type_traits>
 
 #include "internal.h"
@@ -27,10 +28,22 @@ __device__ __forceinline__ long long fidx(long long plane, int pitch, int k, int
     return (long long)k * plane + (long long)y * pitch + kLead + x;
 }
 
+// Stored value as a compute value: FP64 storage is f itself; FP32 storage is
+// the deviation g, read as g in FP32 or as the absolute f = (double) g + rw_k
+// in FP64.
+template <typename S, typename T>
+__device__ __forceinline__ T load_as(const StepParams &p, S v, int k)
+{
+    if constexpr (std::is_same<S, float>::value && std::is_same<T, double>::value)
+        return Ar<double>::add((double)v, p.rw[k]);
+    else
+        return T(v);
+}
+
 // Free flight in pull form at site (x, y) (Sec. 2): f_in_k(x) = f_k(x - v_k);
 // a link leaving the lattice is reflected, f_in_k(x) = f_opp(k)(x) (halfway
 // bounce-back, Sec. 4.4.1), plus the moving-wall term for links through the lid.
-// Reads storage type S, returns compute type T.
+// Reads storage type S, returns compute type T (see load_as).
 template <int Q, typename S, typename T>
 __device__ __forceinline__ void pull(const StepParams &p, const S *__restrict__ f, int x, int y, T fin[Q])
 {
@@ -43,9 +56,9 @@ __device__ __forceinline__ void pull(const StepParams &p, const S *__restrict__ 
         if (wrapx) sx = sx < 0 ? sx + p.nx : (sx >= p.nx ? sx - p.nx : sx);
         if (wrapy) sy = sy < 0 ? sy + p.ny : (sy >= p.ny ? sy - p.ny : sy);
         if (sx >= 0 && sx < p.nx && sy >= 0 && sy < p.ny) {
-            fin[k] = T(f[fidx(p.plane, p.pitch, k, sy, sx)]);
+            fin[k] = load_as<S, T>(p, f[fidx(p.plane, p.pitch, k, sy, sx)], k);
         } else {
-            T v = T(f[fidx(p.plane, p.pitch, Lat<Q>::opp(k), y, x)]);
+            T v = load_as<S, T>(p, f[fidx(p.plane, p.pitch, Lat<Q>::opp(k), y, x)], Lat<Q>::opp(k));
             if (Q == 9 && sy > p.ny - 1) v = A::add(v, T(p.lid[k]));
             fin[k] = v;
         }
@@ -53,8 +66,11 @@ __device__ __forceinline__ void pull(const StepParams &p, const S *__restrict__ 
 }
 
 // Median of the dS stencil of site (x, y), tile-local position (tx, ty) in a
-// shared array with row stride `ld` (Sec. 3.5; wall rules of Sec. 4.4): returns
-// false for sites the filter skips.
+// shared array with row stride `ld` (Sec. 3.5; wall rules of Sec. 4.4, read for
+// walls half a link outside the lattice: a node next to one wall uses itself
+// and its two neighbours along that wall, a corner node itself and its inward
+// x and y neighbours, every other node the 3x3 block; the two end sites of a
+// closed D1Q3 tube are not filtered).  Returns false for sites the filter skips.
 template <int Q, typename T>
 __device__ __forceinline__ bool stencil_median(const StepParams &p, const T *s, int ld, int tx, int ty,
                                                int x, int y, T &med)
@@ -66,11 +82,10 @@ __device__ __forceinline__ bool stencil_median(const StepParams &p, const T *s, 
         return true;
     } else {
         const bool wallx = p.boundary == 0, wally = p.boundary != 1;
-        if ((wallx && (x == 0 || x == p.nx - 1)) || (wally && (y == 0 || y == p.ny - 1))) return false;
-        const bool nearx = wallx && (x == 1 || x == p.nx - 2);
-        const bool neary = wally && (y == 1 || y == p.ny - 2);
+        const bool nearx = wallx && (x == 0 || x == p.nx - 1);
+        const bool neary = wally && (y == 0 || y == p.ny - 1);
         if (nearx && neary) {
-            const int dx = x == 1 ? 1 : -1, dy = y == 1 ? 1 : -1;
+            const int dx = x == 0 ? 1 : -1, dy = y == 0 ? 1 : -1;
             med = med3(S_(0, 0), S_(dx, 0), S_(0, dy));
         } else if (neary) {
             med = med3(S_(-1, 0), S_(0, 0), S_(1, 0));
@@ -110,7 +125,8 @@ __global__ void __launch_bounds__(256) k_tiled(StepParams p, const T *__restrict
     const int xs = wrapx ? (x < 0 ? x + p.nx : (x >= p.nx ? x - p.nx : x)) : x;
     const int ys = wrapy ? (y < 0 ? y + p.ny : (y >= p.ny ? y - p.ny : y)) : y;
 
-    T fin[Q], fs[Q], fp[Q];
+    // FP64: fs = f*, fp = f'.  FP32: fs = g*, fp = g' (deviations), fa = absolute f*.
+    T fin[Q], fs[Q], fp[Q], fa[Q];
     T ds = T(0), dsin = T(0), rho = T(0);
     bool bad = false;
     if (valid) {
@@ -120,7 +136,13 @@ __global__ void __launch_bounds__(256) k_tiled(StepParams p, const T *__restrict
 #pragma unroll
             for (int k = 0; k < Q; ++k) fin[k] = src[fidx(p.plane, p.pitch, k, ys, xs)];
         }
-        bad = site_collide<Q, T>(fin, T(p.a), p.collide != 0, fs, fp, ds, dsin, rho);
+        if constexpr (std::is_same<T, double>::value) {
+            bad = site_collide<Q, T>(fin, T(p.a), p.collide != 0, fs, fp, ds, dsin, rho);
+#pragma unroll
+            for (int k = 0; k < Q; ++k) fa[k] = fs[k];
+        } else {
+            bad = site_collide_dev<Q>(fin, (float)p.a, p.collide != 0, p.rho_ref, p.rwf, fs, fp, fa, ds, dsin, rho);
+        }
         if (bad) ds = T(INFINITY);
     }
     sds[ty * BX + tx] = ds;
@@ -134,7 +156,17 @@ __global__ void __launch_bounds__(256) k_tiled(StepParams p, const T *__restrict
     if (own) {
         T phi_pos = T(1), phi_med = T(1);
         if (!bad) {
-            if (p.limiters & 1u) phi_pos = phi_positivity<Q, T>(fs, fp);
+            if (p.limiters & 1u) {
+                if constexpr (std::is_same<T, double>::value) {
+                    phi_pos = phi_positivity<Q, T>(fs, fp);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < Q; ++k) {
+                        const float fpa = p.rwf[k] + fp[k];  // absolute f'
+                        if (fpa < 0.f) phi_pos = fminf(phi_pos, fa[k] / (fa[k] - fpa));
+                    }
+                }
+            }
             if (p.limiters & 4u) {
                 T med;
                 if (stencil_median<Q, T>(p, sds, BX, tx, ty, x, y, med))
@@ -176,7 +208,7 @@ __global__ void __launch_bounds__(256) k_tiled(StepParams p, const T *__restrict
                         pull<Q, T, double>(p, src, x, y, fin64);
                     } else {
 #pragma unroll
-                        for (int k = 0; k < Q; ++k) fin64[k] = (double)src[fidx(p.plane, p.pitch, k, y, x)];
+                        for (int k = 0; k < Q; ++k) fin64[k] = load_as<T, double>(p, src[fidx(p.plane, p.pitch, k, y, x)], k);
                     }
                     const bool b64 = site_collide<Q, double>(fin64, p.a, p.collide != 0, fs64, fp64, d64, din64, r64);
                     key = d64;
@@ -228,29 +260,34 @@ __global__ void k_delta_s(StepParams p, const T *__restrict__ f, double *__restr
 }
 
 template <int Q, typename T>
-__global__ void k_init(int nx, int ny, int pitch, long long plane, const double *__restrict__ rho,
-                       const double *__restrict__ ux, const double *__restrict__ uy, T *__restrict__ f)
+__global__ void k_init(StepParams p, const double *__restrict__ rho, const double *__restrict__ ux,
+                       const double *__restrict__ uy, T *__restrict__ f)
 {
-    const long long n = (long long)nx * ny;
+    const long long n = (long long)p.nx * p.ny;
     for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(s % nx), y = (int)(s / nx);
+        const int x = (int)(s % p.nx), y = (int)(s / p.nx);
         double fs[Q];
         feq<Q, double>(rho[s], ux[s], uy ? uy[s] : 0.0, fs);
 #pragma unroll
-        for (int k = 0; k < Q; ++k) f[fidx(plane, pitch, k, y, x)] = T(fs[k]);
+        for (int k = 0; k < Q; ++k) {
+            if constexpr (std::is_same<T, float>::value)
+                f[fidx(p.plane, p.pitch, k, y, x)] = (float)Ar<double>::sub(fs[k], p.rw[k]);
+            else
+                f[fidx(p.plane, p.pitch, k, y, x)] = fs[k];
+        }
     }
 }
 
 template <int Q, typename T>
-__global__ void k_moments(int nx, int ny, int pitch, long long plane, const T *__restrict__ f,
-                          double *__restrict__ rho, double *__restrict__ ux, double *__restrict__ uy)
+__global__ void k_moments(StepParams p, const T *__restrict__ f, double *__restrict__ rho, double *__restrict__ ux,
+                          double *__restrict__ uy)
 {
-    const long long n = (long long)nx * ny;
+    const long long n = (long long)p.nx * p.ny;
     for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(s % nx), y = (int)(s / nx);
+        const int x = (int)(s % p.nx), y = (int)(s / p.nx);
         double g[Q], r, a, b;
 #pragma unroll
-        for (int k = 0; k < Q; ++k) g[k] = (double)f[fidx(plane, pitch, k, y, x)];
+        for (int k = 0; k < Q; ++k) g[k] = load_as<T, double>(p, f[fidx(p.plane, p.pitch, k, y, x)], k);
         moments<Q, double>(g, r, a, b);
         rho[s] = r;
         ux[s] = a;
@@ -259,24 +296,29 @@ __global__ void k_moments(int nx, int ny, int pitch, long long plane, const T *_
 }
 
 template <typename T>
-__global__ void k_get(int q, int nx, int ny, int pitch, long long plane, const T *__restrict__ f, double *__restrict__ out)
+__global__ void k_get(int q, StepParams p, const T *__restrict__ f, double *__restrict__ out)
 {
-    const long long n = (long long)nx * ny, tot = n * q;
+    const long long n = (long long)p.nx * p.ny, tot = n * q;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
         const int k = (int)(e / n);
         const long long s = e % n;
-        out[e] = (double)f[fidx(plane, pitch, k, (int)(s / nx), (int)(s % nx))];
+        out[e] = load_as<T, double>(p, f[fidx(p.plane, p.pitch, k, (int)(s / p.nx), (int)(s % p.nx))], k);
     }
 }
 
 template <typename T>
-__global__ void k_set(int q, int nx, int ny, int pitch, long long plane, const double *__restrict__ in, T *__restrict__ f)
+__global__ void k_set(int q, StepParams p, const double *__restrict__ in, T *__restrict__ f)
 {
-    const long long n = (long long)nx * ny, tot = n * q;
+    const long long n = (long long)p.nx * p.ny, tot = n * q;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
         const int k = (int)(e / n);
         const long long s = e % n;
-        f[fidx(plane, pitch, k, (int)(s / nx), (int)(s % nx))] = T(in[e]);
+        T v;
+        if constexpr (std::is_same<T, float>::value)
+            v = (float)Ar<double>::sub(in[e], p.rw[k]);
+        else
+            v = in[e];
+        f[fidx(p.plane, p.pitch, k, (int)(s / p.nx), (int)(s % p.nx))] = v;
     }
 }
 
@@ -316,52 +358,52 @@ cudaError_t launch_delta_s(int q, const StepParams &p, const T *f, double *out, 
 }
 
 template <typename T>
-cudaError_t launch_init(int q, int nx, int ny, int pitch, long long plane, const double *rho, const double *ux,
-                        const double *uy, T *f, cudaStream_t s)
+cudaError_t launch_init(int q, const StepParams &p, const double *rho, const double *ux, const double *uy, T *f,
+                        cudaStream_t s)
 {
-    const int g = grid_for((long long)nx * ny, 256);
+    const int g = grid_for((long long)p.nx * p.ny, 256);
     if (q == 9)
-        k_init<9, T><<<g, 256, 0, s>>>(nx, ny, pitch, plane, rho, ux, uy, f);
+        k_init<9, T><<<g, 256, 0, s>>>(p, rho, ux, uy, f);
     else
-        k_init<3, T><<<g, 256, 0, s>>>(nx, ny, pitch, plane, rho, ux, nullptr, f);
+        k_init<3, T><<<g, 256, 0, s>>>(p, rho, ux, nullptr, f);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_moments(int q, int nx, int ny, int pitch, long long plane, const T *f, double *rho, double *ux,
-                           double *uy, cudaStream_t s)
+cudaError_t launch_moments(int q, const StepParams &p, const T *f, double *rho, double *ux, double *uy,
+                           cudaStream_t s)
 {
-    const int g = grid_for((long long)nx * ny, 256);
+    const int g = grid_for((long long)p.nx * p.ny, 256);
     if (q == 9)
-        k_moments<9, T><<<g, 256, 0, s>>>(nx, ny, pitch, plane, f, rho, ux, uy);
+        k_moments<9, T><<<g, 256, 0, s>>>(p, f, rho, ux, uy);
     else
-        k_moments<3, T><<<g, 256, 0, s>>>(nx, ny, pitch, plane, f, rho, ux, uy);
+        k_moments<3, T><<<g, 256, 0, s>>>(p, f, rho, ux, uy);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_get(int q, int nx, int ny, int pitch, long long plane, const T *f, double *out, cudaStream_t s)
+cudaError_t launch_get(int q, const StepParams &p, const T *f, double *out, cudaStream_t s)
 {
-    k_get<T><<<grid_for((long long)nx * ny * q, 256), 256, 0, s>>>(q, nx, ny, pitch, plane, f, out);
+    k_get<T><<<grid_for((long long)p.nx * p.ny * q, 256), 256, 0, s>>>(q, p, f, out);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_set(int q, int nx, int ny, int pitch, long long plane, const double *in, T *f, cudaStream_t s)
+cudaError_t launch_set(int q, const StepParams &p, const double *in, T *f, cudaStream_t s)
 {
-    k_set<T><<<grid_for((long long)nx * ny * q, 256), 256, 0, s>>>(q, nx, ny, pitch, plane, in, f);
+    k_set<T><<<grid_for((long long)p.nx * p.ny * q, 256), 256, 0, s>>>(q, p, in, f);
     return cudaGetLastError();
 }
 
 #define LBM_INST(T)                                                                                           \
     template cudaError_t launch_tiled<T>(int, const StepParams &, const T *, T *, int *, cudaStream_t);     \
     template cudaError_t launch_delta_s<T>(int, const StepParams &, const T *, double *, cudaStream_t);     \
-    template cudaError_t launch_init<T>(int, int, int, int, long long, const double *, const double *,      \
+    template cudaError_t launch_init<T>(int, const StepParams &, const double *, const double *,           \
                                         const double *, T *, cudaStream_t);                                  \
-    template cudaError_t launch_moments<T>(int, int, int, int, long long, const T *, double *, double *,    \
-                                           double *, cudaStream_t);                                          \
-    template cudaError_t launch_get<T>(int, int, int, int, long long, const T *, double *, cudaStream_t);   \
-    template cudaError_t launch_set<T>(int, int, int, int, long long, const double *, T *, cudaStream_t);
+    template cudaError_t launch_moments<T>(int, const StepParams &, const T *, double *, double *, double *, \
+                                           cudaStream_t);                                                    \
+    template cudaError_t launch_get<T>(int, const StepParams &, const T *, double *, cudaStream_t);         \
+    template cudaError_t launch_set<T>(int, const StepParams &, const double *, T *, cudaStream_t);
 LBM_INST(float)
 LBM_INST(double)
 #undef LBM_INST

@@ -34,7 +34,7 @@ class Config(ctypes.Structure):
         ("median_mode", ctypes.c_int32), ("kernel", ctypes.c_int32), ("beta", ctypes.c_double),
         ("u_lid", ctypes.c_double), ("rho_wall", ctypes.c_double), ("delta_median", ctypes.c_double),
         ("delta_ehrenfest", ctypes.c_double), ("k_max", ctypes.c_int64),
-        ("stats_history", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("stats_history", ctypes.c_int32), ("reserved", ctypes.c_int32), ("rho_ref", ctypes.c_double),
     ]
 
 

@@ -34,7 +34,7 @@ def test_config_validation_without_gpu(lib):
     from paper_0704_0043_gb300 import lbm
     base = dict(lattice=lbm.D2Q9, nx=100, ny=100, precision=lbm.FP32, boundary=lbm.BC_WALLS)
     assert lbm.footprint_bytes(**base) > 2 * 9 * 100 * 100 * 4
-    bad = [dict(nx=3), dict(lattice=3), dict(beta=1.5), dict(limiters=8), dict(k_max=-1),
+    bad = [dict(nx=1), dict(lattice=3), dict(beta=1.5), dict(limiters=8), dict(k_max=-1),
            dict(lattice=lbm.D1Q3, ny=2), dict(lattice=lbm.D1Q3, ny=1, boundary=lbm.BC_CHANNEL),
            dict(precision=7), dict(delta_median=-1.0), dict(median_mode=5),
            dict(kernel=lbm.KERNEL_FUSED, precision=lbm.FP64)]

@@ -116,11 +116,9 @@ def stencil(p, dS, i, j):
             return None
         return [dS[(0, i - 1)], dS[(0, i)], dS[(0, i + 1)]]
     wallx, wally = bc == "walls", bc != "periodic"
-    if (wallx and i in (0, nx - 1)) or (wally and j in (0, ny - 1)):
-        return None
-    nearx, neary = wallx and i in (1, nx - 2), wally and j in (1, ny - 2)
+    nearx, neary = wallx and i in (0, nx - 1), wally and j in (0, ny - 1)
     if nearx and neary:
-        return [dS[(j, i)], dS[(j, 2 if i == 1 else nx - 3)], dS[(2 if j == 1 else ny - 3, i)]]
+        return [dS[(j, i)], dS[(j, 1 if i == 0 else nx - 2)], dS[(1 if j == 0 else ny - 2, i)]]
     if neary:
         return [dS[(j, (i + d) % nx)] for d in (-1, 0, 1)]
     if nearx:

@@ -95,17 +95,15 @@ def test_positivity_rule_lands_on_the_positivity_boundary():
 
 
 def _stencil(dS, i, j):
-    """Wall rules of Sec. 4.4 (reading stated in the design notes): boundary
-    nodes unfiltered; next to one wall, the node and its two neighbours along
-    that wall; next to two walls, the node and its inward x and y neighbours;
-    elsewhere the 3 x 3 block."""
+    """Wall rules of Sec. 4.4 for walls half a link outside the lattice: a
+    node next to one wall uses itself and its two neighbours along that wall,
+    a corner node itself and its inward x and y neighbours, every other node
+    the 3 x 3 block."""
     ny, nx = dS.shape
-    if i in (0, nx - 1) or j in (0, ny - 1):
-        return None
-    nearx, neary = i in (1, nx - 2), j in (1, ny - 2)
+    nearx, neary = i in (0, nx - 1), j in (0, ny - 1)
     if nearx and neary:
-        ii = 2 if i == 1 else nx - 3
-        jj = 2 if j == 1 else ny - 3
+        ii = 1 if i == 0 else nx - 2
+        jj = 1 if j == 0 else ny - 2
         return np.array([dS[j, i], dS[j, ii], dS[jj, i]])
     if neary:
         return dS[j, i - 1:i + 2]
@@ -126,8 +124,6 @@ def test_median_filter_matches_numpy_median(mode, delta):
     for j in range(ny):
         for i in range(nx):
             st = _stencil(dS, i, j)
-            if st is None:
-                continue
             med = float(np.median(st))
             x = dS[j, i]
             if mode == oracle.MEDIAN_THRESHOLD:
