@@ -273,8 +273,7 @@ def main():
     kern_s = step_ms / 1e3 / max(timed, 1)
     achieved = bps * w.sites / kern_s / 1e9
     peak, peak_kind = peaks()
-    kname = "fused" if (args.kernel == "fused" or (args.kernel == "auto" and lbm.KERNEL_AUTO == 0 and
-                                                   lat_uses_fused(lat))) else "tiled"
+    kname = "fused" if lat.step_kernel() == lbm.KERNEL_FUSED else "tiled"
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_kind": peak_kind,
             "traffic": traffic_from_profile(kname, w.sites),
@@ -307,10 +306,6 @@ def main():
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
-
-
-def lat_uses_fused(lat) -> bool:
-    return False
 
 
 def end_to_end(lat, w, steps, torch):

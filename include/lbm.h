@@ -200,6 +200,10 @@ int64_t lbm_footprint_bytes(const lbm_config *cfg);
 lbm_status lbm_timing(lbm_ctx *ctx, int32_t enable);
 lbm_status lbm_timing_read(lbm_ctx *ctx, double *step_kernel_ms, double *tail_kernel_ms, int64_t *steps);
 
+/* The step kernel lbm_step launches for this context: LBM_KERNEL_TILED or
+ * LBM_KERNEL_FUSED (-1 for a NULL context). */
+int32_t lbm_step_kernel(const lbm_ctx *ctx);
+
 /* Number of kernel launches the context has enqueued so far. */
 int64_t lbm_launch_count(const lbm_ctx *ctx);
 

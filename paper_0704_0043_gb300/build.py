@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "liblbm.so")
-SOURCES = ["lbm_api.cu", "step_tiled.cu", "finalize.cu", "step_fused.cu"]
+SOURCES = ["lbm_api.cu", "step_tiled.cu", "finalize.cu", "step_fused.cu", "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
          "-I", INCLUDE, "-I", CSRC]
@@ -32,7 +32,7 @@ def _nvcc() -> str:
 
 
 def _deps():
-    out = [os.path.join(INCLUDE, "lbm.h")]
+    out = [os.path.join(INCLUDE, name) for name in os.listdir(INCLUDE) if name.endswith(".h")]
     for name in os.listdir(CSRC):
         if name.endswith((".h", ".cuh", ".cu")):
             out.append(os.path.join(CSRC, name))

@@ -63,10 +63,21 @@ __device__ double block_sum(double v, double *red)
     return r;
 }
 
-template <int Q, typename T>
-__global__ void __launch_bounds__(kFinThreads) k_finalize(FinalParams p, T *__restrict__ f)
+// BATCHED: block b finishes instance b of `table`; otherwise the single (p0, f0).
+template <int Q, typename T, bool BATCHED>
+__global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, T *__restrict__ f0,
+                                                          const FinalArgs *__restrict__ table)
 {
     using A = Ar<T>;
+    __shared__ __align__(16) FinalArgs sA;
+    if constexpr (BATCHED) {
+        const unsigned *from = reinterpret_cast<const unsigned *>(table + blockIdx.x);
+        unsigned *to = reinterpret_cast<unsigned *>(&sA);
+        for (int i = threadIdx.x; i < (int)(sizeof(FinalArgs) / 4); i += kFinThreads) to[i] = from[i];
+        __syncthreads();
+    }
+    const FinalParams &p = BATCHED ? sA.p : p0;
+    T *__restrict__ f = BATCHED ? (T *)sA.f : f0;
     __shared__ double red[kFinThreads];
     __shared__ double tot[P_NSTAT];
     __shared__ unsigned hist[256];
@@ -77,32 +88,44 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(FinalParams p, T *__re
     __shared__ int s_idx[kSortCap];
     const int t = threadIdx.x;
 
-    for (int i = 0; i < P_NSTAT; ++i) {
-        double v = 0.0;
-        for (int r = t; r < p.nblocks; r += kFinThreads) v += p.partials[(long long)r * P_NSTAT + i];
-        v = block_sum(v, red);
-        if (t == 0) tot[i] = v;
+    __shared__ int s_valid;
+    // block partials: warp w reduces statistic w over the rows, in a fixed order
+    {
+        const int warp = t >> 5, lane = t & 31;
+        if (warp < P_NSTAT) {
+            double v = 0.0;
+            for (int r = lane; r < p.nblocks; r += 32) v += p.partials[(long long)r * P_NSTAT + warp];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) tot[warp] = v;
+        }
     }
-
     const int nrec = p.ehrenfest ? *p.cand_count : 0;
     const int n = nrec < p.cand_cap ? nrec : p.cand_cap;
     const long long k = p.k_max;
-    if (t == 0) s_nsel = 0;
+    if (t == 0) {
+        s_nsel = 0;
+        s_valid = 0;
+    }
     if (Q == 9 && p.recompute) {
         // FP64 key of each recorded site from the pre-step populations; sites at
         // or below the threshold drop out (key -1)
         for (int i = t; i < n; i += kFinThreads) {
             const int site = p.cand[i].site;
-            double g[9], gs[9], gp[9], d64, din64, r64;
+            double g[9], d64;
             pull_d2q9_f64(p, site % p.nx, site / p.nx, g);
-            const bool bad = site_collide<9, double>(g, p.a, true, gs, gp, d64, din64, r64);
-            p.cand[i].key = (!bad && d64 > p.delta_e) ? d64 : -1.0;
+            const bool ok = key_dS9(g, p.a, d64);
+            p.cand[i].key = (ok && d64 > p.delta_e) ? d64 : -1.0;
         }
     }
     __syncthreads();
-    int nv = 0;
-    for (int i = t; i < n; i += kFinThreads) nv += p.cand[i].key > p.delta_e;
-    const int n_valid = (int)block_sum((double)nv, red);
+    {
+        int nv = 0;
+        for (int i = t; i < n; i += kFinThreads) nv += p.cand[i].key > p.delta_e;
+        if (nv) atomicAdd(&s_valid, nv);
+    }
+    __syncthreads();
+    const int n_valid = s_valid;
     double ehr_sum = 0.0;
     if (p.ehrenfest && k > 0 && n_valid > 0) {
         unsigned long long kv = 0;  // threshold dS pattern
@@ -239,7 +262,6 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(FinalParams p, T *__re
         }
     }
     const double esum = block_sum(ehr_sum, red);
-    __syncthreads();
     if (t == 0) {
         long long step = p.counters[0];
         if (p.collide) {
@@ -274,9 +296,20 @@ template <typename T>
 cudaError_t launch_finalize(int q, const FinalParams &p, T *f, cudaStream_t s)
 {
     if (q == 9)
-        k_finalize<9, T><<<1, kFinThreads, 0, s>>>(p, f);
+        k_finalize<9, T, false><<<1, kFinThreads, 0, s>>>(p, f, nullptr);
     else
-        k_finalize<3, T><<<1, kFinThreads, 0, s>>>(p, f);
+        k_finalize<3, T, false><<<1, kFinThreads, 0, s>>>(p, f, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_batched_f32(int q, const FinalArgs *table, int n, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    const FinalParams none{};
+    if (q == 9)
+        k_finalize<9, float, true><<<n, kFinThreads, 0, s>>>(none, nullptr, table);
+    else
+        k_finalize<3, float, true><<<n, kFinThreads, 0, s>>>(none, nullptr, table);
     return cudaGetLastError();
 }
 

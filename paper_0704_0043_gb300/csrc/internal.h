@@ -4,6 +4,11 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+
 namespace lbm {
 
 // Device layout of a population field: plane-major, rows padded.  Element
@@ -88,6 +93,29 @@ struct FinalParams {
     double rw[9];
 };
 
+// Arguments of one fused-kernel instance (a lattice, its buffers and its
+// strip / segment decomposition).
+struct FusedArgs {
+    StepParams p;
+    const float *src;
+    float *dst;
+    int strips, seg_rows, blocks;
+    float a, delta_m, thr_e, rho_ref;
+    float lid4, lid7, lid8;  // FP32 moving-wall terms of the links through the lid
+};
+
+// One tiled-kernel instance (batched launches) and one tail instance.
+struct TiledArgs {
+    StepParams p;
+    const void *src;
+    void *dst;
+    int gx, blocks;  // blocks along x, blocks in total
+};
+struct FinalArgs {
+    FinalParams p;
+    void *f;
+};
+
 // Launchers (stream-ordered, no synchronisation).  Return cudaGetLastError().
 template <typename T>
 cudaError_t launch_tiled(int q, const StepParams &p, const T *src, T *dst, int *nblocks,
@@ -113,6 +141,58 @@ cudaError_t launch_delta_s(int q, const StepParams &p, const T *f, double *out, 
 cudaError_t launch_fused_d2q9(const StepParams &p, const float *src, float *dst, int *nblocks,
                               cudaStream_t s);
 int fused_d2q9_blocks(int nx, int ny);
+// Fills the instance arguments for block width T (256 or 320) and a target
+// number of blocks per SM wave (`slots`); returns the block count.
+int fused_make_args(const StepParams &p, const float *src, float *dst, int T, int slots, FusedArgs *out);
+int fused_pick_T(int nx);
+// Batched launches: `blocks` blocks in total; block b runs instance map[b].x
+// with local block id map[b].y (tables in device memory).
+cudaError_t launch_fused_batched(int T, const FusedArgs *table, const int2 *map, int blocks, cudaStream_t s);
+cudaError_t launch_tiled_batched_f32(int q, const TiledArgs *table, const int2 *map, int blocks, cudaStream_t s);
+cudaError_t launch_finalize_batched_f32(int q, const FinalArgs *table, int n, cudaStream_t s);
+int tiled_grid_x(int q, int nx);
+int tiled_blocks_for(int q, int nx, int ny);
 bool fused_d2q9_fits(long long plane);  // 32-bit plane offsets inside the kernel
 
+}  // namespace lbm
+
+// Library-owned state of one lattice (opaque to callers, see include/lbm.h).
+struct lbm_ctx {
+    lbm_config cfg{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int q = 9;
+    int pitch = 0;
+    long long plane = 0;
+    size_t elem = 4;
+    size_t field_bytes = 0;
+    void *buf[2] = {nullptr, nullptr};
+    int cur = 0;
+    lbm::Cand *cand = nullptr;
+    int cand_cap = 0;
+    int *counts = nullptr;  // [0] candidate count, [1] chosen count
+    int *sel = nullptr;
+    int sel_cap = 0;
+    double *partials = nullptr;
+    int partial_rows = 0;
+    unsigned *status = nullptr;
+    lbm::DevStats *ring = nullptr;
+    int ring_len = 1;
+    long long *counters = nullptr;  // [0] steps, [1] records
+    double *stage = nullptr;
+    size_t stage_bytes = 0;
+    bool ready = false;
+    bool timing = false;
+    std::vector<cudaEvent_t> events;  // three per timed step
+    size_t events_used = 0;
+    long long launches = 0;
+    int64_t device_bytes = 0;
+    std::string err;
+};
+
+namespace lbm {
+// Per-step parameters of a context (collide = 0 for a limiter pass).
+StepParams ctx_step_params(lbm_ctx *c, int collide, unsigned limiters);
+FinalParams ctx_final_params(lbm_ctx *c, int collide, unsigned limiters, int nblocks);
+bool ctx_uses_fused(const lbm_ctx *c);
 }  // namespace lbm

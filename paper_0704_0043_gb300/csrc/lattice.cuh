@@ -108,12 +108,13 @@ __device__ __forceinline__ void feq9(T rho, T ux, T uy, T fs[9])
 {
     using A = Ar<T>;
     const T usq = A::add(A::mul(ux, ux), A::mul(uy, uy));
-    const T tail = A::div(A::mul(T(3), usq), T(2));
+    const T tail = A::mul(A::mul(T(3), usq), T(0.5));
     const T c[9] = {T(0), ux, uy, -ux, -uy, A::add(ux, uy), A::sub(uy, ux), -A::add(ux, uy),
                     A::sub(ux, uy)};
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-        T poly = A::add(A::add(T(1), A::mul(T(3), c[k])), A::div(A::mul(T(9), A::mul(c[k], c[k])), T(2)));
+        // x / 2 and x * 0.5 round the same real number: identical results
+        T poly = A::add(A::add(T(1), A::mul(T(3), c[k])), A::mul(A::mul(T(9), A::mul(c[k], c[k])), T(0.5)));
         poly = A::sub(poly, tail);
         fs[k] = A::mul(A::mul(rho, T(Lat<9>::w(k))), poly);
     }
@@ -129,7 +130,7 @@ __device__ __forceinline__ void feq3(T rho, T u, T fs[3])
 {
     using A = Ar<T>;
     const T uu = A::mul(u, u);
-    fs[0] = A::mul(A::div(A::mul(T(2), rho), T(3)), A::sub(T(1), A::div(A::mul(T(3), uu), T(2))));
+    fs[0] = A::mul(A::div(A::mul(T(2), rho), T(3)), A::sub(T(1), A::mul(A::mul(T(3), uu), T(0.5))));
     const T r6 = A::div(rho, T(6));
     fs[1] = A::mul(r6, A::add(A::sub(T(1), A::mul(T(3), u)), A::mul(T(3), uu)));
     fs[2] = A::mul(r6, A::add(A::add(T(1), A::mul(T(3), u)), A::mul(T(3), uu)));
@@ -192,6 +193,27 @@ __device__ __forceinline__ bool site_collide(const T fin[Q], T a, bool collide, 
     return bad;
 }
 
+// FP64 dS(f') of the collision alone (the Ehrenfests' key): same operations as
+// site_collide, without dS(f_in).  Returns false for a site that cannot be limited.
+__device__ __forceinline__ bool key_dS9(const double fin[9], double a, double &ds)
+{
+    using A = Ar<double>;
+    double rho, ux, uy, fs[9];
+    moments9<double>(fin, rho, ux, uy);
+    feq9<double>(rho, ux, uy, fs);
+    bool bad = !(rho > 0.0) || !isfinite(rho) || !isfinite(ux) || !isfinite(uy);
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        bad |= !(fs[k] > 0.0) || !isfinite(fin[k]);
+        const double fp = A::add(fs[k], A::mul(a, A::sub(fs[k], fin[k])));
+        const double d = A::sub(fp, fs[k]);
+        s = A::add(s, A::div(A::mul(d, d), fs[k]));
+    }
+    ds = s;
+    return !bad && isfinite(s);
+}
+
 // Positivity rule (Sec. 3.1): largest lambda <= 1 such that f* + lambda (f' - f*) >= 0.
 template <int Q, typename T>
 __device__ __forceinline__ T phi_positivity(const T fs[Q], const T fp[Q])
@@ -241,16 +263,23 @@ __device__ __forceinline__ void moments9_dev(const float g[9], float rho_ref, fl
     rho = rho_ref + drho;
     const float jx = ((g[1] - g[3]) + (g[5] - g[6])) + (g[8] - g[7]);
     const float jy = ((g[2] - g[4]) + (g[5] + g[6])) - (g[7] + g[8]);
-    const float inv = __fdividef(1.0f, rho);
+    const float inv = __frcp_rn(rho);
     ux = jx * inv;
     uy = jy * inv;
 }
 
+// The odd part 3 W_k rho (v_k.u) carries all the momentum; its FP32
+// coefficients 3 W_1 = 1/3 and 3 W_5 = 1/12 are chosen so that 2 c1 + 4 c5 = 1
+// holds exactly for the stored FP32 values (fl(1/3) and 11184810 * 2^-27).
+// With the nearest-FP32 weights instead, sum_k v_k f*_k = rho u (1 + 7.5e-9),
+// and since f' = f* + a (f* - f_in), every collision would multiply the
+// momentum by 1 + 2 beta * 7.5e-9.
 __device__ __forceinline__ void feq9_dev(float drho, float rho, float ux, float uy, float gs[9])
 {
     const float w1 = 1.0f / 9.0f, w5 = 1.0f / 36.0f;
+    const float c1 = 0x1.555556p-2f, c5 = 0x1.555554p-4f;
     const float m = -1.5f * fmaf(ux, ux, uy * uy);
-    const float b1 = 3.0f * w1 * rho, b5 = 3.0f * w5 * rho;
+    const float b1 = c1 * rho, b5 = c5 * rho;
     const float cp = ux + uy, cm = uy - ux;
     float e = fmaf(4.5f * ux, ux, m), A = w1 * fmaf(rho, e, drho), B = b1 * ux;
     gs[1] = A + B;
@@ -279,7 +308,7 @@ __device__ __forceinline__ void moments3_dev(const float g[3], float rho_ref, fl
 {
     drho = (g[0] + g[1]) + g[2];
     rho = rho_ref + drho;
-    ux = __fdividef(g[2] - g[1], rho);
+    ux = (g[2] - g[1]) * __frcp_rn(rho);
     uy = 0.0f;
 }
 

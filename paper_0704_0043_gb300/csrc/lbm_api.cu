@@ -19,39 +19,6 @@
 
 using namespace lbm;
 
-struct lbm_ctx {
-    lbm_config cfg{};
-    cudaStream_t stream = nullptr;
-    int device = 0;
-    int q = 9;
-    int pitch = 0;
-    long long plane = 0;
-    size_t elem = 4;
-    size_t field_bytes = 0;
-    void *buf[2] = {nullptr, nullptr};
-    int cur = 0;
-    Cand *cand = nullptr;
-    int cand_cap = 0;
-    int *counts = nullptr;  // [0] candidate count, [1] chosen count
-    int *sel = nullptr;
-    int sel_cap = 0;
-    double *partials = nullptr;
-    int partial_rows = 0;
-    unsigned *status = nullptr;
-    DevStats *ring = nullptr;
-    int ring_len = 1;
-    long long *counters = nullptr;  // [0] steps, [1] records
-    double *stage = nullptr;
-    size_t stage_bytes = 0;
-    bool ready = false;
-    bool timing = false;
-    std::vector<cudaEvent_t> events;  // three per timed step
-    size_t events_used = 0;
-    long long launches = 0;
-    int64_t device_bytes = 0;
-    std::string err;
-};
-
 namespace {
 
 thread_local std::string g_err;
@@ -366,6 +333,15 @@ void to_public(const DevStats &d, lbm_step_stats *o)
 }
 
 }  // namespace
+
+namespace lbm {
+StepParams ctx_step_params(lbm_ctx *c, int collide, unsigned limiters) { return step_params(c, collide, limiters); }
+FinalParams ctx_final_params(lbm_ctx *c, int collide, unsigned limiters, int nblocks)
+{
+    return final_params(c, collide, limiters, nblocks);
+}
+bool ctx_uses_fused(const lbm_ctx *c) { return fused_applies(c->cfg); }
+}  // namespace lbm
 
 extern "C" {
 
@@ -711,6 +687,12 @@ lbm_status lbm_timing_read(lbm_ctx *c, double *step_ms, double *tail_ms, int64_t
 int64_t lbm_device_bytes(const lbm_ctx *c) { return c ? c->device_bytes : 0; }
 
 int64_t lbm_launch_count(const lbm_ctx *c) { return c ? c->launches : 0; }
+
+int32_t lbm_step_kernel(const lbm_ctx *c)
+{
+    if (!c) return -1;
+    return fused_applies(c->cfg) ? LBM_KERNEL_FUSED : LBM_KERNEL_TILED;
+}
 
 const char *lbm_last_error(const lbm_ctx *c) { return c ? c->err.c_str() : g_err.c_str(); }
 

@@ -107,17 +107,36 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
-template <int Q, typename T>
-__global__ void __launch_bounds__(256) k_tiled(StepParams p, const T *__restrict__ src, T *__restrict__ dst)
+// BATCHED: block b runs instance map[b].x of `table` as its block map[b].y
+// (tiles numbered row by row); otherwise the single instance (p0, src0, dst0).
+template <int Q, typename T, bool BATCHED>
+__global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const T *__restrict__ src0, T *__restrict__ dst0,
+                                               const TiledArgs *__restrict__ table, const int2 *__restrict__ map)
 {
     using A = Ar<T>;
     constexpr int BX = Q == 9 ? kTX : kT1;
     constexpr int BY = Q == 9 ? kTY : 1;
     __shared__ T sds[BY * BX];
     __shared__ double sred[8][P_NSTAT];
+    __shared__ __align__(16) TiledArgs sA;
+    int bx = (int)blockIdx.x, by = (int)blockIdx.y, gx = (int)gridDim.x;
+    if constexpr (BATCHED) {
+        const int2 m = map[blockIdx.x];
+        const unsigned *from = reinterpret_cast<const unsigned *>(table + m.x);
+        unsigned *to = reinterpret_cast<unsigned *>(&sA);
+        for (int i = threadIdx.y * blockDim.x + threadIdx.x; i < (int)(sizeof(TiledArgs) / 4); i += BX * BY)
+            to[i] = from[i];
+        __syncthreads();
+        gx = sA.gx;
+        bx = m.y % gx;
+        by = m.y / gx;
+    }
+    const StepParams &p = BATCHED ? sA.p : p0;
+    const T *__restrict__ src = BATCHED ? (const T *)sA.src : src0;
+    T *__restrict__ dst = BATCHED ? (T *)sA.dst : dst0;
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int x = (int)blockIdx.x * (BX - 2) - 1 + tx;
-    const int y = Q == 9 ? (int)blockIdx.y * (BY - 2) - 1 + ty : 0;
+    const int x = bx * (BX - 2) - 1 + tx;
+    const int y = Q == 9 ? by * (BY - 2) - 1 + ty : 0;
     const bool wrapx = p.boundary != 0;
     const bool wrapy = (Q == 9) && p.boundary == 1;
     bool valid = wrapx ? (x >= -1 && x <= p.nx) : (x >= 0 && x < p.nx);
@@ -242,7 +261,7 @@ __global__ void __launch_bounds__(256) k_tiled(StepParams p, const T *__restrict
     if (lin < P_NSTAT) {
         double v = 0.0;
         for (int w = 0; w < (BX * BY) / 32; ++w) v += sred[w][lin];
-        p.partials[((long long)blockIdx.y * gridDim.x + blockIdx.x) * P_NSTAT + lin] = v;
+        p.partials[((long long)by * gx + bx) * P_NSTAT + lin] = v;
     }
 }
 
@@ -336,13 +355,31 @@ cudaError_t launch_tiled(int q, const StepParams &p, const T *src, T *dst, int *
 {
     if (q == 9) {
         dim3 grid((p.nx + kTX - 3) / (kTX - 2), (p.ny + kTY - 3) / (kTY - 2));
-        k_tiled<9, T><<<grid, dim3(kTX, kTY), 0, s>>>(p, src, dst);
+        k_tiled<9, T, false><<<grid, dim3(kTX, kTY), 0, s>>>(p, src, dst, nullptr, nullptr);
         *nblocks = (int)(grid.x * grid.y);
     } else {
         dim3 grid((p.nx + kT1 - 3) / (kT1 - 2));
-        k_tiled<3, T><<<grid, dim3(kT1), 0, s>>>(p, src, dst);
+        k_tiled<3, T, false><<<grid, dim3(kT1), 0, s>>>(p, src, dst, nullptr, nullptr);
         *nblocks = (int)grid.x;
     }
+    return cudaGetLastError();
+}
+
+int tiled_grid_x(int q, int nx) { return q == 9 ? (nx + kTX - 3) / (kTX - 2) : (nx + kT1 - 3) / (kT1 - 2); }
+
+int tiled_blocks_for(int q, int nx, int ny)
+{
+    return q == 9 ? tiled_grid_x(9, nx) * ((ny + kTY - 3) / (kTY - 2)) : tiled_grid_x(3, nx);
+}
+
+cudaError_t launch_tiled_batched_f32(int q, const TiledArgs *table, const int2 *map, int blocks, cudaStream_t s)
+{
+    if (blocks <= 0) return cudaSuccess;
+    const StepParams none{};
+    if (q == 9)
+        k_tiled<9, float, true><<<blocks, dim3(kTX, kTY), 0, s>>>(none, nullptr, nullptr, table, map);
+    else
+        k_tiled<3, float, true><<<blocks, dim3(kT1), 0, s>>>(none, nullptr, nullptr, table, map);
     return cudaGetLastError();
 }
 

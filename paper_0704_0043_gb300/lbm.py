@@ -96,6 +96,8 @@ def lib():
         L.lbm_footprint_bytes.restype = ctypes.c_int64
         L.lbm_timing.argtypes = [vp, ctypes.c_int32]
         L.lbm_timing_read.argtypes = [vp, dp, dp, ctypes.POINTER(ctypes.c_int64)]
+        L.lbm_step_kernel.argtypes = [vp]
+        L.lbm_step_kernel.restype = ctypes.c_int32
         L.lbm_launch_count.argtypes = [vp]
         L.lbm_launch_count.restype = ctypes.c_int64
         L.lbm_last_error.argtypes = [vp]
@@ -285,6 +287,10 @@ class Lattice:
 
     def device_bytes(self) -> int:
         return lib().lbm_device_bytes(self._h)
+
+    def step_kernel(self) -> int:
+        """KERNEL_TILED or KERNEL_FUSED: the kernel lbm_step launches."""
+        return lib().lbm_step_kernel(self._h)
 
     def launch_count(self) -> int:
         return lib().lbm_launch_count(self._h)

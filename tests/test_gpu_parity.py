@@ -171,7 +171,7 @@ def test_fp32_one_step_against_oracle(nx, ny, kernel):
     f0 = rand_state(9, ny, nx, 21 + nx, eps=0.15, heavy=max(2, nx * ny // 250))
     g.set_populations(f0)
     f = g.get_populations()  # the exact stored FP32 state (deviations from rho_ref W)
-    assert np.abs(f - f0).max() < 1e-8
+    assert np.abs(f - f0).max() < 1e-7
     # dS of the next collision is evaluated in FP64 from the stored values
     np.testing.assert_array_equal(g.delta_s(), oracle.delta_s(oc, f))
     g.step(1)
@@ -211,14 +211,15 @@ def test_fused_and_tiled_fp32_agree_over_many_steps():
     assert sa["n_ehr"] > 0 and sb["n_med"] > 0
 
 
-def test_fp32_cavity_100_matches_fp64_oracle_after_1000_steps():
+@pytest.mark.parametrize("kernel", [lbm.KERNEL_AUTO, lbm.KERNEL_TILED])
+def test_fp32_cavity_100_matches_fp64_oracle_after_1000_steps(kernel):
     """Config: 100 x 100 cavity, lid 0.1, Re = 5000, median delta = 1e-3, FP32 on
     the GPU vs the FP64 oracle: rho and u within 1e-5 absolute after 1000 steps."""
     w = inputs.cavity100_workload()
     g, oc = pair(lattice=lbm.D2Q9, nx=100, ny=100, boundary=lbm.BC_WALLS, beta=w.beta,
                  u_lid=w.u_lid, rho_wall=w.rho0, precision=lbm.FP32, limiters=w.limiters,
-                 delta_median=w.delta_median)
-    assert g.config.kernel == lbm.KERNEL_AUTO  # the fused kernel for an FP32 cavity
+                 delta_median=w.delta_median, kernel=kernel)
+    assert g.step_kernel() == (lbm.KERNEL_FUSED if kernel == lbm.KERNEL_AUTO else lbm.KERNEL_TILED)
     rho, ux, uy = inputs.cavity_rest(100, 100, w.rho0)
     g.init(rho, ux, uy)
     f0 = oracle.init(oc, rho, ux, uy)
@@ -227,9 +228,9 @@ def test_fp32_cavity_100_matches_fp64_oracle_after_1000_steps():
     assert rc == 0
     grho, gux, guy = g.moments()
     orho, oux, ouy = oracle.moments(oc, f)
-    assert np.abs(grho - orho).max() < 1e-5
-    assert np.abs(gux - oux).max() < 1e-5
-    assert np.abs(guy - ouy).max() < 1e-5
+    err = (np.abs(grho - orho).max(), np.abs(gux - oux).max(), np.abs(guy - ouy).max())
+    print("max |d rho|, |d ux|, |d uy| after 1000 steps:", err)
+    assert max(err) < 1e-5, err
     gs = g.stats()
     assert abs(gs["mass"] - st["mass"]) < 1e-5 * st["mass"]
 
