@@ -211,6 +211,39 @@ int64_t lbm_launch_count(const lbm_ctx *ctx);
  * of lbm_create and lbm_footprint_bytes on the calling thread. */
 const char *lbm_last_error(const lbm_ctx *ctx);
 
+/* Size of the static device scratch array of lbm_step_noalloc, and the
+ * largest lattice (nx * ny) it accepts. */
+#define LBM_NOALLOC_SCRATCH_BYTES (8u << 20)
+#define LBM_NOALLOC_MAX_SITES 262144
+
+/* One limited LBGK step of a lattice held entirely in caller memory, without
+ * any device allocation.  The paper has no counterpart: this entry point exists
+ * for callers that cannot call cudaMalloc (a framework that owns all device
+ * memory through its own pool, a host that allows no allocation once running,
+ * a process that must not grow its footprint).
+ *   cfg:   as for lbm_create; precision must be LBM_FP64 (the arithmetic and the
+ *          result are those of an LBM_FP64 context, bit for bit).
+ *   f_in:  device pointer, q * nx * ny doubles, the populations before the step
+ *          (plane-major oracle layout, as lbm_get_populations writes them).
+ *   f_out: device pointer, same size, receives the populations after the step;
+ *          must not overlap f_in.
+ *   stats: host pointer or NULL; receives this step's sums (stats->step is 1).
+ *   cuda_stream: cudaStream_t as void*; the call synchronises it before returning.
+ * Scratch (block sums, Ehrenfests' candidates, selected sites, counters, the
+ * stats record) comes from one file-scope static device array of
+ * LBM_NOALLOC_SCRATCH_BYTES, which every GPU that loads the library holds until
+ * the process exits.  Lattices above LBM_NOALLOC_MAX_SITES sites, or whose
+ * scratch would not fit the array (any lattice up to 512 x 512 fits), are
+ * rejected with LBM_ERR_INVALID_ARG and a message in lbm_last_error(NULL).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  The call never calls cudaMalloc, cudaFree or any
+ * allocating routine.  All calls share the one array, and each clears what must
+ * start at zero: calls that overlap on the GPU (other threads or streams) race
+ * on it and must be serialised by the caller. */
+lbm_status lbm_step_noalloc(const lbm_config *cfg, const double *f_in, double *f_out,
+                            lbm_step_stats *stats, void *cuda_stream);
+
 /* Static name of a status code. */
 const char *lbm_status_string(lbm_status s);
 

@@ -137,6 +137,10 @@ cudaError_t launch_set(int q, const StepParams &p, const double *in, T *f, cudaS
 template <typename T>
 cudaError_t launch_delta_s(int q, const StepParams &p, const T *f, double *out, cudaStream_t s);
 
+// Sets the calling thread's error message (read by lbm_last_error(NULL)); returns s.
+int set_thread_error_impl(int s, const char *msg);
+#define set_thread_error(s, msg) ((lbm_status)::lbm::set_thread_error_impl((int)(s), (msg)))
+
 // Fused FP32 D2Q9 step for LBM_BC_WALLS (row-streaming kernel).
 cudaError_t launch_fused_d2q9(const StepParams &p, const float *src, float *dst, int *nblocks,
                               cudaStream_t s);

@@ -335,6 +335,11 @@ void to_public(const DevStats &d, lbm_step_stats *o)
 }  // namespace
 
 namespace lbm {
+int set_thread_error_impl(int s, const char *msg)
+{
+    g_err = msg;
+    return s;
+}
 StepParams ctx_step_params(lbm_ctx *c, int collide, unsigned limiters) { return step_params(c, collide, limiters); }
 FinalParams ctx_final_params(lbm_ctx *c, int collide, unsigned limiters, int nblocks)
 {

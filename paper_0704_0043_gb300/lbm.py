@@ -105,6 +105,8 @@ def lib():
         L.lbm_status_string.argtypes = [ctypes.c_int]
         L.lbm_status_string.restype = ctypes.c_char_p
         L.lbm_abi_version.restype = ctypes.c_int32
+        L.lbm_step_noalloc.argtypes = [cfgp, vp, vp, ctypes.POINTER(StepStats), vp]
+        L.lbm_step_noalloc.restype = ctypes.c_int
         for name in ("lbm_create", "lbm_destroy", "lbm_init", "lbm_step", "lbm_delta_s", "lbm_limit",
                      "lbm_moments", "lbm_stats", "lbm_stats_history", "lbm_limited_sites",
                      "lbm_get_populations", "lbm_set_populations", "lbm_synchronize",
@@ -173,6 +175,22 @@ def footprint_bytes(**kw) -> int:
     if n == 0:
         raise LBMError(ERR_INVALID_ARG, lib().lbm_last_error(None).decode())
     return n
+
+
+def step_noalloc(f_in, f_out, stream: int | None = None, **cfg) -> dict:
+    """lbm_step_noalloc: one FP64 limited step from device array f_in into
+    device array f_out (torch CUDA tensors, q * nx * ny float64 each), with no
+    device allocation by the library.  Returns the step's stats."""
+    c = default_config(**cfg)
+    q = 3 if c.lattice == D1Q3 else 9
+    n = q * c.nx * c.ny
+    pi, ki = _ptr(f_in, n, False)
+    po, ko = _ptr(f_out, n, True)
+    st = StepStats()
+    s = current_stream_handle() if stream is None else stream
+    _check(lib().lbm_step_noalloc(ctypes.byref(c), ctypes.c_void_p(pi), ctypes.c_void_p(po),
+                                  ctypes.byref(st), ctypes.c_void_p(s)))
+    return st.as_dict()
 
 
 class Lattice:
