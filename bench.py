@@ -27,7 +27,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-BYTES_PER_SITE = {("d2q9", "fp32"): 72, ("d2q9", "fp64"): 144, ("d1q3", "fp32"): 24,
+BYTES_PER_SITE = {("d2q9", "fp32"): 72, ("d2q9", "bf16"): 36, ("d2q9", "fp16"): 36, ("d2q9", "fp64"): 144, ("d1q3", "fp32"): 24,
                   ("d1q3", "fp64"): 48}
 FALLBACK_HBM_GBS = 6800.0
 
@@ -38,9 +38,15 @@ def parse():
     ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cavity4096", choices=["cavity4096", "batched", "serve"],
+                    help="cavity4096: the 4096^2 cavity (default); batched: 256 cavities of sides "
+                         "64..512; serve: Poisson-arriving solves through the continuous-batching server")
+    ap.add_argument("--requests", type=int, default=200, help="serve: requests in the trace")
     ap.add_argument("--develop", type=int, default=500,
                     help="untimed steps before warm-up so the flow has left the rest state")
     ap.add_argument("--kernel", default="auto", choices=["auto", "tiled", "fused"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16"],
+                    help="population storage (arithmetic is FP32 in all three)")
     ap.add_argument("--side", type=int, default=4096,
                     help="cavity side (4096 is the workload; smaller sides are for profiling)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -149,10 +155,11 @@ def workload(side: int = 4096):
     return w
 
 
-def lattice_kwargs(w, kernel: str):
+def lattice_kwargs(w, kernel: str, precision: str = "fp32"):
     from paper_0704_0043_gb300 import lbm
     km = {"auto": lbm.KERNEL_AUTO, "tiled": lbm.KERNEL_TILED, "fused": lbm.KERNEL_FUSED}[kernel]
-    return dict(lattice=lbm.D2Q9, nx=w.nx, ny=w.ny, boundary=lbm.BC_WALLS, precision=lbm.FP32,
+    pm = {"fp32": lbm.FP32, "bf16": lbm.BF16, "fp16": lbm.FP16}[precision]
+    return dict(lattice=lbm.D2Q9, nx=w.nx, ny=w.ny, boundary=lbm.BC_WALLS, precision=pm,
                 beta=w.beta, u_lid=w.u_lid, rho_wall=w.rho0, limiters=w.limiters,
                 delta_median=w.delta_median, delta_ehrenfest=w.delta_ehrenfest, k_max=w.k_max,
                 kernel=km)
@@ -211,10 +218,139 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_batched(args):
+    """256 cavities (sides U{64..512}, Re U[2000, 7500], lid 0.1, one limiter each
+    drawn from positivity / Ehrenfests' / median), FP32, advanced together by the
+    batch engine (shared launches, CUDA-graph replay, autotuned tiles), against
+    the same lattices stepped one after another through lbm_step."""
+    import torch
+    from paper_0704_0043_gb300 import build as lbm_build
+    from paper_0704_0043_gb300 import inputs, lbm
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    lbm_build.build()
+    ws = inputs.batched_cavities()
+    sites = sum(w.sites for w in ws)
+    def kw(w):
+        return dict(lattice=lbm.D2Q9, nx=w.nx, ny=w.ny, boundary=lbm.BC_WALLS, precision=lbm.FP32,
+                    beta=w.beta, u_lid=w.u_lid, rho_wall=w.rho0, limiters=w.limiters,
+                    delta_median=w.delta_median, delta_ehrenfest=w.delta_ehrenfest, k_max=w.k_max)
+    b = lbm.Batch()
+    slots = [b.add(**kw(w)) for w in ws]
+    for s, w in zip(slots, ws):
+        b.init(s, *inputs.cavity_rest(w.nx, w.ny, w.rho0))
+    graph = 50
+    b.set_graph(graph)
+    tuned_ms = b.tune(3)
+    def sync_batch():
+        try:
+            b.synchronize()
+        except lbm.LBMError as e:  # lattices that blew up keep their (equal-cost) steps
+            if e.status != lbm.ERR_NONFINITE:
+                raise
+    b.step(max(args.warmup, 2 * graph))
+    sync_batch()
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = b.launch_count()
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    sampler.start()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    b.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    t_batch = ev0.elapsed_time(ev1) / 1e3
+    launches = b.launch_count() - l0
+    sync_batch()
+    nonfinite = sum(b.lattice_status(s) != lbm.OK for s in slots)
+    # the same lattices one by one (plain per-instance launches)
+    plain_steps = max(20, args.steps // 10)
+    lats = []
+    for w in ws:
+        g = lbm.Lattice(**kw(w))
+        g.init(*inputs.cavity_rest(w.nx, w.ny, w.rho0))
+        g.step(2)
+        lats.append(g)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(plain_steps):
+        for g in lats:
+            g.step(1)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_plain = ev0.elapsed_time(ev1) / 1e3
+    v = sites * args.steps / t_batch / 1e6
+    vp = sites * plain_steps / t_plain / 1e6
+    peak, kind = peaks()
+    out = {"metric": "batched limited-LBM MLUPS", "value": v, "unit": "MLUPS", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_batch * 1e3 / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic",
+           "config": {"workload": "batched_cavities_256", "lattices": len(ws), "sites": sites,
+                      "sides": "U{64..512}", "graph_steps": graph, "tuned_ms_per_step": tuned_ms},
+           "plain_value": vp, "plain_steps": plain_steps, "batched_over_plain": v / vp,
+           "nonfinite_lattices": nonfinite,
+           "roofline": {"bound": "hbm", "achieved": 72 * sites * args.steps / t_batch / 1e9,
+                        "peak": peak, "unit": "GB/s", "frac": 72 * sites * args.steps / t_batch / 1e9 / peak,
+                        "peak_kind": kind, "note": "whole batched step (all launches), not one kernel"},
+           "gpu_launches": launches, "clocks": clocks}
+    print(json.dumps(out), flush=True)
+    b.close()
+
+
+def run_serve(args):
+    """Poisson arrivals (200/s): 70 % cavities of side 100..1024, 30 % shock
+    tubes of 800..1e6 sites (density ratio 1:2..1:4), 1e3..1e5 steps each,
+    served by continuous batching with admission by HBM footprint.  The 200/s
+    trace offers far more work than one GPU can do (an overload run); the same
+    requests are then replayed at about 70 % of the measured capacity."""
+    import torch
+    from paper_0704_0043_gb300 import build as lbm_build
+    from paper_0704_0043_gb300 import inputs, serve
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    lbm_build.build()
+    free, total = torch.cuda.mem_get_info()
+    budget = int(free * 0.7)
+    trace = inputs.serving_trace(n_requests=args.requests)
+    work = sum(w.sites * w.steps for _, w in trace)
+    out_runs = {}
+    for label, scale in (("overload_200hz", 1.0), ("capacity_70pct", None)):
+        if scale is None:
+            cap_rps = out_runs["overload_200hz"]["aggregate_mlups"] * 1e6 / (work / len(trace))
+            rate = 0.7 * cap_rps
+            scale = 200.0 / rate
+        reqs = serve.requests_from_trace([(t * scale, w) for t, w in trace])
+        srv = serve.Server(memory_bytes=budget, quantum=1000, graph_steps=0)
+        t0 = time.perf_counter()
+        res = srv.run(reqs, realtime=True)
+        wall = time.perf_counter() - t0
+        s = serve.summarize(res, wall, srv.site_updates)
+        s["arrival_rate_hz"] = 200.0 / scale
+        s["rounds"] = srv.rounds
+        out_runs[label] = s
+        srv.close()
+    o = out_runs["overload_200hz"]
+    print(json.dumps({"metric": "served limited-LBM MLUPS", "value": o["aggregate_mlups"], "unit": "MLUPS",
+                      "n_gpus": 1, "steps": None, "warmup": 0, "higher_is_better": True,
+                      "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                      "config": {"workload": "serving_trace_7040044", "requests": len(trace),
+                                 "site_updates": work, "memory_budget_bytes": budget,
+                                 "quantum_steps": 1000},
+                      "p50_latency_s": o["p50_latency_s"], "p99_latency_s": o["p99_latency_s"],
+                      "runs": out_runs}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "batched":
+        run_batched(args)
+        return
+    if args.workload == "serve":
+        run_serve(args)
         return
     import numpy as np
     import torch
@@ -237,7 +373,7 @@ def main():
     lbm.lib()
 
     w = workload(args.side)
-    lat = lbm.Lattice(**lattice_kwargs(w, args.kernel))
+    lat = lbm.Lattice(**lattice_kwargs(w, args.kernel, args.precision))
     rho, ux, uy = inputs.cavity_rest(w.nx, w.ny, w.rho0)
     lat.init(rho, ux, uy)
     lat.step(args.develop + args.warmup)
@@ -269,14 +405,14 @@ def main():
     mlups = world * w.sites * args.steps / elapsed / 1e6
 
     # roofline of the step kernel (the dominant launch): algorithmic bytes / event time
-    bps = BYTES_PER_SITE[("d2q9", "fp32")]
+    bps = BYTES_PER_SITE[("d2q9", args.precision)]
     kern_s = step_ms / 1e3 / max(timed, 1)
     achieved = bps * w.sites / kern_s / 1e9
     peak, peak_kind = peaks()
     kname = "fused" if lat.step_kernel() == lbm.KERNEL_FUSED else "tiled"
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_kind": peak_kind,
-            "traffic": traffic_from_profile(kname, w.sites),
+            "traffic": traffic_from_profile(f"{kname}_{args.precision}", w.sites),
             "kernel": kname, "kernel_ms": kern_s * 1e3, "tail_kernel_ms": tail_ms / max(timed, 1),
             "bytes_per_site": bps}
 
@@ -292,7 +428,7 @@ def main():
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "reynolds": 7500,
                       "u_lid": w.u_lid, "beta": w.beta, "limiters": "median+ehrenfest",
-                      "delta": 1e-3, "k_max": w.k_max, "storage": "fp32", "sums": "fp64",
+                      "delta": 1e-3, "k_max": w.k_max, "storage": args.precision, "sums": "fp64",
                       "kernel": kname, "develop_steps": args.develop,
                       "l2": "inputs larger than L2 (1.2 GB population buffers vs 129 MB L2)",
                       "parallelism": f"replicas{world}" if world > 1 else "single"},

@@ -55,11 +55,12 @@ typedef enum {
 enum { LBM_D1Q3 = 1, LBM_D2Q9 = 2 };
 
 /* Storage precision of the populations.  LBM_FP64 stores f and evaluates
- * every operation in the oracle's order with no FMA contraction.  LBM_FP32
- * stores the deviations g_k = f_k - rho_ref W_k from a uniform rest state and
- * computes in FP32 on them (FP64 for the global sums and the Ehrenfests' keys);
- * every transfer in or out of the library converts to and from f in FP64. */
-enum { LBM_FP64 = 0, LBM_FP32 = 1 };
+ * every operation in the oracle's order with no FMA contraction.  LBM_FP32,
+ * LBM_BF16 and LBM_FP16 store the deviations g_k = f_k - rho_ref W_k from a
+ * uniform rest state (in 32, 16 and 16 bits) and compute in FP32 on them (FP64
+ * for the global sums and the Ehrenfests' keys); every transfer in or out of
+ * the library converts to and from f in FP64. */
+enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_BF16 = 2, LBM_FP16 = 3 };
 
 enum {
     LBM_BC_WALLS = 0,    /* D2Q9: still walls left, right, bottom, lid on top; D1Q3: closed ends */
@@ -78,16 +79,16 @@ enum {
 
 /* Kernel choice for lbm_step. */
 enum {
-    LBM_KERNEL_AUTO = 0,    /* fused FP32 D2Q9 kernel where it applies, else the tiled kernel */
+    LBM_KERNEL_AUTO = 0,    /* fused D2Q9 cavity kernel where it applies, else the tiled kernel */
     LBM_KERNEL_TILED = 1,   /* overlapping-tile kernel: every lattice, boundary and precision */
-    LBM_KERNEL_FUSED = 2    /* FP32 D2Q9 with LBM_BC_WALLS only: row-streaming fused kernel */
+    LBM_KERNEL_FUSED = 2    /* D2Q9 with LBM_BC_WALLS, FP32/BF16/FP16 storage: row-streaming fused kernel */
 };
 
 typedef struct lbm_config {
     int32_t lattice;         /* LBM_D1Q3 or LBM_D2Q9 */
     int32_t nx, ny;          /* sites; ny must be 1 for D1Q3; nx, ny >= 2 for D2Q9 walls */
     int32_t boundary;        /* LBM_BC_* */
-    int32_t precision;       /* LBM_FP64 or LBM_FP32 */
+    int32_t precision;       /* LBM_FP64, LBM_FP32, LBM_BF16 or LBM_FP16 */
     uint32_t limiters;       /* LBM_LIM_* bits applied by lbm_step */
     int32_t median_mode;     /* LBM_MEDIAN_* */
     int32_t kernel;          /* LBM_KERNEL_* */

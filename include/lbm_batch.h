@@ -61,19 +61,36 @@ lbm_status lbm_batch_limited_sites(lbm_batch *b, int32_t slot, int64_t *idx, int
  * Errors: LBM_ERR_STATE (a lattice was never initialised), LBM_ERR_CUDA. */
 lbm_status lbm_batch_step(lbm_batch *b, int64_t nsteps);
 
-/* Waits for the batch; returns the first sticky lattice status. */
+/* Waits for the batch and collects every lattice's status (a lattice that
+ * met a nonfinite site reports LBM_ERR_NONFINITE); returns the first failing
+ * one, LBM_OK if none.  The other lattices are unaffected: their steps are
+ * independent. */
 lbm_status lbm_batch_synchronize(lbm_batch *b);
+
+/* Status of one lattice as collected by lbm_batch_synchronize; it stays set
+ * until the lattice is re-initialised (lbm_batch_init /
+ * lbm_batch_set_populations) or removed.  LBM_ERR_INVALID_ARG for an empty
+ * slot. */
+lbm_status lbm_batch_lattice_status(const lbm_batch *b, int32_t slot);
 
 /* CUDA-graph replay: runs of `steps_per_graph` steps (even, >= 2; 0 turns it
  * off) are captured once after the batch changes and replayed. */
 lbm_status lbm_batch_set_graph(lbm_batch *b, int32_t steps_per_graph);
 
 /* Tile-shape autotuner: times `trial_steps` batched steps for each candidate
- * (block width 256 or 320 columns; 1, 2 or 4 waves of blocks over the SMs),
+ * (strips chosen per lattice or at most 120 columns wide; 1, 2 or 4 waves of
+ * blocks over the SMs),
  * keeps the fastest, and restores every lattice's state, counters and stats
  * to what they were before.  *best_ms receives the winning time per step
  * (may be NULL). */
 lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_steps, double *best_ms);
+
+/* Fixes the fused kernel's shape: block_width = widest column strip of a
+ * block (a multiple of 8 up to 240; 0: chosen per lattice), waves 1, 2 or 4
+ * (blocks per lattice in proportion to its sites, 2 blocks per SM per wave).
+ * The shape changes the speed only, never a result.
+ * Errors: LBM_ERR_INVALID_ARG. */
+lbm_status lbm_batch_set_shape(lbm_batch *b, int32_t block_width, int32_t waves);
 
 /* Kernel launches enqueued by lbm_batch_step so far (graph replays count
  * their captured launches). */

@@ -25,6 +25,7 @@ struct lbm_batch {
     cudaStream_t run = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr, t0 = nullptr, t1 = nullptr;
     std::vector<lbm_ctx *> slots;
+    std::vector<lbm_status> slot_status;  // sticky per-lattice status seen by lbm_batch_synchronize
     // launch tables (host copies kept while the device copies are in use)
     bool dirty = true;
     int phase = 0;               // steps since the tables were built, mod 2
@@ -41,8 +42,8 @@ struct lbm_batch {
     int2 *fmap = nullptr, *t3map = nullptr, *t9map = nullptr;
     int fblocks = 0, t3blocks = 0, t9blocks = 0, n9 = 0, n3 = 0;
     // shape
-    int T = 0;      // fused block width; 0 = chosen from the lattices
-    int waves = 2;  // fused block budget, in waves of 2 blocks per SM
+    int max_width = 0;  // widest fused strip in columns; 0 = automatic (up to 240)
+    int waves = 2;      // fused block budget, in waves of 2 blocks per SM
     // graph replay
     int graph_steps = 0;
     cudaGraphExec_t exec = nullptr;
@@ -65,17 +66,6 @@ lbm_status bfail(lbm_batch *b, lbm_status s, const std::string &m)
             return bfail(b, e_ == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA,              \
                          std::string(#call) + " failed: " + cudaGetErrorString(e_));                  \
     } while (0)
-
-int sm_count_host()
-{
-    int dev = 0, sms = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        sms <= 0) {
-        cudaGetLastError();
-        sms = 152;
-    }
-    return sms;
-}
 
 lbm_ctx *get(lbm_batch *b, int32_t slot)
 {
@@ -122,15 +112,6 @@ lbm_status leave(lbm_batch *b)
     return LBM_OK;
 }
 
-void fill_recompute(FinalParams &f, const StepParams &p, const float *src)
-{
-    f.recompute = 1;
-    f.src = src;
-    f.boundary = p.boundary;
-    f.a = p.a;
-    f.delta_e = p.delta_e;
-    for (int k = 0; k < 9; ++k) f.lid[k] = p.lid[k];
-}
 
 lbm_status rebuild(lbm_batch *b)
 {
@@ -145,21 +126,14 @@ lbm_status rebuild(lbm_batch *b)
     b->h_t3map.clear();
     b->h_t9map.clear();
     b->cur_build.assign(b->slots.size(), 0);
-    // block width of the fused launch and block budget per lattice
+    // fused block budget per lattice, in proportion to its sites
     long long fused_sites = 0;
-    int T = b->T;
-    long long w256 = 0, w320 = 0;
     for (lbm_ctx *c : b->slots) {
         if (!c) continue;
         if (!c->ready) return bfail(b, LBM_ERR_STATE, "a lattice of the batch was never initialised");
-        if (ctx_uses_fused(c)) {
-            fused_sites += (long long)c->cfg.nx * c->cfg.ny;
-            w256 += (long long)((c->cfg.nx + 253) / 254) * 256;
-            w320 += (long long)((c->cfg.nx + 317) / 318) * 320;
-        }
+        if (ctx_uses_fused(c)) fused_sites += (long long)c->cfg.nx * c->cfg.ny;
     }
-    if (T == 0) T = w320 < w256 ? 320 : 256;
-    const double budget = (double)b->waves * 2.0 * sm_count_host();
+    const double budget = (double)b->waves * fused_slots();
     for (size_t i = 0; i < b->slots.size(); ++i) {
         lbm_ctx *c = b->slots[i];
         if (!c) continue;
@@ -172,10 +146,11 @@ lbm_status rebuild(lbm_batch *b)
                 const long long sites = (long long)c->cfg.nx * c->cfg.ny;
                 const int slots = std::max(1, (int)std::lround(budget * (double)sites / (double)fused_sites));
                 FusedArgs A;
-                const int blocks = fused_make_args(p, (const float *)src, (float *)dst, T, slots, &A);
+                const int blocks = fused_make_args(p, src, dst, b->max_width, slots, &A);
                 b->h_fused[k].push_back(A);
                 FinalArgs F{ctx_final_params(c, 1, lim, blocks), dst};
-                fill_recompute(F.p, p, (const float *)src);
+                F.p.src = src;
+                F.p.recompute = 1;
                 b->h_fin9[k].push_back(F);
                 if (k == 0)
                     for (int lb = 0; lb < blocks; ++lb)
@@ -188,6 +163,7 @@ lbm_status rebuild(lbm_batch *b)
                 A.gx = tiled_grid_x(c->q, c->cfg.nx);
                 A.blocks = tiled_blocks_for(c->q, c->cfg.nx, c->cfg.ny);
                 FinalArgs F{ctx_final_params(c, 1, lim, A.blocks), dst};
+                F.p.src = src;
                 auto &tab = c->q == 9 ? b->h_t9[k] : b->h_t3[k];
                 auto &map = c->q == 9 ? b->h_t9map : b->h_t3map;
                 tab.push_back(A);
@@ -197,8 +173,6 @@ lbm_status rebuild(lbm_batch *b)
             }
         }
     }
-    b->T = T == 0 ? 256 : T;
-    if (b->T != 256 && b->T != 320) b->T = 256;
     // one device allocation holds every table
     auto sz = [](size_t n, size_t e) { return ((n * e + 255) / 256) * 256; };
     const size_t nf = b->h_fused[0].size(), nt3 = b->h_t3[0].size(), nt9 = b->h_t9[0].size();
@@ -251,7 +225,7 @@ int launches_per_step(const lbm_batch *b)
 cudaError_t one_step(lbm_batch *b, int k)
 {
     cudaError_t e = cudaSuccess;
-    if (b->fblocks && e == cudaSuccess) e = launch_fused_batched(b->T, b->fused[k], b->fmap, b->fblocks, b->run);
+    if (b->fblocks && e == cudaSuccess) e = launch_fused_batched(b->fused[k], b->fmap, b->fblocks, b->run);
     if (b->t3blocks && e == cudaSuccess) e = launch_tiled_batched_f32(3, b->t3[k], b->t3map, b->t3blocks, b->run);
     if (b->t9blocks && e == cudaSuccess) e = launch_tiled_batched_f32(9, b->t9[k], b->t9map, b->t9blocks, b->run);
     if (b->n9 && e == cudaSuccess) e = launch_finalize_batched_f32(9, b->fin9[k], b->n9, b->run);
@@ -357,14 +331,17 @@ lbm_status lbm_batch_add(lbm_batch *b, const lbm_config *cfg, int32_t *slot)
     lbm_status s = lbm_create(cfg, (void *)b->run, &c);
     if (s != LBM_OK) return bfail(b, s, lbm_last_error(nullptr));
     invalidate(b);
+    b->slot_status.resize(b->slots.size(), LBM_OK);
     for (size_t i = 0; i < b->slots.size(); ++i) {
         if (!b->slots[i]) {
             b->slots[i] = c;
+            b->slot_status[i] = LBM_OK;
             *slot = (int32_t)i;
             return LBM_OK;
         }
     }
     b->slots.push_back(c);
+    b->slot_status.push_back(LBM_OK);
     *slot = (int32_t)b->slots.size() - 1;
     return LBM_OK;
 }
@@ -377,6 +354,7 @@ lbm_status lbm_batch_remove(lbm_batch *b, int32_t slot)
     BCK(b, cudaStreamSynchronize(b->run));
     lbm_destroy(c);
     b->slots[(size_t)slot] = nullptr;
+    b->slot_status[(size_t)slot] = LBM_OK;
     return LBM_OK;
 }
 
@@ -406,6 +384,7 @@ lbm_status lbm_batch_init(lbm_batch *b, int32_t slot, const double *rho, const d
     if (s != LBM_OK) return s;
     s = lbm_init(c, rho, ux, uy);
     if (s != LBM_OK) return bfail(b, s, lbm_last_error(c));
+    b->slot_status[(size_t)slot] = LBM_OK;
     return leave(b);
 }
 
@@ -418,6 +397,7 @@ lbm_status lbm_batch_set_populations(lbm_batch *b, int32_t slot, const double *f
     if (s != LBM_OK) return s;
     s = lbm_set_populations(c, f);
     if (s != LBM_OK) return bfail(b, s, lbm_last_error(c));
+    b->slot_status[(size_t)slot] = LBM_OK;
     return leave(b);
 }
 
@@ -464,15 +444,25 @@ lbm_status lbm_batch_synchronize(lbm_batch *b)
     BCK(b, cudaStreamSynchronize(b->run));
     materialise(b);
     lbm_status first = LBM_OK;
-    for (lbm_ctx *c : b->slots) {
+    for (size_t i = 0; i < b->slots.size(); ++i) {
+        lbm_ctx *c = b->slots[i];
         if (!c) continue;
         lbm_status s = lbm_synchronize(c);
-        if (s != LBM_OK && first == LBM_OK) {
-            first = s;
-            b->err = lbm_last_error(c);
+        if (s != LBM_OK) {
+            b->slot_status[i] = s;
+            if (first == LBM_OK) {
+                first = s;
+                b->err = lbm_last_error(c);
+            }
         }
     }
     return first;
+}
+
+lbm_status lbm_batch_lattice_status(const lbm_batch *b, int32_t slot)
+{
+    if (!b || slot < 0 || slot >= (int32_t)b->slots.size() || !b->slots[(size_t)slot]) return LBM_ERR_INVALID_ARG;
+    return b->slot_status[(size_t)slot];
 }
 
 lbm_status lbm_batch_set_graph(lbm_batch *b, int32_t steps_per_graph)
@@ -482,6 +472,18 @@ lbm_status lbm_batch_set_graph(lbm_batch *b, int32_t steps_per_graph)
         return bfail(b, LBM_ERR_INVALID_ARG, "steps_per_graph must be 0 or an even number >= 2");
     drop_graph(b);
     b->graph_steps = steps_per_graph;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_set_shape(lbm_batch *b, int32_t block_width, int32_t waves)
+{
+    if (!b) return LBM_ERR_INVALID_ARG;
+    if (block_width != 0 && (block_width < 8 || block_width > 240 || (block_width & 7)))
+        return bfail(b, LBM_ERR_INVALID_ARG, "block_width must be 0 or a multiple of 8 in [8, 240]");
+    if (waves != 1 && waves != 2 && waves != 4) return bfail(b, LBM_ERR_INVALID_ARG, "waves must be 1, 2 or 4");
+    invalidate(b);
+    b->max_width = block_width;
+    b->waves = waves;
     return LBM_OK;
 }
 
@@ -513,15 +515,15 @@ lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_steps, double *best_ms)
         BCK(b, cudaMemcpyAsync(m + c->field_bytes + ring + 32, c->counts, 2 * sizeof(int), cudaMemcpyDeviceToDevice, b->run));
         snaps.push_back({c, c->cur, mem});
     }
-    const int Ts[2] = {256, 320};
+    const int Ts[2] = {0, 120};
     const int Ws[3] = {1, 2, 4};
     double best = 1e300;
-    int bestT = 256, bestW = 2;
+    int bestT = 0, bestW = 2;
     lbm_status rs = LBM_OK;
     for (int T : Ts) {
         for (int W : Ws) {
             invalidate(b);
-            b->T = T;
+            b->max_width = T;
             b->waves = W;
             const int gs = b->graph_steps;
             b->graph_steps = 0;
@@ -563,7 +565,7 @@ lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_steps, double *best_ms)
     b->dirty = true;  // tables for the restored buffers
     b->phase = 0;
     drop_graph(b);
-    b->T = bestT;
+    b->max_width = bestT;
     b->waves = bestW;
     if (rs != LBM_OK) return rs;
     if (best_ms) *best_ms = best;

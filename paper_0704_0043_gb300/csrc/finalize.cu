@@ -28,22 +28,51 @@ __device__ __forceinline__ long long fidx(long long plane, int pitch, int k, int
 
 // Free flight into site (x, y) of a D2Q9 cavity / channel / periodic lattice,
 // evaluated in FP64 from FP32 storage exactly as the FP64 path evaluates it.
+template <typename S>
 __device__ void pull_d2q9_f64(const FinalParams &p, int x, int y, double fin[9])
 {
+    const S *src = (const S *)p.src;
     const bool wrapx = p.boundary != 0, wrapy = p.boundary == 1;
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
         int sx = x - Lat<9>::cx(k), sy = y - Lat<9>::cy(k);
         if (wrapx) sx = sx < 0 ? sx + p.nx : (sx >= p.nx ? sx - p.nx : sx);
         if (wrapy) sy = sy < 0 ? sy + p.ny : (sy >= p.ny ? sy - p.ny : sy);
-        // FP32 storage holds g = f - rho_ref W; the absolute value is (double) g + rw
+        // FP32 / BF16 / FP16 storage holds g = f - rho_ref W; the absolute value is (double) g + rw
         if (sx >= 0 && sx < p.nx && sy >= 0 && sy < p.ny) {
-            fin[k] = Ar<double>::add((double)p.src[fidx(p.plane, p.pitch, k, sy, sx)], p.rw[k]);
+            fin[k] = Ar<double>::add((double)s2f(src[fidx(p.plane, p.pitch, k, sy, sx)]), p.rw[k]);
         } else {
             const int q = Lat<9>::opp(k);
-            double v = Ar<double>::add((double)p.src[fidx(p.plane, p.pitch, q, y, x)], p.rw[q]);
+            double v = Ar<double>::add((double)s2f(src[fidx(p.plane, p.pitch, q, y, x)]), p.rw[q]);
             if (sy > p.ny - 1) v = Ar<double>::add(v, p.lid[k]);
             fin[k] = v;
+        }
+    }
+}
+
+// The pass's input at site (x, y) in FP32: after free flight (collide) with the
+// step kernels' FP32 arithmetic (bounce-back, lid term added as hi + lo), or
+// the stored populations themselves (limiter pass).
+template <int Q, typename S>
+__device__ void pull_dev(const FinalParams &p, int x, int y, float g[Q])
+{
+    const S *src = (const S *)p.src;
+    const bool wrapx = p.boundary != 0, wrapy = Q == 9 && p.boundary == 1;
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+        if (!p.collide) {
+            g[k] = s2f(src[fidx(p.plane, p.pitch, k, y, x)]);
+            continue;
+        }
+        int sx = x - Lat<Q>::cx(k), sy = y - Lat<Q>::cy(k);
+        if (wrapx) sx = sx < 0 ? sx + p.nx : (sx >= p.nx ? sx - p.nx : sx);
+        if (wrapy) sy = sy < 0 ? sy + p.ny : (sy >= p.ny ? sy - p.ny : sy);
+        if (sx >= 0 && sx < p.nx && sy >= 0 && sy < p.ny) {
+            g[k] = s2f(src[fidx(p.plane, p.pitch, k, sy, sx)]);
+        } else {
+            float v = s2f(src[fidx(p.plane, p.pitch, Lat<Q>::opp(k), y, x)]);
+            if (Q == 9 && sy > p.ny - 1) v = __fadd_rn(__fadd_rn(v, p.lidf[k]), p.lidlo[k]);
+            g[k] = v;
         }
     }
 }
@@ -64,11 +93,11 @@ __device__ double block_sum(double v, double *red)
 }
 
 // BATCHED: block b finishes instance b of `table`; otherwise the single (p0, f0).
-template <int Q, typename T, bool BATCHED>
-__global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, T *__restrict__ f0,
+template <int Q, typename S, bool BATCHED>
+__global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, S *__restrict__ f0,
                                                           const FinalArgs *__restrict__ table)
 {
-    using A = Ar<T>;
+    using T = compute_t<S>;
     __shared__ __align__(16) FinalArgs sA;
     if constexpr (BATCHED) {
         const unsigned *from = reinterpret_cast<const unsigned *>(table + blockIdx.x);
@@ -77,7 +106,7 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, 
         __syncthreads();
     }
     const FinalParams &p = BATCHED ? sA.p : p0;
-    T *__restrict__ f = BATCHED ? (T *)sA.f : f0;
+    S *__restrict__ f = BATCHED ? (S *)sA.f : f0;
     __shared__ double red[kFinThreads];
     __shared__ double tot[P_NSTAT];
     __shared__ unsigned hist[256];
@@ -107,15 +136,17 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, 
         s_nsel = 0;
         s_valid = 0;
     }
-    if (Q == 9 && p.recompute) {
-        // FP64 key of each recorded site from the pre-step populations; sites at
-        // or below the threshold drop out (key -1)
-        for (int i = t; i < n; i += kFinThreads) {
-            const int site = p.cand[i].site;
-            double g[9], d64;
-            pull_d2q9_f64(p, site % p.nx, site / p.nx, g);
-            const bool ok = key_dS9(g, p.a, d64);
-            p.cand[i].key = (ok && d64 > p.delta_e) ? d64 : -1.0;
+    if constexpr (!std::is_same<S, double>::value) {
+        if (Q == 9 && p.recompute) {
+            // FP64 key of each recorded site from the pre-step populations; sites at
+            // or below the threshold drop out (key -1)
+            for (int i = t; i < n; i += kFinThreads) {
+                const int site = p.cand[i].site;
+                double g[9], d64;
+                pull_d2q9_f64<S>(p, site % p.nx, site / p.nx, g);
+                const bool ok = key_dS9(g, p.a, d64);
+                p.cand[i].key = (ok && d64 > p.delta_e) ? d64 : -1.0;
+            }
         }
     }
     __syncthreads();
@@ -238,18 +269,27 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, 
             const Cand c = p.cand[ci];
             const int x = c.site % p.nx, y = c.site / p.nx;
             T g[Q], fs[Q], rho, ux, uy;
-#pragma unroll
-            for (int q = 0; q < Q; ++q) g[q] = f[fidx(p.plane, p.pitch, q, y, x)];
             if constexpr (std::is_same<T, float>::value) {
-                float drho;  // FP32 storage: deviations, equilibrium in deviation form
+                // FP32 / 16-bit storage: f*(m) in deviation form, m taken from the
+                // pass's input (the collision conserves m), so f* is the very
+                // equilibrium of the step kernel, rounded to storage once
+                float drho, nq[Q];
+                pull_dev<Q, S>(p, x, y, g);
                 moments_dev<Q>(g, p.rho_ref, drho, rho, ux, uy);
                 feq_dev<Q>(drho, rho, ux, uy, fs);
+                // f* as g - n (the limiter with phi = 0): mass and momentum kept
+                neq_dev<Q>(g, fs, nq);
+#pragma unroll
+                for (int q = 0; q < Q; ++q) fs[q] = g[q] - nq[q];
             } else {
+                // FP64: f*(m(f')) from the stored f', in the oracle's order
+#pragma unroll
+                for (int q = 0; q < Q; ++q) g[q] = s2f(f[fidx(p.plane, p.pitch, q, y, x)]);
                 moments<Q, T>(g, rho, ux, uy);
                 feq<Q, T>(rho, ux, uy, fs);
             }
 #pragma unroll
-            for (int q = 0; q < Q; ++q) f[fidx(p.plane, p.pitch, q, y, x)] = fs[q];
+            for (int q = 0; q < Q; ++q) f[fidx(p.plane, p.pitch, q, y, x)] = f2s<S>(fs[q]);
             ehr_sum = Ar<double>::add(ehr_sum, Ar<double>::mul(Ar<double>::mul(c.phi, c.phi), c.key));
         }
         __syncthreads();
@@ -315,5 +355,7 @@ cudaError_t launch_finalize_batched_f32(int q, const FinalArgs *table, int n, cu
 
 template cudaError_t launch_finalize<float>(int, const FinalParams &, float *, cudaStream_t);
 template cudaError_t launch_finalize<double>(int, const FinalParams &, double *, cudaStream_t);
+template cudaError_t launch_finalize<__nv_bfloat16>(int, const FinalParams &, __nv_bfloat16 *, cudaStream_t);
+template cudaError_t launch_finalize<__half>(int, const FinalParams &, __half *, cudaStream_t);
 
 }  // namespace lbm

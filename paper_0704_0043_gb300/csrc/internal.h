@@ -51,6 +51,10 @@ struct StepParams {
     double a;                  // 2 beta - 1
     double delta_m, delta_e;
     double lid[9];             // ((6 W_k) rho_wall) (c_kx u_lid), added on links through the lid
+    // the same term for FP32 arithmetic as an unevaluated sum hi + lo: adding
+    // both parts keeps the rounding of the constant out of every wall step
+    // (a single FP32 constant would bias the lid momentum by ~1e-9 per step)
+    float lidf[9], lidlo[9];
     float rho_ref;             // FP32 storage holds g_k = f_k - rho_ref W_k
     double rw[9];              // rho_ref W_k in FP64 (absolute value of FP32 storage: (double) g + rw)
     float rwf[9];              // rho_ref W_k in FP32
@@ -85,10 +89,14 @@ struct FinalParams {
     // candidates recorded without an FP64 key (fused kernel): the key dS(f') is
     // recomputed in FP64 from the pre-step populations `src` before selection
     int recompute;
-    const float *src;
+    // pre-step populations of the pass (FP32 / BF16 / FP16 storage): the
+    // Ehrenfests' step evaluates f*(m) from them, with the same FP32 free
+    // flight as the step kernel, so the stored result is rounded once
+    const void *src;
     int boundary;
     double a, delta_e;
     double lid[9];
+    float lidf[9], lidlo[9];
     float rho_ref;
     double rw[9];
 };
@@ -97,11 +105,13 @@ struct FinalParams {
 // strip / segment decomposition).
 struct FusedArgs {
     StepParams p;
-    const float *src;
-    float *dst;
+    const void *src;  // float, __nv_bfloat16 or __half deviations
+    void *dst;
     int strips, seg_rows, blocks;
-    float a, delta_m, thr_e, rho_ref;
-    float lid4, lid7, lid8;  // FP32 moving-wall terms of the links through the lid
+    int sw;  // finished columns per strip (a multiple of 8)
+    float a, b2, delta_m, thr_e, rho_ref;  // b2 = 2 beta
+    float lid4, lid7, lid8;  // FP32 moving-wall terms of the links through the lid (hi + lo)
+    float lo4, lo7, lo8;
 };
 
 // One tiled-kernel instance (batched launches) and one tail instance.
@@ -141,17 +151,18 @@ cudaError_t launch_delta_s(int q, const StepParams &p, const T *f, double *out, 
 int set_thread_error_impl(int s, const char *msg);
 #define set_thread_error(s, msg) ((lbm_status)::lbm::set_thread_error_impl((int)(s), (msg)))
 
-// Fused FP32 D2Q9 step for LBM_BC_WALLS (row-streaming kernel).
-cudaError_t launch_fused_d2q9(const StepParams &p, const float *src, float *dst, int *nblocks,
-                              cudaStream_t s);
-int fused_d2q9_blocks(int nx, int ny);
-// Fills the instance arguments for block width T (256 or 320) and a target
-// number of blocks per SM wave (`slots`); returns the block count.
-int fused_make_args(const StepParams &p, const float *src, float *dst, int T, int slots, FusedArgs *out);
-int fused_pick_T(int nx);
+// Fused D2Q9 step for LBM_BC_WALLS (row-streaming kernel; FP32, BF16 or FP16
+// storage).
+template <typename S>
+cudaError_t launch_fused_d2q9(const StepParams &p, const S *src, S *dst, int *nblocks, cudaStream_t s);
+int fused_d2q9_blocks(int nx, int ny);  // most blocks (partial-sum rows) any launch of the lattice uses
+int fused_slots();                      // resident blocks of one wave (2 per SM)
+// Fills the instance arguments: strip width at most `max_width` columns (0:
+// automatic), about `slots` blocks; returns the block count.
+int fused_make_args(const StepParams &p, const void *src, void *dst, int max_width, int slots, FusedArgs *out);
 // Batched launches: `blocks` blocks in total; block b runs instance map[b].x
 // with local block id map[b].y (tables in device memory).
-cudaError_t launch_fused_batched(int T, const FusedArgs *table, const int2 *map, int blocks, cudaStream_t s);
+cudaError_t launch_fused_batched(const FusedArgs *table, const int2 *map, int blocks, cudaStream_t s);
 cudaError_t launch_tiled_batched_f32(int q, const TiledArgs *table, const int2 *map, int blocks, cudaStream_t s);
 cudaError_t launch_finalize_batched_f32(int q, const FinalArgs *table, int n, cudaStream_t s);
 int tiled_grid_x(int q, int nx);

@@ -12,12 +12,31 @@
 //   Ar<float> uses the plain operators; the compiler may fuse them.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <type_traits>
 
 namespace lbm {
+
+// Storage types: double (FP64 contexts: f itself), float, __nv_bfloat16 and
+// __half (the deviations g = f - rho_ref W).  Arithmetic is FP64 for double
+// storage and FP32 otherwise.
+template <typename S>
+using compute_t = typename std::conditional<std::is_same<S, double>::value, double, float>::type;
+
+__device__ __forceinline__ float s2f(float v) { return v; }
+__device__ __forceinline__ float s2f(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float s2f(__half v) { return __half2float(v); }
+__device__ __forceinline__ double s2f(double v) { return v; }
+
+template <typename S> __device__ __forceinline__ S f2s(compute_t<S> v);
+template <> __device__ __forceinline__ double f2s<double>(double v) { return v; }
+template <> __device__ __forceinline__ float f2s<float>(float v) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 f2s<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <> __device__ __forceinline__ __half f2s<__half>(float v) { return __float2half_rn(v); }
 
 template <typename T> struct Ar;
 
@@ -245,6 +264,15 @@ __device__ __forceinline__ T phi_median(T x, T med, T delta, int mode)
     return x > t ? A::sqrt(A::div(t, x)) : T(1);
 }
 
+// Hardware reciprocal approximation (one special-function instruction,
+// relative error below 2^-22): the FP32 entropy denominators.
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // ---------------------------------------------------------------------------
 // FP32 storage holds deviations g_k = f_k - rho_ref W_k from a uniform rest
 // state (the D2Q9 and D1Q3 weights are symmetric under k -> opp(k), so
@@ -339,33 +367,91 @@ __device__ __forceinline__ void feq_dev(float drho, float rho, float ux, float u
         feq3_dev(drho, rho, ux, gs);
 }
 
-// FP32 counterpart of site_collide on deviations: g* and g' (deviations of f*
-// and f'), the absolute f* (rw_k + g*_k, for the entropy denominators and the
-// positivity rule), dS(f') = (2 beta - 1)^2 dS(f_in), dS(f_in), rho.
+// Nonequilibrium part n = g - g* with its mass and momentum sums taken out.
+// In exact arithmetic they vanish; in FP32 they carry the rounding of the
+// moment sums (up to half an ulp of rho u ~ 0.1, i.e. ~4e-9 per site and
+// step).  The collision and the limiters move g along n only (see
+// site_collide_dev), so with these sums removed they conserve mass and
+// momentum to the rounding of the stored values: on a 1000-step cavity run the
+// FP32 error then stays at the level of FP32 storage alone instead of
+// several times above it.  The sums of n are small numbers and nearly exact.
+__device__ __forceinline__ void neq9(const float g[9], const float gs[9], float n[9])
+{
+#pragma unroll
+    for (int k = 0; k < 9; ++k) n[k] = g[k] - gs[k];
+    const float rm = ((n[0] + n[1]) + (n[2] + n[3])) + ((n[4] + n[5]) + (n[6] + n[7])) + n[8];
+    const float hx = 0.5f * (((n[1] - n[3]) + (n[5] - n[6])) + (n[8] - n[7]));
+    const float hy = 0.5f * (((n[2] - n[4]) + (n[5] + n[6])) - (n[7] + n[8]));
+    n[0] -= rm;
+    n[1] -= hx;
+    n[3] += hx;
+    n[2] -= hy;
+    n[4] += hy;
+}
+
+__device__ __forceinline__ void neq3(const float g[3], const float gs[3], float n[3])
+{
+#pragma unroll
+    for (int k = 0; k < 3; ++k) n[k] = g[k] - gs[k];
+    const float rm = (n[0] + n[1]) + n[2];
+    const float hx = 0.5f * (n[2] - n[1]);
+    n[0] -= rm;
+    n[2] -= hx;
+    n[1] += hx;
+}
+
 template <int Q>
-__device__ __forceinline__ bool site_collide_dev(const float g[Q], float a, bool collide, float rho_ref,
-                                                 const float rw[Q], float gs[Q], float gp[Q], float fsa[Q],
-                                                 float &ds, float &ds_in, float &rho)
+__device__ __forceinline__ void neq_dev(const float g[Q], const float gs[Q], float n[Q])
+{
+    if constexpr (Q == 9)
+        neq9(g, gs, n);
+    else
+        neq3(g, gs, n);
+}
+
+// Weight of n in the limited update.  With f* + phi (f' - f*) (Eq. LimGenF)
+// and f' = f* + (2 beta - 1)(f* - f) the result is g - c n with
+// c = 1 + phi (2 beta - 1) after a collision, c = 1 - phi for a limiter pass
+// on stored populations (f' = f); c = 1 (phi = 0) is the Ehrenfests' step.
+__device__ __forceinline__ float limit_weight(float phi, float a, bool collide)
+{
+    return collide ? fmaf(phi, a, 1.f) : 1.f - phi;
+}
+
+// FP32 counterpart of site_collide on deviations: g* and the corrected
+// nonequilibrium part n, g' = g - 2 beta n (collision, b2 = 2 beta) or g'
+// = g, the absolute f* (rw_k + g*_k, for the entropy denominators and the
+// positivity rule), dS(f') = (2 beta - 1)^2 dS(f_in) (quadratic form of
+// Sec. 3.6 with the denominators by the hardware reciprocal), dS(f_in), rho.
+template <int Q>
+__device__ __forceinline__ bool site_collide_dev(const float g[Q], float a, float b2, bool collide, float rho_ref,
+                                                 const float rw[Q], float gs[Q], float n[Q], float gp[Q],
+                                                 float fsa[Q], float &ds, float &ds_in, float &rho)
 {
     float drho, ux, uy;
     moments_dev<Q>(g, rho_ref, drho, rho, ux, uy);
     feq_dev<Q>(drho, rho, ux, uy, gs);
+    neq_dev<Q>(g, gs, n);
     float din = 0.f, fmin = 3.4e38f;
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
-        const float d = gs[k] - g[k];
         fsa[k] = rw[k] + gs[k];
-        din = fmaf(d, __fdividef(d, fsa[k]), din);
-        gp[k] = collide ? fmaf(a, d, gs[k]) : g[k];
+        din = fmaf(n[k] * n[k], rcp_approx(fsa[k]), din);
+        gp[k] = collide ? fmaf(-b2, n[k], g[k]) : g[k];
         fmin = fminf(fmin, fsa[k]);
     }
     ds_in = collide ? din : 0.f;
-    ds = collide ? a * a * din : din;
+    ds = collide ? (a * a) * din : din;
     return !(rho > 0.f) || !(fmin > 0.f) || !isfinite(ds);
 }
 
-template <typename T> __device__ __forceinline__ T tmin(T a, T b) { return b < a ? b : a; }
-template <typename T> __device__ __forceinline__ T tmax(T a, T b) { return a < b ? b : a; }
+// min / max selecting one of the two operands (one instruction each; the
+// values compared here are never NaN)
+__device__ __forceinline__ float tmin(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ float tmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double tmin(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ double tmax(double a, double b) { return fmax(a, b); }
+
 
 template <typename T> __device__ __forceinline__ T med3(T a, T b, T c)
 {

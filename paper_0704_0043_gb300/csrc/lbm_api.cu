@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/lbm.h"
@@ -46,9 +47,22 @@ lbm_status cuda_fail(lbm_ctx *c, cudaError_t e, const char *what)
 
 int lattice_q(int lattice) { return lattice == LBM_D1Q3 ? 3 : 9; }
 
+// Calls fn with a null pointer of the context's storage type.
+template <typename F>
+cudaError_t with_storage(int precision, F &&fn)
+{
+    switch (precision) {
+    case LBM_FP64: return fn((double *)nullptr);
+    case LBM_FP32: return fn((float *)nullptr);
+    case LBM_BF16: return fn((__nv_bfloat16 *)nullptr);
+    default: return fn((__half *)nullptr);
+    }
+}
+#define STORAGE_T typename std::remove_pointer<decltype(tag)>::type
+
 bool fused_applies(const lbm_config &c)
 {
-    return c.lattice == LBM_D2Q9 && c.precision == LBM_FP32 && c.boundary == LBM_BC_WALLS &&
+    return c.lattice == LBM_D2Q9 && c.precision != LBM_FP64 && c.boundary == LBM_BC_WALLS &&
            c.kernel != LBM_KERNEL_TILED && fused_d2q9_fits((long long)c.ny * row_pitch(c.nx));
 }
 
@@ -64,7 +78,8 @@ std::string validate(const lbm_config *c)
     if (c->lattice != LBM_D1Q3 && c->lattice != LBM_D2Q9) return "lattice must be LBM_D1Q3 or LBM_D2Q9";
     if (c->nx < 1 || c->ny < 1) return "nx and ny must be >= 1";
     if ((long long)c->nx * c->ny > 0x7fffffffLL) return "nx * ny must fit a 32-bit site index";
-    if (c->precision != LBM_FP64 && c->precision != LBM_FP32) return "precision must be LBM_FP64 or LBM_FP32";
+    if (c->precision < LBM_FP64 || c->precision > LBM_FP16)
+        return "precision must be LBM_FP64, LBM_FP32, LBM_BF16 or LBM_FP16";
     if (c->lattice == LBM_D1Q3) {
         if (c->ny != 1) return "D1Q3 needs ny == 1";
         if (c->boundary != LBM_BC_WALLS && c->boundary != LBM_BC_PERIODIC)
@@ -83,7 +98,7 @@ std::string validate(const lbm_config *c)
     if (c->median_mode != LBM_MEDIAN_THRESHOLD && c->median_mode != LBM_MEDIAN_GATE) return "unknown median_mode";
     if (c->kernel < LBM_KERNEL_AUTO || c->kernel > LBM_KERNEL_FUSED) return "unknown kernel";
     if (c->kernel == LBM_KERNEL_FUSED && !fused_applies(*c))
-        return "LBM_KERNEL_FUSED needs D2Q9, LBM_FP32 and LBM_BC_WALLS";
+        return "LBM_KERNEL_FUSED needs D2Q9, FP32/BF16/FP16 storage and LBM_BC_WALLS";
     if (c->stats_history < 0) return "stats_history must be >= 0";
     if (!(c->rho_ref > 0.0) || !std::isfinite(c->rho_ref)) return "rho_ref must be finite and > 0";
     return "";
@@ -106,7 +121,7 @@ Sizes sizes_for(const lbm_config &c)
     z.q = lattice_q(c.lattice);
     z.pitch = row_pitch(c.nx);
     z.plane = (long long)c.ny * z.pitch;
-    z.elem = c.precision == LBM_FP64 ? 8 : 4;
+    z.elem = c.precision == LBM_FP64 ? 8 : (c.precision == LBM_FP32 ? 4 : 2);
     z.field = (size_t)z.q * (size_t)z.plane * z.elem;
     const long long n = (long long)c.nx * c.ny;
     z.cand_cap = (c.limiters & LBM_LIM_EHRENFEST) ? (int)n : 1;
@@ -179,6 +194,8 @@ StepParams step_params(lbm_ctx *c, int collide, unsigned limiters)
     for (int k = 0; k < 9; ++k) {
         const bool lid = c->q == 9 && g.boundary != LBM_BC_PERIODIC && Lat<9>::cy(k) == -1;
         p.lid[k] = lid ? ((6.0 * Lat<9>::w(k)) * g.rho_wall) * ((double)Lat<9>::cx(k) * g.u_lid) : 0.0;
+        p.lidf[k] = (float)p.lid[k];
+        p.lidlo[k] = (float)(p.lid[k] - (double)p.lidf[k]);
     }
     p.rho_ref = (float)g.rho_ref;
     for (int k = 0; k < 9; ++k) {
@@ -220,6 +237,18 @@ FinalParams final_params(lbm_ctx *c, int collide, unsigned limiters, int nblocks
     f.stats_ring = c->ring;
     f.ring_len = c->ring_len;
     f.counters = c->counters;
+    const StepParams p = step_params(c, collide, limiters);
+    f.src = c->buf[c->cur];
+    f.boundary = g.boundary;
+    f.a = p.a;
+    f.delta_e = p.delta_e;
+    for (int k = 0; k < 9; ++k) {
+        f.lid[k] = p.lid[k];
+        f.lidf[k] = p.lidf[k];
+        f.lidlo[k] = p.lidlo[k];
+        f.rw[k] = p.rw[k];
+    }
+    f.rho_ref = p.rho_ref;
     return f;
 }
 
@@ -254,30 +283,21 @@ lbm_status run_pass(lbm_ctx *c, int collide, unsigned limiters)
     int nblocks = 0;
     cudaError_t e;
     void *src = c->buf[c->cur], *dst = c->buf[c->cur ^ 1];
-    if (c->cfg.precision == LBM_FP64) {
-        e = launch_tiled<double>(c->q, p, (const double *)src, (double *)dst, &nblocks, c->stream);
-    } else if (collide && fused_applies(c->cfg)) {
-        e = launch_fused_d2q9(p, (const float *)src, (float *)dst, &nblocks, c->stream);
-    } else {
-        e = launch_tiled<float>(c->q, p, (const float *)src, (float *)dst, &nblocks, c->stream);
-    }
+    const bool fused = collide && fused_applies(c->cfg);
+    e = with_storage(c->cfg.precision, [&](auto tag) -> cudaError_t {
+        using S = STORAGE_T;
+        if constexpr (!std::is_same<S, double>::value)
+            if (fused) return launch_fused_d2q9<S>(p, (const S *)src, (S *)dst, &nblocks, c->stream);
+        return launch_tiled<S>(c->q, p, (const S *)src, (S *)dst, &nblocks, c->stream);
+    });
     if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
     if ((ms = mark(c)) != LBM_OK) return ms;
     FinalParams f = final_params(c, collide, limiters, nblocks);
-    if (collide && c->cfg.precision == LBM_FP32 && fused_applies(c->cfg)) {
-        f.recompute = 1;
-        f.src = (const float *)src;
-        f.boundary = c->cfg.boundary;
-        f.a = p.a;
-        f.delta_e = p.delta_e;
-        for (int k = 0; k < 9; ++k) f.lid[k] = p.lid[k];
-    }
-    f.rho_ref = p.rho_ref;
-    for (int k = 0; k < 9; ++k) f.rw[k] = p.rw[k];
-    if (c->cfg.precision == LBM_FP64)
-        e = launch_finalize<double>(c->q, f, (double *)dst, c->stream);
-    else
-        e = launch_finalize<float>(c->q, f, (float *)dst, c->stream);
+    f.recompute = fused ? 1 : 0;
+    e = with_storage(c->cfg.precision, [&](auto tag) -> cudaError_t {
+        using S = STORAGE_T;
+        return launch_finalize<S>(c->q, f, (S *)dst, c->stream);
+    });
     if (e != cudaSuccess) return cuda_fail(c, e, "finalize kernel launch");
     if ((ms = mark(c)) != LBM_OK) return ms;
     c->launches += 2;
@@ -453,10 +473,10 @@ lbm_status lbm_init(lbm_ctx *c, const double *rho, const double *ux, const doubl
     if (uy && c->q == 9 && (s = dev_in(c, uy, n, 2 * n, &dv)) != LBM_OK) return s;
     cudaError_t e;
     const StepParams sp = step_params(c, 1, 0);
-    if (c->cfg.precision == LBM_FP64)
-        e = launch_init<double>(c->q, sp, dr, du, dv, (double *)c->buf[0], c->stream);
-    else
-        e = launch_init<float>(c->q, sp, dr, du, dv, (float *)c->buf[0], c->stream);
+    e = with_storage(c->cfg.precision, [&](auto tag) -> cudaError_t {
+        using S = STORAGE_T;
+        return launch_init<S>(c->q, sp, dr, du, dv, (S *)c->buf[0], c->stream);
+    });
     if (e != cudaSuccess) return cuda_fail(c, e, "init kernel launch");
     c->launches++;
     c->cur = 0;
@@ -502,9 +522,10 @@ lbm_status lbm_delta_s(lbm_ctx *c, double *out)
         dst = c->stage;
     }
     StepParams p = step_params(c, 1, 0);
-    cudaError_t e = c->cfg.precision == LBM_FP64
-                        ? launch_delta_s<double>(c->q, p, (const double *)c->buf[c->cur], dst, c->stream)
-                        : launch_delta_s<float>(c->q, p, (const float *)c->buf[c->cur], dst, c->stream);
+    cudaError_t e = with_storage(c->cfg.precision, [&](auto tag) -> cudaError_t {
+        using S = STORAGE_T;
+        return launch_delta_s<S>(c->q, p, (const S *)c->buf[c->cur], dst, c->stream);
+    });
     if (e != cudaSuccess) return cuda_fail(c, e, "delta_s kernel launch");
     c->launches++;
     if (!dev) CK(c, cudaMemcpyAsync(out, dst, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -530,9 +551,10 @@ lbm_status lbm_moments(lbm_ctx *c, double *rho, double *ux, double *uy)
         dv = uy ? c->stage + 2 * n : nullptr;
     }
     const StepParams sp = step_params(c, 1, 0);
-    cudaError_t e = c->cfg.precision == LBM_FP64
-                        ? launch_moments<double>(c->q, sp, (const double *)c->buf[c->cur], dr, du, dv, c->stream)
-                        : launch_moments<float>(c->q, sp, (const float *)c->buf[c->cur], dr, du, dv, c->stream);
+    cudaError_t e = with_storage(c->cfg.precision, [&](auto tag) -> cudaError_t {
+        using S = STORAGE_T;
+        return launch_moments<S>(c->q, sp, (const S *)c->buf[c->cur], dr, du, dv, c->stream);
+    });
     if (e != cudaSuccess) return cuda_fail(c, e, "moments kernel launch");
     c->launches++;
     if (!dev) {
@@ -613,9 +635,10 @@ lbm_status lbm_get_populations(lbm_ctx *c, double *f)
         dst = c->stage;
     }
     const StepParams sp = step_params(c, 1, 0);
-    cudaError_t e = c->cfg.precision == LBM_FP64
-                        ? launch_get<double>(c->q, sp, (const double *)c->buf[c->cur], dst, c->stream)
-                        : launch_get<float>(c->q, sp, (const float *)c->buf[c->cur], dst, c->stream);
+    cudaError_t e = with_storage(c->cfg.precision, [&](auto tag) -> cudaError_t {
+        using S = STORAGE_T;
+        return launch_get<S>(c->q, sp, (const S *)c->buf[c->cur], dst, c->stream);
+    });
     if (e != cudaSuccess) return cuda_fail(c, e, "get kernel launch");
     c->launches++;
     if (!dev) CK(c, cudaMemcpyAsync(f, dst, tot * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -635,9 +658,10 @@ lbm_status lbm_set_populations(lbm_ctx *c, const double *f)
         if ((s = dev_in(c, f, tot, 0, &src)) != LBM_OK) return s;
     }
     const StepParams sp = step_params(c, 1, 0);
-    cudaError_t e = c->cfg.precision == LBM_FP64
-                        ? launch_set<double>(c->q, sp, src, (double *)c->buf[0], c->stream)
-                        : launch_set<float>(c->q, sp, src, (float *)c->buf[0], c->stream);
+    cudaError_t e = with_storage(c->cfg.precision, [&](auto tag) -> cudaError_t {
+        using S = STORAGE_T;
+        return launch_set<S>(c->q, sp, src, (S *)c->buf[0], c->stream);
+    });
     if (e != cudaSuccess) return cuda_fail(c, e, "set kernel launch");
     c->launches++;
     c->cur = 0;

@@ -117,6 +117,8 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_config *cfg, const double *f_in
     for (int k = 0; k < 9; ++k) {
         const bool lid = q == 9 && cfg->boundary != LBM_BC_PERIODIC && Lat<9>::cy(k) == -1;
         p.lid[k] = lid ? ((6.0 * Lat<9>::w(k)) * cfg->rho_wall) * ((double)Lat<9>::cx(k) * cfg->u_lid) : 0.0;
+        p.lidf[k] = (float)p.lid[k];
+        p.lidlo[k] = (float)(p.lid[k] - (double)p.lidf[k]);
         p.rw[k] = 0.0;
         p.rwf[k] = 0.0f;
     }

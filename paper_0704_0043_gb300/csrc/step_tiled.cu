@@ -28,16 +28,18 @@ __device__ __forceinline__ long long fidx(long long plane, int pitch, int k, int
     return (long long)k * plane + (long long)y * pitch + kLead + x;
 }
 
-// Stored value as a compute value: FP64 storage is f itself; FP32 storage is
-// the deviation g, read as g in FP32 or as the absolute f = (double) g + rw_k
-// in FP64.
+// Stored value as a compute value: FP64 storage is f itself; FP32 / BF16 /
+// FP16 storage is the deviation g, read as g in FP32 or as the absolute
+// f = (double) g + rw_k in FP64.
 template <typename S, typename T>
 __device__ __forceinline__ T load_as(const StepParams &p, S v, int k)
 {
-    if constexpr (std::is_same<S, float>::value && std::is_same<T, double>::value)
-        return Ar<double>::add((double)v, p.rw[k]);
-    else
+    if constexpr (std::is_same<S, double>::value)
         return T(v);
+    else if constexpr (std::is_same<T, double>::value)
+        return Ar<double>::add((double)s2f(v), p.rw[k]);
+    else
+        return s2f(v);
 }
 
 // Free flight in pull form at site (x, y) (Sec. 2): f_in_k(x) = f_k(x - v_k);
@@ -59,7 +61,12 @@ __device__ __forceinline__ void pull(const StepParams &p, const S *__restrict__ 
             fin[k] = load_as<S, T>(p, f[fidx(p.plane, p.pitch, k, sy, sx)], k);
         } else {
             T v = load_as<S, T>(p, f[fidx(p.plane, p.pitch, Lat<Q>::opp(k), y, x)], Lat<Q>::opp(k));
-            if (Q == 9 && sy > p.ny - 1) v = A::add(v, T(p.lid[k]));
+            if (Q == 9 && sy > p.ny - 1) {
+                if constexpr (std::is_same<T, double>::value)
+                    v = A::add(v, p.lid[k]);
+                else
+                    v = A::add(A::add(v, p.lidf[k]), p.lidlo[k]);
+            }
             fin[k] = v;
         }
     }
@@ -109,10 +116,11 @@ __device__ __forceinline__ double warp_sum(double v)
 
 // BATCHED: block b runs instance map[b].x of `table` as its block map[b].y
 // (tiles numbered row by row); otherwise the single instance (p0, src0, dst0).
-template <int Q, typename T, bool BATCHED>
-__global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const T *__restrict__ src0, T *__restrict__ dst0,
+template <int Q, typename S, bool BATCHED>
+__global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const S *__restrict__ src0, S *__restrict__ dst0,
                                                const TiledArgs *__restrict__ table, const int2 *__restrict__ map)
 {
+    using T = compute_t<S>;
     using A = Ar<T>;
     constexpr int BX = Q == 9 ? kTX : kT1;
     constexpr int BY = Q == 9 ? kTY : 1;
@@ -132,8 +140,8 @@ __global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const T *__r
         by = m.y / gx;
     }
     const StepParams &p = BATCHED ? sA.p : p0;
-    const T *__restrict__ src = BATCHED ? (const T *)sA.src : src0;
-    T *__restrict__ dst = BATCHED ? (T *)sA.dst : dst0;
+    const S *__restrict__ src = BATCHED ? (const S *)sA.src : src0;
+    S *__restrict__ dst = BATCHED ? (S *)sA.dst : dst0;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int x = bx * (BX - 2) - 1 + tx;
     const int y = Q == 9 ? by * (BY - 2) - 1 + ty : 0;
@@ -144,23 +152,26 @@ __global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const T *__r
     const int xs = wrapx ? (x < 0 ? x + p.nx : (x >= p.nx ? x - p.nx : x)) : x;
     const int ys = wrapy ? (y < 0 ? y + p.ny : (y >= p.ny ? y - p.ny : y)) : y;
 
-    // FP64: fs = f*, fp = f'.  FP32: fs = g*, fp = g' (deviations), fa = absolute f*.
+    // FP64: fs = f*, fp = f'.  FP32: fs = g*, fp = g' (deviations), fa = absolute f*,
+    // nq = corrected nonequilibrium part g - g* (lattice.cuh).
     T fin[Q], fs[Q], fp[Q], fa[Q];
+    float nq[Q];
     T ds = T(0), dsin = T(0), rho = T(0);
     bool bad = false;
     if (valid) {
         if (p.collide) {
-            pull<Q, T, T>(p, src, xs, ys, fin);
+            pull<Q, S, T>(p, src, xs, ys, fin);
         } else {
 #pragma unroll
-            for (int k = 0; k < Q; ++k) fin[k] = src[fidx(p.plane, p.pitch, k, ys, xs)];
+            for (int k = 0; k < Q; ++k) fin[k] = load_as<S, T>(p, src[fidx(p.plane, p.pitch, k, ys, xs)], k);
         }
         if constexpr (std::is_same<T, double>::value) {
             bad = site_collide<Q, T>(fin, T(p.a), p.collide != 0, fs, fp, ds, dsin, rho);
 #pragma unroll
             for (int k = 0; k < Q; ++k) fa[k] = fs[k];
         } else {
-            bad = site_collide_dev<Q>(fin, (float)p.a, p.collide != 0, p.rho_ref, p.rwf, fs, fp, fa, ds, dsin, rho);
+            bad = site_collide_dev<Q>(fin, (float)p.a, (float)(1.0 + p.a), p.collide != 0, p.rho_ref, p.rwf, fs, nq,
+                                      fp, fa, ds, dsin, rho);
         }
         if (bad) ds = T(INFINITY);
     }
@@ -194,12 +205,19 @@ __global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const T *__r
         }
         const T phi = phi_pos < phi_med ? phi_pos : phi_med;
         if (phi < T(1)) {
+            if constexpr (std::is_same<T, double>::value) {
 #pragma unroll
-            for (int k = 0; k < Q; ++k) dst[fidx(p.plane, p.pitch, k, y, x)] = A::add(fs[k], A::mul(phi, A::sub(fp[k], fs[k])));
+                for (int k = 0; k < Q; ++k)
+                    dst[fidx(p.plane, p.pitch, k, y, x)] = f2s<S>(A::add(fs[k], A::mul(phi, A::sub(fp[k], fs[k]))));
+            } else {
+                const float c = limit_weight(phi, (float)p.a, p.collide != 0);
+#pragma unroll
+                for (int k = 0; k < Q; ++k) dst[fidx(p.plane, p.pitch, k, y, x)] = f2s<S>(fmaf(-c, nq[k], fin[k]));
+            }
             acc[P_DS_LIM] = Ar<double>::mul(Ar<double>::sub(1.0, Ar<double>::mul((double)phi, (double)phi)), (double)ds);
         } else {
 #pragma unroll
-            for (int k = 0; k < Q; ++k) dst[fidx(p.plane, p.pitch, k, y, x)] = fp[k];
+            for (int k = 0; k < Q; ++k) dst[fidx(p.plane, p.pitch, k, y, x)] = f2s<S>(fp[k]);
         }
         acc[P_MASS] = (double)rho;
         if (!bad) {
@@ -224,10 +242,10 @@ __global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const T *__r
                 if (ds > (float)(p.delta_e * (1.0 - 1.0 / 64.0))) {
                     double fin64[Q], fs64[Q], fp64[Q], d64, din64, r64;
                     if (p.collide) {
-                        pull<Q, T, double>(p, src, x, y, fin64);
+                        pull<Q, S, double>(p, src, x, y, fin64);
                     } else {
 #pragma unroll
-                        for (int k = 0; k < Q; ++k) fin64[k] = load_as<T, double>(p, src[fidx(p.plane, p.pitch, k, y, x)], k);
+                        for (int k = 0; k < Q; ++k) fin64[k] = load_as<S, double>(p, src[fidx(p.plane, p.pitch, k, y, x)], k);
                     }
                     const bool b64 = site_collide<Q, double>(fin64, p.a, p.collide != 0, fs64, fp64, d64, din64, r64);
                     key = d64;
@@ -265,22 +283,22 @@ __global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const T *__r
     }
 }
 
-template <int Q, typename T>
-__global__ void k_delta_s(StepParams p, const T *__restrict__ f, double *__restrict__ out)
+template <int Q, typename S>
+__global__ void k_delta_s(StepParams p, const S *__restrict__ f, double *__restrict__ out)
 {
     const long long n = (long long)p.nx * p.ny;
     for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(s % p.nx), y = (int)(s / p.nx);
         double fin[Q], fs[Q], fp[Q], ds, dsin, rho;
-        pull<Q, T, double>(p, f, x, y, fin);
+        pull<Q, S, double>(p, f, x, y, fin);
         const bool bad = site_collide<Q, double>(fin, p.a, true, fs, fp, ds, dsin, rho);
         out[s] = bad ? (double)INFINITY : ds;
     }
 }
 
-template <int Q, typename T>
+template <int Q, typename S>
 __global__ void k_init(StepParams p, const double *__restrict__ rho, const double *__restrict__ ux,
-                       const double *__restrict__ uy, T *__restrict__ f)
+                       const double *__restrict__ uy, S *__restrict__ f)
 {
     const long long n = (long long)p.nx * p.ny;
     for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
@@ -289,16 +307,16 @@ __global__ void k_init(StepParams p, const double *__restrict__ rho, const doubl
         feq<Q, double>(rho[s], ux[s], uy ? uy[s] : 0.0, fs);
 #pragma unroll
         for (int k = 0; k < Q; ++k) {
-            if constexpr (std::is_same<T, float>::value)
-                f[fidx(p.plane, p.pitch, k, y, x)] = (float)Ar<double>::sub(fs[k], p.rw[k]);
-            else
+            if constexpr (std::is_same<S, double>::value)
                 f[fidx(p.plane, p.pitch, k, y, x)] = fs[k];
+            else
+                f[fidx(p.plane, p.pitch, k, y, x)] = f2s<S>((float)Ar<double>::sub(fs[k], p.rw[k]));
         }
     }
 }
 
-template <int Q, typename T>
-__global__ void k_moments(StepParams p, const T *__restrict__ f, double *__restrict__ rho, double *__restrict__ ux,
+template <int Q, typename S>
+__global__ void k_moments(StepParams p, const S *__restrict__ f, double *__restrict__ rho, double *__restrict__ ux,
                           double *__restrict__ uy)
 {
     const long long n = (long long)p.nx * p.ny;
@@ -306,7 +324,7 @@ __global__ void k_moments(StepParams p, const T *__restrict__ f, double *__restr
         const int x = (int)(s % p.nx), y = (int)(s / p.nx);
         double g[Q], r, a, b;
 #pragma unroll
-        for (int k = 0; k < Q; ++k) g[k] = load_as<T, double>(p, f[fidx(p.plane, p.pitch, k, y, x)], k);
+        for (int k = 0; k < Q; ++k) g[k] = load_as<S, double>(p, f[fidx(p.plane, p.pitch, k, y, x)], k);
         moments<Q, double>(g, r, a, b);
         rho[s] = r;
         ux[s] = a;
@@ -314,29 +332,29 @@ __global__ void k_moments(StepParams p, const T *__restrict__ f, double *__restr
     }
 }
 
-template <typename T>
-__global__ void k_get(int q, StepParams p, const T *__restrict__ f, double *__restrict__ out)
+template <typename S>
+__global__ void k_get(int q, StepParams p, const S *__restrict__ f, double *__restrict__ out)
 {
     const long long n = (long long)p.nx * p.ny, tot = n * q;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
         const int k = (int)(e / n);
         const long long s = e % n;
-        out[e] = load_as<T, double>(p, f[fidx(p.plane, p.pitch, k, (int)(s / p.nx), (int)(s % p.nx))], k);
+        out[e] = load_as<S, double>(p, f[fidx(p.plane, p.pitch, k, (int)(s / p.nx), (int)(s % p.nx))], k);
     }
 }
 
-template <typename T>
-__global__ void k_set(int q, StepParams p, const double *__restrict__ in, T *__restrict__ f)
+template <typename S>
+__global__ void k_set(int q, StepParams p, const double *__restrict__ in, S *__restrict__ f)
 {
     const long long n = (long long)p.nx * p.ny, tot = n * q;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
         const int k = (int)(e / n);
         const long long s = e % n;
-        T v;
-        if constexpr (std::is_same<T, float>::value)
-            v = (float)Ar<double>::sub(in[e], p.rw[k]);
-        else
+        S v;
+        if constexpr (std::is_same<S, double>::value)
             v = in[e];
+        else
+            v = f2s<S>((float)Ar<double>::sub(in[e], p.rw[k]));
         f[fidx(p.plane, p.pitch, k, (int)(s / p.nx), (int)(s % p.nx))] = v;
     }
 }
@@ -443,6 +461,8 @@ cudaError_t launch_set(int q, const StepParams &p, const double *in, T *f, cudaS
     template cudaError_t launch_set<T>(int, const StepParams &, const double *, T *, cudaStream_t);
 LBM_INST(float)
 LBM_INST(double)
+LBM_INST(__nv_bfloat16)
+LBM_INST(__half)
 #undef LBM_INST
 
 }  // namespace lbm

@@ -18,7 +18,7 @@ import numpy as np
 from . import build as _build
 
 D1Q3, D2Q9 = 1, 2
-FP64, FP32 = 0, 1
+FP64, FP32, BF16, FP16 = 0, 1, 2, 3
 BC_WALLS, BC_PERIODIC, BC_CHANNEL = 0, 1, 2
 LIM_POSITIVITY, LIM_EHRENFEST, LIM_MEDIAN = 1, 2, 4
 MEDIAN_THRESHOLD, MEDIAN_GATE = 0, 1
@@ -107,6 +107,33 @@ def lib():
         L.lbm_abi_version.restype = ctypes.c_int32
         L.lbm_step_noalloc.argtypes = [cfgp, vp, vp, ctypes.POINTER(StepStats), vp]
         L.lbm_step_noalloc.restype = ctypes.c_int
+        i32p, i64p = ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)
+        batch_sigs = {
+            "lbm_batch_create": [vp, ctypes.POINTER(vp)], "lbm_batch_destroy": [vp],
+            "lbm_batch_add": [vp, cfgp, i32p], "lbm_batch_remove": [vp, ctypes.c_int32],
+            "lbm_batch_init": [vp, ctypes.c_int32, vp, vp, vp],
+            "lbm_batch_set_populations": [vp, ctypes.c_int32, vp],
+            "lbm_batch_get_populations": [vp, ctypes.c_int32, vp],
+            "lbm_batch_moments": [vp, ctypes.c_int32, vp, vp, vp],
+            "lbm_batch_stats": [vp, ctypes.c_int32, ctypes.POINTER(StepStats)],
+            "lbm_batch_limited_sites": [vp, ctypes.c_int32, vp, ctypes.c_int64, i64p],
+            "lbm_batch_step": [vp, ctypes.c_int64], "lbm_batch_synchronize": [vp],
+            "lbm_batch_set_graph": [vp, ctypes.c_int32],
+            "lbm_batch_set_shape": [vp, ctypes.c_int32, ctypes.c_int32],
+            "lbm_batch_lattice_status": [vp, ctypes.c_int32],
+            "lbm_batch_tune": [vp, ctypes.c_int32, dp],
+        }
+        for name, args in batch_sigs.items():
+            getattr(L, name).argtypes = args
+            getattr(L, name).restype = ctypes.c_int
+        L.lbm_batch_size.argtypes = [vp]
+        L.lbm_batch_size.restype = ctypes.c_int32
+        L.lbm_batch_device_bytes.argtypes = [vp]
+        L.lbm_batch_device_bytes.restype = ctypes.c_int64
+        L.lbm_batch_launch_count.argtypes = [vp]
+        L.lbm_batch_launch_count.restype = ctypes.c_int64
+        L.lbm_batch_last_error.argtypes = [vp]
+        L.lbm_batch_last_error.restype = ctypes.c_char_p
         for name in ("lbm_create", "lbm_destroy", "lbm_init", "lbm_step", "lbm_delta_s", "lbm_limit",
                      "lbm_moments", "lbm_stats", "lbm_stats_history", "lbm_limited_sites",
                      "lbm_get_populations", "lbm_set_populations", "lbm_synchronize",
@@ -312,3 +339,115 @@ class Lattice:
 
     def launch_count(self) -> int:
         return lib().lbm_launch_count(self._h)
+
+
+def _bcheck(status: int, handle):
+    if status != OK:
+        raise LBMError(status, lib().lbm_batch_last_error(handle).decode(errors="replace"))
+
+
+class Batch:
+    """Many lattices stepped together (include/lbm_batch.h)."""
+
+    def __init__(self, stream: int | None = None):
+        self.stream = current_stream_handle() if stream is None else stream
+        h = ctypes.c_void_p()
+        _check(lib().lbm_batch_create(ctypes.c_void_p(self.stream), ctypes.byref(h)))
+        self._h = h
+        self.shapes = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().lbm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add(self, **cfg) -> int:
+        c = default_config(**cfg)
+        slot = ctypes.c_int32()
+        _bcheck(lib().lbm_batch_add(self._h, ctypes.byref(c), ctypes.byref(slot)), self._h)
+        q = 3 if c.lattice == D1Q3 else 9
+        self.shapes[slot.value] = (q, c.ny, c.nx)
+        return slot.value
+
+    def remove(self, slot: int):
+        _bcheck(lib().lbm_batch_remove(self._h, slot), self._h)
+        self.shapes.pop(slot, None)
+
+    def size(self) -> int:
+        return lib().lbm_batch_size(self._h)
+
+    def device_bytes(self) -> int:
+        return lib().lbm_batch_device_bytes(self._h)
+
+    def init(self, slot: int, rho, ux, uy=None):
+        q, ny, nx = self.shapes[slot]
+        p1, k1 = _ptr(rho, nx * ny, False)
+        p2, k2 = _ptr(ux, nx * ny, False)
+        p3, k3 = _ptr(uy, nx * ny, False)
+        _bcheck(lib().lbm_batch_init(self._h, slot, p1, p2, p3), self._h)
+
+    def set_populations(self, slot: int, f):
+        q, ny, nx = self.shapes[slot]
+        p, k = _ptr(f, q * ny * nx, False)
+        _bcheck(lib().lbm_batch_set_populations(self._h, slot, p), self._h)
+
+    def get_populations(self, slot: int, out=None):
+        q, ny, nx = self.shapes[slot]
+        if out is None:
+            out = np.empty((q, ny, nx))
+        p, k = _ptr(out, q * ny * nx, True)
+        _bcheck(lib().lbm_batch_get_populations(self._h, slot, p), self._h)
+        return out
+
+    def moments(self, slot: int, out=None):
+        q, ny, nx = self.shapes[slot]
+        if out is None:
+            out = tuple(np.empty((ny, nx)) for _ in range(3))
+        ptrs = [_ptr(a, nx * ny, True) for a in out]
+        _bcheck(lib().lbm_batch_moments(self._h, slot, ptrs[0][0], ptrs[1][0], ptrs[2][0]), self._h)
+        return out
+
+    def stats(self, slot: int) -> dict:
+        st = StepStats()
+        _bcheck(lib().lbm_batch_stats(self._h, slot, ctypes.byref(st)), self._h)
+        return st.as_dict()
+
+    def limited_sites(self, slot: int, cap: int = 4096) -> np.ndarray:
+        out = np.zeros(max(1, cap), dtype=np.int64)
+        n = ctypes.c_int64()
+        _bcheck(lib().lbm_batch_limited_sites(self._h, slot, out.ctypes.data, cap, ctypes.byref(n)), self._h)
+        return out[:min(n.value, cap)].copy()
+
+    def step(self, nsteps: int = 1):
+        _bcheck(lib().lbm_batch_step(self._h, int(nsteps)), self._h)
+
+    def synchronize(self):
+        _bcheck(lib().lbm_batch_synchronize(self._h), self._h)
+
+    def lattice_status(self, slot: int) -> int:
+        """Status of one lattice as collected by the last synchronize (OK = 0)."""
+        st = lib().lbm_batch_lattice_status(self._h, int(slot))
+        if st == ERR_INVALID_ARG:
+            raise LBMError(st, "no lattice in that slot")
+        return st
+
+    def set_graph(self, steps_per_graph: int):
+        _bcheck(lib().lbm_batch_set_graph(self._h, int(steps_per_graph)), self._h)
+
+    def set_shape(self, block_width: int = 0, waves: int = 2):
+        """Fused kernel shape: widest strip (multiple of 8 up to 240; 0: automatic), 1 / 2 / 4 waves."""
+        _bcheck(lib().lbm_batch_set_shape(self._h, int(block_width), int(waves)), self._h)
+
+    def tune(self, trial_steps: int = 5) -> float:
+        ms = ctypes.c_double()
+        _bcheck(lib().lbm_batch_tune(self._h, int(trial_steps), ctypes.byref(ms)), self._h)
+        return ms.value
+
+    def launch_count(self) -> int:
+        return lib().lbm_batch_launch_count(self._h)

@@ -189,9 +189,9 @@ def test_fp32_one_step_against_oracle(nx, ny, kernel):
 
 
 def test_fused_and_tiled_fp32_agree_over_many_steps():
-    """Two independent FP32 kernels of the same step stay within FP32 noise of
-    each other over 300 steps of a developing cavity (several strips and row
-    segments, ragged edges)."""
+    """The two FP32 kernels evaluate every site with the same FP32 operations
+    (tiles vs row-streaming strips, several strips and row segments, ragged
+    edges): 300 steps of a developing cavity agree bit for bit."""
     nx, ny = 517, 389
     base = dict(lattice=lbm.D2Q9, nx=nx, ny=ny, boundary=lbm.BC_WALLS, beta=0.9, u_lid=0.1,
                 precision=lbm.FP32, limiters=ALL, delta_median=1e-5, delta_ehrenfest=1e-4,
@@ -202,12 +202,11 @@ def test_fused_and_tiled_fp32_agree_over_many_steps():
     for g in (a, b):
         g.init(rho, ux, uy)
         g.step(300)
-    ra, ua, va = a.moments()
-    rb, ub, vb = b.moments()
-    assert np.abs(ra - rb).max() < 2e-6
-    assert np.abs(ua - ub).max() < 2e-6 and np.abs(va - vb).max() < 2e-6
+    np.testing.assert_array_equal(a.get_populations(), b.get_populations())
     sa, sb = a.stats(), b.stats()
     assert abs(sa["mass"] - sb["mass"]) < 1e-9 * sa["mass"]
+    for key in ("n_pos", "n_med", "n_ehr", "n_cand", "n_bad"):
+        assert sa[key] == sb[key], key
     assert sa["n_ehr"] > 0 and sb["n_med"] > 0
 
 

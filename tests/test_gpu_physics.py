@@ -1,0 +1,103 @@
+"""Long-run physics of the limited step against the paper's cavity table.
+
+The 100 x 100 lid-driven cavity at Re = 2000 (lid 0.1, polynomial f*, median
+filter delta = 1e-3) is run to steady state on the GPU (FP32).  The stream
+function is obtained from the velocity by Simpson's rule (Sec. 4.4.1) and the
+vortex centres (extrema of the stream function) are compared with Table vort
+(tests/golden/table_vort_polynomial.txt; all rows agree at Re = 2000) within
+one cell.  Mass must be conserved over the whole run.
+
+FP32, BF16 and FP16 storage must all place the centres within one cell.
+
+Coordinates: here the walls lie half a link outside the lattice, so node i sits
+at (i + 1/2)/N; the paper's nodes sit at i/(N-1).  The two differ by at most
+half a cell, inside the one-cell tolerance.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_0704_0043_gb300 import inputs, lbm
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "table_vort_polynomial.txt")
+
+
+def table(re, row):
+    for line in open(GOLDEN):
+        if line.startswith("#") or not line.strip():
+            continue
+        parts = line.split()
+        if int(parts[0]) == re and parts[1] == row:
+            v = [float(x) for x in parts[2:]]
+            return {"primary": v[0:2], "lower_left": v[2:4], "lower_right": v[4:6], "top_left": v[6:8]}
+    raise KeyError((re, row))
+
+
+def stream_function(ux, n):
+    """psi(x, y) = integral of u_x dy from the bottom wall (psi = 0 there), by
+    Simpson's rule on the half-cell-shifted grid (wall at y = 0, nodes at (j+1/2)/n)."""
+    h = 1.0 / n
+    psi = np.zeros_like(ux)
+    # first node: trapezoid from the wall (u = 0) to y = h/2
+    psi[0] = 0.5 * (0.0 + ux[0]) * (0.5 * h)
+    for j in range(1, n):
+        if j >= 2:
+            # Simpson over [y_{j-2}, y_j]
+            psi[j] = psi[j - 2] + (h / 3.0) * (ux[j - 2] + 4 * ux[j - 1] + ux[j])
+        else:
+            psi[j] = psi[j - 1] + 0.5 * h * (ux[j - 1] + ux[j])
+    return psi
+
+
+def extremum(psi, xs, ys, region, sign):
+    (x0, x1), (y0, y1) = region
+    mask = (xs >= x0) & (xs <= x1) & (ys >= y0) & (ys <= y1)
+    vals = np.where(mask, sign * psi, -np.inf)
+    j, i = np.unravel_index(np.argmax(vals), psi.shape)
+    return xs[j, i], ys[j, i]
+
+
+# Mass: FP32 keeps it to rounding (nonequilibrium-form collision); 16-bit
+# storage rounds every stored deviation, a random walk of about 2^-9 (BF16)
+# or 2^-12 (FP16) of |g| per site and step.
+MASS_RTOL = {lbm.FP32: 1e-6, lbm.BF16: 2e-3, lbm.FP16: 3e-4}
+
+
+@pytest.mark.parametrize("precision", [lbm.FP32, lbm.BF16, lbm.FP16])
+def test_cavity_re2000_vortex_centres_and_mass(precision):
+    n, re, u0 = 100, 2000.0, 0.1
+    beta = inputs.beta_from_nu(inputs.cavity_nu(n, u0, re))
+    g = lbm.Lattice(lattice=lbm.D2Q9, nx=n, ny=n, boundary=lbm.BC_WALLS, precision=precision, beta=beta,
+                    u_lid=u0, rho_wall=1.0, limiters=lbm.LIM_MEDIAN, delta_median=1e-3)
+    g.init(*inputs.cavity_rest(n, n))
+    m0 = float(n * n)  # uniform rest state, rho0 = 1
+    psi_max_prev = None
+    for block in range(15):
+        g.step(10000)
+        rho, ux, uy = g.moments()
+        psi = stream_function(ux, n)
+        psi_max = np.abs(psi).max()
+        # steady state (Sec. 4.4.1): the stream-function maximum changes by less
+        # than 1e-5 (in units of L u0) over 10000 steps
+        if psi_max_prev is not None and abs(psi_max - psi_max_prev) / u0 < 1e-5:
+            break
+        psi_max_prev = psi_max
+    st = g.stats()
+    print("precision", precision, "steps", st["step"], "mass drift", st["mass"] - m0)
+    assert st["n_bad"] == 0
+    assert abs(st["mass"] - m0) < MASS_RTOL[precision] * m0
+    ii, jj = np.meshgrid(np.arange(n), np.arange(n))
+    xs, ys = (ii + 0.5) / n, (jj + 0.5) / n
+    want = table(2000, "b")
+    sign = -np.sign(psi[n // 2, n // 2])  # primary vortex: extremum of psi
+    found = {
+        "primary": extremum(psi, xs, ys, ((0.2, 0.8), (0.2, 0.8)), -sign),
+        "lower_left": extremum(psi, xs, ys, ((0.0, 0.3), (0.0, 0.3)), sign),
+        "lower_right": extremum(psi, xs, ys, ((0.6, 1.0), (0.0, 0.4)), sign),
+    }
+    cell = 1.0 / n
+    for name, (x, y) in found.items():
+        wx, wy = want[name]
+        assert abs(x - wx) <= cell + 0.5 * cell and abs(y - wy) <= cell + 0.5 * cell, (name, (x, y), (wx, wy))
