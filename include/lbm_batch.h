@@ -77,20 +77,19 @@ lbm_status lbm_batch_lattice_status(const lbm_batch *b, int32_t slot);
  * off) are captured once after the batch changes and replayed. */
 lbm_status lbm_batch_set_graph(lbm_batch *b, int32_t steps_per_graph);
 
-/* Tile-shape autotuner: times `trial_steps` batched steps for each candidate
- * (strips chosen per lattice or at most 120 columns wide; 1, 2 or 4 waves of
- * blocks over the SMs),
+/* Work-split autotuner: times `trial_steps` batched steps for each candidate
+ * (segments chosen per lattice or 64 rows; 1, 2 or 4 waves of work items),
  * keeps the fastest, and restores every lattice's state, counters and stats
  * to what they were before.  *best_ms receives the winning time per step
  * (may be NULL). */
 lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_steps, double *best_ms);
 
-/* Fixes the fused kernel's shape: block_width = widest column strip of a
- * block (a multiple of 8 up to 240; 0: chosen per lattice), waves 1, 2 or 4
- * (blocks per lattice in proportion to its sites, 2 blocks per SM per wave).
- * The shape changes the speed only, never a result.
+/* Fixes the fused kernel's work split: seg_rows = rows per work item (a warp
+ * walking a strip of 30 columns; 0: chosen per lattice, else >= 16), waves 1,
+ * 2 or 4 (work items per lattice in proportion to its sites, one wave = the
+ * GPU's resident warps).  The split changes the speed only, never a result.
  * Errors: LBM_ERR_INVALID_ARG. */
-lbm_status lbm_batch_set_shape(lbm_batch *b, int32_t block_width, int32_t waves);
+lbm_status lbm_batch_set_shape(lbm_batch *b, int32_t seg_rows, int32_t waves);
 
 /* Kernel launches enqueued by lbm_batch_step so far (graph replays count
  * their captured launches). */

@@ -42,8 +42,8 @@ struct lbm_batch {
     int2 *fmap = nullptr, *t3map = nullptr, *t9map = nullptr;
     int fblocks = 0, t3blocks = 0, t9blocks = 0, n9 = 0, n3 = 0;
     // shape
-    int max_width = 0;  // widest fused strip in columns; 0 = automatic (up to 240)
-    int waves = 2;      // fused block budget, in waves of 2 blocks per SM
+    int seg_rows = 0;  // rows per fused work item; 0 = automatic
+    int waves = 1;     // fused work-item budget, in waves of resident warps
     // graph replay
     int graph_steps = 0;
     cudaGraphExec_t exec = nullptr;
@@ -146,7 +146,7 @@ lbm_status rebuild(lbm_batch *b)
                 const long long sites = (long long)c->cfg.nx * c->cfg.ny;
                 const int slots = std::max(1, (int)std::lround(budget * (double)sites / (double)fused_sites));
                 FusedArgs A;
-                const int blocks = fused_make_args(p, src, dst, b->max_width, slots, &A);
+                const int blocks = fused_make_args(p, src, dst, b->seg_rows, slots, &A);
                 b->h_fused[k].push_back(A);
                 FinalArgs F{ctx_final_params(c, 1, lim, blocks), dst};
                 F.p.src = src;
@@ -475,14 +475,13 @@ lbm_status lbm_batch_set_graph(lbm_batch *b, int32_t steps_per_graph)
     return LBM_OK;
 }
 
-lbm_status lbm_batch_set_shape(lbm_batch *b, int32_t block_width, int32_t waves)
+lbm_status lbm_batch_set_shape(lbm_batch *b, int32_t seg_rows, int32_t waves)
 {
     if (!b) return LBM_ERR_INVALID_ARG;
-    if (block_width != 0 && (block_width < 8 || block_width > 240 || (block_width & 7)))
-        return bfail(b, LBM_ERR_INVALID_ARG, "block_width must be 0 or a multiple of 8 in [8, 240]");
+    if (seg_rows != 0 && seg_rows < 16) return bfail(b, LBM_ERR_INVALID_ARG, "seg_rows must be 0 or >= 16");
     if (waves != 1 && waves != 2 && waves != 4) return bfail(b, LBM_ERR_INVALID_ARG, "waves must be 1, 2 or 4");
     invalidate(b);
-    b->max_width = block_width;
+    b->seg_rows = seg_rows;
     b->waves = waves;
     return LBM_OK;
 }
@@ -515,15 +514,15 @@ lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_steps, double *best_ms)
         BCK(b, cudaMemcpyAsync(m + c->field_bytes + ring + 32, c->counts, 2 * sizeof(int), cudaMemcpyDeviceToDevice, b->run));
         snaps.push_back({c, c->cur, mem});
     }
-    const int Ts[2] = {0, 120};
+    const int Ts[2] = {0, 64};
     const int Ws[3] = {1, 2, 4};
     double best = 1e300;
-    int bestT = 0, bestW = 2;
+    int bestT = 0, bestW = 1;
     lbm_status rs = LBM_OK;
     for (int T : Ts) {
         for (int W : Ws) {
             invalidate(b);
-            b->max_width = T;
+            b->seg_rows = T;
             b->waves = W;
             const int gs = b->graph_steps;
             b->graph_steps = 0;
@@ -565,7 +564,7 @@ lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_steps, double *best_ms)
     b->dirty = true;  // tables for the restored buffers
     b->phase = 0;
     drop_graph(b);
-    b->max_width = bestT;
+    b->seg_rows = bestT;
     b->waves = bestW;
     if (rs != LBM_OK) return rs;
     if (best_ms) *best_ms = best;

@@ -8,6 +8,12 @@
 // largest (dS, -site) pair by radix selection: eight 8-bit digit passes over the
 // 64-bit pattern of dS (positive doubles order like their bit patterns), then
 // four passes over the site index among the candidates tied at the threshold.
+//
+// The kernel is one block and sits between two step launches, so it is built
+// for latency: up to kCap candidates are kept in shared memory, the FP64 key
+// of a recorded site is evaluated by one warp with a lane per direction (the
+// operations and their order are those of key_dS9, so the key is the same
+// bit for bit), and block sums use warp shuffles.
 #include <type_traits>
 
 #include "internal.h"
@@ -17,7 +23,9 @@ namespace lbm {
 namespace {
 
 constexpr int kFinThreads = 512;
-constexpr int kSortCap = 4096;  // selected sets up to this size are sorted by site in shared memory
+constexpr int kFinWarps = kFinThreads / 32;
+constexpr int kCap = 2048;  // candidates held (and selected sets sorted) in shared memory
+constexpr unsigned kFull = 0xffffffffu;
 
 __device__ __forceinline__ unsigned long long key_bits(double d) { return (unsigned long long)__double_as_longlong(d); }
 
@@ -26,28 +34,67 @@ __device__ __forceinline__ long long fidx(long long plane, int pitch, int k, int
     return (long long)k * plane + (long long)y * pitch + kLead + x;
 }
 
-// Free flight into site (x, y) of a D2Q9 cavity / channel / periodic lattice,
-// evaluated in FP64 from FP32 storage exactly as the FP64 path evaluates it.
+// Population k arriving at site (x, y) of a D2Q9 cavity / channel / periodic
+// lattice, in FP64 from FP32 / 16-bit storage: (double) g + rho_ref W, the
+// value the FP64 path computes from the same stored state.
 template <typename S>
-__device__ void pull_d2q9_f64(const FinalParams &p, int x, int y, double fin[9])
+__device__ double pull_one_f64(const FinalParams &p, int x, int y, int k)
 {
     const S *src = (const S *)p.src;
     const bool wrapx = p.boundary != 0, wrapy = p.boundary == 1;
+    int sx = x - Lat<9>::cx(k), sy = y - Lat<9>::cy(k);
+    if (wrapx) sx = sx < 0 ? sx + p.nx : (sx >= p.nx ? sx - p.nx : sx);
+    if (wrapy) sy = sy < 0 ? sy + p.ny : (sy >= p.ny ? sy - p.ny : sy);
+    if (sx >= 0 && sx < p.nx && sy >= 0 && sy < p.ny)
+        return Ar<double>::add((double)s2f(src[fidx(p.plane, p.pitch, k, sy, sx)]), p.rw[k]);
+    const int q = Lat<9>::opp(k);
+    double v = Ar<double>::add((double)s2f(src[fidx(p.plane, p.pitch, q, y, x)]), p.rw[q]);
+    if (sy > p.ny - 1) v = Ar<double>::add(v, p.lid[k]);
+    return v;
+}
+
+// FP64 Ehrenfests' key dS(f') of `site` evaluated by a whole warp: lane k < 9
+// pulls population k and evaluates f*_k and its dS term; the moments and the
+// final sum run in k order exactly as key_dS9 runs them.  Every lane returns
+// the same key; false for a site that cannot be limited.
+template <typename S>
+__device__ bool key_dS9_warp(const FinalParams &p, int site, double &key)
+{
+    using A = Ar<double>;
+    const int lane = threadIdx.x & 31, k = lane < 9 ? lane : 0;
+    const int x = site % p.nx, y = site / p.nx;
+    const double mine = pull_one_f64<S>(p, x, y, k);
+    double fin[9];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        int sx = x - Lat<9>::cx(k), sy = y - Lat<9>::cy(k);
-        if (wrapx) sx = sx < 0 ? sx + p.nx : (sx >= p.nx ? sx - p.nx : sx);
-        if (wrapy) sy = sy < 0 ? sy + p.ny : (sy >= p.ny ? sy - p.ny : sy);
-        // FP32 / BF16 / FP16 storage holds g = f - rho_ref W; the absolute value is (double) g + rw
-        if (sx >= 0 && sx < p.nx && sy >= 0 && sy < p.ny) {
-            fin[k] = Ar<double>::add((double)s2f(src[fidx(p.plane, p.pitch, k, sy, sx)]), p.rw[k]);
-        } else {
-            const int q = Lat<9>::opp(k);
-            double v = Ar<double>::add((double)s2f(src[fidx(p.plane, p.pitch, q, y, x)]), p.rw[q]);
-            if (sy > p.ny - 1) v = Ar<double>::add(v, p.lid[k]);
-            fin[k] = v;
-        }
-    }
+    for (int j = 0; j < 9; ++j) fin[j] = __shfl_sync(kFull, mine, j);
+    double rho, ux, uy;
+    moments9<double>(fin, rho, ux, uy);
+    // f*_k as in feq9<double>
+    const double usq = A::add(A::mul(ux, ux), A::mul(uy, uy));
+    const double tail = A::mul(A::mul(3.0, usq), 0.5);
+    const double c = k == 0 ? 0.0
+                   : k == 1 ? ux
+                   : k == 2 ? uy
+                   : k == 3 ? -ux
+                   : k == 4 ? -uy
+                   : k == 5 ? A::add(ux, uy)
+                   : k == 6 ? A::sub(uy, ux)
+                   : k == 7 ? -A::add(ux, uy)
+                            : A::sub(ux, uy);
+    double poly = A::add(A::add(1.0, A::mul(3.0, c)), A::mul(A::mul(9.0, A::mul(c, c)), 0.5));
+    poly = A::sub(poly, tail);
+    const double fs = A::mul(A::mul(rho, Lat<9>::w(k)), poly);
+    // collision and the dS term as in key_dS9
+    const double fp = A::add(fs, A::mul(p.a, A::sub(fs, mine)));
+    const double d = A::sub(fp, fs);
+    const double term = A::div(A::mul(d, d), fs);
+    const bool bad_k = lane < 9 && (!(fs > 0.0) || !isfinite(mine));
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < 9; ++j) s = A::add(s, __shfl_sync(kFull, term, j));
+    const bool bad = __any_sync(kFull, bad_k) || !(rho > 0.0) || !isfinite(rho) || !isfinite(ux) || !isfinite(uy);
+    key = s;
+    return !bad && isfinite(s);
 }
 
 // The pass's input at site (x, y) in FP32: after free flight (collide) with the
@@ -77,17 +124,17 @@ __device__ void pull_dev(const FinalParams &p, int x, int y, float g[Q])
     }
 }
 
-// Sum of v over the block in a fixed order (same result every run).
+// Sum over the block in a fixed order: warp shuffles, then warp totals in
+// warp order (same result every run).  Every thread gets the sum.
 __device__ double block_sum(double v, double *red)
 {
-    const int t = threadIdx.x;
-    red[t] = v;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+    if (lane == 0) red[warp] = v;
     __syncthreads();
-    for (int s = kFinThreads / 2; s > 0; s >>= 1) {
-        if (t < s) red[t] += red[t + s];
-        __syncthreads();
-    }
-    const double r = red[0];
+    double r = 0.0;
+    for (int w = 0; w < kFinWarps; ++w) r += red[w];
     __syncthreads();
     return r;
 }
@@ -107,53 +154,84 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, 
     }
     const FinalParams &p = BATCHED ? sA.p : p0;
     S *__restrict__ f = BATCHED ? (S *)sA.f : f0;
-    __shared__ double red[kFinThreads];
+    __shared__ double red[kFinWarps];
     __shared__ double tot[P_NSTAT];
+    __shared__ double s_key[kCap];
+    __shared__ int s_site[kCap];
+    __shared__ int s_idx[kCap];
     __shared__ unsigned hist[256];
     __shared__ unsigned long long s_prefix;
-    __shared__ long long s_rem;
-    __shared__ int s_nsel;
-    __shared__ int s_site[kSortCap];
-    __shared__ int s_idx[kSortCap];
-    const int t = threadIdx.x;
+    __shared__ long long s_rem, s_step, s_rec;
+    __shared__ int s_n, s_nsel, s_valid;
+    __shared__ unsigned s_status;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
 
-    __shared__ int s_valid;
-    // block partials: warp w reduces statistic w over the rows, in a fixed order
-    {
-        const int warp = t >> 5, lane = t & 31;
-        if (warp < P_NSTAT) {
-            double v = 0.0;
-            for (int r = lane; r < p.nblocks; r += 32) v += p.partials[(long long)r * P_NSTAT + warp];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            if (lane == 0) tot[warp] = v;
-        }
-    }
-    const int nrec = p.ehrenfest ? *p.cand_count : 0;
-    const int n = nrec < p.cand_cap ? nrec : p.cand_cap;
-    const long long k = p.k_max;
     if (t == 0) {
+        const int nrec = p.ehrenfest ? *p.cand_count : 0;
+        s_n = nrec < p.cand_cap ? nrec : p.cand_cap;
+        s_step = p.counters[0];
+        s_rec = p.counters[1];
+        s_status = *p.status;
         s_nsel = 0;
         s_valid = 0;
     }
-    if constexpr (!std::is_same<S, double>::value) {
-        if (Q == 9 && p.recompute) {
-            // FP64 key of each recorded site from the pre-step populations; sites at
-            // or below the threshold drop out (key -1)
-            for (int i = t; i < n; i += kFinThreads) {
+    // block partials: warp w reduces statistic w over the rows, in a fixed order
+    if (warp < P_NSTAT) {
+        double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+        int r = lane;
+        for (; r + 96 < p.nblocks; r += 128) {
+            v0 += p.partials[(long long)r * P_NSTAT + warp];
+            v1 += p.partials[(long long)(r + 32) * P_NSTAT + warp];
+            v2 += p.partials[(long long)(r + 64) * P_NSTAT + warp];
+            v3 += p.partials[(long long)(r + 96) * P_NSTAT + warp];
+        }
+        for (; r < p.nblocks; r += 32) v0 += p.partials[(long long)r * P_NSTAT + warp];
+        double v = (v0 + v1) + (v2 + v3);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+        if (lane == 0) tot[warp] = v;
+    }
+    __syncthreads();
+    const int n = s_n;
+    const bool small = n <= kCap;  // candidates held in shared memory
+    const long long k = p.k_max;
+    constexpr bool kLowPrec = !std::is_same<S, double>::value;
+
+    // candidate keys: FP64 dS(f') (recomputed from the pre-step populations for
+    // the fused kernel's records; sites at or below the threshold drop out)
+    const bool recompute = kLowPrec && Q == 9 && p.recompute;
+    if (recompute) {
+        if constexpr (kLowPrec) {
+            for (int i = warp; i < n; i += kFinWarps) {
                 const int site = p.cand[i].site;
-                double g[9], d64;
-                pull_d2q9_f64<S>(p, site % p.nx, site / p.nx, g);
-                const bool ok = key_dS9(g, p.a, d64);
-                p.cand[i].key = (ok && d64 > p.delta_e) ? d64 : -1.0;
+                double d64;
+                const bool ok = key_dS9_warp<S>(p, site, d64);
+                const double key = (ok && d64 > p.delta_e) ? d64 : -1.0;
+                if (lane == 0) {
+                    if (small) {
+                        s_key[i] = key;
+                        s_site[i] = site;
+                    }
+                    p.cand[i].key = key;
+                }
             }
+        }
+    } else if (small) {
+        for (int i = t; i < n; i += kFinThreads) {
+            const Cand c = p.cand[i];
+            s_key[i] = c.key;
+            s_site[i] = c.site;
         }
     }
     __syncthreads();
+    auto key_of = [&](int i) -> double { return small ? s_key[i] : p.cand[i].key; };
+    auto site_of = [&](int i) -> int { return small ? s_site[i] : p.cand[i].site; };
     {
         int nv = 0;
-        for (int i = t; i < n; i += kFinThreads) nv += p.cand[i].key > p.delta_e;
-        if (nv) atomicAdd(&s_valid, nv);
+        for (int i = t; i < n; i += kFinThreads) nv += key_of(i) > p.delta_e;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) nv += __shfl_down_sync(kFull, nv, o);
+        if (lane == 0 && nv) atomicAdd(&s_valid, nv);
     }
     __syncthreads();
     const int n_valid = s_valid;
@@ -161,7 +239,7 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, 
     if (p.ehrenfest && k > 0 && n_valid > 0) {
         unsigned long long kv = 0;  // threshold dS pattern
         int site_thr = 0x7fffffff;
-        bool take_all = (long long)n_valid <= k;
+        const bool take_all = (long long)n_valid <= k;
         if (!take_all) {
             unsigned long long prefix = 0, mask = 0;
             long long rem = k;
@@ -169,7 +247,7 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, 
                 for (int d = t; d < 256; d += kFinThreads) hist[d] = 0;
                 __syncthreads();
                 for (int i = t; i < n; i += kFinThreads) {
-                    const double key = p.cand[i].key;
+                    const double key = key_of(i);
                     const unsigned long long u = key_bits(key);
                     if (key > p.delta_e && (u & mask) == prefix) atomicAdd(&hist[(u >> shift) & 255u], 1u);
                 }
@@ -198,9 +276,9 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, 
                 for (int d = t; d < 256; d += kFinThreads) hist[d] = 0;
                 __syncthreads();
                 for (int i = t; i < n; i += kFinThreads) {
-                    const Cand c = p.cand[i];
-                    const unsigned s = (unsigned)c.site;
-                    if (c.key > p.delta_e && key_bits(c.key) == kv && (s & smask) == sprefix)
+                    const double key = key_of(i);
+                    const unsigned s = (unsigned)site_of(i);
+                    if (key > p.delta_e && key_bits(key) == kv && (s & smask) == sprefix)
                         atomicAdd(&hist[(s >> shift) & 255u], 1u);
                 }
                 __syncthreads();
@@ -223,11 +301,11 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, 
             }
             site_thr = (int)sprefix;
         }
-        // compaction of the chosen candidates (indices into p.cand)
+        // compaction of the chosen candidates (indices into the candidate list)
         for (int i = t; i < n; i += kFinThreads) {
-            const Cand c = p.cand[i];
-            const unsigned long long u = key_bits(c.key);
-            const bool chosen = c.key > p.delta_e && (take_all || u > kv || (u == kv && c.site <= site_thr));
+            const double key = key_of(i);
+            const unsigned long long u = key_bits(key);
+            const bool chosen = key > p.delta_e && (take_all || u > kv || (u == kv && site_of(i) <= site_thr));
             if (chosen) {
                 const int j = atomicAdd(&s_nsel, 1);
                 if (j < p.sel_cap) p.sel[j] = i;
@@ -237,15 +315,19 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, 
         if (t == 0 && s_nsel > p.sel_cap) s_nsel = p.sel_cap;
         __syncthreads();
         const int nsel = s_nsel;
-        const bool sorted = nsel <= kSortCap;
+        const bool sorted = nsel <= kCap;
         if (sorted) {
-            // bitonic sort of the chosen set by site index (padding sorts last)
+            // bitonic sort of the chosen set by site index (padding sorts last);
+            // the candidate arrays are no longer read, so they hold the sort keys
             int m = 1;
             while (m < nsel) m <<= 1;
             for (int i = t; i < m; i += kFinThreads) {
-                s_idx[i] = i < nsel ? p.sel[i] : -1;
-                s_site[i] = i < nsel ? p.cand[p.sel[i]].site : 0x7fffffff;
+                const int ci = i < nsel ? p.sel[i] : -1;
+                s_idx[i] = ci;
+                s_key[i] = (double)(ci >= 0 ? p.cand[ci].site : 0x7fffffff);
             }
+            __syncthreads();
+            for (int i = t; i < m; i += kFinThreads) s_site[i] = (int)s_key[i];
             __syncthreads();
             for (int size = 2; size <= m; size <<= 1) {
                 for (int stride = size >> 1; stride > 0; stride >>= 1) {
@@ -270,14 +352,13 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, 
             const int x = c.site % p.nx, y = c.site / p.nx;
             T g[Q], fs[Q], rho, ux, uy;
             if constexpr (std::is_same<T, float>::value) {
-                // FP32 / 16-bit storage: f*(m) in deviation form, m taken from the
-                // pass's input (the collision conserves m), so f* is the very
-                // equilibrium of the step kernel, rounded to storage once
+                // FP32 / 16-bit storage: f*(m) as g - n (the limiter with phi = 0),
+                // m taken from the pass's input (the collision conserves m), so
+                // mass and momentum are kept and the result is rounded once
                 float drho, nq[Q];
                 pull_dev<Q, S>(p, x, y, g);
                 moments_dev<Q>(g, p.rho_ref, drho, rho, ux, uy);
                 feq_dev<Q>(drho, rho, ux, uy, fs);
-                // f* as g - n (the limiter with phi = 0): mass and momentum kept
                 neq_dev<Q>(g, fs, nq);
 #pragma unroll
                 for (int q = 0; q < Q; ++q) fs[q] = g[q] - nq[q];
@@ -297,18 +378,18 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, 
         if (sorted) {
             for (int r = t; r < nsel; r += kFinThreads) p.sel[r] = s_site[r];
         } else {
-            // unsorted (more than kSortCap chosen): convert in place, one owner per slot
+            // unsorted (more than kCap chosen): convert in place, one owner per slot
             for (int r = t; r < nsel; r += kFinThreads) p.sel[r] = p.cand[p.sel[r]].site;
         }
     }
     const double esum = block_sum(ehr_sum, red);
     if (t == 0) {
-        long long step = p.counters[0];
+        long long step = s_step;
         if (p.collide) {
             step += 1;
             p.counters[0] = step;
         }
-        const long long rec = p.counters[1];
+        const long long rec = s_rec;
         p.counters[1] = rec + 1;
         DevStats st;
         st.step = step;
@@ -321,7 +402,8 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, 
         st.n_ehr = s_nsel;
         st.n_cand = n_valid;
         st.n_bad = (long long)tot[P_NBAD];
-        const unsigned sb = *p.status;
+        // the step kernel set its status bits before this launch began
+        const unsigned sb = s_status;
         st.status = (sb & kStatNonfinite) ? 4 : ((sb & kStatTimeout) ? 5 : 0);
         st.reserved = 0;
         p.stats_ring[rec % p.ring_len] = st;

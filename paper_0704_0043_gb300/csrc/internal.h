@@ -107,8 +107,7 @@ struct FusedArgs {
     StepParams p;
     const void *src;  // float, __nv_bfloat16 or __half deviations
     void *dst;
-    int strips, seg_rows, blocks;
-    int sw;  // finished columns per strip (a multiple of 8)
+    int strips, seg_rows, items, blocks;  // work items (warps): strips of 30 columns x row segments
     float a, b2, delta_m, thr_e, rho_ref;  // b2 = 2 beta
     float lid4, lid7, lid8;  // FP32 moving-wall terms of the links through the lid (hi + lo)
     float lo4, lo7, lo8;
@@ -156,10 +155,10 @@ int set_thread_error_impl(int s, const char *msg);
 template <typename S>
 cudaError_t launch_fused_d2q9(const StepParams &p, const S *src, S *dst, int *nblocks, cudaStream_t s);
 int fused_d2q9_blocks(int nx, int ny);  // most blocks (partial-sum rows) any launch of the lattice uses
-int fused_slots();                      // resident blocks of one wave (2 per SM)
-// Fills the instance arguments: strip width at most `max_width` columns (0:
-// automatic), about `slots` blocks; returns the block count.
-int fused_make_args(const StepParams &p, const void *src, void *dst, int max_width, int slots, FusedArgs *out);
+int fused_slots();                      // resident work items (warps) of one wave
+// Fills the instance arguments: row segments of `seg_rows` rows (0: about
+// `slots` work items); returns the block count.
+int fused_make_args(const StepParams &p, const void *src, void *dst, int seg_rows, int slots, FusedArgs *out);
 // Batched launches: `blocks` blocks in total; block b runs instance map[b].x
 // with local block id map[b].y (tables in device memory).
 cudaError_t launch_fused_batched(const FusedArgs *table, const int2 *map, int blocks, cudaStream_t s);

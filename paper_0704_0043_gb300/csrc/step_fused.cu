@@ -1,41 +1,32 @@
-// step_fused.cu -- row-streaming fused D2Q9 step for the walled cavity.
+// step_fused.cu -- register-streaming fused D2Q9 step for the walled cavity.
 //
 // The same step as the tiled kernel (free flight with halfway bounce-back and
 // moving lid, Sec. 2 and Sec. 4.4.1; polynomial f*, Eq. polyeq2d; LBGK
 // collision, Eq. collLBGK; dS(f'), Sec. 3.6; positivity rule, Sec. 3.1; median
 // filter, Sec. 3.5; Ehrenfests' candidates, Sec. 3.2; FP64 sums, Sec. 3.4),
-// with the same per-site FP32 arithmetic, organised for HBM streaming with
-// warps that run independently of each other:
+// with the same per-site FP32 arithmetic, organised so that every warp streams
+// its own part of the lattice with no shared memory and no barrier:
 //
-//  * A block owns a strip of at most 240 columns (a multiple of 8) and walks a
-//    segment of rows upward.  It has eight compute warps, a load warp and a
-//    store warp.  Compute warp w covers 32 consecutive columns of which lanes
-//    1..30 finish their site; lanes 0 and 31 recompute the neighbouring
-//    warps' edge columns, so each warp holds the whole 3 x 3 dS stencil of its
-//    sites in registers (three rows per lane, the side columns by shuffles)
-//    and never waits for another compute warp.
-//  * Input: the load warp copies, per row, the strip's nine population rows
-//    (bulk asynchronous copies, cp.async.bulk, completion counted on a "full"
-//    mbarrier) into an 8-deep ring of shared-memory stages.  Stage s holds the
-//    rows the pull of row s reads: planes {0,1,3} of row s, {2,5,6} of row
-//    s-1, {4,7,8} of row s+1, so every stored population is read from DRAM
-//    once.  A compute warp releases stage s on its "empty" mbarrier after
-//    finishing row s+1 (the limiter recomputes that row's pull); the load
-//    warp refills a slot once every compute warp has released it.
-//  * Output: a compute warp writes the post-collision deviations of its sites
-//    into a 4-deep ring of shared-memory output rows, applies the limiters to
-//    row r-1 after computing row r (the median needs rows r-2..r), and marks
-//    the row done on an mbarrier; the store warp then writes the finished row
-//    to global memory with bulk asynchronous stores (one per plane).
+//  * Work item = one warp: a strip of 32 consecutive columns, of which lanes
+//    1..30 finish their site (lanes 0 and 31 recompute the neighbouring
+//    strips' edge columns), walked upward over a segment of rows.  Row r is
+//    computed, then row r-1 is finished: its 3 x 3 dS stencil is then in
+//    registers (three rows per lane, the side columns by warp shuffles).
+//  * Free flight reads the populations arriving at row r straight from the
+//    source field: planes {0,1,3} of row r, {2,5,6} of row r-1, {4,7,8} of
+//    row r+1, each a coalesced 32-lane load, so every stored population is
+//    read from DRAM once (strips overlap by two columns, segments by two
+//    rows).  The loads of row r+1 are issued before row r is computed, so a
+//    row of loads is always in flight behind the arithmetic.
+//  * The post-collision deviations are stored at once; a site whose phi
+//    (decided one row later) is below 1 reloads its row, recomputes the
+//    collision exactly and overwrites its populations with the limited ones.
 //  * Arithmetic is FP32 on the deviations g = f - rho_ref W in nonequilibrium
 //    form (lattice.cuh), stored as FP32, BF16 or FP16; no FP64 on the
 //    per-site path.  Sites whose FP32 dS is near or above the Ehrenfests'
 //    threshold are recorded; the tail kernel recomputes their FP64 key from
 //    the pre-step populations.  Sums are kept per thread in FP32 (mass as
-//    rho - rho_ref) and folded into FP64 every 32 rows.
-//  * Every mbarrier wait is bounded by a clock limit and watches a block-wide
-//    abort flag; on expiry the thread sets the timeout status bit and the
-//    flag, and every warp leaves its loop.
+//    rho - rho_ref), folded into FP64 every 128 rows, and reduced per block.
 #include <algorithm>
 #include <type_traits>
 
@@ -45,108 +36,16 @@
 namespace lbm {
 namespace {
 
-constexpr int kW = 8;                // compute warps per block
-constexpr int kThreads = 32 * (kW + 2);
-constexpr int kMaxWidth = 30 * kW;   // finished columns per strip (at most)
-constexpr int kLW = kMaxWidth + 16;  // staged columns per row (halo and 16-byte alignment)
-constexpr int kStages = 8;           // input ring
-constexpr int kOut = 4;              // output ring
-constexpr int kMinSegRows = 16;      // shortest row segment (the halo rows cost 2 / segment)
-constexpr long long kWaitLimit = 4000000000LL;  // clock cycles (about 2 s)
-
-template <typename S> struct FusedSmem {
-    S in[kStages][9][kLW];
-    S out[kOut][9][kMaxWidth];
-    unsigned long long full[kStages], empty[kStages], ofull[kOut], oempty[kOut];
-    int abort;
-};
+constexpr int kWarps = 4;  // independent work items per block
+constexpr int kThreads = 32 * kWarps;
+constexpr int kBlocksPerSM = 6;  // resident blocks per SM (3 for the batched kernel's larger state)
+constexpr int kFoldRows = 128;   // FP32 partial sums are folded into FP64 every kFoldRows rows
+constexpr int kMinSegRows = 16;  // shortest row segment (the two halo rows cost 2 / segment)
 
 struct RowState {
     float ds, pp;
     bool bad, cand;
 };
-
-__device__ __forceinline__ unsigned smem_addr(const void *ptr)
-{
-    return (unsigned)__cvta_generic_to_shared(ptr);
-}
-
-__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity)
-{
-    unsigned ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait for the phase with the given parity.  Gives up when another
-// thread of the block has set the abort flag, or after kWaitLimit cycles (then
-// it sets the flag and the timeout status bit itself).
-__device__ __noinline__ bool mbar_wait_slow(unsigned long long *bar, unsigned parity, volatile int *abort,
-                                            unsigned *status)
-{
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity)) {
-        if (*abort) return false;
-        if (clock64() - t0 > kWaitLimit) {
-            *abort = 1;
-            atomicOr(status, kStatTimeout);
-            return false;
-        }
-    }
-    return true;
-}
-
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, volatile int *abort,
-                                          unsigned *status)
-{
-    return mbar_try_wait(bar, parity) || mbar_wait_slow(bar, parity, abort, status);
-}
-
-// global -> shared bulk copy, completion counted on `bar`
-__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, unsigned long long *bar)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_addr(dst)),
-        "l"(src), "r"(bytes), "r"(smem_addr(bar))
-        : "memory");
-}
-
-// shared -> global bulk copy in the issuing thread's bulk-async group
-__device__ __forceinline__ void bulk_store(void *dst, const void *src, unsigned bytes)
-{
-    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_addr(src)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
-
-// orders this thread's generic-proxy shared-memory writes before later
-// async-proxy (bulk copy) reads of them
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 __device__ __forceinline__ double warp_sum_d(double v)
 {
@@ -170,14 +69,11 @@ __device__ __forceinline__ void sort3(float a, float b, float c, float &lo, floa
 // `table` as its block map[b].y; otherwise the single instance A0.
 // S: storage type of the deviations (float, __nv_bfloat16 or __half).
 template <typename S, bool MED, bool POS, bool BATCHED>
-__global__ void __launch_bounds__(kThreads, 2) k_fused(const FusedArgs A0, const FusedArgs *__restrict__ table,
-                                                       const int2 *__restrict__ map)
+__global__ void __launch_bounds__(kThreads, BATCHED ? 3 : kBlocksPerSM)
+    k_fused(const FusedArgs A0, const FusedArgs *__restrict__ table, const int2 *__restrict__ map)
 {
-    constexpr int E = 16 / (int)sizeof(S);  // elements per 16 bytes
     constexpr unsigned kFull = 0xffffffffu;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    FusedSmem<S> &sm = *reinterpret_cast<FusedSmem<S> *>(smem_raw);
-    __shared__ double red[kW + 2][P_NSTAT];
+    __shared__ double red[kWarps][P_NSTAT];
     __shared__ __align__(16) FusedArgs sA;
     int bid = (int)blockIdx.x;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
@@ -187,153 +83,73 @@ __global__ void __launch_bounds__(kThreads, 2) k_fused(const FusedArgs A0, const
         unsigned *to = reinterpret_cast<unsigned *>(&sA);
         for (int i = t; i < (int)(sizeof(FusedArgs) / 4); i += kThreads) to[i] = from[i];
         bid = m.y;
+        __syncthreads();
     }
-    // The output ring starts zeroed, and only lattice columns are written to
-    // it: the columns a row store carries past the lattice's right edge (up to
-    // the next 16 bytes) keep the row padding's zero fill.
-    {
-        unsigned *o = reinterpret_cast<unsigned *>(&sm.out[0][0][0]);
-        for (int i = t; i < (int)(sizeof(sm.out) / 4); i += kThreads) o[i] = 0u;
-    }
-    __syncthreads();
     const FusedArgs &A = BATCHED ? sA : A0;
     const StepParams &p = A.p;
-    const int nx = p.nx, ny = p.ny;
-    const int plane = (int)p.plane;  // 9 * plane < 2^31 is checked at launch
-    const int strip = bid % A.strips, seg = bid / A.strips;
-    const int c0 = strip * A.sw;           // first column of the strip (a multiple of 8)
-    const int width = min(A.sw, nx - c0);  // finished columns
-    const int nw = (width + 29) / 30;      // compute warps with work
-    const int ys = seg * A.seg_rows, ye = min(ys + A.seg_rows, ny);
-    const int r0 = max(ys - 1, 0);
-    const int rc = min(ye, ny - 1);  // last row whose dS this block computes
-    const int s_first = r0 - 1, s_last = rc + 1;
-    // staged columns [xs0, xs0 + Lc): 16-byte aligned, inside the padded row
-    const int xs0 = c0 - E;
-    const int Lc = min(kLW, ((nx + E - 1) & ~(E - 1)) + E - xs0);
-    volatile int *abort = &sm.abort;
-
-    if (t == 0) {
-        for (int i = 0; i < kStages; ++i) {
-            mbar_init(&sm.full[i], 1);
-            mbar_init(&sm.empty[i], (unsigned)nw);
-        }
-        for (int i = 0; i < kOut; ++i) {
-            mbar_init(&sm.ofull[i], (unsigned)nw);
-            mbar_init(&sm.oempty[i], 1);
-        }
-        sm.abort = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
 
     float s_mass = 0.f, s_ds = 0.f, s_in = 0.f, s_lim = 0.f;
     int n_pos = 0, n_med = 0, n_bad = 0, n_sites = 0, rows_acc = 0;
     double acc_mass = 0.0, acc_ds = 0.0, acc_in = 0.0, acc_lim = 0.0;
 
-    if (warp == kW) {
-        // ---- load warp: stage s into slot (s - s_first) mod kStages ----
+    const int item = bid * kWarps + warp;
+    if (item < A.items) {
         const S *__restrict__ src = (const S *)A.src;
-        const unsigned row_bytes = (unsigned)Lc * (unsigned)sizeof(S);
-        int issued = 0;
-        for (int s = s_first; s <= s_last; ++s) {
-            const unsigned j = (unsigned)(s - s_first), slot = j % kStages;
-            if (j >= kStages) {  // every compute warp released the slot's previous stage
-                bool ok = true;
-                if (lane == 0) ok = mbar_wait(&sm.empty[slot], (j / kStages - 1) & 1u, abort, p.status);
-                if (!__shfl_sync(kFull, (int)ok, 0)) break;
-            }
-            unsigned bytes = 0;
-            if (s >= 0 && s < ny) bytes += 3u * row_bytes;
-            if (s - 1 >= 0 && s - 1 < ny) bytes += 3u * row_bytes;
-            if (s + 1 >= 0 && s + 1 < ny) bytes += 3u * row_bytes;
-            if (lane == 0) mbar_expect_tx(&sm.full[slot], bytes);
-            __syncwarp();
-            if (lane < 9) {
-                const int k = lane;
-                const int row = (k == 0 || k == 1 || k == 3) ? s : ((k == 2 || k == 5 || k == 6) ? s - 1 : s + 1);
-                if (row >= 0 && row < ny)
-                    bulk_load(&sm.in[slot][k][0], src + (long long)k * plane + (long long)row * p.pitch + kLead + xs0,
-                              row_bytes, &sm.full[slot]);
-            }
-            ++issued;
-        }
-        // After an abort, wait (bounded) for the copies still in flight: the
-        // last kStages issued stages (earlier ones were waited for by the
-        // compute warps before their slots were released).
-        if (*abort && lane == 0) {
-            for (int s = s_first + max(0, issued - kStages); s < s_first + issued; ++s) {
-                const unsigned j = (unsigned)(s - s_first);
-                const long long t0 = clock64();
-                while (!mbar_try_wait(&sm.full[j % kStages], (j / kStages) & 1u) && clock64() - t0 < kWaitLimit) {
-                }
-            }
-        }
-    } else if (warp == kW + 1) {
-        // ---- store warp: finished row y from output slot (y - ys) mod kOut ----
         S *__restrict__ dst = (S *)A.dst;
-        const unsigned bytes = (unsigned)((width + E - 1) & ~(E - 1)) * (unsigned)sizeof(S);
-        for (int y = ys; y < ye; ++y) {
-            const unsigned j = (unsigned)(y - ys), slot = j % kOut;
-            bool ok = true;
-            if (lane == 0) ok = mbar_wait(&sm.ofull[slot], (j / kOut) & 1u, abort, p.status);
-            if (!__shfl_sync(kFull, (int)ok, 0)) break;
-            if (lane < 9) {
-                bulk_store(dst + (long long)lane * plane + (long long)y * p.pitch + kLead + c0, &sm.out[slot][lane][0],
-                           bytes);
-                bulk_commit();
-                bulk_wait_read_all();  // the slot may be refilled once its bytes are read
-            }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&sm.oempty[slot]);
-        }
-        if (lane < 9) bulk_wait_all();
-    } else if (warp < nw) {
-        // ---- compute warp ----
-        const int x = c0 - 1 + 30 * warp + lane;  // lattice column of this lane
-        const int o = x - xs0;                     // staged index of column x
-        const int ox = x - c0;                     // output-row index of column x
+        const int nx = p.nx, ny = p.ny, pitch = p.pitch;
+        const int plane = (int)p.plane;  // 9 * plane < 2^31 is checked at launch
+        const int strip = item % A.strips, seg = item / A.strips;
+        const int x = 30 * strip - 1 + lane;  // lattice column of this lane
+        const int ys = seg * A.seg_rows, ye = min(ys + A.seg_rows, ny);
+        const int r0 = max(ys - 1, 0);
+        const int rc = min(ye, ny - 1);  // last row whose dS this warp computes
         const bool xin = x >= 0 && x < nx;
-        const bool xown = xin && lane >= 1 && lane <= 30 && ox < width;
+        const bool xown = xin && lane >= 1 && lane <= 30;
         const bool xwall = x == 0 || x == nx - 1;
         const bool lim_ehr = (p.limiters & 2u) != 0;
         const bool med_on = MED && (p.limiters & 4u) != 0, pos_on = POS && (p.limiters & 1u) != 0;
         const float a = A.a, a2 = A.a * A.a, b2 = A.b2, rho_ref = p.rho_ref;
+        // element offsets, from (plane 0, row q, column x), of the population of
+        // plane k arriving at (x, q): source row q - cy_k, column x - cx_k
+        const int o1 = plane - 1, o3 = 3 * plane + 1;
+        const int o2 = 2 * plane - pitch, o5 = 5 * plane - pitch - 1, o6 = 6 * plane - pitch + 1;
+        const int o4 = 4 * plane + pitch, o7 = 7 * plane + pitch + 1, o8 = 8 * plane + pitch - 1;
+        // columns x - 1 and x + 1 stay inside the padded row (x >= -1, x <= nx + 29)
 
-        auto in_slot = [&](int s) { return (unsigned)(s - s_first) % kStages; };
-        auto wait_stage = [&](int s) -> bool {
-            if (s > s_last) return true;
-            const unsigned j = (unsigned)(s - s_first);
-            return mbar_wait(&sm.full[j % kStages], (j / kStages) & 1u, abort, p.status);
+        // Loads of the populations arriving at row q (rows outside the lattice
+        // are not read; their links are bounce-back links, set by edge_row).
+        auto load_row = [&](int q, float g[9]) {
+            const S *b = src + (long long)q * pitch + kLead + x;
+            g[0] = s2f(b[0]);
+            g[1] = s2f(b[o1]);
+            g[3] = s2f(b[o3]);
+            if (q >= 1) {
+                g[2] = s2f(b[o2]);
+                g[5] = s2f(b[o5]);
+                g[6] = s2f(b[o6]);
+            } else {
+                g[2] = g[5] = g[6] = 0.f;
+            }
+            if (q + 1 < ny) {
+                g[4] = s2f(b[o4]);
+                g[7] = s2f(b[o7]);
+                g[8] = s2f(b[o8]);
+            } else {
+                g[4] = g[7] = g[8] = 0.f;
+            }
         };
-
-        // Free flight into row q: the stored deviations arriving at (x, q).  A
-        // link from outside returns the site's own population of the opposite
-        // direction (halfway bounce-back; planes {0,1,3} of row q sit in stage
-        // q, {2,5,6} in stage q+1, {4,7,8} in stage q-1), plus the lid term.
-        auto pull_row = [&](int q, float g[9]) {
-            const S(*S0)[kLW] = sm.in[in_slot(q)];
-            const S(*Sm)[kLW] = sm.in[in_slot(q - 1)];
-            const S(*Sp)[kLW] = sm.in[in_slot(q + 1)];
-            g[0] = s2f(S0[0][o]);
-            g[1] = s2f(S0[1][o - 1]);
-            g[2] = s2f(S0[2][o]);
-            g[3] = s2f(S0[3][o + 1]);
-            g[4] = s2f(S0[4][o]);
-            g[5] = s2f(S0[5][o - 1]);
-            g[6] = s2f(S0[6][o + 1]);
-            g[7] = s2f(S0[7][o + 1]);
-            g[8] = s2f(S0[8][o - 1]);
+        // Halfway bounce-back at wall sites: a link from outside returns the
+        // site's own population of the opposite direction, plus the lid term.
+        auto edge_row = [&](int q, float g[9]) {
             const bool edge = xin && (xwall || q == 0 || q == ny - 1);
             if (__any_sync(kFull, edge)) {
                 if (edge) {
+                    const S *b = src + (long long)q * pitch + kLead + x;
 #pragma unroll
                     for (int k = 1; k < 9; ++k) {
                         const int sx = x - Lat<9>::cx(k), sy = q - Lat<9>::cy(k);
                         if (sx >= 0 && sx < nx && sy >= 0 && sy < ny) continue;
-                        const int qq = Lat<9>::opp(k);
-                        float v = s2f((qq == 1 || qq == 3) ? S0[qq][o]
-                                                            : ((qq == 2 || qq == 5 || qq == 6) ? Sp[qq][o] : Sm[qq][o]));
+                        float v = s2f(b[Lat<9>::opp(k) * plane]);
                         if (sy > ny - 1) {
                             v += k == 4 ? A.lid4 : (k == 7 ? A.lid7 : A.lid8);
                             v += k == 4 ? A.lo4 : (k == 7 ? A.lo7 : A.lo8);
@@ -344,12 +160,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_fused(const FusedArgs A0, const
             }
         };
 
-        // Row q: free flight, collision, dS; writes g' of the block's own sites
-        // into the output row.  Rare per-site paths sit behind warp votes.
-        auto compute_row = [&](int q) -> RowState {
+        // Row q from its loaded populations: collision, dS; stores g' of the
+        // warp's own sites.  Rare per-site paths sit behind warp votes.
+        auto compute_row = [&](int q, float g[9]) -> RowState {
             RowState st{0.f, 1.f, false, false};
-            float g[9];
-            pull_row(q, g);
+            edge_row(q, g);
             float drho, rho, ux, uy, gs[9], n[9];
             moments9_dev(g, rho_ref, drho, rho, ux, uy);
             feq9_dev(drho, rho, ux, uy, gs);
@@ -384,9 +199,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_fused(const FusedArgs A0, const
             }
             const bool own = xown && q >= ys && q < ye;
             if (own) {
-                S *out = &sm.out[(unsigned)(q - ys) % kOut][0][ox];
+                S *out = dst + (long long)q * pitch + kLead + x;
 #pragma unroll
-                for (int k = 0; k < 9; ++k) out[k * kMaxWidth] = f2s<S>(g[k]);
+                for (int k = 0; k < 9; ++k) out[k * plane] = f2s<S>(g[k]);
                 s_mass += drho;
                 ++n_sites;
                 if (!bad) {
@@ -433,20 +248,20 @@ __global__ void __launch_bounds__(kThreads, 2) k_fused(const FusedArgs A0, const
             const float phi = act ? fminf(st.pp, pm) : 1.f;
             if (__any_sync(kFull, phi < 1.f)) {
                 // the limited update g - (1 + phi (2 beta - 1)) n (Eq. LimGenF in
-                // nonequilibrium form), with g and n recomputed from the staged
-                // rows exactly as the collision computed them (every lane of the
-                // warp takes part: pull_row votes across the warp)
+                // nonequilibrium form), with g and n recomputed exactly as the
+                // collision computed them (every lane takes part: edge_row votes)
                 float g[9];
-                pull_row(y, g);
+                load_row(y, g);
+                edge_row(y, g);
                 if (phi < 1.f) {
                     float drho, rho, ux, uy, gs[9], n[9];
                     moments9_dev(g, rho_ref, drho, rho, ux, uy);
                     feq9_dev(drho, rho, ux, uy, gs);
                     neq9(g, gs, n);
                     const float c = limit_weight(phi, a, true);
-                    S *out = &sm.out[(unsigned)(y - ys) % kOut][0][ox];
+                    S *out = dst + (long long)y * pitch + kLead + x;
 #pragma unroll
-                    for (int k = 0; k < 9; ++k) out[k * kMaxWidth] = f2s<S>(fmaf(-c, n[k], g[k]));
+                    for (int k = 0; k < 9; ++k) out[k * plane] = f2s<S>(fmaf(-c, n[k], g[k]));
                     s_lim = fmaf(1.f - phi * phi, st.ds, s_lim);
                 }
             }
@@ -465,7 +280,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_fused(const FusedArgs A0, const
                         atomicOr(p.status, kStatCandOverflow);
                     }
                 }
-                if (++rows_acc == 32) {
+                if (++rows_acc == kFoldRows) {
                     acc_mass += (double)s_mass;
                     acc_ds += (double)s_ds;
                     acc_in += (double)s_in;
@@ -476,34 +291,29 @@ __global__ void __launch_bounds__(kThreads, 2) k_fused(const FusedArgs A0, const
             }
         };
 
-        // Iteration r computes row r, then finishes row r-1, whose dS stencil
-        // rows r-2, r-1, r are then in registers.
+        // Iteration r computes row r from the loads issued one iteration
+        // earlier and finishes row r-1.  The loop is unrolled twice so that the
+        // two load buffers swap roles by name (no copy waits for a load).
         RowState prev{0.f, 1.f, false, false};
         float ds_m2 = 0.f, ds_m1 = 0.f;  // dS of rows r-2 and r-1 (this lane's column)
-        for (int r = r0; r - 1 < ye; ++r) {
-            RowState cur{0.f, 1.f, false, false};
+        auto body = [&](int r, float(&cmp)[9], float(&ld)[9]) {
+            RowState st{0.f, 1.f, false, false};
             if (r <= rc) {
-                bool ok = wait_stage(r + 1);
-                if (r == r0) ok = ok && wait_stage(r - 1) && wait_stage(r);
-                const unsigned jo = (unsigned)(r - ys);
-                if (ok && r >= ys && r < ye && jo >= kOut)  // output slot free again
-                    ok = mbar_wait(&sm.oempty[jo % kOut], (jo / kOut - 1) & 1u, abort, p.status);
-                if (!__all_sync(kFull, ok)) break;
-                cur = compute_row(r);
+                if (r + 1 <= rc) load_row(r + 1, ld);
+                st = compute_row(r, cmp);
             }
-            if (r - 1 >= ys) {
-                finalise_row(r - 1, prev, ds_m2, ds_m1, cur.ds);
-                fence_proxy_async();  // the row's shared-memory writes before the bulk store reads them
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&sm.ofull[(unsigned)(r - 1 - ys) % kOut]);
-            }
-            if (r - 2 >= s_first) {  // stage r-2 is no longer read by this warp
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&sm.empty[in_slot(r - 2)]);
-            }
+            if (r - 1 >= ys) finalise_row(r - 1, prev, ds_m2, ds_m1, st.ds);
             ds_m2 = ds_m1;
-            ds_m1 = cur.ds;
-            prev = cur;
+            ds_m1 = st.ds;
+            prev = st;
+        };
+        float bufA[9], bufB[9];
+        load_row(r0, bufA);
+        for (int r = r0;;) {
+            body(r, bufA, bufB);
+            if (++r - 1 >= ye) break;
+            body(r, bufB, bufA);
+            if (++r - 1 >= ye) break;
         }
     }
 
@@ -523,7 +333,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_fused(const FusedArgs A0, const
     __syncthreads();
     if (t < P_NSTAT) {
         double v = 0.0;
-        for (int w = 0; w < kW + 2; ++w) v += red[w][t];
+        for (int w = 0; w < kWarps; ++w) v += red[w][t];
         p.partials[(long long)bid * P_NSTAT + t] = v;
     }
 }
@@ -545,15 +355,7 @@ int sm_count()
 template <typename S, bool MED, bool POS, bool BATCHED>
 cudaError_t launch_k(const FusedArgs &A, const FusedArgs *table, const int2 *map, int blocks, cudaStream_t s)
 {
-    const size_t smem = sizeof(FusedSmem<S>);
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_fused<S, MED, POS, BATCHED>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
-    k_fused<S, MED, POS, BATCHED><<<blocks, kThreads, smem, s>>>(A, table, map);
+    k_fused<S, MED, POS, BATCHED><<<blocks, kThreads, 0, s>>>(A, table, map);
     return cudaGetLastError();
 }
 
@@ -573,56 +375,37 @@ cudaError_t launch_lim(const FusedArgs &A, int blocks, cudaStream_t s)
     }
 }
 
-constexpr int kStripChoices = 8;  // strip counts tried above the fewest possible
-
 }  // namespace
 
-int fused_slots() { return 2 * sm_count(); }
+int fused_slots() { return kBlocksPerSM * kWarps * sm_count(); }
 
-// A launch has at most max(strips, slots) blocks (fused_make_args), strips of
-// at least 8 columns, segments of at least kMinSegRows rows, and at most four
-// waves of slots (the batch engine's largest budget).
+// A launch has one block per kWarps work items; items are strips of 30
+// columns times row segments of at least kMinSegRows rows.
 int fused_d2q9_blocks(int nx, int ny)
 {
-    const long long strips = (nx + 7) / 8, segs = (ny + kMinSegRows - 1) / kMinSegRows;
-    const long long most = std::max<long long>(4LL * fused_slots(), strips);
-    return (int)std::min(strips * segs, most);
+    const long long strips = (nx + 29) / 30, segs = (ny + kMinSegRows - 1) / kMinSegRows;
+    return (int)((strips * segs + kWarps - 1) / kWarps);
 }
 
 bool fused_d2q9_fits(long long plane) { return 9LL * plane < 0x7fffffffLL; }
 
-int fused_make_args(const StepParams &p, const void *src, void *dst, int max_width, int slots, FusedArgs *A)
+int fused_make_args(const StepParams &p, const void *src, void *dst, int seg_rows, int slots, FusedArgs *A)
 {
     *A = FusedArgs{};
     A->p = p;
     A->src = src;
     A->dst = dst;
-    slots = std::max(1, slots);
-    // Strip width (a multiple of 8, at most 240 or max_width) and row
-    // segments: the choice with the least work on the busiest block slot,
-    // counted as waves of `slots` blocks x (rows + 2 halo rows) x active warps.
-    const int cap = max_width > 0 ? std::min(kMaxWidth, std::max(8, max_width & ~7)) : kMaxWidth;
-    const int fewest = (p.nx + cap - 1) / cap;
-    long long best = -1;
-    for (int want = fewest; want < fewest + kStripChoices; ++want) {
-        const int sw = std::min(cap, (((p.nx + want - 1) / want) + 7) & ~7);
-        const int strips = (p.nx + sw - 1) / sw;
-        const int warps = (std::min(sw, p.nx) + 29) / 30;
-        int segs = std::max(1, slots / strips);
-        const int seg_rows = std::max(kMinSegRows, (p.ny + segs - 1) / segs);
-        segs = (p.ny + seg_rows - 1) / seg_rows;
-        const long long blocks = (long long)strips * segs;
-        const long long waves = (blocks + slots - 1) / slots;
-        const long long cost = waves * (seg_rows + 2) * warps;
-        if (best < 0 || cost < best || (cost == best && blocks < A->blocks)) {
-            best = cost;
-            A->sw = sw;
-            A->strips = strips;
-            A->seg_rows = seg_rows;
-            A->blocks = (int)blocks;
-        }
-        if (sw == 8) break;
+    // Work items: strips of 30 columns x row segments, about `slots` of them
+    // (one wave of resident warps) unless `seg_rows` fixes the segment.
+    A->strips = (p.nx + 29) / 30;
+    int rows = seg_rows;
+    if (rows <= 0) {
+        const int segs = std::max(1, std::max(1, slots) / A->strips);
+        rows = (p.ny + segs - 1) / segs;
     }
+    A->seg_rows = std::max(kMinSegRows, rows);
+    A->items = A->strips * ((p.ny + A->seg_rows - 1) / A->seg_rows);
+    A->blocks = (A->items + kWarps - 1) / kWarps;
     A->a = (float)p.a;
     A->b2 = (float)(1.0 + p.a);
     A->delta_m = (float)p.delta_m;

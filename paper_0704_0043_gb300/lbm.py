@@ -440,9 +440,9 @@ class Batch:
     def set_graph(self, steps_per_graph: int):
         _bcheck(lib().lbm_batch_set_graph(self._h, int(steps_per_graph)), self._h)
 
-    def set_shape(self, block_width: int = 0, waves: int = 2):
-        """Fused kernel shape: widest strip (multiple of 8 up to 240; 0: automatic), 1 / 2 / 4 waves."""
-        _bcheck(lib().lbm_batch_set_shape(self._h, int(block_width), int(waves)), self._h)
+    def set_shape(self, seg_rows: int = 0, waves: int = 1):
+        """Fused work split: rows per work item (0: automatic, else >= 16), 1 / 2 / 4 waves."""
+        _bcheck(lib().lbm_batch_set_shape(self._h, int(seg_rows), int(waves)), self._h)
 
     def tune(self, trial_steps: int = 5) -> float:
         ms = ctypes.c_double()
