@@ -13,10 +13,12 @@ namespace lbm {
 
 // Device layout of a population field: plane-major, rows padded.  Element
 // (k, y, x) lives at k * plane + y * pitch + kLead + x.  The kLead elements in
-// front of every row and the tail of each row are zero and never written, so
-// row segments may be copied a few elements past either edge of the lattice.
+// front of every row and the kTail (at least) after it are zero and never
+// written, so a warp may read its whole strip of columns a few elements past
+// either edge of the lattice.
 constexpr int kLead = 32;
-__host__ __device__ inline int row_pitch(int nx) { return ((nx + 31) / 32) * 32 + 2 * kLead; }
+constexpr int kTail = 64;
+__host__ __device__ inline int row_pitch(int nx) { return ((nx + 31) / 32) * 32 + kLead + kTail; }
 
 // Sticky device status bits.
 enum : unsigned { kStatNonfinite = 1u, kStatTimeout = 2u, kStatCandOverflow = 4u };

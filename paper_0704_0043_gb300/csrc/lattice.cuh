@@ -284,16 +284,47 @@ __device__ __forceinline__ float rcp_approx(float x)
 // with e_k = 9 (v_k.u)^2 / 2 - 3 u^2 / 2 (Eq. polyeq2d).  The rest deviation
 // closes the mass: g*_0 = drho - sum_{k>0} g*_k.
 
-__device__ __forceinline__ void moments9_dev(const float g[9], float rho_ref, float &drho, float &rho, float &ux,
-                                             float &uy)
+// Explicitly rounded FP32 operations: the compiler fuses nothing, so every
+// kernel that evaluates a site with these functions gets the same bits.  F1
+// works on one site; F2 on the two sites a lane of the fused kernel carries,
+// with the paired FP32 instructions of sm_100 and later (one instruction,
+// two independent correctly rounded results).
+struct F1 {
+    using V = float;
+    static __device__ __forceinline__ V add(V a, V b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ V sub(V a, V b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ V mul(V a, V b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ V fma(V a, V b, V c) { return __fmaf_rn(a, b, c); }
+    static __device__ __forceinline__ V s(float x) { return x; }
+    static __device__ __forceinline__ V rcp_rn(V a) { return __frcp_rn(a); }
+    static __device__ __forceinline__ V rcp_fast(V a) { return rcp_approx(a); }
+};
+
+struct F2 {
+    using V = float2;
+    static __device__ __forceinline__ V add(V a, V b) { return __fadd2_rn(a, b); }
+    // a - b as fma(b, -1, a): the product is exact, so one rounding, as __fsub_rn
+    static __device__ __forceinline__ V sub(V a, V b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+    static __device__ __forceinline__ V mul(V a, V b) { return __fmul2_rn(a, b); }
+    static __device__ __forceinline__ V fma(V a, V b, V c) { return __ffma2_rn(a, b, c); }
+    static __device__ __forceinline__ V s(float x) { return make_float2(x, x); }
+    static __device__ __forceinline__ V rcp_rn(V a) { return make_float2(__frcp_rn(a.x), __frcp_rn(a.y)); }
+    static __device__ __forceinline__ V rcp_fast(V a) { return make_float2(rcp_approx(a.x), rcp_approx(a.y)); }
+};
+
+template <class O>
+__device__ __forceinline__ void moments9_x(const typename O::V g[9], float rho_ref, typename O::V &drho,
+                                           typename O::V &rho, typename O::V &ux, typename O::V &uy)
 {
-    drho = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
-    rho = rho_ref + drho;
-    const float jx = ((g[1] - g[3]) + (g[5] - g[6])) + (g[8] - g[7]);
-    const float jy = ((g[2] - g[4]) + (g[5] + g[6])) - (g[7] + g[8]);
-    const float inv = __frcp_rn(rho);
-    ux = jx * inv;
-    uy = jy * inv;
+    using V = typename O::V;
+    drho = O::add(O::add(O::add(O::add(g[0], g[1]), O::add(g[2], g[3])), O::add(O::add(g[4], g[5]), O::add(g[6], g[7]))),
+                  g[8]);
+    rho = O::add(O::s(rho_ref), drho);
+    const V jx = O::add(O::add(O::sub(g[1], g[3]), O::sub(g[5], g[6])), O::sub(g[8], g[7]));
+    const V jy = O::sub(O::add(O::sub(g[2], g[4]), O::add(g[5], g[6])), O::add(g[7], g[8]));
+    const V inv = O::rcp_rn(rho);
+    ux = O::mul(jx, inv);
+    uy = O::mul(jy, inv);
 }
 
 // The odd part 3 W_k rho (v_k.u) carries all the momentum; its FP32
@@ -302,32 +333,65 @@ __device__ __forceinline__ void moments9_dev(const float g[9], float rho_ref, fl
 // With the nearest-FP32 weights instead, sum_k v_k f*_k = rho u (1 + 7.5e-9),
 // and since f' = f* + a (f* - f_in), every collision would multiply the
 // momentum by 1 + 2 beta * 7.5e-9.
-__device__ __forceinline__ void feq9_dev(float drho, float rho, float ux, float uy, float gs[9])
+template <class O>
+__device__ __forceinline__ void feq9_x(typename O::V drho, typename O::V rho, typename O::V ux, typename O::V uy,
+                                       typename O::V gs[9])
 {
+    using V = typename O::V;
     const float w1 = 1.0f / 9.0f, w5 = 1.0f / 36.0f;
     const float c1 = 0x1.555556p-2f, c5 = 0x1.555554p-4f;
-    const float m = -1.5f * fmaf(ux, ux, uy * uy);
-    const float b1 = c1 * rho, b5 = c5 * rho;
-    const float cp = ux + uy, cm = uy - ux;
-    float e = fmaf(4.5f * ux, ux, m), A = w1 * fmaf(rho, e, drho), B = b1 * ux;
-    gs[1] = A + B;
-    gs[3] = A - B;
-    e = fmaf(4.5f * uy, uy, m);
-    A = w1 * fmaf(rho, e, drho);
-    B = b1 * uy;
-    gs[2] = A + B;
-    gs[4] = A - B;
-    e = fmaf(4.5f * cp, cp, m);
-    A = w5 * fmaf(rho, e, drho);
-    B = b5 * cp;
-    gs[5] = A + B;
-    gs[7] = A - B;
-    e = fmaf(4.5f * cm, cm, m);
-    A = w5 * fmaf(rho, e, drho);
-    B = b5 * cm;
-    gs[6] = A + B;
-    gs[8] = A - B;
-    gs[0] = drho - (((gs[1] + gs[2]) + (gs[3] + gs[4])) + ((gs[5] + gs[6]) + (gs[7] + gs[8])));
+    const V m = O::mul(O::s(-1.5f), O::fma(ux, ux, O::mul(uy, uy)));
+    const V b1 = O::mul(O::s(c1), rho), b5 = O::mul(O::s(c5), rho);
+    const V cp = O::add(ux, uy), cm = O::sub(uy, ux);
+    auto pair = [&](float w, V b, V c, V &plus, V &minus) {
+        const V e = O::fma(O::mul(O::s(4.5f), c), c, m);
+        const V A = O::mul(O::s(w), O::fma(rho, e, drho));
+        const V B = O::mul(b, c);
+        plus = O::add(A, B);
+        minus = O::sub(A, B);
+    };
+    pair(w1, b1, ux, gs[1], gs[3]);
+    pair(w1, b1, uy, gs[2], gs[4]);
+    pair(w5, b5, cp, gs[5], gs[7]);
+    pair(w5, b5, cm, gs[6], gs[8]);
+    gs[0] = O::sub(drho, O::add(O::add(O::add(gs[1], gs[2]), O::add(gs[3], gs[4])),
+                                O::add(O::add(gs[5], gs[6]), O::add(gs[7], gs[8]))));
+}
+
+// Nonequilibrium part n = g - g* with its mass and momentum sums taken out.
+// In exact arithmetic they vanish; in FP32 they carry the rounding of the
+// moment sums (up to half an ulp of rho u ~ 0.1, i.e. ~4e-9 per site and
+// step).  The collision and the limiters move g along n only (see
+// site_collide_dev), so with these sums removed they conserve mass and
+// momentum to the rounding of the stored values: on a 1000-step cavity run the
+// FP32 error then stays at the level of FP32 storage alone instead of
+// several times above it.  The sums of n are small numbers and nearly exact.
+template <class O>
+__device__ __forceinline__ void neq9_x(const typename O::V g[9], const typename O::V gs[9], typename O::V n[9])
+{
+    using V = typename O::V;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) n[k] = O::sub(g[k], gs[k]);
+    const V rm = O::add(O::add(O::add(O::add(n[0], n[1]), O::add(n[2], n[3])), O::add(O::add(n[4], n[5]), O::add(n[6], n[7]))),
+                        n[8]);
+    const V hx = O::mul(O::s(0.5f), O::add(O::add(O::sub(n[1], n[3]), O::sub(n[5], n[6])), O::sub(n[8], n[7])));
+    const V hy = O::mul(O::s(0.5f), O::sub(O::add(O::sub(n[2], n[4]), O::add(n[5], n[6])), O::add(n[7], n[8])));
+    n[0] = O::sub(n[0], rm);
+    n[1] = O::sub(n[1], hx);
+    n[3] = O::add(n[3], hx);
+    n[2] = O::sub(n[2], hy);
+    n[4] = O::add(n[4], hy);
+}
+
+__device__ __forceinline__ void moments9_dev(const float g[9], float rho_ref, float &drho, float &rho, float &ux,
+                                             float &uy)
+{
+    moments9_x<F1>(g, rho_ref, drho, rho, ux, uy);
+}
+
+__device__ __forceinline__ void feq9_dev(float drho, float rho, float ux, float uy, float gs[9])
+{
+    feq9_x<F1>(drho, rho, ux, uy, gs);
 }
 
 // D1Q3 (Eq. polyeq1d): g*_{1,2} = (drho + 3 rho u^2)/6 -/+ rho u / 2.
@@ -367,27 +431,7 @@ __device__ __forceinline__ void feq_dev(float drho, float rho, float ux, float u
         feq3_dev(drho, rho, ux, gs);
 }
 
-// Nonequilibrium part n = g - g* with its mass and momentum sums taken out.
-// In exact arithmetic they vanish; in FP32 they carry the rounding of the
-// moment sums (up to half an ulp of rho u ~ 0.1, i.e. ~4e-9 per site and
-// step).  The collision and the limiters move g along n only (see
-// site_collide_dev), so with these sums removed they conserve mass and
-// momentum to the rounding of the stored values: on a 1000-step cavity run the
-// FP32 error then stays at the level of FP32 storage alone instead of
-// several times above it.  The sums of n are small numbers and nearly exact.
-__device__ __forceinline__ void neq9(const float g[9], const float gs[9], float n[9])
-{
-#pragma unroll
-    for (int k = 0; k < 9; ++k) n[k] = g[k] - gs[k];
-    const float rm = ((n[0] + n[1]) + (n[2] + n[3])) + ((n[4] + n[5]) + (n[6] + n[7])) + n[8];
-    const float hx = 0.5f * (((n[1] - n[3]) + (n[5] - n[6])) + (n[8] - n[7]));
-    const float hy = 0.5f * (((n[2] - n[4]) + (n[5] + n[6])) - (n[7] + n[8]));
-    n[0] -= rm;
-    n[1] -= hx;
-    n[3] += hx;
-    n[2] -= hy;
-    n[4] += hy;
-}
+__device__ __forceinline__ void neq9(const float g[9], const float gs[9], float n[9]) { neq9_x<F1>(g, gs, n); }
 
 __device__ __forceinline__ void neq3(const float g[3], const float gs[3], float n[3])
 {
@@ -435,13 +479,13 @@ __device__ __forceinline__ bool site_collide_dev(const float g[Q], float a, floa
     float din = 0.f, fmin = 3.4e38f;
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
-        fsa[k] = rw[k] + gs[k];
-        din = fmaf(n[k] * n[k], rcp_approx(fsa[k]), din);
-        gp[k] = collide ? fmaf(-b2, n[k], g[k]) : g[k];
+        fsa[k] = __fadd_rn(rw[k], gs[k]);
+        din = __fmaf_rn(__fmul_rn(n[k], n[k]), rcp_approx(fsa[k]), din);
+        gp[k] = collide ? __fmaf_rn(-b2, n[k], g[k]) : g[k];
         fmin = fminf(fmin, fsa[k]);
     }
     ds_in = collide ? din : 0.f;
-    ds = collide ? (a * a) * din : din;
+    ds = collide ? __fmul_rn(__fmul_rn(a, a), din) : din;
     return !(rho > 0.f) || !(fmin > 0.f) || !isfinite(ds);
 }
 

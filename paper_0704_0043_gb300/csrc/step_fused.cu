@@ -4,29 +4,32 @@
 // moving lid, Sec. 2 and Sec. 4.4.1; polynomial f*, Eq. polyeq2d; LBGK
 // collision, Eq. collLBGK; dS(f'), Sec. 3.6; positivity rule, Sec. 3.1; median
 // filter, Sec. 3.5; Ehrenfests' candidates, Sec. 3.2; FP64 sums, Sec. 3.4),
-// with the same per-site FP32 arithmetic, organised so that every warp streams
-// its own part of the lattice with no shared memory and no barrier:
+// with the same per-site FP32 operations (lattice.cuh), organised so that
+// every warp streams its own part of the lattice with no shared memory and
+// no barrier:
 //
-//  * Work item = one warp: a strip of 32 consecutive columns, of which lanes
-//    1..30 finish their site (lanes 0 and 31 recompute the neighbouring
-//    strips' edge columns), walked upward over a segment of rows.  Row r is
-//    computed, then row r-1 is finished: its 3 x 3 dS stencil is then in
-//    registers (three rows per lane, the side columns by warp shuffles).
+//  * Work item = one warp: a strip of 64 consecutive columns walked upward
+//    over a segment of rows.  Lane l carries two columns, l and l + 32 of the
+//    strip, and evaluates both sites with paired FP32 instructions (F2).  The
+//    strip's first and last columns recompute the neighbouring strips' edge
+//    columns; the other 62 are finished here.  Row r is computed, then row
+//    r-1 is finished: its 3 x 3 dS stencil is then in registers (three rows
+//    per lane, the side columns by warp shuffles).
 //  * Free flight reads the populations arriving at row r straight from the
 //    source field: planes {0,1,3} of row r, {2,5,6} of row r-1, {4,7,8} of
 //    row r+1, each a coalesced 32-lane load, so every stored population is
 //    read from DRAM once (strips overlap by two columns, segments by two
-//    rows).  The loads of row r+1 are issued before row r is computed, so a
-//    row of loads is always in flight behind the arithmetic.
+//    rows).  The loads of row r+1 are issued before row r is computed; the
+//    row loop is unrolled twice so the two load buffers swap by name.
 //  * The post-collision deviations are stored at once; a site whose phi
 //    (decided one row later) is below 1 reloads its row, recomputes the
 //    collision exactly and overwrites its populations with the limited ones.
 //  * Arithmetic is FP32 on the deviations g = f - rho_ref W in nonequilibrium
-//    form (lattice.cuh), stored as FP32, BF16 or FP16; no FP64 on the
-//    per-site path.  Sites whose FP32 dS is near or above the Ehrenfests'
-//    threshold are recorded; the tail kernel recomputes their FP64 key from
-//    the pre-step populations.  Sums are kept per thread in FP32 (mass as
-//    rho - rho_ref), folded into FP64 every 128 rows, and reduced per block.
+//    form, stored as FP32, BF16 or FP16; no FP64 on the per-site path.  Sites
+//    whose FP32 dS is near or above the Ehrenfests' threshold are recorded;
+//    the tail kernel recomputes their FP64 key from the pre-step populations.
+//    Sums are kept per thread in FP32 (mass as rho - rho_ref), folded into
+//    FP64 every 128 rows, and reduced per block.
 #include <algorithm>
 #include <type_traits>
 
@@ -38,19 +41,21 @@ namespace {
 
 constexpr int kWarps = 4;  // independent work items per block
 constexpr int kThreads = 32 * kWarps;
-constexpr int kBlocksPerSM = 6;  // resident blocks per SM (3 for the batched kernel's larger state)
-constexpr int kFoldRows = 128;   // FP32 partial sums are folded into FP64 every kFoldRows rows
+constexpr int kBlocksPerSM = 4;  // resident blocks per SM (3 for the batched kernel's larger state)
+constexpr int kStripCols = 62;   // finished columns per strip (64 computed)
 constexpr int kMinSegRows = 16;  // shortest row segment (the two halo rows cost 2 / segment)
+constexpr int kFoldRows = 128;   // FP32 partial sums are folded into FP64 every kFoldRows rows
+constexpr unsigned kFull = 0xffffffffu;
 
 struct RowState {
-    float ds, pp;
-    bool bad, cand;
+    float2 ds, pp;
+    bool bad_a, bad_b, cand_a, cand_b;
 };
 
 __device__ __forceinline__ double warp_sum_d(double v)
 {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
     return v;
 }
 
@@ -64,6 +69,23 @@ __device__ __forceinline__ void sort3(float a, float b, float c, float &lo, floa
     hi = fmaxf(t2, t3);
 }
 
+// Neighbours of the two columns a lane carries (a = strip column l, b = l + 32):
+// left of a is a of lane l-1, right of a is a of lane l+1 (b of lane 0 for
+// lane 31), left of b is b of lane l-1 (a of lane 31 for lane 0), right of b
+// is b of lane l+1.  The strip's outer columns get values they never use.
+struct Sides {
+    float al, ar, bl, br;
+};
+__device__ __forceinline__ Sides sides(float a, float b, int lane)
+{
+    Sides s;
+    s.al = __shfl_up_sync(kFull, a, 1);
+    s.ar = __shfl_sync(kFull, lane == 0 ? b : a, (lane + 1) & 31);
+    s.bl = __shfl_sync(kFull, lane == 31 ? a : b, (lane - 1) & 31);
+    s.br = __shfl_down_sync(kFull, b, 1);
+    return s;
+}
+
 // MED / POS: the median / positivity code is compiled in (each still follows
 // the instance's limiter bits).  BATCHED: block b runs instance map[b].x of
 // `table` as its block map[b].y; otherwise the single instance A0.
@@ -72,7 +94,7 @@ template <typename S, bool MED, bool POS, bool BATCHED>
 __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : kBlocksPerSM)
     k_fused(const FusedArgs A0, const FusedArgs *__restrict__ table, const int2 *__restrict__ map)
 {
-    constexpr unsigned kFull = 0xffffffffu;
+    using O = F2;
     __shared__ double red[kWarps][P_NSTAT];
     __shared__ __align__(16) FusedArgs sA;
     int bid = (int)blockIdx.x;
@@ -99,13 +121,15 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : kBlocksPerSM)
         const int nx = p.nx, ny = p.ny, pitch = p.pitch;
         const int plane = (int)p.plane;  // 9 * plane < 2^31 is checked at launch
         const int strip = item % A.strips, seg = item / A.strips;
-        const int x = 30 * strip - 1 + lane;  // lattice column of this lane
+        const int xa = kStripCols * strip - 1 + lane, xb = xa + 32;  // the lane's two columns
         const int ys = seg * A.seg_rows, ye = min(ys + A.seg_rows, ny);
         const int r0 = max(ys - 1, 0);
         const int rc = min(ye, ny - 1);  // last row whose dS this warp computes
-        const bool xin = x >= 0 && x < nx;
-        const bool xown = xin && lane >= 1 && lane <= 30;
-        const bool xwall = x == 0 || x == nx - 1;
+        // every lane reads its columns x - 1 .. x + 1, at most 63 past the
+        // lattice's last column: inside the zero row padding (kTail)
+        const bool in_a = xa >= 0 && xa < nx, in_b = xb < nx;
+        const bool own_a = in_a && lane >= 1, own_b = in_b && lane <= 30;
+        const bool wall_a = xa == 0 || xa == nx - 1, wall_b = xb == nx - 1;
         const bool lim_ehr = (p.limiters & 2u) != 0;
         const bool med_on = MED && (p.limiters & 4u) != 0, pos_on = POS && (p.limiters & 1u) != 0;
         const float a = A.a, a2 = A.a * A.a, b2 = A.b2, rho_ref = p.rho_ref;
@@ -114,190 +138,239 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : kBlocksPerSM)
         const int o1 = plane - 1, o3 = 3 * plane + 1;
         const int o2 = 2 * plane - pitch, o5 = 5 * plane - pitch - 1, o6 = 6 * plane - pitch + 1;
         const int o4 = 4 * plane + pitch, o7 = 7 * plane + pitch + 1, o8 = 8 * plane + pitch - 1;
-        // columns x - 1 and x + 1 stay inside the padded row (x >= -1, x <= nx + 29)
 
         // Loads of the populations arriving at row q (rows outside the lattice
         // are not read; their links are bounce-back links, set by edge_row).
-        auto load_row = [&](int q, float g[9]) {
-            const S *b = src + (long long)q * pitch + kLead + x;
-            g[0] = s2f(b[0]);
-            g[1] = s2f(b[o1]);
-            g[3] = s2f(b[o3]);
-            if (q >= 1) {
-                g[2] = s2f(b[o2]);
-                g[5] = s2f(b[o5]);
-                g[6] = s2f(b[o6]);
+        auto load_row = [&](int q, float2 g[9]) {
+            const S *ba = src + (long long)q * pitch + kLead + xa;
+            auto ld = [&](int off) { return make_float2(s2f(ba[off]), s2f(ba[off + 32])); };
+            g[0] = ld(0);
+            g[1] = ld(o1);
+            g[3] = ld(o3);
+            if (q >= 1) {  // the same for the whole warp
+                g[2] = ld(o2);
+                g[5] = ld(o5);
+                g[6] = ld(o6);
             } else {
-                g[2] = g[5] = g[6] = 0.f;
+                g[2] = g[5] = g[6] = make_float2(0.f, 0.f);
             }
             if (q + 1 < ny) {
-                g[4] = s2f(b[o4]);
-                g[7] = s2f(b[o7]);
-                g[8] = s2f(b[o8]);
+                g[4] = ld(o4);
+                g[7] = ld(o7);
+                g[8] = ld(o8);
             } else {
-                g[4] = g[7] = g[8] = 0.f;
+                g[4] = g[7] = g[8] = make_float2(0.f, 0.f);
             }
         };
         // Halfway bounce-back at wall sites: a link from outside returns the
         // site's own population of the opposite direction, plus the lid term.
-        auto edge_row = [&](int q, float g[9]) {
-            const bool edge = xin && (xwall || q == 0 || q == ny - 1);
-            if (__any_sync(kFull, edge)) {
-                if (edge) {
-                    const S *b = src + (long long)q * pitch + kLead + x;
+        auto edge_col = [&](int q, int x, const S *b, float2 g[9], bool second) {
 #pragma unroll
-                    for (int k = 1; k < 9; ++k) {
-                        const int sx = x - Lat<9>::cx(k), sy = q - Lat<9>::cy(k);
-                        if (sx >= 0 && sx < nx && sy >= 0 && sy < ny) continue;
-                        float v = s2f(b[Lat<9>::opp(k) * plane]);
-                        if (sy > ny - 1) {
-                            v += k == 4 ? A.lid4 : (k == 7 ? A.lid7 : A.lid8);
-                            v += k == 4 ? A.lo4 : (k == 7 ? A.lo7 : A.lo8);
-                        }
-                        g[k] = v;
-                    }
+            for (int k = 1; k < 9; ++k) {
+                const int sx = x - Lat<9>::cx(k), sy = q - Lat<9>::cy(k);
+                if (sx >= 0 && sx < nx && sy >= 0 && sy < ny) continue;
+                float v = s2f(b[Lat<9>::opp(k) * plane]);
+                if (sy > ny - 1) {
+                    v += k == 4 ? A.lid4 : (k == 7 ? A.lid7 : A.lid8);
+                    v += k == 4 ? A.lo4 : (k == 7 ? A.lo7 : A.lo8);
                 }
+                if (second)
+                    g[k].y = v;
+                else
+                    g[k].x = v;
             }
+        };
+        auto edge_row = [&](int q, float2 g[9]) {
+            const bool yedge = q == 0 || q == ny - 1;
+            const bool ea = in_a && (wall_a || yedge), eb = in_b && (wall_b || yedge);
+            if (__any_sync(kFull, ea || eb)) {
+                const S *ba = src + (long long)q * pitch + kLead + xa;
+                if (ea) edge_col(q, xa, ba, g, false);
+                if (eb) edge_col(q, xb, ba + 32, g, true);
+            }
+        };
+        // g*, and the corrected nonequilibrium part of the pulled row q
+        auto collide = [&](const float2 g[9], float2 &drho, float2 &rho, float2 &ux, float2 &uy, float2 gs[9],
+                           float2 n[9]) {
+            moments9_x<O>(g, rho_ref, drho, rho, ux, uy);
+            feq9_x<O>(drho, rho, ux, uy, gs);
+            neq9_x<O>(g, gs, n);
         };
 
         // Row q from its loaded populations: collision, dS; stores g' of the
         // warp's own sites.  Rare per-site paths sit behind warp votes.
-        auto compute_row = [&](int q, float g[9]) -> RowState {
-            RowState st{0.f, 1.f, false, false};
+        auto compute_row = [&](int q, float2 g[9]) -> RowState {
+            RowState st{make_float2(0.f, 0.f), make_float2(1.f, 1.f), false, false, false, false};
             edge_row(q, g);
-            float drho, rho, ux, uy, gs[9], n[9];
-            moments9_dev(g, rho_ref, drho, rho, ux, uy);
-            feq9_dev(drho, rho, ux, uy, gs);
-            neq9(g, gs, n);
-            float din = 0.f, fpmin = 3.4e38f;
+            float2 drho, rho, ux, uy, gs[9], n[9];
+            collide(g, drho, rho, ux, uy, gs, n);
+            float2 din = make_float2(0.f, 0.f);
+            float fpmin_a = 3.4e38f, fpmin_b = 3.4e38f;
 #pragma unroll
             for (int k = 0; k < 9; ++k) {
-                din = fmaf(n[k] * n[k], rcp_approx(p.rwf[k] + gs[k]), din);  // / absolute f*
-                g[k] = fmaf(-b2, n[k], g[k]);                                // g' = g - 2 beta n
-                if (pos_on) fpmin = fminf(fpmin, p.rwf[k] + g[k]);
-            }
-            float ds = a2 * din;  // dS(f') = (2 beta - 1)^2 dS(f_in) for the same f*
-            // f*_k >= rho W_k (1/2 - 3 u^2 / 2) > 0 whenever u^2 < 1/3; only fast
-            // flows need the explicit test of every f*_k
-            const float usq = fmaf(ux, ux, uy * uy);
-            bool bad = !(rho > 0.f) || !isfinite(ds);
-            if (__any_sync(kFull, !(usq < 0.3f))) {
-                float fsmin = 3.4e38f;
-#pragma unroll
-                for (int k = 0; k < 9; ++k) fsmin = fminf(fsmin, p.rwf[k] + gs[k]);
-                bad = bad || !(fsmin > 0.f);
-            }
-            if (bad) ds = __int_as_float(0x7f800000);
-            if (pos_on && __any_sync(kFull, !bad && fpmin < 0.f)) {
-                if (!bad && fpmin < 0.f) {  // positivity rule (Sec. 3.1)
-#pragma unroll
-                    for (int k = 0; k < 9; ++k) {
-                        const float fpa = p.rwf[k] + g[k], fsa = p.rwf[k] + gs[k];
-                        if (fpa < 0.f) st.pp = fminf(st.pp, fsa / (fsa - fpa));
-                    }
+                const float2 fsa = O::add(O::s(p.rwf[k]), gs[k]);  // absolute f*
+                din = O::fma(O::mul(n[k], n[k]), O::rcp_fast(fsa), din);
+                g[k] = O::fma(O::s(-b2), n[k], g[k]);  // g' = g - 2 beta n
+                if (pos_on) {
+                    fpmin_a = fminf(fpmin_a, p.rwf[k] + g[k].x);
+                    fpmin_b = fminf(fpmin_b, p.rwf[k] + g[k].y);
                 }
             }
-            const bool own = xown && q >= ys && q < ye;
-            if (own) {
-                S *out = dst + (long long)q * pitch + kLead + x;
+            float2 ds = O::mul(O::s(a2), din);  // dS(f') = (2 beta - 1)^2 dS(f_in) for the same f*
+            // f*_k >= rho W_k (1/2 - 3 u^2 / 2) > 0 whenever u^2 < 1/3; only fast
+            // flows need the explicit test of every f*_k
+            const float2 usq = O::fma(ux, ux, O::mul(uy, uy));
+            bool bad_a = !(rho.x > 0.f) || !isfinite(ds.x), bad_b = !(rho.y > 0.f) || !isfinite(ds.y);
+            if (__any_sync(kFull, !(usq.x < 0.3f) || !(usq.y < 0.3f))) {
+                float fa = 3.4e38f, fb = 3.4e38f;
 #pragma unroll
-                for (int k = 0; k < 9; ++k) out[k * plane] = f2s<S>(g[k]);
-                s_mass += drho;
+                for (int k = 0; k < 9; ++k) {
+                    fa = fminf(fa, p.rwf[k] + gs[k].x);
+                    fb = fminf(fb, p.rwf[k] + gs[k].y);
+                }
+                bad_a = bad_a || !(fa > 0.f);
+                bad_b = bad_b || !(fb > 0.f);
+            }
+            if (bad_a) ds.x = __int_as_float(0x7f800000);
+            if (bad_b) ds.y = __int_as_float(0x7f800000);
+            if (pos_on && __any_sync(kFull, (!bad_a && fpmin_a < 0.f) || (!bad_b && fpmin_b < 0.f))) {
+                // positivity rule (Sec. 3.1)
+#pragma unroll
+                for (int k = 0; k < 9; ++k) {
+                    const float fpa = p.rwf[k] + g[k].x, fsa = p.rwf[k] + gs[k].x;
+                    if (!bad_a && fpa < 0.f) st.pp.x = fminf(st.pp.x, fsa / (fsa - fpa));
+                    const float fpb = p.rwf[k] + g[k].y, fsb = p.rwf[k] + gs[k].y;
+                    if (!bad_b && fpb < 0.f) st.pp.y = fminf(st.pp.y, fsb / (fsb - fpb));
+                }
+            }
+            const bool rown = q >= ys && q < ye;
+            const bool oa = own_a && rown, ob = own_b && rown;
+            S *out = dst + (long long)q * pitch + kLead + xa;
+            if (oa) {
+#pragma unroll
+                for (int k = 0; k < 9; ++k) out[k * plane] = f2s<S>(g[k].x);
+                s_mass += drho.x;
                 ++n_sites;
-                if (!bad) {
-                    s_ds += ds;
-                    s_in += din;
+                if (!bad_a) {
+                    s_ds += ds.x;
+                    s_in += din.x;
                 } else {
                     ++n_bad;
                 }
-                n_pos += st.pp < 1.f;
+                n_pos += st.pp.x < 1.f;
             }
-            if (__any_sync(kFull, own && bad) && lane == 0) atomicOr(p.status, kStatNonfinite);
+            if (ob) {
+#pragma unroll
+                for (int k = 0; k < 9; ++k) out[k * plane + 32] = f2s<S>(g[k].y);
+                s_mass += drho.y;
+                ++n_sites;
+                if (!bad_b) {
+                    s_ds += ds.y;
+                    s_in += din.y;
+                } else {
+                    ++n_bad;
+                }
+                n_pos += st.pp.y < 1.f;
+            }
+            if (__any_sync(kFull, (oa && bad_a) || (ob && bad_b)) && lane == 0) atomicOr(p.status, kStatNonfinite);
             // Ehrenfests' candidates: the tail kernel recomputes the FP64 key of
             // every site recorded here from the pre-step populations
-            st.cand = lim_ehr && !bad && own && ds > A.thr_e;
-            st.bad = bad;
+            st.cand_a = lim_ehr && !bad_a && oa && ds.x > A.thr_e;
+            st.cand_b = lim_ehr && !bad_b && ob && ds.y > A.thr_e;
+            st.bad_a = bad_a;
+            st.bad_b = bad_b;
             st.ds = ds;
             return st;
         };
 
+        auto record = [&](int y, int x, float phi) {
+            const int slot = atomicAdd(p.cand_count, 1);
+            if (slot < p.cand_cap) {
+                Cand cd;
+                cd.key = 0.0;
+                cd.phi = (double)phi;
+                cd.site = y * nx + x;
+                cd.pad = 0;
+                p.cand[slot] = cd;
+            } else {
+                atomicOr(p.status, kStatCandOverflow);
+            }
+        };
+
         // Row y: median of dS (rows y-1, y, y+1 in dm, d0, dp), phi = min(phi_pos,
         // phi_med), limited update where phi < 1, candidate record, sums.
-        auto finalise_row = [&](int y, const RowState &st, float dm, float d0, float dp) {
-            const bool act = xown && y >= ys && y < ye;
-            float pm = 1.f;
+        auto finalise_row = [&](int y, const RowState &st, float2 dm, float2 d0, float2 dp) {
+            const bool rown = y >= ys && y < ye;
+            const bool act_a = own_a && rown, act_b = own_b && rown;
+            float pm_a = 1.f, pm_b = 1.f;
             if (med_on) {
                 // 3 x 3 median from sorted columns: the median of (largest column
                 // minimum, median of the column medians, smallest column maximum);
                 // wall rows and columns take the near-wall stencils
-                float lo, mid, hi;
-                sort3(dm, d0, dp, lo, mid, hi);
-                const float lo_l = __shfl_up_sync(kFull, lo, 1), lo_r = __shfl_down_sync(kFull, lo, 1);
-                const float mid_l = __shfl_up_sync(kFull, mid, 1), mid_r = __shfl_down_sync(kFull, mid, 1);
-                const float hi_l = __shfl_up_sync(kFull, hi, 1), hi_r = __shfl_down_sync(kFull, hi, 1);
-                float med = med3(fmaxf(fmaxf(lo_l, lo), lo_r), med3(mid_l, mid, mid_r), fminf(fminf(hi_l, hi), hi_r));
+                float loa, mida, hia, lob, midb, hib;
+                sort3(dm.x, d0.x, dp.x, loa, mida, hia);
+                sort3(dm.y, d0.y, dp.y, lob, midb, hib);
+                const Sides lo = sides(loa, lob, lane), mid = sides(mida, midb, lane), hi = sides(hia, hib, lane);
+                float med_a = med3(fmaxf(fmaxf(lo.al, loa), lo.ar), med3(mid.al, mida, mid.ar),
+                                   fminf(fminf(hi.al, hia), hi.ar));
+                float med_b = med3(fmaxf(fmaxf(lo.bl, lob), lo.br), med3(mid.bl, midb, mid.br),
+                                   fminf(fminf(hi.bl, hib), hi.br));
                 const bool ywall = y == 0 || y == ny - 1;  // the same for the whole warp
                 if (ywall) {
-                    const float d_l = __shfl_up_sync(kFull, d0, 1), d_r = __shfl_down_sync(kFull, d0, 1);
-                    med = xwall ? med3(d0, x == 0 ? d_r : d_l, y == 0 ? dp : dm) : med3(d_l, d0, d_r);
-                } else if (xwall) {
-                    med = mid;
+                    const Sides d = sides(d0.x, d0.y, lane);
+                    const float vin_a = y == 0 ? dp.x : dm.x, vin_b = y == 0 ? dp.y : dm.y;
+                    med_a = wall_a ? med3(d0.x, xa == 0 ? d.ar : d.al, vin_a) : med3(d.al, d0.x, d.ar);
+                    med_b = wall_b ? med3(d0.y, d.bl, vin_b) : med3(d.bl, d0.y, d.br);
+                } else {
+                    if (wall_a) med_a = mida;
+                    if (wall_b) med_b = midb;
                 }
-                if (act && !st.bad) pm = phi_median<float>(st.ds, med, A.delta_m, p.median_mode);
+                if (act_a && !st.bad_a) pm_a = phi_median<float>(st.ds.x, med_a, A.delta_m, p.median_mode);
+                if (act_b && !st.bad_b) pm_b = phi_median<float>(st.ds.y, med_b, A.delta_m, p.median_mode);
             }
-            const float phi = act ? fminf(st.pp, pm) : 1.f;
-            if (__any_sync(kFull, phi < 1.f)) {
+            const float phi_a = act_a ? fminf(st.pp.x, pm_a) : 1.f, phi_b = act_b ? fminf(st.pp.y, pm_b) : 1.f;
+            if (__any_sync(kFull, phi_a < 1.f || phi_b < 1.f)) {
                 // the limited update g - (1 + phi (2 beta - 1)) n (Eq. LimGenF in
                 // nonequilibrium form), with g and n recomputed exactly as the
                 // collision computed them (every lane takes part: edge_row votes)
-                float g[9];
+                float2 g[9];
                 load_row(y, g);
                 edge_row(y, g);
-                if (phi < 1.f) {
-                    float drho, rho, ux, uy, gs[9], n[9];
-                    moments9_dev(g, rho_ref, drho, rho, ux, uy);
-                    feq9_dev(drho, rho, ux, uy, gs);
-                    neq9(g, gs, n);
-                    const float c = limit_weight(phi, a, true);
-                    S *out = dst + (long long)y * pitch + kLead + x;
+                if (phi_a < 1.f || phi_b < 1.f) {
+                    float2 drho, rho, ux, uy, gs[9], n[9];
+                    collide(g, drho, rho, ux, uy, gs, n);
+                    const float2 mc = make_float2(-limit_weight(phi_a, a, true), -limit_weight(phi_b, a, true));
+                    S *out = dst + (long long)y * pitch + kLead + xa;
 #pragma unroll
-                    for (int k = 0; k < 9; ++k) out[k * plane] = f2s<S>(fmaf(-c, n[k], g[k]));
-                    s_lim = fmaf(1.f - phi * phi, st.ds, s_lim);
+                    for (int k = 0; k < 9; ++k) {
+                        const float2 v = O::fma(mc, n[k], g[k]);
+                        if (phi_a < 1.f) out[k * plane] = f2s<S>(v.x);
+                        if (phi_b < 1.f) out[k * plane + 32] = f2s<S>(v.y);
+                    }
+                    if (phi_a < 1.f) s_lim = fmaf(1.f - phi_a * phi_a, st.ds.x, s_lim);
+                    if (phi_b < 1.f) s_lim = fmaf(1.f - phi_b * phi_b, st.ds.y, s_lim);
                 }
             }
-            if (act) {
-                n_med += pm < 1.f;
-                if (st.cand) {
-                    const int slot = atomicAdd(p.cand_count, 1);
-                    if (slot < p.cand_cap) {
-                        Cand cd;
-                        cd.key = 0.0;
-                        cd.phi = (double)phi;
-                        cd.site = y * nx + x;
-                        cd.pad = 0;
-                        p.cand[slot] = cd;
-                    } else {
-                        atomicOr(p.status, kStatCandOverflow);
-                    }
-                }
-                if (++rows_acc == kFoldRows) {
-                    acc_mass += (double)s_mass;
-                    acc_ds += (double)s_ds;
-                    acc_in += (double)s_in;
-                    acc_lim += (double)s_lim;
-                    s_mass = s_ds = s_in = s_lim = 0.f;
-                    rows_acc = 0;
-                }
+            if (act_a) n_med += pm_a < 1.f;
+            if (act_b) n_med += pm_b < 1.f;
+            if (st.cand_a) record(y, xa, phi_a);
+            if (st.cand_b) record(y, xb, phi_b);
+            if (rown && ++rows_acc == kFoldRows) {
+                acc_mass += (double)s_mass;
+                acc_ds += (double)s_ds;
+                acc_in += (double)s_in;
+                acc_lim += (double)s_lim;
+                s_mass = s_ds = s_in = s_lim = 0.f;
+                rows_acc = 0;
             }
         };
 
         // Iteration r computes row r from the loads issued one iteration
-        // earlier and finishes row r-1.  The loop is unrolled twice so that the
-        // two load buffers swap roles by name (no copy waits for a load).
-        RowState prev{0.f, 1.f, false, false};
-        float ds_m2 = 0.f, ds_m1 = 0.f;  // dS of rows r-2 and r-1 (this lane's column)
-        auto body = [&](int r, float(&cmp)[9], float(&ld)[9]) {
-            RowState st{0.f, 1.f, false, false};
+        // earlier and finishes row r-1.
+        RowState prev{make_float2(0.f, 0.f), make_float2(1.f, 1.f), false, false, false, false};
+        float2 ds_m2 = make_float2(0.f, 0.f), ds_m1 = make_float2(0.f, 0.f);  // dS of rows r-2, r-1
+        auto body = [&](int r, float2(&cmp)[9], float2(&ld)[9]) {
+            RowState st{make_float2(0.f, 0.f), make_float2(1.f, 1.f), false, false, false, false};
             if (r <= rc) {
                 if (r + 1 <= rc) load_row(r + 1, ld);
                 st = compute_row(r, cmp);
@@ -307,7 +380,7 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : kBlocksPerSM)
             ds_m1 = st.ds;
             prev = st;
         };
-        float bufA[9], bufB[9];
+        float2 bufA[9], bufB[9];
         load_row(r0, bufA);
         for (int r = r0;;) {
             body(r, bufA, bufB);
@@ -379,11 +452,11 @@ cudaError_t launch_lim(const FusedArgs &A, int blocks, cudaStream_t s)
 
 int fused_slots() { return kBlocksPerSM * kWarps * sm_count(); }
 
-// A launch has one block per kWarps work items; items are strips of 30
+// A launch has one block per kWarps work items; items are strips of 62
 // columns times row segments of at least kMinSegRows rows.
 int fused_d2q9_blocks(int nx, int ny)
 {
-    const long long strips = (nx + 29) / 30, segs = (ny + kMinSegRows - 1) / kMinSegRows;
+    const long long strips = (nx + kStripCols - 1) / kStripCols, segs = (ny + kMinSegRows - 1) / kMinSegRows;
     return (int)((strips * segs + kWarps - 1) / kWarps);
 }
 
@@ -395,9 +468,9 @@ int fused_make_args(const StepParams &p, const void *src, void *dst, int seg_row
     A->p = p;
     A->src = src;
     A->dst = dst;
-    // Work items: strips of 30 columns x row segments, about `slots` of them
+    // Work items: strips of 62 columns x row segments, about `slots` of them
     // (one wave of resident warps) unless `seg_rows` fixes the segment.
-    A->strips = (p.nx + 29) / 30;
+    A->strips = (p.nx + kStripCols - 1) / kStripCols;
     int rows = seg_rows;
     if (rows <= 0) {
         const int segs = std::max(1, std::max(1, slots) / A->strips);
