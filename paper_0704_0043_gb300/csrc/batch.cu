@@ -133,7 +133,7 @@ lbm_status rebuild(lbm_batch *b)
         if (!c->ready) return bfail(b, LBM_ERR_STATE, "a lattice of the batch was never initialised");
         if (ctx_uses_fused(c)) fused_sites += (long long)c->cfg.nx * c->cfg.ny;
     }
-    const double budget = (double)b->waves * fused_slots();
+    const double budget = (double)b->waves * fused_slots(4, true);
     for (size_t i = 0; i < b->slots.size(); ++i) {
         lbm_ctx *c = b->slots[i];
         if (!c) continue;

@@ -157,7 +157,7 @@ int set_thread_error_impl(int s, const char *msg);
 template <typename S>
 cudaError_t launch_fused_d2q9(const StepParams &p, const S *src, S *dst, int *nblocks, cudaStream_t s);
 int fused_d2q9_blocks(int nx, int ny);  // most blocks (partial-sum rows) any launch of the lattice uses
-int fused_slots();                      // resident work items (warps) of one wave
+int fused_slots(int elem_bytes, bool batched);  // resident work items (warps) of one wave
 // Fills the instance arguments: row segments of `seg_rows` rows (0: about
 // `slots` work items); returns the block count.
 int fused_make_args(const StepParams &p, const void *src, void *dst, int seg_rows, int slots, FusedArgs *out);

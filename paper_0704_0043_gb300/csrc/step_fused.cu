@@ -19,8 +19,11 @@
 //    source field: planes {0,1,3} of row r, {2,5,6} of row r-1, {4,7,8} of
 //    row r+1, each a coalesced 32-lane load, so every stored population is
 //    read from DRAM once (strips overlap by two columns, segments by two
-//    rows).  The loads of row r+1 are issued before row r is computed; the
-//    row loop is unrolled twice so the two load buffers swap by name.
+//    rows).  FP32 rows are copied asynchronously (cp.async) into a per-warp
+//    ring of shared-memory rows two rows ahead of the arithmetic; each lane
+//    reads back only its own copies, so no barrier is needed.  16-bit rows
+//    are loaded into registers one row ahead (the row loop is unrolled twice
+//    so the two load buffers swap by name).
 //  * The post-collision deviations are stored at once; a site whose phi
 //    (decided one row later) is below 1 reloads its row, recomputes the
 //    collision exactly and overwrites its populations with the limited ones.
@@ -41,7 +44,8 @@ namespace {
 
 constexpr int kWarps = 4;  // independent work items per block
 constexpr int kThreads = 32 * kWarps;
-constexpr int kBlocksPerSM = 4;  // resident blocks per SM (3 for the batched kernel's larger state)
+constexpr int kBlocksPerSM = 5;  // resident FP32 blocks per SM (16-bit: 4; batched: 3)
+constexpr int kRing = 3;         // FP32: rows in each warp's shared-memory load ring
 constexpr int kStripCols = 62;   // finished columns per strip (64 computed)
 constexpr int kMinSegRows = 16;  // shortest row segment (the two halo rows cost 2 / segment)
 constexpr int kFoldRows = 128;   // FP32 partial sums are folded into FP64 every kFoldRows rows
@@ -69,6 +73,17 @@ __device__ __forceinline__ void sort3(float a, float b, float c, float &lo, floa
     hi = fmaxf(t2, t3);
 }
 
+// Asynchronous 4-byte global -> shared copy (the lane's own ring slot) and its
+// group bookkeeping; a thread only ever reads back what it copied itself.
+__device__ __forceinline__ void cp_async4(void *dst_smem, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst_smem)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 // Neighbours of the two columns a lane carries (a = strip column l, b = l + 32):
 // left of a is a of lane l-1, right of a is a of lane l+1 (b of lane 0 for
 // lane 31), left of b is b of lane l-1 (a of lane 31 for lane 0), right of b
@@ -91,10 +106,16 @@ __device__ __forceinline__ Sides sides(float a, float b, int lane)
 // `table` as its block map[b].y; otherwise the single instance A0.
 // S: storage type of the deviations (float, __nv_bfloat16 or __half).
 template <typename S, bool MED, bool POS, bool BATCHED>
-__global__ void __launch_bounds__(kThreads, BATCHED ? 3 : kBlocksPerSM)
+__global__ void __launch_bounds__(kThreads, BATCHED ? 3 : (sizeof(S) == 4 ? kBlocksPerSM : 4))
     k_fused(const FusedArgs A0, const FusedArgs *__restrict__ table, const int2 *__restrict__ map)
 {
     using O = F2;
+    // FP32 storage streams through a per-warp ring of shared-memory rows filled
+    // by asynchronous copies (kRing - 1 rows in flight, no registers held);
+    // 16-bit storage (2-byte elements, below the copy granule) loads into
+    // registers one row ahead
+    constexpr bool kAsync = sizeof(S) == 4;
+    __shared__ float2 ring[kAsync ? kWarps : 1][kAsync ? kRing : 1][9][32];
     __shared__ double red[kWarps][P_NSTAT];
     __shared__ __align__(16) FusedArgs sA;
     int bid = (int)blockIdx.x;
@@ -380,13 +401,67 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : kBlocksPerSM)
             ds_m1 = st.ds;
             prev = st;
         };
-        float2 bufA[9], bufB[9];
-        load_row(r0, bufA);
-        for (int r = r0;;) {
-            body(r, bufA, bufB);
-            if (++r - 1 >= ye) break;
-            body(r, bufB, bufA);
-            if (++r - 1 >= ye) break;
+        if constexpr (kAsync) {
+            float2(*my)[9][32] = ring[warp];
+#pragma unroll
+            for (int j = 0; j < kRing; ++j)
+#pragma unroll
+                for (int k = 0; k < 9; ++k) my[j][k][lane] = make_float2(0.f, 0.f);
+            __syncwarp();
+            // copies of the populations arriving at row q into ring slot j (rows
+            // outside the lattice are skipped; edge_row sets those links)
+            auto issue = [&](int q) {
+                if (q <= rc) {
+                    float2(*sl)[32] = my[(q - r0) % kRing];
+                    const S *ba = src + (long long)q * pitch + kLead + xa;
+                    auto cp = [&](int k, int off) {
+                        cp_async4(&sl[k][lane].x, ba + off);
+                        cp_async4(&sl[k][lane].y, ba + off + 32);
+                    };
+                    cp(0, 0);
+                    cp(1, o1);
+                    cp(3, o3);
+                    if (q >= 1) {
+                        cp(2, o2);
+                        cp(5, o5);
+                        cp(6, o6);
+                    }
+                    if (q + 1 < ny) {
+                        cp(4, o4);
+                        cp(7, o7);
+                        cp(8, o8);
+                    }
+                }
+                cp_async_commit();  // one group per row (empty past the last row)
+            };
+#pragma unroll
+            for (int j = 0; j < kRing - 1; ++j) issue(r0 + j);
+            for (int r = r0; r - 1 < ye; ++r) {
+                RowState st{make_float2(0.f, 0.f), make_float2(1.f, 1.f), false, false, false, false};
+                if (r <= rc) {
+                    issue(r + kRing - 1);  // refills the slot row r-1 used
+                    cp_async_wait<kRing - 1>();  // this thread's copies of row r have landed
+                    float2 g[9];
+                    const float2(*sl)[32] = my[(r - r0) % kRing];
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) g[k] = sl[k][lane];
+                    st = compute_row(r, g);
+                }
+                if (r - 1 >= ys) finalise_row(r - 1, prev, ds_m2, ds_m1, st.ds);
+                ds_m2 = ds_m1;
+                ds_m1 = st.ds;
+                prev = st;
+            }
+            cp_async_wait<0>();
+        } else {
+            float2 bufA[9], bufB[9];
+            load_row(r0, bufA);
+            for (int r = r0;;) {
+                body(r, bufA, bufB);
+                if (++r - 1 >= ye) break;
+                body(r, bufB, bufA);
+                if (++r - 1 >= ye) break;
+            }
         }
     }
 
@@ -450,7 +525,11 @@ cudaError_t launch_lim(const FusedArgs &A, int blocks, cudaStream_t s)
 
 }  // namespace
 
-int fused_slots() { return kBlocksPerSM * kWarps * sm_count(); }
+int fused_slots(int elem_bytes, bool batched)
+{
+    const int per_sm = batched ? 3 : (elem_bytes == 4 ? kBlocksPerSM : 4);  // as in the launch bounds
+    return per_sm * kWarps * sm_count();
+}
 
 // A launch has one block per kWarps work items; items are strips of 62
 // columns times row segments of at least kMinSegRows rows.
@@ -497,7 +576,7 @@ template <typename S>
 cudaError_t launch_fused_d2q9(const StepParams &p, const S *src, S *dst, int *nblocks, cudaStream_t s)
 {
     FusedArgs A;
-    *nblocks = fused_make_args(p, src, dst, 0, fused_slots(), &A);
+    *nblocks = fused_make_args(p, src, dst, 0, fused_slots((int)sizeof(S), false), &A);
     return launch_lim<S>(A, A.blocks, s);
 }
 
