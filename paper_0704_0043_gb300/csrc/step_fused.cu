@@ -20,7 +20,7 @@
 //    row r+1, each a coalesced 32-lane load, so every stored population is
 //    read from DRAM once (strips overlap by two columns, segments by two
 //    rows).  FP32 rows are copied asynchronously (cp.async) into a per-warp
-//    ring of shared-memory rows two rows ahead of the arithmetic; each lane
+//    ring of shared-memory rows one row ahead of the arithmetic; each lane
 //    reads back only its own copies, so no barrier is needed.  16-bit rows
 //    are loaded into registers one row ahead (the row loop is unrolled twice
 //    so the two load buffers swap by name).
@@ -45,7 +45,8 @@ namespace {
 constexpr int kWarps = 4;  // independent work items per block
 constexpr int kThreads = 32 * kWarps;
 constexpr int kBlocksPerSM = 5;  // resident FP32 blocks per SM (16-bit: 4; batched: 3)
-constexpr int kRing = 3;         // FP32: rows in each warp's shared-memory load ring
+constexpr int kRing = 2;         // FP32: rows in each warp's shared-memory load ring
+constexpr int kCarveout = -1;    // preferred shared-memory carveout in percent (-1: the driver's choice)
 constexpr int kStripCols = 62;   // finished columns per strip (64 computed)
 constexpr int kMinSegRows = 16;  // shortest row segment (the two halo rows cost 2 / segment)
 constexpr int kFoldRows = 128;   // FP32 partial sums are folded into FP64 every kFoldRows rows
@@ -154,6 +155,9 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : (sizeof(S) == 4 ? kBlo
         const bool lim_ehr = (p.limiters & 2u) != 0;
         const bool med_on = MED && (p.limiters & 4u) != 0, pos_on = POS && (p.limiters & 1u) != 0;
         const float a = A.a, a2 = A.a * A.a, b2 = A.b2, rho_ref = p.rho_ref;
+        // rho_ref W_k takes three values (rest, axis, diagonal), kept in registers
+        const float2 rw0 = O::s(p.rwf[0]), rw1 = O::s(p.rwf[1]), rw5 = O::s(p.rwf[5]);
+        auto rwk = [&](int k) { return k == 0 ? rw0 : (k <= 4 ? rw1 : rw5); };
         // element offsets, from (plane 0, row q, column x), of the population of
         // plane k arriving at (x, q): source row q - cy_k, column x - cx_k
         const int o1 = plane - 1, o3 = 3 * plane + 1;
@@ -229,12 +233,12 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : (sizeof(S) == 4 ? kBlo
             float fpmin_a = 3.4e38f, fpmin_b = 3.4e38f;
 #pragma unroll
             for (int k = 0; k < 9; ++k) {
-                const float2 fsa = O::add(O::s(p.rwf[k]), gs[k]);  // absolute f*
+                const float2 fsa = O::add(rwk(k), gs[k]);  // absolute f*
                 din = O::fma(O::mul(n[k], n[k]), O::rcp_fast(fsa), din);
                 g[k] = O::fma(O::s(-b2), n[k], g[k]);  // g' = g - 2 beta n
                 if (pos_on) {
-                    fpmin_a = fminf(fpmin_a, p.rwf[k] + g[k].x);
-                    fpmin_b = fminf(fpmin_b, p.rwf[k] + g[k].y);
+                    fpmin_a = fminf(fpmin_a, rwk(k).x + g[k].x);
+                    fpmin_b = fminf(fpmin_b, rwk(k).y + g[k].y);
                 }
             }
             float2 ds = O::mul(O::s(a2), din);  // dS(f') = (2 beta - 1)^2 dS(f_in) for the same f*
@@ -252,8 +256,8 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : (sizeof(S) == 4 ? kBlo
                 bad_a = bad_a || !(fa > 0.f);
                 bad_b = bad_b || !(fb > 0.f);
             }
-            if (bad_a) ds.x = __int_as_float(0x7f800000);
-            if (bad_b) ds.y = __int_as_float(0x7f800000);
+            ds.x = bad_a ? __int_as_float(0x7f800000) : ds.x;
+            ds.y = bad_b ? __int_as_float(0x7f800000) : ds.y;
             if (pos_on && __any_sync(kFull, (!bad_a && fpmin_a < 0.f) || (!bad_b && fpmin_b < 0.f))) {
                 // positivity rule (Sec. 3.1)
 #pragma unroll
@@ -267,32 +271,18 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : (sizeof(S) == 4 ? kBlo
             const bool rown = q >= ys && q < ye;
             const bool oa = own_a && rown, ob = own_b && rown;
             S *out = dst + (long long)q * pitch + kLead + xa;
-            if (oa) {
 #pragma unroll
-                for (int k = 0; k < 9; ++k) out[k * plane] = f2s<S>(g[k].x);
-                s_mass += drho.x;
-                ++n_sites;
-                if (!bad_a) {
-                    s_ds += ds.x;
-                    s_in += din.x;
-                } else {
-                    ++n_bad;
-                }
-                n_pos += st.pp.x < 1.f;
+            for (int k = 0; k < 9; ++k) {
+                if (oa) out[k * plane] = f2s<S>(g[k].x);
+                if (ob) out[k * plane + 32] = f2s<S>(g[k].y);
             }
-            if (ob) {
-#pragma unroll
-                for (int k = 0; k < 9; ++k) out[k * plane + 32] = f2s<S>(g[k].y);
-                s_mass += drho.y;
-                ++n_sites;
-                if (!bad_b) {
-                    s_ds += ds.y;
-                    s_in += din.y;
-                } else {
-                    ++n_bad;
-                }
-                n_pos += st.pp.y < 1.f;
-            }
+            const bool ga = oa && !bad_a, gb = ob && !bad_b;
+            s_mass += (oa ? drho.x : 0.f) + (ob ? drho.y : 0.f);
+            s_ds += (ga ? ds.x : 0.f) + (gb ? ds.y : 0.f);
+            s_in += (ga ? din.x : 0.f) + (gb ? din.y : 0.f);
+            n_sites += (int)oa + (int)ob;
+            n_bad += (int)(oa && bad_a) + (int)(ob && bad_b);
+            if (pos_on) n_pos += (int)(oa && st.pp.x < 1.f) + (int)(ob && st.pp.y < 1.f);
             if (__any_sync(kFull, (oa && bad_a) || (ob && bad_b)) && lane == 0) atomicOr(p.status, kStatNonfinite);
             // Ehrenfests' candidates: the tail kernel recomputes the FP64 key of
             // every site recorded here from the pre-step populations
@@ -372,10 +362,11 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : (sizeof(S) == 4 ? kBlo
                     if (phi_b < 1.f) s_lim = fmaf(1.f - phi_b * phi_b, st.ds.y, s_lim);
                 }
             }
-            if (act_a) n_med += pm_a < 1.f;
-            if (act_b) n_med += pm_b < 1.f;
-            if (st.cand_a) record(y, xa, phi_a);
-            if (st.cand_b) record(y, xb, phi_b);
+            n_med += (int)(act_a && pm_a < 1.f) + (int)(act_b && pm_b < 1.f);
+            if (__any_sync(kFull, st.cand_a || st.cand_b)) {
+                if (st.cand_a) record(y, xa, phi_a);
+                if (st.cand_b) record(y, xb, phi_b);
+            }
             if (rown && ++rows_acc == kFoldRows) {
                 acc_mass += (double)s_mass;
                 acc_ds += (double)s_ds;
@@ -410,9 +401,11 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : (sizeof(S) == 4 ? kBlo
             __syncwarp();
             // copies of the populations arriving at row q into ring slot j (rows
             // outside the lattice are skipped; edge_row sets those links)
+            int put = 0, get = 0;  // ring slots of the next row to copy and to read
             auto issue = [&](int q) {
                 if (q <= rc) {
-                    float2(*sl)[32] = my[(q - r0) % kRing];
+                    float2(*sl)[32] = my[put];
+                    put = put + 1 == kRing ? 0 : put + 1;
                     const S *ba = src + (long long)q * pitch + kLead + xa;
                     auto cp = [&](int k, int off) {
                         cp_async4(&sl[k][lane].x, ba + off);
@@ -442,7 +435,8 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : (sizeof(S) == 4 ? kBlo
                     issue(r + kRing - 1);  // refills the slot row r-1 used
                     cp_async_wait<kRing - 1>();  // this thread's copies of row r have landed
                     float2 g[9];
-                    const float2(*sl)[32] = my[(r - r0) % kRing];
+                    const float2(*sl)[32] = my[get];
+                    get = get + 1 == kRing ? 0 : get + 1;
 #pragma unroll
                     for (int k = 0; k < 9; ++k) g[k] = sl[k][lane];
                     st = compute_row(r, g);
@@ -503,6 +497,14 @@ int sm_count()
 template <typename S, bool MED, bool POS, bool BATCHED>
 cudaError_t launch_k(const FusedArgs &A, const FusedArgs *table, const int2 *map, int blocks, cudaStream_t s)
 {
+    static bool configured = false;
+    if (!configured && kCarveout >= 0) {
+        // shared memory vs L1 split (percent of the unified array for shared memory)
+        if (cudaFuncSetAttribute(k_fused<S, MED, POS, BATCHED>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 kCarveout) != cudaSuccess)
+            cudaGetLastError();
+    }
+    configured = true;
     k_fused<S, MED, POS, BATCHED><<<blocks, kThreads, 0, s>>>(A, table, map);
     return cudaGetLastError();
 }
