@@ -124,8 +124,9 @@ __device__ void pull_dev(const FinalParams &p, int x, int y, float g[Q])
     }
 }
 
-// Sum over the block in a fixed order: warp shuffles, then warp totals in
-// warp order (same result every run).  Every thread gets the sum.
+// Sum over the block in a fixed order (same result every run): warp shuffle
+// trees, then a shuffle tree over the warp totals.  Every thread gets the sum.
+// FP64 additions are slow on this GPU, so the dependent chain is kept short.
 __device__ double block_sum(double v, double *red)
 {
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -133,8 +134,14 @@ __device__ double block_sum(double v, double *red)
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
     if (lane == 0) red[warp] = v;
     __syncthreads();
-    double r = 0.0;
-    for (int w = 0; w < kFinWarps; ++w) r += red[w];
+    if (warp == 0) {
+        double r = lane < kFinWarps ? red[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(kFull, r, o);
+        if (lane == 0) red[kFinWarps] = r;
+    }
+    __syncthreads();
+    const double r = red[kFinWarps];
     __syncthreads();
     return r;
 }
@@ -154,7 +161,7 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, 
     }
     const FinalParams &p = BATCHED ? sA.p : p0;
     S *__restrict__ f = BATCHED ? (S *)sA.f : f0;
-    __shared__ double red[kFinWarps];
+    __shared__ double red[kFinWarps + 1];
     __shared__ double tot[P_NSTAT];
     __shared__ double s_key[kCap];
     __shared__ int s_site[kCap];
@@ -175,22 +182,26 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, 
         s_nsel = 0;
         s_valid = 0;
     }
-    // block partials: warp w reduces statistic w over the rows, in a fixed order
-    if (warp < P_NSTAT) {
+    // block partials: warps 2s and 2s+1 reduce statistic s over alternate
+    // 32-row groups, in a fixed order (short FP64 dependency chains)
+    if (warp < 2 * P_NSTAT) {
+        const int stat = warp >> 1, half = warp & 1;
         double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
-        int r = lane;
-        for (; r + 96 < p.nblocks; r += 128) {
-            v0 += p.partials[(long long)r * P_NSTAT + warp];
-            v1 += p.partials[(long long)(r + 32) * P_NSTAT + warp];
-            v2 += p.partials[(long long)(r + 64) * P_NSTAT + warp];
-            v3 += p.partials[(long long)(r + 96) * P_NSTAT + warp];
+        int r = lane + 32 * half;
+        for (; r + 192 < p.nblocks; r += 256) {
+            v0 += p.partials[(long long)r * P_NSTAT + stat];
+            v1 += p.partials[(long long)(r + 64) * P_NSTAT + stat];
+            v2 += p.partials[(long long)(r + 128) * P_NSTAT + stat];
+            v3 += p.partials[(long long)(r + 192) * P_NSTAT + stat];
         }
-        for (; r < p.nblocks; r += 32) v0 += p.partials[(long long)r * P_NSTAT + warp];
+        for (; r < p.nblocks; r += 64) v0 += p.partials[(long long)r * P_NSTAT + stat];
         double v = (v0 + v1) + (v2 + v3);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
-        if (lane == 0) tot[warp] = v;
+        if (lane == 0) red[warp] = v;
     }
+    __syncthreads();
+    if (t < P_NSTAT) tot[t] = red[2 * t] + red[2 * t + 1];
     __syncthreads();
     const int n = s_n;
     const bool small = n <= kCap;  // candidates held in shared memory
@@ -236,7 +247,8 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, 
     __syncthreads();
     const int n_valid = s_valid;
     double ehr_sum = 0.0;
-    if (p.ehrenfest && k > 0 && n_valid > 0) {
+    const bool ehr_active = p.ehrenfest && k > 0 && n_valid > 0;  // the same for the whole block
+    if (ehr_active) {
         unsigned long long kv = 0;  // threshold dS pattern
         int site_thr = 0x7fffffff;
         const bool take_all = (long long)n_valid <= k;
@@ -382,7 +394,7 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, 
             for (int r = t; r < nsel; r += kFinThreads) p.sel[r] = p.cand[p.sel[r]].site;
         }
     }
-    const double esum = block_sum(ehr_sum, red);
+    const double esum = ehr_active ? block_sum(ehr_sum, red) : 0.0;
     if (t == 0) {
         long long step = s_step;
         if (p.collide) {
