@@ -57,13 +57,6 @@ struct RowState {
     bool bad_a, bad_b, cand_a, cand_b;
 };
 
-__device__ __forceinline__ double warp_sum_d(double v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
-    return v;
-}
-
 // Sorted column (lo <= mid <= hi) of three values.
 __device__ __forceinline__ void sort3(float a, float b, float c, float &lo, float &mid, float &hi)
 {
@@ -459,18 +452,34 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : (sizeof(S) == 4 ? kBlo
         }
     }
 
-    double acc[P_NSTAT];
-    acc[P_MASS] = acc_mass + (double)s_mass + (double)n_sites * (double)p.rho_ref;
-    acc[P_SUM_DS] = acc_ds + (double)s_ds;
-    acc[P_SUM_IN] = acc_in + (double)s_in;
-    acc[P_DS_LIM] = acc_lim + (double)s_lim;
-    acc[P_NPOS] = (double)n_pos;
-    acc[P_NMED] = (double)n_med;
-    acc[P_NBAD] = (double)n_bad;
+    // Warp totals.  FP64 instructions are slow on this GPU and every warp
+    // reaches this point at about the same time, so the FP64 work is kept
+    // small: counts are summed as integers, and the four FP sums share one
+    // butterfly in which each level halves the sums a lane carries (lanes 0,
+    // 8, 16, 24 end with the mass, dS, dS_in and dS_lim totals; fixed order).
+    const int tot_sites = __reduce_add_sync(kFull, n_sites), tot_pos = __reduce_add_sync(kFull, n_pos);
+    const int tot_med = __reduce_add_sync(kFull, n_med), tot_bad = __reduce_add_sync(kFull, n_bad);
+    {
+        const double v0 = acc_mass + (double)s_mass, v1 = acc_ds + (double)s_ds;
+        const double v2 = acc_in + (double)s_in, v3 = acc_lim + (double)s_lim;
+        const bool hi16 = (lane & 16) != 0, hi8 = (lane & 8) != 0;
+        double x0 = hi16 ? v2 : v0, x1 = hi16 ? v3 : v1;
+        const double y0 = hi16 ? v0 : v2, y1 = hi16 ? v1 : v3;
+        x0 += __shfl_xor_sync(kFull, y0, 16);
+        x1 += __shfl_xor_sync(kFull, y1, 16);
+        double z = hi8 ? x1 : x0;
+        z += __shfl_xor_sync(kFull, hi8 ? x0 : x1, 8);
 #pragma unroll
-    for (int i = 0; i < P_NSTAT; ++i) {
-        const double v = warp_sum_d(acc[i]);
-        if (lane == 0) red[warp][i] = v;
+        for (int o = 4; o > 0; o >>= 1) z += __shfl_xor_sync(kFull, z, o);
+        if ((lane & 7) == 0) {
+            const int stat = lane >> 3;  // P_MASS, P_SUM_DS, P_SUM_IN, P_DS_LIM
+            red[warp][stat] = stat == P_MASS ? fma((double)tot_sites, (double)p.rho_ref, z) : z;
+        }
+        if (lane == 0) {
+            red[warp][P_NPOS] = (double)tot_pos;
+            red[warp][P_NMED] = (double)tot_med;
+            red[warp][P_NBAD] = (double)tot_bad;
+        }
     }
     __syncthreads();
     if (t < P_NSTAT) {
