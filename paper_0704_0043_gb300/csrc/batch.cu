@@ -150,7 +150,7 @@ lbm_status rebuild(lbm_batch *b)
                 b->h_fused[k].push_back(A);
                 FinalArgs F{ctx_final_params(c, 1, lim, blocks), dst};
                 F.p.src = src;
-                F.p.recompute = 1;
+                F.p.fixed = 1;  // one work item per warp in batched launches: no counter to clear
                 b->h_fin9[k].push_back(F);
                 if (k == 0)
                     for (int lb = 0; lb < blocks; ++lb)

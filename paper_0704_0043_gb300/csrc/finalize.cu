@@ -10,10 +10,9 @@
 // four passes over the site index among the candidates tied at the threshold.
 //
 // The kernel is one block and sits between two step launches, so it is built
-// for latency: up to kCap candidates are kept in shared memory, the FP64 key
-// of a recorded site is evaluated by one warp with a lane per direction (the
-// operations and their order are those of key_dS9, so the key is the same
-// bit for bit), and block sums use warp shuffles.
+// for latency: the candidates arrive with their FP64 keys (the step kernels
+// evaluate them where they find them), up to kCap of them are kept in shared
+// memory, and sums use warp shuffles or exact integer arithmetic.
 #include <type_traits>
 
 #include "internal.h"
@@ -32,69 +31,6 @@ __device__ __forceinline__ unsigned long long key_bits(double d) { return (unsig
 __device__ __forceinline__ long long fidx(long long plane, int pitch, int k, int y, int x)
 {
     return (long long)k * plane + (long long)y * pitch + kLead + x;
-}
-
-// Population k arriving at site (x, y) of a D2Q9 cavity / channel / periodic
-// lattice, in FP64 from FP32 / 16-bit storage: (double) g + rho_ref W, the
-// value the FP64 path computes from the same stored state.
-template <typename S>
-__device__ double pull_one_f64(const FinalParams &p, int x, int y, int k)
-{
-    const S *src = (const S *)p.src;
-    const bool wrapx = p.boundary != 0, wrapy = p.boundary == 1;
-    int sx = x - Lat<9>::cx(k), sy = y - Lat<9>::cy(k);
-    if (wrapx) sx = sx < 0 ? sx + p.nx : (sx >= p.nx ? sx - p.nx : sx);
-    if (wrapy) sy = sy < 0 ? sy + p.ny : (sy >= p.ny ? sy - p.ny : sy);
-    if (sx >= 0 && sx < p.nx && sy >= 0 && sy < p.ny)
-        return Ar<double>::add((double)s2f(src[fidx(p.plane, p.pitch, k, sy, sx)]), p.rw[k]);
-    const int q = Lat<9>::opp(k);
-    double v = Ar<double>::add((double)s2f(src[fidx(p.plane, p.pitch, q, y, x)]), p.rw[q]);
-    if (sy > p.ny - 1) v = Ar<double>::add(v, p.lid[k]);
-    return v;
-}
-
-// FP64 Ehrenfests' key dS(f') of `site` evaluated by a whole warp: lane k < 9
-// pulls population k and evaluates f*_k and its dS term; the moments and the
-// final sum run in k order exactly as key_dS9 runs them.  Every lane returns
-// the same key; false for a site that cannot be limited.
-template <typename S>
-__device__ bool key_dS9_warp(const FinalParams &p, int site, double &key)
-{
-    using A = Ar<double>;
-    const int lane = threadIdx.x & 31, k = lane < 9 ? lane : 0;
-    const int x = site % p.nx, y = site / p.nx;
-    const double mine = pull_one_f64<S>(p, x, y, k);
-    double fin[9];
-#pragma unroll
-    for (int j = 0; j < 9; ++j) fin[j] = __shfl_sync(kFull, mine, j);
-    double rho, ux, uy;
-    moments9<double>(fin, rho, ux, uy);
-    // f*_k as in feq9<double>
-    const double usq = A::add(A::mul(ux, ux), A::mul(uy, uy));
-    const double tail = A::mul(A::mul(3.0, usq), 0.5);
-    const double c = k == 0 ? 0.0
-                   : k == 1 ? ux
-                   : k == 2 ? uy
-                   : k == 3 ? -ux
-                   : k == 4 ? -uy
-                   : k == 5 ? A::add(ux, uy)
-                   : k == 6 ? A::sub(uy, ux)
-                   : k == 7 ? -A::add(ux, uy)
-                            : A::sub(ux, uy);
-    double poly = A::add(A::add(1.0, A::mul(3.0, c)), A::mul(A::mul(9.0, A::mul(c, c)), 0.5));
-    poly = A::sub(poly, tail);
-    const double fs = A::mul(A::mul(rho, Lat<9>::w(k)), poly);
-    // collision and the dS term as in key_dS9
-    const double fp = A::add(fs, A::mul(p.a, A::sub(fs, mine)));
-    const double d = A::sub(fp, fs);
-    const double term = A::div(A::mul(d, d), fs);
-    const bool bad_k = lane < 9 && (!(fs > 0.0) || !isfinite(mine));
-    double s = 0.0;
-#pragma unroll
-    for (int j = 0; j < 9; ++j) s = A::add(s, __shfl_sync(kFull, term, j));
-    const bool bad = __any_sync(kFull, bad_k) || !(rho > 0.0) || !isfinite(rho) || !isfinite(ux) || !isfinite(uy);
-    key = s;
-    return !bad && isfinite(s);
 }
 
 // The pass's input at site (x, y) in FP32: after free flight (collide) with the
@@ -125,25 +61,37 @@ __device__ void pull_dev(const FinalParams &p, int x, int y, float g[Q])
 }
 
 // Sum over the block in a fixed order (same result every run): warp shuffle
-// trees, then a shuffle tree over the warp totals.  Every thread gets the sum.
+// trees, then a shuffle tree over the warp totals; thread 0 gets the sum.
 // FP64 additions are slow on this GPU, so the dependent chain is kept short.
-__device__ double block_sum(double v, double *red)
+// `warp0_only`: the other warps hold zeros, so warp 0's tree is the sum (the
+// same bits: adding the zero totals changes nothing).
+__device__ double block_sum0(double v, double *red, bool warp0_only)
 {
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    if (warp0_only && warp != 0) return 0.0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+    if (warp0_only) return v;
     if (lane == 0) red[warp] = v;
     __syncthreads();
     if (warp == 0) {
         double r = lane < kFinWarps ? red[lane] : 0.0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(kFull, r, o);
-        if (lane == 0) red[kFinWarps] = r;
+        v = r;
     }
-    __syncthreads();
-    const double r = red[kFinWarps];
-    __syncthreads();
-    return r;
+    return v;
+}
+
+// Value of a 128-bit two's-complement fixed-point number in units of 2^-64
+// (the fused kernel's sums): the high and low 64-bit magnitudes are converted
+// separately, so the result is the same on every run.
+__device__ double fx_to_double(unsigned __int128 x)
+{
+    const bool neg = (unsigned long long)(x >> 127) != 0;
+    const unsigned __int128 m = neg ? (unsigned __int128)0 - x : x;
+    const double d = (double)(unsigned long long)(m >> 64) * 18446744073709551616.0 + (double)(unsigned long long)m;
+    return (neg ? -d : d) * 5.42101086242752217003726400434970855712890625e-20;  // 2^-64
 }
 
 // BATCHED: block b finishes instance b of `table`; otherwise the single (p0, f0).
@@ -163,6 +111,9 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, 
     S *__restrict__ f = BATCHED ? (S *)sA.f : f0;
     __shared__ double red[kFinWarps + 1];
     __shared__ double tot[P_NSTAT];
+    __shared__ unsigned __int128 s_fx[4];
+    __shared__ unsigned long long s_cnt[5];
+    __shared__ unsigned long long s_fxw[kFinWarps][13];
     __shared__ double s_key[kCap];
     __shared__ int s_site[kCap];
     __shared__ int s_idx[kCap];
@@ -182,9 +133,86 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, 
         s_nsel = 0;
         s_valid = 0;
     }
-    // block partials: warps 2s and 2s+1 reduce statistic s over alternate
-    // 32-row groups, in a fixed order (short FP64 dependency chains)
-    if (warp < 2 * P_NSTAT) {
+    if (p.fixed) {
+        // fixed-point rows of the fused kernel: exact integer sums, so the
+        // order does not matter.  Each 128-byte row is read as eight 16-byte
+        // chunks (coalesced: lane l takes chunk l % 8 of a row); chunk c < 4
+        // is FP statistic c (low, high word), chunk 4 the site and positivity
+        // counts, chunk 5 the median and nonfinite counts, chunk 6 the bits.
+        const int c = lane & 7;
+        unsigned __int128 v = 0;
+        unsigned long long u0 = 0, u1 = 0;
+        const ulonglong2 *chunks = reinterpret_cast<const ulonglong2 *>(p.partials);
+        constexpr int kStride = kFinThreads / 8;  // rows per pass of the block
+        for (int r0 = t >> 3; r0 < p.nblocks; r0 += 8 * kStride) {
+            ulonglong2 w[8];  // eight loads in flight, then the sums
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int r = r0 + i * kStride;
+                w[i] = r < p.nblocks ? chunks[(long long)r * (kFxWords / 2) + c] : make_ulonglong2(0ull, 0ull);
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                if (c < 4) {
+                    v += ((unsigned __int128)w[i].y << 64) | w[i].x;
+                } else if (c < 6) {
+                    u0 += w[i].x;
+                    u1 += w[i].y;
+                } else if (c == 6) {
+                    u0 |= w[i].x;
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 8; o <= 16; o <<= 1) {  // lanes holding the same chunk
+            const unsigned long long lo = __shfl_xor_sync(kFull, (unsigned long long)v, o);
+            const unsigned long long hi = __shfl_xor_sync(kFull, (unsigned long long)(v >> 64), o);
+            const unsigned long long a0 = __shfl_xor_sync(kFull, u0, o), a1 = __shfl_xor_sync(kFull, u1, o);
+            v += ((unsigned __int128)hi << 64) | lo;
+            u0 = c == 6 ? (u0 | a0) : u0 + a0;
+            u1 += a1;
+        }
+        if (lane < 8) {
+            if (c < 4) {
+                s_fxw[warp][2 * c] = (unsigned long long)v;
+                s_fxw[warp][2 * c + 1] = (unsigned long long)(v >> 64);
+            } else if (c < 6) {
+                s_fxw[warp][FX_SITES + 2 * (c - 4)] = u0;
+                s_fxw[warp][FX_SITES + 2 * (c - 4) + 1] = u1;
+            } else if (c == 6) {
+                s_fxw[warp][FX_BAD] = u0;
+            }
+        }
+        __syncthreads();
+        if (t < 9) {  // t < 4: FP statistic t; 4..7: the counts; 8: the nonfinite bits
+            unsigned __int128 a = 0;
+            unsigned long long b = 0;
+            for (int w = 0; w < kFinWarps; ++w) {
+                if (t < 4)
+                    a += ((unsigned __int128)s_fxw[w][2 * t + 1] << 64) | s_fxw[w][2 * t];
+                else if (t < 8)
+                    b += s_fxw[w][4 + t];
+                else
+                    b |= s_fxw[w][12];
+            }
+            if (t < 4)
+                s_fx[t] = a;
+            else
+                s_cnt[t - 4] = b;
+        }
+        __syncthreads();
+        if (t < P_NSTAT) {  // one statistic per thread
+            if (t <= P_DS_LIM) {
+                double v = ((s_cnt[4] >> t) & 1u) ? __longlong_as_double(0x7ff8000000000000LL) : fx_to_double(s_fx[t]);
+                if (t == P_MASS) v = Ar<double>::add(v, Ar<double>::mul((double)s_cnt[0], (double)p.rho_ref));
+                tot[t] = v;
+            } else {
+                tot[t] = (double)s_cnt[t - P_NPOS + 1];  // positivity, median, nonfinite counts
+            }
+        }
+    } else if (warp < 2 * P_NSTAT) {
+        // block partials: warps 2s and 2s+1 reduce statistic s over alternate
+        // 32-row groups, in a fixed order (short FP64 dependency chains)
         const int stat = warp >> 1, half = warp & 1;
         double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
         int r = lane + 32 * half;
@@ -201,33 +229,15 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, 
         if (lane == 0) red[warp] = v;
     }
     __syncthreads();
-    if (t < P_NSTAT) tot[t] = red[2 * t] + red[2 * t + 1];
+    if (!p.fixed && t < P_NSTAT) tot[t] = red[2 * t] + red[2 * t + 1];
     __syncthreads();
     const int n = s_n;
     const bool small = n <= kCap;  // candidates held in shared memory
     const long long k = p.k_max;
-    constexpr bool kLowPrec = !std::is_same<S, double>::value;
 
-    // candidate keys: FP64 dS(f') (recomputed from the pre-step populations for
-    // the fused kernel's records; sites at or below the threshold drop out)
-    const bool recompute = kLowPrec && Q == 9 && p.recompute;
-    if (recompute) {
-        if constexpr (kLowPrec) {
-            for (int i = warp; i < n; i += kFinWarps) {
-                const int site = p.cand[i].site;
-                double d64;
-                const bool ok = key_dS9_warp<S>(p, site, d64);
-                const double key = (ok && d64 > p.delta_e) ? d64 : -1.0;
-                if (lane == 0) {
-                    if (small) {
-                        s_key[i] = key;
-                        s_site[i] = site;
-                    }
-                    p.cand[i].key = key;
-                }
-            }
-        }
-    } else if (small) {
+    // candidate keys: FP64 dS(f'), written with the candidates by the step
+    // kernels (sites at or below the threshold carry -1)
+    if (small) {
         for (int i = t; i < n; i += kFinThreads) {
             const Cand c = p.cand[i];
             s_key[i] = c.key;
@@ -394,7 +404,9 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, 
             for (int r = t; r < nsel; r += kFinThreads) p.sel[r] = p.cand[p.sel[r]].site;
         }
     }
-    const double esum = ehr_active ? block_sum(ehr_sum, red) : 0.0;
+    // thread r applied chosen site r: with at most 32 of them only warp 0
+    // holds terms
+    const double esum = ehr_active ? block_sum0(ehr_sum, red, s_nsel <= 32) : 0.0;
     if (t == 0) {
         long long step = s_step;
         if (p.collide) {
@@ -421,6 +433,7 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, 
         p.stats_ring[rec % p.ring_len] = st;
         *p.sel_count = s_nsel;
         *p.cand_count = 0;
+        if (p.work != nullptr) *p.work = 0;  // the next fused launch starts at its first item
     }
 }
 

@@ -14,10 +14,11 @@ namespace lbm {
 // Device layout of a population field: plane-major, rows padded.  Element
 // (k, y, x) lives at k * plane + y * pitch + kLead + x.  The kLead elements in
 // front of every row and the kTail (at least) after it are zero and never
-// written, so a warp may read its whole strip of columns a few elements past
-// either edge of the lattice.
+// written, so a warp may read a window of columns around its strip a few
+// elements past either edge of the lattice (the fused kernel's 16-byte
+// copies reach up to 68 columns past the last column).
 constexpr int kLead = 32;
-constexpr int kTail = 64;
+constexpr int kTail = 96;
 __host__ __device__ inline int row_pitch(int nx) { return ((nx + 31) / 32) * 32 + kLead + kTail; }
 
 // Sticky device status bits.
@@ -26,6 +27,19 @@ enum : unsigned { kStatNonfinite = 1u, kStatTimeout = 2u, kStatCandOverflow = 4u
 // Per-block partial sums written by the step kernels, reduced in a fixed
 // order by the finalise kernel.
 enum { P_MASS = 0, P_SUM_DS, P_SUM_IN, P_DS_LIM, P_NPOS, P_NMED, P_NBAD, P_NSTAT };
+
+// The fused kernel hands out its work items dynamically, so which warp sums
+// which sites varies from run to run.  To keep the step statistics the same
+// bit for bit, it sums them exactly: each work item's FP32 sums (a fixed
+// evaluation order within the item) are converted to 128-bit two's-complement
+// fixed point in units of 2^-64 and added as integers, whose sum does not
+// depend on the order.  A fixed-point partial row holds kFxWords words:
+// FX_SUM + 2 s (low word) and FX_SUM + 2 s + 1 (high word) for the FP
+// statistic s = P_MASS (sum of rho - rho_ref) .. P_DS_LIM; the site and
+// limiter counts; and a bit per FP statistic that met a nonfinite or
+// out-of-range (>= 2^63) item sum.
+constexpr int kFxWords = 16;
+enum { FX_SUM = 0, FX_SITES = 8, FX_NPOS, FX_NMED, FX_NBAD, FX_BAD };
 
 // Ehrenfests' candidate: FP64 key dS(f'), phi of the limiter pass, site index.
 struct Cand {
@@ -64,13 +78,16 @@ struct StepParams {
     Cand *cand;
     int *cand_count;
     int cand_cap;
-    double *partials;          // [blocks][P_NSTAT]
+    double *partials;          // [blocks][P_NSTAT] doubles; fused kernel: [blocks][kFxWords] fixed-point words
     unsigned *status;
+    int *work;                 // fused kernel: counter of work items handed out (nullptr: one item per warp)
     double *ds_out;            // optional FP64 dS(f') field (nx * ny) or nullptr
 };
 
 struct FinalParams {
     int nblocks;               // partial rows to reduce
+    int fixed;                 // the rows are fixed-point rows of the fused kernel
+    int *work;                 // work-item counter to clear for the next step, or nullptr
     double one_minus_a2;       // 1 - (2 beta - 1)^2
     long long k_max;
     int ehrenfest;             // apply Ehrenfests' step
@@ -88,9 +105,6 @@ struct FinalParams {
     DevStats *stats_ring;
     int ring_len;
     long long *counters;       // [0] steps taken (incremented when collide), [1] records written
-    // candidates recorded without an FP64 key (fused kernel): the key dS(f') is
-    // recomputed in FP64 from the pre-step populations `src` before selection
-    int recompute;
     // pre-step populations of the pass (FP32 / BF16 / FP16 storage): the
     // Ehrenfests' step evaluates f*(m) from them, with the same FP32 free
     // flight as the step kernel, so the stored result is rounded once
@@ -186,7 +200,7 @@ struct lbm_ctx {
     int cur = 0;
     lbm::Cand *cand = nullptr;
     int cand_cap = 0;
-    int *counts = nullptr;  // [0] candidate count, [1] chosen count
+    int *counts = nullptr;  // [0] candidate count, [1] chosen count, [2] fused work items handed out, [3] unused
     int *sel = nullptr;
     int sel_cap = 0;
     double *partials = nullptr;

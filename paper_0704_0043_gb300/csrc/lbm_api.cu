@@ -129,8 +129,9 @@ Sizes sizes_for(const lbm_config &c)
     z.sel_cap = (int)std::max<long long>(1, std::min<long long>(c.k_max, n));
     z.sel = (size_t)z.sel_cap * sizeof(int);
     z.rows = tiled_blocks(c);
-    if (fused_applies(c)) z.rows = std::max(z.rows, fused_d2q9_blocks(c.nx, c.ny));
     z.partials = (size_t)z.rows * P_NSTAT * sizeof(double);
+    if (fused_applies(c))
+        z.partials = std::max(z.partials, (size_t)fused_d2q9_blocks(c.nx, c.ny) * kFxWords * sizeof(unsigned long long));
     z.ring_len = std::max(1, c.stats_history);
     z.ring = (size_t)z.ring_len * sizeof(DevStats);
     return z;
@@ -208,6 +209,7 @@ StepParams step_params(lbm_ctx *c, int collide, unsigned limiters)
     p.cand_cap = c->cand_cap;
     p.partials = c->partials;
     p.status = c->status;
+    p.work = c->counts + 2;
     p.ds_out = nullptr;
     return p;
 }
@@ -293,7 +295,8 @@ lbm_status run_pass(lbm_ctx *c, int collide, unsigned limiters)
     if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
     if ((ms = mark(c)) != LBM_OK) return ms;
     FinalParams f = final_params(c, collide, limiters, nblocks);
-    f.recompute = fused ? 1 : 0;
+    f.fixed = fused ? 1 : 0;
+    f.work = fused ? c->counts + 2 : nullptr;
     e = with_storage(c->cfg.precision, [&](auto tag) -> cudaError_t {
         using S = STORAGE_T;
         return launch_finalize<S>(c->q, f, (S *)dst, c->stream);
@@ -321,7 +324,7 @@ lbm_status reset_counters(lbm_ctx *c)
 {
     CK(c, cudaMemsetAsync(c->counters, 0, 2 * sizeof(long long), c->stream));
     CK(c, cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->stream));
-    CK(c, cudaMemsetAsync(c->counts, 0, 2 * sizeof(int), c->stream));
+    CK(c, cudaMemsetAsync(c->counts, 0, 4 * sizeof(int), c->stream));
     CK(c, cudaMemsetAsync(c->ring, 0, (size_t)c->ring_len * sizeof(DevStats), c->stream));
     return LBM_OK;
 }
@@ -432,7 +435,7 @@ lbm_status lbm_create(const lbm_config *cfg, void *cuda_stream, lbm_ctx **out)
     alloc(&c->buf[0], z.field);
     alloc(&c->buf[1], z.field);
     alloc((void **)&c->cand, z.cand);
-    alloc((void **)&c->counts, 2 * sizeof(int));
+    alloc((void **)&c->counts, 4 * sizeof(int));
     alloc((void **)&c->sel, z.sel);
     alloc((void **)&c->partials, z.partials);
     alloc((void **)&c->status, sizeof(unsigned));

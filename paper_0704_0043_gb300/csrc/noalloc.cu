@@ -158,7 +158,6 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_config *cfg, const double *f_in
     f.stats_ring = (DevStats *)(base + L.ring);
     f.ring_len = 1;
     f.counters = (long long *)(base + L.counters);
-    f.recompute = 0;
     f.rho_ref = p.rho_ref;
     if (launch_finalize<double>(q, f, dst, s) != cudaSuccess) return LBM_ERR_CUDA;
 

@@ -28,15 +28,23 @@
 //    (decided one row later) is below 1 reloads its row, recomputes the
 //    collision exactly and overwrites its populations with the limited ones.
 //  * Arithmetic is FP32 on the deviations g = f - rho_ref W in nonequilibrium
-//    form, stored as FP32, BF16 or FP16; no FP64 on the per-site path.  Sites
-//    whose FP32 dS is near or above the Ehrenfests' threshold are recorded;
-//    the tail kernel recomputes their FP64 key from the pre-step populations.
-//    Sums are kept per thread in FP32 (mass as rho - rho_ref), folded into
-//    FP64 every 128 rows, and reduced per block.
+//    form, stored as FP32, BF16 or FP16; no FP64 on the per-site path.  A site
+//    whose FP32 dS is near or above the Ehrenfests' threshold is recorded with
+//    its FP64 key, evaluated by the warp from the pre-step populations.
+//    Sums are kept per thread in FP32 (mass as rho - rho_ref); at the end of
+//    a work item (and every 128 rows) the warp adds them up in a fixed order
+//    and folds the totals exactly into 128-bit fixed point, so the step's
+//    statistics do not depend on which warp ran which item.
+//  * Load balance: warps of one SM progress at different rates (the warp
+//    scheduler favours older warps), so a static split leaves most warps idle
+//    at the end of the launch.  The launch is one wave of resident warps; each
+//    warp runs its first item, then takes further (short) items from a
+//    counter in device memory until none are left.
 #include <algorithm>
 #include <type_traits>
 
 #include "internal.h"
+#include "keys.cuh"
 #include "lattice.cuh"
 
 namespace lbm {
@@ -46,16 +54,44 @@ constexpr int kWarps = 4;  // independent work items per block
 constexpr int kThreads = 32 * kWarps;
 constexpr int kBlocksPerSM = 5;  // resident FP32 blocks per SM (16-bit: 4; batched: 3)
 constexpr int kRing = 2;         // FP32: rows in each warp's shared-memory load ring
+constexpr int kWin = 72;         // FP32: columns of each plane copied per row (16-byte aligned window)
 constexpr int kCarveout = -1;    // preferred shared-memory carveout in percent (-1: the driver's choice)
 constexpr int kStripCols = 62;   // finished columns per strip (64 computed)
 constexpr int kMinSegRows = 16;  // shortest row segment (the two halo rows cost 2 / segment)
-constexpr int kFoldRows = 128;   // FP32 partial sums are folded into FP64 every kFoldRows rows
+constexpr int kFoldRows = 128;   // FP32 partial sums are folded into fixed point every kFoldRows rows
+constexpr int kItemsPerWarp = 5; // dynamic work: about this many items per resident warp
 constexpr unsigned kFull = 0xffffffffu;
 
 struct RowState {
     float2 ds, pp;
     bool bad_a, bad_b, cand_a, cand_b;
 };
+
+// Adds the FP32 value v exactly to acc, a 128-bit two's-complement fixed-point
+// number in units of 2^-64 (bits of v below 2^-64 are dropped, truncating
+// toward zero).  A nonfinite v, or |v| >= 2^63, sets `bad` instead.
+__device__ __forceinline__ void fx_add(unsigned __int128 &acc, float v, bool &bad)
+{
+    const unsigned u = __float_as_uint(v);
+    const int e = (int)((u >> 23) & 0xffu);  // biased exponent: v = +-m 2^(e - 150)
+    if (e == 0xff) {
+        bad = true;
+        return;
+    }
+    if (e == 0) return;  // zero or subnormal (below 2^-126)
+    const unsigned long long m = (u & 0x7fffffu) | 0x800000u;
+    const int sh = e - 150 + 64;  // v = +-m 2^sh units
+    if (sh >= 104) {
+        bad = true;
+        return;
+    }
+    unsigned __int128 x = 0;
+    if (sh >= 0)
+        x = (unsigned __int128)m << sh;
+    else if (sh > -24)
+        x = (unsigned __int128)(m >> -sh);
+    acc += (u >> 31) ? (unsigned __int128)0 - x : x;
+}
 
 // Sorted column (lo <= mid <= hi) of three values.
 __device__ __forceinline__ void sort3(float a, float b, float c, float &lo, float &mid, float &hi)
@@ -67,14 +103,14 @@ __device__ __forceinline__ void sort3(float a, float b, float c, float &lo, floa
     hi = fmaxf(t2, t3);
 }
 
-// Asynchronous 4-byte global -> shared copy (the lane's own ring slot) and its
-// group bookkeeping; a thread only ever reads back what it copied itself.
-__device__ __forceinline__ void cp_async4(void *dst_smem, const void *src)
+// Asynchronous 16-byte global -> shared copy (both addresses 16-byte aligned).
+__device__ __forceinline__ void cp_async16(void *dst_smem, const void *src)
 {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst_smem)),
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst_smem)),
                  "l"(src)
                  : "memory");
 }
+// cp.async group bookkeeping (per thread).
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
@@ -105,12 +141,11 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : (sizeof(S) == 4 ? kBlo
 {
     using O = F2;
     // FP32 storage streams through a per-warp ring of shared-memory rows filled
-    // by asynchronous copies (kRing - 1 rows in flight, no registers held);
-    // 16-bit storage (2-byte elements, below the copy granule) loads into
-    // registers one row ahead
+    // by 16-byte asynchronous copies (kRing - 1 rows in flight, no registers
+    // held); 16-bit storage loads into registers one row ahead
     constexpr bool kAsync = sizeof(S) == 4;
-    __shared__ float2 ring[kAsync ? kWarps : 1][kAsync ? kRing : 1][9][32];
-    __shared__ double red[kWarps][P_NSTAT];
+    __shared__ __align__(16) float ring[kAsync ? kWarps : 1][kAsync ? kRing : 1][9][kWin];
+    __shared__ unsigned long long sfx[kWarps][kFxWords];
     __shared__ __align__(16) FusedArgs sA;
     int bid = (int)blockIdx.x;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
@@ -127,10 +162,28 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : (sizeof(S) == 4 ? kBlo
 
     float s_mass = 0.f, s_ds = 0.f, s_in = 0.f, s_lim = 0.f;
     int n_pos = 0, n_med = 0, n_bad = 0, n_sites = 0, rows_acc = 0;
-    double acc_mass = 0.0, acc_ds = 0.0, acc_in = 0.0, acc_lim = 0.0;
+    // fixed-point totals: lane 0 mass, lane 8 dS, lane 16 dS_in, lane 24 dS_lim
+    unsigned __int128 fx_acc = 0;
+    bool fx_bad = false;
+    // Adds the lanes' FP32 sums in a fixed order (a butterfly in which each
+    // level halves the sums a lane carries) and folds the four totals into
+    // fixed point; every lane takes part.
+    auto flush = [&]() {
+        const bool hi16 = (lane & 16) != 0, hi8 = (lane & 8) != 0;
+        float x0 = hi16 ? s_in : s_mass, x1 = hi16 ? s_lim : s_ds;
+        const float y0 = hi16 ? s_mass : s_in, y1 = hi16 ? s_ds : s_lim;
+        x0 += __shfl_xor_sync(kFull, y0, 16);
+        x1 += __shfl_xor_sync(kFull, y1, 16);
+        float z = hi8 ? x1 : x0;
+        z += __shfl_xor_sync(kFull, hi8 ? x0 : x1, 8);
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) z += __shfl_xor_sync(kFull, z, o);
+        if ((lane & 7) == 0) fx_add(fx_acc, z, fx_bad);
+        s_mass = s_ds = s_in = s_lim = 0.f;
+    };
 
-    const int item = bid * kWarps + warp;
-    if (item < A.items) {
+    int item = bid * kWarps + warp;
+    while (item < A.items) {
         const S *__restrict__ src = (const S *)A.src;
         S *__restrict__ dst = (S *)A.dst;
         const int nx = p.nx, ny = p.ny, pitch = p.pitch;
@@ -277,8 +330,8 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : (sizeof(S) == 4 ? kBlo
             n_bad += (int)(oa && bad_a) + (int)(ob && bad_b);
             if (pos_on) n_pos += (int)(oa && st.pp.x < 1.f) + (int)(ob && st.pp.y < 1.f);
             if (__any_sync(kFull, (oa && bad_a) || (ob && bad_b)) && lane == 0) atomicOr(p.status, kStatNonfinite);
-            // Ehrenfests' candidates: the tail kernel recomputes the FP64 key of
-            // every site recorded here from the pre-step populations
+            // Ehrenfests' candidates (FP32 dS near or above the threshold); the
+            // FP64 key decides
             st.cand_a = lim_ehr && !bad_a && oa && ds.x > A.thr_e;
             st.cand_b = lim_ehr && !bad_b && ob && ds.y > A.thr_e;
             st.bad_a = bad_a;
@@ -287,17 +340,49 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : (sizeof(S) == 4 ? kBlo
             return st;
         };
 
-        auto record = [&](int y, int x, float phi) {
-            const int slot = atomicAdd(p.cand_count, 1);
-            if (slot < p.cand_cap) {
-                Cand cd;
-                cd.key = 0.0;
-                cd.phi = (double)phi;
-                cd.site = y * nx + x;
-                cd.pad = 0;
-                p.cand[slot] = cd;
-            } else {
-                atomicOr(p.status, kStatCandOverflow);
+        // Ehrenfests' candidates of row y (flags ca / cb of the lanes' two
+        // columns), one at a time: the whole warp evaluates the candidate's
+        // FP64 key dS(f') from the pre-step populations (the FP64 path's
+        // operations and order), and lane 0 records it (key -1 when the site
+        // is at or below the threshold or cannot be limited)
+        auto record = [&](int y, bool ca, bool cb, float phi_a, float phi_b) {
+            unsigned ma = __ballot_sync(kFull, ca), mb = __ballot_sync(kFull, cb);
+            while (ma | mb) {  // the same for the whole warp
+                const bool first = ma != 0;
+                const int l = __ffs(first ? ma : mb) - 1;
+                if (first)
+                    ma &= ma - 1;
+                else
+                    mb &= mb - 1;
+                const int site = y * nx + kStripCols * strip - 1 + l + (first ? 0 : 32);
+                const float phi = __shfl_sync(kFull, first ? phi_a : phi_b, l);
+                KeyGeom kg;
+                kg.nx = nx;
+                kg.ny = ny;
+                kg.pitch = pitch;
+                kg.boundary = p.boundary;
+                kg.plane = p.plane;
+                kg.a = p.a;
+                kg.rw0 = p.rw[0];
+                kg.rw1 = p.rw[1];
+                kg.rw5 = p.rw[5];
+                kg.lid4 = p.lid[4];
+                kg.lid7 = p.lid[7];
+                kg.lid8 = p.lid[8];
+                const double key = key_dS9_warp<S>(kg, src, site, p.delta_e);
+                if (lane == 0) {
+                    const int slot = atomicAdd(p.cand_count, 1);
+                    if (slot < p.cand_cap) {
+                        Cand cd;
+                        cd.key = key;
+                        cd.phi = (double)phi;
+                        cd.site = site;
+                        cd.pad = 0;
+                        p.cand[slot] = cd;
+                    } else {
+                        atomicOr(p.status, kStatCandOverflow);
+                    }
+                }
             }
         };
 
@@ -356,16 +441,9 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : (sizeof(S) == 4 ? kBlo
                 }
             }
             n_med += (int)(act_a && pm_a < 1.f) + (int)(act_b && pm_b < 1.f);
-            if (__any_sync(kFull, st.cand_a || st.cand_b)) {
-                if (st.cand_a) record(y, xa, phi_a);
-                if (st.cand_b) record(y, xb, phi_b);
-            }
-            if (rown && ++rows_acc == kFoldRows) {
-                acc_mass += (double)s_mass;
-                acc_ds += (double)s_ds;
-                acc_in += (double)s_in;
-                acc_lim += (double)s_lim;
-                s_mass = s_ds = s_in = s_lim = 0.f;
+            if (__any_sync(kFull, st.cand_a || st.cand_b)) record(y, st.cand_a, st.cand_b, phi_a, phi_b);
+            if (rown && ++rows_acc == kFoldRows) {  // the same for the whole warp
+                flush();
                 rows_acc = 0;
             }
         };
@@ -386,52 +464,64 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : (sizeof(S) == 4 ? kBlo
             prev = st;
         };
         if constexpr (kAsync) {
-            float2(*my)[9][32] = ring[warp];
-#pragma unroll
-            for (int j = 0; j < kRing; ++j)
-#pragma unroll
-                for (int k = 0; k < 9; ++k) my[j][k][lane] = make_float2(0.f, 0.f);
-            __syncwarp();
-            // copies of the populations arriving at row q into ring slot j (rows
-            // outside the lattice are skipped; edge_row sets those links)
+            // Row q's populations arrive by 16-byte copies of the window of
+            // columns [cb, cb + kWin) of every plane k, from source row q - cy_k
+            // (lanes 0..17 copy one 16-byte chunk each); the lanes then read their
+            // two columns shifted by -cx_k.  cb is 16-byte aligned and at most the
+            // strip's first pulled column xa - 1 of lane 0; the window reaches
+            // past its last one, column xb + 1 of lane 31.
+            float(*my)[9][kWin] = ring[warp];
+            float *flat = &my[0][0][0];
+            for (int i = lane; i < kRing * 9 * kWin; i += 32) flat[i] = 0.f;
+            const int xa0 = kStripCols * strip - 1;  // lane 0's column
+            const int cb = (xa0 - 1) & ~3;
+            const int d0 = xa0 - cb + lane;  // window index of the lane's column a
+            const bool copier = lane < kWin / 4;
+            const int p2 = 2 * plane - pitch, p5 = 5 * plane - pitch, p6 = 6 * plane - pitch;
+            const int p4 = 4 * plane + pitch, p7 = 7 * plane + pitch, p8 = 8 * plane + pitch;
             int put = 0, get = 0;  // ring slots of the next row to copy and to read
             auto issue = [&](int q) {
                 if (q <= rc) {
-                    float2(*sl)[32] = my[put];
+                    float(*sl)[kWin] = my[put];
                     put = put + 1 == kRing ? 0 : put + 1;
-                    const S *ba = src + (long long)q * pitch + kLead + xa;
-                    auto cp = [&](int k, int off) {
-                        cp_async4(&sl[k][lane].x, ba + off);
-                        cp_async4(&sl[k][lane].y, ba + off + 32);
-                    };
-                    cp(0, 0);
-                    cp(1, o1);
-                    cp(3, o3);
-                    if (q >= 1) {
-                        cp(2, o2);
-                        cp(5, o5);
-                        cp(6, o6);
-                    }
-                    if (q + 1 < ny) {
-                        cp(4, o4);
-                        cp(7, o7);
-                        cp(8, o8);
+                    if (copier) {
+                        const S *ba = src + (long long)q * pitch + kLead + cb + 4 * lane;
+                        auto cp = [&](int k, int off) { cp_async16(&sl[k][4 * lane], ba + off); };
+                        cp(0, 0);
+                        cp(1, plane);
+                        cp(3, 3 * plane);
+                        if (q >= 1) {  // rows outside the lattice are skipped; edge_row sets those links
+                            cp(2, p2);
+                            cp(5, p5);
+                            cp(6, p6);
+                        }
+                        if (q + 1 < ny) {
+                            cp(4, p4);
+                            cp(7, p7);
+                            cp(8, p8);
+                        }
                     }
                 }
                 cp_async_commit();  // one group per row (empty past the last row)
             };
+            __syncwarp();
 #pragma unroll
             for (int j = 0; j < kRing - 1; ++j) issue(r0 + j);
             for (int r = r0; r - 1 < ye; ++r) {
                 RowState st{make_float2(0.f, 0.f), make_float2(1.f, 1.f), false, false, false, false};
                 if (r <= rc) {
-                    issue(r + kRing - 1);  // refills the slot row r-1 used
+                    __syncwarp();                // every lane is done with the slot row r-1 used
+                    issue(r + kRing - 1);        // refills it
                     cp_async_wait<kRing - 1>();  // this thread's copies of row r have landed
+                    __syncwarp();                // and so have the other lanes'
                     float2 g[9];
-                    const float2(*sl)[32] = my[get];
+                    const float *sb = &my[get][0][0] + d0;
                     get = get + 1 == kRing ? 0 : get + 1;
 #pragma unroll
-                    for (int k = 0; k < 9; ++k) g[k] = sl[k][lane];
+                    for (int k = 0; k < 9; ++k) {
+                        const int o = k * kWin - Lat<9>::cx(k);
+                        g[k] = make_float2(sb[o], sb[o + 32]);
+                    }
                     st = compute_row(r, g);
                 }
                 if (r - 1 >= ys) finalise_row(r - 1, prev, ds_m2, ds_m1, st.ds);
@@ -450,42 +540,51 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : (sizeof(S) == 4 ? kBlo
                 if (++r - 1 >= ye) break;
             }
         }
+        // the item's sums, then the next item
+        flush();
+        rows_acc = 0;
+        if (BATCHED || p.work == nullptr) break;
+        int next = 0;
+        if (lane == 0) next = (int)gridDim.x * kWarps + atomicAdd(p.work, 1);
+        item = __shfl_sync(kFull, next, 0);
     }
 
-    // Warp totals.  FP64 instructions are slow on this GPU and every warp
-    // reaches this point at about the same time, so the FP64 work is kept
-    // small: counts are summed as integers, and the four FP sums share one
-    // butterfly in which each level halves the sums a lane carries (lanes 0,
-    // 8, 16, 24 end with the mass, dS, dS_in and dS_lim totals; fixed order).
+    // Block row of fixed-point totals and counts: integer sums, so the order
+    // in which warps and blocks are added does not matter.
     const int tot_sites = __reduce_add_sync(kFull, n_sites), tot_pos = __reduce_add_sync(kFull, n_pos);
     const int tot_med = __reduce_add_sync(kFull, n_med), tot_bad = __reduce_add_sync(kFull, n_bad);
-    {
-        const double v0 = acc_mass + (double)s_mass, v1 = acc_ds + (double)s_ds;
-        const double v2 = acc_in + (double)s_in, v3 = acc_lim + (double)s_lim;
-        const bool hi16 = (lane & 16) != 0, hi8 = (lane & 8) != 0;
-        double x0 = hi16 ? v2 : v0, x1 = hi16 ? v3 : v1;
-        const double y0 = hi16 ? v0 : v2, y1 = hi16 ? v1 : v3;
-        x0 += __shfl_xor_sync(kFull, y0, 16);
-        x1 += __shfl_xor_sync(kFull, y1, 16);
-        double z = hi8 ? x1 : x0;
-        z += __shfl_xor_sync(kFull, hi8 ? x0 : x1, 8);
-#pragma unroll
-        for (int o = 4; o > 0; o >>= 1) z += __shfl_xor_sync(kFull, z, o);
-        if ((lane & 7) == 0) {
-            const int stat = lane >> 3;  // P_MASS, P_SUM_DS, P_SUM_IN, P_DS_LIM
-            red[warp][stat] = stat == P_MASS ? fma((double)tot_sites, (double)p.rho_ref, z) : z;
-        }
-        if (lane == 0) {
-            red[warp][P_NPOS] = (double)tot_pos;
-            red[warp][P_NMED] = (double)tot_med;
-            red[warp][P_NBAD] = (double)tot_bad;
-        }
+    const unsigned bad_lanes = __ballot_sync(kFull, fx_bad);
+    if ((lane & 7) == 0) {
+        const int stat = lane >> 3;  // P_MASS .. P_DS_LIM
+        sfx[warp][FX_SUM + 2 * stat] = (unsigned long long)fx_acc;
+        sfx[warp][FX_SUM + 2 * stat + 1] = (unsigned long long)(fx_acc >> 64);
+    }
+    if (lane == 0) {
+        sfx[warp][FX_SITES] = (unsigned long long)tot_sites;
+        sfx[warp][FX_NPOS] = (unsigned long long)tot_pos;
+        sfx[warp][FX_NMED] = (unsigned long long)tot_med;
+        sfx[warp][FX_NBAD] = (unsigned long long)tot_bad;
+        sfx[warp][FX_BAD] = (bad_lanes & 1u) | ((bad_lanes >> 7) & 2u) | ((bad_lanes >> 14) & 4u) |
+                            ((bad_lanes >> 21) & 8u);
     }
     __syncthreads();
-    if (t < P_NSTAT) {
-        double v = 0.0;
-        for (int w = 0; w < kWarps; ++w) v += red[w][t];
-        p.partials[(long long)bid * P_NSTAT + t] = v;
+    if (t < kFxWords) {
+        unsigned long long *row = reinterpret_cast<unsigned long long *>(p.partials) + (long long)bid * kFxWords;
+        if (t < 4) {
+            unsigned __int128 v = 0;
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w)
+                v += ((unsigned __int128)sfx[w][FX_SUM + 2 * t + 1] << 64) | sfx[w][FX_SUM + 2 * t];
+            row[FX_SUM + 2 * t] = (unsigned long long)v;
+            row[FX_SUM + 2 * t + 1] = (unsigned long long)(v >> 64);
+        } else if (t >= FX_SITES && t <= FX_BAD) {
+            unsigned long long v = 0;
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) v = t == FX_BAD ? (v | sfx[w][t]) : v + sfx[w][t];
+            row[t] = v;
+        } else if (t > FX_BAD) {
+            row[t] = 0;
+        }
     }
 }
 
@@ -586,9 +685,21 @@ int fused_make_args(const StepParams &p, const void *src, void *dst, int seg_row
 template <typename S>
 cudaError_t launch_fused_d2q9(const StepParams &p, const S *src, S *dst, int *nblocks, cudaStream_t s)
 {
+    // Dynamic work: one wave of resident blocks over short row segments, about
+    // kItemsPerWarp items per warp; warps past their first item take the next
+    // from the counter p.work (cleared by the tail kernel after the launch).
+    const int slots = fused_slots((int)sizeof(S), false);
+    int rows = 0;
+    if (p.work != nullptr) {
+        const long long strips = (p.nx + kStripCols - 1) / kStripCols;
+        rows = (int)std::max<long long>(kMinSegRows, (strips * p.ny + (long long)kItemsPerWarp * slots - 1) /
+                                                         ((long long)kItemsPerWarp * slots));
+    }
     FusedArgs A;
-    *nblocks = fused_make_args(p, src, dst, 0, fused_slots((int)sizeof(S), false), &A);
-    return launch_lim<S>(A, A.blocks, s);
+    fused_make_args(p, src, dst, rows, slots, &A);
+    const int blocks = p.work != nullptr ? std::min(A.blocks, slots / kWarps) : A.blocks;
+    *nblocks = blocks;
+    return launch_lim<S>(A, blocks, s);
 }
 
 template cudaError_t launch_fused_d2q9<float>(const StepParams &, const float *, float *, int *, cudaStream_t);
