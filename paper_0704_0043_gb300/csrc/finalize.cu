@@ -16,6 +16,7 @@
 #include <type_traits>
 
 #include "internal.h"
+#include "keys.cuh"
 #include "lattice.cuh"
 
 namespace lbm {
@@ -134,8 +135,9 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, 
         s_valid = 0;
     }
     if (p.fixed) {
-        // fixed-point rows of the fused kernel: exact integer sums, so the
-        // order does not matter.  Each 128-byte row is read as eight 16-byte
+        // fixed-point accumulator rows of the fused kernel (kFxRows of them):
+        // exact integer sums, so the order does not matter; the rows are
+        // cleared for the next step once read.  Each 128-byte row is read as eight 16-byte
         // chunks (coalesced: lane l takes chunk l % 8 of a row); chunk c < 4
         // is FP statistic c (low, high word), chunk 4 the site and positivity
         // counts, chunk 5 the median and nonfinite counts, chunk 6 the bits.
@@ -144,12 +146,12 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, 
         unsigned long long u0 = 0, u1 = 0;
         const ulonglong2 *chunks = reinterpret_cast<const ulonglong2 *>(p.partials);
         constexpr int kStride = kFinThreads / 8;  // rows per pass of the block
-        for (int r0 = t >> 3; r0 < p.nblocks; r0 += 8 * kStride) {
+        for (int r0 = t >> 3; r0 < kFxRows; r0 += 8 * kStride) {
             ulonglong2 w[8];  // eight loads in flight, then the sums
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 const int r = r0 + i * kStride;
-                w[i] = r < p.nblocks ? chunks[(long long)r * (kFxWords / 2) + c] : make_ulonglong2(0ull, 0ull);
+                w[i] = r < kFxRows ? chunks[(long long)r * (kFxWords / 2) + c] : make_ulonglong2(0ull, 0ull);
             }
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
@@ -184,6 +186,8 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, 
             }
         }
         __syncthreads();
+        if (t < kFxRows * kFxWords / 2)
+            reinterpret_cast<ulonglong2 *>(p.partials)[t] = make_ulonglong2(0ull, 0ull);
         if (t < 9) {  // t < 4: FP statistic t; 4..7: the counts; 8: the nonfinite bits
             unsigned __int128 a = 0;
             unsigned long long b = 0;
@@ -236,10 +240,32 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, 
     const long long k = p.k_max;
 
     // candidate keys: FP64 dS(f'), written with the candidates by the step
-    // kernels (sites at or below the threshold carry -1)
-    if (small) {
-        for (int i = t; i < n; i += kFinThreads) {
-            const Cand c = p.cand[i];
+    // kernels (sites at or below the threshold carry -1); the fused kernel
+    // leaves NaN where a warp had more candidates than it keys itself, and
+    // those are keyed here, one thread per candidate, with the same operations
+    constexpr bool kLowPrec = !std::is_same<S, double>::value;
+    for (int i = t; i < n; i += kFinThreads) {
+        Cand c = p.cand[i];
+        if constexpr (kLowPrec && Q == 9) {
+            if (isnan(c.key)) {
+                KeyGeom kg;
+                kg.nx = p.nx;
+                kg.ny = p.ny;
+                kg.pitch = p.pitch;
+                kg.boundary = p.boundary;
+                kg.plane = p.plane;
+                kg.a = p.a;
+                kg.rw0 = p.rw[0];
+                kg.rw1 = p.rw[1];
+                kg.rw5 = p.rw[5];
+                kg.lid4 = p.lid[4];
+                kg.lid7 = p.lid[7];
+                kg.lid8 = p.lid[8];
+                c.key = key_dS9_lane<S>(kg, (const S *)p.src, c.site, p.delta_e);
+                p.cand[i].key = c.key;
+            }
+        }
+        if (small) {
             s_key[i] = c.key;
             s_site[i] = c.site;
         }

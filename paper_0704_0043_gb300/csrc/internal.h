@@ -38,7 +38,11 @@ enum { P_MASS = 0, P_SUM_DS, P_SUM_IN, P_DS_LIM, P_NPOS, P_NMED, P_NBAD, P_NSTAT
 // statistic s = P_MASS (sum of rho - rho_ref) .. P_DS_LIM; the site and
 // limiter counts; and a bit per FP statistic that met a nonfinite or
 // out-of-range (>= 2^63) item sum.
+// Each block of the fused kernel adds its row atomically into accumulator row
+// (block % kFxRows) of its lattice's partials; the tail kernel sums the
+// kFxRows rows and clears them.
 constexpr int kFxWords = 16;
+constexpr int kFxRows = 8;
 enum { FX_SUM = 0, FX_SITES = 8, FX_NPOS, FX_NMED, FX_NBAD, FX_BAD };
 
 // Ehrenfests' candidate: FP64 key dS(f'), phi of the limiter pass, site index.
@@ -78,7 +82,7 @@ struct StepParams {
     Cand *cand;
     int *cand_count;
     int cand_cap;
-    double *partials;          // [blocks][P_NSTAT] doubles; fused kernel: [blocks][kFxWords] fixed-point words
+    double *partials;          // [blocks][P_NSTAT] doubles; fused kernel: [kFxRows][kFxWords] fixed-point accumulators
     unsigned *status;
     int *work;                 // fused kernel: counter of work items handed out (nullptr: one item per warp)
     double *ds_out;            // optional FP64 dS(f') field (nx * ny) or nullptr
@@ -94,7 +98,7 @@ struct FinalParams {
     int collide;
     int nx, ny, pitch;
     long long plane;
-    const double *partials;
+    double *partials;          // fused kernel: the accumulator rows, cleared once read
     Cand *cand;
     int *cand_count;
     int cand_cap;

@@ -88,4 +88,43 @@ __device__ __noinline__ double key_dS9_warp(const KeyGeom p, const S *src, int s
     return !bad && isfinite(s) && s > delta_e ? s : -1.0;
 }
 
+// The same key evaluated by one thread alone (lane-parallel keying of many
+// candidates: each lane keys its own site).  The operations and their order
+// are those of key_dS9_warp, so both give the same bits.
+template <typename S>
+__device__ __noinline__ double key_dS9_lane(const KeyGeom p, const S *src, int site, double delta_e)
+{
+    using A = Ar<double>;
+    const int x = site % p.nx, y = site / p.nx;
+    double fin[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) fin[k] = pull_one_f64<S>(p, src, x, y, k);
+    double rho, ux, uy;
+    moments9<double>(fin, rho, ux, uy);
+    const double usq = A::add(A::mul(ux, ux), A::mul(uy, uy));
+    const double tail = A::mul(A::mul(3.0, usq), 0.5);
+    bool bad = !(rho > 0.0) || !isfinite(rho) || !isfinite(ux) || !isfinite(uy);
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const double c = k == 0 ? 0.0
+                       : k == 1 ? ux
+                       : k == 2 ? uy
+                       : k == 3 ? -ux
+                       : k == 4 ? -uy
+                       : k == 5 ? A::add(ux, uy)
+                       : k == 6 ? A::sub(uy, ux)
+                       : k == 7 ? -A::add(ux, uy)
+                                : A::sub(ux, uy);
+        double poly = A::add(A::add(1.0, A::mul(3.0, c)), A::mul(A::mul(9.0, A::mul(c, c)), 0.5));
+        poly = A::sub(poly, tail);
+        const double fs = A::mul(A::mul(rho, Lat<9>::w(k)), poly);
+        const double fp = A::add(fs, A::mul(p.a, A::sub(fs, fin[k])));
+        const double d = A::sub(fp, fs);
+        s = A::add(s, A::div(A::mul(d, d), fs));
+        bad = bad || !(fs > 0.0) || !isfinite(fin[k]);
+    }
+    return !bad && isfinite(s) && s > delta_e ? s : -1.0;
+}
+
 }  // namespace lbm

@@ -131,7 +131,7 @@ Sizes sizes_for(const lbm_config &c)
     z.rows = tiled_blocks(c);
     z.partials = (size_t)z.rows * P_NSTAT * sizeof(double);
     if (fused_applies(c))
-        z.partials = std::max(z.partials, (size_t)fused_d2q9_blocks(c.nx, c.ny) * kFxWords * sizeof(unsigned long long));
+        z.partials = std::max(z.partials, (size_t)kFxRows * kFxWords * sizeof(unsigned long long));
     z.ring_len = std::max(1, c.stats_history);
     z.ring = (size_t)z.ring_len * sizeof(DevStats);
     return z;
@@ -325,6 +325,8 @@ lbm_status reset_counters(lbm_ctx *c)
     CK(c, cudaMemsetAsync(c->counters, 0, 2 * sizeof(long long), c->stream));
     CK(c, cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->stream));
     CK(c, cudaMemsetAsync(c->counts, 0, 4 * sizeof(int), c->stream));
+    if (fused_applies(c->cfg))  // the fused kernel's fixed-point accumulators
+        CK(c, cudaMemsetAsync(c->partials, 0, (size_t)kFxRows * kFxWords * sizeof(unsigned long long), c->stream));
     CK(c, cudaMemsetAsync(c->ring, 0, (size_t)c->ring_len * sizeof(DevStats), c->stream));
     return LBM_OK;
 }

@@ -60,6 +60,8 @@ constexpr int kStripCols = 62;   // finished columns per strip (64 computed)
 constexpr int kMinSegRows = 16;  // shortest row segment (the two halo rows cost 2 / segment)
 constexpr int kFoldRows = 128;   // FP32 partial sums are folded into fixed point every kFoldRows rows
 constexpr int kItemsPerWarp = 5; // dynamic work: about this many items per resident warp
+constexpr int kLaneKeys = 3;     // candidates of an item from which each lane keys its own
+constexpr int kCandList = 32;    // candidates a warp keys itself per item (the tail keys the rest)
 constexpr unsigned kFull = 0xffffffffu;
 
 struct RowState {
@@ -146,6 +148,7 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : (sizeof(S) == 4 ? kBlo
     constexpr bool kAsync = sizeof(S) == 4;
     __shared__ __align__(16) float ring[kAsync ? kWarps : 1][kAsync ? kRing : 1][9][kWin];
     __shared__ unsigned long long sfx[kWarps][kFxWords];
+    __shared__ int cand_list[kWarps][kCandList];  // candidate slots of the warp's current item
     __shared__ __align__(16) FusedArgs sA;
     int bid = (int)blockIdx.x;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
@@ -181,6 +184,9 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : (sizeof(S) == 4 ? kBlo
         if ((lane & 7) == 0) fx_add(fx_acc, z, fx_bad);
         s_mass = s_ds = s_in = s_lim = 0.f;
     };
+
+    int *list = cand_list[warp];
+    int n_list = 0;  // candidates recorded in the current item (the same for the whole warp)
 
     int item = bid * kWarps + warp;
     while (item < A.items) {
@@ -341,49 +347,33 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : (sizeof(S) == 4 ? kBlo
         };
 
         // Ehrenfests' candidates of row y (flags ca / cb of the lanes' two
-        // columns), one at a time: the whole warp evaluates the candidate's
-        // FP64 key dS(f') from the pre-step populations (the FP64 path's
-        // operations and order), and lane 0 records it (key -1 when the site
-        // is at or below the threshold or cannot be limited)
+        // columns) are recorded at once without their key (NaN); the warp
+        // keeps their slots in its list and keys them when the item is done,
+        // away from the row loop's registers
         auto record = [&](int y, bool ca, bool cb, float phi_a, float phi_b) {
-            unsigned ma = __ballot_sync(kFull, ca), mb = __ballot_sync(kFull, cb);
-            while (ma | mb) {  // the same for the whole warp
-                const bool first = ma != 0;
-                const int l = __ffs(first ? ma : mb) - 1;
-                if (first)
-                    ma &= ma - 1;
-                else
-                    mb &= mb - 1;
-                const int site = y * nx + kStripCols * strip - 1 + l + (first ? 0 : 32);
-                const float phi = __shfl_sync(kFull, first ? phi_a : phi_b, l);
-                KeyGeom kg;
-                kg.nx = nx;
-                kg.ny = ny;
-                kg.pitch = pitch;
-                kg.boundary = p.boundary;
-                kg.plane = p.plane;
-                kg.a = p.a;
-                kg.rw0 = p.rw[0];
-                kg.rw1 = p.rw[1];
-                kg.rw5 = p.rw[5];
-                kg.lid4 = p.lid[4];
-                kg.lid7 = p.lid[7];
-                kg.lid8 = p.lid[8];
-                const double key = key_dS9_warp<S>(kg, src, site, p.delta_e);
-                if (lane == 0) {
-                    const int slot = atomicAdd(p.cand_count, 1);
+            auto put = [&](bool c, int x, float phi) {
+                int slot = -1;
+                if (c) {
+                    slot = atomicAdd(p.cand_count, 1);
                     if (slot < p.cand_cap) {
                         Cand cd;
-                        cd.key = key;
+                        cd.key = __longlong_as_double(0x7ff8000000000000LL);
                         cd.phi = (double)phi;
-                        cd.site = site;
+                        cd.site = y * nx + x;
                         cd.pad = 0;
                         p.cand[slot] = cd;
                     } else {
                         atomicOr(p.status, kStatCandOverflow);
+                        slot = -1;
                     }
                 }
-            }
+                const unsigned m = __ballot_sync(kFull, slot >= 0);
+                const int at = n_list + __popc(m & ((1u << lane) - 1u));
+                if (slot >= 0 && at < kCandList) list[at] = slot;
+                n_list += __popc(m);
+            };
+            put(ca, xa, phi_a);
+            put(cb, xb, phi_b);
         };
 
         // Row y: median of dS (rows y-1, y, y+1 in dm, d0, dp), phi = min(phi_pos,
@@ -540,6 +530,43 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : (sizeof(S) == 4 ? kBlo
                 if (++r - 1 >= ye) break;
             }
         }
+        // FP64 keys dS(f') of the item's candidates, from the pre-step
+        // populations with the FP64 path's operations and order (-1 when the
+        // site is at or below the threshold or cannot be limited).  A few are
+        // keyed one at a time by the whole warp (a lane per direction, the
+        // shortest latency), more lane-parallel; past kCandList the tail
+        // kernel keys the rest.
+        if (n_list > 0) {  // the same for the whole warp
+            KeyGeom kg;
+            kg.nx = nx;
+            kg.ny = ny;
+            kg.pitch = pitch;
+            kg.boundary = p.boundary;
+            kg.plane = p.plane;
+            kg.a = p.a;
+            kg.rw0 = p.rw[0];
+            kg.rw1 = p.rw[1];
+            kg.rw5 = p.rw[5];
+            kg.lid4 = p.lid[4];
+            kg.lid7 = p.lid[7];
+            kg.lid8 = p.lid[8];
+            const int n = min(n_list, kCandList);
+            __syncwarp();
+            if (n >= kLaneKeys) {
+                if (lane < n) {
+                    const int slot = list[lane];
+                    p.cand[slot].key = key_dS9_lane<S>(kg, src, p.cand[slot].site, p.delta_e);
+                }
+            } else {
+                for (int i = 0; i < n; ++i) {
+                    const int slot = list[i];
+                    const double key = key_dS9_warp<S>(kg, src, p.cand[slot].site, p.delta_e);
+                    if (lane == 0) p.cand[slot].key = key;
+                }
+            }
+            __syncwarp();
+            n_list = 0;
+        }
         // the item's sums, then the next item
         flush();
         rows_acc = 0;
@@ -568,22 +595,28 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : (sizeof(S) == 4 ? kBlo
                             ((bad_lanes >> 21) & 8u);
     }
     __syncthreads();
+    // added atomically to accumulator row bid % kFxRows of the instance (a
+    // 128-bit sum as two 64-bit adds with the carry passed on); the tail
+    // kernel reads the rows and clears them for the next step
     if (t < kFxWords) {
-        unsigned long long *row = reinterpret_cast<unsigned long long *>(p.partials) + (long long)bid * kFxWords;
+        unsigned long long *row = reinterpret_cast<unsigned long long *>(p.partials) + (long long)(bid % kFxRows) * kFxWords;
         if (t < 4) {
             unsigned __int128 v = 0;
 #pragma unroll
             for (int w = 0; w < kWarps; ++w)
                 v += ((unsigned __int128)sfx[w][FX_SUM + 2 * t + 1] << 64) | sfx[w][FX_SUM + 2 * t];
-            row[FX_SUM + 2 * t] = (unsigned long long)v;
-            row[FX_SUM + 2 * t + 1] = (unsigned long long)(v >> 64);
+            const unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)(v >> 64);
+            const unsigned long long old = atomicAdd(row + FX_SUM + 2 * t, lo);
+            atomicAdd(row + FX_SUM + 2 * t + 1, hi + (old + lo < old ? 1ull : 0ull));
         } else if (t >= FX_SITES && t <= FX_BAD) {
             unsigned long long v = 0;
 #pragma unroll
             for (int w = 0; w < kWarps; ++w) v = t == FX_BAD ? (v | sfx[w][t]) : v + sfx[w][t];
-            row[t] = v;
-        } else if (t > FX_BAD) {
-            row[t] = 0;
+            if (t == FX_BAD) {
+                if (v) atomicOr(row + t, v);
+            } else {
+                atomicAdd(row + t, v);
+            }
         }
     }
 }

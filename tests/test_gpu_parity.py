@@ -188,6 +188,31 @@ def test_fp32_one_step_against_oracle(nx, ny, kernel):
     np.testing.assert_allclose(st["dS_lim"], r.stats["dS_lim"], rtol=1e-3)
 
 
+@pytest.mark.parametrize("eps,delta_e,heavy_per", [(0.15, 1e-4, 0), (0.02, 2e-3, 100)])
+def test_fp32_dense_ehrenfest_candidates_against_oracle(eps, delta_e, heavy_per):
+    """Many Ehrenfests' candidates per work item: with delta = 1e-4 nearly every
+    site is one (each warp keys 32 of an item's candidates itself, the tail
+    kernel the rest); with one heavy site in 100 an item holds several (keyed
+    lane-parallel).  The selected set and the candidate count equal the
+    oracle's, and the populations agree."""
+    nx, ny = 300, 200
+    k = nx * ny // 1000
+    cfg = dict(lattice=lbm.D2Q9, nx=nx, ny=ny, boundary=lbm.BC_WALLS, beta=0.97, u_lid=0.1,
+               precision=lbm.FP32, limiters=ALL, delta_median=1e-4, delta_ehrenfest=delta_e,
+               k_max=k, kernel=lbm.KERNEL_FUSED)
+    g, oc = pair(**cfg)
+    f0 = rand_state(9, ny, nx, 77, eps=eps, heavy=nx * ny // heavy_per if heavy_per else 0)
+    g.set_populations(f0)
+    f = g.get_populations()
+    g.step(1)
+    r = oracle.step(oc, f)
+    st = g.stats()
+    assert st["n_cand"] == r.stats["n_cand"] and st["n_ehr"] == r.stats["n_ehr"] == k
+    assert r.stats["n_cand"] > (nx * ny // 2 if heavy_per == 0 else 5 * k)
+    np.testing.assert_array_equal(g.limited_sites(), np.sort(r.selected))
+    np.testing.assert_allclose(g.get_populations(), r.f, rtol=2e-5, atol=2e-7)
+
+
 def test_fused_and_tiled_fp32_agree_over_many_steps():
     """The two FP32 kernels evaluate every site with the same FP32 operations
     (tiles vs row-streaming strips, several strips and row segments, ragged
