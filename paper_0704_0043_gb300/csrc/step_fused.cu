@@ -52,9 +52,10 @@ namespace {
 
 constexpr int kWarps = 4;  // independent work items per block
 constexpr int kThreads = 32 * kWarps;
-constexpr int kBlocksPerSM = 5;  // resident FP32 blocks per SM (16-bit: 4; batched: 3)
+constexpr int kBlocksPerSM = 5;  // resident blocks per SM (batched: 3)
 constexpr int kRing = 2;         // FP32: rows in each warp's shared-memory load ring
 constexpr int kWin = 72;         // FP32: columns of each plane copied per row (16-byte aligned window)
+constexpr int kWin16 = 80;       // 16-bit storage: the same window, 8-column aligned
 constexpr int kCarveout = -1;    // preferred shared-memory carveout in percent (-1: the driver's choice)
 constexpr int kStripCols = 62;   // finished columns per strip (64 computed)
 constexpr int kMinSegRows = 16;  // shortest row segment (the two halo rows cost 2 / segment)
@@ -138,15 +139,16 @@ __device__ __forceinline__ Sides sides(float a, float b, int lane)
 // `table` as its block map[b].y; otherwise the single instance A0.
 // S: storage type of the deviations (float, __nv_bfloat16 or __half).
 template <typename S, bool MED, bool POS, bool BATCHED>
-__global__ void __launch_bounds__(kThreads, BATCHED ? 3 : (sizeof(S) == 4 ? kBlocksPerSM : 4))
+__global__ void __launch_bounds__(kThreads, BATCHED ? 3 : kBlocksPerSM)
     k_fused(const FusedArgs A0, const FusedArgs *__restrict__ table, const int2 *__restrict__ map)
 {
     using O = F2;
-    // FP32 storage streams through a per-warp ring of shared-memory rows filled
-    // by 16-byte asynchronous copies (kRing - 1 rows in flight, no registers
-    // held); 16-bit storage loads into registers one row ahead
-    constexpr bool kAsync = sizeof(S) == 4;
-    __shared__ __align__(16) float ring[kAsync ? kWarps : 1][kAsync ? kRing : 1][9][kWin];
+    // Rows stream through a per-warp ring of shared-memory rows filled by
+    // 16-byte asynchronous copies (kRing - 1 rows in flight, no registers
+    // held): windows of 72 FP32 or 80 16-bit columns
+    constexpr int kChunk = 16 / (int)sizeof(S);          // elements per 16-byte copy
+    constexpr int kWinS = sizeof(S) == 4 ? kWin : kWin16;  // window columns (a multiple of kChunk)
+    __shared__ __align__(16) S ring[kWarps][kRing][9][kWinS];
     __shared__ unsigned long long sfx[kWarps][kFxWords];
     __shared__ int cand_list[kWarps][kCandList];  // candidate slots of the warp's current item
     __shared__ __align__(16) FusedArgs sA;
@@ -438,45 +440,30 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : (sizeof(S) == 4 ? kBlo
             }
         };
 
-        // Iteration r computes row r from the loads issued one iteration
-        // earlier and finishes row r-1.
-        RowState prev{make_float2(0.f, 0.f), make_float2(1.f, 1.f), false, false, false, false};
-        float2 ds_m2 = make_float2(0.f, 0.f), ds_m1 = make_float2(0.f, 0.f);  // dS of rows r-2, r-1
-        auto body = [&](int r, float2(&cmp)[9], float2(&ld)[9]) {
-            RowState st{make_float2(0.f, 0.f), make_float2(1.f, 1.f), false, false, false, false};
-            if (r <= rc) {
-                if (r + 1 <= rc) load_row(r + 1, ld);
-                st = compute_row(r, cmp);
-            }
-            if (r - 1 >= ys) finalise_row(r - 1, prev, ds_m2, ds_m1, st.ds);
-            ds_m2 = ds_m1;
-            ds_m1 = st.ds;
-            prev = st;
-        };
-        if constexpr (kAsync) {
-            // Row q's populations arrive by 16-byte copies of the window of
-            // columns [cb, cb + kWin) of every plane k, from source row q - cy_k
-            // (lanes 0..17 copy one 16-byte chunk each); the lanes then read their
-            // two columns shifted by -cx_k.  cb is 16-byte aligned and at most the
-            // strip's first pulled column xa - 1 of lane 0; the window reaches
-            // past its last one, column xb + 1 of lane 31.
-            float(*my)[9][kWin] = ring[warp];
-            float *flat = &my[0][0][0];
-            for (int i = lane; i < kRing * 9 * kWin; i += 32) flat[i] = 0.f;
+        {
+            // Row q's populations arrive by 16-byte asynchronous copies of the
+            // window of columns [cb, cb + kWinS) of every plane k, from source
+            // row q - cy_k (one 16-byte chunk per copying lane); the lanes then
+            // read their two columns shifted by -cx_k.  cb is 16-byte aligned
+            // and at most the strip's first pulled column (lane 0's column - 1);
+            // the window reaches past its last (lane 31's second column + 1).
+            S(*my)[9][kWinS] = ring[warp];
+            S *flat = &my[0][0][0];
+            for (int i = lane; i < kRing * 9 * kWinS; i += 32) flat[i] = f2s<S>(0.f);
             const int xa0 = kStripCols * strip - 1;  // lane 0's column
-            const int cb = (xa0 - 1) & ~3;
+            const int cb = (xa0 - 1) & ~(kChunk - 1);
             const int d0 = xa0 - cb + lane;  // window index of the lane's column a
-            const bool copier = lane < kWin / 4;
+            const bool copier = lane < kWinS / kChunk;
             const int p2 = 2 * plane - pitch, p5 = 5 * plane - pitch, p6 = 6 * plane - pitch;
             const int p4 = 4 * plane + pitch, p7 = 7 * plane + pitch, p8 = 8 * plane + pitch;
             int put = 0, get = 0;  // ring slots of the next row to copy and to read
             auto issue = [&](int q) {
                 if (q <= rc) {
-                    float(*sl)[kWin] = my[put];
+                    S(*sl)[kWinS] = my[put];
                     put = put + 1 == kRing ? 0 : put + 1;
                     if (copier) {
-                        const S *ba = src + (long long)q * pitch + kLead + cb + 4 * lane;
-                        auto cp = [&](int k, int off) { cp_async16(&sl[k][4 * lane], ba + off); };
+                        const S *ba = src + (long long)q * pitch + kLead + cb + kChunk * lane;
+                        auto cp = [&](int k, int off) { cp_async16(&sl[k][kChunk * lane], ba + off); };
                         cp(0, 0);
                         cp(1, plane);
                         cp(3, 3 * plane);
@@ -494,6 +481,9 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : (sizeof(S) == 4 ? kBlo
                 }
                 cp_async_commit();  // one group per row (empty past the last row)
             };
+            // Iteration r computes row r and finishes row r-1.
+            RowState prev{make_float2(0.f, 0.f), make_float2(1.f, 1.f), false, false, false, false};
+            float2 ds_m2 = make_float2(0.f, 0.f), ds_m1 = make_float2(0.f, 0.f);  // dS of rows r-2, r-1
             __syncwarp();
 #pragma unroll
             for (int j = 0; j < kRing - 1; ++j) issue(r0 + j);
@@ -505,12 +495,12 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : (sizeof(S) == 4 ? kBlo
                     cp_async_wait<kRing - 1>();  // this thread's copies of row r have landed
                     __syncwarp();                // and so have the other lanes'
                     float2 g[9];
-                    const float *sb = &my[get][0][0] + d0;
+                    const S *sb = &my[get][0][0] + d0;
                     get = get + 1 == kRing ? 0 : get + 1;
 #pragma unroll
                     for (int k = 0; k < 9; ++k) {
-                        const int o = k * kWin - Lat<9>::cx(k);
-                        g[k] = make_float2(sb[o], sb[o + 32]);
+                        const int o = k * kWinS - Lat<9>::cx(k);
+                        g[k] = make_float2(s2f(sb[o]), s2f(sb[o + 32]));
                     }
                     st = compute_row(r, g);
                 }
@@ -520,15 +510,6 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : (sizeof(S) == 4 ? kBlo
                 prev = st;
             }
             cp_async_wait<0>();
-        } else {
-            float2 bufA[9], bufB[9];
-            load_row(r0, bufA);
-            for (int r = r0;;) {
-                body(r, bufA, bufB);
-                if (++r - 1 >= ye) break;
-                body(r, bufB, bufA);
-                if (++r - 1 >= ye) break;
-            }
         }
         // FP64 keys dS(f') of the item's candidates, from the pre-step
         // populations with the FP64 path's operations and order (-1 when the
@@ -670,7 +651,8 @@ cudaError_t launch_lim(const FusedArgs &A, int blocks, cudaStream_t s)
 
 int fused_slots(int elem_bytes, bool batched)
 {
-    const int per_sm = batched ? 3 : (elem_bytes == 4 ? kBlocksPerSM : 4);  // as in the launch bounds
+    (void)elem_bytes;  // every storage type runs kBlocksPerSM blocks per SM
+    const int per_sm = batched ? 3 : kBlocksPerSM;  // as in the launch bounds
     return per_sm * kWarps * sm_count();
 }
 
