@@ -262,9 +262,13 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, 
                 kg.lid7 = p.lid[7];
                 kg.lid8 = p.lid[8];
                 c.key = key_dS9_lane<S>(kg, (const S *)p.src, c.site, p.delta_e);
-                p.cand[i].key = c.key;
             }
         }
+        // below the threshold -> -1, so that from here on a key is valid
+        // exactly when its bit pattern is a positive integer (FP64 compares
+        // are slow on this GPU; positive doubles order like their patterns)
+        if (!(c.key > p.delta_e) && c.key != -1.0) c.key = -1.0;
+        if (!small || isnan(p.cand[i].key)) p.cand[i].key = c.key;
         if (small) {
             s_key[i] = c.key;
             s_site[i] = c.site;
@@ -275,7 +279,7 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, 
     auto site_of = [&](int i) -> int { return small ? s_site[i] : p.cand[i].site; };
     {
         int nv = 0;
-        for (int i = t; i < n; i += kFinThreads) nv += key_of(i) > p.delta_e;
+        for (int i = t; i < n; i += kFinThreads) nv += (long long)key_bits(key_of(i)) > 0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) nv += __shfl_down_sync(kFull, nv, o);
         if (lane == 0 && nv) atomicAdd(&s_valid, nv);
@@ -297,7 +301,7 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, 
                 for (int i = t; i < n; i += kFinThreads) {
                     const double key = key_of(i);
                     const unsigned long long u = key_bits(key);
-                    if (key > p.delta_e && (u & mask) == prefix) atomicAdd(&hist[(u >> shift) & 255u], 1u);
+                    if ((long long)u > 0 && (u & mask) == prefix) atomicAdd(&hist[(u >> shift) & 255u], 1u);
                 }
                 __syncthreads();
                 if (t == 0) {
@@ -326,7 +330,7 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, 
                 for (int i = t; i < n; i += kFinThreads) {
                     const double key = key_of(i);
                     const unsigned s = (unsigned)site_of(i);
-                    if (key > p.delta_e && key_bits(key) == kv && (s & smask) == sprefix)
+                    if ((long long)key_bits(key) > 0 && key_bits(key) == kv && (s & smask) == sprefix)
                         atomicAdd(&hist[(s >> shift) & 255u], 1u);
                 }
                 __syncthreads();
@@ -353,7 +357,7 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, 
         for (int i = t; i < n; i += kFinThreads) {
             const double key = key_of(i);
             const unsigned long long u = key_bits(key);
-            const bool chosen = key > p.delta_e && (take_all || u > kv || (u == kv && site_of(i) <= site_thr));
+            const bool chosen = (long long)u > 0 && (take_all || u > kv || (u == kv && site_of(i) <= site_thr));
             if (chosen) {
                 const int j = atomicAdd(&s_nsel, 1);
                 if (j < p.sel_cap) p.sel[j] = i;

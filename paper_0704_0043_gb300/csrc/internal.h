@@ -127,7 +127,7 @@ struct FusedArgs {
     StepParams p;
     const void *src;  // float, __nv_bfloat16 or __half deviations
     void *dst;
-    int strips, seg_rows, items, blocks;  // work items (warps): strips of 30 columns x row segments
+    int strips, seg_rows, items, blocks;  // work items: strips of 62 finished columns x row segments
     float a, b2, delta_m, thr_e, rho_ref;  // b2 = 2 beta
     float lid4, lid7, lid8;  // FP32 moving-wall terms of the links through the lid (hi + lo)
     float lo4, lo7, lo8;

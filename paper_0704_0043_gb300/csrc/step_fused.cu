@@ -1,40 +1,37 @@
-// step_fused.cu -- register-streaming fused D2Q9 step for the walled cavity.
+// step_fused.cu -- row-streaming fused D2Q9 step for the walled cavity.
 //
 // The same step as the tiled kernel (free flight with halfway bounce-back and
 // moving lid, Sec. 2 and Sec. 4.4.1; polynomial f*, Eq. polyeq2d; LBGK
 // collision, Eq. collLBGK; dS(f'), Sec. 3.6; positivity rule, Sec. 3.1; median
-// filter, Sec. 3.5; Ehrenfests' candidates, Sec. 3.2; FP64 sums, Sec. 3.4),
-// with the same per-site FP32 operations (lattice.cuh), organised so that
-// every warp streams its own part of the lattice with no shared memory and
-// no barrier:
+// filter, Sec. 3.5; Ehrenfests' candidates, Sec. 3.2; sums, Sec. 3.4), with
+// the same per-site FP32 operations (lattice.cuh), organised so that every
+// warp streams its own part of the lattice and never waits for another:
 //
-//  * Work item = one warp: a strip of 64 consecutive columns walked upward
-//    over a segment of rows.  Lane l carries two columns, l and l + 32 of the
-//    strip, and evaluates both sites with paired FP32 instructions (F2).  The
-//    strip's first and last columns recompute the neighbouring strips' edge
-//    columns; the other 62 are finished here.  Row r is computed, then row
-//    r-1 is finished: its 3 x 3 dS stencil is then in registers (three rows
-//    per lane, the side columns by warp shuffles).
+//  * Work item = a strip of 64 consecutive columns walked upward over a
+//    segment of rows by one warp.  Lane l carries two columns, l and l + 32
+//    of the strip, and evaluates both sites with paired FP32 instructions
+//    (F2).  The strip's first and last columns recompute the neighbouring
+//    strips' edge columns; the other 62 are finished here.  Row r is
+//    computed, then row r-1 is finished: its 3 x 3 dS stencil is then in
+//    registers (three rows per lane, the side columns by warp shuffles).
 //  * Free flight reads the populations arriving at row r straight from the
 //    source field: planes {0,1,3} of row r, {2,5,6} of row r-1, {4,7,8} of
-//    row r+1, each a coalesced 32-lane load, so every stored population is
-//    read from DRAM once (strips overlap by two columns, segments by two
-//    rows).  FP32 rows are copied asynchronously (cp.async) into a per-warp
-//    ring of shared-memory rows one row ahead of the arithmetic; each lane
-//    reads back only its own copies, so no barrier is needed.  16-bit rows
-//    are loaded into registers one row ahead (the row loop is unrolled twice
-//    so the two load buffers swap by name).
+//    row r+1, so every stored population is read from DRAM once (strips
+//    overlap by two columns, segments by two rows).  Each plane's row window
+//    arrives by 16-byte asynchronous copies (cp.async) in a per-warp ring of
+//    shared-memory rows one row ahead of the arithmetic; the lanes read their
+//    columns shifted by -cx.
 //  * The post-collision deviations are stored at once; a site whose phi
 //    (decided one row later) is below 1 reloads its row, recomputes the
 //    collision exactly and overwrites its populations with the limited ones.
 //  * Arithmetic is FP32 on the deviations g = f - rho_ref W in nonequilibrium
 //    form, stored as FP32, BF16 or FP16; no FP64 on the per-site path.  A site
-//    whose FP32 dS is near or above the Ehrenfests' threshold is recorded with
-//    its FP64 key, evaluated by the warp from the pre-step populations.
-//    Sums are kept per thread in FP32 (mass as rho - rho_ref); at the end of
-//    a work item (and every 128 rows) the warp adds them up in a fixed order
-//    and folds the totals exactly into 128-bit fixed point, so the step's
-//    statistics do not depend on which warp ran which item.
+//    whose FP32 dS is near or above the Ehrenfests' threshold is recorded, and
+//    its warp evaluates the FP64 key from the pre-step populations after the
+//    item.  Sums are kept per thread in FP32 (mass as rho - rho_ref); at the
+//    end of a work item (and every 128 rows) the warp adds them up in a fixed
+//    order and folds the totals exactly into 128-bit fixed point, so the
+//    step's statistics do not depend on which warp ran which item.
 //  * Load balance: warps of one SM progress at different rates (the warp
 //    scheduler favours older warps), so a static split leaves most warps idle
 //    at the end of the launch.  The launch is one wave of resident warps; each
@@ -259,10 +256,11 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : kBlocksPerSM)
                     g[k].x = v;
             }
         };
+        const bool wall_strip = __any_sync(kFull, (in_a && wall_a) || (in_b && wall_b));  // the same for the whole item
         auto edge_row = [&](int q, float2 g[9]) {
             const bool yedge = q == 0 || q == ny - 1;
             const bool ea = in_a && (wall_a || yedge), eb = in_b && (wall_b || yedge);
-            if (__any_sync(kFull, ea || eb)) {
+            if (wall_strip || yedge) {  // the same for the whole warp
                 const S *ba = src + (long long)q * pitch + kLead + xa;
                 if (ea) edge_col(q, xa, ba, g, false);
                 if (eb) edge_col(q, xb, ba + 32, g, true);
@@ -337,7 +335,6 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : kBlocksPerSM)
             n_sites += (int)oa + (int)ob;
             n_bad += (int)(oa && bad_a) + (int)(ob && bad_b);
             if (pos_on) n_pos += (int)(oa && st.pp.x < 1.f) + (int)(ob && st.pp.y < 1.f);
-            if (__any_sync(kFull, (oa && bad_a) || (ob && bad_b)) && lane == 0) atomicOr(p.status, kStatNonfinite);
             // Ehrenfests' candidates (FP32 dS near or above the threshold); the
             // FP64 key decides
             st.cand_a = lim_ehr && !bad_a && oa && ds.x > A.thr_e;
@@ -593,6 +590,7 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : kBlocksPerSM)
             unsigned long long v = 0;
 #pragma unroll
             for (int w = 0; w < kWarps; ++w) v = t == FX_BAD ? (v | sfx[w][t]) : v + sfx[w][t];
+            if (t == FX_NBAD && v != 0) atomicOr(p.status, kStatNonfinite);  // a site was nonfinite
             if (t == FX_BAD) {
                 if (v) atomicOr(row + t, v);
             } else {
