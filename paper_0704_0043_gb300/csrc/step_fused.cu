@@ -403,8 +403,14 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : kBlocksPerSM)
                     if (wall_a) med_a = mida;
                     if (wall_b) med_b = midb;
                 }
-                if (act_a && !st.bad_a) pm_a = phi_median<float>(st.ds.x, med_a, A.delta_m, p.median_mode);
-                if (act_b && !st.bad_b) pm_b = phi_median<float>(st.ds.y, med_b, A.delta_m, p.median_mode);
+                // phi_med < 1 needs dS above both delta and the median; the
+                // division and square root run only behind that (rare) test
+                const bool ca = act_a && !st.bad_a && st.ds.x > A.delta_m && st.ds.x > med_a;
+                const bool cb = act_b && !st.bad_b && st.ds.y > A.delta_m && st.ds.y > med_b;
+                if (__any_sync(kFull, ca || cb)) {
+                    if (ca) pm_a = phi_median<float>(st.ds.x, med_a, A.delta_m, p.median_mode);
+                    if (cb) pm_b = phi_median<float>(st.ds.y, med_b, A.delta_m, p.median_mode);
+                }
             }
             const float phi_a = act_a ? fminf(st.pp.x, pm_a) : 1.f, phi_b = act_b ? fminf(st.pp.y, pm_b) : 1.f;
             if (__any_sync(kFull, phi_a < 1.f || phi_b < 1.f)) {
