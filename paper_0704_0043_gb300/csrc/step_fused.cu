@@ -381,7 +381,13 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : kBlocksPerSM)
             const bool rown = y >= ys && y < ye;
             const bool act_a = own_a && rown, act_b = own_b && rown;
             float pm_a = 1.f, pm_b = 1.f;
-            if (med_on) {
+            // phi_med < 1 needs dS above delta (and above the median): the
+            // median is formed only when some site of the warp's row passes the
+            // first, cheap test (rare), and the division and square root only
+            // where both hold
+            const bool xa_on = act_a && !st.bad_a && st.ds.x > A.delta_m;
+            const bool xb_on = act_b && !st.bad_b && st.ds.y > A.delta_m;
+            if (med_on && __any_sync(kFull, xa_on || xb_on)) {
                 // 3 x 3 median from sorted columns: the median of (largest column
                 // minimum, median of the column medians, smallest column maximum);
                 // wall rows and columns take the near-wall stencils
@@ -403,14 +409,8 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : kBlocksPerSM)
                     if (wall_a) med_a = mida;
                     if (wall_b) med_b = midb;
                 }
-                // phi_med < 1 needs dS above both delta and the median; the
-                // division and square root run only behind that (rare) test
-                const bool ca = act_a && !st.bad_a && st.ds.x > A.delta_m && st.ds.x > med_a;
-                const bool cb = act_b && !st.bad_b && st.ds.y > A.delta_m && st.ds.y > med_b;
-                if (__any_sync(kFull, ca || cb)) {
-                    if (ca) pm_a = phi_median<float>(st.ds.x, med_a, A.delta_m, p.median_mode);
-                    if (cb) pm_b = phi_median<float>(st.ds.y, med_b, A.delta_m, p.median_mode);
-                }
+                if (xa_on && st.ds.x > med_a) pm_a = phi_median<float>(st.ds.x, med_a, A.delta_m, p.median_mode);
+                if (xb_on && st.ds.y > med_b) pm_b = phi_median<float>(st.ds.y, med_b, A.delta_m, p.median_mode);
             }
             const float phi_a = act_a ? fminf(st.pp.x, pm_a) : 1.f, phi_b = act_b ? fminf(st.pp.y, pm_b) : 1.f;
             if (__any_sync(kFull, phi_a < 1.f || phi_b < 1.f)) {
