@@ -196,8 +196,12 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : kBlocksPerSM)
         const int strip = item % A.strips, seg = item / A.strips;
         const int xa = kStripCols * strip - 1 + lane, xb = xa + 32;  // the lane's two columns
         const int ys = seg * A.seg_rows, ye = min(ys + A.seg_rows, ny);
-        const int r0 = max(ys - 1, 0);
-        const int rc = min(ye, ny - 1);  // last row whose dS this warp computes
+        // The walk computes its own rows [ys, ye) only.  The median of its first
+        // and last row also needs dS of the rows just outside (ys - 1, ye); in
+        // the rare rows whose median is formed at all, those are evaluated on
+        // demand (halo_ds), so items pay no halo rows in the common case.
+        const int r0 = ys;
+        const int rc = ye - 1;  // last row whose dS this warp computes
         // every lane reads its columns x - 1 .. x + 1, at most 63 past the
         // lattice's last column: inside the zero row padding (kTail)
         const bool in_a = xa >= 0 && xa < nx, in_b = xb < nx;
@@ -276,28 +280,20 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : kBlocksPerSM)
 
         // Row q from its loaded populations: collision, dS; stores g' of the
         // warp's own sites.  Rare per-site paths sit behind warp votes.
-        auto compute_row = [&](int q, float2 g[9]) -> RowState {
-            RowState st{make_float2(0.f, 0.f), make_float2(1.f, 1.f), false, false, false, false};
-            edge_row(q, g);
-            float2 drho, rho, ux, uy, gs[9], n[9];
-            collide(g, drho, rho, ux, uy, gs, n);
-            float2 din = make_float2(0.f, 0.f);
-            float fpmin_a = 3.4e38f, fpmin_b = 3.4e38f;
+        // dS(f') of a computed row (infinite at sites that cannot be limited:
+        // rho <= 0, some f*_k <= 0, nonfinite); din = dS(f_in)
+        auto row_ds = [&](const float2 gs[9], const float2 n[9], float2 rho, float2 ux, float2 uy, float2 &din,
+                          bool &bad_a, bool &bad_b) -> float2 {
+            din = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int k = 0; k < 9; ++k) {
-                const float2 fsa = O::add(rwk(k), gs[k]);  // absolute f*
-                din = O::fma(O::mul(n[k], n[k]), O::rcp_fast(fsa), din);
-                g[k] = O::fma(O::s(-b2), n[k], g[k]);  // g' = g - 2 beta n
-                if (pos_on) {
-                    fpmin_a = fminf(fpmin_a, rwk(k).x + g[k].x);
-                    fpmin_b = fminf(fpmin_b, rwk(k).y + g[k].y);
-                }
-            }
+            for (int k = 0; k < 9; ++k)
+                din = O::fma(O::mul(n[k], n[k]), O::rcp_fast(O::add(rwk(k), gs[k])), din);  // / absolute f*
             float2 ds = O::mul(O::s(a2), din);  // dS(f') = (2 beta - 1)^2 dS(f_in) for the same f*
             // f*_k >= rho W_k (1/2 - 3 u^2 / 2) > 0 whenever u^2 < 1/3; only fast
             // flows need the explicit test of every f*_k
             const float2 usq = O::fma(ux, ux, O::mul(uy, uy));
-            bool bad_a = !(rho.x > 0.f) || !isfinite(ds.x), bad_b = !(rho.y > 0.f) || !isfinite(ds.y);
+            bad_a = !(rho.x > 0.f) || !isfinite(ds.x);
+            bad_b = !(rho.y > 0.f) || !isfinite(ds.y);
             if (__any_sync(kFull, !(usq.x < 0.3f) || !(usq.y < 0.3f))) {
                 float fa = 3.4e38f, fb = 3.4e38f;
 #pragma unroll
@@ -310,6 +306,35 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : kBlocksPerSM)
             }
             ds.x = bad_a ? __int_as_float(0x7f800000) : ds.x;
             ds.y = bad_b ? __int_as_float(0x7f800000) : ds.y;
+            return ds;
+        };
+        // dS(f') of row q, outside the walk, from global loads (the whole warp)
+        auto halo_ds = [&](int q) -> float2 {
+            float2 g[9];
+            load_row(q, g);
+            edge_row(q, g);
+            float2 drho, rho, ux, uy, gs[9], n[9], din;
+            collide(g, drho, rho, ux, uy, gs, n);
+            bool bad_a, bad_b;
+            return row_ds(gs, n, rho, ux, uy, din, bad_a, bad_b);
+        };
+
+        auto compute_row = [&](int q, float2 g[9]) -> RowState {
+            RowState st{make_float2(0.f, 0.f), make_float2(1.f, 1.f), false, false, false, false};
+            edge_row(q, g);
+            float2 drho, rho, ux, uy, gs[9], n[9], din;
+            collide(g, drho, rho, ux, uy, gs, n);
+            bool bad_a, bad_b;
+            float2 ds = row_ds(gs, n, rho, ux, uy, din, bad_a, bad_b);
+            float fpmin_a = 3.4e38f, fpmin_b = 3.4e38f;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                g[k] = O::fma(O::s(-b2), n[k], g[k]);  // g' = g - 2 beta n
+                if (pos_on) {
+                    fpmin_a = fminf(fpmin_a, rwk(k).x + g[k].x);
+                    fpmin_b = fminf(fpmin_b, rwk(k).y + g[k].y);
+                }
+            }
             if (pos_on && __any_sync(kFull, (!bad_a && fpmin_a < 0.f) || (!bad_b && fpmin_b < 0.f))) {
                 // positivity rule (Sec. 3.1)
 #pragma unroll
@@ -388,6 +413,19 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : kBlocksPerSM)
             const bool xa_on = act_a && !st.bad_a && st.ds.x > A.delta_m;
             const bool xb_on = act_b && !st.bad_b && st.ds.y > A.delta_m;
             if (med_on && __any_sync(kFull, xa_on || xb_on)) {
+                // the rows just outside the walk, when the stencil reaches them
+                // (one evaluation site in the code for both)
+#pragma unroll 1
+                for (int side = 0; side < 2; ++side) {
+                    const int hq = side == 0 ? (y == ys && ys > 0 ? ys - 1 : -1) : (y == ye - 1 && ye < ny ? ye : -1);
+                    if (hq >= 0) {  // the same for the whole warp
+                        const float2 v = halo_ds(hq);
+                        if (side == 0)
+                            dm = v;
+                        else
+                            dp = v;
+                    }
+                }
                 // 3 x 3 median from sorted columns: the median of (largest column
                 // minimum, median of the column medians, smallest column maximum);
                 // wall rows and columns take the near-wall stencils
