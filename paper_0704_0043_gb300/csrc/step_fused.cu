@@ -55,9 +55,9 @@ constexpr int kWin = 72;         // FP32: columns of each plane copied per row (
 constexpr int kWin16 = 80;       // 16-bit storage: the same window, 8-column aligned
 constexpr int kCarveout = -1;    // preferred shared-memory carveout in percent (-1: the driver's choice)
 constexpr int kStripCols = 62;   // finished columns per strip (64 computed)
-constexpr int kMinSegRows = 16;  // shortest row segment (the two halo rows cost 2 / segment)
+constexpr int kMinSegRows = 4;   // shortest row segment (an item costs a ring prologue and a few atomics)
 constexpr int kFoldRows = 128;   // FP32 partial sums are folded into fixed point every kFoldRows rows
-constexpr int kItemsPerWarp = 5; // dynamic work: about this many items per resident warp
+constexpr int kItemsPerWarp = 10;  // dynamic work: about this many items per resident warp
 constexpr int kLaneKeys = 3;     // candidates of an item from which each lane keys its own
 constexpr int kCandList = 32;    // candidates a warp keys itself per item (the tail keys the rest)
 constexpr unsigned kFull = 0xffffffffu;
