@@ -78,15 +78,15 @@ lbm_status lbm_batch_lattice_status(const lbm_batch *b, int32_t slot);
 lbm_status lbm_batch_set_graph(lbm_batch *b, int32_t steps_per_graph);
 
 /* Work-split autotuner: times `trial_steps` batched steps for each candidate
- * (segments chosen per lattice or 64 rows; 1, 2 or 4 waves of work items),
+ * (segments chosen per lattice, 8 or 16 rows; 1, 2, 4 or 8 waves of work items),
  * keeps the fastest, and restores every lattice's state, counters and stats
  * to what they were before.  *best_ms receives the winning time per step
  * (may be NULL). */
 lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_steps, double *best_ms);
 
 /* Fixes the fused kernel's work split: seg_rows = rows per work item (a warp
- * walking a strip of 30 columns; 0: chosen per lattice, else >= 16), waves 1,
- * 2 or 4 (work items per lattice in proportion to its sites, one wave = the
+ * walking a strip of 62 columns; 0: chosen per lattice, else >= 4), waves 1,
+ * 2, 4 or 8 (work items per lattice in proportion to its sites, one wave = the
  * GPU's resident warps).  The split changes the speed only, never a result.
  * Errors: LBM_ERR_INVALID_ARG. */
 lbm_status lbm_batch_set_shape(lbm_batch *b, int32_t seg_rows, int32_t waves);

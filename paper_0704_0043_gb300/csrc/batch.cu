@@ -478,8 +478,9 @@ lbm_status lbm_batch_set_graph(lbm_batch *b, int32_t steps_per_graph)
 lbm_status lbm_batch_set_shape(lbm_batch *b, int32_t seg_rows, int32_t waves)
 {
     if (!b) return LBM_ERR_INVALID_ARG;
-    if (seg_rows != 0 && seg_rows < 16) return bfail(b, LBM_ERR_INVALID_ARG, "seg_rows must be 0 or >= 16");
-    if (waves != 1 && waves != 2 && waves != 4) return bfail(b, LBM_ERR_INVALID_ARG, "waves must be 1, 2 or 4");
+    if (seg_rows != 0 && seg_rows < 4) return bfail(b, LBM_ERR_INVALID_ARG, "seg_rows must be 0 or >= 4");
+    if (waves != 1 && waves != 2 && waves != 4 && waves != 8)
+        return bfail(b, LBM_ERR_INVALID_ARG, "waves must be 1, 2, 4 or 8");
     invalidate(b);
     b->seg_rows = seg_rows;
     b->waves = waves;
@@ -514,8 +515,10 @@ lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_steps, double *best_ms)
         BCK(b, cudaMemcpyAsync(m + c->field_bytes + ring + 32, c->counts, 2 * sizeof(int), cudaMemcpyDeviceToDevice, b->run));
         snaps.push_back({c, c->cur, mem});
     }
-    const int Ts[2] = {0, 64};
-    const int Ws[3] = {1, 2, 4};
+    // short items in several waves let the block scheduler even out the
+    // warps' different rates (an item costs no halo rows)
+    const int Ts[3] = {0, 8, 16};
+    const int Ws[4] = {1, 2, 4, 8};
     double best = 1e300;
     int bestT = 0, bestW = 1;
     lbm_status rs = LBM_OK;

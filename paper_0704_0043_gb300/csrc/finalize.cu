@@ -112,9 +112,6 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, 
     S *__restrict__ f = BATCHED ? (S *)sA.f : f0;
     __shared__ double red[kFinWarps + 1];
     __shared__ double tot[P_NSTAT];
-    __shared__ unsigned __int128 s_fx[4];
-    __shared__ unsigned long long s_cnt[5];
-    __shared__ unsigned long long s_fxw[kFinWarps][13];
     __shared__ double s_key[kCap];
     __shared__ int s_site[kCap];
     __shared__ int s_idx[kCap];
@@ -135,83 +132,50 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, 
         s_valid = 0;
     }
     if (p.fixed) {
-        // fixed-point accumulator rows of the fused kernel (kFxRows of them):
-        // exact integer sums, so the order does not matter; the rows are
-        // cleared for the next step once read.  Each 128-byte row is read as eight 16-byte
-        // chunks (coalesced: lane l takes chunk l % 8 of a row); chunk c < 4
-        // is FP statistic c (low, high word), chunk 4 the site and positivity
-        // counts, chunk 5 the median and nonfinite counts, chunk 6 the bits.
-        const int c = lane & 7;
-        unsigned __int128 v = 0;
-        unsigned long long u0 = 0, u1 = 0;
-        const ulonglong2 *chunks = reinterpret_cast<const ulonglong2 *>(p.partials);
-        constexpr int kStride = kFinThreads / 8;  // rows per pass of the block
-        for (int r0 = t >> 3; r0 < kFxRows; r0 += 8 * kStride) {
-            ulonglong2 w[8];  // eight loads in flight, then the sums
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int r = r0 + i * kStride;
-                w[i] = r < kFxRows ? chunks[(long long)r * (kFxWords / 2) + c] : make_ulonglong2(0ull, 0ull);
-            }
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                if (c < 4) {
-                    v += ((unsigned __int128)w[i].y << 64) | w[i].x;
-                } else if (c < 6) {
-                    u0 += w[i].x;
-                    u1 += w[i].y;
-                } else if (c == 6) {
-                    u0 |= w[i].x;
-                }
-            }
-        }
-#pragma unroll
-        for (int o = 8; o <= 16; o <<= 1) {  // lanes holding the same chunk
-            const unsigned long long lo = __shfl_xor_sync(kFull, (unsigned long long)v, o);
-            const unsigned long long hi = __shfl_xor_sync(kFull, (unsigned long long)(v >> 64), o);
-            const unsigned long long a0 = __shfl_xor_sync(kFull, u0, o), a1 = __shfl_xor_sync(kFull, u1, o);
-            v += ((unsigned __int128)hi << 64) | lo;
-            u0 = c == 6 ? (u0 | a0) : u0 + a0;
-            u1 += a1;
-        }
-        if (lane < 8) {
+        // the fused kernel's kFxRows fixed-point accumulator rows (exact integer
+        // sums, so the order does not matter), reduced by warp 0 alone: lane l
+        // reads 16-byte chunk l % 8 of rows l / 8 and l / 8 + 4 and clears them
+        // for the next step.  Chunk c < 4 is FP statistic c (low, high word),
+        // chunk 4 the site and positivity counts, chunk 5 the median and
+        // nonfinite counts, chunk 6 the nonfinite bits.
+        static_assert(kFxRows == 8 && kFxWords == 16, "warp 0 reads 8 rows of 8 chunks");
+        if (warp == 0) {
+            const int c = lane & 7;
+            ulonglong2 *chunks = reinterpret_cast<ulonglong2 *>(p.partials);
+            const ulonglong2 w0 = chunks[lane], w1 = chunks[lane + 32];
+            chunks[lane] = make_ulonglong2(0ull, 0ull);
+            chunks[lane + 32] = make_ulonglong2(0ull, 0ull);
+            unsigned __int128 v = 0;
+            unsigned long long u0 = 0, u1 = 0;
             if (c < 4) {
-                s_fxw[warp][2 * c] = (unsigned long long)v;
-                s_fxw[warp][2 * c + 1] = (unsigned long long)(v >> 64);
+                v = (((unsigned __int128)w0.y << 64) | w0.x) + (((unsigned __int128)w1.y << 64) | w1.x);
             } else if (c < 6) {
-                s_fxw[warp][FX_SITES + 2 * (c - 4)] = u0;
-                s_fxw[warp][FX_SITES + 2 * (c - 4) + 1] = u1;
+                u0 = w0.x + w1.x;
+                u1 = w0.y + w1.y;
             } else if (c == 6) {
-                s_fxw[warp][FX_BAD] = u0;
+                u0 = w0.x | w1.x;
             }
-        }
-        __syncthreads();
-        if (t < kFxRows * kFxWords / 2)
-            reinterpret_cast<ulonglong2 *>(p.partials)[t] = make_ulonglong2(0ull, 0ull);
-        if (t < 9) {  // t < 4: FP statistic t; 4..7: the counts; 8: the nonfinite bits
-            unsigned __int128 a = 0;
-            unsigned long long b = 0;
-            for (int w = 0; w < kFinWarps; ++w) {
-                if (t < 4)
-                    a += ((unsigned __int128)s_fxw[w][2 * t + 1] << 64) | s_fxw[w][2 * t];
-                else if (t < 8)
-                    b += s_fxw[w][4 + t];
-                else
-                    b |= s_fxw[w][12];
+#pragma unroll
+            for (int o = 8; o <= 16; o <<= 1) {  // lanes holding the same chunk
+                const unsigned long long lo = __shfl_xor_sync(kFull, (unsigned long long)v, o);
+                const unsigned long long hi = __shfl_xor_sync(kFull, (unsigned long long)(v >> 64), o);
+                const unsigned long long a0 = __shfl_xor_sync(kFull, u0, o), a1 = __shfl_xor_sync(kFull, u1, o);
+                v += ((unsigned __int128)hi << 64) | lo;
+                u0 = c == 6 ? (u0 | a0) : u0 + a0;
+                u1 += a1;
             }
-            if (t < 4)
-                s_fx[t] = a;
-            else
-                s_cnt[t - 4] = b;
-        }
-        __syncthreads();
-        if (t < P_NSTAT) {  // one statistic per thread
-            if (t <= P_DS_LIM) {
-                double v = ((s_cnt[4] >> t) & 1u) ? __longlong_as_double(0x7ff8000000000000LL) : fx_to_double(s_fx[t]);
-                if (t == P_MASS) v = Ar<double>::add(v, Ar<double>::mul((double)s_cnt[0], (double)p.rho_ref));
-                tot[t] = v;
-            } else {
-                tot[t] = (double)s_cnt[t - P_NPOS + 1];  // positivity, median, nonfinite counts
+            // lanes 0..7 hold chunk totals; lanes 0..3 need the site count
+            // (chunk 4) and the nonfinite bits (chunk 6)
+            const unsigned long long sites = __shfl_sync(kFull, u0, 4), bits = __shfl_sync(kFull, u0, 6);
+            if (lane < 4) {  // FP statistic lane
+                double d = ((bits >> lane) & 1u) ? __longlong_as_double(0x7ff8000000000000LL) : fx_to_double(v);
+                if (lane == P_MASS) d = Ar<double>::add(d, Ar<double>::mul((double)sites, (double)p.rho_ref));
+                tot[lane] = d;
+            } else if (lane == 4) {
+                tot[P_NPOS] = (double)u1;
+            } else if (lane == 5) {
+                tot[P_NMED] = (double)u0;
+                tot[P_NBAD] = (double)u1;
             }
         }
     } else if (warp < 2 * P_NSTAT) {

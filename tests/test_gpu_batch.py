@@ -94,7 +94,7 @@ def test_batch_add_remove_and_tune_keep_states():
         np.testing.assert_array_equal(b.get_populations(slots[i]), g.get_populations())
 
 
-@pytest.mark.parametrize("seg_rows,waves", [(0, 1), (16, 2), (0, 4), (64, 1)])
+@pytest.mark.parametrize("seg_rows,waves", [(0, 1), (16, 2), (0, 4), (64, 1), (8, 8), (4, 2)])
 def test_batch_shape_never_changes_results(seg_rows, waves):
     """The fused kernel's segment length and work-item budget change the work
     split only: every lattice matches its lone run bit for bit."""
