@@ -17,7 +17,8 @@
 //  * Free flight reads the populations arriving at row r straight from the
 //    source field: planes {0,1,3} of row r, {2,5,6} of row r-1, {4,7,8} of
 //    row r+1, so every stored population is read from DRAM once (strips
-//    overlap by two columns, segments by two rows).  Each plane's row window
+//    overlap by two columns; an item's pull also reads three planes of the
+//    rows just outside it).  Each plane's row window
 //    arrives by 16-byte asynchronous copies (cp.async) in a per-warp ring of
 //    shared-memory rows one row ahead of the arithmetic; the lanes read their
 //    columns shifted by -cx.
