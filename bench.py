@@ -145,6 +145,9 @@ def traffic_from_profile(kernel_name: str, sites: int):
     return ent["dram_bytes_per_site"] * sites
 
 
+TIMING_EVERY = 8  # the step and tail kernels are timed with CUDA events on one step in 8
+
+
 def workload(side: int = 4096):
     from paper_0704_0043_gb300 import inputs
     w = inputs.cavity4096_workload()
@@ -386,7 +389,9 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     launches0 = lat.launch_count()
-    lat.timing(True)
+    # per-kernel events on one step in TIMING_EVERY (events between the kernels
+    # delay the next launch, so timing every step would slow the measured run)
+    lat.timing(True, every=TIMING_EVERY)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     lat.step(args.steps)
@@ -414,6 +419,7 @@ def main():
             "frac": achieved / peak, "peak_kind": peak_kind,
             "traffic": traffic_from_profile(f"{kname}_{args.precision}", w.sites),
             "kernel": kname, "kernel_ms": kern_s * 1e3, "tail_kernel_ms": tail_ms / max(timed, 1),
+            "timed_launches": timed, "timed_every": TIMING_EVERY,
             "bytes_per_site": bps}
 
     e2e = None

@@ -194,10 +194,14 @@ int64_t lbm_device_bytes(const lbm_ctx *ctx);
 int64_t lbm_footprint_bytes(const lbm_config *cfg);
 
 /* Per-kernel timing with CUDA events recorded on the context's stream.  While
- * enabled, every step records an event before its step kernel, one between
+ * enabled, a timed step records an event before its step kernel, one between
  * the step kernel and its one-block tail kernel, and one after the tail.
+ * enable = 0 turns timing off, 1 times every step, N > 1 times one step in N
+ * (the first, then every N-th: events between the kernels also delay the
+ * following launch, so sampling keeps that cost off most steps).
  * lbm_timing_read synchronises, returns the summed milliseconds of each kernel
- * kind and the number of timed steps, and clears the record. */
+ * kind and the number of timed steps, and clears the record.
+ * Errors: LBM_ERR_INVALID_ARG (NULL context, enable < 0). */
 lbm_status lbm_timing(lbm_ctx *ctx, int32_t enable);
 lbm_status lbm_timing_read(lbm_ctx *ctx, double *step_kernel_ms, double *tail_kernel_ms, int64_t *steps);
 

@@ -101,6 +101,11 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, 
                                                           const FinalArgs *__restrict__ table)
 {
     using T = compute_t<S>;
+    // Launched as a programmatic dependent of the step kernel: wait for it to
+    // finish before any memory access, then let the next step kernel be
+    // scheduled early.  Both are no-ops in an ordinary launch.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     __shared__ __align__(16) FinalArgs sA;
     if constexpr (BATCHED) {
         const unsigned *from = reinterpret_cast<const unsigned *>(table + blockIdx.x);
@@ -436,11 +441,20 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, 
 template <typename T>
 cudaError_t launch_finalize(int q, const FinalParams &p, T *f, cudaStream_t s)
 {
-    if (q == 9)
-        k_finalize<9, T, false><<<1, kFinThreads, 0, s>>>(p, f, nullptr);
-    else
-        k_finalize<3, T, false><<<1, kFinThreads, 0, s>>>(p, f, nullptr);
-    return cudaGetLastError();
+    // programmatic dependent launch (see k_finalize)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(1);
+    cfg.blockDim = dim3(kFinThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const FinalArgs *none = nullptr;
+    if (q == 9) return cudaLaunchKernelEx(&cfg, k_finalize<9, T, false>, p, f, none);
+    return cudaLaunchKernelEx(&cfg, k_finalize<3, T, false>, p, f, none);
 }
 
 cudaError_t launch_finalize_batched_f32(int q, const FinalArgs *table, int n, cudaStream_t s)

@@ -217,6 +217,9 @@ struct lbm_ctx {
     size_t stage_bytes = 0;
     bool ready = false;
     bool timing = false;
+    bool timing_now = false;    // the current pass records its events
+    int timing_every = 1;       // record one pass in this many
+    long long timing_pass = 0;  // passes since timing was enabled
     std::vector<cudaEvent_t> events;  // three per timed step
     size_t events_used = 0;
     long long launches = 0;

@@ -268,7 +268,7 @@ lbm_status next_event(lbm_ctx *c, cudaEvent_t *ev)
 
 lbm_status mark(lbm_ctx *c)
 {
-    if (!c->timing) return LBM_OK;
+    if (!c->timing || !c->timing_now) return LBM_OK;
     cudaEvent_t ev;
     lbm_status s = next_event(c, &ev);
     if (s != LBM_OK) return s;
@@ -279,6 +279,9 @@ lbm_status mark(lbm_ctx *c)
 // One pass (step or limiter pass) from buf[cur] into buf[cur ^ 1].
 lbm_status run_pass(lbm_ctx *c, int collide, unsigned limiters)
 {
+    // timing samples every timing_every-th pass (the events between kernels
+    // would otherwise also cost every pass their gap)
+    c->timing_now = c->timing && (c->timing_every <= 1 || c->timing_pass++ % c->timing_every == 0);
     lbm_status ms = mark(c);
     if (ms != LBM_OK) return ms;
     StepParams p = step_params(c, collide, limiters);
@@ -693,7 +696,10 @@ lbm_status lbm_get_config(const lbm_ctx *c, lbm_config *out)
 lbm_status lbm_timing(lbm_ctx *c, int32_t enable)
 {
     if (!c) return fail(nullptr, LBM_ERR_INVALID_ARG, "ctx is NULL");
+    if (enable < 0) return fail(c, LBM_ERR_INVALID_ARG, "enable must be >= 0");
     c->timing = enable != 0;
+    c->timing_every = enable > 1 ? enable : 1;
+    c->timing_pass = 0;
     c->events_used = 0;
     return LBM_OK;
 }

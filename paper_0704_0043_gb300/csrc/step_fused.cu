@@ -141,6 +141,11 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : kBlocksPerSM)
     k_fused(const FusedArgs A0, const FusedArgs *__restrict__ table, const int2 *__restrict__ map)
 {
     using O = F2;
+    // Launched as a programmatic dependent of the previous kernel: wait for it
+    // to finish before any memory access, then let the next kernel (the tail)
+    // be scheduled early.  Both are no-ops in an ordinary launch.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     // Rows stream through a per-warp ring of shared-memory rows filled by
     // 16-byte asynchronous copies (kRing - 1 rows in flight, no registers
     // held): windows of 72 FP32 or 80 16-bit columns
@@ -670,7 +675,26 @@ cudaError_t launch_k(const FusedArgs &A, const FusedArgs *table, const int2 *map
             cudaGetLastError();
     }
     configured = true;
-    k_fused<S, MED, POS, BATCHED><<<blocks, kThreads, 0, s>>>(A, table, map);
+    if constexpr (BATCHED) {
+        k_fused<S, MED, POS, BATCHED><<<blocks, kThreads, 0, s>>>(A, table, map);
+    } else {
+        // programmatic dependent launch: the blocks may become resident while
+        // the previous kernel of the stream (the tail) still runs; they wait
+        // for it (griddepcontrol.wait) before touching memory
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(blocks);
+        cfg.blockDim = dim3(kThreads);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        const FusedArgs *tab = table;
+        const int2 *mp = map;
+        return cudaLaunchKernelEx(&cfg, k_fused<S, MED, POS, BATCHED>, A, tab, mp);
+    }
     return cudaGetLastError();
 }
 

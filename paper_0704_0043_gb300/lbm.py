@@ -321,8 +321,9 @@ class Lattice:
     def synchronize(self):
         _check(lib().lbm_synchronize(self._h), self._h)
 
-    def timing(self, enable: bool):
-        _check(lib().lbm_timing(self._h, 1 if enable else 0), self._h)
+    def timing(self, enable: bool, every: int = 1):
+        """Per-kernel event timing on (one step in `every`) or off."""
+        _check(lib().lbm_timing(self._h, max(1, int(every)) if enable else 0), self._h)
 
     def timing_read(self):
         """(step-kernel ms, tail-kernel ms, timed steps) since timing was enabled."""

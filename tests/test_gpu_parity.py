@@ -325,6 +325,20 @@ def test_fused_dynamic_work_items_are_deterministic():
         np.testing.assert_allclose(sa[key], st[key], rtol=1e-5)
 
 
+def test_kernel_timing_samples_every_nth_step():
+    """lbm_timing with enable = N times the first step and every N-th after
+    it; enable = 1 times every step."""
+    g = lbm.Lattice(lattice=lbm.D2Q9, nx=128, ny=96, boundary=lbm.BC_WALLS, beta=0.9, u_lid=0.1,
+                    precision=lbm.FP32, limiters=ALL, k_max=4)
+    g.init(*inputs.cavity_rest(128, 96))
+    for every, steps, want in ((4, 12, 3), (4, 13, 4), (1, 5, 5)):
+        g.timing(True, every=every)
+        g.step(steps)
+        k, t, n = g.timing_read()
+        g.timing(False)
+        assert n == want and k > 0.0 and t > 0.0, (every, steps, n)
+
+
 def test_nonfinite_site_reports_status():
     g, _ = pair(lattice=lbm.D2Q9, nx=40, ny=30, boundary=lbm.BC_WALLS, beta=0.9,
                 precision=lbm.FP32, limiters=ALL, k_max=3)
