@@ -28,6 +28,7 @@ D1Q3, D2Q9 = 1, 2
 BC_WALLS, BC_PERIODIC, BC_CHANNEL = 0, 1, 2
 LIM_POSITIVITY, LIM_EHRENFEST, LIM_MEDIAN = 1, 2, 4
 MEDIAN_THRESHOLD, MEDIAN_GATE = 0, 1
+EQ_POLYNOMIAL, EQ_ENTROPIC = 0, 1
 
 
 def build(force: bool = False) -> str:
@@ -51,7 +52,7 @@ class _Config(ctypes.Structure):
         ("boundary", ctypes.c_int), ("beta", ctypes.c_double), ("u_lid", ctypes.c_double),
         ("rho_wall", ctypes.c_double), ("limiters", ctypes.c_uint),
         ("delta_median", ctypes.c_double), ("delta_ehrenfest", ctypes.c_double),
-        ("k_max", ctypes.c_longlong), ("median_mode", ctypes.c_int),
+        ("k_max", ctypes.c_longlong), ("median_mode", ctypes.c_int), ("equilibrium", ctypes.c_int),
     ]
 
 
@@ -78,6 +79,12 @@ def _load():
         cp = ctypes.POINTER(_Config)
         sp = ctypes.POINTER(Stats)
         lib.orc_feq.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
+        lib.orc_feq_entropic.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
+        lib.orc_feq_entropic.restype = ctypes.c_int
+        lib.orc_entropy.argtypes = [ctypes.c_int, dp]
+        lib.orc_entropy.restype = ctypes.c_double
+        lib.orc_rel_entropy.argtypes = [ctypes.c_int, dp, dp]
+        lib.orc_rel_entropy.restype = ctypes.c_double
         lib.orc_site_moments.argtypes = [ctypes.c_int, dp, dp, dp, dp]
         lib.orc_init.argtypes = [cp, dp, dp, dp, dp]
         lib.orc_moments.argtypes = [cp, dp, dp, dp, dp]
@@ -114,6 +121,7 @@ class Config:
     delta_ehrenfest: float = 1e-3
     k_max: int = 0
     median_mode: int = MEDIAN_THRESHOLD
+    equilibrium: int = EQ_POLYNOMIAL
 
     @property
     def q(self) -> int:
@@ -129,7 +137,7 @@ class Config:
     def _c(self) -> _Config:
         return _Config(self.lattice, self.nx, self.ny, self.boundary, self.beta, self.u_lid,
                        self.rho_wall, self.limiters, self.delta_median, self.delta_ehrenfest,
-                       self.k_max, self.median_mode)
+                       self.k_max, self.median_mode, self.equilibrium)
 
 
 def _f64(a, shape=None):
@@ -146,6 +154,28 @@ def feq(lattice: int, rho: float, ux: float, uy: float = 0.0) -> np.ndarray:
     return out
 
 
+def feq_entropic(lattice: int, rho: float, ux: float, uy: float = 0.0):
+    """Entropic quasiequilibrium at one site (Eq. entropiceq1d / Eq. maxwellian), or None
+    where it does not exist (|u_j| >= 1)."""
+    out = np.zeros(3 if lattice == D1Q3 else 9)
+    if _load().orc_feq_entropic(lattice, rho, ux, uy, _dp(out)):
+        return None
+    return out
+
+
+def entropy(lattice: int, f) -> float:
+    """Lattice entropy S(f) of one site (Sec. 4.1)."""
+    f = _f64(f)
+    return _load().orc_entropy(lattice, _dp(f))
+
+
+def rel_entropy(f, fs) -> float:
+    """sum_k f_k ln(f_k / fs_k) (Eq. DelS); +inf if some f_k < 0."""
+    f = _f64(f)
+    fs = _f64(fs)
+    return _load().orc_rel_entropy(len(f), _dp(f), _dp(fs))
+
+
 def site_moments(lattice: int, f) -> tuple:
     """rho, ux, uy of one site's populations (Eq. macro_dis)."""
     f = _f64(f)
@@ -155,7 +185,7 @@ def site_moments(lattice: int, f) -> tuple:
 
 
 def init(cfg: Config, rho, ux, uy=None) -> np.ndarray:
-    """Populations at polynomial equilibrium for the given density and velocity fields."""
+    """Populations at equilibrium (the configured f*) for the given density and velocity fields."""
     rho = _f64(rho, (cfg.sites,))
     ux = _f64(ux, (cfg.sites,))
     uy = None if uy is None else _f64(uy, (cfg.sites,))

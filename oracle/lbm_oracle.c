@@ -13,8 +13,10 @@
  *      Sec. 4.4.1); a link through the moving lid gains 6 W_k rho_w (v_k . u_w)
  *   2. moments rho, u                                                   Eq. macro_dis
  *   3. polynomial quasiequilibrium f*                                   Eq. polyeq1d / polyeq2d
+ *      (or the entropic one                                             Eq. entropiceq1d / maxwellian)
  *   4. LBGK collision  f' = f* + (2 beta - 1)(f* - f_in)                Eq. collLBGK, lbgkLB
  *   5. dS(f') = sum_k (f'_k - f*_k)^2 / f*_k                            Sec. 3.6, quadratic form of Eq. DelS
+ *      (entropic f*: dS(f') = sum_k f'_k ln(f'_k / f*_k)                Eq. DelS)
  *   6. phi_pos: positivity rule, closest nonnegative point of the line
  *      through f' and f*                                                Sec. 3.1
  *   7. phi_med: median of dS over the stencil, homothety sqrt(dS_t/dS)  Sec. 3.5, Eq. entrHom
@@ -67,6 +69,99 @@ void orc_feq(int lattice, double rho, double ux, double uy, double *feq)
     }
 }
 
+int orc_feq_entropic(int lattice, double rho, double ux, double uy, double *feq)
+{
+    if (lattice == ORC_D1Q3) {
+        /* Eq. entropiceq1d.  As printed, f2* - f3* = rho u, i.e. the printed f2*
+         * is the population whose velocity makes sum_k v_k f*_k = rho u hold
+         * (Eq. macro_dis): v = +1.  Index 1 (v = -1) takes the printed f3*. */
+        if (!(fabs(ux) < 1.0)) return 1;
+        double u = ux;
+        double sq = sqrt(1.0 + 3.0 * (u * u));
+        feq[0] = ((2.0 * rho) / 3.0) * (2.0 - sq);
+        feq[1] = -(rho / 6.0) * ((3.0 * u + 1.0) - 2.0 * sq);
+        feq[2] = (rho / 6.0) * ((3.0 * u - 1.0) + 2.0 * sq);
+        return 0;
+    }
+    /* Eq. maxwellian: f*_k = rho W_k prod_{j = x, y} (2 - sqrt(1 + 3 u_j^2))
+     * ((2 u_j + sqrt(1 + 3 u_j^2)) / (1 - u_j))^{v_kj}, v_kj in {-1, 0, 1}. */
+    if (!(fabs(ux) < 1.0) || !(fabs(uy) < 1.0)) return 1;
+    double u[2] = {ux, uy};
+    double A[2], X[2];
+    for (int j = 0; j < 2; ++j) {
+        double sq = sqrt(1.0 + 3.0 * (u[j] * u[j]));
+        A[j] = 2.0 - sq;
+        X[j] = (2.0 * u[j] + sq) / (1.0 - u[j]);
+    }
+    for (int k = 0; k < 9; ++k) {
+        int v[2] = {cx9[k], cy9[k]};
+        double f = rho * w9(k);
+        for (int j = 0; j < 2; ++j) {
+            double P = A[j];
+            if (v[j] == 1) P = A[j] * X[j];
+            if (v[j] == -1) P = A[j] / X[j];
+            f = f * P;
+        }
+        feq[k] = f;
+    }
+    return 0;
+}
+
+double orc_entropy(int lattice, const double *f)
+{
+    double h = 0.0;
+    if (lattice == ORC_D1Q3) {
+        /* Sec. 4.1: H = f1 log(f1/4) + f2 log(f2) + f3 log(f3), S = -H */
+        if (f[0] > 0.0) h += f[0] * log(f[0] / 4.0);
+        if (f[1] > 0.0) h += f[1] * log(f[1]);
+        if (f[2] > 0.0) h += f[2] * log(f[2]);
+        return -h;
+    }
+    for (int k = 0; k < 9; ++k)
+        if (f[k] > 0.0) h += f[k] * log(f[k] / w9(k));
+    return -h;
+}
+
+double orc_rel_entropy(int q, const double *f, const double *fs)
+{
+    /* Eq. DelS: dS = sum_k f_k ln(f_k / f*_k).  A negative population lies
+     * outside the domain of S: dS = +inf.  A zero one contributes 0 ln 0 = 0. */
+    for (int k = 0; k < q; ++k)
+        if (f[k] < 0.0) return INFINITY;
+    double s = 0.0;
+    for (int k = 0; k < q; ++k) {
+        if (f[k] > 0.0) s += f[k] * log(f[k] / fs[k]);
+        else if (!(f[k] == 0.0)) return NAN;
+    }
+    return s;
+}
+
+/* f* of the configured kind; returns 1 where it does not exist. */
+static int site_feq(const orc_config *cfg, double rho, double ux, double uy, double *fs)
+{
+    if (cfg->equilibrium == ORC_EQ_ENTROPIC) return orc_feq_entropic(cfg->lattice, rho, ux, uy, fs);
+    orc_feq(cfg->lattice, rho, ux, uy, fs);
+    return 0;
+}
+
+/* dS(f) of the configured kind (quadratic form, or Eq. DelS for entropic f*). */
+static double site_dS(const orc_config *cfg, int q, const double *f, const double *fs)
+{
+    if (cfg->equilibrium == ORC_EQ_ENTROPIC) return orc_rel_entropy(q, f, fs);
+    double s = 0.0;
+    for (int k = 0; k < q; ++k) {
+        double d = f[k] - fs[k];
+        s += (d * d) / fs[k];
+    }
+    return s;
+}
+
+/* A dS value that is allowed to be +inf (entropic f*, population below zero). */
+static int dS_ok(const orc_config *cfg, double x)
+{
+    return cfg->equilibrium == ORC_EQ_ENTROPIC ? !isnan(x) : isfinite(x);
+}
+
 void orc_site_moments(int lattice, const double *f, double *rho, double *ux, double *uy)
 {
     /* Eq. macro_dis: rho = sum_k f_k, rho u = sum_k v_k f_k, summed in k order. */
@@ -94,7 +189,8 @@ void orc_init(const orc_config *cfg, const double *rho, const double *ux, const 
     long long n = (long long)cfg->nx * cfg->ny;
     double feq[9];
     for (long long s = 0; s < n; ++s) {
-        orc_feq(cfg->lattice, rho[s], ux[s], uy ? uy[s] : 0.0, feq);
+        for (int k = 0; k < q; ++k) feq[k] = NAN;
+        site_feq(cfg, rho[s], ux[s], uy ? uy[s] : 0.0, feq);
         for (int k = 0; k < q; ++k) f[k * n + s] = feq[k];
     }
 }
@@ -151,8 +247,10 @@ static void pull(const orc_config *cfg, const double *f, int i, int j, double *f
 
 /*
  * Steps 2-5 at one site.  Writes f* and f' (q values each), dS(f') and
- * dS(f_in); returns 1 if the site cannot be limited (rho <= 0, f*_k <= 0 for
- * some k, or a nonfinite value), in which case *dS = +inf.
+ * dS(f_in); returns 1 if the site cannot be limited (rho <= 0, no f* or
+ * f*_k <= 0 for some k, or a nonfinite value), in which case *dS = +inf.
+ * With entropic f*, dS(f') and dS(f_in) may be +inf without the site being
+ * flagged (a negative population).
  */
 static int site_collide(const orc_config *cfg, const double *fin, double *fs, double *fp,
                         double *dS, double *dS_in, double *rho_out)
@@ -160,22 +258,18 @@ static int site_collide(const orc_config *cfg, const double *fin, double *fs, do
     int q = nq(cfg->lattice);
     double rho, ux, uy;
     orc_site_moments(cfg->lattice, fin, &rho, &ux, &uy);
-    orc_feq(cfg->lattice, rho, ux, uy, fs);
+    int bad = !(rho > 0.0) || !isfinite(rho) || !isfinite(ux) || !isfinite(uy);
+    if (site_feq(cfg, rho, ux, uy, fs)) {
+        bad = 1;
+        for (int k = 0; k < q; ++k) fs[k] = 0.0;
+    }
     double a = 2.0 * cfg->beta - 1.0;
     for (int k = 0; k < q; ++k) fp[k] = fs[k] + a * (fs[k] - fin[k]);
-    int bad = !(rho > 0.0) || !isfinite(rho) || !isfinite(ux) || !isfinite(uy);
     for (int k = 0; k < q; ++k)
-        if (!(fs[k] > 0.0) || !isfinite(fin[k])) bad = 1;
-    double s = 0.0, si = 0.0;
-    for (int k = 0; k < q; ++k) {
-        double d = fp[k] - fs[k];
-        s += (d * d) / fs[k];
-    }
-    for (int k = 0; k < q; ++k) {
-        double d = fin[k] - fs[k];
-        si += (d * d) / fs[k];
-    }
-    if (!isfinite(s) || !isfinite(si)) bad = 1;
+        if (!(fs[k] > 0.0) || !isfinite(fs[k]) || !isfinite(fin[k])) bad = 1;
+    double s = bad ? 0.0 : site_dS(cfg, q, fp, fs);
+    double si = bad ? 0.0 : site_dS(cfg, q, fin, fs);
+    if (!dS_ok(cfg, s) || !dS_ok(cfg, si)) bad = 1;
     *rho_out = rho;
     *dS = bad ? INFINITY : s;
     *dS_in = bad ? 0.0 : si;
@@ -313,11 +407,20 @@ static void limit_core(const orc_config *cfg, unsigned limiters, const double *f
         if (phi_pos < 1.0) st->n_pos++;
         if (phi_med < 1.0) st->n_med++;
         if (p < 1.0) {
+            double fo[9], fsl[9];
             for (int k = 0; k < q; ++k) {
                 double fsk = fs[k * n + s];
                 f_out[k * n + s] = fsk + p * (fp[k * n + s] - fsk);
+                fo[k] = f_out[k * n + s];
+                fsl[k] = fsk;
             }
-            st->dS_lim += (1.0 - p * p) * dS[s];
+            if (cfg->equilibrium == ORC_EQ_ENTROPIC) {
+                /* entropy difference dS(f') - dS(f_out) at the same f* */
+                double d_out = orc_rel_entropy(q, fo, fsl);
+                if (isfinite(dS[s]) && isfinite(d_out)) st->dS_lim += dS[s] - d_out;
+            } else {
+                st->dS_lim += (1.0 - p * p) * dS[s];
+            }
         } else {
             /* phi = 1 is the identity: the post-collision state is stored as is. */
             for (int k = 0; k < q; ++k) f_out[k * n + s] = fp[k * n + s];
@@ -347,9 +450,15 @@ static void limit_core(const orc_config *cfg, unsigned limiters, const double *f
             /* Ehrenfests' step: equilibrate the limited state at s, f -> f*(m(f)). */
             for (int k = 0; k < q; ++k) fl[k] = f_out[k * n + s];
             orc_site_moments(cfg->lattice, fl, &r, &a, &b);
-            orc_feq(cfg->lattice, r, a, b, feq);
+            site_feq(cfg, r, a, b, feq);
             for (int k = 0; k < q; ++k) f_out[k * n + s] = feq[k];
-            st->dS_lim += (phi[s] * phi[s]) * dS[s];
+            if (cfg->equilibrium == ORC_EQ_ENTROPIC) {
+                /* the entropy the step adds: dS of the limited state w.r.t. its own f* */
+                double d_l = orc_rel_entropy(q, fl, feq);
+                if (isfinite(d_l)) st->dS_lim += d_l;
+            } else {
+                st->dS_lim += (phi[s] * phi[s]) * dS[s];
+            }
             st->n_ehr++;
             if (sel) sel[t] = s;
         }
@@ -389,18 +498,17 @@ static int run_collide_and_limit(const orc_config *cfg, unsigned limiters, int d
                 double ux, uy;
                 for (int k = 0; k < q; ++k) fin[k] = f_st[k * n + s];
                 orc_site_moments(cfg->lattice, fin, &rho, &ux, &uy);
-                orc_feq(cfg->lattice, rho, ux, uy, fsl);
                 b = !(rho > 0.0) || !isfinite(rho) || !isfinite(ux) || !isfinite(uy);
+                if (site_feq(cfg, rho, ux, uy, fsl)) {
+                    b = 1;
+                    for (int k = 0; k < q; ++k) fsl[k] = 0.0;
+                }
                 for (int k = 0; k < q; ++k) {
                     fpl[k] = fin[k];
-                    if (!(fsl[k] > 0.0) || !isfinite(fin[k])) b = 1;
+                    if (!(fsl[k] > 0.0) || !isfinite(fsl[k]) || !isfinite(fin[k])) b = 1;
                 }
-                ds = 0.0;
-                for (int k = 0; k < q; ++k) {
-                    double d = fpl[k] - fsl[k];
-                    ds += (d * d) / fsl[k];
-                }
-                if (!isfinite(ds)) b = 1;
+                ds = b ? 0.0 : site_dS(cfg, q, fpl, fsl);
+                if (!dS_ok(cfg, ds)) b = 1;
                 if (b) ds = INFINITY;
                 dsi = 0.0;
             }
@@ -412,14 +520,23 @@ static int run_collide_and_limit(const orc_config *cfg, unsigned limiters, int d
             bad[s] = (unsigned char)b;
             st.mass += rho;
             if (!b) {
-                st.sum_dS += ds;
-                sum_in += dsi;
+                if (cfg->equilibrium == ORC_EQ_ENTROPIC) {
+                    /* entropy differences where both entropies are finite */
+                    if (isfinite(ds)) st.sum_dS += ds;
+                    if (isfinite(ds) && isfinite(dsi)) sum_in += dsi - ds;
+                } else {
+                    st.sum_dS += ds;
+                    sum_in += dsi;
+                }
             } else {
                 st.n_bad++;
             }
         }
     }
-    st.dS_lbgk = do_stream ? (1.0 - a * a) * sum_in : 0.0;
+    if (cfg->equilibrium == ORC_EQ_ENTROPIC)
+        st.dS_lbgk = do_stream ? sum_in : 0.0;
+    else
+        st.dS_lbgk = do_stream ? (1.0 - a * a) * sum_in : 0.0;
     limit_core(cfg, limiters, fs, fp, dS, bad, f_out, phi_field, sel, n_sel, &st);
     if (dS_field) memcpy(dS_field, dS, sizeof(double) * (size_t)n);
     if (stats) *stats = st;

@@ -16,6 +16,8 @@
  *   - the LBGK collision with over-relaxation (Eq. collLBGK, Eq. lbgkLB),
  *   - the nonequilibrium entropy in its quadratic Kullback form (Eq. DelS
  *     and the quadratic approximation that follows it in Sec. 3.6),
+ *   - optionally entropic quasiequilibria (Eq. entropiceq1d, Eq. maxwellian)
+ *     with the exact relative entropy of Eq. DelS,
  *   - the limiters f -> f* + phi (f - f*) (Eq. LimGenF): the positivity rule
  *     (Sec. 3.1), the entropic median filter (Sec. 3.5, Sec. 4.3.2, Sec. 4.4)
  *     and Ehrenfests' trimming with at most k sites per step (Sec. 3.2),
@@ -47,6 +49,9 @@ extern "C" {
 #define ORC_MEDIAN_THRESHOLD 0 /* dS_t = max(dS_med, delta); phi = sqrt(dS_t/dS) where dS > dS_t */
 #define ORC_MEDIAN_GATE 1      /* phi = sqrt(dS_med/dS) where dS > delta and dS_med < dS */
 
+#define ORC_EQ_POLYNOMIAL 0 /* Eq. polyeq1d / polyeq2d; dS in its quadratic form */
+#define ORC_EQ_ENTROPIC 1   /* Eq. entropiceq1d / maxwellian; dS = sum_k f_k ln(f_k / f*_k) (Eq. DelS) */
+
 typedef struct {
     int lattice;            /* ORC_D1Q3 or ORC_D2Q9 */
     int nx, ny;             /* lattice size; ny = 1 for D1Q3 */
@@ -59,8 +64,18 @@ typedef struct {
     double delta_ehrenfest; /* Ehrenfests' threshold */
     long long k_max;        /* at most this many Ehrenfests' sites per step */
     int median_mode;        /* ORC_MEDIAN_* */
+    int equilibrium;        /* ORC_EQ_* */
 } orc_config;
 
+/*
+ * With entropic quasiequilibria (ORC_EQ_ENTROPIC) dS is the exact relative
+ * entropy, which is +inf for a state with a negative population (outside the
+ * domain of S; such a site is not flagged bad).  The entropy productions are
+ * then evaluated as entropy differences at the sites where both entropies are
+ * finite:  dS_lbgk = sum [dS(f_in) - dS(f')],  dS_lim = sum [dS(f') - dS(f_out)]
+ * over the limited sites plus dS(f_lim) w.r.t. f*(m(f_lim)) at each
+ * Ehrenfests' site, and sum_dS skips infinite values.
+ */
 typedef struct {
     double mass;      /* sum of rho over sites (after free flight) */
     double sum_dS;    /* sum of dS(f') over sites, f' = post-collision, pre-limiter */
@@ -75,6 +90,21 @@ typedef struct {
 
 /* Polynomial quasiequilibrium f*(rho, u) at one site (Eq. polyeq1d / Eq. polyeq2d). */
 void orc_feq(int lattice, double rho, double ux, double uy, double *feq);
+
+/*
+ * Entropic quasiequilibrium f*(rho, u) at one site: Eq. entropiceq1d (D1Q3;
+ * the printed f2* is the v = +1 population and f3* the v = -1 one, the order
+ * in which sum_k v_k f*_k = rho u) and Eq. maxwellian (D2Q9).  Defined for
+ * |u_x|, |u_y| < 1; returns 0 there, else 1 (feq is then left unspecified).
+ */
+int orc_feq_entropic(int lattice, double rho, double ux, double uy, double *feq);
+
+/* Lattice entropy with 0 ln 0 = 0: D2Q9 S(f) = -sum_k f_k ln(f_k / W_k) (Sec. 4.1, Sec. 3.6);
+ * D1Q3 S = -H, H = f_rest ln(f_rest / 4) + f_left ln f_left + f_right ln f_right (Sec. 4.1). */
+double orc_entropy(int lattice, const double *f);
+
+/* Relative entropy sum_k f_k ln(f_k / fs_k) (Eq. DelS) of q populations, 0 ln 0 = 0, +inf if some f_k < 0. */
+double orc_rel_entropy(int q, const double *f, const double *fs);
 
 /* Moments rho, u of one site's populations (Eq. macro_dis). */
 void orc_site_moments(int lattice, const double *f, double *rho, double *ux, double *uy);
