@@ -45,7 +45,9 @@ def parse():
     ap.add_argument("--develop", type=int, default=500,
                     help="untimed steps before warm-up so the flow has left the rest state")
     ap.add_argument("--kernel", default="auto", choices=["auto", "tiled", "fused"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16"],
+    ap.add_argument("--equilibrium", default="polynomial", choices=["polynomial", "entropic"],
+                    help="entropic: Eq. maxwellian f* with the exact dS of Eq. DelS (needs --precision fp64)")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16", "fp64"],
                     help="population storage (arithmetic is FP32 in all three)")
     ap.add_argument("--side", type=int, default=4096,
                     help="cavity side (4096 is the workload; smaller sides are for profiling)")
@@ -120,19 +122,26 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def source_hash() -> str:
+# The sources each step kernel is compiled from (its .cu file and every header
+# it includes): a recorded ncu figure stays valid while these are unchanged.
+KERNEL_SOURCES = {
+    "fused": ["paper_0704_0043_gb300/csrc/step_fused.cu", "paper_0704_0043_gb300/csrc/keys.cuh",
+              "paper_0704_0043_gb300/csrc/lattice.cuh", "paper_0704_0043_gb300/csrc/internal.h",
+              "include/lbm.h"],
+    "tiled": ["paper_0704_0043_gb300/csrc/step_tiled.cu", "paper_0704_0043_gb300/csrc/lattice.cuh",
+              "paper_0704_0043_gb300/csrc/internal.h", "include/lbm.h"],
+}
+
+
+def source_hash(kernel: str) -> str:
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_0704_0043_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, name), "rb") as fh:
-                h.update(name.encode() + fh.read())
+    for rel in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(rel.encode() + fh.read())
     return h.hexdigest()[:16]
 
 
-def traffic_from_profile(kernel_name: str, sites: int):
-    """DRAM bytes per launch of the step kernel from the committed ncu summary,
-    scaled to this lattice; None when the kernel sources changed since."""
+def _profile_entry(kernel_name: str):
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as fh:
@@ -140,7 +149,26 @@ def traffic_from_profile(kernel_name: str, sites: int):
     except Exception:
         return None
     ent = d.get(kernel_name)
-    if not ent or ent.get("src_hash") != source_hash():
+    if not ent or ent.get("src_hash") != source_hash(kernel_name.split("_")[0]):
+        return None
+    return ent
+
+
+def fp64_flops_from_profile(kernel_name: str, sites: int):
+    """Executed FP64 FLOPs per launch (dadd + dmul + 2 dfma per thread
+    instruction, from ncu) scaled to this lattice; None when the kernel's
+    sources changed since the count was taken."""
+    ent = _profile_entry(kernel_name)
+    if not ent or "fp64_flops_per_site" not in ent:
+        return None
+    return ent["fp64_flops_per_site"] * sites
+
+
+def traffic_from_profile(kernel_name: str, sites: int):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary,
+    scaled to this lattice; None when the kernel's sources changed since."""
+    ent = _profile_entry(kernel_name)
+    if not ent:
         return None
     return ent["dram_bytes_per_site"] * sites
 
@@ -158,29 +186,31 @@ def workload(side: int = 4096):
     return w
 
 
-def lattice_kwargs(w, kernel: str, precision: str = "fp32"):
+def lattice_kwargs(w, kernel: str, precision: str = "fp32", equilibrium: str = "polynomial"):
     from paper_0704_0043_gb300 import lbm
     km = {"auto": lbm.KERNEL_AUTO, "tiled": lbm.KERNEL_TILED, "fused": lbm.KERNEL_FUSED}[kernel]
-    pm = {"fp32": lbm.FP32, "bf16": lbm.BF16, "fp16": lbm.FP16}[precision]
+    pm = {"fp32": lbm.FP32, "bf16": lbm.BF16, "fp16": lbm.FP16, "fp64": lbm.FP64}[precision]
+    em = {"polynomial": lbm.EQ_POLYNOMIAL, "entropic": lbm.EQ_ENTROPIC}[equilibrium]
     return dict(lattice=lbm.D2Q9, nx=w.nx, ny=w.ny, boundary=lbm.BC_WALLS, precision=pm,
                 beta=w.beta, u_lid=w.u_lid, rho_wall=w.rho0, limiters=w.limiters,
                 delta_median=w.delta_median, delta_ehrenfest=w.delta_ehrenfest, k_max=w.k_max,
-                kernel=km)
+                kernel=km, equilibrium=em)
 
 
-def oracle_cfg(w, side: int):
+def oracle_cfg(w, side: int, equilibrium: str = "polynomial"):
     import oracle
     return oracle.Config(lattice=oracle.D2Q9, nx=side, ny=side, boundary=oracle.BC_WALLS,
                          beta=w.beta, u_lid=w.u_lid, rho_wall=w.rho0, limiters=w.limiters,
                          delta_median=w.delta_median, delta_ehrenfest=w.delta_ehrenfest,
-                         k_max=max(1, int(1e-4 * side * side)))
+                         k_max=max(1, int(1e-4 * side * side)),
+                         equilibrium=oracle.EQ_ENTROPIC if equilibrium == "entropic" else oracle.EQ_POLYNOMIAL)
 
 
-def cpu_baseline(w, steps: int = 1):
+def cpu_baseline(w, steps: int = 1, equilibrium: str = "polynomial"):
     """The FP64 oracle as it stands, single-threaded, on `steps` full-size steps."""
     import oracle
     from paper_0704_0043_gb300 import inputs
-    oc = oracle_cfg(w, w.nx)
+    oc = oracle_cfg(w, w.nx, equilibrium)
     rho, ux, uy = inputs.cavity_rest(w.nx, w.ny, w.rho0)
     f = oracle.init(oc, rho, ux, uy)
     t0 = time.perf_counter()
@@ -376,7 +406,12 @@ def main():
     lbm.lib()
 
     w = workload(args.side)
-    lat = lbm.Lattice(**lattice_kwargs(w, args.kernel, args.precision))
+    entropic = args.equilibrium == "entropic"
+    if entropic:
+        if args.precision != "fp64":
+            raise SystemExit("--equilibrium entropic needs --precision fp64")
+        w.name = w.name.replace("cavity_d2q9", "cavity_d2q9_entropic")
+    lat = lbm.Lattice(**lattice_kwargs(w, args.kernel, args.precision, args.equilibrium))
     rho, ux, uy = inputs.cavity_rest(w.nx, w.ny, w.rho0)
     lat.init(rho, ux, uy)
     lat.step(args.develop + args.warmup)
@@ -422,21 +457,43 @@ def main():
             "timed_launches": timed, "timed_every": TIMING_EVERY,
             "bytes_per_site": bps}
 
+    if entropic:
+        # The entropic step is bound by FP64 arithmetic (a logarithm per population
+        # and sqrt / divisions for f*), not by HBM: the roofline is the FP64 pipe
+        # (152 SMs x 2 FP64 FMA per clock x 2 FLOP at the sampled SM clock), and
+        # the executed FP64 FLOPs per site come from one ncu count of the kernel's
+        # FP64 instructions (profiles/traffic.json).
+        fl = fp64_flops_from_profile("tiled_fp64_entropic", w.sites)
+        mhz = (clocks or {}).get("sm_mhz") or 2070.0
+        fpeak = 152 * 2 * 2 * mhz * 1e6 / 1e9
+        roof_hbm = dict(roof)
+        roof = {"bound": "alu", "unit": "GFLOP/s", "peak": fpeak,
+                "peak_kind": "derived: 152 SMs x 4 FP64 FLOP/clk x sampled SM clock",
+                "achieved": fl / kern_s / 1e9 if fl else None,
+                "frac": (fl / kern_s / 1e9) / fpeak if fl else None,
+                "fp64_flops_per_site": fl / w.sites if fl else None,
+                "traffic": traffic_from_profile("tiled_fp64_entropic", w.sites), "kernel": kname,
+                "kernel_ms": kern_s * 1e3,
+                "tail_kernel_ms": roof_hbm["tail_kernel_ms"], "timed_launches": timed,
+                "timed_every": TIMING_EVERY, "hbm": {k: roof_hbm[k] for k in ("achieved", "peak", "frac", "bytes_per_site")}}
+
     e2e = None
     if not args.no_e2e:
         e2e = end_to_end(lat, w, args.steps, torch)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(w, 1)
+        cpu = cpu_baseline(w, 1, args.equilibrium)
     out = {"metric": "limited-LBM MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": elapsed * 1e3 / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
+           "data": "synthetic",
            "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "reynolds": 7500,
                       "u_lid": w.u_lid, "beta": w.beta, "limiters": "median+ehrenfest",
                       "delta": 1e-3, "k_max": w.k_max, "storage": args.precision, "sums": "fp64",
+                      "equilibrium": args.equilibrium,
                       "kernel": kname, "develop_steps": args.develop,
-                      "l2": "inputs larger than L2 (1.2 GB population buffers vs 129 MB L2)",
+                      "l2": f"inputs larger than L2 ({9 * w.sites * (8 if args.precision == 'fp64' else 4 if args.precision == 'fp32' else 2) / 1e9:.1f} GB population buffers vs 129 MB L2)",
                       "parallelism": f"replicas{world}" if world > 1 else "single"},
            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
            "clocks": clocks,

@@ -7,9 +7,11 @@
  * One step (Eq. lbgkLB; the limiter is "a post-processing routine immediately
  * following the collision step", Sec. 4.3.2):
  *   free flight in pull form, halfway bounce-back walls, moving lid (Sec. 2, Sec. 4.4.1)
- *   -> moments (Eq. macro_dis) -> polynomial f* (Eq. polyeq1d / Eq. polyeq2d)
+ *   -> moments (Eq. macro_dis) -> polynomial f* (Eq. polyeq1d / Eq. polyeq2d),
+ *      or entropic f* (Eq. entropiceq1d / Eq. maxwellian, LBM_EQ_ENTROPIC)
  *   -> LBGK collision f' = f* + (2 beta - 1)(f* - f)      (Eq. collLBGK)
- *   -> dS(f') = sum_k (f'_k - f*_k)^2 / f*_k              (Sec. 3.6, quadratic form of Eq. DelS)
+ *   -> dS(f') = sum_k (f'_k - f*_k)^2 / f*_k              (Sec. 3.6, quadratic form of Eq. DelS;
+ *      LBM_EQ_ENTROPIC: sum_k f'_k ln(f'_k / f*_k), Eq. DelS)
  *   -> limiters f -> f* + phi (f - f*)                     (Eq. LimGenF):
  *      positivity rule (Sec. 3.1), median filter (Sec. 3.5), Ehrenfests' trimming (Sec. 3.2)
  *   -> stored field for the next step, plus FP64 sums (Sec. 3.4, Sec. 4.3.1).
@@ -77,6 +79,21 @@ enum {
     LBM_MEDIAN_GATE = 1       /* phi = sqrt(dS_med/dS) where dS > delta and dS_med < dS */
 };
 
+/* Quasiequilibrium and nonequilibrium entropy.
+ * LBM_EQ_POLYNOMIAL: f* of Eq. polyeq1d / Eq. polyeq2d, dS(f) = sum_k (f_k - f*_k)^2 / f*_k
+ *   (the quadratic form of Eq. DelS, Sec. 3.6).
+ * LBM_EQ_ENTROPIC: f* of Eq. entropiceq1d / Eq. maxwellian (the D1Q3 population with
+ *   v = +1 takes the printed f2*, the assignment under which sum_k v_k f*_k = rho u),
+ *   and the exact dS(f) = sum_k f_k ln(f_k / f*_k) of Eq. DelS, with 0 ln 0 = 0 and
+ *   dS = +inf for a state with a negative population (not an error: the limiters act
+ *   on it; the median homothety is then 0).  Sites with |u_x| or |u_y| >= 1 have no
+ *   entropic f* and are flagged (LBM_ERR_NONFINITE).  The stats are entropy
+ *   differences: dS_lbgk = sum [dS(f_in) - dS(f')], dS_lim = sum [dS(f') - dS(f_out)]
+ *   plus dS of each Ehrenfests' site's state w.r.t. its own f*, each over the sites
+ *   where both values are finite; sum_dS skips infinite values.  FP64 storage and the
+ *   tiled kernel only; lbm_init then starts from the entropic f*. */
+enum { LBM_EQ_POLYNOMIAL = 0, LBM_EQ_ENTROPIC = 1 };
+
 /* Kernel choice for lbm_step. */
 enum {
     LBM_KERNEL_AUTO = 0,    /* fused D2Q9 cavity kernel where it applies, else the tiled kernel */
@@ -99,7 +116,7 @@ typedef struct lbm_config {
     double delta_ehrenfest;  /* Ehrenfests' threshold: sites with dS > delta are candidates */
     int64_t k_max;           /* Ehrenfests' step acts on at most k_max sites per step (>= 0) */
     int32_t stats_history;   /* per-step stats kept on the device (ring length, >= 1) */
-    int32_t reserved;        /* must be 0 */
+    int32_t equilibrium;     /* LBM_EQ_* (LBM_EQ_ENTROPIC needs LBM_FP64) */
     double rho_ref;          /* reference density of the FP32 deviation storage (> 0, default 1) */
 } lbm_config;
 
@@ -134,7 +151,8 @@ lbm_status lbm_create(const lbm_config *cfg, void *cuda_stream, lbm_ctx **out);
 /* Synchronises the context's stream and frees everything it owns.  NULL is a no-op. */
 lbm_status lbm_destroy(lbm_ctx *ctx);
 
-/* Populations at polynomial equilibrium f*(rho, u) (Eq. polyeq1d / Eq. polyeq2d),
+/* Populations at equilibrium f*(rho, u) of the configured kind (Eq. polyeq1d / Eq. polyeq2d;
+ * LBM_EQ_ENTROPIC: Eq. entropiceq1d / Eq. maxwellian, NaN where |u_j| >= 1),
  * evaluated in FP64 and stored at the context's precision; resets the step
  * counter and the stats.  rho, ux: nx * ny doubles; uy: nx * ny doubles or NULL
  * (taken as 0; ignored for D1Q3).  Errors: LBM_ERR_INVALID_ARG (NULL rho/ux). */

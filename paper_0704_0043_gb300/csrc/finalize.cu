@@ -388,11 +388,18 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, 
 #pragma unroll
                 for (int q = 0; q < Q; ++q) g[q] = s2f(f[fidx(p.plane, p.pitch, q, y, x)]);
                 moments<Q, T>(g, rho, ux, uy);
-                feq<Q, T>(rho, ux, uy, fs);
+                if (p.eq == 1) {
+                    // entropic f*: the step adds dS of the limited state w.r.t. its own f*
+                    feq_any<Q>(1, rho, ux, uy, fs);
+                    const double d = rel_entropy<Q>(g, fs);
+                    if (isfinite(d)) ehr_sum = Ar<double>::add(ehr_sum, d);
+                } else {
+                    feq<Q, T>(rho, ux, uy, fs);
+                }
             }
 #pragma unroll
             for (int q = 0; q < Q; ++q) f[fidx(p.plane, p.pitch, q, y, x)] = f2s<S>(fs[q]);
-            ehr_sum = Ar<double>::add(ehr_sum, Ar<double>::mul(Ar<double>::mul(c.phi, c.phi), c.key));
+            if (p.eq != 1) ehr_sum = Ar<double>::add(ehr_sum, Ar<double>::mul(Ar<double>::mul(c.phi, c.phi), c.key));
         }
         __syncthreads();
         // the chosen sites, as site indices, for lbm_limited_sites

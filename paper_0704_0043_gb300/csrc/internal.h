@@ -68,6 +68,7 @@ struct StepParams {
     unsigned limiters;
     int median_mode;
     int collide;               // 1: free flight + collision; 0: limiter pass on stored state
+    int eq;                    // 0: polynomial f*, quadratic dS; 1: entropic f*, exact dS (FP64 storage)
     double a;                  // 2 beta - 1
     double delta_m, delta_e;
     double lid[9];             // ((6 W_k) rho_wall) (c_kx u_lid), added on links through the lid
@@ -96,6 +97,7 @@ struct FinalParams {
     long long k_max;
     int ehrenfest;             // apply Ehrenfests' step
     int collide;
+    int eq;                    // as StepParams::eq
     int nx, ny, pitch;
     long long plane;
     double *partials;          // fused kernel: the accumulator rows, cleared once read

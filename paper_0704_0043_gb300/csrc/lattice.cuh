@@ -174,6 +174,107 @@ __device__ __forceinline__ void feq(T rho, T ux, T uy, T fs[Q])
         feq3<T>(rho, ux, fs);
 }
 
+// Entropic quasiequilibria (FP64 only), in the oracle's operation order.
+// Eq. maxwellian: f*_k = rho W_k prod_j A_j X_j^{v_kj} with
+// A_j = 2 - sqrt(1 + 3 u_j^2), X_j = (2 u_j + sqrt(1 + 3 u_j^2)) / (1 - u_j);
+// v_kj = -1 divides by X_j.  Exists for |u_x|, |u_y| < 1 (returns false otherwise).
+__device__ __forceinline__ bool feq_ent9(double rho, double ux, double uy, double fs[9])
+{
+    using A = Ar<double>;
+    if (!(fabs(ux) < 1.0) || !(fabs(uy) < 1.0)) return false;
+    const double u[2] = {ux, uy};
+    double Aj[2], Xj[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const double sq = A::sqrt(A::add(1.0, A::mul(3.0, A::mul(u[j], u[j]))));
+        Aj[j] = A::sub(2.0, sq);
+        Xj[j] = A::div(A::add(A::mul(2.0, u[j]), sq), A::sub(1.0, u[j]));
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const int v[2] = {Lat<9>::cx(k), Lat<9>::cy(k)};
+        double f = A::mul(rho, Lat<9>::w(k));
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const double P = v[j] == 1 ? A::mul(Aj[j], Xj[j]) : (v[j] == -1 ? A::div(Aj[j], Xj[j]) : Aj[j]);
+            f = A::mul(f, P);
+        }
+        fs[k] = f;
+    }
+    return true;
+}
+
+// Eq. entropiceq1d, with the printed f2* as the v = +1 population (index 2)
+// and the printed f3* as the v = -1 one (index 1): the assignment under which
+// sum_k v_k f*_k = rho u.
+__device__ __forceinline__ bool feq_ent3(double rho, double u, double fs[3])
+{
+    using A = Ar<double>;
+    if (!(fabs(u) < 1.0)) return false;
+    const double sq = A::sqrt(A::add(1.0, A::mul(3.0, A::mul(u, u))));
+    fs[0] = A::mul(A::div(A::mul(2.0, rho), 3.0), A::sub(2.0, sq));
+    const double r6 = A::div(rho, 6.0);
+    fs[1] = A::mul(-r6, A::sub(A::add(A::mul(3.0, u), 1.0), A::mul(2.0, sq)));
+    fs[2] = A::mul(r6, A::add(A::sub(A::mul(3.0, u), 1.0), A::mul(2.0, sq)));
+    return true;
+}
+
+// f* of either kind (eq = 1: entropic); false where the entropic f* does not exist.
+template <int Q>
+__device__ __forceinline__ bool feq_any(int eq, double rho, double ux, double uy, double fs[Q])
+{
+    if (eq == 1) {
+        if constexpr (Q == 9)
+            return feq_ent9(rho, ux, uy, fs);
+        else
+            return feq_ent3(rho, ux, fs);
+    }
+    feq<Q, double>(rho, ux, uy, fs);
+    return true;
+}
+
+// f ln(f / f*) for f > 0, f* > 0 (FP64).  Where f is within 2^-5 of f*
+// (almost every site of a flow) by the series of the inverse hyperbolic
+// tangent, ln(f / f*) = 2 atanh z = 2 (z + z^3/3 + z^5/5 + ...) with
+// z = (f - f*) / (f + f*): f - f* is exact there (Sterbenz), z carries two
+// roundings, and with |z| < 0.016 the terms past z^9/9 are below 1e-19 of the
+// sum, so the logarithm is within a few ulps of ln(f / f*) itself.  Elsewhere
+// the CUDA logarithm of the rounded ratio.  The series costs one division and
+// five multiply-adds instead of a division and a general logarithm.
+__device__ __forceinline__ double f_ln_ratio(double f, double fs)
+{
+    const double d = f - fs;
+    if (!(fabs(d) < 0.03125 * fs)) return Ar<double>::mul(f, log(Ar<double>::div(f, fs)));
+    const double z = d / (f + fs);
+    const double w = z * z;
+    double p = fma(w, 1.0 / 9.0, 1.0 / 7.0);
+    p = fma(p, w, 1.0 / 5.0);
+    p = fma(p, w, 1.0 / 3.0);
+    const double t = 2.0 * z;
+    return f * fma(t * w, p, t);
+}
+
+// Eq. DelS: sum_k f_k ln(f_k / f*_k), k order, 0 ln 0 = 0; +inf for a state
+// with a negative population (outside the domain of the entropy), NaN for a
+// NaN population.
+template <int Q>
+__device__ __forceinline__ double rel_entropy(const double f[Q], const double fs[Q])
+{
+    using A = Ar<double>;
+    bool neg = false, nan = false;
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+        neg |= f[k] < 0.0;
+        nan |= !(f[k] >= 0.0) && !(f[k] < 0.0);
+    }
+    if (neg) return (double)INFINITY;
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < Q; ++k)
+        if (f[k] > 0.0) s = A::add(s, f_ln_ratio(f[k], fs[k]));
+    return nan ? (double)NAN : s;
+}
+
 // Quadratic nonequilibrium entropy (Sec. 3.6): sum_k (g_k - f*_k)^2 / f*_k, k order.
 template <int Q, typename T>
 __device__ __forceinline__ T quad_entropy(const T g[Q], const T fs[Q])
@@ -191,19 +292,41 @@ __device__ __forceinline__ T quad_entropy(const T g[Q], const T fs[Q])
 // Collision and entropy at one site from its arriving populations f_in:
 // f*, f' = f* + a (f* - f_in) with a = 2 beta - 1 (Eq. collLBGK), dS(f'),
 // dS(f_in) and rho.  With collide = false (limiter pass on a stored state)
-// f' = f_in.  Returns true for a site that cannot be limited: rho <= 0,
-// f*_k <= 0 for some k, or a nonfinite value.
+// f' = f_in.  Returns true for a site that cannot be limited: rho <= 0, no f*
+// or f*_k <= 0 for some k, or a nonfinite value.  eq = 1 (FP64 only):
+// entropic f* and the exact relative entropy, which is +inf (not an error)
+// for a state with a negative population; need_in = false skips dS(f_in).
 template <int Q, typename T>
 __device__ __forceinline__ bool site_collide(const T fin[Q], T a, bool collide, T fs[Q], T fp[Q],
-                                             T &ds, T &ds_in, T &rho)
+                                             T &ds, T &ds_in, T &rho, int eq = 0, bool need_in = true)
 {
     using A = Ar<T>;
     T ux, uy;
     moments<Q, T>(fin, rho, ux, uy);
+    bool bad = !(rho > T(0)) || !isfinite(rho) || !isfinite(ux) || !isfinite(uy);
+    if constexpr (std::is_same<T, double>::value) {
+        if (eq == 1) {
+            if (!feq_any<Q>(1, rho, ux, uy, fs)) {
+                bad = true;
+#pragma unroll
+                for (int k = 0; k < Q; ++k) fs[k] = 0.0;
+            }
+#pragma unroll
+            for (int k = 0; k < Q; ++k) fp[k] = collide ? A::add(fs[k], A::mul(a, A::sub(fs[k], fin[k]))) : fin[k];
+#pragma unroll
+            for (int k = 0; k < Q; ++k) bad |= !(fs[k] > 0.0) || !isfinite(fs[k]) || !isfinite(fin[k]);
+            ds = bad ? 0.0 : rel_entropy<Q>(fp, fs);
+            // dS(f_in) feeds only the statistics: sites that only supply a
+            // stencil value (need_in = false) skip it; with finite populations
+            // and f* > 0 it is never NaN, so the flag does not depend on it
+            ds_in = (bad || !collide || !need_in) ? 0.0 : rel_entropy<Q>(fin, fs);
+            bad |= isnan(ds) || isnan(ds_in);
+            return bad;
+        }
+    }
     feq<Q, T>(rho, ux, uy, fs);
 #pragma unroll
     for (int k = 0; k < Q; ++k) fp[k] = collide ? A::add(fs[k], A::mul(a, A::sub(fs[k], fin[k]))) : fin[k];
-    bool bad = !(rho > T(0)) || !isfinite(rho) || !isfinite(ux) || !isfinite(uy);
 #pragma unroll
     for (int k = 0; k < Q; ++k) bad |= !(fs[k] > T(0)) || !isfinite(fin[k]);
     ds = quad_entropy<Q, T>(fp, fs);

@@ -97,6 +97,9 @@ std::string validate(const lbm_config *c)
     if (c->k_max < 0) return "k_max must be >= 0";
     if (c->median_mode != LBM_MEDIAN_THRESHOLD && c->median_mode != LBM_MEDIAN_GATE) return "unknown median_mode";
     if (c->kernel < LBM_KERNEL_AUTO || c->kernel > LBM_KERNEL_FUSED) return "unknown kernel";
+    if (c->equilibrium != LBM_EQ_POLYNOMIAL && c->equilibrium != LBM_EQ_ENTROPIC) return "unknown equilibrium";
+    if (c->equilibrium == LBM_EQ_ENTROPIC && c->precision != LBM_FP64)
+        return "entropic quasiequilibria need LBM_FP64 storage";
     if (c->kernel == LBM_KERNEL_FUSED && !fused_applies(*c))
         return "LBM_KERNEL_FUSED needs D2Q9, FP32/BF16/FP16 storage and LBM_BC_WALLS";
     if (c->stats_history < 0) return "stats_history must be >= 0";
@@ -189,6 +192,7 @@ StepParams step_params(lbm_ctx *c, int collide, unsigned limiters)
     p.limiters = limiters;
     p.median_mode = g.median_mode;
     p.collide = collide;
+    p.eq = g.equilibrium == LBM_EQ_ENTROPIC ? 1 : 0;
     p.a = 2.0 * g.beta - 1.0;
     p.delta_m = g.delta_median;
     p.delta_e = g.delta_ehrenfest;
@@ -220,7 +224,9 @@ FinalParams final_params(lbm_ctx *c, int collide, unsigned limiters, int nblocks
     FinalParams f{};
     f.nblocks = nblocks;
     const double a = 2.0 * g.beta - 1.0;
-    f.one_minus_a2 = 1.0 - a * a;
+    // entropic f*: the step kernel sums dS(f_in) - dS(f') itself (no quadratic identity)
+    f.one_minus_a2 = g.equilibrium == LBM_EQ_ENTROPIC ? 1.0 : 1.0 - a * a;
+    f.eq = g.equilibrium == LBM_EQ_ENTROPIC ? 1 : 0;
     f.k_max = g.k_max;
     f.ehrenfest = (limiters & LBM_LIM_EHRENFEST) ? 1 : 0;
     f.collide = collide;
@@ -397,6 +403,7 @@ void lbm_config_default(lbm_config *c)
     c->delta_ehrenfest = 1e-3;
     c->k_max = 0;
     c->stats_history = 1;
+    c->equilibrium = LBM_EQ_POLYNOMIAL;
     c->rho_ref = 1.0;
 }
 

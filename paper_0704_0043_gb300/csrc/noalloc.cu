@@ -111,6 +111,7 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_config *cfg, const double *f_in
     p.limiters = cfg->limiters;
     p.median_mode = cfg->median_mode;
     p.collide = 1;
+    p.eq = cfg->equilibrium == LBM_EQ_ENTROPIC ? 1 : 0;
     p.a = 2.0 * cfg->beta - 1.0;
     p.delta_m = cfg->delta_median;
     p.delta_e = cfg->delta_ehrenfest;
@@ -136,7 +137,8 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_config *cfg, const double *f_in
 
     FinalParams f{};
     f.nblocks = nblocks;
-    f.one_minus_a2 = 1.0 - p.a * p.a;
+    f.one_minus_a2 = p.eq ? 1.0 : 1.0 - p.a * p.a;  // entropic f*: the step sums dS(f_in) - dS(f')
+    f.eq = p.eq;
     f.k_max = cfg->k_max;
     f.ehrenfest = ehr ? 1 : 0;
     f.collide = 1;

@@ -166,7 +166,9 @@ __global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const S *__r
             for (int k = 0; k < Q; ++k) fin[k] = load_as<S, T>(p, src[fidx(p.plane, p.pitch, k, ys, xs)], k);
         }
         if constexpr (std::is_same<T, double>::value) {
-            bad = site_collide<Q, T>(fin, T(p.a), p.collide != 0, fs, fp, ds, dsin, rho);
+            // entropic f*: the halo ring only supplies dS(f') to the median stencils
+            const bool owner = tx >= 1 && tx <= BX - 2 && (Q == 3 || (ty >= 1 && ty <= BY - 2));
+            bad = site_collide<Q, T>(fin, T(p.a), p.collide != 0, fs, fp, ds, dsin, rho, p.eq, owner);
 #pragma unroll
             for (int k = 0; k < Q; ++k) fa[k] = fs[k];
         } else {
@@ -197,7 +199,9 @@ __global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const S *__r
                     }
                 }
             }
-            if (p.limiters & 4u) {
+            // the homothety acts only where dS > delta_m (both acceptance
+            // rules), so the median is formed only there
+            if ((p.limiters & 4u) && ds > T(p.delta_m)) {
                 T med;
                 if (stencil_median<Q, T>(p, sds, BX, tx, ty, x, y, med))
                     phi_med = phi_median<T>(ds, med, T(p.delta_m), p.median_mode);
@@ -206,23 +210,39 @@ __global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const S *__r
         const T phi = phi_pos < phi_med ? phi_pos : phi_med;
         if (phi < T(1)) {
             if constexpr (std::is_same<T, double>::value) {
+                double fo[Q];
 #pragma unroll
-                for (int k = 0; k < Q; ++k)
-                    dst[fidx(p.plane, p.pitch, k, y, x)] = f2s<S>(A::add(fs[k], A::mul(phi, A::sub(fp[k], fs[k]))));
+                for (int k = 0; k < Q; ++k) {
+                    fo[k] = A::add(fs[k], A::mul(phi, A::sub(fp[k], fs[k])));
+                    dst[fidx(p.plane, p.pitch, k, y, x)] = f2s<S>(fo[k]);
+                }
+                if (p.eq == 1) {
+                    // entropic f*: the entropy difference dS(f') - dS(f_out) at the same f*
+                    const double dout = rel_entropy<Q>(fo, fs);
+                    if (isfinite(ds) && isfinite(dout)) acc[P_DS_LIM] = A::sub(ds, dout);
+                } else {
+                    acc[P_DS_LIM] = A::mul(A::sub(1.0, A::mul(phi, phi)), ds);
+                }
             } else {
                 const float c = limit_weight(phi, (float)p.a, p.collide != 0);
 #pragma unroll
                 for (int k = 0; k < Q; ++k) dst[fidx(p.plane, p.pitch, k, y, x)] = f2s<S>(fmaf(-c, nq[k], fin[k]));
+                acc[P_DS_LIM] = Ar<double>::mul(Ar<double>::sub(1.0, Ar<double>::mul((double)phi, (double)phi)), (double)ds);
             }
-            acc[P_DS_LIM] = Ar<double>::mul(Ar<double>::sub(1.0, Ar<double>::mul((double)phi, (double)phi)), (double)ds);
         } else {
 #pragma unroll
             for (int k = 0; k < Q; ++k) dst[fidx(p.plane, p.pitch, k, y, x)] = f2s<S>(fp[k]);
         }
         acc[P_MASS] = (double)rho;
         if (!bad) {
-            acc[P_SUM_DS] = (double)ds;
-            acc[P_SUM_IN] = (double)dsin;
+            if (p.eq == 1) {
+                // entropic f*: sums of entropy differences where both entropies are finite
+                if (isfinite(ds)) acc[P_SUM_DS] = (double)ds;
+                if (isfinite(ds) && isfinite(dsin)) acc[P_SUM_IN] = Ar<double>::sub((double)dsin, (double)ds);
+            } else {
+                acc[P_SUM_DS] = (double)ds;
+                acc[P_SUM_IN] = (double)dsin;
+            }
         } else {
             acc[P_NBAD] = 1.0;
             atomicOr(p.status, kStatNonfinite);
@@ -291,7 +311,7 @@ __global__ void k_delta_s(StepParams p, const S *__restrict__ f, double *__restr
         const int x = (int)(s % p.nx), y = (int)(s / p.nx);
         double fin[Q], fs[Q], fp[Q], ds, dsin, rho;
         pull<Q, S, double>(p, f, x, y, fin);
-        const bool bad = site_collide<Q, double>(fin, p.a, true, fs, fp, ds, dsin, rho);
+        const bool bad = site_collide<Q, double>(fin, p.a, true, fs, fp, ds, dsin, rho, p.eq);
         out[s] = bad ? (double)INFINITY : ds;
     }
 }
@@ -304,7 +324,10 @@ __global__ void k_init(StepParams p, const double *__restrict__ rho, const doubl
     for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(s % p.nx), y = (int)(s / p.nx);
         double fs[Q];
-        feq<Q, double>(rho[s], ux[s], uy ? uy[s] : 0.0, fs);
+        if (!feq_any<Q>(p.eq, rho[s], ux[s], uy ? uy[s] : 0.0, fs)) {
+#pragma unroll
+            for (int k = 0; k < Q; ++k) fs[k] = (double)NAN;  // no entropic f* for |u_j| >= 1
+        }
 #pragma unroll
         for (int k = 0; k < Q; ++k) {
             if constexpr (std::is_same<S, double>::value)

@@ -22,6 +22,7 @@ FP64, FP32, BF16, FP16 = 0, 1, 2, 3
 BC_WALLS, BC_PERIODIC, BC_CHANNEL = 0, 1, 2
 LIM_POSITIVITY, LIM_EHRENFEST, LIM_MEDIAN = 1, 2, 4
 MEDIAN_THRESHOLD, MEDIAN_GATE = 0, 1
+EQ_POLYNOMIAL, EQ_ENTROPIC = 0, 1
 KERNEL_AUTO, KERNEL_TILED, KERNEL_FUSED = 0, 1, 2
 
 OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_STATE = range(7)
@@ -34,7 +35,7 @@ class Config(ctypes.Structure):
         ("median_mode", ctypes.c_int32), ("kernel", ctypes.c_int32), ("beta", ctypes.c_double),
         ("u_lid", ctypes.c_double), ("rho_wall", ctypes.c_double), ("delta_median", ctypes.c_double),
         ("delta_ehrenfest", ctypes.c_double), ("k_max", ctypes.c_int64),
-        ("stats_history", ctypes.c_int32), ("reserved", ctypes.c_int32), ("rho_ref", ctypes.c_double),
+        ("stats_history", ctypes.c_int32), ("equilibrium", ctypes.c_int32), ("rho_ref", ctypes.c_double),
     ]
 
 

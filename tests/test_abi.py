@@ -37,13 +37,16 @@ def test_config_validation_without_gpu(lib):
     bad = [dict(nx=1), dict(lattice=3), dict(beta=1.5), dict(limiters=8), dict(k_max=-1),
            dict(lattice=lbm.D1Q3, ny=2), dict(lattice=lbm.D1Q3, ny=1, boundary=lbm.BC_CHANNEL),
            dict(precision=7), dict(delta_median=-1.0), dict(median_mode=5),
-           dict(kernel=lbm.KERNEL_FUSED, precision=lbm.FP64)]
+           dict(kernel=lbm.KERNEL_FUSED, precision=lbm.FP64),
+           dict(equilibrium=2), dict(equilibrium=lbm.EQ_ENTROPIC),
+           dict(equilibrium=lbm.EQ_ENTROPIC, precision=lbm.BF16)]
     for b in bad:
         cfg = dict(base)
         cfg.update(b)
         with pytest.raises(lbm.LBMError) as e:
             lbm.footprint_bytes(**cfg)
         assert e.value.status == lbm.ERR_INVALID_ARG
+    assert lbm.footprint_bytes(**dict(base, precision=lbm.FP64, equilibrium=lbm.EQ_ENTROPIC)) > 0
     # FP64 doubles the population storage
     f32 = lbm.footprint_bytes(**base)
     f64 = lbm.footprint_bytes(**dict(base, precision=lbm.FP64))

@@ -1,0 +1,206 @@
+"""Parity of the entropic-quasiequilibrium path (LBM_EQ_ENTROPIC, FP64 storage)
+with the FP64 oracle, through the C ABI.
+
+Both sides evaluate f* (Eq. entropiceq1d / Eq. maxwellian) with the same
+correctly rounded operations (sqrt, division, products) in the same order, so
+f* and the collision f' agree bit for bit.  The exact nonequilibrium entropy of
+Eq. DelS takes one logarithm per population, and the device and host logarithms
+are each within an ulp or so of the true value but not bitwise equal.  The
+tolerance on dS at a site is therefore derived from its terms:
+
+    |dS_gpu - dS_oracle| <= 16 eps * (sum_k |f'_k ln(f'_k / f*_k)| + dS) + 2 eps * sum_k f'_k,
+
+eps = 2^-52.  The last term is the oracle's rounding of the ratio f'_k / f*_k
+before its logarithm (an absolute error of up to eps in each logarithm); the
+device evaluates ln(f'_k / f*_k) near 1 without forming the ratio.
+
+and populations after the limiters (whose homothety factors sqrt(dS_t / dS)
+inherit that error) are compared to 1e-12 absolute, far below the 1e-6 and
+larger shifts a wrong term, sign or index produces.  Each step is compared from
+the same stored state (the GPU lattice is reset to the oracle's state before
+every step), so the comparison is one step deep; a separate run compares 300
+unsynchronised cavity steps.  Counts and Ehrenfests' sets must be identical.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_0704_0043_gb300 import inputs, lbm
+
+pytestmark = pytest.mark.gpu
+
+ALL = lbm.LIM_POSITIVITY | lbm.LIM_EHRENFEST | lbm.LIM_MEDIAN
+W9 = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+W3 = np.array([2 / 3, 1 / 6, 1 / 6])
+EPS = 2.0 ** -52
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_0704_0043_gb300 import build
+    build.build()
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+
+
+def pair(**cfg):
+    cfg = dict(cfg, precision=lbm.FP64, equilibrium=lbm.EQ_ENTROPIC)
+    g = lbm.Lattice(**cfg)
+    c = g.config
+    oc = oracle.Config(lattice=c.lattice, nx=c.nx, ny=c.ny, boundary=c.boundary, beta=c.beta,
+                       u_lid=c.u_lid, rho_wall=c.rho_wall, limiters=c.limiters,
+                       delta_median=c.delta_median, delta_ehrenfest=c.delta_ehrenfest, k_max=c.k_max,
+                       median_mode=c.median_mode, equilibrium=oracle.EQ_ENTROPIC)
+    return g, oc
+
+
+def rand_state(q, ny, nx, seed, eps=0.15, neg_frac=0.0, heavy=0):
+    w = W9 if q == 9 else W3
+    f = inputs.random_populations(seed, q, ny, nx, w, eps, neg_frac=neg_frac)
+    rng = np.random.default_rng(seed + 99)
+    for _ in range(heavy):
+        j, i = rng.integers(0, ny), rng.integers(0, nx)
+        if q == 9:
+            f[rng.integers(1, 9), j, i] *= 4.0
+        else:
+            f[0, j, i] *= 0.3
+    return f
+
+
+def ds_bound(oc, f):
+    """Per-site tolerance on dS(f') of the next collision (see the module docstring)."""
+    free = oracle.step(dataclasses.replace(oc, limiters=0), f)
+    q = oc.q
+    fp = free.f.reshape(q, -1)
+    ds = free.dS.reshape(-1)
+    out = np.zeros(oc.sites)
+    for s in range(oc.sites):
+        if not np.isfinite(ds[s]):
+            continue
+        rho, ux, uy = oracle.site_moments(oc.lattice, fp[:, s])
+        fs = oracle.feq_entropic(oc.lattice, rho, ux, uy)
+        x = fp[:, s]
+        pos = x > 0
+        t = np.abs(x[pos] * np.log(x[pos] / fs[pos])).sum()
+        out[s] = 16 * EPS * (t + abs(ds[s])) + 2 * EPS * x[pos].sum() + 1e-300
+    return out.reshape(oc.ny, oc.nx), free.dS
+
+
+def assert_ds_close(got, want, bound):
+    inf = ~np.isfinite(want)
+    np.testing.assert_array_equal(~np.isfinite(got), inf)
+    np.testing.assert_array_equal(got[inf], want[inf])
+    err = np.abs(got[~inf] - want[~inf])
+    assert (err <= bound[~inf]).all(), (err.max(), (err / bound[~inf]).max())
+
+
+def stats_close(a, b):
+    for key in ("mass", "sum_dS", "dS_lbgk", "dS_lim"):
+        assert abs(a[key] - b[key]) <= 1e-10 * abs(b[key]) + 1e-13, (key, a[key], b[key])
+    for key in ("n_pos", "n_med", "n_ehr", "n_cand", "n_bad"):
+        assert a[key] == b[key], (key, a[key], b[key])
+
+
+CASES = [
+    dict(lattice=lbm.D2Q9, nx=67, ny=41, boundary=lbm.BC_WALLS, beta=0.97, u_lid=0.1,
+         limiters=ALL, delta_median=1e-4, delta_ehrenfest=2e-3, k_max=7),
+    dict(lattice=lbm.D2Q9, nx=45, ny=20, boundary=lbm.BC_CHANNEL, beta=0.9, u_lid=0.05,
+         rho_wall=1.3, limiters=ALL, delta_median=0.0, delta_ehrenfest=1e-3, k_max=5),
+    dict(lattice=lbm.D2Q9, nx=33, ny=13, boundary=lbm.BC_PERIODIC, beta=0.99, limiters=ALL,
+         delta_median=1e-5, delta_ehrenfest=1e-3, k_max=9, median_mode=lbm.MEDIAN_GATE),
+    dict(lattice=lbm.D2Q9, nx=4, ny=4, boundary=lbm.BC_WALLS, beta=0.95, u_lid=0.1, limiters=ALL,
+         delta_median=0.0, delta_ehrenfest=1e-4, k_max=2),
+    dict(lattice=lbm.D1Q3, nx=600, ny=1, boundary=lbm.BC_WALLS, beta=0.999, limiters=ALL,
+         delta_median=1e-6, delta_ehrenfest=1e-3, k_max=4),
+    dict(lattice=lbm.D1Q3, nx=517, ny=1, boundary=lbm.BC_PERIODIC, beta=0.8, limiters=ALL,
+         delta_median=0.0, delta_ehrenfest=5e-4, k_max=3),
+]
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_entropic_steps_match_oracle(case):
+    g, oc = pair(**CASES[case])
+    cur = rand_state(g.q, g.ny, g.nx, 20 + case, neg_frac=0.02, heavy=max(1, g.sites // 200))
+    acted = {"n_pos": 0, "n_med": 0, "n_ehr": 0}
+    saw_inf = False
+    for step in range(8):
+        g.set_populations(cur)
+        bound, want_ds = ds_bound(oc, cur)
+        assert_ds_close(g.delta_s(), want_ds, bound)
+        saw_inf |= bool(np.isinf(want_ds).any())
+        g.step(1)
+        r = oracle.step(oc, cur)
+        got = g.get_populations()
+        np.testing.assert_allclose(got, r.f, rtol=0, atol=1e-12, err_msg=f"step {step}")
+        stats_close(g.stats(), r.stats)
+        np.testing.assert_array_equal(g.limited_sites(), np.sort(r.selected))
+        for k in acted:
+            acted[k] += r.stats[k]
+        cur = r.f
+    assert acted["n_med"] > 0 and acted["n_ehr"] > 0, acted
+    if CASES[case]["beta"] > 0.9:
+        # sites with a negative post-collision population (dS = +inf) were exercised
+        assert acted["n_pos"] > 0 and saw_inf, acted
+
+
+def test_entropic_init_is_bitwise_and_rest_is_a_fixed_point():
+    g, oc = pair(lattice=lbm.D2Q9, nx=70, ny=38, boundary=lbm.BC_PERIODIC, beta=0.96)
+    rho, ux, uy = inputs.random_moments(3, 70, 38, umax=0.3)
+    g.init(rho, ux, uy)
+    np.testing.assert_array_equal(g.get_populations(), oracle.init(oc, rho, ux, uy))
+    g1, oc1 = pair(lattice=lbm.D1Q3, nx=301, ny=1, boundary=lbm.BC_PERIODIC, beta=0.9)
+    r1, u1, _ = inputs.random_moments(4, 301, 1, umax=0.5)
+    g1.init(r1, u1)
+    np.testing.assert_array_equal(g1.get_populations(), oracle.init(oc1, r1, u1))
+    # a uniform entropic equilibrium stays put
+    n = 70 * 38
+    g.init(np.full(n, 1.2), np.full(n, 0.05), np.full(n, -0.1))
+    f0 = g.get_populations()
+    g.step(3)
+    np.testing.assert_allclose(g.get_populations(), f0, rtol=4e-15, atol=0)
+
+
+def test_entropic_limit_pass_matches_oracle():
+    g, oc = pair(lattice=lbm.D2Q9, nx=50, ny=29, boundary=lbm.BC_WALLS, beta=0.96, u_lid=0.1,
+                 limiters=ALL, delta_median=0.0, delta_ehrenfest=1e-3, k_max=11)
+    f = rand_state(9, 29, 50, 4, eps=0.25, neg_frac=0.03)
+    g.set_populations(f)
+    g.limit(ALL)
+    r = oracle.limit(oc, f, ALL)
+    np.testing.assert_allclose(g.get_populations(), r.f, rtol=0, atol=1e-12)
+    stats_close(g.stats(), r.stats)
+    np.testing.assert_array_equal(g.limited_sites(), np.sort(r.selected))
+
+
+def test_entropic_cavity_run_tracks_oracle():
+    # 300 unsynchronised steps of a 64^2 lid-driven cavity, median filter on
+    cfg = dict(lattice=lbm.D2Q9, nx=64, ny=64, boundary=lbm.BC_WALLS, beta=1.0 / (6 * 0.0064 + 1),
+               u_lid=0.1, limiters=lbm.LIM_MEDIAN, delta_median=1e-3)
+    g, oc = pair(**cfg)
+    n = 64 * 64
+    g.init(np.ones(n), np.zeros(n), np.zeros(n))
+    f = oracle.init(oc, np.ones(n), np.zeros(n), np.zeros(n))
+    g.step(300)
+    f, st, rc = oracle.run(oc, f, 300)
+    assert rc == 0
+    rho, ux, uy = g.moments()
+    orho, oux, ouy = oracle.moments(oc, f)
+    np.testing.assert_allclose(rho, orho, rtol=0, atol=1e-11)
+    np.testing.assert_allclose(ux, oux, rtol=0, atol=1e-11)
+    np.testing.assert_allclose(uy, ouy, rtol=0, atol=1e-11)
+    stats_close(g.stats(), st)
+
+
+def test_entropic_site_without_equilibrium_reports_status():
+    g, oc = pair(lattice=lbm.D2Q9, nx=16, ny=12, boundary=lbm.BC_PERIODIC, beta=0.9)
+    f = oracle.init(oc, np.ones(192), np.zeros(192), np.zeros(192))
+    f[3, 5, 7] = -0.6  # arrives at (6, 5) with |u_x| > 1: no entropic f*
+    g.set_populations(f)
+    g.step(1)
+    with pytest.raises(lbm.LBMError) as e:
+        g.synchronize()
+    assert e.value.status == lbm.ERR_NONFINITE
+    r = oracle.step(oc, f)
+    assert g.stats(check=False)["n_bad"] == r.stats["n_bad"] >= 1
