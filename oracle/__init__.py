@@ -27,6 +27,7 @@ _LIB_PATH = os.path.join(_BUILD, "liblbm_oracle.so")
 D1Q3, D2Q9 = 1, 2
 BC_WALLS, BC_PERIODIC, BC_CHANNEL = 0, 1, 2
 LIM_POSITIVITY, LIM_EHRENFEST, LIM_MEDIAN = 1, 2, 4
+LIM_SMOOTH, LIM_THRESHOLD = 8, 16
 MEDIAN_THRESHOLD, MEDIAN_GATE = 0, 1
 EQ_POLYNOMIAL, EQ_ENTROPIC = 0, 1
 
@@ -53,6 +54,8 @@ class _Config(ctypes.Structure):
         ("rho_wall", ctypes.c_double), ("limiters", ctypes.c_uint),
         ("delta_median", ctypes.c_double), ("delta_ehrenfest", ctypes.c_double),
         ("k_max", ctypes.c_longlong), ("median_mode", ctypes.c_int), ("equilibrium", ctypes.c_int),
+        ("smooth_delta", ctypes.c_double), ("smooth_k", ctypes.c_double),
+        ("threshold_c", ctypes.c_double), ("threshold_delta", ctypes.c_double),
     ]
 
 
@@ -122,6 +125,10 @@ class Config:
     k_max: int = 0
     median_mode: int = MEDIAN_THRESHOLD
     equilibrium: int = EQ_POLYNOMIAL
+    smooth_delta: float = 1e-2
+    smooth_k: float = 0.5
+    threshold_c: float = 10.0
+    threshold_delta: float = 0.0
 
     @property
     def q(self) -> int:
@@ -137,7 +144,8 @@ class Config:
     def _c(self) -> _Config:
         return _Config(self.lattice, self.nx, self.ny, self.boundary, self.beta, self.u_lid,
                        self.rho_wall, self.limiters, self.delta_median, self.delta_ehrenfest,
-                       self.k_max, self.median_mode, self.equilibrium)
+                       self.k_max, self.median_mode, self.equilibrium, self.smooth_delta,
+                       self.smooth_k, self.threshold_c, self.threshold_delta)
 
 
 def _f64(a, shape=None):

@@ -20,7 +20,9 @@
  *   6. phi_pos: positivity rule, closest nonnegative point of the line
  *      through f' and f*                                                Sec. 3.1
  *   7. phi_med: median of dS over the stencil, homothety sqrt(dS_t/dS)  Sec. 3.5, Eq. entrHom
- *   8. phi = min(phi_pos, phi_med);  f_out = f* + phi (f' - f*)         Eq. LimGenF
+ *      phi_smooth = 1 / (1 + alpha dS^k), alpha = delta / E(dS)^k        Eq. smooth1 (Sec. 4.3.2)
+ *      phi_thr = sqrt(dS_t / dS), dS_t = max(c E(dS), delta)            Sec. 3.4, Eq. entrHom
+ *   8. phi = min of the limiters' phi;  f_out = f* + phi (f' - f*)      Eq. LimGenF
  *   9. Ehrenfests' step f -> f* at the (at most k) sites of largest
  *      dS > delta, ties broken by lower site index                      Sec. 3.2, Sec. 4.3.2
  *  10. sums: mass, sum dS, LBGK and limiter entropy production          Sec. 3.4, Sec. 4.3.1
@@ -374,9 +376,33 @@ static void limit_core(const orc_config *cfg, unsigned limiters, const double *f
     long long n = (long long)cfg->nx * cfg->ny;
     double *phi = (double *)malloc(sizeof(double) * (size_t)n);
     double v[9];
+    /* E(dS): mean of dS(f') over the sites with a finite value, in site order */
+    double e_sum = 0.0;
+    long long e_cnt = 0;
+    for (long long s = 0; s < n; ++s)
+        if (!bad[s] && isfinite(dS[s])) {
+            e_sum += dS[s];
+            e_cnt++;
+        }
+    double E = e_cnt > 0 ? e_sum / (double)e_cnt : 0.0;
     for (long long s = 0; s < n; ++s) {
-        double phi_pos = 1.0, phi_med = 1.0;
+        double phi_pos = 1.0, phi_med = 1.0, phi_ens = 1.0;
         if (!bad[s]) {
+            if ((limiters & ORC_LIM_SMOOTH) && E > 0.0 && dS[s] > 0.0) {
+                /* Eq. smooth1 with the ensemble-dependent alpha of Sec. 4.3.2 */
+                double alpha = cfg->smooth_delta / pow(E, cfg->smooth_k);
+                double p_s = 1.0 / (1.0 + alpha * pow(dS[s], cfg->smooth_k));
+                if (p_s < phi_ens) phi_ens = p_s;
+            }
+            if (limiters & ORC_LIM_THRESHOLD) {
+                /* Sec. 3.4: dS_t = max(dS_0, delta), homothety where dS > dS_t */
+                double t = cfg->threshold_c * E;
+                if (t < cfg->threshold_delta) t = cfg->threshold_delta;
+                if (dS[s] > t) {
+                    double p_t = sqrt(t / dS[s]);
+                    if (p_t < phi_ens) phi_ens = p_t;
+                }
+            }
             if (limiters & ORC_LIM_POSITIVITY) {
                 /* Sec. 3.1: move along {f* + lambda (f' - f*)} to the positivity boundary. */
                 for (int k = 0; k < q; ++k) {
@@ -403,6 +429,7 @@ static void limit_core(const orc_config *cfg, unsigned limiters, const double *f
             }
         }
         double p = phi_pos < phi_med ? phi_pos : phi_med;
+        if (phi_ens < p) p = phi_ens;
         phi[s] = p;
         if (phi_pos < 1.0) st->n_pos++;
         if (phi_med < 1.0) st->n_med++;

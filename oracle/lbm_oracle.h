@@ -45,6 +45,8 @@ extern "C" {
 #define ORC_LIM_POSITIVITY 1u
 #define ORC_LIM_EHRENFEST 2u
 #define ORC_LIM_MEDIAN 4u
+#define ORC_LIM_SMOOTH 8u     /* ensemble-dependent smooth limiter, Eq. smooth1 with alpha = delta / E(dS)^k */
+#define ORC_LIM_THRESHOLD 16u /* threshold filter, dS_t = max(c E(dS), delta) (Sec. 3.4, Sec. 4.3.2) */
 
 #define ORC_MEDIAN_THRESHOLD 0 /* dS_t = max(dS_med, delta); phi = sqrt(dS_t/dS) where dS > dS_t */
 #define ORC_MEDIAN_GATE 1      /* phi = sqrt(dS_med/dS) where dS > delta and dS_med < dS */
@@ -65,9 +67,21 @@ typedef struct {
     long long k_max;        /* at most this many Ehrenfests' sites per step */
     int median_mode;        /* ORC_MEDIAN_* */
     int equilibrium;        /* ORC_EQ_* */
+    double smooth_delta;    /* ORC_LIM_SMOOTH: alpha = smooth_delta / E(dS)^smooth_k */
+    double smooth_k;        /* ORC_LIM_SMOOTH: exponent k (> 0) */
+    double threshold_c;     /* ORC_LIM_THRESHOLD: dS_0 = threshold_c * E(dS) */
+    double threshold_delta; /* ORC_LIM_THRESHOLD: dS_t = max(dS_0, threshold_delta) */
 } orc_config;
 
 /*
+ * The ensemble-dependent limiters use E(dS), the mean of dS(f') over the
+ * sites that are not flagged and have a finite dS, of the state being limited
+ * (before any limiter).  Smooth limiter (Eq. smooth1): phi = 1 / (1 + alpha
+ * dS^k), alpha = smooth_delta / E^k, phi = 1 where E <= 0 or dS = 0.
+ * Threshold filter (Sec. 3.4 with dS_0 = c E as in Sec. 4.3.2): phi =
+ * sqrt(dS_t / dS) where dS > dS_t.  All limiters compose as the minimum of
+ * their phi, before Ehrenfests' step.
+ *
  * With entropic quasiequilibria (ORC_EQ_ENTROPIC) dS is the exact relative
  * entropy, which is +inf for a state with a negative population (outside the
  * domain of S; such a site is not flagged bad).  The entropy productions are
