@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--develop", type=int, default=500,
                     help="untimed steps before warm-up so the flow has left the rest state")
     ap.add_argument("--kernel", default="auto", choices=["auto", "tiled", "fused"])
+    ap.add_argument("--limiters", default="median+ehrenfest",
+                    choices=["median+ehrenfest", "smooth+ehrenfest", "threshold+ehrenfest"],
+                    help="smooth / threshold: the ensemble-dependent limiters (tiled kernel, E(dS) reduction first)")
     ap.add_argument("--equilibrium", default="polynomial", choices=["polynomial", "entropic"],
                     help="entropic: Eq. maxwellian f* with the exact dS of Eq. DelS (needs --precision fp64)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16", "fp64"],
@@ -406,6 +409,10 @@ def main():
     lbm.lib()
 
     w = workload(args.side)
+    if args.limiters != "median+ehrenfest":
+        # Eq. smooth1 with k = 1/2, delta = 0.01, or the threshold filter with dS_t = 10 E(dS)
+        w.limiters = (lbm.LIM_SMOOTH if args.limiters.startswith("smooth") else lbm.LIM_THRESHOLD) | lbm.LIM_EHRENFEST
+        w.name = w.name + "_" + args.limiters.split("+")[0]
     entropic = args.equilibrium == "entropic"
     if entropic:
         if args.precision != "fp64":
@@ -446,6 +453,11 @@ def main():
 
     # roofline of the step kernel (the dominant launch): algorithmic bytes / event time
     bps = BYTES_PER_SITE[("d2q9", args.precision)]
+    ensemble = args.limiters != "median+ehrenfest"
+    if ensemble:
+        # the pass first reads every population once more for E(dS) (k_ens_partial);
+        # the library's events bracket that reduction and the step kernel together
+        bps += bps // 2
     kern_s = step_ms / 1e3 / max(timed, 1)
     achieved = bps * w.sites / kern_s / 1e9
     peak, peak_kind = peaks()
@@ -456,6 +468,9 @@ def main():
             "kernel": kname, "kernel_ms": kern_s * 1e3, "tail_kernel_ms": tail_ms / max(timed, 1),
             "timed_launches": timed, "timed_every": TIMING_EVERY,
             "bytes_per_site": bps}
+    if ensemble:
+        roof["kernel"] = "k_ens_partial + k_ens_mean + k_tiled"
+        roof["traffic"] = traffic_from_profile("tiled_fp32_ensemble", w.sites)
 
     if entropic:
         # The entropic step is bound by FP64 arithmetic (a logarithm per population
@@ -489,7 +504,7 @@ def main():
            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
            "data": "synthetic",
            "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "reynolds": 7500,
-                      "u_lid": w.u_lid, "beta": w.beta, "limiters": "median+ehrenfest",
+                      "u_lid": w.u_lid, "beta": w.beta, "limiters": args.limiters,
                       "delta": 1e-3, "k_max": w.k_max, "storage": args.precision, "sums": "fp64",
                       "equilibrium": args.equilibrium,
                       "kernel": kname, "develop_steps": args.develop,

@@ -42,7 +42,7 @@
 extern "C" {
 #endif
 
-#define LBM_ABI_VERSION 1
+#define LBM_ABI_VERSION 2
 
 typedef enum {
     LBM_OK = 0,
@@ -70,8 +70,17 @@ enum {
     LBM_BC_CHANNEL = 2   /* D2Q9: periodic in x, still bottom wall, lid on top */
 };
 
-/* Limiters (bit set). */
-enum { LBM_LIM_POSITIVITY = 1, LBM_LIM_EHRENFEST = 2, LBM_LIM_MEDIAN = 4 };
+/* Limiters (bit set).  LBM_LIM_SMOOTH and LBM_LIM_THRESHOLD are ensemble-dependent: they
+ * use E(dS), the mean of dS(f') over the sites with a finite value (not flagged), of the
+ * pass being limited, so a pass with either bit first runs a reduction over the lattice.
+ *   LBM_LIM_SMOOTH: phi = 1 / (1 + alpha dS^k), alpha = smooth_delta / E^k (Eq. smooth1,
+ *     with the ensemble-dependent alpha of Sec. 4.3.2); phi = 1 where E <= 0 or dS = 0.
+ *   LBM_LIM_THRESHOLD: dS_t = max(threshold_c E, threshold_delta); phi = sqrt(dS_t / dS)
+ *     where dS > dS_t (Sec. 3.4, Eq. entrHom, with dS_0 = c E as in Sec. 4.3.2).
+ * Every limiter's phi is combined as the minimum, before Ehrenfests' step.  The two
+ * ensemble limiters run on the tiled kernel (not in batches, not in lbm_step_noalloc). */
+enum { LBM_LIM_POSITIVITY = 1, LBM_LIM_EHRENFEST = 2, LBM_LIM_MEDIAN = 4, LBM_LIM_SMOOTH = 8,
+       LBM_LIM_THRESHOLD = 16 };
 
 /* Median-filter acceptance rule (Sec. 3.5 with the tolerance of Sec. 4.3.2). */
 enum {
@@ -118,6 +127,10 @@ typedef struct lbm_config {
     int32_t stats_history;   /* per-step stats kept on the device (ring length, >= 1) */
     int32_t equilibrium;     /* LBM_EQ_* (LBM_EQ_ENTROPIC needs LBM_FP64) */
     double rho_ref;          /* reference density of the FP32 deviation storage (> 0, default 1) */
+    double smooth_delta;     /* LBM_LIM_SMOOTH: alpha = smooth_delta / E(dS)^smooth_k (>= 0, default 0.01) */
+    double smooth_k;         /* LBM_LIM_SMOOTH: exponent k (> 0, default 0.5) */
+    double threshold_c;      /* LBM_LIM_THRESHOLD: dS_0 = threshold_c * E(dS) (>= 0, default 10) */
+    double threshold_delta;  /* LBM_LIM_THRESHOLD: dS_t = max(dS_0, threshold_delta) (>= 0, default 0) */
 } lbm_config;
 
 typedef struct lbm_step_stats {

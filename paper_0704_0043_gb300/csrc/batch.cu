@@ -327,6 +327,8 @@ lbm_status lbm_batch_add(lbm_batch *b, const lbm_config *cfg, int32_t *slot)
 {
     if (!b || !cfg || !slot) return bfail(b, LBM_ERR_INVALID_ARG, "NULL argument");
     if (cfg->precision != LBM_FP32) return bfail(b, LBM_ERR_INVALID_ARG, "batched lattices use LBM_FP32");
+    if (cfg->limiters & (LBM_LIM_SMOOTH | LBM_LIM_THRESHOLD))
+        return bfail(b, LBM_ERR_INVALID_ARG, "the ensemble-dependent limiters are not available in batches");
     lbm_ctx *c = nullptr;
     lbm_status s = lbm_create(cfg, (void *)b->run, &c);
     if (s != LBM_OK) return bfail(b, s, lbm_last_error(nullptr));

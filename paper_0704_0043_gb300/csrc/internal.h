@@ -87,6 +87,9 @@ struct StepParams {
     unsigned *status;
     int *work;                 // fused kernel: counter of work items handed out (nullptr: one item per warp)
     double *ds_out;            // optional FP64 dS(f') field (nx * ny) or nullptr
+    // ensemble-dependent limiters (LBM_LIM_SMOOTH / LBM_LIM_THRESHOLD)
+    double smooth_delta, smooth_k, threshold_c, threshold_delta;
+    const double *ens;         // {E(dS), smooth_delta / E^smooth_k} of this pass (the ensemble reduction)
 };
 
 struct FinalParams {
@@ -167,6 +170,11 @@ template <typename T>
 cudaError_t launch_set(int q, const StepParams &p, const double *in, T *f, cudaStream_t s);
 template <typename T>
 cudaError_t launch_delta_s(int q, const StepParams &p, const T *f, double *out, cudaStream_t s);
+// E(dS) of the pass p is about to run and the smooth limiter's alpha, into
+// ens[2 kEnsBlocks], ens[2 kEnsBlocks + 1] (ens[0 .. 2 kEnsBlocks) is scratch).
+constexpr int kEnsBlocks = 608;
+template <typename T>
+cudaError_t launch_ens_mean(int q, const StepParams &p, const T *src, double *ens, cudaStream_t s);
 
 // Sets the calling thread's error message (read by lbm_last_error(NULL)); returns s.
 int set_thread_error_impl(int s, const char *msg);
@@ -206,6 +214,7 @@ struct lbm_ctx {
     int cur = 0;
     lbm::Cand *cand = nullptr;
     int cand_cap = 0;
+    double *ens = nullptr;  // [kEnsBlocks][2] partial sums and counts of dS, then E(dS)
     int *counts = nullptr;  // [0] candidate count, [1] chosen count, [2] fused work items handed out, [3] unused
     int *sel = nullptr;
     int sel_cap = 0;

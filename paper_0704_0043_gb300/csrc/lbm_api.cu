@@ -63,6 +63,7 @@ cudaError_t with_storage(int precision, F &&fn)
 bool fused_applies(const lbm_config &c)
 {
     return c.lattice == LBM_D2Q9 && c.precision != LBM_FP64 && c.boundary == LBM_BC_WALLS &&
+           (c.limiters & (LBM_LIM_SMOOTH | LBM_LIM_THRESHOLD)) == 0 &&
            c.kernel != LBM_KERNEL_TILED && fused_d2q9_fits((long long)c.ny * row_pitch(c.nx));
 }
 
@@ -90,7 +91,12 @@ std::string validate(const lbm_config *c)
         if (c->boundary == LBM_BC_WALLS && (c->nx < 2 || c->ny < 2)) return "D2Q9 cavity needs nx, ny >= 2";
         if (c->boundary == LBM_BC_CHANNEL && c->ny < 2) return "D2Q9 channel needs ny >= 2";
     }
-    if (c->limiters & ~7u) return "unknown limiter bits";
+    if (c->limiters & ~31u) return "unknown limiter bits";
+    if (!(c->smooth_delta >= 0.0) || !std::isfinite(c->smooth_delta)) return "smooth_delta must be finite and >= 0";
+    if (!(c->smooth_k > 0.0) || !std::isfinite(c->smooth_k)) return "smooth_k must be finite and > 0";
+    if (!(c->threshold_c >= 0.0) || !std::isfinite(c->threshold_c)) return "threshold_c must be finite and >= 0";
+    if (!(c->threshold_delta >= 0.0) || !std::isfinite(c->threshold_delta))
+        return "threshold_delta must be finite and >= 0";
     if (!(c->beta >= 0.0 && c->beta <= 1.0)) return "beta must lie in [0, 1]";
     if (!std::isfinite(c->u_lid) || !std::isfinite(c->rho_wall)) return "u_lid and rho_wall must be finite";
     if (!(c->delta_median >= 0.0) || !(c->delta_ehrenfest >= 0.0)) return "delta_median and delta_ehrenfest must be >= 0";
@@ -107,6 +113,8 @@ std::string validate(const lbm_config *c)
     return "";
 }
 
+size_t ens_bytes() { return (2 * (size_t)kEnsBlocks + 2) * sizeof(double); }
+
 struct Sizes {
     int q, pitch;
     long long plane;
@@ -114,7 +122,7 @@ struct Sizes {
     int cand_cap, sel_cap, rows, ring_len;
     int64_t total() const
     {
-        return (int64_t)(2 * field + cand + sel + partials + ring + 64 * sizeof(long long) + 4096);
+        return (int64_t)(2 * field + cand + sel + partials + ring + ens_bytes() + 64 * sizeof(long long) + 4096);
     }
 };
 
@@ -215,6 +223,11 @@ StepParams step_params(lbm_ctx *c, int collide, unsigned limiters)
     p.status = c->status;
     p.work = c->counts + 2;
     p.ds_out = nullptr;
+    p.smooth_delta = g.smooth_delta;
+    p.smooth_k = g.smooth_k;
+    p.threshold_c = g.threshold_c;
+    p.threshold_delta = g.threshold_delta;
+    p.ens = c->ens + 2 * kEnsBlocks;
     return p;
 }
 
@@ -295,6 +308,15 @@ lbm_status run_pass(lbm_ctx *c, int collide, unsigned limiters)
     cudaError_t e;
     void *src = c->buf[c->cur], *dst = c->buf[c->cur ^ 1];
     const bool fused = collide && fused_applies(c->cfg);
+    if (limiters & (LBM_LIM_SMOOTH | LBM_LIM_THRESHOLD)) {
+        // E(dS) of this pass, before any site is limited
+        e = with_storage(c->cfg.precision, [&](auto tag) -> cudaError_t {
+            using S = STORAGE_T;
+            return launch_ens_mean<S>(c->q, p, (const S *)src, c->ens, c->stream);
+        });
+        if (e != cudaSuccess) return cuda_fail(c, e, "ensemble reduction launch");
+        c->launches += 2;
+    }
     e = with_storage(c->cfg.precision, [&](auto tag) -> cudaError_t {
         using S = STORAGE_T;
         if constexpr (!std::is_same<S, double>::value)
@@ -345,7 +367,7 @@ void free_all(lbm_ctx *c)
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     c->events.clear();
     void *ptrs[] = {c->buf[0], c->buf[1], c->cand, c->counts, c->sel, c->partials,
-                    c->status, c->ring, c->counters, c->stage};
+                    c->status, c->ring, c->counters, c->stage, c->ens};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -405,6 +427,10 @@ void lbm_config_default(lbm_config *c)
     c->stats_history = 1;
     c->equilibrium = LBM_EQ_POLYNOMIAL;
     c->rho_ref = 1.0;
+    c->smooth_delta = 1e-2;
+    c->smooth_k = 0.5;
+    c->threshold_c = 10.0;
+    c->threshold_delta = 0.0;
 }
 
 int64_t lbm_footprint_bytes(const lbm_config *cfg)
@@ -453,6 +479,7 @@ lbm_status lbm_create(const lbm_config *cfg, void *cuda_stream, lbm_ctx **out)
     alloc((void **)&c->status, sizeof(unsigned));
     alloc((void **)&c->ring, z.ring);
     alloc((void **)&c->counters, 2 * sizeof(long long));
+    alloc((void **)&c->ens, ens_bytes());
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -516,7 +543,7 @@ lbm_status lbm_step(lbm_ctx *c, int64_t nsteps)
 lbm_status lbm_limit(lbm_ctx *c, uint32_t limiters)
 {
     if (!c) return fail(nullptr, LBM_ERR_INVALID_ARG, "ctx is NULL");
-    if (limiters & ~7u) return fail(c, LBM_ERR_INVALID_ARG, "unknown limiter bits");
+    if (limiters & ~31u) return fail(c, LBM_ERR_INVALID_ARG, "unknown limiter bits");
     if (!c->ready) return fail(c, LBM_ERR_STATE, "lbm_limit before lbm_init / lbm_set_populations");
     if ((limiters & LBM_LIM_EHRENFEST) && c->cand_cap < c->cfg.nx * c->cfg.ny)
         return fail(c, LBM_ERR_INVALID_ARG, "Ehrenfests' limiter needs LBM_LIM_EHRENFEST in the config at create");

@@ -207,7 +207,32 @@ __global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const S *__r
                     phi_med = phi_median<T>(ds, med, T(p.delta_m), p.median_mode);
             }
         }
-        const T phi = phi_pos < phi_med ? phi_pos : phi_med;
+        T phi = phi_pos < phi_med ? phi_pos : phi_med;
+        if (!bad && (p.limiters & 24u)) {
+            // ensemble-dependent limiters: ens = {E(dS), alpha = delta / E^k} of this pass
+            const double E = p.ens[0];
+            T pe = T(1);
+            if ((p.limiters & 8u) && E > 0.0 && ds > T(0)) {
+                // Eq. smooth1 (Sec. 4.3.2); k = 1/2 by a square root
+                if constexpr (std::is_same<T, double>::value) {
+                    const double pk = p.smooth_k == 0.5 ? sqrt(ds) : pow(ds, p.smooth_k);
+                    pe = 1.0 / (1.0 + p.ens[1] * pk);
+                } else {
+                    const float pk = p.smooth_k == 0.5 ? sqrtf(ds) : powf(ds, (float)p.smooth_k);
+                    pe = 1.0f / (1.0f + (float)p.ens[1] * pk);
+                }
+            }
+            if (p.limiters & 16u) {
+                // threshold filter: dS_t = max(c E, delta), homothety where dS > dS_t (Sec. 3.4)
+                double t = p.threshold_c * E;
+                if (t < p.threshold_delta) t = p.threshold_delta;
+                if ((double)ds > t) {
+                    const T pt = T(sqrt(t / (double)ds));
+                    if (pt < pe) pe = pt;
+                }
+            }
+            if (pe < phi) phi = pe;
+        }
         if (phi < T(1)) {
             if constexpr (std::is_same<T, double>::value) {
                 double fo[Q];
@@ -300,6 +325,86 @@ __global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const S *__r
         double v = 0.0;
         for (int w = 0; w < (BX * BY) / 32; ++w) v += sred[w][lin];
         p.partials[((long long)by * gx + bx) * P_NSTAT + lin] = v;
+    }
+}
+
+// E(dS) of a pass (Sec. 3.3, Sec. 4.3.2): the ensemble-dependent limiters need
+// the mean of dS(f') over the lattice before any site is limited.  Block b
+// sums dS(f') of sites b, b + gridDim.x * 256, ... with the same evaluation as
+// k_tiled (so the same values), over the sites that are not flagged and have a
+// finite dS; k_ens_mean adds the block partials in block order.
+template <int Q, typename S>
+__global__ void __launch_bounds__(256) k_ens_partial(StepParams p, const S *__restrict__ src,
+                                                     double *__restrict__ part)
+{
+    using T = compute_t<S>;
+    __shared__ double sw[8][2];
+    const long long n = (long long)p.nx * p.ny;
+    double sum = 0.0, cnt = 0.0;
+    for (long long s = blockIdx.x * 256LL + threadIdx.x; s < n; s += (long long)gridDim.x * 256) {
+        const int x = (int)(s % p.nx), y = (int)(s / p.nx);
+        T fin[Q], fs[Q], fp[Q], fa[Q];
+        float nq[Q];
+        T ds, dsin, rho;
+        bool bad;
+        if (p.collide) {
+            pull<Q, S, T>(p, src, x, y, fin);
+        } else {
+#pragma unroll
+            for (int k = 0; k < Q; ++k) fin[k] = load_as<S, T>(p, src[fidx(p.plane, p.pitch, k, y, x)], k);
+        }
+        if constexpr (std::is_same<T, double>::value) {
+            bad = site_collide<Q, T>(fin, T(p.a), p.collide != 0, fs, fp, ds, dsin, rho, p.eq, false);
+        } else {
+            bad = site_collide_dev<Q>(fin, (float)p.a, (float)(1.0 + p.a), p.collide != 0, p.rho_ref, p.rwf, fs, nq,
+                                      fp, fa, ds, dsin, rho);
+        }
+        if (!bad && isfinite((double)ds)) {
+            sum += (double)ds;
+            cnt += 1.0;
+        }
+    }
+    sum = warp_sum(sum);
+    cnt = warp_sum(cnt);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        sw[warp][0] = sum;
+        sw[warp][1] = cnt;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        double v = 0.0;
+        for (int w = 0; w < 8; ++w) v += sw[w][threadIdx.x];
+        part[2 * blockIdx.x + threadIdx.x] = v;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_ens_mean(const double *__restrict__ part, int nblk, double smooth_delta,
+                                                  double smooth_k, double *__restrict__ out)
+{
+    __shared__ double sw[8][2];
+    double sum = 0.0, cnt = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += 256) {
+        sum += part[2 * b];
+        cnt += part[2 * b + 1];
+    }
+    sum = warp_sum(sum);
+    cnt = warp_sum(cnt);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        sw[warp][0] = sum;
+        sw[warp][1] = cnt;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0, c = 0.0;
+        for (int w = 0; w < 8; ++w) {
+            s += sw[w][0];
+            c += sw[w][1];
+        }
+        const double E = c > 0.0 ? s / c : 0.0;
+        out[0] = E;
+        out[1] = E > 0.0 ? smooth_delta / pow(E, smooth_k) : 0.0;  // alpha of Eq. smooth1
     }
 }
 
@@ -436,6 +541,17 @@ cudaError_t launch_delta_s(int q, const StepParams &p, const T *f, double *out, 
 }
 
 template <typename T>
+cudaError_t launch_ens_mean(int q, const StepParams &p, const T *src, double *ens, cudaStream_t s)
+{
+    if (q == 9)
+        k_ens_partial<9, T><<<kEnsBlocks, 256, 0, s>>>(p, src, ens);
+    else
+        k_ens_partial<3, T><<<kEnsBlocks, 256, 0, s>>>(p, src, ens);
+    k_ens_mean<<<1, 256, 0, s>>>(ens, kEnsBlocks, p.smooth_delta, p.smooth_k, ens + 2 * kEnsBlocks);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_init(int q, const StepParams &p, const double *rho, const double *ux, const double *uy, T *f,
                         cudaStream_t s)
 {
@@ -476,6 +592,7 @@ cudaError_t launch_set(int q, const StepParams &p, const double *in, T *f, cudaS
 #define LBM_INST(T)                                                                                           \
     template cudaError_t launch_tiled<T>(int, const StepParams &, const T *, T *, int *, cudaStream_t);     \
     template cudaError_t launch_delta_s<T>(int, const StepParams &, const T *, double *, cudaStream_t);     \
+    template cudaError_t launch_ens_mean<T>(int, const StepParams &, const T *, double *, cudaStream_t);    \
     template cudaError_t launch_init<T>(int, const StepParams &, const double *, const double *,           \
                                         const double *, T *, cudaStream_t);                                  \
     template cudaError_t launch_moments<T>(int, const StepParams &, const T *, double *, double *, double *, \

@@ -20,7 +20,7 @@ from . import build as _build
 D1Q3, D2Q9 = 1, 2
 FP64, FP32, BF16, FP16 = 0, 1, 2, 3
 BC_WALLS, BC_PERIODIC, BC_CHANNEL = 0, 1, 2
-LIM_POSITIVITY, LIM_EHRENFEST, LIM_MEDIAN = 1, 2, 4
+LIM_POSITIVITY, LIM_EHRENFEST, LIM_MEDIAN, LIM_SMOOTH, LIM_THRESHOLD = 1, 2, 4, 8, 16
 MEDIAN_THRESHOLD, MEDIAN_GATE = 0, 1
 EQ_POLYNOMIAL, EQ_ENTROPIC = 0, 1
 KERNEL_AUTO, KERNEL_TILED, KERNEL_FUSED = 0, 1, 2
@@ -36,6 +36,8 @@ class Config(ctypes.Structure):
         ("u_lid", ctypes.c_double), ("rho_wall", ctypes.c_double), ("delta_median", ctypes.c_double),
         ("delta_ehrenfest", ctypes.c_double), ("k_max", ctypes.c_int64),
         ("stats_history", ctypes.c_int32), ("equilibrium", ctypes.c_int32), ("rho_ref", ctypes.c_double),
+        ("smooth_delta", ctypes.c_double), ("smooth_k", ctypes.c_double), ("threshold_c", ctypes.c_double),
+        ("threshold_delta", ctypes.c_double),
     ]
 
 

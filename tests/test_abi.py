@@ -34,12 +34,14 @@ def test_config_validation_without_gpu(lib):
     from paper_0704_0043_gb300 import lbm
     base = dict(lattice=lbm.D2Q9, nx=100, ny=100, precision=lbm.FP32, boundary=lbm.BC_WALLS)
     assert lbm.footprint_bytes(**base) > 2 * 9 * 100 * 100 * 4
-    bad = [dict(nx=1), dict(lattice=3), dict(beta=1.5), dict(limiters=8), dict(k_max=-1),
+    bad = [dict(nx=1), dict(lattice=3), dict(beta=1.5), dict(limiters=64), dict(k_max=-1),
            dict(lattice=lbm.D1Q3, ny=2), dict(lattice=lbm.D1Q3, ny=1, boundary=lbm.BC_CHANNEL),
            dict(precision=7), dict(delta_median=-1.0), dict(median_mode=5),
            dict(kernel=lbm.KERNEL_FUSED, precision=lbm.FP64),
            dict(equilibrium=2), dict(equilibrium=lbm.EQ_ENTROPIC),
-           dict(equilibrium=lbm.EQ_ENTROPIC, precision=lbm.BF16)]
+           dict(equilibrium=lbm.EQ_ENTROPIC, precision=lbm.BF16), dict(limiters=32),
+           dict(smooth_k=0.0), dict(smooth_delta=-1.0), dict(threshold_c=float("nan")),
+           dict(threshold_delta=-1e-3), dict(limiters=lbm.LIM_SMOOTH, kernel=lbm.KERNEL_FUSED)]
     for b in bad:
         cfg = dict(base)
         cfg.update(b)
@@ -55,7 +57,7 @@ def test_config_validation_without_gpu(lib):
 
 def test_abi_version_and_status_names(lib):
     lib.lbm_abi_version.restype = ctypes.c_int32
-    assert lib.lbm_abi_version() == 1
+    assert lib.lbm_abi_version() == 2
     lib.lbm_status_string.restype = ctypes.c_char_p
     assert lib.lbm_status_string(4) == b"LBM_ERR_NONFINITE"
 
