@@ -185,6 +185,9 @@ __global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const S *__r
     double acc[P_NSTAT];
 #pragma unroll
     for (int i = 0; i < P_NSTAT; ++i) acc[i] = 0.0;
+    // FP32 storage: the three dS sums as FP32 terms and the counts as flags (see below)
+    float fsum_ds = 0.f, fsum_in = 0.f, fsum_lim = 0.f;
+    bool c_pos = false, c_med = false, c_bad = false;
     if (own) {
         T phi_pos = T(1), phi_med = T(1);
         if (!bad) {
@@ -252,7 +255,7 @@ __global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const S *__r
                 const float c = limit_weight(phi, (float)p.a, p.collide != 0);
 #pragma unroll
                 for (int k = 0; k < Q; ++k) dst[fidx(p.plane, p.pitch, k, y, x)] = f2s<S>(fmaf(-c, nq[k], fin[k]));
-                acc[P_DS_LIM] = Ar<double>::mul(Ar<double>::sub(1.0, Ar<double>::mul((double)phi, (double)phi)), (double)ds);
+                fsum_lim = __fmul_rn(__fsub_rn(1.f, __fmul_rn((float)phi, (float)phi)), (float)ds);
             }
         } else {
 #pragma unroll
@@ -264,16 +267,22 @@ __global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const S *__r
                 // entropic f*: sums of entropy differences where both entropies are finite
                 if (isfinite(ds)) acc[P_SUM_DS] = (double)ds;
                 if (isfinite(ds) && isfinite(dsin)) acc[P_SUM_IN] = Ar<double>::sub((double)dsin, (double)ds);
-            } else {
+            } else if constexpr (std::is_same<T, double>::value) {
                 acc[P_SUM_DS] = (double)ds;
                 acc[P_SUM_IN] = (double)dsin;
+            } else {
+                fsum_ds = (float)ds;
+                fsum_in = (float)dsin;
             }
         } else {
             acc[P_NBAD] = 1.0;
+            c_bad = true;
             atomicOr(p.status, kStatNonfinite);
         }
         acc[P_NPOS] = phi_pos < T(1) ? 1.0 : 0.0;
         acc[P_NMED] = phi_med < T(1) ? 1.0 : 0.0;
+        c_pos = phi_pos < T(1);
+        c_med = phi_med < T(1);
         if ((p.limiters & 2u) && !bad) {
             // Ehrenfests' candidates are decided on an FP64 dS(f').  FP32 storage:
             // sites near or above the threshold recompute their collision in FP64
@@ -315,10 +324,37 @@ __global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const S *__r
     }
     // block partial sums, fixed order
     const int lin = ty * BX + tx, warp = lin >> 5, lane = lin & 31;
+    if constexpr (std::is_same<T, double>::value) {
 #pragma unroll
-    for (int i = 0; i < P_NSTAT; ++i) {
-        const double v = warp_sum(acc[i]);
-        if (lane == 0) sred[warp][i] = v;
+        for (int i = 0; i < P_NSTAT; ++i) {
+            const double v = warp_sum(acc[i]);
+            if (lane == 0) sred[warp][i] = v;
+        }
+    } else {
+        // FP32 storage: GB300's FP64 pipe is slow, and seven FP64 warp sums per
+        // site bound this kernel.  The dS terms are FP32 values: a warp adds its
+        // 32 in FP32 (~1e-6 relative); the mass stays FP64 (its total must keep
+        // the per-step mass changes); the counts come from ballots, exactly.
+        // The block adds the warp totals in FP64 in a fixed order.
+        const double m = warp_sum(acc[P_MASS]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            fsum_ds = __fadd_rn(fsum_ds, __shfl_down_sync(0xffffffffu, fsum_ds, o));
+            fsum_in = __fadd_rn(fsum_in, __shfl_down_sync(0xffffffffu, fsum_in, o));
+            fsum_lim = __fadd_rn(fsum_lim, __shfl_down_sync(0xffffffffu, fsum_lim, o));
+        }
+        const int npos = __popc(__ballot_sync(0xffffffffu, c_pos));
+        const int nmed = __popc(__ballot_sync(0xffffffffu, c_med));
+        const int nbad = __popc(__ballot_sync(0xffffffffu, c_bad));
+        if (lane == 0) {
+            sred[warp][P_MASS] = m;
+            sred[warp][P_SUM_DS] = (double)fsum_ds;
+            sred[warp][P_SUM_IN] = (double)fsum_in;
+            sred[warp][P_DS_LIM] = (double)fsum_lim;
+            sred[warp][P_NPOS] = (double)npos;
+            sred[warp][P_NMED] = (double)nmed;
+            sred[warp][P_NBAD] = (double)nbad;
+        }
     }
     __syncthreads();
     if (lin < P_NSTAT) {
@@ -341,6 +377,10 @@ __global__ void __launch_bounds__(256) k_ens_partial(StepParams p, const S *__re
     __shared__ double sw[8][2];
     const long long n = (long long)p.nx * p.ny;
     double sum = 0.0, cnt = 0.0;
+    // FP32 storage: a thread's own terms in FP32 and an integer count (GB300's
+    // FP64 pipe would otherwise bound this read-once pass)
+    float fsum = 0.f;
+    int icnt = 0;
     for (long long s = blockIdx.x * 256LL + threadIdx.x; s < n; s += (long long)gridDim.x * 256) {
         const int x = (int)(s % p.nx), y = (int)(s / p.nx);
         T fin[Q], fs[Q], fp[Q], fa[Q];
@@ -359,10 +399,21 @@ __global__ void __launch_bounds__(256) k_ens_partial(StepParams p, const S *__re
             bad = site_collide_dev<Q>(fin, (float)p.a, (float)(1.0 + p.a), p.collide != 0, p.rho_ref, p.rwf, fs, nq,
                                       fp, fa, ds, dsin, rho);
         }
-        if (!bad && isfinite((double)ds)) {
-            sum += (double)ds;
-            cnt += 1.0;
+        if constexpr (std::is_same<T, double>::value) {
+            if (!bad && isfinite(ds)) {
+                sum += ds;
+                cnt += 1.0;
+            }
+        } else {
+            if (!bad && isfinite(ds)) {
+                fsum = __fadd_rn(fsum, ds);
+                icnt += 1;
+            }
         }
+    }
+    if constexpr (!std::is_same<T, double>::value) {
+        sum = (double)fsum;
+        cnt = (double)icnt;
     }
     sum = warp_sum(sum);
     cnt = warp_sum(cnt);
