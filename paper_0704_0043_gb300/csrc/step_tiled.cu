@@ -178,6 +178,31 @@ __global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const S *__r
         if (bad) ds = T(INFINITY);
     }
     sds[ty * BX + tx] = ds;
+    // FP32 storage: the block's parameters in FP32, converted once (conversions
+    // and compares of doubles run on this GPU's slow FP64 pipe; per thread they
+    // bound the kernel).  Each equals the per-thread expression it replaces, so
+    // the results do not change: kc[0] = delta_m, kc[1] = the Ehrenfests'
+    // recording threshold, kc[2] = 2 beta - 1, kc[3] = alpha of the smooth
+    // limiter, kc[4] = dS_t rounded down (for a float dS, dS > kc[4] exactly when
+    // (double) dS > dS_t), kc[5] = smooth_k; ke: E > 0, k = 1/2, thresholds on
+    __shared__ float kc[6];
+    __shared__ int ke[3];
+    if constexpr (!std::is_same<T, double>::value) {
+        if (tx == 0 && ty == 0) {
+            kc[0] = (float)p.delta_m;
+            kc[1] = (float)(p.delta_e * (1.0 - 1.0 / 64.0));
+            kc[2] = (float)p.a;
+            const double E = (p.limiters & 24u) ? p.ens[0] : 0.0;
+            double t = p.threshold_c * E;
+            if (t < p.threshold_delta) t = p.threshold_delta;
+            kc[3] = (p.limiters & 24u) ? (float)p.ens[1] : 0.f;
+            kc[4] = __double2float_rd(t);
+            kc[5] = (float)p.smooth_k;
+            ke[0] = E > 0.0;
+            ke[1] = p.smooth_k == 0.5;
+            ke[2] = (p.limiters & 16u) != 0;
+        }
+    }
     __syncthreads();
 
     const bool own = valid && tx >= 1 && tx <= BX - 2 && (Q == 3 || (ty >= 1 && ty <= BY - 2)) && x >= 0 &&
@@ -186,7 +211,7 @@ __global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const S *__r
 #pragma unroll
     for (int i = 0; i < P_NSTAT; ++i) acc[i] = 0.0;
     // FP32 storage: the three dS sums as FP32 terms and the counts as flags (see below)
-    float fsum_ds = 0.f, fsum_in = 0.f, fsum_lim = 0.f;
+    float fsum_ds = 0.f, fsum_in = 0.f, fsum_lim = 0.f, fmass = 0.f;
     bool c_pos = false, c_med = false, c_bad = false;
     if (own) {
         T phi_pos = T(1), phi_med = T(1);
@@ -204,33 +229,47 @@ __global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const S *__r
             }
             // the homothety acts only where dS > delta_m (both acceptance
             // rules), so the median is formed only there
-            if ((p.limiters & 4u) && ds > T(p.delta_m)) {
+            T dm;
+            if constexpr (std::is_same<T, double>::value)
+                dm = p.delta_m;
+            else
+                dm = kc[0];
+            if ((p.limiters & 4u) && ds > dm) {
                 T med;
                 if (stencil_median<Q, T>(p, sds, BX, tx, ty, x, y, med))
-                    phi_med = phi_median<T>(ds, med, T(p.delta_m), p.median_mode);
+                    phi_med = phi_median<T>(ds, med, dm, p.median_mode);
             }
         }
         T phi = phi_pos < phi_med ? phi_pos : phi_med;
         if (!bad && (p.limiters & 24u)) {
             // ensemble-dependent limiters: ens = {E(dS), alpha = delta / E^k} of this pass
-            const double E = p.ens[0];
             T pe = T(1);
-            if ((p.limiters & 8u) && E > 0.0 && ds > T(0)) {
-                // Eq. smooth1 (Sec. 4.3.2); k = 1/2 by a square root
-                if constexpr (std::is_same<T, double>::value) {
+            if constexpr (std::is_same<T, double>::value) {
+                const double E = p.ens[0];
+                if ((p.limiters & 8u) && E > 0.0 && ds > 0.0) {
+                    // Eq. smooth1 (Sec. 4.3.2); k = 1/2 by a square root
                     const double pk = p.smooth_k == 0.5 ? sqrt(ds) : pow(ds, p.smooth_k);
                     pe = 1.0 / (1.0 + p.ens[1] * pk);
-                } else {
-                    const float pk = p.smooth_k == 0.5 ? sqrtf(ds) : powf(ds, (float)p.smooth_k);
-                    pe = 1.0f / (1.0f + (float)p.ens[1] * pk);
                 }
-            }
-            if (p.limiters & 16u) {
-                // threshold filter: dS_t = max(c E, delta), homothety where dS > dS_t (Sec. 3.4)
-                double t = p.threshold_c * E;
-                if (t < p.threshold_delta) t = p.threshold_delta;
-                if ((double)ds > t) {
-                    const T pt = T(sqrt(t / (double)ds));
+                if (p.limiters & 16u) {
+                    // threshold filter: dS_t = max(c E, delta), homothety where dS > dS_t (Sec. 3.4)
+                    double t = p.threshold_c * E;
+                    if (t < p.threshold_delta) t = p.threshold_delta;
+                    if (ds > t) {
+                        const double pt = sqrt(t / ds);
+                        if (pt < pe) pe = pt;
+                    }
+                }
+            } else {
+                if ((p.limiters & 8u) && ke[0] && ds > 0.f) {
+                    const float pk = ke[1] ? sqrtf(ds) : powf(ds, kc[5]);
+                    pe = 1.0f / (1.0f + kc[3] * pk);
+                }
+                if (ke[2] && ds > kc[4]) {
+                    // rare: the exact dS_t of the limited site
+                    double t = p.threshold_c * p.ens[0];
+                    if (t < p.threshold_delta) t = p.threshold_delta;
+                    const float pt = (float)sqrt(t / (double)ds);
                     if (pt < pe) pe = pt;
                 }
             }
@@ -252,7 +291,7 @@ __global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const S *__r
                     acc[P_DS_LIM] = A::mul(A::sub(1.0, A::mul(phi, phi)), ds);
                 }
             } else {
-                const float c = limit_weight(phi, (float)p.a, p.collide != 0);
+                const float c = limit_weight(phi, kc[2], p.collide != 0);
 #pragma unroll
                 for (int k = 0; k < Q; ++k) dst[fidx(p.plane, p.pitch, k, y, x)] = f2s<S>(fmaf(-c, nq[k], fin[k]));
                 fsum_lim = __fmul_rn(__fsub_rn(1.f, __fmul_rn((float)phi, (float)phi)), (float)ds);
@@ -262,6 +301,7 @@ __global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const S *__r
             for (int k = 0; k < Q; ++k) dst[fidx(p.plane, p.pitch, k, y, x)] = f2s<S>(fp[k]);
         }
         acc[P_MASS] = (double)rho;
+        if constexpr (!std::is_same<T, double>::value) fmass = __fsub_rn((float)rho, p.rho_ref);  // exact
         if (!bad) {
             if (p.eq == 1) {
                 // entropic f*: sums of entropy differences where both entropies are finite
@@ -293,7 +333,7 @@ __global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const S *__r
                 key = ds;
                 is = ds > p.delta_e;
             } else {
-                if (ds > (float)(p.delta_e * (1.0 - 1.0 / 64.0))) {
+                if (ds > kc[1]) {
                     double fin64[Q], fs64[Q], fp64[Q], d64, din64, r64;
                     if (p.collide) {
                         pull<Q, S, double>(p, src, x, y, fin64);
@@ -333,12 +373,15 @@ __global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const S *__r
     } else {
         // FP32 storage: GB300's FP64 pipe is slow, and seven FP64 warp sums per
         // site bound this kernel.  The dS terms are FP32 values: a warp adds its
-        // 32 in FP32 (~1e-6 relative); the mass stays FP64 (its total must keep
-        // the per-step mass changes); the counts come from ballots, exactly.
-        // The block adds the warp totals in FP64 in a fixed order.
-        const double m = warp_sum(acc[P_MASS]);
+        // 32 in FP32 (~1e-6 relative).  The mass is rho_ref times the warp's
+        // owned sites plus the FP32 sum of rho - rho_ref (each term exact, the
+        // sum of 32 small terms within ~1e-6 of itself, i.e. ~1e-13 of the
+        // mass); the counts come from ballots, exactly.  The block adds the
+        // warp totals in FP64 in a fixed order.
+        const int nown = __popc(__ballot_sync(0xffffffffu, own));
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
+            fmass = __fadd_rn(fmass, __shfl_down_sync(0xffffffffu, fmass, o));
             fsum_ds = __fadd_rn(fsum_ds, __shfl_down_sync(0xffffffffu, fsum_ds, o));
             fsum_in = __fadd_rn(fsum_in, __shfl_down_sync(0xffffffffu, fsum_in, o));
             fsum_lim = __fadd_rn(fsum_lim, __shfl_down_sync(0xffffffffu, fsum_lim, o));
@@ -347,7 +390,7 @@ __global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const S *__r
         const int nmed = __popc(__ballot_sync(0xffffffffu, c_med));
         const int nbad = __popc(__ballot_sync(0xffffffffu, c_bad));
         if (lane == 0) {
-            sred[warp][P_MASS] = m;
+            sred[warp][P_MASS] = (double)p.rho_ref * (double)nown + (double)fmass;
             sred[warp][P_SUM_DS] = (double)fsum_ds;
             sred[warp][P_SUM_IN] = (double)fsum_in;
             sred[warp][P_DS_LIM] = (double)fsum_lim;
