@@ -477,7 +477,11 @@ static void limit_core(const orc_config *cfg, unsigned limiters, const double *f
             /* Ehrenfests' step: equilibrate the limited state at s, f -> f*(m(f)). */
             for (int k = 0; k < q; ++k) fl[k] = f_out[k * n + s];
             orc_site_moments(cfg->lattice, fl, &r, &a, &b);
-            site_feq(cfg, r, a, b, feq);
+            st->n_ehr++;
+            if (sel) sel[t] = s;
+            /* entropic f*: where the limited state's moments have no f* (|u_j|
+             * rounded to 1 or more) the site keeps its populations */
+            if (site_feq(cfg, r, a, b, feq)) continue;
             for (int k = 0; k < q; ++k) f_out[k * n + s] = feq[k];
             if (cfg->equilibrium == ORC_EQ_ENTROPIC) {
                 /* the entropy the step adds: dS of the limited state w.r.t. its own f* */
@@ -486,8 +490,6 @@ static void limit_core(const orc_config *cfg, unsigned limiters, const double *f
             } else {
                 st->dS_lim += (phi[s] * phi[s]) * dS[s];
             }
-            st->n_ehr++;
-            if (sel) sel[t] = s;
         }
         free(c);
     }

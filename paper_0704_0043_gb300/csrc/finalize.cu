@@ -372,6 +372,7 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, 
             const Cand c = p.cand[ci];
             const int x = c.site % p.nx, y = c.site / p.nx;
             T g[Q], fs[Q], rho, ux, uy;
+            bool write = true;
             if constexpr (std::is_same<T, float>::value) {
                 // FP32 / 16-bit storage: f*(m) as g - n (the limiter with phi = 0),
                 // m taken from the pass's input (the collision conserves m), so
@@ -390,15 +391,18 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, 
                 moments<Q, T>(g, rho, ux, uy);
                 if (p.eq == 1) {
                     // entropic f*: the step adds dS of the limited state w.r.t. its own f*
-                    feq_any<Q>(1, rho, ux, uy, fs);
-                    const double d = rel_entropy<Q>(g, fs);
+                    // where the limited state's moments have no entropic f* the site keeps its populations
+                    write = feq_any<Q>(1, rho, ux, uy, fs);
+                    const double d = write ? rel_entropy<Q>(g, fs) : (double)NAN;
                     if (isfinite(d)) ehr_sum = Ar<double>::add(ehr_sum, d);
                 } else {
                     feq<Q, T>(rho, ux, uy, fs);
                 }
             }
+            if (write) {
 #pragma unroll
-            for (int q = 0; q < Q; ++q) f[fidx(p.plane, p.pitch, q, y, x)] = f2s<S>(fs[q]);
+                for (int q = 0; q < Q; ++q) f[fidx(p.plane, p.pitch, q, y, x)] = f2s<S>(fs[q]);
+            }
             if (p.eq != 1) ehr_sum = Ar<double>::add(ehr_sum, Ar<double>::mul(Ar<double>::mul(c.phi, c.phi), c.key));
         }
         __syncthreads();
