@@ -27,7 +27,7 @@ _LIB_PATH = os.path.join(_BUILD, "liblbm_oracle.so")
 D1Q3, D2Q9 = 1, 2
 BC_WALLS, BC_PERIODIC, BC_CHANNEL = 0, 1, 2
 LIM_POSITIVITY, LIM_EHRENFEST, LIM_MEDIAN = 1, 2, 4
-LIM_SMOOTH, LIM_THRESHOLD = 8, 16
+LIM_SMOOTH, LIM_THRESHOLD, LIM_ENTTHRESH = 8, 16, 32
 MEDIAN_THRESHOLD, MEDIAN_GATE = 0, 1
 EQ_POLYNOMIAL, EQ_ENTROPIC = 0, 1
 
@@ -56,6 +56,7 @@ class _Config(ctypes.Structure):
         ("k_max", ctypes.c_longlong), ("median_mode", ctypes.c_int), ("equilibrium", ctypes.c_int),
         ("smooth_delta", ctypes.c_double), ("smooth_k", ctypes.c_double),
         ("threshold_c", ctypes.c_double), ("threshold_delta", ctypes.c_double),
+        ("entthresh_delta0", ctypes.c_double),
     ]
 
 
@@ -129,6 +130,7 @@ class Config:
     smooth_k: float = 0.5
     threshold_c: float = 10.0
     threshold_delta: float = 0.0
+    entthresh_delta0: float = 0.1
 
     @property
     def q(self) -> int:
@@ -145,7 +147,7 @@ class Config:
         return _Config(self.lattice, self.nx, self.ny, self.boundary, self.beta, self.u_lid,
                        self.rho_wall, self.limiters, self.delta_median, self.delta_ehrenfest,
                        self.k_max, self.median_mode, self.equilibrium, self.smooth_delta,
-                       self.smooth_k, self.threshold_c, self.threshold_delta)
+                       self.smooth_k, self.threshold_c, self.threshold_delta, self.entthresh_delta0)
 
 
 def _f64(a, shape=None):

@@ -354,6 +354,33 @@ typedef struct {
     long long s;
 } cand_t;
 
+static int dbl_desc(const void *pa, const void *pb)
+{
+    double a = *(const double *)pa, b = *(const double *)pb;
+    return (a < b) - (a > b);
+}
+
+/*
+ * Eq. EntThresh on the empirical distribution of the n values v: the dS_0 >= 0
+ * with sum_s max(v_s - dS_0, 0) = rhs, for 0 <= rhs <= sum_s v_s.  With v
+ * sorted in descending order and m values above dS_0 the left side is
+ * S_m - m dS_0 (S_m the sum of the m largest), so dS_0 = (S_m - rhs) / m for
+ * the m whose segment [v_(m+1), v_m] holds it.
+ */
+static double entthresh(double *v, long long n, double rhs)
+{
+    if (n <= 0 || !(rhs > 0.0)) return n > 0 ? INFINITY : 0.0;
+    qsort(v, (size_t)n, sizeof(double), dbl_desc);
+    double S = 0.0;
+    for (long long m = 1; m <= n; ++m) {
+        S += v[m - 1];
+        double t = (S - rhs) / (double)m;
+        double lo = m < n ? v[m] : 0.0;
+        if (t >= lo) return t > 0.0 ? t : 0.0;
+    }
+    return 0.0;
+}
+
 static int cand_cmp(const void *pa, const void *pb)
 {
     const cand_t *a = (const cand_t *)pa, *b = (const cand_t *)pb;
@@ -385,6 +412,19 @@ static void limit_core(const orc_config *cfg, unsigned limiters, const double *f
             e_cnt++;
         }
     double E = e_cnt > 0 ? e_sum / (double)e_cnt : 0.0;
+    double t_ent = 0.0;
+    if (limiters & ORC_LIM_ENTTHRESH) {
+        /* Eq. EntThresh over the same sites as E; dS_t = max(dS_0, delta) */
+        double *v = (double *)malloc(sizeof(double) * (size_t)(e_cnt > 0 ? e_cnt : 1));
+        long long m = 0;
+        for (long long s = 0; s < n; ++s)
+            if (!bad[s] && isfinite(dS[s])) v[m++] = dS[s];
+        double a = 2.0 * cfg->beta - 1.0;
+        double rhs = cfg->entthresh_delta0 * ((1.0 - a * a) * e_sum);
+        t_ent = entthresh(v, m, rhs);
+        if (t_ent < cfg->threshold_delta) t_ent = cfg->threshold_delta;
+        free(v);
+    }
     for (long long s = 0; s < n; ++s) {
         double phi_pos = 1.0, phi_med = 1.0, phi_ens = 1.0;
         if (!bad[s]) {
@@ -393,6 +433,10 @@ static void limit_core(const orc_config *cfg, unsigned limiters, const double *f
                 double alpha = cfg->smooth_delta / pow(E, cfg->smooth_k);
                 double p_s = 1.0 / (1.0 + alpha * pow(dS[s], cfg->smooth_k));
                 if (p_s < phi_ens) phi_ens = p_s;
+            }
+            if ((limiters & ORC_LIM_ENTTHRESH) && dS[s] > t_ent) {
+                double p_e = sqrt(t_ent / dS[s]);
+                if (p_e < phi_ens) phi_ens = p_e;
             }
             if (limiters & ORC_LIM_THRESHOLD) {
                 /* Sec. 3.4: dS_t = max(dS_0, delta), homothety where dS > dS_t */

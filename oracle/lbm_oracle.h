@@ -47,6 +47,7 @@ extern "C" {
 #define ORC_LIM_MEDIAN 4u
 #define ORC_LIM_SMOOTH 8u     /* ensemble-dependent smooth limiter, Eq. smooth1 with alpha = delta / E(dS)^k */
 #define ORC_LIM_THRESHOLD 16u /* threshold filter, dS_t = max(c E(dS), delta) (Sec. 3.4, Sec. 4.3.2) */
+#define ORC_LIM_ENTTHRESH 32u /* threshold filter with dS_0 solving Eq. EntThresh, dS_t = max(dS_0, delta) */
 
 #define ORC_MEDIAN_THRESHOLD 0 /* dS_t = max(dS_med, delta); phi = sqrt(dS_t/dS) where dS > dS_t */
 #define ORC_MEDIAN_GATE 1      /* phi = sqrt(dS_med/dS) where dS > delta and dS_med < dS */
@@ -70,7 +71,8 @@ typedef struct {
     double smooth_delta;    /* ORC_LIM_SMOOTH: alpha = smooth_delta / E(dS)^smooth_k */
     double smooth_k;        /* ORC_LIM_SMOOTH: exponent k (> 0) */
     double threshold_c;     /* ORC_LIM_THRESHOLD: dS_0 = threshold_c * E(dS) */
-    double threshold_delta; /* ORC_LIM_THRESHOLD: dS_t = max(dS_0, threshold_delta) */
+    double threshold_delta; /* ORC_LIM_THRESHOLD / ORC_LIM_ENTTHRESH: dS_t = max(dS_0, threshold_delta) */
+    double entthresh_delta0; /* ORC_LIM_ENTTHRESH: delta_0 of Eq. EntThresh (Eq. LimEntLim's bound) */
 } orc_config;
 
 /*
@@ -79,7 +81,12 @@ typedef struct {
  * (before any limiter).  Smooth limiter (Eq. smooth1): phi = 1 / (1 + alpha
  * dS^k), alpha = smooth_delta / E^k, phi = 1 where E <= 0 or dS = 0.
  * Threshold filter (Sec. 3.4 with dS_0 = c E as in Sec. 4.3.2): phi =
- * sqrt(dS_t / dS) where dS > dS_t.  All limiters compose as the minimum of
+ * sqrt(dS_t / dS) where dS > dS_t.  ORC_LIM_ENTTHRESH takes dS_0 from Eq.
+ * EntThresh on the ensemble's own distribution of dS (the limit of the
+ * histogram estimate of Sec. 3.4): sum_s max(dS_s - dS_0, 0) =
+ * delta_0 [1 - (2 beta - 1)^2] sum_s dS_s over the same sites as E, solved
+ * exactly (its left side is continuous, piecewise linear and decreasing).
+ * Parity unpinned against a GPU path: no GPU path implements it yet.  All limiters compose as the minimum of
  * their phi, before Ehrenfests' step.
  *
  * With entropic quasiequilibria (ORC_EQ_ENTROPIC) dS is the exact relative

@@ -121,3 +121,40 @@ def test_ensemble_limiters_compose_with_the_others_as_the_minimum():
     phis = [oracle.limit(cfg, f, lim).phi for lim in lims]
     both = oracle.limit(cfg, f, sum(lims)).phi
     np.testing.assert_array_equal(both, np.minimum.reduce(phis))
+
+
+# Eq. EntThresh: dS_0 solves sum_s max(dS_s - dS_0, 0) = delta_0 [1 - (2 beta - 1)^2] sum_s dS_s on the
+# ensemble's own distribution.  In the quadratic entropy the homothety sqrt(dS_t / dS) brings each limited
+# site to dS_t, so the limiter's entropy production equals the right-hand side: Eq. LimEntLim holds with
+# equality, delta_lim S = delta_0 [1 - (2 beta - 1)^2] sum dS.
+
+@pytest.mark.parametrize("delta0", [0.05, 0.3, 0.9])
+def test_entthresh_limiter_spends_exactly_its_entropy_budget(delta0):
+    f = _state(7, nx=24, ny=17, eps=0.3)
+    cfg = _cfg(24, 17, oracle.LIM_ENTTHRESH, beta=0.93, entthresh_delta0=delta0)
+    r = oracle.step(cfg, f)
+    a = 2 * cfg.beta - 1
+    assert 0 < r.stats["dS_lim"]
+    assert r.stats["dS_lim"] == pytest.approx(delta0 * (1 - a * a) * r.stats["sum_dS"], rel=1e-12)
+    # the limited sites are exactly those above one common threshold
+    hit = r.phi < 1
+    assert hit.any() and (~hit).any()
+    assert r.dS[hit].min() > r.dS[~hit].max()
+
+
+def test_entthresh_limiter_on_a_uniform_field():
+    f = _uniform_state()
+    cfg = _cfg(8, 6, oracle.LIM_ENTTHRESH, beta=0.9, entthresh_delta0=0.5)
+    a = 2 * cfg.beta - 1
+    r = oracle.limit(cfg, f, oracle.LIM_ENTTHRESH)
+    # every dS equal: dS_0 = dS (1 - delta_0 [1 - a^2]), phi = sqrt of that ratio
+    np.testing.assert_allclose(r.phi, np.sqrt(1 - 0.5 * (1 - a * a)), rtol=1e-14)
+
+
+def test_entthresh_limiter_switched_off():
+    f = _state(8)
+    r = oracle.limit(_cfg(13, 11, oracle.LIM_ENTTHRESH, entthresh_delta0=0.0), f, oracle.LIM_ENTTHRESH)
+    assert np.array_equal(r.f, f)
+    r = oracle.limit(_cfg(13, 11, oracle.LIM_ENTTHRESH, entthresh_delta0=0.5, threshold_delta=1e9), f,
+                     oracle.LIM_ENTTHRESH)
+    assert np.array_equal(r.f, f)
