@@ -30,6 +30,7 @@ LIM_POSITIVITY, LIM_EHRENFEST, LIM_MEDIAN = 1, 2, 4
 LIM_SMOOTH, LIM_THRESHOLD, LIM_ENTTHRESH = 8, 16, 32
 MEDIAN_THRESHOLD, MEDIAN_GATE = 0, 1
 EQ_POLYNOMIAL, EQ_ENTROPIC = 0, 1
+COLL_LBGK, COLL_ELBM = 0, 1
 
 
 def build(force: bool = False) -> str:
@@ -56,7 +57,7 @@ class _Config(ctypes.Structure):
         ("k_max", ctypes.c_longlong), ("median_mode", ctypes.c_int), ("equilibrium", ctypes.c_int),
         ("smooth_delta", ctypes.c_double), ("smooth_k", ctypes.c_double),
         ("threshold_c", ctypes.c_double), ("threshold_delta", ctypes.c_double),
-        ("entthresh_delta0", ctypes.c_double),
+        ("entthresh_delta0", ctypes.c_double), ("collision", ctypes.c_int),
     ]
 
 
@@ -89,6 +90,8 @@ def _load():
         lib.orc_entropy.restype = ctypes.c_double
         lib.orc_rel_entropy.argtypes = [ctypes.c_int, dp, dp]
         lib.orc_rel_entropy.restype = ctypes.c_double
+        lib.orc_elbm_alpha.argtypes = [ctypes.c_int, dp, dp, ctypes.POINTER(ctypes.c_int)]
+        lib.orc_elbm_alpha.restype = ctypes.c_double
         lib.orc_site_moments.argtypes = [ctypes.c_int, dp, dp, dp, dp]
         lib.orc_init.argtypes = [cp, dp, dp, dp, dp]
         lib.orc_moments.argtypes = [cp, dp, dp, dp, dp]
@@ -131,6 +134,7 @@ class Config:
     threshold_c: float = 10.0
     threshold_delta: float = 0.0
     entthresh_delta0: float = 0.1
+    collision: int = COLL_LBGK
 
     @property
     def q(self) -> int:
@@ -147,7 +151,8 @@ class Config:
         return _Config(self.lattice, self.nx, self.ny, self.boundary, self.beta, self.u_lid,
                        self.rho_wall, self.limiters, self.delta_median, self.delta_ehrenfest,
                        self.k_max, self.median_mode, self.equilibrium, self.smooth_delta,
-                       self.smooth_k, self.threshold_c, self.threshold_delta, self.entthresh_delta0)
+                       self.smooth_k, self.threshold_c, self.threshold_delta, self.entthresh_delta0,
+                       self.collision)
 
 
 def _f64(a, shape=None):
@@ -184,6 +189,15 @@ def rel_entropy(f, fs) -> float:
     f = _f64(f)
     fs = _f64(fs)
     return _load().orc_rel_entropy(len(f), _dp(f), _dp(fs))
+
+
+def elbm_alpha(f, fs):
+    """ELBM's alpha for one site (Eq. entropy_estimate) and whether the positivity boundary was taken."""
+    f = _f64(f)
+    fs = _f64(fs)
+    pos = ctypes.c_int(0)
+    a = _load().orc_elbm_alpha(len(f), _dp(f), _dp(fs), ctypes.byref(pos))
+    return a, bool(pos.value)
 
 
 def site_moments(lattice: int, f) -> tuple:

@@ -138,6 +138,42 @@ double orc_rel_entropy(int q, const double *f, const double *fs)
     return s;
 }
 
+double orc_elbm_alpha(int q, const double *f, const double *fs, int *pos)
+{
+    if (pos) *pos = 0;
+    int same = 1;
+    for (int k = 0; k < q; ++k)
+        if (f[k] != fs[k]) same = 0;
+    if (same) return 2.0;
+    /* positivity boundary of f + alpha (f* - f): the smallest f_k / (f_k - f*_k) over f*_k < f_k */
+    double amax = INFINITY;
+    for (int k = 0; k < q; ++k)
+        if (fs[k] < f[k]) {
+            double r = f[k] / (f[k] - fs[k]);
+            if (r < amax) amax = r;
+        }
+    double g[9];
+    double ds0 = orc_rel_entropy(q, f, fs);
+    /* h(alpha) = S(f~) - S(f) = dS(f) - dS(f~) */
+    for (int k = 0; k < q; ++k) g[k] = f[k] + amax * (fs[k] - f[k]);
+    for (int k = 0; k < q; ++k)
+        if (g[k] < 0.0) g[k] = 0.0; /* the boundary itself: the vanishing population is zero */
+    if (ds0 - orc_rel_entropy(q, g, fs) >= 0.0) {
+        if (pos) *pos = 1;
+        return amax;
+    }
+    double lo = 1.0, hi = amax;
+    for (int it = 0; it < 200 && hi - lo > 1e-15; ++it) {
+        double mid = 0.5 * (lo + hi);
+        for (int k = 0; k < q; ++k) g[k] = f[k] + mid * (fs[k] - f[k]);
+        if (ds0 - orc_rel_entropy(q, g, fs) >= 0.0)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
 /* f* of the configured kind; returns 1 where it does not exist. */
 static int site_feq(const orc_config *cfg, double rho, double ux, double uy, double *fs)
 {
@@ -269,6 +305,11 @@ static int site_collide(const orc_config *cfg, const double *fin, double *fs, do
     for (int k = 0; k < q; ++k) fp[k] = fs[k] + a * (fs[k] - fin[k]);
     for (int k = 0; k < q; ++k)
         if (!(fs[k] > 0.0) || !isfinite(fs[k]) || !isfinite(fin[k])) bad = 1;
+    if (cfg->collision == ORC_COLL_ELBM && !bad) {
+        /* Eq. elbm: F(f) = (1 - beta) f + beta f~ = f + beta alpha (f* - f) */
+        double alpha = orc_elbm_alpha(q, fin, fs, NULL);
+        for (int k = 0; k < q; ++k) fp[k] = fin[k] + (cfg->beta * alpha) * (fs[k] - fin[k]);
+    }
     double s = bad ? 0.0 : site_dS(cfg, q, fp, fs);
     double si = bad ? 0.0 : site_dS(cfg, q, fin, fs);
     if (!dS_ok(cfg, s) || !dS_ok(cfg, si)) bad = 1;

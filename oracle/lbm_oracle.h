@@ -55,6 +55,9 @@ extern "C" {
 #define ORC_EQ_POLYNOMIAL 0 /* Eq. polyeq1d / polyeq2d; dS in its quadratic form */
 #define ORC_EQ_ENTROPIC 1   /* Eq. entropiceq1d / maxwellian; dS = sum_k f_k ln(f_k / f*_k) (Eq. DelS) */
 
+#define ORC_COLL_LBGK 0 /* f' = f* + (2 beta - 1)(f* - f), Eq. lbgkLB */
+#define ORC_COLL_ELBM 1 /* f' = (1 - beta) f + beta f~, f~ = f + alpha (f* - f), S(f~) = S(f) (Eq. elbm, Eq. entropy_estimate) */
+
 typedef struct {
     int lattice;            /* ORC_D1Q3 or ORC_D2Q9 */
     int nx, ny;             /* lattice size; ny = 1 for D1Q3 */
@@ -73,6 +76,7 @@ typedef struct {
     double threshold_c;     /* ORC_LIM_THRESHOLD: dS_0 = threshold_c * E(dS) */
     double threshold_delta; /* ORC_LIM_THRESHOLD / ORC_LIM_ENTTHRESH: dS_t = max(dS_0, threshold_delta) */
     double entthresh_delta0; /* ORC_LIM_ENTTHRESH: delta_0 of Eq. EntThresh (Eq. LimEntLim's bound) */
+    int collision;           /* ORC_COLL_* (ELBM needs ORC_EQ_ENTROPIC) */
 } orc_config;
 
 /*
@@ -126,6 +130,20 @@ double orc_entropy(int lattice, const double *f);
 
 /* Relative entropy sum_k f_k ln(f_k / fs_k) (Eq. DelS) of q populations, 0 ln 0 = 0, +inf if some f_k < 0. */
 double orc_rel_entropy(int q, const double *f, const double *fs);
+
+/*
+ * ELBM (Sec. 3.7, Eq. elbm; the LBGK step of Eq. lbgkLB is its alpha = 2 case):
+ * the nontrivial root alpha > 1 of S(f + alpha (f* - f)) = S(f) for one site's
+ * populations f and their entropic f*, by bisection on [1, alpha_max] to a
+ * bracket of 1e-15, returning the end with no entropy decrease (Sec. 4.2).
+ * alpha_max is the positivity boundary of the line; where the entropy is still
+ * above S(f) there, no root exists in the positive cone and alpha_max is
+ * returned (the positivity rule, Sec. 3.1).  f = f* returns 2.  The entropy
+ * difference is evaluated as dS(f) - dS(f~) (Eq. DelS, same f*), which equals
+ * S(f~) - S(f) for states with the moments of f*.  *pos (may be NULL) is set
+ * to 1 when the positivity boundary was taken.
+ */
+double orc_elbm_alpha(int q, const double *f, const double *fs, int *pos);
 
 /* Moments rho, u of one site's populations (Eq. macro_dis). */
 void orc_site_moments(int lattice, const double *f, double *rho, double *ux, double *uy);
