@@ -87,11 +87,14 @@ class Server:
     memory_bytes: device budget for resident lattices (admission by footprint).
     quantum: steps per batched round between admission / retirement decisions.
     graph_steps: CUDA-graph replay length inside a round (0: plain launches).
+    batch: the batch to serve from (default: a new lbm.Batch on `stream`); any
+    object with lbm.Batch's add / init / step / synchronize / lattice_status /
+    moments / stats / remove methods.
     """
 
     def __init__(self, memory_bytes: int, quantum: int = 500, graph_steps: int = 0,
-                 stream: int | None = None, clock=time.perf_counter):
-        self.batch = lbm.Batch(stream)
+                 stream: int | None = None, clock=time.perf_counter, batch=None):
+        self.batch = lbm.Batch(stream) if batch is None else batch
         if graph_steps:
             self.batch.set_graph(graph_steps)
         self.memory_bytes = int(memory_bytes)
