@@ -176,6 +176,22 @@ def traffic_from_profile(kernel_name: str, sites: int):
     return ent["dram_bytes_per_site"] * sites
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest x over the ranks of the default process group (x itself
+    when there is none): the timed region ends when the slowest replica does."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(world: int, sites: int, steps: int, elapsed_s: float) -> float:
+    """Site updates of all replicas (each runs its own lattice) per second, in millions."""
+    return world * sites * steps / elapsed_s / 1e6
+
+
 TIMING_EVERY = 8  # the step and tail kernels are timed with CUDA events on one step in 8
 
 
@@ -445,11 +461,8 @@ def main():
     clocks = sampler.stop()
     elapsed = ev0.elapsed_time(ev1) / 1e3
     st = lat.stats()
-    if dist is not None:
-        t = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
-    mlups = world * w.sites * args.steps / elapsed / 1e6
+    elapsed = max_over_ranks(elapsed, dist, "cuda")
+    mlups = whole_job_mlups(world, w.sites, args.steps, elapsed)
 
     # roofline of the step kernel (the dominant launch): algorithmic bytes / event time
     bps = BYTES_PER_SITE[("d2q9", args.precision)]
