@@ -16,6 +16,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import os
 import statistics
@@ -136,11 +137,24 @@ KERNEL_SOURCES = {
 }
 
 
-def source_hash(kernel: str) -> str:
+def _code_only(text: str) -> str:
+    """Source text without comments and whitespace: what the compiler sees."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return re.sub(r"\s+", "", text)
+
+
+def source_hash(kernel: str, read=None) -> str:
+    """Hash of the code (comments and whitespace dropped) of the sources the
+    kernel is compiled from; `read(rel)` returns a file's text (default: the tree)."""
     h = hashlib.sha256()
     for rel in KERNEL_SOURCES[kernel]:
-        with open(os.path.join(ROOT, rel), "rb") as fh:
-            h.update(rel.encode() + fh.read())
+        if read is None:
+            with open(os.path.join(ROOT, rel), encoding="utf-8") as fh:
+                text = fh.read()
+        else:
+            text = read(rel)
+        h.update(rel.encode() + _code_only(text).encode())
     return h.hexdigest()[:16]
 
 

@@ -183,9 +183,12 @@ lbm_status lbm_step(lbm_ctx *ctx, int64_t nsteps);
  * stored values: nx * ny doubles into `out`.  No population is modified. */
 lbm_status lbm_delta_s(lbm_ctx *ctx, double *out);
 
-/* Applies `limiters` to the stored populations themselves, with no free flight
- * and no collision: f' := f, f* := f*(m(f)), then the same limiter pass as a
- * step (Sec. 3).  Counts and sums go to the stats (step counter unchanged). */
+/* Applies `limiters` (any LBM_LIM_* bits; Ehrenfests' only if configured at
+ * create) to the stored populations themselves, with no free flight and no
+ * collision: f' := f, f* := f*(m(f)) of the configured kind, then the same
+ * limiter pass as a step (Sec. 3; the ensemble-dependent limiters take E(dS)
+ * of the stored state).  Counts and sums go to the stats (step counter
+ * unchanged).  Errors: LBM_ERR_INVALID_ARG (unknown bits). */
 lbm_status lbm_limit(lbm_ctx *ctx, uint32_t limiters);
 
 /* rho, u (Eq. macro_dis) of the stored populations, FP64, nx * ny each;
