@@ -66,3 +66,37 @@ def test_no_cpu_fallback_in_the_binding():
     """The binding only marshals arguments: it never imports the oracle."""
     src = open(os.path.join(ROOT, "paper_0704_0043_gb300", "lbm.py")).read()
     assert "oracle" not in src.replace("oracle layout", "")
+
+
+def test_python_struct_layouts_match_the_c_header(tmp_path):
+    """The ctypes mirrors of lbm_config and lbm_step_stats have the header's
+    size and every field's offset (a C program built against include/lbm.h
+    prints them)."""
+    import shutil
+    import subprocess
+    from paper_0704_0043_gb300 import lbm
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not found")
+    structs = {"lbm_config": lbm.Config, "lbm_step_stats": lbm.StepStats}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "lbm.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run([gcc, "-std=c11", "-I", inc, "-o", str(exe), str(src)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            cname, what, val = line.split()
+            got[(cname, what)] = int(val)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)

@@ -103,3 +103,36 @@ def test_post_collision_dS_and_lbgk_entropy_production(lattice):
         assert abs(r.stats["sum_dS"] - r.dS[0, 0]) == 0
         # the next-collision dS field of the stored state agrees with the step
         assert oracle.delta_s(cfg, f)[0, 0] == r.dS[0, 0]
+
+
+def test_oracle_struct_layouts_match_its_header(tmp_path):
+    """The oracle's ctypes mirrors (orc_config, orc_stats) have the C header's
+    size and field offsets (a C program built against oracle/lbm_oracle.h prints them)."""
+    import ctypes
+    import os
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not found")
+    structs = {"orc_config": oracle._Config, "orc_stats": oracle.Stats}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "lbm_oracle.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    inc = os.path.dirname(os.path.abspath(oracle.__file__))
+    subprocess.run([gcc, "-std=c11", "-I", inc, "-o", str(exe), str(src)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n"):
+        if line:
+            cname, what, val = line.split()
+            got[(cname, what)] = int(val)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
