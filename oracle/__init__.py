@@ -25,7 +25,7 @@ _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liblbm_oracle.so")
 
 D1Q3, D2Q9 = 1, 2
-BC_WALLS, BC_PERIODIC, BC_CHANNEL = 0, 1, 2
+BC_WALLS, BC_PERIODIC, BC_CHANNEL, BC_NODE_WALLS, BC_DIFFUSIVE = 0, 1, 2, 3, 4
 LIM_POSITIVITY, LIM_EHRENFEST, LIM_MEDIAN = 1, 2, 4
 LIM_SMOOTH, LIM_THRESHOLD, LIM_ENTTHRESH = 8, 16, 32
 MEDIAN_THRESHOLD, MEDIAN_GATE = 0, 1

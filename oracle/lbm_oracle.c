@@ -283,6 +283,88 @@ static void pull(const orc_config *cfg, const double *f, int i, int j, double *f
     }
 }
 
+/* Cavities with boundary nodes on the walls (ORC_BC_NODE_WALLS, ORC_BC_DIFFUSIVE). */
+static int node_walls(const orc_config *cfg)
+{
+    return cfg->lattice == ORC_D2Q9 &&
+           (cfg->boundary == ORC_BC_NODE_WALLS || cfg->boundary == ORC_BC_DIFFUSIVE);
+}
+
+static int boundary_node(const orc_config *cfg, int i, int j)
+{
+    return node_walls(cfg) && (i == 0 || i == cfg->nx - 1 || j == 0 || j == cfg->ny - 1);
+}
+
+static int site_feq(const orc_config *cfg, double rho, double ux, double uy, double *fs);
+
+/*
+ * Step 1 at a boundary node (Sec. 4.4): free flight brings the populations whose
+ * source lies on the lattice; the others come from the wall rule.  The lid is
+ * the top row without its corners and moves with (u_lid, 0); the other walls
+ * and the corners are at rest.
+ *  - bounce-back (Sec. 4.4.1): f_k = f_opp(k) + 6 W_k rho_wall (v_k . u_wall), the
+ *    population that has just arrived moving the other way, plus the momentum
+ *    of the moving wall;
+ *  - diffusive Maxwell wall (Sec. 4.4.2): f_k = gamma f*_k(1, u_wall) with
+ *    gamma = (sum of the arrived f_opp(k)) / (sum of f*_k(1, u_wall)), both sums
+ *    over the populations the wall returns, so that the wall returns the mass it
+ *    receives; in the corners, bounce-back.
+ * In a corner two of the missing populations point out of the lattice again
+ * (their opposite is missing too); they never reach the fluid and keep their
+ * stored values.
+ */
+static void wall_node(const orc_config *cfg, const double *f, int i, int j, double *fo)
+{
+    int nx = cfg->nx, ny = cfg->ny;
+    long long n = (long long)nx * ny, s = (long long)j * nx + i;
+    int known[9];
+    for (int k = 0; k < 9; ++k) {
+        int si = i - cx9[k], sj = j - cy9[k];
+        known[k] = si >= 0 && si < nx && sj >= 0 && sj < ny;
+        fo[k] = known[k] ? f[k * n + (long long)sj * nx + si] : 0.0;
+    }
+    int corner = (i == 0 || i == nx - 1) && (j == 0 || j == ny - 1);
+    int lid = j == ny - 1 && !corner;
+    double uw = lid ? cfg->u_lid : 0.0;
+    if (cfg->boundary == ORC_BC_DIFFUSIVE && !corner) {
+        double fw[9];
+        site_feq(cfg, 1.0, uw, 0.0, fw);  /* density is a linear factor of f*: take 1 */
+        double arrived = 0.0, returned = 0.0;
+        for (int k = 0; k < 9; ++k)
+            if (!known[k]) {
+                arrived += fo[opp9[k]];
+                returned += fw[k];
+            }
+        double gamma = arrived / returned;
+        for (int k = 0; k < 9; ++k)
+            if (!known[k]) fo[k] = gamma * fw[k];
+        return;
+    }
+    for (int k = 0; k < 9; ++k) {
+        if (known[k]) continue;
+        if (known[opp9[k]]) {
+            double v = fo[opp9[k]];
+            if (lid) v += ((6.0 * w9(k)) * cfg->rho_wall) * ((double)cx9[k] * uw);
+            fo[k] = v;
+        } else {
+            fo[k] = f[k * n + s];
+        }
+    }
+}
+
+/* Mass a boundary node carries into the next step: the populations whose
+ * destination lies on the lattice (the others have been returned by the wall
+ * rule and are never streamed again). */
+static double wall_node_mass(const orc_config *cfg, int i, int j, const double *fo)
+{
+    double m = 0.0;
+    for (int k = 0; k < 9; ++k) {
+        int di = i + cx9[k], dj = j + cy9[k];
+        if (di >= 0 && di < cfg->nx && dj >= 0 && dj < cfg->ny) m += fo[k];
+    }
+    return m;
+}
+
 /*
  * Steps 2-5 at one site.  Writes f* and f' (q values each), dS(f') and
  * dS(f_in); returns 1 if the site cannot be limited (rho <= 0, no f* or
@@ -359,6 +441,36 @@ static int median_stencil(const orc_config *cfg, const double *dS, int i, int j,
         return 3;
     }
 #define DS(a, b) dS[(long long)(b) * nx + (a)]
+    if (node_walls(cfg)) {
+        /* Sec. 4.4: boundary nodes are not filtered; a node next to one wall uses
+         * the three nodes along that wall (itself and its two neighbours), a node
+         * next to two walls itself and its inward neighbours along x and y; all
+         * other nodes the 3x3 block. */
+        if (boundary_node(cfg, i, j)) return 0;
+        int nearx = i == 1 || i == nx - 2, neary = j == 1 || j == ny - 2;
+        if (nearx && neary) {
+            v[0] = DS(i, j);
+            v[1] = DS(i == 1 ? 2 : nx - 3, j);
+            v[2] = DS(i, j == 1 ? 2 : ny - 3);
+            return 3;
+        }
+        if (neary) {
+            v[0] = DS(i - 1, j);
+            v[1] = DS(i, j);
+            v[2] = DS(i + 1, j);
+            return 3;
+        }
+        if (nearx) {
+            v[0] = DS(i, j - 1);
+            v[1] = DS(i, j);
+            v[2] = DS(i, j + 1);
+            return 3;
+        }
+        int m = 0;
+        for (int b = -1; b <= 1; ++b)
+            for (int a = -1; a <= 1; ++a) v[m++] = DS(i + a, j + b);
+        return 9;
+    }
     int wallx = cfg->boundary == ORC_BC_WALLS;
     int wally = cfg->boundary != ORC_BC_PERIODIC;
     int nearx = wallx && (i == 0 || i == nx - 1);
@@ -604,6 +716,22 @@ static int run_collide_and_limit(const orc_config *cfg, unsigned limiters, int d
             long long s = (long long)j * nx + i;
             double rho, ds, dsi;
             int b;
+            if (boundary_node(cfg, i, j)) {
+                /* a boundary node: free flight and the wall rule (step), or its
+                 * stored state (limiter pass); no collision, no limiter */
+                if (do_stream)
+                    wall_node(cfg, f_st, i, j, fin);
+                else
+                    for (int k = 0; k < 9; ++k) fin[k] = f_st[k * n + s];
+                for (int k = 0; k < 9; ++k) {
+                    fs[k * n + s] = fin[k];
+                    fp[k * n + s] = fin[k];
+                }
+                dS[s] = 0.0;
+                bad[s] = 2;
+                st.mass += wall_node_mass(cfg, i, j, fin);
+                continue;
+            }
             if (do_stream) {
                 pull(cfg, f_st, i, j, fin);
                 b = site_collide(cfg, fin, fsl, fpl, &ds, &dsi, &rho);
@@ -702,6 +830,10 @@ int orc_delta_s(const orc_config *cfg, const double *f_st, double *dS_field)
     int rc = 0;
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
+            if (boundary_node(cfg, i, j)) {  /* not collided: no nonequilibrium entropy */
+                dS_field[(long long)j * nx + i] = 0.0;
+                continue;
+            }
             pull(cfg, f_st, i, j, fin);
             rc |= site_collide(cfg, fin, fs, fp, &ds, &dsi, &rho);
             dS_field[(long long)j * nx + i] = ds;

@@ -41,6 +41,14 @@ extern "C" {
 #define ORC_BC_WALLS 0    /* D2Q9: cavity (three still walls, lid on top); D1Q3: closed tube ends */
 #define ORC_BC_PERIODIC 1 /* periodic in every direction */
 #define ORC_BC_CHANNEL 2  /* D2Q9: periodic in x, still wall at the bottom, lid on top */
+/* D2Q9 cavities whose outer ring of nodes lies on the walls (boundary nodes, Sec. 4.4):
+ * boundary nodes are not collided and not limited; after free flight the
+ * populations they lack (those that would come from outside the lattice) are
+ * supplied by the wall rule.  The lid is the top row without its two corners,
+ * moving with (u_lid, 0); the other walls and the four corners are at rest. */
+#define ORC_BC_NODE_WALLS 3 /* bounce-back: f_k = f_opp(k) + 6 W_k rho_wall (v_k . u_wall) (Sec. 4.4.1) */
+#define ORC_BC_DIFFUSIVE 4  /* diffusive Maxwell wall: f_k = gamma f*_k(1, u_wall) (Sec. 4.4.2);
+                               bounce-back in the corners */
 
 #define ORC_LIM_POSITIVITY 1u
 #define ORC_LIM_EHRENFEST 2u
