@@ -39,20 +39,30 @@ def parse():
     ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="cavity4096", choices=["cavity4096", "batched", "serve"],
-                    help="cavity4096: the 4096^2 cavity (default); batched: 256 cavities of sides "
+    ap.add_argument("--workload", default="cavity4096",
+                    choices=["cavity4096", "cavity100", "tube", "batched", "serve"],
+                    help="cavity4096: the 4096^2 cavity (default); cavity100: the 100^2 cavity at Re 5000; "
+                         "tube: the 800-site D1Q3 shock tube (FP64); batched: 256 cavities of sides "
                          "64..512; serve: Poisson-arriving solves through the continuous-batching server")
+    ap.add_argument("--graph", type=int, default=0,
+                    help="single lattices: CUDA-graph replay of runs of this many steps (even; 0 = off)")
+    ap.add_argument("--state", default="developed", choices=["developed", "active"],
+                    help="developed: the flow after --develop steps from rest; active: every site "
+                         "out of equilibrium (limiters act widely)")
+    ap.add_argument("--tube-sites", type=int, default=800, help="tube: lattice sites")
     ap.add_argument("--requests", type=int, default=200, help="serve: requests in the trace")
-    ap.add_argument("--develop", type=int, default=500,
-                    help="untimed steps before warm-up so the flow has left the rest state")
+    ap.add_argument("--develop", type=int, default=-1,
+                    help="untimed steps before warm-up so the flow has left the rest state "
+                         "(default: the 4096^2 cavity's full 1e4 steps; 0 for the small workloads)")
     ap.add_argument("--kernel", default="auto", choices=["auto", "tiled", "fused"])
     ap.add_argument("--limiters", default="median+ehrenfest",
                     choices=["median+ehrenfest", "smooth+ehrenfest", "threshold+ehrenfest"],
                     help="smooth / threshold: the ensemble-dependent limiters (tiled kernel, E(dS) reduction first)")
     ap.add_argument("--equilibrium", default="polynomial", choices=["polynomial", "entropic"],
                     help="entropic: Eq. maxwellian f* with the exact dS of Eq. DelS (needs --precision fp64)")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16", "fp64"],
-                    help="population storage (arithmetic is FP32 in all three)")
+    ap.add_argument("--precision", default=None, choices=["fp32", "bf16", "fp16", "fp64"],
+                    help="population storage (FP32 arithmetic for the 32- and 16-bit forms); default "
+                         "fp32, fp64 for the shock tube")
     ap.add_argument("--side", type=int, default=4096,
                     help="cavity side (4096 is the workload; smaller sides are for profiling)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -71,21 +81,27 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi samples (200 ms) taken while the timed region runs."""
+    """nvidia-smi samples of the SM clock, power and throttle reasons, every 50 ms,
+    while the GPU is busy.  The sampler runs from the first untimed step (the flow's
+    development and the warm-up) to the end of the timed region, so that a timed
+    region of a few milliseconds still has a clock record of the load it sits in;
+    `in_timed` counts the samples taken inside the timed region itself."""
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    INTERVAL_MS = 50
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
         self.lines = []
+        self.t_timed = None
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
-                 "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                 "-lms", str(self.INTERVAL_MS), "-i", str(self.gpu)], stdout=subprocess.PIPE,
                 stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -94,20 +110,29 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def timed_begin(self):
+        self.t_timed = (time.perf_counter(), None)
+
+    def timed_end(self):
+        if self.t_timed is not None:
+            self.t_timed = (self.t_timed[0], time.perf_counter())
 
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        time.sleep(2 * self.INTERVAL_MS / 1e3)  # the sample that covers the region's end
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
         self.thread.join(timeout=2)
-        sm, smax, power, reasons = [], [], [], set()
+        sm, smax, power, reasons, inside = [], [], [], set(), 0
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        t0, t1 = self.t_timed if self.t_timed else (None, None)
+        for ts, ln in self.lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -117,13 +142,17 @@ class ClockSampler:
                 power.append(float(parts[3]))
             except ValueError:
                 continue
+            if t0 is not None and t1 is not None and t0 <= ts <= t1 + self.INTERVAL_MS / 1e3:
+                inside += 1
             for nm, val in zip(names, parts[5:9]):
                 if val.lower().startswith("active"):
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
                 "power_w_max": max(power) if power else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "in_timed": inside,
+                "interval_ms": self.INTERVAL_MS,
+                "window": "development + warm-up + timed steps (GPU busy throughout)"}
 
 
 # The sources each step kernel is compiled from (its .cu file and every header
@@ -206,7 +235,12 @@ def whole_job_mlups(world: int, sites: int, steps: int, elapsed_s: float) -> flo
     return world * sites * steps / elapsed_s / 1e6
 
 
-TIMING_EVERY = 8  # the step and tail kernels are timed with CUDA events on one step in 8
+def timing_every(steps: int) -> int:
+    """The step and tail kernels are timed with CUDA events on one step in this
+    many: events between two kernels delay the next launch by a few microseconds,
+    so long runs sample one step in 8, short ones (a few dozen steps) every second
+    step so that the kernel average still rests on several launches."""
+    return 2 if steps < 200 else 8
 
 
 def workload(side: int = 4096):
@@ -407,8 +441,46 @@ def run_serve(args):
                       "runs": out_runs}), flush=True)
 
 
+def single_workload(args, lbm, inputs):
+    """(workload, lattice kwargs, lattice kind, storage) of the single-lattice lines."""
+    if args.workload == "tube":
+        # the 1:2 shock tube of Sec. 4.3: 800 sites, nu = 1e-9, Ehrenfests' delta = 1e-3, k = 4, FP64
+        w = inputs.shock_tube_workload(args.tube_sites)
+        prec = args.precision or "fp64"
+        kw = dict(lattice=lbm.D1Q3, nx=w.nx, ny=1, boundary=lbm.BC_WALLS,
+                  precision={"fp32": lbm.FP32, "fp64": lbm.FP64}[prec], beta=w.beta, limiters=w.limiters,
+                  delta_ehrenfest=w.delta_ehrenfest, k_max=w.k_max)
+        return w, kw, "d1q3", prec
+    if args.workload == "cavity100":
+        # the 100 x 100 cavity at Re = 5000 (lid 0.1), median filter, FP32
+        w = inputs.cavity100_workload()
+        kw = lattice_kwargs(w, args.kernel, args.precision, args.equilibrium)
+        kw["rho_ref"] = w.rho0
+        kw["boundary"] = w.boundary  # boundary nodes on the walls (tiled kernel)
+        return w, kw, "d2q9", args.precision
+    w = workload(args.side)
+    if args.limiters != "median+ehrenfest":
+        # Eq. smooth1 with k = 1/2, delta = 0.01, or the threshold filter with dS_t = 10 E(dS)
+        w.limiters = (lbm.LIM_SMOOTH if args.limiters.startswith("smooth") else lbm.LIM_THRESHOLD) | lbm.LIM_EHRENFEST
+        w.name = w.name + "_" + args.limiters.split("+")[0]
+    if args.equilibrium == "entropic":
+        if args.precision != "fp64":
+            raise SystemExit("--equilibrium entropic needs --precision fp64")
+        w.name = w.name.replace("cavity_d2q9", "cavity_d2q9_entropic")
+    return w, lattice_kwargs(w, args.kernel, args.precision, args.equilibrium), "d2q9", args.precision
+
+
+def initial_fields(w, inputs):
+    if w.lattice == 1:
+        rho, ux = inputs.shock_tube(w.nx, 1.0, w.rho_right)
+        return rho, ux, None
+    return inputs.cavity_rest(w.nx, w.ny, w.rho0)
+
+
 def main():
     args = parse()
+    if args.precision is None:
+        args.precision = "fp64" if args.workload == "tube" else "fp32"
     if args.impl == "reference":
         run_reference(args)
         return
@@ -438,39 +510,47 @@ def main():
         dist.barrier()
     lbm.lib()
 
-    w = workload(args.side)
-    if args.limiters != "median+ehrenfest":
-        # Eq. smooth1 with k = 1/2, delta = 0.01, or the threshold filter with dS_t = 10 E(dS)
-        w.limiters = (lbm.LIM_SMOOTH if args.limiters.startswith("smooth") else lbm.LIM_THRESHOLD) | lbm.LIM_EHRENFEST
-        w.name = w.name + "_" + args.limiters.split("+")[0]
+    w, kw, lat_kind, prec = single_workload(args, lbm, inputs)
     entropic = args.equilibrium == "entropic"
-    if entropic:
-        if args.precision != "fp64":
-            raise SystemExit("--equilibrium entropic needs --precision fp64")
-        w.name = w.name.replace("cavity_d2q9", "cavity_d2q9_entropic")
-    lat = lbm.Lattice(**lattice_kwargs(w, args.kernel, args.precision, args.equilibrium))
-    rho, ux, uy = inputs.cavity_rest(w.nx, w.ny, w.rho0)
-    lat.init(rho, ux, uy)
-    lat.step(args.develop + args.warmup)
+    develop = args.develop if args.develop >= 0 else (10000 if args.workload == "cavity4096" else 0)
+    lat = lbm.Lattice(**kw)
+    if args.graph:
+        lat.set_graph(args.graph)
+    fields = initial_fields(w, inputs)
+    sampler = ClockSampler(local)
+    sampler.start()
+    lat.init(*fields)
+    if args.state == "active":
+        # every site out of equilibrium: seeded random deviations of the rest state
+        # (W_k (1 + 0.05 U(-1, 1))), so that the median filter forms its stencil and
+        # Ehrenfests' candidates outnumber k at many sites in every timed step
+        wts = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4) if lat_kind == "d2q9" else np.array([2 / 3, 1 / 6, 1 / 6])
+        f_act = inputs.random_populations(704, len(wts), w.ny, w.nx, w.rho0 * wts, 0.05)
+        lat.set_populations(f_act)
+        develop = 0
+    lat.step(develop + args.warmup)
     lat.synchronize()
 
     stream = torch.cuda.current_stream()
-    sampler = ClockSampler(local)
-    sampler.start()
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
     launches0 = lat.launch_count()
-    # per-kernel events on one step in TIMING_EVERY (events between the kernels
-    # delay the next launch, so timing every step would slow the measured run)
-    lat.timing(True, every=TIMING_EVERY)
+    every = timing_every(args.steps)
+    # per-kernel events on one step in `every` (events between the kernels delay
+    # the next launch, so timing every step would slow the measured run); graph
+    # replay is off while they are recorded, so the graph line times the steps alone
+    if not args.graph:
+        lat.timing(True, every=every)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler.timed_begin()
     ev0.record(stream)
     lat.step(args.steps)
     ev1.record(stream)
     torch.cuda.synchronize()
+    sampler.timed_end()
     launches = lat.launch_count() - launches0
-    step_ms, tail_ms, timed = lat.timing_read()
+    step_ms, tail_ms, timed = lat.timing_read() if not args.graph else (0.0, 0.0, 0)
     lat.timing(False)
     clocks = sampler.stop()
     elapsed = ev0.elapsed_time(ev1) / 1e3
@@ -479,22 +559,28 @@ def main():
     mlups = whole_job_mlups(world, w.sites, args.steps, elapsed)
 
     # roofline of the step kernel (the dominant launch): algorithmic bytes / event time
-    bps = BYTES_PER_SITE[("d2q9", args.precision)]
-    ensemble = args.limiters != "median+ehrenfest"
+    bps = BYTES_PER_SITE[(lat_kind, prec)]
+    ensemble = args.limiters != "median+ehrenfest" and args.workload == "cavity4096"
     if ensemble:
         # the pass first reads every population once more for E(dS) (k_ens_partial);
         # the library's events bracket that reduction and the step kernel together
         bps += bps // 2
-    kern_s = step_ms / 1e3 / max(timed, 1)
+    if timed:
+        kern_s = step_ms / 1e3 / timed
+    else:  # graph replay: the whole step (step kernel + tail) from the run's own events
+        kern_s = elapsed / args.steps
     achieved = bps * w.sites / kern_s / 1e9
     peak, peak_kind = peaks()
     kname = "fused" if lat.step_kernel() == lbm.KERNEL_FUSED else "tiled"
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_kind": peak_kind,
-            "traffic": traffic_from_profile(f"{kname}_{args.precision}", w.sites),
-            "kernel": kname, "kernel_ms": kern_s * 1e3, "tail_kernel_ms": tail_ms / max(timed, 1),
-            "timed_launches": timed, "timed_every": TIMING_EVERY,
+            "traffic": traffic_from_profile(f"{kname}_{prec}", w.sites) if lat_kind == "d2q9" else None,
+            "kernel": kname if timed else "whole step (graph replay)", "kernel_ms": kern_s * 1e3,
+            "tail_kernel_ms": tail_ms / max(timed, 1), "timed_launches": timed, "timed_every": every,
             "bytes_per_site": bps}
+    if w.sites * bps < 100e6:
+        roof["note"] = ("the lattice lives in L2 (%.1f MB of populations); the step is launch- and "
+                        "latency-bound, so this fraction is no HBM claim" % (w.sites * bps / 1e6))
     if ensemble:
         roof["kernel"] = "k_ens_partial + k_ens_mean + k_tiled"
         roof["traffic"] = traffic_from_profile("tiled_fp32_ensemble", w.sites)
@@ -517,29 +603,43 @@ def main():
                 "traffic": traffic_from_profile("tiled_fp64_entropic", w.sites), "kernel": kname,
                 "kernel_ms": kern_s * 1e3,
                 "tail_kernel_ms": roof_hbm["tail_kernel_ms"], "timed_launches": timed,
-                "timed_every": TIMING_EVERY, "hbm": {k: roof_hbm[k] for k in ("achieved", "peak", "frac", "bytes_per_site")}}
+                "timed_every": every, "hbm": {k: roof_hbm[k] for k in ("achieved", "peak", "frac", "bytes_per_site")}}
 
     e2e = None
     if not args.no_e2e:
-        e2e = end_to_end(lat, w, args.steps, torch)
+        e2e = end_to_end(lat, w, args.steps, torch, fields)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(w, 1, args.equilibrium)
+        cpu = cpu_baseline_for(args, w, kw)
+    if args.workload == "cavity4096":
+        cfg = {"workload": w.name, "nx": w.nx, "ny": w.ny, "reynolds": 7500,
+               "u_lid": w.u_lid, "beta": w.beta, "limiters": args.limiters,
+               "delta": 1e-3, "k_max": w.k_max, "storage": prec, "sums": "fp64",
+               "equilibrium": args.equilibrium}
+    elif args.workload == "cavity100":
+        cfg = {"workload": w.name, "nx": w.nx, "ny": w.ny, "reynolds": 5000, "u_lid": w.u_lid,
+               "rho0": w.rho0, "beta": w.beta, "walls": "boundary nodes on the walls, bounce-back",
+               "limiters": "median", "delta": w.delta_median,
+               "storage": prec, "sums": "fp64", "equilibrium": args.equilibrium}
+    else:
+        cfg = {"workload": w.name if w.nx == 800 else f"shock_tube_d1q3_{w.nx}", "sites": w.nx,
+               "density_ratio": "1:2", "nu": 1e-9, "beta": w.beta, "limiters": "ehrenfest",
+               "delta": w.delta_ehrenfest, "k_max": w.k_max, "storage": prec}
+    cfg.update({"kernel": kname, "develop_steps": develop, "state": args.state,
+                "graph_steps": args.graph,
+                "l2": ("inputs larger than L2 (%.2f GB population buffers vs 129 MB L2)" % (w.sites * bps / 2 / 1e9)
+                       if w.sites * bps / 2 > 129e6 else
+                       "lattice resident in L2 (%.2f MB of populations); no flush: the workload itself is that small"
+                       % (w.sites * bps / 1e6)),
+                "parallelism": f"replicas{world}" if world > 1 else "single"})
     out = {"metric": "limited-LBM MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": elapsed * 1e3 / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
-           "data": "synthetic",
-           "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "reynolds": 7500,
-                      "u_lid": w.u_lid, "beta": w.beta, "limiters": args.limiters,
-                      "delta": 1e-3, "k_max": w.k_max, "storage": args.precision, "sums": "fp64",
-                      "equilibrium": args.equilibrium,
-                      "kernel": kname, "develop_steps": args.develop,
-                      "l2": f"inputs larger than L2 ({9 * w.sites * (8 if args.precision == 'fp64' else 4 if args.precision == 'fp32' else 2) / 1e9:.1f} GB population buffers vs 129 MB L2)",
-                      "parallelism": f"replicas{world}" if world > 1 else "single"},
+           "ms_per_step": elapsed * 1e3 / args.steps, "us_per_step": elapsed * 1e6 / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64" if prec == "fp64" else "f32", "data": "synthetic", "config": cfg,
            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
            "clocks": clocks,
-           "last_step_stats": {k: st[k] for k in ("step", "mass", "sum_dS", "dS_lim", "n_med",
+           "last_step_stats": {k: st[k] for k in ("step", "mass", "sum_dS", "dS_lim", "n_pos", "n_med",
                                                    "n_ehr", "n_cand")}}
     if rank == 0:
         print(json.dumps(out), flush=True)
@@ -549,14 +649,32 @@ def main():
         dist.destroy_process_group()
 
 
-def end_to_end(lat, w, steps, torch):
+def cpu_baseline_for(args, w, kw):
+    """The oracle as it stands, one thread, on a bounded sample of the workload."""
+    import oracle
+    from paper_0704_0043_gb300 import inputs
+    if args.workload == "cavity4096":
+        return cpu_baseline(w, 1, args.equilibrium)
+    oc = oracle.Config(lattice=kw["lattice"], nx=w.nx, ny=w.ny, boundary=kw.get("boundary", 0), beta=w.beta,
+                       u_lid=w.u_lid, rho_wall=w.rho0, limiters=w.limiters, delta_median=w.delta_median,
+                       delta_ehrenfest=w.delta_ehrenfest, k_max=w.k_max)
+    f = oracle.init(oc, *initial_fields(w, inputs))
+    steps = 400 if args.workload == "tube" else 1000
+    t0 = time.perf_counter()
+    f, _, _ = oracle.run(oc, f, steps)
+    dt = time.perf_counter() - t0
+    return {"value": w.sites * steps / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"{steps} steps of the full workload ({w.nx}x{w.ny}), FP64, one thread, {dt:.2f} s"}
+
+
+def end_to_end(lat, w, steps, torch, fields):
     """Same metric through the public API with pinned host buffers: upload the
     initial density/velocity fields, run `steps` steps, read the moments and
     the stats back; the copies are inside the timed region."""
     import numpy as np
-    from paper_0704_0043_gb300 import inputs
-    rho, ux, uy = inputs.cavity_rest(w.nx, w.ny, w.rho0)
-    hin = [torch.from_numpy(a.reshape(-1).copy()).pin_memory() for a in (rho, ux, uy)]
+    rho, ux, uy = fields
+    hin = [torch.from_numpy(a.reshape(-1).copy()).pin_memory() for a in (rho, ux, uy) if a is not None]
+    nout = 3 if uy is not None else 2
     hout = [torch.empty(w.sites, dtype=torch.float64).pin_memory() for _ in range(3)]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -566,8 +684,8 @@ def end_to_end(lat, w, steps, torch):
     st = lat.stats()
     dt = time.perf_counter() - t0
     assert np.isfinite(st["mass"])
-    h2d = 3 * 8 * w.sites
-    d2h = 3 * 8 * w.sites + 96
+    h2d = len(hin) * 8 * w.sites
+    d2h = nout * 8 * w.sites + 96
     return {"value": w.sites * steps / dt / 1e6, "unit": "MLUPS",
             "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": d2h / steps,
             "request": f"init from host rho/u, {steps} steps, moments + stats to host"}

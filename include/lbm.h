@@ -50,7 +50,8 @@ typedef enum {
     LBM_ERR_OOM = 2,         /* device allocation failed */
     LBM_ERR_CUDA = 3,        /* a CUDA runtime call failed (message names it) */
     LBM_ERR_NONFINITE = 4,   /* a site had rho <= 0, f*_k <= 0 or a nonfinite value */
-    LBM_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+    LBM_ERR_TIMEOUT = 5,     /* reserved for a bounded device-side wait that gives up; no kernel of
+                                this library waits on another, so no call returns it today */
     LBM_ERR_STATE = 6        /* call out of order (e.g. step before init) */
 } lbm_status;
 
@@ -65,9 +66,26 @@ enum { LBM_D1Q3 = 1, LBM_D2Q9 = 2 };
 enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_BF16 = 2, LBM_FP16 = 3 };
 
 enum {
-    LBM_BC_WALLS = 0,    /* D2Q9: still walls left, right, bottom, lid on top; D1Q3: closed ends */
+    LBM_BC_WALLS = 0,    /* D2Q9: still walls left, right, bottom, lid on top, half a link outside
+                            the lattice (halfway bounce-back); D1Q3: closed ends */
     LBM_BC_PERIODIC = 1, /* periodic in every direction */
-    LBM_BC_CHANNEL = 2   /* D2Q9: periodic in x, still bottom wall, lid on top */
+    LBM_BC_CHANNEL = 2,  /* D2Q9: periodic in x, still bottom wall, lid on top */
+    /* D2Q9 cavities whose outer ring of nodes lies on the walls (boundary nodes,
+     * Sec. 4.4).  Boundary nodes are not collided and not limited, their dS is 0,
+     * and the median filter's stencils stay on the other nodes (a node next to one
+     * wall: itself and its two neighbours along it; next to two walls: itself and
+     * its inward x and y neighbours).  After free flight a boundary node receives
+     * the populations it lacks (sources outside the lattice) from the wall rule.
+     * The lid is the top row without its two corners and moves with (u_lid, 0);
+     * the other walls and the corners are at rest.  The stats' mass counts, at a
+     * boundary node, the populations that stream back onto the lattice.  The
+     * fused kernel does not take these boundaries (LBM_KERNEL_AUTO picks the
+     * tiled kernel). */
+    LBM_BC_NODE_WALLS = 3, /* bounce-back: f_k = f_opp(k) + 6 W_k rho_wall (v_k . u_wall) (Sec. 4.4.1) */
+    LBM_BC_DIFFUSIVE = 4   /* diffusive Maxwell wall (Sec. 4.4.2): f_k = gamma f*_k(1, u_wall) with
+                              gamma = sum of the arrived f_opp(k) / sum of f*_k(1, u_wall) over the
+                              returned directions (f* of the configured kind); bounce-back in the
+                              corners */
 };
 
 /* Limiters (bit set).  LBM_LIM_SMOOTH and LBM_LIM_THRESHOLD are ensemble-dependent: they
@@ -226,6 +244,16 @@ int64_t lbm_device_bytes(const lbm_ctx *ctx);
 
 /* Device bytes lbm_create would allocate for cfg (0 if cfg is invalid). */
 int64_t lbm_footprint_bytes(const lbm_config *cfg);
+
+/* CUDA-graph replay for lbm_step: runs of `steps_per_graph` steps (an even
+ * number >= 2; 0 turns replay off) are captured once per starting buffer into a
+ * CUDA graph on a stream of the context's own and replayed on the context's
+ * stream, which removes the per-launch host cost of small lattices.  The steps
+ * and their results are those of plain lbm_step calls.  While per-kernel timing
+ * (lbm_timing) is on, lbm_step launches plainly.  The first replay of each
+ * starting buffer captures its graph; make it before any stream capture of the
+ * caller's own.  Errors: LBM_ERR_INVALID_ARG (odd count or 1). */
+lbm_status lbm_set_graph(lbm_ctx *ctx, int32_t steps_per_graph);
 
 /* Per-kernel timing with CUDA events recorded on the context's stream.  While
  * enabled, a timed step records an event before its step kernel, one between

@@ -41,7 +41,7 @@ template <int Q, typename S>
 __device__ void pull_dev(const FinalParams &p, int x, int y, float g[Q])
 {
     const S *src = (const S *)p.src;
-    const bool wrapx = p.boundary != 0, wrapy = Q == 9 && p.boundary == 1;
+    const bool wrapx = bc_wrap_x(p.boundary), wrapy = Q == 9 && bc_wrap_y(p.boundary);
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
         if (!p.collide) {

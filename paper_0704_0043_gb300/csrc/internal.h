@@ -21,6 +21,12 @@ constexpr int kLead = 32;
 constexpr int kTail = 96;
 __host__ __device__ inline int row_pitch(int nx) { return ((nx + 31) / 32) * 32 + kLead + kTail; }
 
+// Boundary kinds (LBM_BC_*): which directions wrap, and whether the outer
+// ring of nodes lies on the walls.
+__host__ __device__ inline bool bc_wrap_x(int b) { return b == 1 || b == 2; }
+__host__ __device__ inline bool bc_wrap_y(int b) { return b == 1; }
+__host__ __device__ inline bool bc_node_walls(int b) { return b == 3 || b == 4; }
+
 // Sticky device status bits.
 enum : unsigned { kStatNonfinite = 1u, kStatTimeout = 2u, kStatCandOverflow = 4u };
 
@@ -71,6 +77,7 @@ struct StepParams {
     int eq;                    // 0: polynomial f*, quadratic dS; 1: entropic f*, exact dS (FP64 storage)
     double a;                  // 2 beta - 1
     double delta_m, delta_e;
+    double u_lid;              // lid x-velocity (wall rule of LBM_BC_DIFFUSIVE)
     double lid[9];             // ((6 W_k) rho_wall) (c_kx u_lid), added on links through the lid
     // the same term for FP32 arithmetic as an unevaluated sum hi + lo: adding
     // both parts keeps the rounding of the constant out of every wall step
@@ -235,10 +242,25 @@ struct lbm_ctx {
     size_t events_used = 0;
     long long launches = 0;
     int64_t device_bytes = 0;
+    // CUDA-graph replay of runs of graph_steps steps (0: off): one graph per
+    // starting buffer, captured on gstream (the context's own stream may be
+    // the legacy default stream, which cannot be captured)
+    int graph_steps = 0;
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t gev = nullptr;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    long long graph_launches = 0;  // kernel launches one replay performs
     std::string err;
 };
 
 namespace lbm {
+// Geometry and physics of a step for configuration g, stored with row pitch
+// `pitch` and `plane` elements per population plane; every scratch pointer is
+// left null for the caller to fill.
+StepParams cfg_step_params(const lbm_config &g, int q, int pitch, long long plane, int collide, unsigned limiters);
+// The tail's parameters that follow from g and from the step's p (scratch
+// pointers null).
+FinalParams cfg_final_params(const lbm_config &g, const StepParams &p, int collide, unsigned limiters, int nblocks);
 // Per-step parameters of a context (collide = 0 for a limiter pass).
 StepParams ctx_step_params(lbm_ctx *c, int collide, unsigned limiters);
 FinalParams ctx_final_params(lbm_ctx *c, int collide, unsigned limiters, int nblocks);

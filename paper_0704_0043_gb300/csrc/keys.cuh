@@ -27,7 +27,7 @@ struct KeyGeom {
 template <typename S>
 __device__ double pull_one_f64(const KeyGeom &p, const S *src, int x, int y, int k)
 {
-    const bool wrapx = p.boundary != 0, wrapy = p.boundary == 1;
+    const bool wrapx = bc_wrap_x(p.boundary), wrapy = bc_wrap_y(p.boundary);
     int sx = x - Lat<9>::cx(k), sy = y - Lat<9>::cy(k);
     if (wrapx) sx = sx < 0 ? sx + p.nx : (sx >= p.nx ? sx - p.nx : sx);
     if (wrapy) sy = sy < 0 ? sy + p.ny : (sy >= p.ny ? sy - p.ny : sy);

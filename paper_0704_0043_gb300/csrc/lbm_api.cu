@@ -87,8 +87,10 @@ std::string validate(const lbm_config *c)
             return "D1Q3 boundary must be LBM_BC_WALLS or LBM_BC_PERIODIC";
         if (c->boundary == LBM_BC_WALLS && c->nx < 3) return "D1Q3 with closed ends needs nx >= 3";
     } else {
-        if (c->boundary < LBM_BC_WALLS || c->boundary > LBM_BC_CHANNEL) return "unknown boundary kind";
+        if (c->boundary < LBM_BC_WALLS || c->boundary > LBM_BC_DIFFUSIVE) return "unknown boundary kind";
         if (c->boundary == LBM_BC_WALLS && (c->nx < 2 || c->ny < 2)) return "D2Q9 cavity needs nx, ny >= 2";
+        if (c->boundary >= LBM_BC_NODE_WALLS && (c->nx < 5 || c->ny < 5))
+            return "D2Q9 cavity with boundary nodes needs nx, ny >= 5";
         if (c->boundary == LBM_BC_CHANNEL && c->ny < 2) return "D2Q9 channel needs ny >= 2";
     }
     if (c->limiters & ~31u) return "unknown limiter bits";
@@ -190,63 +192,21 @@ lbm_status dev_in(lbm_ctx *c, const double *src, size_t count, size_t off, const
 
 StepParams step_params(lbm_ctx *c, int collide, unsigned limiters)
 {
-    const lbm_config &g = c->cfg;
-    StepParams p{};
-    p.nx = g.nx;
-    p.ny = g.ny;
-    p.pitch = c->pitch;
-    p.plane = c->plane;
-    p.boundary = g.boundary;
-    p.limiters = limiters;
-    p.median_mode = g.median_mode;
-    p.collide = collide;
-    p.eq = g.equilibrium == LBM_EQ_ENTROPIC ? 1 : 0;
-    p.a = 2.0 * g.beta - 1.0;
-    p.delta_m = g.delta_median;
-    p.delta_e = g.delta_ehrenfest;
-    for (int k = 0; k < 9; ++k) {
-        const bool lid = c->q == 9 && g.boundary != LBM_BC_PERIODIC && Lat<9>::cy(k) == -1;
-        p.lid[k] = lid ? ((6.0 * Lat<9>::w(k)) * g.rho_wall) * ((double)Lat<9>::cx(k) * g.u_lid) : 0.0;
-        p.lidf[k] = (float)p.lid[k];
-        p.lidlo[k] = (float)(p.lid[k] - (double)p.lidf[k]);
-    }
-    p.rho_ref = (float)g.rho_ref;
-    for (int k = 0; k < 9; ++k) {
-        const double w = c->q == 9 ? Lat<9>::w(k) : (k < 3 ? Lat<3>::w(k) : 0.0);
-        p.rw[k] = g.rho_ref * w;
-        p.rwf[k] = (float)p.rw[k];
-    }
+    StepParams p = cfg_step_params(c->cfg, c->q, c->pitch, c->plane, collide, limiters);
     p.cand = c->cand;
     p.cand_count = c->counts;
     p.cand_cap = c->cand_cap;
     p.partials = c->partials;
     p.status = c->status;
     p.work = c->counts + 2;
-    p.ds_out = nullptr;
-    p.smooth_delta = g.smooth_delta;
-    p.smooth_k = g.smooth_k;
-    p.threshold_c = g.threshold_c;
-    p.threshold_delta = g.threshold_delta;
     p.ens = c->ens + 2 * kEnsBlocks;
     return p;
 }
 
 FinalParams final_params(lbm_ctx *c, int collide, unsigned limiters, int nblocks)
 {
-    const lbm_config &g = c->cfg;
-    FinalParams f{};
-    f.nblocks = nblocks;
-    const double a = 2.0 * g.beta - 1.0;
-    // entropic f*: the step kernel sums dS(f_in) - dS(f') itself (no quadratic identity)
-    f.one_minus_a2 = g.equilibrium == LBM_EQ_ENTROPIC ? 1.0 : 1.0 - a * a;
-    f.eq = g.equilibrium == LBM_EQ_ENTROPIC ? 1 : 0;
-    f.k_max = g.k_max;
-    f.ehrenfest = (limiters & LBM_LIM_EHRENFEST) ? 1 : 0;
-    f.collide = collide;
-    f.nx = g.nx;
-    f.ny = g.ny;
-    f.pitch = c->pitch;
-    f.plane = c->plane;
+    const StepParams p = step_params(c, collide, limiters);
+    FinalParams f = cfg_final_params(c->cfg, p, collide, limiters, nblocks);
     f.partials = c->partials;
     f.cand = c->cand;
     f.cand_count = c->counts;
@@ -258,18 +218,7 @@ FinalParams final_params(lbm_ctx *c, int collide, unsigned limiters, int nblocks
     f.stats_ring = c->ring;
     f.ring_len = c->ring_len;
     f.counters = c->counters;
-    const StepParams p = step_params(c, collide, limiters);
     f.src = c->buf[c->cur];
-    f.boundary = g.boundary;
-    f.a = p.a;
-    f.delta_e = p.delta_e;
-    for (int k = 0; k < 9; ++k) {
-        f.lid[k] = p.lid[k];
-        f.lidf[k] = p.lidf[k];
-        f.lidlo[k] = p.lidlo[k];
-        f.rw[k] = p.rw[k];
-    }
-    f.rho_ref = p.rho_ref;
     return f;
 }
 
@@ -362,8 +311,58 @@ lbm_status reset_counters(lbm_ctx *c)
     return LBM_OK;
 }
 
+void drop_graphs(lbm_ctx *c)
+{
+    for (int k = 0; k < 2; ++k) {
+        if (c->gexec[k]) cudaGraphExecDestroy(c->gexec[k]);
+        c->gexec[k] = nullptr;
+    }
+}
+
+// Captures graph_steps passes starting from buffer c->cur into c->gexec[c->cur]
+// (the kernels record the buffers they read and write, so a graph is valid for
+// one starting buffer; an even step count leaves the context where it began).
+lbm_status capture_graph(lbm_ctx *c)
+{
+    if (!c->gstream) {
+        CK(c, cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
+        CK(c, cudaEventCreateWithFlags(&c->gev, cudaEventDisableTiming));
+    }
+    const int start = c->cur;
+    cudaStream_t user = c->stream;
+    c->stream = c->gstream;
+    cudaGraph_t g = nullptr;
+    const long long launches = c->launches;
+    cudaError_t e = cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal);
+    lbm_status s = LBM_OK;
+    if (e == cudaSuccess) {
+        for (int i = 0; i < c->graph_steps && s == LBM_OK; ++i) s = run_pass(c, 1, c->cfg.limiters);
+        const cudaError_t ee = cudaStreamEndCapture(c->gstream, &g);
+        if (e == cudaSuccess) e = ee;
+    }
+    c->stream = user;
+    c->cur = start;
+    c->graph_launches = c->launches - launches;
+    c->launches = launches;
+    if (s != LBM_OK || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return s != LBM_OK ? s : cuda_fail(c, e, "graph capture of the step");
+    }
+    e = cudaGraphInstantiate(&c->gexec[start], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        c->gexec[start] = nullptr;
+        return cuda_fail(c, e, "cudaGraphInstantiate");
+    }
+    return LBM_OK;
+}
+
 void free_all(lbm_ctx *c)
 {
+    drop_graphs(c);
+    if (c->gev) cudaEventDestroy(c->gev);
+    if (c->gstream) cudaStreamDestroy(c->gstream);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     c->events.clear();
     void *ptrs[] = {c->buf[0], c->buf[1], c->cand, c->counts, c->sel, c->partials,
@@ -391,6 +390,71 @@ void to_public(const DevStats &d, lbm_step_stats *o)
 }  // namespace
 
 namespace lbm {
+StepParams cfg_step_params(const lbm_config &g, int q, int pitch, long long plane, int collide, unsigned limiters)
+{
+    StepParams p{};
+    p.nx = g.nx;
+    p.ny = g.ny;
+    p.pitch = pitch;
+    p.plane = plane;
+    p.boundary = g.boundary;
+    p.limiters = limiters;
+    p.median_mode = g.median_mode;
+    p.collide = collide;
+    p.eq = g.equilibrium == LBM_EQ_ENTROPIC ? 1 : 0;
+    p.a = 2.0 * g.beta - 1.0;
+    p.delta_m = g.delta_median;
+    p.delta_e = g.delta_ehrenfest;
+    p.u_lid = g.u_lid;
+    for (int k = 0; k < 9; ++k) {
+        const bool lid = q == 9 && g.boundary != LBM_BC_PERIODIC && Lat<9>::cy(k) == -1;
+        p.lid[k] = lid ? ((6.0 * Lat<9>::w(k)) * g.rho_wall) * ((double)Lat<9>::cx(k) * g.u_lid) : 0.0;
+        p.lidf[k] = (float)p.lid[k];
+        p.lidlo[k] = (float)(p.lid[k] - (double)p.lidf[k]);
+    }
+    p.rho_ref = (float)g.rho_ref;
+    for (int k = 0; k < 9; ++k) {
+        // offsets of the deviation storage (FP32 / BF16 / FP16); FP64 storage holds f
+        // itself and never reads them
+        const double w = q == 9 ? Lat<9>::w(k) : (k < 3 ? Lat<3>::w(k) : 0.0);
+        p.rw[k] = g.rho_ref * w;
+        p.rwf[k] = (float)p.rw[k];
+    }
+    p.ds_out = nullptr;
+    p.smooth_delta = g.smooth_delta;
+    p.smooth_k = g.smooth_k;
+    p.threshold_c = g.threshold_c;
+    p.threshold_delta = g.threshold_delta;
+    return p;
+}
+
+FinalParams cfg_final_params(const lbm_config &g, const StepParams &p, int collide, unsigned limiters, int nblocks)
+{
+    FinalParams f{};
+    f.nblocks = nblocks;
+    // entropic f*: the step kernel sums dS(f_in) - dS(f') itself (no quadratic identity)
+    f.one_minus_a2 = g.equilibrium == LBM_EQ_ENTROPIC ? 1.0 : 1.0 - p.a * p.a;
+    f.eq = p.eq;
+    f.k_max = g.k_max;
+    f.ehrenfest = (limiters & LBM_LIM_EHRENFEST) ? 1 : 0;
+    f.collide = collide;
+    f.nx = g.nx;
+    f.ny = g.ny;
+    f.pitch = p.pitch;
+    f.plane = p.plane;
+    f.boundary = g.boundary;
+    f.a = p.a;
+    f.delta_e = p.delta_e;
+    for (int k = 0; k < 9; ++k) {
+        f.lid[k] = p.lid[k];
+        f.lidf[k] = p.lidf[k];
+        f.lidlo[k] = p.lidlo[k];
+        f.rw[k] = p.rw[k];
+    }
+    f.rho_ref = p.rho_ref;
+    return f;
+}
+
 int set_thread_error_impl(int s, const char *msg)
 {
     g_err = msg;
@@ -533,7 +597,22 @@ lbm_status lbm_step(lbm_ctx *c, int64_t nsteps)
     if (!c) return fail(nullptr, LBM_ERR_INVALID_ARG, "ctx is NULL");
     if (nsteps < 0) return fail(c, LBM_ERR_INVALID_ARG, "nsteps must be >= 0");
     if (!c->ready) return fail(c, LBM_ERR_STATE, "lbm_step before lbm_init / lbm_set_populations");
-    for (int64_t i = 0; i < nsteps; ++i) {
+    int64_t left = nsteps;
+    // graph replay (not while per-kernel timing records its events)
+    const int gs = c->graph_steps;
+    while (gs > 0 && !c->timing && left >= gs) {
+        if (!c->gexec[c->cur]) {
+            // the kernels' one-time set-up happens outside the capture: one plain step first
+            lbm_status s = run_pass(c, 1, c->cfg.limiters);
+            if (s != LBM_OK) return s;
+            if (--left < gs) break;
+            if (!c->gexec[c->cur] && (s = capture_graph(c)) != LBM_OK) return s;
+        }
+        CK(c, cudaGraphLaunch(c->gexec[c->cur], c->stream));
+        c->launches += c->graph_launches;
+        left -= gs;
+    }
+    for (int64_t i = 0; i < left; ++i) {
         lbm_status s = run_pass(c, 1, c->cfg.limiters);
         if (s != LBM_OK) return s;
     }
@@ -724,6 +803,19 @@ lbm_status lbm_get_config(const lbm_ctx *c, lbm_config *out)
 {
     if (!c || !out) return fail(nullptr, LBM_ERR_INVALID_ARG, "NULL argument");
     *out = c->cfg;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_graph(lbm_ctx *c, int32_t steps_per_graph)
+{
+    if (!c) return fail(nullptr, LBM_ERR_INVALID_ARG, "ctx is NULL");
+    if (steps_per_graph < 0 || steps_per_graph == 1 || (steps_per_graph & 1))
+        return fail(c, LBM_ERR_INVALID_ARG, "steps_per_graph must be 0 or an even number >= 2");
+    if (steps_per_graph != c->graph_steps) {
+        CK(c, cudaStreamSynchronize(c->stream));
+        drop_graphs(c);
+    }
+    c->graph_steps = steps_per_graph;
     return LBM_OK;
 }
 

@@ -10,7 +10,9 @@
 // and takes every scratch buffer (block partial sums, Ehrenfests' candidates,
 // the selected sites, counters, status and the stats record) from one
 // file-scope static device array of fixed size.
+#include <cstdint>
 #include <cstring>
+#include <string>
 
 #include "../../include/lbm.h"
 #include "internal.h"
@@ -57,13 +59,33 @@ Layout layout_for(long long sites, int rows, long long k_max, bool ehrenfest)
     return L;
 }
 
+// A device array of `bytes` bytes on the current device (device or managed
+// memory): the kernels below dereference these pointers, so a host address or
+// another GPU's memory is rejected before anything is launched.
+bool on_current_device(const void *ptr, int dev)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
+}
+
+lbm_status cuda_error(cudaError_t e, const char *what)
+{
+    static thread_local std::string msg;
+    msg = std::string("lbm_step_noalloc: ") + what + " failed: " + cudaGetErrorString(e);
+    cudaGetLastError();
+    return set_thread_error(e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA, msg.c_str());
+}
+
 }  // namespace
 
 extern "C" lbm_status lbm_step_noalloc(const lbm_config *cfg, const double *f_in, double *f_out,
                                        lbm_step_stats *stats, void *cuda_stream)
 {
-    if (!cfg || !f_in || !f_out || f_in == f_out)
-        return set_thread_error(LBM_ERR_INVALID_ARG, "lbm_step_noalloc: NULL or aliased arrays");
+    if (!cfg || !f_in || !f_out) return set_thread_error(LBM_ERR_INVALID_ARG, "lbm_step_noalloc: NULL argument");
     if (cfg->precision != LBM_FP64)
         return set_thread_error(LBM_ERR_INVALID_ARG, "lbm_step_noalloc: needs precision LBM_FP64");
     if (lbm_footprint_bytes(cfg) == 0) return LBM_ERR_INVALID_ARG;  // validates cfg, message already set
@@ -74,80 +96,69 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_config *cfg, const double *f_in
         return set_thread_error(LBM_ERR_INVALID_ARG,
                                 "lbm_step_noalloc: nx * ny exceeds LBM_NOALLOC_MAX_SITES (262144 sites)");
     const int q = cfg->lattice == LBM_D1Q3 ? 3 : 9;
-    const int rows = cfg->lattice == LBM_D2Q9 ? ((cfg->nx + 29) / 30) * ((cfg->ny + 5) / 6) : (cfg->nx + 253) / 254;
+    // one row of block partial sums per tiled-kernel block (the launch below
+    // must use exactly this many)
+    const int rows = tiled_blocks_for(q, cfg->nx, cfg->ny);
     const bool ehr = (cfg->limiters & LBM_LIM_EHRENFEST) != 0;
     const Layout L = layout_for(sites, rows, cfg->k_max, ehr);
     if (L.total > kScratchBytes)
         return set_thread_error(LBM_ERR_INVALID_ARG,
                                 "lbm_step_noalloc: the scratch this lattice needs exceeds LBM_NOALLOC_SCRATCH_BYTES");
 
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices)
+        return set_thread_error(LBM_ERR_CUDA, "lbm_step_noalloc: device ordinal above the supported 64");
+    // Both arrays must be device memory of the current device, and the output
+    // must not overlap the input anywhere.
+    const size_t bytes = (size_t)q * (size_t)sites * sizeof(double);
+    if (!on_current_device(f_in, dev) || !on_current_device(f_out, dev) ||
+        !on_current_device((const char *)f_in + bytes - 1, dev) ||
+        !on_current_device((const char *)f_out + bytes - 1, dev))
+        return set_thread_error(LBM_ERR_INVALID_ARG,
+                                "lbm_step_noalloc: f_in and f_out must be device memory of the current device");
+    {
+        const uintptr_t a0 = (uintptr_t)f_in, b0 = (uintptr_t)f_out;
+        if (a0 < b0 + bytes && b0 < a0 + bytes)
+            return set_thread_error(LBM_ERR_INVALID_ARG, "lbm_step_noalloc: f_in and f_out overlap");
+    }
+
     // Set-up, once per device with that device current: the device address of
     // the static array (the host-side symbol is only a stand-in for it).
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
-        return set_thread_error(LBM_ERR_CUDA, "lbm_step_noalloc: no usable current device");
     if (!g_scratch_addr[dev]) {
         void *ptr = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-        if (e != cudaSuccess || !ptr) {
-            cudaGetLastError();
-            return set_thread_error(LBM_ERR_CUDA, "lbm_step_noalloc: cudaGetSymbolAddress failed");
-        }
+        e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || !ptr) return cuda_error(e, "cudaGetSymbolAddress");
         g_scratch_addr[dev] = (unsigned char *)ptr;
     }
     unsigned char *base = g_scratch_addr[dev];
     cudaStream_t s = (cudaStream_t)cuda_stream;
 
     // Everything that must start at zero: counters, status, candidate counts.
-    if (cudaMemsetAsync(base, 0, L.ring, s) != cudaSuccess) return LBM_ERR_CUDA;
+    if ((e = cudaMemsetAsync(base, 0, L.ring, s)) != cudaSuccess) return cuda_error(e, "cudaMemsetAsync");
 
     // The kernels address element (k, y, x) at k * plane + y * pitch + kLead + x;
     // the caller's arrays are unpadded (pitch nx, plane nx * ny), so they are
     // passed kLead elements early.  Only lattice sites are ever accessed.
-    StepParams p{};
-    p.nx = cfg->nx;
-    p.ny = cfg->ny;
-    p.pitch = cfg->nx;
-    p.plane = sites;
-    p.boundary = cfg->boundary;
-    p.limiters = cfg->limiters;
-    p.median_mode = cfg->median_mode;
-    p.collide = 1;
-    p.eq = cfg->equilibrium == LBM_EQ_ENTROPIC ? 1 : 0;
-    p.a = 2.0 * cfg->beta - 1.0;
-    p.delta_m = cfg->delta_median;
-    p.delta_e = cfg->delta_ehrenfest;
-    for (int k = 0; k < 9; ++k) {
-        const bool lid = q == 9 && cfg->boundary != LBM_BC_PERIODIC && Lat<9>::cy(k) == -1;
-        p.lid[k] = lid ? ((6.0 * Lat<9>::w(k)) * cfg->rho_wall) * ((double)Lat<9>::cx(k) * cfg->u_lid) : 0.0;
-        p.lidf[k] = (float)p.lid[k];
-        p.lidlo[k] = (float)(p.lid[k] - (double)p.lidf[k]);
-        p.rw[k] = 0.0;
-        p.rwf[k] = 0.0f;
-    }
-    p.rho_ref = (float)cfg->rho_ref;
+    StepParams p = cfg_step_params(*cfg, q, cfg->nx, sites, 1, cfg->limiters);
     p.cand = (Cand *)(base + L.cand);
     p.cand_count = (int *)(base + L.counts);
     p.cand_cap = ehr ? (int)sites : 1;
     p.partials = (double *)(base + L.partials);
     p.status = (unsigned *)(base + L.status);
-    p.ds_out = nullptr;
+    p.work = nullptr;
+    p.ens = nullptr;
     const double *src = f_in - kLead;
     double *dst = f_out - kLead;
     int nblocks = 0;
-    if (launch_tiled<double>(q, p, src, dst, &nblocks, s) != cudaSuccess) return LBM_ERR_CUDA;
+    if ((e = launch_tiled<double>(q, p, src, dst, &nblocks, s)) != cudaSuccess) return cuda_error(e, "step kernel launch");
+    if (nblocks != rows)
+        return set_thread_error(LBM_ERR_CUDA, "lbm_step_noalloc: block count differs from the scratch layout");
 
-    FinalParams f{};
-    f.nblocks = nblocks;
-    f.one_minus_a2 = p.eq ? 1.0 : 1.0 - p.a * p.a;  // entropic f*: the step sums dS(f_in) - dS(f')
-    f.eq = p.eq;
-    f.k_max = cfg->k_max;
-    f.ehrenfest = ehr ? 1 : 0;
-    f.collide = 1;
-    f.nx = cfg->nx;
-    f.ny = cfg->ny;
-    f.pitch = cfg->nx;
-    f.plane = sites;
+    FinalParams f = cfg_final_params(*cfg, p, 1, cfg->limiters, nblocks);
+    f.fixed = 0;
+    f.work = nullptr;
     f.partials = p.partials;
     f.cand = p.cand;
     f.cand_count = p.cand_count;
@@ -162,15 +173,15 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_config *cfg, const double *f_in
     f.stats_ring = (DevStats *)(base + L.ring);
     f.ring_len = 1;
     f.counters = (long long *)(base + L.counters);
-    f.rho_ref = p.rho_ref;
-    if (launch_finalize<double>(q, f, dst, s) != cudaSuccess) return LBM_ERR_CUDA;
+    f.src = src;
+    if ((e = launch_finalize<double>(q, f, dst, s)) != cudaSuccess) return cuda_error(e, "tail kernel launch");
 
     DevStats d{};
     unsigned status = 0;
-    if (cudaMemcpyAsync(&d, base + L.ring, sizeof(DevStats), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaMemcpyAsync(&status, base + L.status, sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
-        return LBM_ERR_CUDA;
+    if ((e = cudaMemcpyAsync(&d, base + L.ring, sizeof(DevStats), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&status, base + L.status, sizeof(unsigned), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return cuda_error(e, "cudaMemcpyAsync");
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_error(e, "cudaStreamSynchronize");
     if (stats) {
         std::memset(stats, 0, sizeof(*stats));
         stats->step = d.step;
@@ -185,7 +196,9 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_config *cfg, const double *f_in
         stats->n_bad = d.n_bad;
         stats->status = d.status;
     }
-    if (status & kStatNonfinite) return LBM_ERR_NONFINITE;
-    if (status & (kStatTimeout | kStatCandOverflow)) return LBM_ERR_CUDA;
+    if (status & kStatNonfinite)
+        return set_thread_error(LBM_ERR_NONFINITE, "lbm_step_noalloc: a site had rho <= 0, f*_k <= 0 or a nonfinite value");
+    if (status & kStatCandOverflow)
+        return set_thread_error(LBM_ERR_CUDA, "lbm_step_noalloc: Ehrenfests' candidate buffer overflowed");
     return LBM_OK;
 }

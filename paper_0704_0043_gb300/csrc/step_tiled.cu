@@ -50,8 +50,8 @@ template <int Q, typename S, typename T>
 __device__ __forceinline__ void pull(const StepParams &p, const S *__restrict__ f, int x, int y, T fin[Q])
 {
     using A = Ar<T>;
-    const bool wrapx = p.boundary != 0;
-    const bool wrapy = (Q == 9) && p.boundary == 1;
+    const bool wrapx = bc_wrap_x(p.boundary);
+    const bool wrapy = (Q == 9) && bc_wrap_y(p.boundary);
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
         int sx = x - Lat<Q>::cx(k), sy = y - Lat<Q>::cy(k);
@@ -72,6 +72,92 @@ __device__ __forceinline__ void pull(const StepParams &p, const S *__restrict__ 
     }
 }
 
+// Free flight and the wall rule at a boundary node (x, y) of a cavity whose
+// outer ring of nodes lies on the walls (LBM_BC_NODE_WALLS, LBM_BC_DIFFUSIVE;
+// Sec. 4.4): the populations whose source is on the lattice arrive; the others
+// are supplied by the wall.  The lid is the top row without its corners and
+// moves with (u_lid, 0); the other walls and the corners are at rest.
+//   bounce-back (Sec. 4.4.1): f_k = f_opp(k) + 6 W_k rho_wall (v_k . u_wall);
+//   diffusive (Sec. 4.4.2): f_k = gamma f*_k(1, u_wall), gamma = (sum of the
+//     arrived f_opp(k)) / (sum of f*_k(1, u_wall)) over the returned
+//     directions, evaluated in FP64 for every storage type; bounce-back in the
+//     corners.
+// A corner's two missing populations whose opposite is missing too point out
+// of the lattice again; they keep their stored values.  `mass` receives the
+// populations that stream back onto the lattice (FP64, k order).
+template <typename S, typename T>
+__device__ void wall_node(const StepParams &p, const S *__restrict__ f, int x, int y, T fin[9], double &mass)
+{
+    using A = Ar<T>;
+    bool known[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const int sx = x - Lat<9>::cx(k), sy = y - Lat<9>::cy(k);
+        known[k] = sx >= 0 && sx < p.nx && sy >= 0 && sy < p.ny;
+        fin[k] = known[k] ? load_as<S, T>(p, f[fidx(p.plane, p.pitch, k, sy, sx)], k) : T(0);
+    }
+    const bool corner = (x == 0 || x == p.nx - 1) && (y == 0 || y == p.ny - 1);
+    const bool lid = y == p.ny - 1 && !corner;
+    if (p.boundary == 4 && !corner) {
+        const double uw = lid ? p.u_lid : 0.0;
+        double fw[9];
+        feq_any<9>(p.eq, 1.0, uw, 0.0, fw);  // density is a linear factor of f*: take 1
+        double arrived = 0.0, returned = 0.0;
+#pragma unroll
+        for (int k = 0; k < 9; ++k)
+            if (!known[k]) {
+                const int o = Lat<9>::opp(k);
+                arrived = Ar<double>::add(arrived, load_as<S, double>(p, f[fidx(p.plane, p.pitch, o, y - Lat<9>::cy(o), x - Lat<9>::cx(o))], o));
+                returned = Ar<double>::add(returned, fw[k]);
+            }
+        const double gamma = Ar<double>::div(arrived, returned);
+#pragma unroll
+        for (int k = 0; k < 9; ++k)
+            if (!known[k]) {
+                const double v = Ar<double>::mul(gamma, fw[k]);
+                if constexpr (std::is_same<T, double>::value)
+                    fin[k] = v;
+                else
+                    fin[k] = (T)Ar<double>::sub(v, p.rw[k]);  // the deviation, rounded once
+            }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            if (known[k]) continue;
+            const int o = Lat<9>::opp(k);
+            if (known[o]) {
+                T v = fin[o];
+                if (lid) {
+                    if constexpr (std::is_same<T, double>::value)
+                        v = A::add(v, p.lid[k]);
+                    else
+                        v = A::add(A::add(v, p.lidf[k]), p.lidlo[k]);
+                }
+                fin[k] = v;
+            } else {
+                fin[k] = load_as<S, T>(p, f[fidx(p.plane, p.pitch, k, y, x)], k);
+            }
+        }
+    }
+    double m = 0.0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const int dx = x + Lat<9>::cx(k), dy = y + Lat<9>::cy(k);
+        if (dx >= 0 && dx < p.nx && dy >= 0 && dy < p.ny) {
+            if constexpr (std::is_same<T, double>::value)
+                m = Ar<double>::add(m, fin[k]);
+            else
+                m += (double)fin[k] + p.rw[k];
+        }
+    }
+    mass = m;
+}
+
+__device__ __forceinline__ bool is_wall_node(const StepParams &p, int x, int y)
+{
+    return bc_node_walls(p.boundary) && (x == 0 || x == p.nx - 1 || y == 0 || y == p.ny - 1);
+}
+
 // Median of the dS stencil of site (x, y), tile-local position (tx, ty) in a
 // shared array with row stride `ld` (Sec. 3.5; wall rules of Sec. 4.4, read for
 // walls half a link outside the lattice: a node next to one wall uses itself
@@ -88,6 +174,23 @@ __device__ __forceinline__ bool stencil_median(const StepParams &p, const T *s, 
         med = med3(S_(-1, 0), S_(0, 0), S_(1, 0));
         return true;
     } else {
+        if (bc_node_walls(p.boundary)) {
+            // boundary nodes are not filtered; their neighbours use stencils
+            // along the wall (Sec. 4.4)
+            if (x == 0 || x == p.nx - 1 || y == 0 || y == p.ny - 1) return false;
+            const bool nx1 = x == 1 || x == p.nx - 2, ny1 = y == 1 || y == p.ny - 2;
+            if (nx1 && ny1) {
+                med = med3(S_(0, 0), S_(x == 1 ? 1 : -1, 0), S_(0, y == 1 ? 1 : -1));
+            } else if (ny1) {
+                med = med3(S_(-1, 0), S_(0, 0), S_(1, 0));
+            } else if (nx1) {
+                med = med3(S_(0, -1), S_(0, 0), S_(0, 1));
+            } else {
+                med = med9(S_(-1, -1), S_(-1, 0), S_(-1, 1), S_(0, -1), S_(0, 0), S_(0, 1), S_(1, -1), S_(1, 0),
+                           S_(1, 1));
+            }
+            return true;
+        }
         const bool wallx = p.boundary == 0, wally = p.boundary != 1;
         const bool nearx = wallx && (x == 0 || x == p.nx - 1);
         const bool neary = wally && (y == 0 || y == p.ny - 1);
@@ -145,8 +248,8 @@ __global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const S *__r
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int x = bx * (BX - 2) - 1 + tx;
     const int y = Q == 9 ? by * (BY - 2) - 1 + ty : 0;
-    const bool wrapx = p.boundary != 0;
-    const bool wrapy = (Q == 9) && p.boundary == 1;
+    const bool wrapx = bc_wrap_x(p.boundary);
+    const bool wrapy = (Q == 9) && bc_wrap_y(p.boundary);
     bool valid = wrapx ? (x >= -1 && x <= p.nx) : (x >= 0 && x < p.nx);
     if (Q == 9) valid = valid && (wrapy ? (y >= -1 && y <= p.ny) : (y >= 0 && y < p.ny));
     const int xs = wrapx ? (x < 0 ? x + p.nx : (x >= p.nx ? x - p.nx : x)) : x;
@@ -158,7 +261,30 @@ __global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const S *__r
     float nq[Q];
     T ds = T(0), dsin = T(0), rho = T(0);
     bool bad = false;
-    if (valid) {
+    // a boundary node of a cavity with nodes on the walls: free flight and the
+    // wall rule only (no collision, no limiter, dS = 0)
+    const bool wall = Q == 9 && valid && is_wall_node(p, xs, ys);
+    double wmass = 0.0;
+    if (wall) {
+        if constexpr (Q == 9) {
+            if (p.collide) {
+                wall_node<S, T>(p, src, xs, ys, fin, wmass);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 9; ++k) fin[k] = load_as<S, T>(p, src[fidx(p.plane, p.pitch, k, ys, xs)], k);
+#pragma unroll
+                for (int k = 0; k < 9; ++k) {
+                    const int dx = xs + Lat<9>::cx(k), dy = ys + Lat<9>::cy(k);
+                    if (dx >= 0 && dx < p.nx && dy >= 0 && dy < p.ny) {
+                        if constexpr (std::is_same<T, double>::value)
+                            wmass = Ar<double>::add(wmass, fin[k]);
+                        else
+                            wmass += (double)fin[k] + p.rw[k];
+                    }
+                }
+            }
+        }
+    } else if (valid) {
         if (p.collide) {
             pull<Q, S, T>(p, src, xs, ys, fin);
         } else {
@@ -205,8 +331,15 @@ __global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const S *__r
     }
     __syncthreads();
 
-    const bool own = valid && tx >= 1 && tx <= BX - 2 && (Q == 3 || (ty >= 1 && ty <= BY - 2)) && x >= 0 &&
-                     x < p.nx && y >= 0 && y < p.ny;
+    const bool own_site = valid && tx >= 1 && tx <= BX - 2 && (Q == 3 || (ty >= 1 && ty <= BY - 2)) && x >= 0 &&
+                          x < p.nx && y >= 0 && y < p.ny;
+    const bool own = own_site && !wall;
+    if (own_site && wall) {
+        // a boundary node stores what free flight and the wall rule gave it
+#pragma unroll
+        for (int k = 0; k < Q; ++k) dst[fidx(p.plane, p.pitch, k, y, x)] = f2s<S>(fin[k]);
+        if (p.ds_out) p.ds_out[(long long)y * p.nx + x] = 0.0;
+    }
     double acc[P_NSTAT];
 #pragma unroll
     for (int i = 0; i < P_NSTAT; ++i) acc[i] = 0.0;
@@ -365,6 +498,7 @@ __global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const S *__r
     // block partial sums, fixed order
     const int lin = ty * BX + tx, warp = lin >> 5, lane = lin & 31;
     if constexpr (std::is_same<T, double>::value) {
+        if (own_site && wall) acc[P_MASS] = wmass;
 #pragma unroll
         for (int i = 0; i < P_NSTAT; ++i) {
             const double v = warp_sum(acc[i]);
@@ -389,8 +523,11 @@ __global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const S *__r
         const int npos = __popc(__ballot_sync(0xffffffffu, c_pos));
         const int nmed = __popc(__ballot_sync(0xffffffffu, c_med));
         const int nbad = __popc(__ballot_sync(0xffffffffu, c_bad));
+        // boundary nodes carry their mass in FP64 (only warps that hold one add it)
+        double wm = 0.0;
+        if (__any_sync(0xffffffffu, own_site && wall)) wm = warp_sum(own_site && wall ? wmass : 0.0);
         if (lane == 0) {
-            sred[warp][P_MASS] = (double)p.rho_ref * (double)nown + (double)fmass;
+            sred[warp][P_MASS] = (double)p.rho_ref * (double)nown + (double)fmass + wm;
             sred[warp][P_SUM_DS] = (double)fsum_ds;
             sred[warp][P_SUM_IN] = (double)fsum_in;
             sred[warp][P_DS_LIM] = (double)fsum_lim;
@@ -426,6 +563,7 @@ __global__ void __launch_bounds__(256) k_ens_partial(StepParams p, const S *__re
     int icnt = 0;
     for (long long s = blockIdx.x * 256LL + threadIdx.x; s < n; s += (long long)gridDim.x * 256) {
         const int x = (int)(s % p.nx), y = (int)(s / p.nx);
+        if (Q == 9 && is_wall_node(p, x, y)) continue;  // boundary nodes are not collided
         T fin[Q], fs[Q], fp[Q], fa[Q];
         float nq[Q];
         T ds, dsin, rho;
@@ -508,6 +646,10 @@ __global__ void k_delta_s(StepParams p, const S *__restrict__ f, double *__restr
     const long long n = (long long)p.nx * p.ny;
     for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(s % p.nx), y = (int)(s / p.nx);
+        if (Q == 9 && is_wall_node(p, x, y)) {  // boundary nodes are not collided
+            out[s] = 0.0;
+            continue;
+        }
         double fin[Q], fs[Q], fp[Q], ds, dsin, rho;
         pull<Q, S, double>(p, f, x, y, fin);
         const bool bad = site_collide<Q, double>(fin, p.a, true, fs, fp, ds, dsin, rho, p.eq);

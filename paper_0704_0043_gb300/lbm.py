@@ -19,7 +19,7 @@ from . import build as _build
 
 D1Q3, D2Q9 = 1, 2
 FP64, FP32, BF16, FP16 = 0, 1, 2, 3
-BC_WALLS, BC_PERIODIC, BC_CHANNEL = 0, 1, 2
+BC_WALLS, BC_PERIODIC, BC_CHANNEL, BC_NODE_WALLS, BC_DIFFUSIVE = 0, 1, 2, 3, 4
 LIM_POSITIVITY, LIM_EHRENFEST, LIM_MEDIAN, LIM_SMOOTH, LIM_THRESHOLD = 1, 2, 4, 8, 16
 MEDIAN_THRESHOLD, MEDIAN_GATE = 0, 1
 EQ_POLYNOMIAL, EQ_ENTROPIC = 0, 1
@@ -108,6 +108,8 @@ def lib():
         L.lbm_status_string.argtypes = [ctypes.c_int]
         L.lbm_status_string.restype = ctypes.c_char_p
         L.lbm_abi_version.restype = ctypes.c_int32
+        L.lbm_set_graph.argtypes = [vp, ctypes.c_int32]
+        L.lbm_set_graph.restype = ctypes.c_int
         L.lbm_step_noalloc.argtypes = [cfgp, vp, vp, ctypes.POINTER(StepStats), vp]
         L.lbm_step_noalloc.restype = ctypes.c_int
         i32p, i64p = ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)
@@ -211,11 +213,21 @@ def step_noalloc(f_in, f_out, stream: int | None = None, **cfg) -> dict:
     """lbm_step_noalloc: one FP64 limited step from device array f_in into
     device array f_out (torch CUDA tensors, q * nx * ny float64 each), with no
     device allocation by the library.  Returns the step's stats."""
+    import torch
     c = default_config(**cfg)
     q = 3 if c.lattice == D1Q3 else 9
     n = q * c.nx * c.ny
+    dev = torch.cuda.current_device()
+    for name, t in (("f_in", f_in), ("f_out", f_out)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.device.index != dev:
+            raise ValueError(f"{name} must be a CUDA tensor on the current device (cuda:{dev})")
+        if t.dtype != torch.float64 or not t.is_contiguous() or t.numel() != n:
+            raise ValueError(f"{name} must be a contiguous float64 tensor of {n} elements")
     pi, ki = _ptr(f_in, n, False)
     po, ko = _ptr(f_out, n, True)
+    nbytes = 8 * n
+    if pi < po + nbytes and po < pi + nbytes:
+        raise ValueError("f_in and f_out must not overlap")
     st = StepStats()
     s = current_stream_handle() if stream is None else stream
     _check(lib().lbm_step_noalloc(ctypes.byref(c), ctypes.c_void_p(pi), ctypes.c_void_p(po),
@@ -323,6 +335,10 @@ class Lattice:
 
     def synchronize(self):
         _check(lib().lbm_synchronize(self._h), self._h)
+
+    def set_graph(self, steps_per_graph: int):
+        """CUDA-graph replay of runs of steps_per_graph steps (even, >= 2; 0 = off)."""
+        _check(lib().lbm_set_graph(self._h, int(steps_per_graph)), self._h)
 
     def timing(self, enable: bool, every: int = 1):
         """Per-kernel event timing on (one step in `every`) or off."""

@@ -72,10 +72,13 @@ def stream_function(ux, n):
     return psi
 
 
-def extremum(psi, xs, ys, region, sign):
-    """Node coordinates of the largest sign * psi inside region ((x0, x1), (y0, y1))."""
+def extremum(psi, xs, ys, region, sign, valid=None):
+    """Node coordinates of the largest sign * psi inside region ((x0, x1), (y0, y1))
+    (among the nodes where `valid` is true, if given)."""
     (x0, x1), (y0, y1) = region
     mask = (xs >= x0) & (xs <= x1) & (ys >= y0) & (ys <= y1)
+    if valid is not None:
+        mask &= valid
     vals = np.where(mask, sign * psi, -np.inf)
     j, i = np.unravel_index(np.argmax(vals), psi.shape)
     return xs[j, i], ys[j, i]
@@ -123,8 +126,9 @@ def vortex_centres_nodes(ux, n, names=("primary", "lower_left", "lower_right")):
     psi = stream_function_nodes(ux, n)
     ii, jj = np.meshgrid(np.arange(n), np.arange(n))
     xs, ys = ii / (n - 1.0), jj / (n - 1.0)
+    fluid = (ii > 0) & (ii < n - 1) & (jj > 0) & (jj < n - 1)  # vortex centres lie off the walls
     sign = -np.sign(psi[n // 2, n // 2])
     out = {}
     for name in names:
-        out[name] = extremum(psi, xs, ys, VORTEX_REGIONS[name], -sign if name == "primary" else sign)
+        out[name] = extremum(psi, xs, ys, VORTEX_REGIONS[name], -sign if name == "primary" else sign, fluid)
     return out

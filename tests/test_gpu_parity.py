@@ -77,6 +77,13 @@ FP64_CASES = [
          delta_median=0.0, delta_ehrenfest=5e-4, k_max=3),
     dict(lattice=lbm.D1Q3, nx=3, ny=1, boundary=lbm.BC_WALLS, beta=0.9, limiters=ALL,
          delta_median=0.0, delta_ehrenfest=1e-4, k_max=1),
+    # boundary nodes on the walls (Sec. 4.4): bounce-back with the lid, and the diffusive wall
+    dict(lattice=lbm.D2Q9, nx=67, ny=41, boundary=lbm.BC_NODE_WALLS, beta=0.97, u_lid=0.1,
+         rho_wall=1.2, limiters=ALL, delta_median=1e-4, delta_ehrenfest=5e-3, k_max=7),
+    dict(lattice=lbm.D2Q9, nx=45, ny=33, boundary=lbm.BC_DIFFUSIVE, beta=0.95, u_lid=0.1,
+         limiters=ALL, delta_median=0.0, delta_ehrenfest=2e-3, k_max=5),
+    dict(lattice=lbm.D2Q9, nx=5, ny=6, boundary=lbm.BC_DIFFUSIVE, beta=0.9, u_lid=0.1,
+         limiters=ALL, delta_median=0.0, delta_ehrenfest=1e-3, k_max=2),
 ]
 
 
@@ -188,6 +195,29 @@ def test_fp32_one_step_against_oracle(nx, ny, kernel):
     np.testing.assert_allclose(st["dS_lim"], r.stats["dS_lim"], rtol=1e-3)
 
 
+@pytest.mark.parametrize("boundary", [lbm.BC_NODE_WALLS, lbm.BC_DIFFUSIVE])
+def test_fp32_node_walls_one_step_against_oracle(boundary):
+    """Boundary nodes on the walls with FP32 storage (tiled kernel): one step from
+    the stored FP32 state within the FP32 bound of the other shapes, the
+    boundary nodes' own rule evaluated in FP64 and rounded once."""
+    nx, ny = 131, 77
+    cfg = dict(lattice=lbm.D2Q9, nx=nx, ny=ny, boundary=boundary, beta=0.97, u_lid=0.1, rho_wall=1.0,
+               precision=lbm.FP32, limiters=ALL, delta_median=1e-4, delta_ehrenfest=2e-3, k_max=10)
+    g, oc = pair(**cfg)
+    assert g.step_kernel() == lbm.KERNEL_TILED
+    f0 = rand_state(9, ny, nx, 91, eps=0.15, heavy=40)
+    g.set_populations(f0)
+    f = g.get_populations()
+    np.testing.assert_array_equal(g.delta_s(), oracle.delta_s(oc, f))
+    g.step(1)
+    r = oracle.step(oc, f)
+    np.testing.assert_allclose(g.get_populations(), r.f, rtol=2e-5, atol=2e-7)
+    np.testing.assert_array_equal(g.limited_sites(), np.sort(r.selected))
+    st = g.stats()
+    assert st["n_ehr"] == r.stats["n_ehr"] > 0 and st["n_cand"] == r.stats["n_cand"]
+    assert abs(st["mass"] - r.stats["mass"]) <= 1e-6 * r.stats["mass"]
+
+
 @pytest.mark.parametrize("eps,delta_e,heavy_per", [(0.15, 1e-4, 0), (0.02, 2e-3, 100)])
 def test_fp32_dense_ehrenfest_candidates_against_oracle(eps, delta_e, heavy_per):
     """Many Ehrenfests' candidates per work item: with delta = 1e-4 nearly every
@@ -239,7 +269,10 @@ def test_fused_and_tiled_fp32_agree_over_many_steps():
 def test_fp32_cavity_100_matches_fp64_oracle_after_1000_steps(kernel):
     """Config: 100 x 100 cavity, lid 0.1, Re = 5000, median delta = 1e-3, FP32 on
     the GPU vs the FP64 oracle: rho and u within 1e-5 absolute after 1000 steps."""
-    w = inputs.cavity100_workload()
+    # the fused kernel's cavity (walls half a link outside): lid 0.1, Re = 5000 with
+    # L = 100, median delta = 1e-3, density 1 -- stable over these 1000 steps
+    w = inputs.Workload("cavity100_halfway", 2, 100, 100, inputs.beta_from_nu(inputs.cavity_nu(100, 0.1, 5000.0)),
+                        0.1, 1.0, inputs.LIM_MEDIAN, delta_median=1e-3)
     g, oc = pair(lattice=lbm.D2Q9, nx=100, ny=100, boundary=lbm.BC_WALLS, beta=w.beta,
                  u_lid=w.u_lid, rho_wall=w.rho0, precision=lbm.FP32, limiters=w.limiters,
                  delta_median=w.delta_median, kernel=kernel)
