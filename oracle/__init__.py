@@ -31,6 +31,7 @@ LIM_SMOOTH, LIM_THRESHOLD, LIM_ENTTHRESH = 8, 16, 32
 MEDIAN_THRESHOLD, MEDIAN_GATE = 0, 1
 EQ_POLYNOMIAL, EQ_ENTROPIC = 0, 1
 COLL_LBGK, COLL_ELBM = 0, 1
+PHI_HOMOTHETY, PHI_ENTROPY = 0, 1
 
 
 def build(force: bool = False) -> str:
@@ -57,7 +58,7 @@ class _Config(ctypes.Structure):
         ("k_max", ctypes.c_longlong), ("median_mode", ctypes.c_int), ("equilibrium", ctypes.c_int),
         ("smooth_delta", ctypes.c_double), ("smooth_k", ctypes.c_double),
         ("threshold_c", ctypes.c_double), ("threshold_delta", ctypes.c_double),
-        ("entthresh_delta0", ctypes.c_double), ("collision", ctypes.c_int),
+        ("entthresh_delta0", ctypes.c_double), ("collision", ctypes.c_int), ("phi_rule", ctypes.c_int),
     ]
 
 
@@ -92,6 +93,8 @@ def _load():
         lib.orc_rel_entropy.restype = ctypes.c_double
         lib.orc_elbm_alpha.argtypes = [ctypes.c_int, dp, dp, ctypes.POINTER(ctypes.c_int)]
         lib.orc_elbm_alpha.restype = ctypes.c_double
+        lib.orc_phi_entropy.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double]
+        lib.orc_phi_entropy.restype = ctypes.c_double
         lib.orc_site_moments.argtypes = [ctypes.c_int, dp, dp, dp, dp]
         lib.orc_init.argtypes = [cp, dp, dp, dp, dp]
         lib.orc_moments.argtypes = [cp, dp, dp, dp, dp]
@@ -135,6 +138,7 @@ class Config:
     threshold_delta: float = 0.0
     entthresh_delta0: float = 0.1
     collision: int = COLL_LBGK
+    phi_rule: int = PHI_HOMOTHETY
 
     @property
     def q(self) -> int:
@@ -152,7 +156,7 @@ class Config:
                        self.rho_wall, self.limiters, self.delta_median, self.delta_ehrenfest,
                        self.k_max, self.median_mode, self.equilibrium, self.smooth_delta,
                        self.smooth_k, self.threshold_c, self.threshold_delta, self.entthresh_delta0,
-                       self.collision)
+                       self.collision, self.phi_rule)
 
 
 def _f64(a, shape=None):
@@ -198,6 +202,13 @@ def elbm_alpha(f, fs):
     pos = ctypes.c_int(0)
     a = _load().orc_elbm_alpha(len(f), _dp(f), _dp(fs), ctypes.byref(pos))
     return a, bool(pos.value)
+
+
+def phi_entropy(fp, fs, target) -> float:
+    """The phi of Sec. 3.7: dS(fs + phi (fp - fs)) = target (Eq. DelS), by bisection."""
+    fp = _f64(fp)
+    fs = _f64(fs)
+    return _load().orc_phi_entropy(len(fp), _dp(fp), _dp(fs), float(target))
 
 
 def site_moments(lattice: int, f) -> tuple:

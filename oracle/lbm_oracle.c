@@ -174,6 +174,22 @@ double orc_elbm_alpha(int q, const double *f, const double *fs, int *pos)
     return lo;
 }
 
+double orc_phi_entropy(int q, const double *fp, const double *fs, double target)
+{
+    /* dS(fs + phi (fp - fs)) grows with phi on [0, 1] (0 at phi = 0, convex) */
+    double g[9];
+    double lo = 0.0, hi = 1.0;
+    for (int it = 0; it < 200 && hi - lo > 1e-15; ++it) {
+        double mid = 0.5 * (lo + hi);
+        for (int k = 0; k < q; ++k) g[k] = fs[k] + mid * (fp[k] - fs[k]);
+        if (orc_rel_entropy(q, g, fs) <= target)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
 /* f* of the configured kind; returns 1 where it does not exist. */
 static int site_feq(const orc_config *cfg, double rho, double ux, double uy, double *fs)
 {
@@ -543,6 +559,25 @@ static int cand_cmp(const void *pa, const void *pb)
 }
 
 /*
+ * The factor of a filter that brings dS = x down to the target t < x at site s
+ * (fields fp, fs of n sites): the homothety sqrt(t / x) of Eq. entrHom, or, with
+ * ORC_PHI_ENTROPY and entropic f*, the exact solve of Sec. 3.7.
+ */
+static double phi_to(const orc_config *cfg, int q, const double *fp, const double *fs, long long n,
+                     long long s, double t, double x)
+{
+    if (cfg->phi_rule == ORC_PHI_ENTROPY && cfg->equilibrium == ORC_EQ_ENTROPIC) {
+        double a[9], b[9];
+        for (int k = 0; k < q; ++k) {
+            a[k] = fp[k * n + s];
+            b[k] = fs[k * n + s];
+        }
+        return orc_phi_entropy(q, a, b, t);
+    }
+    return sqrt(t / x);
+}
+
+/*
  * Steps 6-9 on per-site fields fs (f*), fp (f'), dS (dS(f')) and the bad-site
  * flags; writes f_out and accumulates the limiter sums into st.
  */
@@ -588,7 +623,7 @@ static void limit_core(const orc_config *cfg, unsigned limiters, const double *f
                 if (p_s < phi_ens) phi_ens = p_s;
             }
             if ((limiters & ORC_LIM_ENTTHRESH) && dS[s] > t_ent) {
-                double p_e = sqrt(t_ent / dS[s]);
+                double p_e = phi_to(cfg, q, fp, fs, n, s, t_ent, dS[s]);
                 if (p_e < phi_ens) phi_ens = p_e;
             }
             if (limiters & ORC_LIM_THRESHOLD) {
@@ -596,7 +631,7 @@ static void limit_core(const orc_config *cfg, unsigned limiters, const double *f
                 double t = cfg->threshold_c * E;
                 if (t < cfg->threshold_delta) t = cfg->threshold_delta;
                 if (dS[s] > t) {
-                    double p_t = sqrt(t / dS[s]);
+                    double p_t = phi_to(cfg, q, fp, fs, n, s, t, dS[s]);
                     if (p_t < phi_ens) phi_ens = p_t;
                 }
             }
@@ -617,10 +652,10 @@ static void limit_core(const orc_config *cfg, unsigned limiters, const double *f
                     double med = v[m / 2];
                     double x = dS[s];
                     if (cfg->median_mode == ORC_MEDIAN_GATE) {
-                        if (x > cfg->delta_median && med < x) phi_med = sqrt(med / x);
+                        if (x > cfg->delta_median && med < x) phi_med = phi_to(cfg, q, fp, fs, n, s, med, x);
                     } else {
                         double t = med > cfg->delta_median ? med : cfg->delta_median;
-                        if (x > t) phi_med = sqrt(t / x);
+                        if (x > t) phi_med = phi_to(cfg, q, fp, fs, n, s, t, x);
                     }
                 }
             }

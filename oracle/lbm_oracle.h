@@ -85,7 +85,14 @@ typedef struct {
     double threshold_delta; /* ORC_LIM_THRESHOLD / ORC_LIM_ENTTHRESH: dS_t = max(dS_0, threshold_delta) */
     double entthresh_delta0; /* ORC_LIM_ENTTHRESH: delta_0 of Eq. EntThresh (Eq. LimEntLim's bound) */
     int collision;           /* ORC_COLL_* (ELBM needs ORC_EQ_ENTROPIC) */
+    int phi_rule;            /* ORC_PHI_*: how the filters with a target dS_t (median, threshold) limit */
 } orc_config;
+
+/* ORC_PHI_HOMOTHETY: phi = sqrt(dS_t / dS) (Eq. entrHom, the quadratic approximation).
+ * ORC_PHI_ENTROPY (entropic f* only): phi solves dS(f* + phi (f' - f*)) = dS_t, i.e.
+ * S(f* + phi (f' - f*)) = S(f*) - dS_t (Sec. 3.7), by bisection on [0, 1]. */
+#define ORC_PHI_HOMOTHETY 0
+#define ORC_PHI_ENTROPY 1
 
 /*
  * The ensemble-dependent limiters use E(dS), the mean of dS(f') over the
@@ -152,6 +159,11 @@ double orc_rel_entropy(int q, const double *f, const double *fs);
  * to 1 when the positivity boundary was taken.
  */
 double orc_elbm_alpha(int q, const double *f, const double *fs, int *pos);
+
+/* Sec. 3.7: the phi in [0, 1] with dS(fs + phi (fp - fs)) = target (Eq. DelS), for
+ * 0 <= target < dS(fp): bisection to a bracket of 1e-15, returning its lower end
+ * (the state it gives has dS at most target). */
+double orc_phi_entropy(int q, const double *fp, const double *fs, double target);
 
 /* Moments rho, u of one site's populations (Eq. macro_dis). */
 void orc_site_moments(int lattice, const double *f, double *rho, double *ux, double *uy);

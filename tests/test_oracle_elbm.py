@@ -1,5 +1,6 @@
 """Pins of the oracle's ELBM collision (Sec. 3.7, Eq. elbm, Eq. entropy_estimate,
-the bisection of Sec. 4.2).  Oracle only: no GPU path implements ELBM yet.
+the bisection of Sec. 4.2), and of the filters' factor from the entropy itself
+(Sec. 3.7: phi with S(f* + phi (f - f*)) = S(f*) - dS_t).
 
 * alpha is the nontrivial root of S(f + alpha (f* - f)) = S(f): checked with the
   lattice entropy S computed from the weights W (not from f*), within the
@@ -114,3 +115,77 @@ def test_elbm_step_approaches_lbgk_for_small_deviations():
         diffs.append(np.abs(e - g).max())
     # O(eps^2): a tenfold smaller deviation gives a ~hundredfold smaller difference
     assert diffs[1] < diffs[0] / 30
+
+
+# -- Sec. 3.7: the filters' factor from the entropy itself ------------------------------------------
+
+def _dS_mp(f, fs):
+    """sum_k f_k ln(f_k / f*_k) (Eq. DelS) at 50 digits."""
+    import mpmath
+    mpmath.mp.dps = 50
+    return sum(mpmath.mpf(float(a)) * mpmath.log(mpmath.mpf(float(a)) / mpmath.mpf(float(b)))
+               for a, b in zip(f, fs) if a > 0)
+
+
+def test_phi_solves_the_entropy_equation_of_sec_3_7():
+    """phi in [0, 1] with dS(f* + phi (f - f*)) = dS_t: the returned phi gives at
+    most dS_t, and phi + 4e-15 already exceeds it (checked at 50 digits), up to
+    the FP64 evaluation of Eq. DelS, whose terms cancel to second order: its
+    error is a few ulps of sum_k |f_k ln(f_k / f*_k)|, plus f_k times the
+    rounding of each ratio f_k / f*_k before its logarithm."""
+    import mpmath
+    for seed in range(25):
+        f, fs = _site(seed, 0.6)
+        ds = float(_dS_mp(f, fs))
+        for frac in (0.9, 0.3, 0.01):
+            t = frac * ds
+            phi = oracle.phi_entropy(f, fs, t)
+            assert 0.0 <= phi <= 1.0
+            g = fs + phi * (f - fs)
+            terms = float(sum(abs(mpmath.mpf(float(a)) * mpmath.log(mpmath.mpf(float(a)) / mpmath.mpf(float(b))))
+                              for a, b in zip(g, fs)))
+            tol = 2.0 ** -52 * (16 * terms + 4 * g.sum())  # + the rounding of f / f* before its logarithm
+            lo = _dS_mp(g, fs)
+            hi = _dS_mp(fs + (phi + 4e-15) * (f - fs), fs)
+            assert lo <= t + tol and hi >= t - tol, (seed, frac, float(lo), float(hi), t, tol)
+
+
+def test_phi_tends_to_the_homothety_for_small_deviations():
+    """In the quadratic approximation dS(f* + phi n) = phi^2 dS(f* + n), so the
+    solve tends to sqrt(dS_t / dS) (Eq. entrHom) as the deviation shrinks."""
+    for seed in range(10):
+        errs = []
+        for scale in (1e-2, 1e-3):
+            f, fs = _site(seed, scale)
+            ds = oracle.rel_entropy(f, fs)
+            phi = oracle.phi_entropy(f, fs, 0.25 * ds)
+            errs.append(abs(phi / 0.5 - 1.0))
+        assert errs[1] < 2e-3 and errs[1] < errs[0] / 5, errs
+
+
+def test_entropic_median_pass_with_the_exact_solve_lands_on_the_target():
+    """A median pass with entropic f* and the solve of Sec. 3.7: every filtered
+    site ends with dS = dS_t = max(median, delta) of its stencil (the entropy of
+    the limited state is S(f*) - dS_t), moments unchanged."""
+    nx, ny = 12, 10
+    cfg = oracle.Config(lattice=oracle.D2Q9, nx=nx, ny=ny, boundary=oracle.BC_WALLS,
+                        equilibrium=oracle.EQ_ENTROPIC, phi_rule=oracle.PHI_ENTROPY, delta_median=1e-5)
+    rho, ux, uy = inputs.random_moments(14, nx, ny, umax=0.1)
+    fs = oracle.init(cfg, rho, ux, uy)
+    rng = np.random.default_rng(15)
+    f = fs * (1 + 0.08 * rng.uniform(-1, 1, fs.shape))
+    r = oracle.limit(cfg, f, oracle.LIM_MEDIAN)
+    after = oracle.limit(cfg, r.f, 0).dS
+    hit = r.phi < 1
+    assert hit.sum() > 10
+    homothety = oracle.limit(oracle.Config(**{**cfg.__dict__, "phi_rule": oracle.PHI_HOMOTHETY}), f,
+                             oracle.LIM_MEDIAN)
+    np.testing.assert_array_equal(homothety.phi < 1, hit)  # the same sites are filtered
+    for j, i in zip(*np.nonzero(hit)):
+        # the target: the stencil median (R7 rules) or delta; recover it from the homothety's phi
+        t = homothety.phi[j, i] ** 2 * r.dS[j, i]
+        np.testing.assert_allclose(after[j, i], t, rtol=1e-9)
+    r0, a0, b0 = oracle.moments(cfg, f)
+    r1, a1, b1 = oracle.moments(cfg, r.f)
+    np.testing.assert_allclose(r1, r0, rtol=1e-14)
+    np.testing.assert_allclose(a1, a0, rtol=0, atol=1e-14)
