@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cavity4096",
-                    choices=["cavity4096", "cavity100", "tube", "batched", "serve"],
+                    choices=["cavity4096", "cavity100", "tube", "batched", "serve", "hopf"],
                     help="cavity4096: the 4096^2 cavity (default); cavity100: the 100^2 cavity at Re 5000; "
                          "tube: the 800-site D1Q3 shock tube (FP64); batched: 256 cavities of sides "
                          "64..512; serve: Poisson-arriving solves through the continuous-batching server")
@@ -50,6 +50,10 @@ def parse():
                     help="developed: the flow after --develop steps from rest; active: every site "
                          "out of equilibrium (limiters act widely)")
     ap.add_argument("--tube-sites", type=int, default=800, help="tube: lattice sites")
+    ap.add_argument("--hopf-re", default="7000,7125,7250,7375,7500,7625,7750,7875",
+                    help="hopf: Reynolds numbers of the sweep (one lattice each)")
+    ap.add_argument("--hopf-steps", type=int, default=0,
+                    help="hopf: steps per lattice (default 5000 L / u0, the paper's protocol)")
     ap.add_argument("--requests", type=int, default=200, help="serve: requests in the trace")
     ap.add_argument("--develop", type=int, default=-1,
                     help="untimed steps before warm-up so the flow has left the rest state "
@@ -399,6 +403,119 @@ def run_batched(args):
     b.close()
 
 
+def hopf_energy(u, L, u0):
+    """E_u^2 of Sec. 4.4.2 (Eq. energy): E_u = || sqrt(L / (u0 |u|)) (u - mean(u)) ||_2 over the
+    final 1 % of the control-point signal u, |u| its length, so E_u^2 = (L / u0) var(u)."""
+    import numpy as np
+    u = np.asarray(u, dtype=np.float64)
+    return float((L / u0) * np.mean((u - u.mean()) ** 2))
+
+
+def hopf_fit(res, e2):
+    """Re_c of Sec. 4.4.2: E_u^2 grows linearly with Re past a Hopf bifurcation, so a
+    line fitted through the points clearly above the steady level (E_u^2 above a
+    tenth of the largest) meets E_u^2 = 0 at the critical Re.  None with fewer than
+    two such points."""
+    import numpy as np
+    res, e2 = np.asarray(res, float), np.asarray(e2, float)
+    up = e2 > 0.1 * e2.max() if e2.max() > 0 else np.zeros_like(e2, bool)
+    if up.sum() < 2:
+        return None
+    a, b = np.polyfit(res[up], e2[up], 1)
+    return float(-b / a) if a > 0 else None
+
+
+def dominant_frequency(u, L, u0):
+    """Frequency of the largest non-zero Fourier mode of the control-point signal,
+    in cycles per non-dimensional time unit L / u0 (one sample per step)."""
+    import numpy as np
+    u = np.asarray(u, float) - np.mean(u)
+    spec = np.abs(np.fft.rfft(u * np.hanning(len(u))))
+    freq = np.fft.rfftfreq(len(u), d=u0 / L)  # d = non-dimensional time per step
+    k = 1 + int(np.argmax(spec[1:]))
+    return float(freq[k])
+
+
+def run_hopf(args):
+    """The first Hopf bifurcation of the lid-driven cavity (Sec. 4.4.2): 100 x 100,
+    boundary nodes on the walls with the diffusive Maxwell wall, lid 0.1, density 1,
+    median filter delta = 1e-3, polynomial f* in FP32 (the paper finds no
+    significant difference between polynomial and entropic f* in the cavity,
+    Sec. 4.4.1), one lattice per Re of the sweep, all in one batch with graph
+    replay.  Each lattice records u at the control point (L/16, 13L/16) every step;
+    E_u^2 of the final 1 % of 5000 non-dimensional time units (5000 L / u0 steps)
+    gives Re_c by the line fit of Sec. 4.4.2."""
+    import numpy as np
+    import torch
+    from paper_0704_0043_gb300 import build as lbm_build
+    from paper_0704_0043_gb300 import inputs, lbm
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    lbm_build.build()
+    n, u0 = 100, 0.1
+    L = n - 1  # between the wall nodes
+    res = [float(r) for r in args.hopf_re.split(",")]
+    steps = args.hopf_steps if args.hopf_steps > 0 else int(round(5000 * L / u0))
+    rec = max(2, steps // 100)
+    ci, cj = int(round(L / 16)), int(round(13 * L / 16))
+    b = lbm.Batch()
+    slots = []
+    for re in res:
+        s = b.add(lattice=lbm.D2Q9, nx=n, ny=n, boundary=lbm.BC_DIFFUSIVE, precision=lbm.FP32,
+                  beta=inputs.beta_from_nu(inputs.cavity_nu(L, u0, re)), u_lid=u0, rho_wall=1.0,
+                  limiters=lbm.LIM_MEDIAN, delta_median=1e-3)
+        b.init(s, *inputs.cavity_rest(n, n))
+        b.probe(s, cj * n + ci, rec)
+        slots.append(s)
+    b.set_graph(1000)
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    sampler.start()
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = b.launch_count()
+    torch.cuda.synchronize()
+    sampler.timed_begin()
+    ev0.record(stream)
+    b.step(steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    sampler.timed_end()
+    clocks = sampler.stop()
+    t = ev0.elapsed_time(ev1) / 1e3
+    failed = []
+    try:
+        b.synchronize()
+    except lbm.LBMError:
+        pass
+    e2, freqs = [], []
+    for re, s in zip(res, slots):
+        if b.lattice_status(s) != lbm.OK:
+            failed.append(re)
+            e2.append(float("nan"))
+            freqs.append(float("nan"))
+            continue
+        sig = b.probe_read(s, rec)[:, 1]  # u_x at the control point, final 1 %
+        e2.append(hopf_energy(sig, L, u0))
+        freqs.append(dominant_frequency(sig, L, u0))
+    ok = [i for i, v in enumerate(e2) if np.isfinite(v)]
+    re_c = hopf_fit([res[i] for i in ok], [e2[i] for i in ok])
+    sites = len(res) * n * n
+    v = sites * steps / t / 1e6
+    out = {"metric": "batched limited-LBM MLUPS", "value": v, "unit": "MLUPS", "n_gpus": 1, "steps": steps,
+           "warmup": 0, "ms_per_step": t * 1e3 / steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "hopf_sweep_cavity100_diffusive", "lattices": len(res), "nx": n, "ny": n,
+                      "walls": "diffusive Maxwell (boundary nodes)", "u_lid": u0, "rho0": 1.0,
+                      "limiters": "median", "delta": 1e-3, "equilibrium": "polynomial", "storage": "fp32",
+                      "control_point": [ci, cj], "record_steps": rec, "graph_steps": 1000,
+                      "l2": "lattices resident in L2 (no flush: the workload itself is that small)"},
+           "hopf": {"re": res, "E_u2": e2, "re_c_fit": re_c, "dominant_frequency": freqs,
+                    "frequency_unit": "cycles per L/u0", "failed_re": failed,
+                    "paper": {"re_c": 7135, "omega_at_7375": 0.525}},
+           "gpu_launches": b.launch_count() - l0, "clocks": clocks}
+    print(json.dumps(out), flush=True)
+    b.close()
+
+
 def run_serve(args):
     """Poisson arrivals (200/s): 70 % cavities of side 100..1024, 30 % shock
     tubes of 800..1e6 sites (density ratio 1:2..1:4), 1e3..1e5 steps each,
@@ -489,6 +606,9 @@ def main():
         return
     if args.workload == "serve":
         run_serve(args)
+        return
+    if args.workload == "hopf":
+        run_hopf(args)
         return
     import numpy as np
     import torch

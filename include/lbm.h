@@ -42,7 +42,7 @@
 extern "C" {
 #endif
 
-#define LBM_ABI_VERSION 2
+#define LBM_ABI_VERSION 3
 
 typedef enum {
     LBM_OK = 0,
@@ -121,6 +121,23 @@ enum {
  *   tiled kernel only; lbm_init then starts from the entropic f*. */
 enum { LBM_EQ_POLYNOMIAL = 0, LBM_EQ_ENTROPIC = 1 };
 
+/* Collision (needs LBM_EQ_ENTROPIC and LBM_FP64 for ELBM).
+ * LBM_COLL_LBGK: f' = f* + (2 beta - 1)(f* - f) (Eq. collLBGK, Eq. lbgkLB).
+ * LBM_COLL_ELBM: f' = (1 - beta) f + beta f~ with f~ = f + alpha (f* - f) (Eq. elbm),
+ *   alpha the nontrivial root of S(f~) = S(f) (Eq. entropy_estimate) found per site by
+ *   bisection on [1, alpha_max] to a bracket of 1e-15, keeping the end where the
+ *   entropy does not decrease (Sec. 4.2); alpha_max is the positivity boundary of the
+ *   line f + alpha (f* - f), taken when the entropy is still above S(f) there (no
+ *   root in the positive cone: the positivity rule); f = f* gives alpha = 2. */
+enum { LBM_COLL_LBGK = 0, LBM_COLL_ELBM = 1 };
+
+/* Factor of the filters with a target dS_t (median filter, threshold filter).
+ * LBM_PHI_HOMOTHETY: phi = sqrt(dS_t / dS) (Eq. entrHom, exact in the quadratic form).
+ * LBM_PHI_ENTROPY (LBM_EQ_ENTROPIC only): phi in [0, 1] solves
+ *   S(f* + phi (f' - f*)) = S(f*) - dS_t, i.e. dS(f* + phi (f' - f*)) = dS_t with the
+ *   exact dS of Eq. DelS (Sec. 3.7), by bisection to a bracket of 1e-15 (the lower end). */
+enum { LBM_PHI_HOMOTHETY = 0, LBM_PHI_ENTROPY = 1 };
+
 /* Kernel choice for lbm_step. */
 enum {
     LBM_KERNEL_AUTO = 0,    /* fused D2Q9 cavity kernel where it applies, else the tiled kernel */
@@ -149,6 +166,9 @@ typedef struct lbm_config {
     double smooth_k;         /* LBM_LIM_SMOOTH: exponent k (> 0, default 0.5) */
     double threshold_c;      /* LBM_LIM_THRESHOLD: dS_0 = threshold_c * E(dS) (>= 0, default 10) */
     double threshold_delta;  /* LBM_LIM_THRESHOLD: dS_t = max(dS_0, threshold_delta) (>= 0, default 0) */
+    int32_t collision;       /* LBM_COLL_* (default LBM_COLL_LBGK) */
+    int32_t phi_rule;        /* LBM_PHI_* (default LBM_PHI_HOMOTHETY) */
+    double entthresh_delta0; /* LBM_LIM_ENTTHRESH: delta_0 of Eq. EntThresh (>= 0, default 0.1) */
 } lbm_config;
 
 typedef struct lbm_step_stats {
@@ -244,6 +264,20 @@ int64_t lbm_device_bytes(const lbm_ctx *ctx);
 
 /* Device bytes lbm_create would allocate for cfg (0 if cfg is invalid). */
 int64_t lbm_footprint_bytes(const lbm_config *cfg);
+
+/* Control-point record (the monitoring point of Sec. 4.4.2): after every
+ * subsequent step the tail kernel stores rho, u_x, u_y (Eq. macro_dis, FP64, the
+ * values lbm_moments would give) of `site` (index j * nx + i) in a device ring of
+ * `capacity` samples, which this call allocates (device memory).  site = -1 stops
+ * recording.  Synchronises.  Errors: LBM_ERR_INVALID_ARG (site out of range,
+ * capacity < 1), LBM_ERR_OOM. */
+lbm_status lbm_probe(lbm_ctx *ctx, int64_t site, int64_t capacity);
+
+/* The most recent min(cap, recorded, capacity) samples of the control point,
+ * oldest first, as (rho, u_x, u_y) triples (3 doubles each) into `out` (host or
+ * device); *n receives the number of samples written.  Synchronises.
+ * Errors: LBM_ERR_STATE (no probe set), LBM_ERR_INVALID_ARG. */
+lbm_status lbm_probe_read(lbm_ctx *ctx, double *out, int64_t cap, int64_t *n);
 
 /* CUDA-graph replay for lbm_step: runs of `steps_per_graph` steps (an even
  * number >= 2; 0 turns replay off) are captured once per starting buffer into a

@@ -56,6 +56,10 @@ lbm_status lbm_batch_moments(lbm_batch *b, int32_t slot, double *rho, double *ux
 lbm_status lbm_batch_stats(lbm_batch *b, int32_t slot, lbm_step_stats *out);
 lbm_status lbm_batch_limited_sites(lbm_batch *b, int32_t slot, int64_t *idx, int64_t cap, int64_t *n);
 
+/* Control-point record of one lattice: as lbm_probe / lbm_probe_read of lbm.h. */
+lbm_status lbm_batch_probe(lbm_batch *b, int32_t slot, int64_t site, int64_t capacity);
+lbm_status lbm_batch_probe_read(lbm_batch *b, int32_t slot, double *out, int64_t cap, int64_t *n);
+
 /* Advances every lattice of the batch by nsteps limited LBGK steps
  * (asynchronous; statuses surface at the next synchronising call).
  * Errors: LBM_ERR_STATE (a lattice was never initialised), LBM_ERR_CUDA. */

@@ -428,6 +428,24 @@ lbm_status lbm_batch_limited_sites(lbm_batch *b, int32_t slot, int64_t *idx, int
     BATCH_READ(lbm_limited_sites(c, idx, cap, n))
 }
 
+lbm_status lbm_batch_probe(lbm_batch *b, int32_t slot, int64_t site, int64_t capacity)
+{
+    lbm_ctx *c = get(b, slot);
+    if (!c) return bfail(b, LBM_ERR_INVALID_ARG, "no lattice in that slot");
+    invalidate(b);  // the launch tables carry each lattice's tail parameters
+    lbm_status s = enter(b);
+    if (s != LBM_OK) return s;
+    s = lbm_probe(c, site, capacity);
+    lbm_status s2 = leave(b);
+    if (s != LBM_OK) return bfail(b, s, lbm_last_error(c));
+    return s2;
+}
+
+lbm_status lbm_batch_probe_read(lbm_batch *b, int32_t slot, double *out, int64_t cap, int64_t *n)
+{
+    BATCH_READ(lbm_probe_read(c, out, cap, n))
+}
+
 lbm_status lbm_batch_step(lbm_batch *b, int64_t nsteps)
 {
     if (!b) return LBM_ERR_INVALID_ARG;

@@ -441,6 +441,26 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, 
         st.status = (sb & kStatNonfinite) ? 4 : ((sb & kStatTimeout) ? 5 : 0);
         st.reserved = 0;
         p.stats_ring[rec % p.ring_len] = st;
+        if (p.probe != nullptr && p.collide) {
+            // the control point's moments after the whole step (Ehrenfests' writes
+            // are visible: the block synchronised after them), as lbm_moments
+            // evaluates them
+            const int x = p.probe_site % p.nx, y = p.probe_site / p.nx;
+            double g[Q], r, a, b;
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const S v = f[fidx(p.plane, p.pitch, q, y, x)];
+                if constexpr (std::is_same<S, double>::value)
+                    g[q] = v;
+                else
+                    g[q] = Ar<double>::add((double)s2f(v), p.rw[q]);
+            }
+            moments<Q, double>(g, r, a, b);
+            double *slot = p.probe + 3 * ((step - 1) % p.probe_cap);
+            slot[0] = r;
+            slot[1] = a;
+            slot[2] = b;
+        }
         *p.sel_count = s_nsel;
         *p.cand_count = 0;
         if (p.work != nullptr) *p.work = 0;  // the next fused launch starts at its first item

@@ -78,6 +78,9 @@ struct StepParams {
     double a;                  // 2 beta - 1
     double delta_m, delta_e;
     double u_lid;              // lid x-velocity (wall rule of LBM_BC_DIFFUSIVE)
+    double beta;               // LBGK / ELBM relaxation parameter (Eq. elbm)
+    int coll;                  // LBM_COLL_* (ELBM: FP64 entropic path)
+    int phi_rule;              // LBM_PHI_* (LBM_PHI_ENTROPY: FP64 entropic path)
     double lid[9];             // ((6 W_k) rho_wall) (c_kx u_lid), added on links through the lid
     // the same term for FP32 arithmetic as an unevaluated sum hi + lo: adding
     // both parts keeps the rounding of the constant out of every wall step
@@ -131,6 +134,11 @@ struct FinalParams {
     float lidf[9], lidlo[9];
     float rho_ref;
     double rw[9];
+    // control-point record (Sec. 4.4.2): after each step, rho, u_x, u_y of site
+    // probe_site into probe[3 ((step - 1) mod probe_cap) ...]; probe == nullptr: off
+    double *probe;
+    long long probe_cap;
+    int probe_site;
 };
 
 // Arguments of one fused-kernel instance (a lattice, its buffers and its
@@ -250,6 +258,10 @@ struct lbm_ctx {
     cudaEvent_t gev = nullptr;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     long long graph_launches = 0;  // kernel launches one replay performs
+    // control-point record (lbm_probe)
+    double *probe = nullptr;
+    long long probe_cap = 0, probe_alloc = 0, probe_step0 = 0;
+    int probe_site = -1;
     std::string err;
 };
 

@@ -275,6 +275,83 @@ __device__ __forceinline__ double rel_entropy(const double f[Q], const double fs
     return nan ? (double)NAN : s;
 }
 
+// ELBM's alpha (Eq. entropy_estimate, Sec. 4.2): the nontrivial root of
+// S(f + alpha (f* - f)) = S(f), i.e. dS(f) - dS(f + alpha (f* - f)) = 0 with the
+// exact dS of Eq. DelS, by bisection on [1, alpha_max] to a bracket of 1e-15,
+// returning the end where the entropy does not decrease.  alpha_max is the
+// positivity boundary of the line (the smallest f_k / (f_k - f*_k) over
+// f*_k < f_k); where the entropy is still at least S(f) there, no root lies in
+// the positive cone and alpha_max itself is returned (the positivity rule).
+// f = f* gives 2, the LBGK step.  The operations are those of the oracle's
+// bisection; the logarithms are the device's (f_ln_ratio), so the root agrees
+// to the evaluation error of dS.
+template <int Q>
+__device__ double elbm_alpha(const double f[Q], const double fs[Q])
+{
+    using A = Ar<double>;
+    bool same = true;
+#pragma unroll
+    for (int k = 0; k < Q; ++k) same = same && f[k] == fs[k];
+    if (same) return 2.0;
+    double amax = (double)INFINITY;
+#pragma unroll
+    for (int k = 0; k < Q; ++k)
+        if (fs[k] < f[k]) {
+            const double r = A::div(f[k], A::sub(f[k], fs[k]));
+            if (r < amax) amax = r;
+        }
+    const double ds0 = rel_entropy<Q>(f, fs);
+    double g[Q];
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+        g[k] = A::add(f[k], A::mul(amax, A::sub(fs[k], f[k])));
+        if (g[k] < 0.0) g[k] = 0.0;  // the boundary itself: the vanishing population is zero
+    }
+    if (A::sub(ds0, rel_entropy<Q>(g, fs)) >= 0.0) return amax;
+    double lo = 1.0, hi = amax;
+    for (int it = 0; it < 200 && A::sub(hi, lo) > 1e-15; ++it) {
+        const double mid = A::mul(0.5, A::add(lo, hi));
+#pragma unroll
+        for (int k = 0; k < Q; ++k) g[k] = A::add(f[k], A::mul(mid, A::sub(fs[k], f[k])));
+        if (A::sub(ds0, rel_entropy<Q>(g, fs)) >= 0.0)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// Sec. 3.7: the phi in [0, 1] with dS(f* + phi (f' - f*)) = target (Eq. DelS), by
+// bisection to a bracket of 1e-15, returning the lower end; dS along the
+// segment grows from 0 at f*.
+template <int Q>
+__device__ double phi_entropy(const double fp[Q], const double fs[Q], double target)
+{
+    using A = Ar<double>;
+    double g[Q];
+    double lo = 0.0, hi = 1.0;
+    for (int it = 0; it < 200 && A::sub(hi, lo) > 1e-15; ++it) {
+        const double mid = A::mul(0.5, A::add(lo, hi));
+#pragma unroll
+        for (int k = 0; k < Q; ++k) g[k] = A::add(fs[k], A::mul(mid, A::sub(fp[k], fs[k])));
+        if (rel_entropy<Q>(g, fs) <= target)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// Median-filter factor with the solve of Sec. 3.7 (mode and tolerance as phi_median).
+template <int Q>
+__device__ double phi_median_entropy(const double fp[Q], const double fs[Q], double x, double med, double delta,
+                                     int mode)
+{
+    if (mode == 1) return (x > delta && med < x) ? phi_entropy<Q>(fp, fs, med) : 1.0;
+    const double t = med > delta ? med : delta;
+    return x > t ? phi_entropy<Q>(fp, fs, t) : 1.0;
+}
+
 // Quadratic nonequilibrium entropy (Sec. 3.6): sum_k (g_k - f*_k)^2 / f*_k, k order.
 template <int Q, typename T>
 __device__ __forceinline__ T quad_entropy(const T g[Q], const T fs[Q])
@@ -298,7 +375,8 @@ __device__ __forceinline__ T quad_entropy(const T g[Q], const T fs[Q])
 // for a state with a negative population; need_in = false skips dS(f_in).
 template <int Q, typename T>
 __device__ __forceinline__ bool site_collide(const T fin[Q], T a, bool collide, T fs[Q], T fp[Q],
-                                             T &ds, T &ds_in, T &rho, int eq = 0, bool need_in = true)
+                                             T &ds, T &ds_in, T &rho, int eq = 0, bool need_in = true,
+                                             int coll = 0, double beta = 0.0)
 {
     using A = Ar<T>;
     T ux, uy;
@@ -315,6 +393,12 @@ __device__ __forceinline__ bool site_collide(const T fin[Q], T a, bool collide, 
             for (int k = 0; k < Q; ++k) fp[k] = collide ? A::add(fs[k], A::mul(a, A::sub(fs[k], fin[k]))) : fin[k];
 #pragma unroll
             for (int k = 0; k < Q; ++k) bad |= !(fs[k] > 0.0) || !isfinite(fs[k]) || !isfinite(fin[k]);
+            if (coll == 1 && collide && !bad) {
+                // Eq. elbm: f' = (1 - beta) f + beta f~ = f + (beta alpha)(f* - f)
+                const double ba = A::mul(beta, elbm_alpha<Q>(fin, fs));
+#pragma unroll
+                for (int k = 0; k < Q; ++k) fp[k] = A::add(fin[k], A::mul(ba, A::sub(fs[k], fin[k])));
+            }
             ds = bad ? 0.0 : rel_entropy<Q>(fp, fs);
             // dS(f_in) feeds only the statistics: sites that only supply a
             // stencil value (need_in = false) skip it; with finite populations

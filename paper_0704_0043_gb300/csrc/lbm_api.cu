@@ -110,6 +110,14 @@ std::string validate(const lbm_config *c)
         return "entropic quasiequilibria need LBM_FP64 storage";
     if (c->kernel == LBM_KERNEL_FUSED && !fused_applies(*c))
         return "LBM_KERNEL_FUSED needs D2Q9, FP32/BF16/FP16 storage and LBM_BC_WALLS";
+    if (c->collision != LBM_COLL_LBGK && c->collision != LBM_COLL_ELBM) return "unknown collision";
+    if (c->collision == LBM_COLL_ELBM && c->equilibrium != LBM_EQ_ENTROPIC)
+        return "ELBM needs entropic quasiequilibria (LBM_EQ_ENTROPIC, LBM_FP64)";
+    if (c->phi_rule != LBM_PHI_HOMOTHETY && c->phi_rule != LBM_PHI_ENTROPY) return "unknown phi_rule";
+    if (c->phi_rule == LBM_PHI_ENTROPY && c->equilibrium != LBM_EQ_ENTROPIC)
+        return "LBM_PHI_ENTROPY needs entropic quasiequilibria (LBM_EQ_ENTROPIC, LBM_FP64)";
+    if (!(c->entthresh_delta0 >= 0.0) || !std::isfinite(c->entthresh_delta0))
+        return "entthresh_delta0 must be finite and >= 0";
     if (c->stats_history < 0) return "stats_history must be >= 0";
     if (!(c->rho_ref > 0.0) || !std::isfinite(c->rho_ref)) return "rho_ref must be finite and > 0";
     return "";
@@ -219,6 +227,9 @@ FinalParams final_params(lbm_ctx *c, int collide, unsigned limiters, int nblocks
     f.ring_len = c->ring_len;
     f.counters = c->counters;
     f.src = c->buf[c->cur];
+    f.probe = c->probe_site >= 0 ? c->probe : nullptr;
+    f.probe_cap = c->probe_cap;
+    f.probe_site = c->probe_site;
     return f;
 }
 
@@ -366,7 +377,7 @@ void free_all(lbm_ctx *c)
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     c->events.clear();
     void *ptrs[] = {c->buf[0], c->buf[1], c->cand, c->counts, c->sel, c->partials,
-                    c->status, c->ring, c->counters, c->stage, c->ens};
+                    c->status, c->ring, c->counters, c->stage, c->ens, c->probe};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -406,6 +417,9 @@ StepParams cfg_step_params(const lbm_config &g, int q, int pitch, long long plan
     p.delta_m = g.delta_median;
     p.delta_e = g.delta_ehrenfest;
     p.u_lid = g.u_lid;
+    p.beta = g.beta;
+    p.coll = g.collision;
+    p.phi_rule = g.phi_rule;
     for (int k = 0; k < 9; ++k) {
         const bool lid = q == 9 && g.boundary != LBM_BC_PERIODIC && Lat<9>::cy(k) == -1;
         p.lid[k] = lid ? ((6.0 * Lat<9>::w(k)) * g.rho_wall) * ((double)Lat<9>::cx(k) * g.u_lid) : 0.0;
@@ -495,6 +509,9 @@ void lbm_config_default(lbm_config *c)
     c->smooth_k = 0.5;
     c->threshold_c = 10.0;
     c->threshold_delta = 0.0;
+    c->collision = LBM_COLL_LBGK;
+    c->phi_rule = LBM_PHI_HOMOTHETY;
+    c->entthresh_delta0 = 0.1;
 }
 
 int64_t lbm_footprint_bytes(const lbm_config *cfg)
@@ -816,6 +833,66 @@ lbm_status lbm_set_graph(lbm_ctx *c, int32_t steps_per_graph)
         drop_graphs(c);
     }
     c->graph_steps = steps_per_graph;
+    return LBM_OK;
+}
+
+lbm_status lbm_probe(lbm_ctx *c, int64_t site, int64_t capacity)
+{
+    if (!c) return fail(nullptr, LBM_ERR_INVALID_ARG, "ctx is NULL");
+    const long long n = (long long)c->cfg.nx * c->cfg.ny;
+    if (site < -1 || site >= n) return fail(c, LBM_ERR_INVALID_ARG, "site must be -1 or in [0, nx * ny)");
+    if (site >= 0 && capacity < 1) return fail(c, LBM_ERR_INVALID_ARG, "capacity must be >= 1");
+    CK(c, cudaStreamSynchronize(c->stream));
+    drop_graphs(c);  // the graphs carry the tail's parameters
+    if (site < 0) {
+        c->probe_site = -1;
+        return LBM_OK;
+    }
+    if (capacity > c->probe_alloc) {
+        if (c->probe) {
+            cudaFree(c->probe);
+            c->device_bytes -= c->probe_alloc * 3 * (int64_t)sizeof(double);
+            c->probe = nullptr;
+            c->probe_alloc = 0;
+        }
+        CK(c, cudaMalloc((void **)&c->probe, (size_t)capacity * 3 * sizeof(double)));
+        c->probe_alloc = capacity;
+        c->device_bytes += capacity * 3 * (int64_t)sizeof(double);
+    }
+    long long steps = 0;
+    CK(c, cudaMemcpy(&steps, c->counters, sizeof(long long), cudaMemcpyDeviceToHost));
+    c->probe_site = (int)site;
+    c->probe_cap = capacity;
+    c->probe_step0 = steps;
+    return LBM_OK;
+}
+
+lbm_status lbm_probe_read(lbm_ctx *c, double *out, int64_t cap, int64_t *n)
+{
+    if (!c) return fail(nullptr, LBM_ERR_INVALID_ARG, "ctx is NULL");
+    if (!n || cap < 0 || (cap > 0 && !out)) return fail(c, LBM_ERR_INVALID_ARG, "bad output arguments");
+    *n = 0;
+    if (c->probe_site < 0) return fail(c, LBM_ERR_STATE, "no probe set (lbm_probe)");
+    long long steps = 0;
+    CK(c, cudaMemcpyAsync(&steps, c->counters, sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    const long long have = std::min<long long>(steps - c->probe_step0, c->probe_cap);
+    const long long take = std::min<long long>(std::max<long long>(have, 0), cap);
+    std::vector<double> ring((size_t)c->probe_cap * 3);
+    if (take > 0) CK(c, cudaMemcpy(ring.data(), c->probe, ring.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    std::vector<double> w((size_t)take * 3);
+    for (long long i = 0; i < take; ++i) {
+        const long long st = steps - take + 1 + i;  // step numbers, oldest first
+        const long long slot = (st - 1) % c->probe_cap;
+        for (int j = 0; j < 3; ++j) w[(size_t)(3 * i + j)] = ring[(size_t)(3 * slot + j)];
+    }
+    if (take > 0) {
+        if (is_device_ptr(out))
+            CK(c, cudaMemcpy(out, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice));
+        else
+            std::memcpy(out, w.data(), w.size() * sizeof(double));
+    }
+    *n = take;
     return LBM_OK;
 }
 

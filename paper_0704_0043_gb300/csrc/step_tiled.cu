@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const S *__r
         if constexpr (std::is_same<T, double>::value) {
             // entropic f*: the halo ring only supplies dS(f') to the median stencils
             const bool owner = tx >= 1 && tx <= BX - 2 && (Q == 3 || (ty >= 1 && ty <= BY - 2));
-            bad = site_collide<Q, T>(fin, T(p.a), p.collide != 0, fs, fp, ds, dsin, rho, p.eq, owner);
+            bad = site_collide<Q, T>(fin, T(p.a), p.collide != 0, fs, fp, ds, dsin, rho, p.eq, owner, p.coll, p.beta);
 #pragma unroll
             for (int k = 0; k < Q; ++k) fa[k] = fs[k];
         } else {
@@ -369,8 +369,16 @@ __global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const S *__r
                 dm = kc[0];
             if ((p.limiters & 4u) && ds > dm) {
                 T med;
-                if (stencil_median<Q, T>(p, sds, BX, tx, ty, x, y, med))
-                    phi_med = phi_median<T>(ds, med, dm, p.median_mode);
+                if (stencil_median<Q, T>(p, sds, BX, tx, ty, x, y, med)) {
+                    if constexpr (std::is_same<T, double>::value) {
+                        // entropic f* with the solve of Sec. 3.7, else the homothety
+                        phi_med = (p.phi_rule == 1 && p.eq == 1)
+                                      ? phi_median_entropy<Q>(fp, fs, ds, med, dm, p.median_mode)
+                                      : phi_median<T>(ds, med, dm, p.median_mode);
+                    } else {
+                        phi_med = phi_median<T>(ds, med, dm, p.median_mode);
+                    }
+                }
             }
         }
         T phi = phi_pos < phi_med ? phi_pos : phi_med;
@@ -389,7 +397,7 @@ __global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const S *__r
                     double t = p.threshold_c * E;
                     if (t < p.threshold_delta) t = p.threshold_delta;
                     if (ds > t) {
-                        const double pt = sqrt(t / ds);
+                        const double pt = (p.phi_rule == 1 && p.eq == 1) ? phi_entropy<Q>(fp, fs, t) : sqrt(t / ds);
                         if (pt < pe) pe = pt;
                     }
                 }
@@ -575,7 +583,7 @@ __global__ void __launch_bounds__(256) k_ens_partial(StepParams p, const S *__re
             for (int k = 0; k < Q; ++k) fin[k] = load_as<S, T>(p, src[fidx(p.plane, p.pitch, k, y, x)], k);
         }
         if constexpr (std::is_same<T, double>::value) {
-            bad = site_collide<Q, T>(fin, T(p.a), p.collide != 0, fs, fp, ds, dsin, rho, p.eq, false);
+            bad = site_collide<Q, T>(fin, T(p.a), p.collide != 0, fs, fp, ds, dsin, rho, p.eq, false, p.coll, p.beta);
         } else {
             bad = site_collide_dev<Q>(fin, (float)p.a, (float)(1.0 + p.a), p.collide != 0, p.rho_ref, p.rwf, fs, nq,
                                       fp, fa, ds, dsin, rho);
@@ -652,7 +660,7 @@ __global__ void k_delta_s(StepParams p, const S *__restrict__ f, double *__restr
         }
         double fin[Q], fs[Q], fp[Q], ds, dsin, rho;
         pull<Q, S, double>(p, f, x, y, fin);
-        const bool bad = site_collide<Q, double>(fin, p.a, true, fs, fp, ds, dsin, rho, p.eq);
+        const bool bad = site_collide<Q, double>(fin, p.a, true, fs, fp, ds, dsin, rho, p.eq, true, p.coll, p.beta);
         out[s] = bad ? (double)INFINITY : ds;
     }
 }

@@ -24,6 +24,8 @@ LIM_POSITIVITY, LIM_EHRENFEST, LIM_MEDIAN, LIM_SMOOTH, LIM_THRESHOLD = 1, 2, 4, 
 MEDIAN_THRESHOLD, MEDIAN_GATE = 0, 1
 EQ_POLYNOMIAL, EQ_ENTROPIC = 0, 1
 KERNEL_AUTO, KERNEL_TILED, KERNEL_FUSED = 0, 1, 2
+COLL_LBGK, COLL_ELBM = 0, 1
+PHI_HOMOTHETY, PHI_ENTROPY = 0, 1
 
 OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_STATE = range(7)
 
@@ -37,7 +39,8 @@ class Config(ctypes.Structure):
         ("delta_ehrenfest", ctypes.c_double), ("k_max", ctypes.c_int64),
         ("stats_history", ctypes.c_int32), ("equilibrium", ctypes.c_int32), ("rho_ref", ctypes.c_double),
         ("smooth_delta", ctypes.c_double), ("smooth_k", ctypes.c_double), ("threshold_c", ctypes.c_double),
-        ("threshold_delta", ctypes.c_double),
+        ("threshold_delta", ctypes.c_double), ("collision", ctypes.c_int32), ("phi_rule", ctypes.c_int32),
+        ("entthresh_delta0", ctypes.c_double),
     ]
 
 
@@ -108,6 +111,10 @@ def lib():
         L.lbm_status_string.argtypes = [ctypes.c_int]
         L.lbm_status_string.restype = ctypes.c_char_p
         L.lbm_abi_version.restype = ctypes.c_int32
+        L.lbm_probe.argtypes = [vp, ctypes.c_int64, ctypes.c_int64]
+        L.lbm_probe.restype = ctypes.c_int
+        L.lbm_probe_read.argtypes = [vp, vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
+        L.lbm_probe_read.restype = ctypes.c_int
         L.lbm_set_graph.argtypes = [vp, ctypes.c_int32]
         L.lbm_set_graph.restype = ctypes.c_int
         L.lbm_step_noalloc.argtypes = [cfgp, vp, vp, ctypes.POINTER(StepStats), vp]
@@ -127,6 +134,8 @@ def lib():
             "lbm_batch_set_shape": [vp, ctypes.c_int32, ctypes.c_int32],
             "lbm_batch_lattice_status": [vp, ctypes.c_int32],
             "lbm_batch_tune": [vp, ctypes.c_int32, dp],
+            "lbm_batch_probe": [vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64],
+            "lbm_batch_probe_read": [vp, ctypes.c_int32, vp, ctypes.c_int64, i64p],
         }
         for name, args in batch_sigs.items():
             getattr(L, name).argtypes = args
@@ -336,6 +345,18 @@ class Lattice:
     def synchronize(self):
         _check(lib().lbm_synchronize(self._h), self._h)
 
+    def probe(self, site: int, capacity: int = 1):
+        """Record rho, u_x, u_y of `site` (j * nx + i) after every step (ring of
+        `capacity` samples); site = -1 stops."""
+        _check(lib().lbm_probe(self._h, int(site), int(capacity)), self._h)
+
+    def probe_read(self, cap: int) -> np.ndarray:
+        """The most recent samples of the control point, oldest first: (n, 3) array."""
+        out = np.zeros((max(1, cap), 3))
+        n = ctypes.c_int64()
+        _check(lib().lbm_probe_read(self._h, out.ctypes.data, int(cap), ctypes.byref(n)), self._h)
+        return out[:n.value].copy()
+
     def set_graph(self, steps_per_graph: int):
         """CUDA-graph replay of runs of steps_per_graph steps (even, >= 2; 0 = off)."""
         _check(lib().lbm_set_graph(self._h, int(steps_per_graph)), self._h)
@@ -459,6 +480,17 @@ class Batch:
 
     def set_graph(self, steps_per_graph: int):
         _bcheck(lib().lbm_batch_set_graph(self._h, int(steps_per_graph)), self._h)
+
+    def probe(self, slot: int, site: int, capacity: int = 1):
+        """Record rho, u_x, u_y of `site` of lattice `slot` after every step."""
+        _bcheck(lib().lbm_batch_probe(self._h, int(slot), int(site), int(capacity)), self._h)
+
+    def probe_read(self, slot: int, cap: int) -> np.ndarray:
+        out = np.zeros((max(1, cap), 3))
+        n = ctypes.c_int64()
+        _bcheck(lib().lbm_batch_probe_read(self._h, int(slot), out.ctypes.data, int(cap), ctypes.byref(n)),
+                self._h)
+        return out[:n.value].copy()
 
     def set_shape(self, seg_rows: int = 0, waves: int = 1):
         """Fused work split: rows per work item (0: automatic, else >= 16), 1 / 2 / 4 waves."""

@@ -57,7 +57,7 @@ def test_config_validation_without_gpu(lib):
 
 def test_abi_version_and_status_names(lib):
     lib.lbm_abi_version.restype = ctypes.c_int32
-    assert lib.lbm_abi_version() == 2
+    assert lib.lbm_abi_version() == 3
     lib.lbm_status_string.restype = ctypes.c_char_p
     assert lib.lbm_status_string(4) == b"LBM_ERR_NONFINITE"
 
