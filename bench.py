@@ -60,7 +60,7 @@ def parse():
                          "(default: the 4096^2 cavity's full 1e4 steps; 0 for the small workloads)")
     ap.add_argument("--kernel", default="auto", choices=["auto", "tiled", "fused"])
     ap.add_argument("--limiters", default="median+ehrenfest",
-                    choices=["median+ehrenfest", "smooth+ehrenfest", "threshold+ehrenfest"],
+                    choices=["median+ehrenfest", "smooth+ehrenfest", "threshold+ehrenfest", "entthresh+ehrenfest"],
                     help="smooth / threshold: the ensemble-dependent limiters (tiled kernel, E(dS) reduction first)")
     ap.add_argument("--equilibrium", default="polynomial", choices=["polynomial", "entropic"],
                     help="entropic: Eq. maxwellian f* with the exact dS of Eq. DelS (needs --precision fp64)")
@@ -578,7 +578,9 @@ def single_workload(args, lbm, inputs):
     w = workload(args.side)
     if args.limiters != "median+ehrenfest":
         # Eq. smooth1 with k = 1/2, delta = 0.01, or the threshold filter with dS_t = 10 E(dS)
-        w.limiters = (lbm.LIM_SMOOTH if args.limiters.startswith("smooth") else lbm.LIM_THRESHOLD) | lbm.LIM_EHRENFEST
+        # or Eq. EntThresh's dS_0 with delta_0 = 0.1
+        kind = {"smooth": lbm.LIM_SMOOTH, "threshold": lbm.LIM_THRESHOLD, "entthresh": lbm.LIM_ENTTHRESH}
+        w.limiters = kind[args.limiters.split("+")[0]] | lbm.LIM_EHRENFEST
         w.name = w.name + "_" + args.limiters.split("+")[0]
     if args.equilibrium == "entropic":
         if args.precision != "fp64":
@@ -685,6 +687,8 @@ def main():
         # the pass first reads every population once more for E(dS) (k_ens_partial);
         # the library's events bracket that reduction and the step kernel together
         bps += bps // 2
+        if args.limiters.startswith("entthresh"):
+            bps += 8  # Eq. EntThresh: the dS field written once and read once (FP32)
     if timed:
         kern_s = step_ms / 1e3 / timed
     else:  # graph replay: the whole step (step kernel + tail) from the run's own events
@@ -702,7 +706,8 @@ def main():
         roof["note"] = ("the lattice lives in L2 (%.1f MB of populations); the step is launch- and "
                         "latency-bound, so this fraction is no HBM claim" % (w.sites * bps / 1e6))
     if ensemble:
-        roof["kernel"] = "k_ens_partial + k_ens_mean + k_tiled"
+        roof["kernel"] = ("k_ens_partial + k_ens_mean + EntThresh solve + k_tiled" if args.limiters.startswith("entthresh")
+                          else "k_ens_partial + k_ens_mean + k_tiled")
         roof["traffic"] = traffic_from_profile("tiled_fp32_ensemble", w.sites)
 
     if entropic:

@@ -95,10 +95,20 @@ enum {
  *     with the ensemble-dependent alpha of Sec. 4.3.2); phi = 1 where E <= 0 or dS = 0.
  *   LBM_LIM_THRESHOLD: dS_t = max(threshold_c E, threshold_delta); phi = sqrt(dS_t / dS)
  *     where dS > dS_t (Sec. 3.4, Eq. entrHom, with dS_0 = c E as in Sec. 4.3.2).
- * Every limiter's phi is combined as the minimum, before Ehrenfests' step.  The two
- * ensemble limiters run on the tiled kernel (not in batches, not in lbm_step_noalloc). */
+ * Every limiter's phi is combined as the minimum, before Ehrenfests' step.  The
+ * ensemble limiters (these two and LBM_LIM_ENTTHRESH) run on the tiled kernel (not in
+ * batches, not in lbm_step_noalloc). */
 enum { LBM_LIM_POSITIVITY = 1, LBM_LIM_EHRENFEST = 2, LBM_LIM_MEDIAN = 4, LBM_LIM_SMOOTH = 8,
-       LBM_LIM_THRESHOLD = 16 };
+       LBM_LIM_THRESHOLD = 16, LBM_LIM_ENTTHRESH = 32 };
+/* LBM_LIM_ENTTHRESH: the threshold filter with dS_0 from Eq. EntThresh, solved on the
+ *   pass's own distribution of dS (the sites E(dS) is taken over):
+ *   sum_s max(dS_s - dS_0, 0) = entthresh_delta0 (1 - (2 beta - 1)^2) sum_s dS_s, so that the
+ *   limiter's entropy production stays within delta_0 of LBGK's (Eq. LimEntLim);
+ *   dS_t = max(dS_0, threshold_delta), phi = sqrt(dS_t / dS) where dS > dS_t (or the solve
+ *   of LBM_PHI_ENTROPY).  dS_0 is found exactly by a radix descent over the bit patterns
+ *   of the dS field (dS_0 = +inf when the right side is 0: nothing is limited); its sums
+ *   are added by atomics, so it is reproducible to rounding.  Needs the bit at create
+ *   (the field is allocated then); tiled kernel; not in batches or lbm_step_noalloc. */
 
 /* Median-filter acceptance rule (Sec. 3.5 with the tolerance of Sec. 4.3.2). */
 enum {

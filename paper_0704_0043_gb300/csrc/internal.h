@@ -27,6 +27,26 @@ __host__ __device__ inline bool bc_wrap_x(int b) { return b == 1 || b == 2; }
 __host__ __device__ inline bool bc_wrap_y(int b) { return b == 1; }
 __host__ __device__ inline bool bc_node_walls(int b) { return b == 3 || b == 4; }
 
+// Ensemble-dependent limiter bits (LBM_LIM_SMOOTH | LBM_LIM_THRESHOLD |
+// LBM_LIM_ENTTHRESH): a pass with any of them first reduces dS over the lattice.
+constexpr unsigned kLimEnsemble = 8u | 16u | 32u;
+
+// State of the device solve of Eq. EntThresh (entthresh.cu): a radix descent
+// over the bit patterns of the pass's dS field, 8 bits a level, keeping
+// prefix (the determined high bits of the bin that holds dS_0), and the count
+// and sum of the values above that bin.
+struct EntState {
+    double rhs;                  // delta_0 (1 - (2 beta - 1)^2) sum dS
+    double s_above;              // sum of the values above the current bin
+    unsigned long long m_above;  // their count
+    unsigned long long prefix;   // determined high bits (in place)
+    double t;                    // result: dS_t = max(dS_0, threshold_delta)
+    int done;                    // the solve ended early (no value, rhs <= 0, or dS_0 = 0)
+    int pad;
+    unsigned long long cnt[256];  // histogram of the current level: counts
+    double sum[256];              // and sums
+};
+
 // Sticky device status bits.
 enum : unsigned { kStatNonfinite = 1u, kStatTimeout = 2u, kStatCandOverflow = 4u };
 
@@ -99,7 +119,9 @@ struct StepParams {
     double *ds_out;            // optional FP64 dS(f') field (nx * ny) or nullptr
     // ensemble-dependent limiters (LBM_LIM_SMOOTH / LBM_LIM_THRESHOLD)
     double smooth_delta, smooth_k, threshold_c, threshold_delta;
-    const double *ens;         // {E(dS), smooth_delta / E^smooth_k} of this pass (the ensemble reduction)
+    const double *ens;         // {E(dS), smooth_delta / E^smooth_k, sum dS, count} of this pass (the ensemble reduction)
+    void *ent_field;           // LBM_LIM_ENTTHRESH: dS of every site (compute type; 0 where excluded)
+    EntState *ent;             // LBM_LIM_ENTTHRESH: the solve's state; ent->t is the pass's dS_t
 };
 
 struct FinalParams {
@@ -190,6 +212,12 @@ cudaError_t launch_delta_s(int q, const StepParams &p, const T *f, double *out, 
 constexpr int kEnsBlocks = 608;
 template <typename T>
 cudaError_t launch_ens_mean(int q, const StepParams &p, const T *src, double *ens, cudaStream_t s);
+// Eq. EntThresh on the field p.ent_field (filled by the ensemble reduction):
+// p.ent->t = max(dS_0, threshold_delta).  T is the compute type of the field.
+template <typename T>
+cudaError_t launch_entthresh(const StepParams &p, double delta0, long long n, cudaStream_t s);
+// launches of one EntThresh solve (for the launch count)
+int entthresh_launches(bool fp64);
 
 // Sets the calling thread's error message (read by lbm_last_error(NULL)); returns s.
 int set_thread_error_impl(int s, const char *msg);
@@ -229,7 +257,9 @@ struct lbm_ctx {
     int cur = 0;
     lbm::Cand *cand = nullptr;
     int cand_cap = 0;
-    double *ens = nullptr;  // [kEnsBlocks][2] partial sums and counts of dS, then E(dS)
+    double *ens = nullptr;  // [kEnsBlocks][2] partial sums and counts of dS, then E(dS), alpha, sum, count
+    void *ent_field = nullptr;   // LBM_LIM_ENTTHRESH: the pass's dS field
+    lbm::EntState *ent = nullptr;  // LBM_LIM_ENTTHRESH: solve state
     int *counts = nullptr;  // [0] candidate count, [1] chosen count, [2] fused work items handed out, [3] unused
     int *sel = nullptr;
     int sel_cap = 0;

@@ -63,7 +63,7 @@ cudaError_t with_storage(int precision, F &&fn)
 bool fused_applies(const lbm_config &c)
 {
     return c.lattice == LBM_D2Q9 && c.precision != LBM_FP64 && c.boundary == LBM_BC_WALLS &&
-           (c.limiters & (LBM_LIM_SMOOTH | LBM_LIM_THRESHOLD)) == 0 &&
+           (c.limiters & kLimEnsemble) == 0 &&
            c.kernel != LBM_KERNEL_TILED && fused_d2q9_fits((long long)c.ny * row_pitch(c.nx));
 }
 
@@ -93,7 +93,7 @@ std::string validate(const lbm_config *c)
             return "D2Q9 cavity with boundary nodes needs nx, ny >= 5";
         if (c->boundary == LBM_BC_CHANNEL && c->ny < 2) return "D2Q9 channel needs ny >= 2";
     }
-    if (c->limiters & ~31u) return "unknown limiter bits";
+    if (c->limiters & ~63u) return "unknown limiter bits";
     if (!(c->smooth_delta >= 0.0) || !std::isfinite(c->smooth_delta)) return "smooth_delta must be finite and >= 0";
     if (!(c->smooth_k > 0.0) || !std::isfinite(c->smooth_k)) return "smooth_k must be finite and > 0";
     if (!(c->threshold_c >= 0.0) || !std::isfinite(c->threshold_c)) return "threshold_c must be finite and >= 0";
@@ -123,16 +123,17 @@ std::string validate(const lbm_config *c)
     return "";
 }
 
-size_t ens_bytes() { return (2 * (size_t)kEnsBlocks + 2) * sizeof(double); }
+size_t ens_bytes() { return (2 * (size_t)kEnsBlocks + 4) * sizeof(double); }
 
 struct Sizes {
     int q, pitch;
     long long plane;
-    size_t elem, field, cand, sel, partials, ring;
+    size_t elem, field, cand, sel, partials, ring, ent;
     int cand_cap, sel_cap, rows, ring_len;
     int64_t total() const
     {
-        return (int64_t)(2 * field + cand + sel + partials + ring + ens_bytes() + 64 * sizeof(long long) + 4096);
+        return (int64_t)(2 * field + cand + sel + partials + ring + ens_bytes() + ent + 64 * sizeof(long long) +
+                         4096);
     }
 };
 
@@ -155,6 +156,10 @@ Sizes sizes_for(const lbm_config &c)
         z.partials = std::max(z.partials, (size_t)kFxRows * kFxWords * sizeof(unsigned long long));
     z.ring_len = std::max(1, c.stats_history);
     z.ring = (size_t)z.ring_len * sizeof(DevStats);
+    // Eq. EntThresh: the pass's dS field (compute precision) and the solve's state
+    z.ent = (c.limiters & LBM_LIM_ENTTHRESH)
+                ? (size_t)n * (c.precision == LBM_FP64 ? sizeof(double) : sizeof(float)) + sizeof(EntState)
+                : 0;
     return z;
 }
 
@@ -208,6 +213,8 @@ StepParams step_params(lbm_ctx *c, int collide, unsigned limiters)
     p.status = c->status;
     p.work = c->counts + 2;
     p.ens = c->ens + 2 * kEnsBlocks;
+    p.ent_field = (limiters & LBM_LIM_ENTTHRESH) ? c->ent_field : nullptr;
+    p.ent = c->ent;
     return p;
 }
 
@@ -268,7 +275,7 @@ lbm_status run_pass(lbm_ctx *c, int collide, unsigned limiters)
     cudaError_t e;
     void *src = c->buf[c->cur], *dst = c->buf[c->cur ^ 1];
     const bool fused = collide && fused_applies(c->cfg);
-    if (limiters & (LBM_LIM_SMOOTH | LBM_LIM_THRESHOLD)) {
+    if (limiters & kLimEnsemble) {
         // E(dS) of this pass, before any site is limited
         e = with_storage(c->cfg.precision, [&](auto tag) -> cudaError_t {
             using S = STORAGE_T;
@@ -276,6 +283,15 @@ lbm_status run_pass(lbm_ctx *c, int collide, unsigned limiters)
         });
         if (e != cudaSuccess) return cuda_fail(c, e, "ensemble reduction launch");
         c->launches += 2;
+        if (limiters & LBM_LIM_ENTTHRESH) {
+            // dS_0 of Eq. EntThresh on the field the reduction wrote
+            const long long n = (long long)c->cfg.nx * c->cfg.ny;
+            const bool fp64 = c->cfg.precision == LBM_FP64;
+            e = fp64 ? launch_entthresh<double>(p, c->cfg.entthresh_delta0, n, c->stream)
+                     : launch_entthresh<float>(p, c->cfg.entthresh_delta0, n, c->stream);
+            if (e != cudaSuccess) return cuda_fail(c, e, "EntThresh launch");
+            c->launches += entthresh_launches(fp64);
+        }
     }
     e = with_storage(c->cfg.precision, [&](auto tag) -> cudaError_t {
         using S = STORAGE_T;
@@ -377,7 +393,7 @@ void free_all(lbm_ctx *c)
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     c->events.clear();
     void *ptrs[] = {c->buf[0], c->buf[1], c->cand, c->counts, c->sel, c->partials,
-                    c->status, c->ring, c->counters, c->stage, c->ens, c->probe};
+                    c->status, c->ring, c->counters, c->stage, c->ens, c->probe, c->ent_field, c->ent};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -561,6 +577,10 @@ lbm_status lbm_create(const lbm_config *cfg, void *cuda_stream, lbm_ctx **out)
     alloc((void **)&c->ring, z.ring);
     alloc((void **)&c->counters, 2 * sizeof(long long));
     alloc((void **)&c->ens, ens_bytes());
+    if (z.ent) {
+        alloc(&c->ent_field, z.ent - sizeof(EntState));
+        alloc((void **)&c->ent, sizeof(EntState));
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -639,10 +659,12 @@ lbm_status lbm_step(lbm_ctx *c, int64_t nsteps)
 lbm_status lbm_limit(lbm_ctx *c, uint32_t limiters)
 {
     if (!c) return fail(nullptr, LBM_ERR_INVALID_ARG, "ctx is NULL");
-    if (limiters & ~31u) return fail(c, LBM_ERR_INVALID_ARG, "unknown limiter bits");
+    if (limiters & ~63u) return fail(c, LBM_ERR_INVALID_ARG, "unknown limiter bits");
     if (!c->ready) return fail(c, LBM_ERR_STATE, "lbm_limit before lbm_init / lbm_set_populations");
     if ((limiters & LBM_LIM_EHRENFEST) && c->cand_cap < c->cfg.nx * c->cfg.ny)
         return fail(c, LBM_ERR_INVALID_ARG, "Ehrenfests' limiter needs LBM_LIM_EHRENFEST in the config at create");
+    if ((limiters & LBM_LIM_ENTTHRESH) && !c->ent)
+        return fail(c, LBM_ERR_INVALID_ARG, "LBM_LIM_ENTTHRESH needs the bit in the config at create");
     return run_pass(c, 0, limiters);
 }
 

@@ -89,7 +89,7 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_config *cfg, const double *f_in
     if (cfg->precision != LBM_FP64)
         return set_thread_error(LBM_ERR_INVALID_ARG, "lbm_step_noalloc: needs precision LBM_FP64");
     if (lbm_footprint_bytes(cfg) == 0) return LBM_ERR_INVALID_ARG;  // validates cfg, message already set
-    if (cfg->limiters & (LBM_LIM_SMOOTH | LBM_LIM_THRESHOLD))
+    if (cfg->limiters & kLimEnsemble)
         return set_thread_error(LBM_ERR_INVALID_ARG, "lbm_step_noalloc: no ensemble-dependent limiters");
     const long long sites = (long long)cfg->nx * cfg->ny;
     if (sites > LBM_NOALLOC_MAX_SITES)

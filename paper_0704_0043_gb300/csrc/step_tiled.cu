@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const S *__r
     // recording threshold, kc[2] = 2 beta - 1, kc[3] = alpha of the smooth
     // limiter, kc[4] = dS_t rounded down (for a float dS, dS > kc[4] exactly when
     // (double) dS > dS_t), kc[5] = smooth_k; ke: E > 0, k = 1/2, thresholds on
-    __shared__ float kc[6];
+    __shared__ float kc[7];
     __shared__ int ke[3];
     if constexpr (!std::is_same<T, double>::value) {
         if (tx == 0 && ty == 0) {
@@ -319,6 +319,8 @@ __global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const S *__r
             kc[1] = (float)(p.delta_e * (1.0 - 1.0 / 64.0));
             kc[2] = (float)p.a;
             const double E = (p.limiters & 24u) ? p.ens[0] : 0.0;
+            // Eq. EntThresh's dS_t rounded down (for a float dS, dS > kc[6] exactly when (double) dS > dS_t)
+            kc[6] = (p.limiters & 32u) ? __double2float_rd(p.ent->t) : 0.f;
             double t = p.threshold_c * E;
             if (t < p.threshold_delta) t = p.threshold_delta;
             kc[3] = (p.limiters & 24u) ? (float)p.ens[1] : 0.f;
@@ -382,7 +384,7 @@ __global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const S *__r
             }
         }
         T phi = phi_pos < phi_med ? phi_pos : phi_med;
-        if (!bad && (p.limiters & 24u)) {
+        if (!bad && (p.limiters & kLimEnsemble)) {
             // ensemble-dependent limiters: ens = {E(dS), alpha = delta / E^k} of this pass
             T pe = T(1);
             if constexpr (std::is_same<T, double>::value) {
@@ -391,6 +393,12 @@ __global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const S *__r
                     // Eq. smooth1 (Sec. 4.3.2); k = 1/2 by a square root
                     const double pk = p.smooth_k == 0.5 ? sqrt(ds) : pow(ds, p.smooth_k);
                     pe = 1.0 / (1.0 + p.ens[1] * pk);
+                }
+                if ((p.limiters & 32u) && ds > p.ent->t) {
+                    // Eq. EntThresh's dS_t (Sec. 3.4), homothety or the solve of Sec. 3.7
+                    const double t = p.ent->t;
+                    const double pt = (p.phi_rule == 1 && p.eq == 1) ? phi_entropy<Q>(fp, fs, t) : sqrt(t / ds);
+                    if (pt < pe) pe = pt;
                 }
                 if (p.limiters & 16u) {
                     // threshold filter: dS_t = max(c E, delta), homothety where dS > dS_t (Sec. 3.4)
@@ -405,6 +413,11 @@ __global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const S *__r
                 if ((p.limiters & 8u) && ke[0] && ds > 0.f) {
                     const float pk = ke[1] ? sqrtf(ds) : powf(ds, kc[5]);
                     pe = 1.0f / (1.0f + kc[3] * pk);
+                }
+                if ((p.limiters & 32u) && ds > kc[6]) {
+                    // rare: Eq. EntThresh's exact dS_t at the limited site
+                    const float pt = (float)sqrt(p.ent->t / (double)ds);
+                    if (pt < pe) pe = pt;
                 }
                 if (ke[2] && ds > kc[4]) {
                     // rare: the exact dS_t of the limited site
@@ -571,7 +584,10 @@ __global__ void __launch_bounds__(256) k_ens_partial(StepParams p, const S *__re
     int icnt = 0;
     for (long long s = blockIdx.x * 256LL + threadIdx.x; s < n; s += (long long)gridDim.x * 256) {
         const int x = (int)(s % p.nx), y = (int)(s / p.nx);
-        if (Q == 9 && is_wall_node(p, x, y)) continue;  // boundary nodes are not collided
+        if (Q == 9 && is_wall_node(p, x, y)) {  // boundary nodes are not collided
+            if (p.ent_field) ((T *)p.ent_field)[s] = T(0);
+            continue;
+        }
         T fin[Q], fs[Q], fp[Q], fa[Q];
         float nq[Q];
         T ds, dsin, rho;
@@ -599,6 +615,8 @@ __global__ void __launch_bounds__(256) k_ens_partial(StepParams p, const S *__re
                 icnt += 1;
             }
         }
+        // Eq. EntThresh works on the same values (0 where the site is left out)
+        if (p.ent_field) ((T *)p.ent_field)[s] = (!bad && isfinite(ds) && ds > T(0)) ? ds : T(0);
     }
     if constexpr (!std::is_same<T, double>::value) {
         sum = (double)fsum;
@@ -645,6 +663,8 @@ __global__ void __launch_bounds__(256) k_ens_mean(const double *__restrict__ par
         const double E = c > 0.0 ? s / c : 0.0;
         out[0] = E;
         out[1] = E > 0.0 ? smooth_delta / pow(E, smooth_k) : 0.0;  // alpha of Eq. smooth1
+        out[2] = s;  // sum and count (Eq. EntThresh's right side)
+        out[3] = c;
     }
 }
 

@@ -20,7 +20,7 @@ from . import build as _build
 D1Q3, D2Q9 = 1, 2
 FP64, FP32, BF16, FP16 = 0, 1, 2, 3
 BC_WALLS, BC_PERIODIC, BC_CHANNEL, BC_NODE_WALLS, BC_DIFFUSIVE = 0, 1, 2, 3, 4
-LIM_POSITIVITY, LIM_EHRENFEST, LIM_MEDIAN, LIM_SMOOTH, LIM_THRESHOLD = 1, 2, 4, 8, 16
+LIM_POSITIVITY, LIM_EHRENFEST, LIM_MEDIAN, LIM_SMOOTH, LIM_THRESHOLD, LIM_ENTTHRESH = 1, 2, 4, 8, 16, 32
 MEDIAN_THRESHOLD, MEDIAN_GATE = 0, 1
 EQ_POLYNOMIAL, EQ_ENTROPIC = 0, 1
 KERNEL_AUTO, KERNEL_TILED, KERNEL_FUSED = 0, 1, 2

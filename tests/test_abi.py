@@ -39,7 +39,7 @@ def test_config_validation_without_gpu(lib):
            dict(precision=7), dict(delta_median=-1.0), dict(median_mode=5),
            dict(kernel=lbm.KERNEL_FUSED, precision=lbm.FP64),
            dict(equilibrium=2), dict(equilibrium=lbm.EQ_ENTROPIC),
-           dict(equilibrium=lbm.EQ_ENTROPIC, precision=lbm.BF16), dict(limiters=32),
+           dict(equilibrium=lbm.EQ_ENTROPIC, precision=lbm.BF16), dict(limiters=128),
            dict(smooth_k=0.0), dict(smooth_delta=-1.0), dict(threshold_c=float("nan")),
            dict(threshold_delta=-1e-3), dict(limiters=lbm.LIM_SMOOTH, kernel=lbm.KERNEL_FUSED)]
     for b in bad:
