@@ -63,7 +63,7 @@ def parse():
                     choices=["median+ehrenfest", "smooth+ehrenfest", "threshold+ehrenfest", "entthresh+ehrenfest"],
                     help="smooth / threshold: the ensemble-dependent limiters (tiled kernel, E(dS) reduction first)")
     ap.add_argument("--equilibrium", default="polynomial", choices=["polynomial", "entropic"],
-                    help="entropic: Eq. maxwellian f* with the exact dS of Eq. DelS (needs --precision fp64)")
+                    help="entropic: Eq. maxwellian f* with the exact dS of Eq. DelS")
     ap.add_argument("--precision", default=None, choices=["fp32", "bf16", "fp16", "fp64"],
                     help="population storage (FP32 arithmetic for the 32- and 16-bit forms); default "
                          "fp32, fp64 for the shock tube")
@@ -583,8 +583,6 @@ def single_workload(args, lbm, inputs):
         w.limiters = kind[args.limiters.split("+")[0]] | lbm.LIM_EHRENFEST
         w.name = w.name + "_" + args.limiters.split("+")[0]
     if args.equilibrium == "entropic":
-        if args.precision != "fp64":
-            raise SystemExit("--equilibrium entropic needs --precision fp64")
         w.name = w.name.replace("cavity_d2q9", "cavity_d2q9_entropic")
     return w, lattice_kwargs(w, args.kernel, args.precision, args.equilibrium), "d2q9", args.precision
 
@@ -706,11 +704,11 @@ def main():
         roof["note"] = ("the lattice lives in L2 (%.1f MB of populations); the step is launch- and "
                         "latency-bound, so this fraction is no HBM claim" % (w.sites * bps / 1e6))
     if ensemble:
-        roof["kernel"] = ("k_ens_partial + k_ens_mean + EntThresh solve + k_tiled" if args.limiters.startswith("entthresh")
-                          else "k_ens_partial + k_ens_mean + k_tiled")
+        roof["kernel"] = "k_ens_partial + k_ens_mean + " + ("EntThresh solve + " if args.limiters.startswith("entthresh")
+                                                               else "") + ("k_fused" if kname == "fused" else "k_tiled")
         roof["traffic"] = traffic_from_profile("tiled_fp32_ensemble", w.sites)
 
-    if entropic:
+    if entropic and prec == "fp64":
         # The entropic step is bound by FP64 arithmetic (a logarithm per population
         # and sqrt / divisions for f*), not by HBM: the roofline is the FP64 pipe
         # (152 SMs x 2 FP64 FMA per clock x 2 FLOP at the sampled SM clock), and

@@ -327,6 +327,8 @@ lbm_status lbm_batch_add(lbm_batch *b, const lbm_config *cfg, int32_t *slot)
 {
     if (!b || !cfg || !slot) return bfail(b, LBM_ERR_INVALID_ARG, "NULL argument");
     if (cfg->precision != LBM_FP32) return bfail(b, LBM_ERR_INVALID_ARG, "batched lattices use LBM_FP32");
+    if (cfg->equilibrium != LBM_EQ_POLYNOMIAL)
+        return bfail(b, LBM_ERR_INVALID_ARG, "batched lattices use polynomial quasiequilibria");
     if (cfg->limiters & kLimEnsemble)
         return bfail(b, LBM_ERR_INVALID_ARG, "the ensemble-dependent limiters are not available in batches");
     lbm_ctx *c = nullptr;

@@ -230,6 +230,7 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, 
                 kg.lid4 = p.lid[4];
                 kg.lid7 = p.lid[7];
                 kg.lid8 = p.lid[8];
+                kg.eq = p.eq;
                 c.key = key_dS9_lane<S>(kg, (const S *)p.src, c.site, p.delta_e);
             }
         }
@@ -380,7 +381,30 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, 
                 float drho, nq[Q];
                 pull_dev<Q, S>(p, x, y, g);
                 moments_dev<Q>(g, p.rho_ref, drho, rho, ux, uy);
-                feq_dev<Q>(drho, rho, ux, uy, fs);
+                if (p.eq == 1) {
+                    // entropic f*: from the limited state in FP64 (the stored values), the
+                    // entropy the step adds, dS w.r.t. its own f*; a state whose moments
+                    // have no entropic f* keeps its populations
+                    double fl[Q], fsd[Q], r2, a2, b2;
+#pragma unroll
+                    for (int q = 0; q < Q; ++q)
+                        fl[q] = Ar<double>::add((double)s2f(f[fidx(p.plane, p.pitch, q, y, x)]), p.rw[q]);
+                    moments<Q, double>(fl, r2, a2, b2);
+                    write = feq_any<Q>(1, r2, a2, b2, fsd);
+                    if (write) {
+                        const double d = rel_entropy<Q>(fl, fsd);
+                        if (isfinite(d)) ehr_sum = Ar<double>::add(ehr_sum, d);
+                        if constexpr (Q == 9)
+                            feq_ent9_x<F1>(drho, rho, ux, uy, fs);
+                        else
+                            feq_ent3_dev(drho, rho, ux, fs);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < Q; ++q) fs[q] = 0.f;
+                    }
+                } else {
+                    feq_dev<Q>(drho, rho, ux, uy, fs);
+                }
                 neq_dev<Q>(g, fs, nq);
 #pragma unroll
                 for (int q = 0; q < Q; ++q) fs[q] = g[q] - nq[q];

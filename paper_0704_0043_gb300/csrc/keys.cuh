@@ -13,6 +13,7 @@ namespace lbm {
 // moving-lid terms of the links through the lid (directions 4, 7, 8).
 struct KeyGeom {
     int nx, ny, pitch, boundary;
+    int eq;  // 1: entropic f* and the exact dS of Eq. DelS (key_ent9)
     long long plane;
     double a;
     double rw0, rw1, rw5;
@@ -41,6 +42,21 @@ __device__ double pull_one_f64(const KeyGeom &p, const S *src, int x, int y, int
     return v;
 }
 
+// FP64 key with entropic f* (Eq. maxwellian) and the exact dS of Eq. DelS, from
+// the same pulled FP64 populations: the evaluation of the FP64 path
+// (site_collide with eq = 1), so the key is the value an LBM_FP64 context
+// would compare with delta_e; +inf for a state with a negative population.
+template <typename S>
+__device__ __noinline__ double key_ent9(const KeyGeom p, const S *src, int site, double delta_e)
+{
+    const int x = site % p.nx, y = site / p.nx;
+    double fin[9], fs[9], fp[9], ds, dsin, rho;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) fin[k] = pull_one_f64<S>(p, src, x, y, k);
+    const bool bad = site_collide<9, double>(fin, p.a, true, fs, fp, ds, dsin, rho, 1, false);
+    return !bad && ds > delta_e ? ds : -1.0;
+}
+
 // FP64 key dS(f') of `site`, evaluated by the whole (converged) warp: lane k < 9
 // pulls population k and evaluates f*_k and its dS term; the moments and the
 // final sum run in k order exactly as the sequential FP64 evaluation runs them,
@@ -53,6 +69,7 @@ __device__ __noinline__ double key_dS9_warp(const KeyGeom p, const S *src, int s
 {
     using A = Ar<double>;
     constexpr unsigned kAll = 0xffffffffu;
+    if (p.eq == 1) return key_ent9<S>(p, src, site, delta_e);  // every lane, the same value
     const int lane = threadIdx.x & 31, k = lane < 9 ? lane : 0;
     const int x = site % p.nx, y = site / p.nx;
     const double mine = pull_one_f64<S>(p, src, x, y, k);
@@ -95,6 +112,7 @@ template <typename S>
 __device__ __noinline__ double key_dS9_lane(const KeyGeom p, const S *src, int site, double delta_e)
 {
     using A = Ar<double>;
+    if (p.eq == 1) return key_ent9<S>(p, src, site, delta_e);
     const int x = site % p.nx, y = site / p.nx;
     double fin[9];
 #pragma unroll

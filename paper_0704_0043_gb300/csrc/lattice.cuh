@@ -505,6 +505,8 @@ struct F1 {
     static __device__ __forceinline__ V s(float x) { return x; }
     static __device__ __forceinline__ V rcp_rn(V a) { return __frcp_rn(a); }
     static __device__ __forceinline__ V rcp_fast(V a) { return rcp_approx(a); }
+    static __device__ __forceinline__ V div(V a, V b) { return __fdiv_rn(a, b); }
+    static __device__ __forceinline__ V sqrt(V a) { return __fsqrt_rn(a); }
 };
 
 struct F2 {
@@ -517,6 +519,8 @@ struct F2 {
     static __device__ __forceinline__ V s(float x) { return make_float2(x, x); }
     static __device__ __forceinline__ V rcp_rn(V a) { return make_float2(__frcp_rn(a.x), __frcp_rn(a.y)); }
     static __device__ __forceinline__ V rcp_fast(V a) { return make_float2(rcp_approx(a.x), rcp_approx(a.y)); }
+    static __device__ __forceinline__ V div(V a, V b) { return make_float2(__fdiv_rn(a.x, b.x), __fdiv_rn(a.y, b.y)); }
+    static __device__ __forceinline__ V sqrt(V a) { return make_float2(__fsqrt_rn(a.x), __fsqrt_rn(a.y)); }
 };
 
 template <class O>
@@ -588,6 +592,112 @@ __device__ __forceinline__ void neq9_x(const typename O::V g[9], const typename 
     n[3] = O::add(n[3], hx);
     n[2] = O::sub(n[2], hy);
     n[4] = O::add(n[4], hy);
+}
+
+// ---------------------------------------------------------------------------
+// Entropic quasiequilibria on FP32 deviations.  Eq. maxwellian is the product
+// over the axes of A_j X_j^{v_j} with A_j = 2 - s_j, X_j = (2 u_j + s_j) / (1 - u_j),
+// s_j = sqrt(1 + 3 u_j^2) (Eq. entropiceq1d is one such factor).  Written as
+// 1 + d, each factor has a cancellation-free d (a = s - 1 = 3 u^2 / (1 + s)):
+//   v = 0:  d0 = -a
+//   v = +1: dp = (u (3 - 2a) - a^2) / (1 - u)
+//   v = -1: dm = (u (a - 3) - 2a) / (1 + 2u + a)
+// so f*_k = rho W_k (1 + e_k), e_k = dx + dy + dx dy, and the deviation is
+// g*_k = W_k (drho + rho e_k); the rest deviation closes the mass as in the
+// polynomial form.  Needs |u_x|, |u_y| < 1 (the caller flags the site otherwise).
+template <class O>
+__device__ __forceinline__ void ent_axis(typename O::V u, typename O::V &d0, typename O::V &dp, typename O::V &dm)
+{
+    using V = typename O::V;
+    const V u2 = O::mul(u, u);
+    const V s = O::sqrt(O::fma(O::s(3.f), u2, O::s(1.f)));
+    const V a = O::div(O::mul(O::s(3.f), u2), O::add(O::s(1.f), s));
+    d0 = O::mul(O::s(-1.f), a);
+    dp = O::div(O::fma(u, O::fma(O::s(-2.f), a, O::s(3.f)), O::mul(O::s(-1.f), O::mul(a, a))), O::sub(O::s(1.f), u));
+    dm = O::div(O::fma(u, O::sub(a, O::s(3.f)), O::mul(O::s(-2.f), a)),
+                O::add(O::fma(O::s(2.f), u, O::s(1.f)), a));
+}
+
+template <class O>
+__device__ __forceinline__ void feq_ent9_x(typename O::V drho, typename O::V rho, typename O::V ux, typename O::V uy,
+                                           typename O::V gs[9])
+{
+    using V = typename O::V;
+    V x0, xp, xm, y0, yp, ym;
+    ent_axis<O>(ux, x0, xp, xm);
+    ent_axis<O>(uy, y0, yp, ym);
+    const float w1 = 1.0f / 9.0f, w5 = 1.0f / 36.0f;
+    auto g = [&](float w, V dx, V dy) {
+        const V e = O::fma(dx, dy, O::add(dx, dy));
+        return O::mul(O::s(w), O::fma(rho, e, drho));
+    };
+    gs[1] = g(w1, xp, y0);
+    gs[2] = g(w1, x0, yp);
+    gs[3] = g(w1, xm, y0);
+    gs[4] = g(w1, x0, ym);
+    gs[5] = g(w5, xp, yp);
+    gs[6] = g(w5, xm, yp);
+    gs[7] = g(w5, xm, ym);
+    gs[8] = g(w5, xp, ym);
+    gs[0] = O::sub(drho, O::add(O::add(O::add(gs[1], gs[2]), O::add(gs[3], gs[4])),
+                                O::add(O::add(gs[5], gs[6]), O::add(gs[7], gs[8]))));
+}
+
+// D1Q3 (Eq. entropiceq1d; index 1 is v = -1, index 2 is v = +1)
+__device__ __forceinline__ void feq_ent3_dev(float drho, float rho, float u, float gs[3])
+{
+    float d0, dp, dm;
+    ent_axis<F1>(u, d0, dp, dm);
+    gs[1] = (1.0f / 6.0f) * __fmaf_rn(rho, dm, drho);
+    gs[2] = (1.0f / 6.0f) * __fmaf_rn(rho, dp, drho);
+    gs[0] = drho - (gs[1] + gs[2]);
+}
+
+// One term of Eq. DelS written without cancellation: with d = f - f* and
+// f = f* + d >= 0, f ln(f / f*) - (f - f*) = f* h(f / f*), h(x) = x ln x - x + 1
+// >= 0; the terms sum to dS because sum_k (f_k - f*_k) = 0 (shared mass).
+// With z = d / (2 f* + d), h = 2 z^2 (1 + z/3 + z^2/3 + z^3/5 + z^4/5 + z^5/7 +
+// z^6/7 + ...) / (1 - z) (the series of 2 atanh z multiplied out); for
+// |z| < 0.1 the omitted terms are below 1e-8 of the sum.  Farther out the
+// logarithm directly.  A negative f gives +inf (outside the entropy's domain);
+// f = 0 gives f* (0 ln 0 = 0).
+__device__ __forceinline__ float ent_term1(float d, float fs)
+{
+    const float f = __fadd_rn(fs, d);
+    if (!(f >= 0.f)) return f < 0.f ? __int_as_float(0x7f800000) : f;  // +inf, or NaN through
+    const float z = __fdiv_rn(d, __fadd_rn(__fadd_rn(fs, fs), d));
+    if (fabsf(z) < 0.1f) {
+        const float w = __fmul_rn(z, z);
+        const float odd = __fmaf_rn(w, __fmaf_rn(w, 1.0f / 7.0f, 1.0f / 5.0f), 1.0f / 3.0f);
+        const float even = __fmaf_rn(w, __fmaf_rn(w, __fmaf_rn(w, 1.0f / 7.0f, 1.0f / 5.0f), 1.0f / 3.0f), 1.0f);
+        const float P = __fmaf_rn(z, odd, even);
+        return __fmul_rn(fs, __fdiv_rn(__fmul_rn(__fmul_rn(2.f, w), P), __fsub_rn(1.f, z)));
+    }
+    if (f == 0.f) return fs;
+    return __fsub_rn(__fmul_rn(f, logf(__fdiv_rn(f, fs))), d);
+}
+
+// Eq. DelS of a D2Q9 / D1Q3 state f* + d (absolute f* in fsa), k order; +inf if
+// some population is negative.
+template <int Q>
+__device__ __forceinline__ float rel_entropy_dev(const float d[Q], const float fsa[Q])
+{
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < Q; ++k) s = __fadd_rn(s, ent_term1(d[k], fsa[k]));
+    return s;
+}
+
+// The paired form for the fused kernel: the same operations per component.
+__device__ __forceinline__ float2 rel_entropy9_x(const float2 d[9], const float2 fsa[9])
+{
+    float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        s.x = __fadd_rn(s.x, ent_term1(d[k].x, fsa[k].x));
+        s.y = __fadd_rn(s.y, ent_term1(d[k].y, fsa[k].y));
+    }
+    return s;
 }
 
 __device__ __forceinline__ void moments9_dev(const float g[9], float rho_ref, float &drho, float &rho, float &ux,
@@ -677,10 +787,37 @@ __device__ __forceinline__ float limit_weight(float phi, float a, bool collide)
 template <int Q>
 __device__ __forceinline__ bool site_collide_dev(const float g[Q], float a, float b2, bool collide, float rho_ref,
                                                  const float rw[Q], float gs[Q], float n[Q], float gp[Q],
-                                                 float fsa[Q], float &ds, float &ds_in, float &rho)
+                                                 float fsa[Q], float &ds, float &ds_in, float &rho, int eq = 0)
 {
     float drho, ux, uy;
     moments_dev<Q>(g, rho_ref, drho, rho, ux, uy);
+    if (eq == 1) {
+        // entropic f* (Eq. maxwellian / Eq. entropiceq1d) and the exact dS of
+        // Eq. DelS: dS(f') from f' - f* = -(2 beta - 1) n, dS(f_in) from n;
+        // +inf (not a flag) for a state with a negative population
+        const bool nofs = !(fabsf(ux) < 1.f) || !(fabsf(uy) < 1.f);
+        if (nofs) {
+#pragma unroll
+            for (int k = 0; k < Q; ++k) gs[k] = 0.f;
+        } else if constexpr (Q == 9) {
+            feq_ent9_x<F1>(drho, rho, ux, uy, gs);
+        } else {
+            feq_ent3_dev(drho, rho, ux, gs);
+        }
+        neq_dev<Q>(g, gs, n);
+        float fmin = 3.4e38f, dp[Q];
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            fsa[k] = __fadd_rn(rw[k], gs[k]);
+            gp[k] = collide ? __fmaf_rn(-b2, n[k], g[k]) : g[k];
+            dp[k] = collide ? __fmul_rn(-a, n[k]) : n[k];
+            fmin = fminf(fmin, fsa[k]);
+        }
+        const bool bad = nofs || !(rho > 0.f) || !(fmin > 0.f);
+        ds = bad ? 0.f : rel_entropy_dev<Q>(dp, fsa);
+        ds_in = (bad || !collide) ? 0.f : rel_entropy_dev<Q>(n, fsa);
+        return bad || isnan(ds) || isnan(ds_in);
+    }
     feq_dev<Q>(drho, rho, ux, uy, gs);
     neq_dev<Q>(g, gs, n);
     float din = 0.f, fmin = 3.4e38f;

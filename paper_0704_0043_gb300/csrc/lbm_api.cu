@@ -63,7 +63,6 @@ cudaError_t with_storage(int precision, F &&fn)
 bool fused_applies(const lbm_config &c)
 {
     return c.lattice == LBM_D2Q9 && c.precision != LBM_FP64 && c.boundary == LBM_BC_WALLS &&
-           (c.limiters & kLimEnsemble) == 0 &&
            c.kernel != LBM_KERNEL_TILED && fused_d2q9_fits((long long)c.ny * row_pitch(c.nx));
 }
 
@@ -106,16 +105,15 @@ std::string validate(const lbm_config *c)
     if (c->median_mode != LBM_MEDIAN_THRESHOLD && c->median_mode != LBM_MEDIAN_GATE) return "unknown median_mode";
     if (c->kernel < LBM_KERNEL_AUTO || c->kernel > LBM_KERNEL_FUSED) return "unknown kernel";
     if (c->equilibrium != LBM_EQ_POLYNOMIAL && c->equilibrium != LBM_EQ_ENTROPIC) return "unknown equilibrium";
-    if (c->equilibrium == LBM_EQ_ENTROPIC && c->precision != LBM_FP64)
-        return "entropic quasiequilibria need LBM_FP64 storage";
+
     if (c->kernel == LBM_KERNEL_FUSED && !fused_applies(*c))
         return "LBM_KERNEL_FUSED needs D2Q9, FP32/BF16/FP16 storage and LBM_BC_WALLS";
     if (c->collision != LBM_COLL_LBGK && c->collision != LBM_COLL_ELBM) return "unknown collision";
-    if (c->collision == LBM_COLL_ELBM && c->equilibrium != LBM_EQ_ENTROPIC)
-        return "ELBM needs entropic quasiequilibria (LBM_EQ_ENTROPIC, LBM_FP64)";
+    if (c->collision == LBM_COLL_ELBM && (c->equilibrium != LBM_EQ_ENTROPIC || c->precision != LBM_FP64))
+        return "ELBM needs entropic quasiequilibria (LBM_EQ_ENTROPIC) and LBM_FP64 storage";
     if (c->phi_rule != LBM_PHI_HOMOTHETY && c->phi_rule != LBM_PHI_ENTROPY) return "unknown phi_rule";
-    if (c->phi_rule == LBM_PHI_ENTROPY && c->equilibrium != LBM_EQ_ENTROPIC)
-        return "LBM_PHI_ENTROPY needs entropic quasiequilibria (LBM_EQ_ENTROPIC, LBM_FP64)";
+    if (c->phi_rule == LBM_PHI_ENTROPY && (c->equilibrium != LBM_EQ_ENTROPIC || c->precision != LBM_FP64))
+        return "LBM_PHI_ENTROPY needs entropic quasiequilibria (LBM_EQ_ENTROPIC) and LBM_FP64 storage";
     if (!(c->entthresh_delta0 >= 0.0) || !std::isfinite(c->entthresh_delta0))
         return "entthresh_delta0 must be finite and >= 0";
     if (c->stats_history < 0) return "stats_history must be >= 0";

@@ -64,9 +64,37 @@ constexpr int kCandList = 32;    // candidates a warp keys itself per item (the 
 constexpr unsigned kFull = 0xffffffffu;
 
 struct RowState {
-    float2 ds, pp;
+    float2 ds, pp, pe;  // dS(f'), phi of the positivity rule, phi of the ensemble-dependent limiters
     bool bad_a, bad_b, cand_a, cand_b;
 };
+
+// What the ensemble-dependent limiters need of their pass (read once per
+// block from the reduction that ran before the step): E(dS) > 0, alpha and k
+// of the smooth limiter, and the threshold filters' dS_t in FP64 with its FP32
+// value rounded down (for a float dS, dS > tf exactly when (double) dS > t).
+struct EnsParams {
+    unsigned lim;  // the pass's ensemble bits
+    bool e_pos, k_half;
+    float alpha, k;
+    double thr_t, ent_t;
+    float thr_f, ent_f;
+};
+
+// phi of the ensemble-dependent limiters at a site with dS(f') = ds (not
+// flagged), the same operations as the tiled kernel's: Eq. smooth1 with the
+// ensemble's alpha, Eq. EntThresh's dS_t and the threshold dS_t = max(c E,
+// delta) with the homothety of Eq. entrHom (rare sites, in FP64 as there).
+__device__ __forceinline__ float ens_phi(const EnsParams &e, float ds)
+{
+    float pe = 1.f;
+    if ((e.lim & 8u) && e.e_pos && ds > 0.f) {
+        const float pk = e.k_half ? sqrtf(ds) : powf(ds, e.k);
+        pe = __fdiv_rn(1.f, __fmaf_rn(e.alpha, pk, 1.f));
+    }
+    if ((e.lim & 32u) && ds > e.ent_f) pe = fminf(pe, (float)sqrt(e.ent_t / (double)ds));
+    if ((e.lim & 16u) && ds > e.thr_f) pe = fminf(pe, (float)sqrt(e.thr_t / (double)ds));
+    return pe;
+}
 
 // Adds the FP32 value v exactly to acc, a 128-bit two's-complement fixed-point
 // number in units of 2^-64 (bits of v below 2^-64 are dropped, truncating
@@ -136,8 +164,8 @@ __device__ __forceinline__ Sides sides(float a, float b, int lane)
 // the instance's limiter bits).  BATCHED: block b runs instance map[b].x of
 // `table` as its block map[b].y; otherwise the single instance A0.
 // S: storage type of the deviations (float, __nv_bfloat16 or __half).
-template <typename S, bool MED, bool POS, bool BATCHED>
-__global__ void __launch_bounds__(kThreads, BATCHED ? 3 : kBlocksPerSM)
+template <typename S, bool MED, bool POS, bool BATCHED, bool ENS = false, bool ENT = false>
+__global__ void __launch_bounds__(kThreads, (BATCHED || ENT) ? 3 : kBlocksPerSM)
     k_fused(const FusedArgs A0, const FusedArgs *__restrict__ table, const int2 *__restrict__ map)
 {
     using O = F2;
@@ -167,6 +195,24 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : kBlocksPerSM)
     }
     const FusedArgs &A = BATCHED ? sA : A0;
     const StepParams &p = A.p;
+    // ensemble-dependent limiters: this pass's E(dS), alpha and dS_t
+    EnsParams ens{};
+    if constexpr (ENS) {
+        ens.lim = p.limiters & kLimEnsemble;
+        if (ens.lim) {
+            const double E = p.ens[0];
+            ens.e_pos = E > 0.0;
+            ens.k_half = p.smooth_k == 0.5;
+            ens.alpha = (float)p.ens[1];
+            ens.k = (float)p.smooth_k;
+            double t = p.threshold_c * E;
+            if (t < p.threshold_delta) t = p.threshold_delta;
+            ens.thr_t = t;
+            ens.thr_f = __double2float_rd(t);
+            ens.ent_t = (ens.lim & 32u) ? p.ent->t : 0.0;
+            ens.ent_f = (ens.lim & 32u) ? __double2float_rd(ens.ent_t) : 0.f;
+        }
+    }
 
     float s_mass = 0.f, s_ds = 0.f, s_in = 0.f, s_lim = 0.f;
     int n_pos = 0, n_med = 0, n_bad = 0, n_sites = 0, rows_acc = 0;
@@ -280,7 +326,20 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : kBlocksPerSM)
         auto collide = [&](const float2 g[9], float2 &drho, float2 &rho, float2 &ux, float2 &uy, float2 gs[9],
                            float2 n[9]) {
             moments9_x<O>(g, rho_ref, drho, rho, ux, uy);
-            feq9_x<O>(drho, rho, ux, uy, gs);
+            if constexpr (ENT) {
+                // entropic f* (Eq. maxwellian); a site with |u_j| >= 1 has none
+                // (flagged in row_ds) and takes g* = 0, as in the tiled kernel
+                feq_ent9_x<O>(drho, rho, ux, uy, gs);
+                const bool na = !(fabsf(ux.x) < 1.f) || !(fabsf(uy.x) < 1.f);
+                const bool nb = !(fabsf(ux.y) < 1.f) || !(fabsf(uy.y) < 1.f);
+#pragma unroll
+                for (int k = 0; k < 9; ++k) {
+                    if (na) gs[k].x = 0.f;
+                    if (nb) gs[k].y = 0.f;
+                }
+            } else {
+                feq9_x<O>(drho, rho, ux, uy, gs);
+            }
             neq9_x<O>(g, gs, n);
         };
 
@@ -290,6 +349,29 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : kBlocksPerSM)
         // rho <= 0, some f*_k <= 0, nonfinite); din = dS(f_in)
         auto row_ds = [&](const float2 gs[9], const float2 n[9], float2 rho, float2 ux, float2 uy, float2 &din,
                           bool &bad_a, bool &bad_b) -> float2 {
+            if constexpr (ENT) {
+                // the exact dS of Eq. DelS without cancellation (lattice.cuh): of
+                // f' from f' - f* = -(2 beta - 1) n, of f_in from n; +inf (no flag)
+                // for a state with a negative population
+                float2 fsa[9], d[9];
+                float fa = 3.4e38f, fb = 3.4e38f;
+#pragma unroll
+                for (int k = 0; k < 9; ++k) {
+                    fsa[k] = O::add(rwk(k), gs[k]);
+                    d[k] = O::mul(O::s(-a), n[k]);
+                    fa = fminf(fa, fsa[k].x);
+                    fb = fminf(fb, fsa[k].y);
+                }
+                bad_a = !(rho.x > 0.f) || !(fabsf(ux.x) < 1.f) || !(fabsf(uy.x) < 1.f) || !(fa > 0.f);
+                bad_b = !(rho.y > 0.f) || !(fabsf(ux.y) < 1.f) || !(fabsf(uy.y) < 1.f) || !(fb > 0.f);
+                float2 ds = rel_entropy9_x(d, fsa);
+                din = rel_entropy9_x(n, fsa);
+                bad_a = bad_a || isnan(ds.x) || isnan(din.x);
+                bad_b = bad_b || isnan(ds.y) || isnan(din.y);
+                ds.x = bad_a ? __int_as_float(0x7f800000) : ds.x;
+                ds.y = bad_b ? __int_as_float(0x7f800000) : ds.y;
+                return ds;
+            }
             din = make_float2(0.f, 0.f);
 #pragma unroll
             for (int k = 0; k < 9; ++k)
@@ -326,7 +408,8 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : kBlocksPerSM)
         };
 
         auto compute_row = [&](int q, float2 g[9]) -> RowState {
-            RowState st{make_float2(0.f, 0.f), make_float2(1.f, 1.f), false, false, false, false};
+            RowState st{make_float2(0.f, 0.f), make_float2(1.f, 1.f), make_float2(1.f, 1.f), false, false, false,
+                        false};
             edge_row(q, g);
             float2 drho, rho, ux, uy, gs[9], n[9], din;
             collide(g, drho, rho, ux, uy, gs, n);
@@ -351,6 +434,14 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : kBlocksPerSM)
                     if (!bad_b && fpb < 0.f) st.pp.y = fminf(st.pp.y, fsb / (fsb - fpb));
                 }
             }
+            if constexpr (ENS) {
+                // site-local, like the positivity rule: applied with the median's
+                // phi one row later (the row is then recomputed from its sources)
+                if (ens.lim) {
+                    if (!bad_a) st.pe.x = ens_phi(ens, ds.x);
+                    if (!bad_b) st.pe.y = ens_phi(ens, ds.y);
+                }
+            }
             const bool rown = q >= ys && q < ye;
             const bool oa = own_a && rown, ob = own_b && rown;
             S *out = dst + (long long)q * pitch + kLead + xa;
@@ -361,8 +452,16 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : kBlocksPerSM)
             }
             const bool ga = oa && !bad_a, gb = ob && !bad_b;
             s_mass += (oa ? drho.x : 0.f) + (ob ? drho.y : 0.f);
-            s_ds += (ga ? ds.x : 0.f) + (gb ? ds.y : 0.f);
-            s_in += (ga ? din.x : 0.f) + (gb ? din.y : 0.f);
+            if constexpr (ENT) {
+                // entropy differences where both entropies are finite
+                const bool fa = ga && isfinite(ds.x), fb = gb && isfinite(ds.y);
+                s_ds += (fa ? ds.x : 0.f) + (fb ? ds.y : 0.f);
+                s_in += ((fa && isfinite(din.x)) ? __fsub_rn(din.x, ds.x) : 0.f) +
+                        ((fb && isfinite(din.y)) ? __fsub_rn(din.y, ds.y) : 0.f);
+            } else {
+                s_ds += (ga ? ds.x : 0.f) + (gb ? ds.y : 0.f);
+                s_in += (ga ? din.x : 0.f) + (gb ? din.y : 0.f);
+            }
             n_sites += (int)oa + (int)ob;
             n_bad += (int)(oa && bad_a) + (int)(ob && bad_b);
             if (pos_on) n_pos += (int)(oa && st.pp.x < 1.f) + (int)(ob && st.pp.y < 1.f);
@@ -456,7 +555,8 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : kBlocksPerSM)
                 if (xa_on && st.ds.x > med_a) pm_a = phi_median<float>(st.ds.x, med_a, A.delta_m, p.median_mode);
                 if (xb_on && st.ds.y > med_b) pm_b = phi_median<float>(st.ds.y, med_b, A.delta_m, p.median_mode);
             }
-            const float phi_a = act_a ? fminf(st.pp.x, pm_a) : 1.f, phi_b = act_b ? fminf(st.pp.y, pm_b) : 1.f;
+            const float phi_a = act_a ? fminf(fminf(st.pp.x, pm_a), st.pe.x) : 1.f;
+            const float phi_b = act_b ? fminf(fminf(st.pp.y, pm_b), st.pe.y) : 1.f;
             if (__any_sync(kFull, phi_a < 1.f || phi_b < 1.f)) {
                 // the limited update g - (1 + phi (2 beta - 1)) n (Eq. LimGenF in
                 // nonequilibrium form), with g and n recomputed exactly as the
@@ -475,8 +575,22 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : kBlocksPerSM)
                         if (phi_a < 1.f) out[k * plane] = f2s<S>(v.x);
                         if (phi_b < 1.f) out[k * plane + 32] = f2s<S>(v.y);
                     }
-                    if (phi_a < 1.f) s_lim = fmaf(1.f - phi_a * phi_a, st.ds.x, s_lim);
-                    if (phi_b < 1.f) s_lim = fmaf(1.f - phi_b * phi_b, st.ds.y, s_lim);
+                    if constexpr (ENT) {
+                        // dS(f') - dS(f_out) at the same f*, f_out - f* = phi (f' - f*)
+                        float2 fsa[9], d[9];
+                        const float2 m = make_float2(__fmul_rn(-phi_a, a), __fmul_rn(-phi_b, a));
+#pragma unroll
+                        for (int k = 0; k < 9; ++k) {
+                            fsa[k] = O::add(rwk(k), gs[k]);
+                            d[k] = O::mul(m, n[k]);
+                        }
+                        const float2 so = rel_entropy9_x(d, fsa);
+                        if (phi_a < 1.f && isfinite(st.ds.x) && isfinite(so.x)) s_lim += __fsub_rn(st.ds.x, so.x);
+                        if (phi_b < 1.f && isfinite(st.ds.y) && isfinite(so.y)) s_lim += __fsub_rn(st.ds.y, so.y);
+                    } else {
+                        if (phi_a < 1.f) s_lim = fmaf(1.f - phi_a * phi_a, st.ds.x, s_lim);
+                        if (phi_b < 1.f) s_lim = fmaf(1.f - phi_b * phi_b, st.ds.y, s_lim);
+                    }
                 }
             }
             n_med += (int)(act_a && pm_a < 1.f) + (int)(act_b && pm_b < 1.f);
@@ -529,13 +643,15 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : kBlocksPerSM)
                 cp_async_commit();  // one group per row (empty past the last row)
             };
             // Iteration r computes row r and finishes row r-1.
-            RowState prev{make_float2(0.f, 0.f), make_float2(1.f, 1.f), false, false, false, false};
+            RowState prev{make_float2(0.f, 0.f), make_float2(1.f, 1.f), make_float2(1.f, 1.f), false, false, false,
+                          false};
             float2 ds_m2 = make_float2(0.f, 0.f), ds_m1 = make_float2(0.f, 0.f);  // dS of rows r-2, r-1
             __syncwarp();
 #pragma unroll
             for (int j = 0; j < kRing - 1; ++j) issue(r0 + j);
             for (int r = r0; r - 1 < ye; ++r) {
-                RowState st{make_float2(0.f, 0.f), make_float2(1.f, 1.f), false, false, false, false};
+                RowState st{make_float2(0.f, 0.f), make_float2(1.f, 1.f), make_float2(1.f, 1.f), false, false,
+                            false, false};
                 if (r <= rc) {
                     __syncwarp();                // every lane is done with the slot row r-1 used
                     issue(r + kRing - 1);        // refills it
@@ -578,6 +694,7 @@ __global__ void __launch_bounds__(kThreads, BATCHED ? 3 : kBlocksPerSM)
             kg.lid4 = p.lid[4];
             kg.lid7 = p.lid[7];
             kg.lid8 = p.lid[8];
+            kg.eq = p.eq;
             const int n = min(n_list, kCandList);
             __syncwarp();
             if (n >= kLaneKeys) {
@@ -664,19 +781,19 @@ int sm_count()
     return sms;
 }
 
-template <typename S, bool MED, bool POS, bool BATCHED>
+template <typename S, bool MED, bool POS, bool BATCHED, bool ENS = false, bool ENT = false>
 cudaError_t launch_k(const FusedArgs &A, const FusedArgs *table, const int2 *map, int blocks, cudaStream_t s)
 {
     static bool configured = false;
     if (!configured && kCarveout >= 0) {
         // shared memory vs L1 split (percent of the unified array for shared memory)
-        if (cudaFuncSetAttribute(k_fused<S, MED, POS, BATCHED>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        if (cudaFuncSetAttribute(k_fused<S, MED, POS, BATCHED, ENS, ENT>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  kCarveout) != cudaSuccess)
             cudaGetLastError();
     }
     configured = true;
     if constexpr (BATCHED) {
-        k_fused<S, MED, POS, BATCHED><<<blocks, kThreads, 0, s>>>(A, table, map);
+        k_fused<S, MED, POS, BATCHED, ENS, ENT><<<blocks, kThreads, 0, s>>>(A, table, map);
     } else {
         // programmatic dependent launch: the blocks may become resident while
         // the previous kernel of the stream (the tail) still runs; they wait
@@ -693,7 +810,7 @@ cudaError_t launch_k(const FusedArgs &A, const FusedArgs *table, const int2 *map
         cfg.numAttrs = 1;
         const FusedArgs *tab = table;
         const int2 *mp = map;
-        return cudaLaunchKernelEx(&cfg, k_fused<S, MED, POS, BATCHED>, A, tab, mp);
+        return cudaLaunchKernelEx(&cfg, k_fused<S, MED, POS, BATCHED, ENS, ENT>, A, tab, mp);
     }
     return cudaGetLastError();
 }
@@ -703,6 +820,10 @@ cudaError_t launch_k(const FusedArgs &A, const FusedArgs *table, const int2 *map
 template <typename S>
 cudaError_t launch_lim(const FusedArgs &A, int blocks, cudaStream_t s)
 {
+    if (A.p.eq == 1)  // entropic f* and the exact dS of Eq. DelS; every limiter bit at run time
+        return launch_k<S, true, true, false, true, true>(A, nullptr, nullptr, blocks, s);
+    if (A.p.limiters & kLimEnsemble)  // the ensemble-dependent limiters follow every bit at run time
+        return launch_k<S, true, true, false, true>(A, nullptr, nullptr, blocks, s);
     if constexpr (std::is_same<S, float>::value) {
         const bool med = (A.p.limiters & 4u) != 0, pos = (A.p.limiters & 1u) != 0;
         if (med && pos) return launch_k<S, true, true, false>(A, nullptr, nullptr, blocks, s);
@@ -770,7 +891,8 @@ cudaError_t launch_fused_d2q9(const StepParams &p, const S *src, S *dst, int *nb
     // Dynamic work: one wave of resident blocks over short row segments, about
     // kItemsPerWarp items per warp; warps past their first item take the next
     // from the counter p.work (cleared by the tail kernel after the launch).
-    const int slots = fused_slots((int)sizeof(S), false);
+    // the entropic variant keeps more registers: three blocks per SM
+    const int slots = p.eq == 1 ? 3 * kWarps * sm_count() : fused_slots((int)sizeof(S), false);
     int rows = 0;
     if (p.work != nullptr) {
         const long long strips = (p.nx + kStripCols - 1) / kStripCols;

@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const S *__r
             for (int k = 0; k < Q; ++k) fa[k] = fs[k];
         } else {
             bad = site_collide_dev<Q>(fin, (float)p.a, (float)(1.0 + p.a), p.collide != 0, p.rho_ref, p.rwf, fs, nq,
-                                      fp, fa, ds, dsin, rho);
+                                      fp, fa, ds, dsin, rho, p.eq);
         }
         if (bad) ds = T(INFINITY);
     }
@@ -412,7 +412,7 @@ __global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const S *__r
             } else {
                 if ((p.limiters & 8u) && ke[0] && ds > 0.f) {
                     const float pk = ke[1] ? sqrtf(ds) : powf(ds, kc[5]);
-                    pe = 1.0f / (1.0f + kc[3] * pk);
+                    pe = __fdiv_rn(1.0f, __fmaf_rn(kc[3], pk, 1.0f));  // explicit: the fused kernel's bits
                 }
                 if ((p.limiters & 32u) && ds > kc[6]) {
                     // rare: Eq. EntThresh's exact dS_t at the limited site
@@ -448,7 +448,17 @@ __global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const S *__r
                 const float c = limit_weight(phi, kc[2], p.collide != 0);
 #pragma unroll
                 for (int k = 0; k < Q; ++k) dst[fidx(p.plane, p.pitch, k, y, x)] = f2s<S>(fmaf(-c, nq[k], fin[k]));
-                fsum_lim = __fmul_rn(__fsub_rn(1.f, __fmul_rn((float)phi, (float)phi)), (float)ds);
+                if (p.eq == 1) {
+                    // entropic f*: dS(f') - dS(f_out) at the same f*, f_out - f* = phi (f' - f*)
+                    float dout[Q];
+                    const float m = p.collide ? __fmul_rn(-(float)phi, kc[2]) : (float)phi;
+#pragma unroll
+                    for (int k = 0; k < Q; ++k) dout[k] = __fmul_rn(m, nq[k]);
+                    const float so = rel_entropy_dev<Q>(dout, fa);
+                    if (isfinite((float)ds) && isfinite(so)) fsum_lim = __fsub_rn((float)ds, so);
+                } else {
+                    fsum_lim = __fmul_rn(__fsub_rn(1.f, __fmul_rn((float)phi, (float)phi)), (float)ds);
+                }
             }
         } else {
 #pragma unroll
@@ -457,16 +467,24 @@ __global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const S *__r
         acc[P_MASS] = (double)rho;
         if constexpr (!std::is_same<T, double>::value) fmass = __fsub_rn((float)rho, p.rho_ref);  // exact
         if (!bad) {
-            if (p.eq == 1) {
-                // entropic f*: sums of entropy differences where both entropies are finite
-                if (isfinite(ds)) acc[P_SUM_DS] = (double)ds;
-                if (isfinite(ds) && isfinite(dsin)) acc[P_SUM_IN] = Ar<double>::sub((double)dsin, (double)ds);
-            } else if constexpr (std::is_same<T, double>::value) {
-                acc[P_SUM_DS] = (double)ds;
-                acc[P_SUM_IN] = (double)dsin;
+            if constexpr (std::is_same<T, double>::value) {
+                if (p.eq == 1) {
+                    // entropic f*: sums of entropy differences where both entropies are finite
+                    if (isfinite(ds)) acc[P_SUM_DS] = ds;
+                    if (isfinite(ds) && isfinite(dsin)) acc[P_SUM_IN] = Ar<double>::sub(dsin, ds);
+                } else {
+                    acc[P_SUM_DS] = ds;
+                    acc[P_SUM_IN] = dsin;
+                }
             } else {
-                fsum_ds = (float)ds;
-                fsum_in = (float)dsin;
+                if (p.eq == 1) {
+                    // entropic f*: sums of entropy differences where both entropies are finite
+                    if (isfinite(ds)) fsum_ds = ds;
+                    if (isfinite(ds) && isfinite(dsin)) fsum_in = __fsub_rn(dsin, ds);
+                } else {
+                    fsum_ds = ds;
+                    fsum_in = dsin;
+                }
             }
         } else {
             acc[P_NBAD] = 1.0;
@@ -495,7 +513,8 @@ __global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const S *__r
 #pragma unroll
                         for (int k = 0; k < Q; ++k) fin64[k] = load_as<S, double>(p, src[fidx(p.plane, p.pitch, k, y, x)], k);
                     }
-                    const bool b64 = site_collide<Q, double>(fin64, p.a, p.collide != 0, fs64, fp64, d64, din64, r64);
+                    const bool b64 = site_collide<Q, double>(fin64, p.a, p.collide != 0, fs64, fp64, d64, din64, r64,
+                                                             p.eq, false);
                     key = d64;
                     is = !b64 && d64 > p.delta_e;
                 }
@@ -566,57 +585,58 @@ __global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const S *__r
 }
 
 // E(dS) of a pass (Sec. 3.3, Sec. 4.3.2): the ensemble-dependent limiters need
-// the mean of dS(f') over the lattice before any site is limited.  Block b
-// sums dS(f') of sites b, b + gridDim.x * 256, ... with the same evaluation as
-// k_tiled (so the same values), over the sites that are not flagged and have a
-// finite dS; k_ens_mean adds the block partials in block order.
+// the mean of dS(f') over the lattice before any site is limited.  Block b walks
+// rows b, b + gridDim.x, ... (its threads along each row, so every warp reads
+// consecutive columns of each plane) and sums dS(f') with the same evaluation
+// as k_tiled (so the same values), over the sites that are not flagged and have
+// a finite dS; k_ens_mean adds the block partials in block order.  With
+// LBM_LIM_ENTTHRESH the values also go to the field the EntThresh solve reads.
 template <int Q, typename S>
 __global__ void __launch_bounds__(256) k_ens_partial(StepParams p, const S *__restrict__ src,
                                                      double *__restrict__ part)
 {
     using T = compute_t<S>;
     __shared__ double sw[8][2];
-    const long long n = (long long)p.nx * p.ny;
     double sum = 0.0, cnt = 0.0;
     // FP32 storage: a thread's own terms in FP32 and an integer count (GB300's
     // FP64 pipe would otherwise bound this read-once pass)
     float fsum = 0.f;
     int icnt = 0;
-    for (long long s = blockIdx.x * 256LL + threadIdx.x; s < n; s += (long long)gridDim.x * 256) {
-        const int x = (int)(s % p.nx), y = (int)(s / p.nx);
-        if (Q == 9 && is_wall_node(p, x, y)) {  // boundary nodes are not collided
-            if (p.ent_field) ((T *)p.ent_field)[s] = T(0);
-            continue;
-        }
-        T fin[Q], fs[Q], fp[Q], fa[Q];
-        float nq[Q];
-        T ds, dsin, rho;
-        bool bad;
-        if (p.collide) {
-            pull<Q, S, T>(p, src, x, y, fin);
-        } else {
+    for (int y = blockIdx.x; y < p.ny; y += gridDim.x) {
+        for (int x = threadIdx.x; x < p.nx; x += 256) {
+            const long long s = (long long)y * p.nx + x;
+            if (Q == 9 && is_wall_node(p, x, y)) {  // boundary nodes are not collided
+                if (p.ent_field) ((T *)p.ent_field)[s] = T(0);
+                continue;
+            }
+            T fin[Q], fs[Q], fp[Q], fa[Q];
+            float nq[Q];
+            T ds, dsin, rho;
+            bool bad;
+            if (p.collide) {
+                pull<Q, S, T>(p, src, x, y, fin);
+            } else {
 #pragma unroll
-            for (int k = 0; k < Q; ++k) fin[k] = load_as<S, T>(p, src[fidx(p.plane, p.pitch, k, y, x)], k);
-        }
-        if constexpr (std::is_same<T, double>::value) {
-            bad = site_collide<Q, T>(fin, T(p.a), p.collide != 0, fs, fp, ds, dsin, rho, p.eq, false, p.coll, p.beta);
-        } else {
-            bad = site_collide_dev<Q>(fin, (float)p.a, (float)(1.0 + p.a), p.collide != 0, p.rho_ref, p.rwf, fs, nq,
-                                      fp, fa, ds, dsin, rho);
-        }
-        if constexpr (std::is_same<T, double>::value) {
-            if (!bad && isfinite(ds)) {
-                sum += ds;
-                cnt += 1.0;
+                for (int k = 0; k < Q; ++k) fin[k] = load_as<S, T>(p, src[fidx(p.plane, p.pitch, k, y, x)], k);
             }
-        } else {
-            if (!bad && isfinite(ds)) {
-                fsum = __fadd_rn(fsum, ds);
-                icnt += 1;
+            if constexpr (std::is_same<T, double>::value) {
+                bad = site_collide<Q, T>(fin, T(p.a), p.collide != 0, fs, fp, ds, dsin, rho, p.eq, false, p.coll,
+                                         p.beta);
+                if (!bad && isfinite(ds)) {
+                    sum += ds;
+                    cnt += 1.0;
+                }
+            } else {
+                bad = site_collide_dev<Q>(fin, (float)p.a, (float)(1.0 + p.a), p.collide != 0, p.rho_ref, p.rwf, fs,
+                                          nq, fp, fa, ds, dsin, rho, p.eq);
+                if (!bad && isfinite(ds)) {
+                    fsum = __fadd_rn(fsum, ds);
+                    icnt += 1;
+                }
             }
+            // Eq. EntThresh works on the same values (0 where the site is left out)
+            if (p.ent_field) ((T *)p.ent_field)[s] = (!bad && isfinite(ds) && ds > T(0)) ? ds : T(0);
         }
-        // Eq. EntThresh works on the same values (0 where the site is left out)
-        if (p.ent_field) ((T *)p.ent_field)[s] = (!bad && isfinite(ds) && ds > T(0)) ? ds : T(0);
     }
     if constexpr (!std::is_same<T, double>::value) {
         sum = (double)fsum;

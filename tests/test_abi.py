@@ -38,10 +38,11 @@ def test_config_validation_without_gpu(lib):
            dict(lattice=lbm.D1Q3, ny=2), dict(lattice=lbm.D1Q3, ny=1, boundary=lbm.BC_CHANNEL),
            dict(precision=7), dict(delta_median=-1.0), dict(median_mode=5),
            dict(kernel=lbm.KERNEL_FUSED, precision=lbm.FP64),
-           dict(equilibrium=2), dict(equilibrium=lbm.EQ_ENTROPIC),
-           dict(equilibrium=lbm.EQ_ENTROPIC, precision=lbm.BF16), dict(limiters=128),
+           dict(equilibrium=2), dict(equilibrium=lbm.EQ_ENTROPIC, collision=lbm.COLL_ELBM),
+           dict(equilibrium=lbm.EQ_ENTROPIC, precision=lbm.BF16, phi_rule=lbm.PHI_ENTROPY),
+           dict(collision=lbm.COLL_ELBM, precision=lbm.FP64), dict(collision=2), dict(limiters=128),
            dict(smooth_k=0.0), dict(smooth_delta=-1.0), dict(threshold_c=float("nan")),
-           dict(threshold_delta=-1e-3), dict(limiters=lbm.LIM_SMOOTH, kernel=lbm.KERNEL_FUSED)]
+           dict(threshold_delta=-1e-3), dict(limiters=lbm.LIM_SMOOTH, kernel=lbm.KERNEL_FUSED, precision=lbm.FP64)]
     for b in bad:
         cfg = dict(base)
         cfg.update(b)

@@ -205,3 +205,119 @@ def test_entropic_site_without_equilibrium_reports_status():
     r = oracle.step(oc, f)
     assert g.stats(check=False)["n_bad"] == r.stats["n_bad"] >= 1
 
+
+
+# -- FP32 / 16-bit storage (FP32 arithmetic): entropic f* in deviation form and the
+# cancellation-free dS of Eq. DelS (lattice.cuh), on the fused and the tiled kernel
+
+def pair32(**cfg):
+    cfg = dict(cfg, equilibrium=lbm.EQ_ENTROPIC)
+    g = lbm.Lattice(**cfg)
+    c = g.config
+    oc = oracle.Config(lattice=c.lattice, nx=c.nx, ny=c.ny, boundary=c.boundary, beta=c.beta,
+                       u_lid=c.u_lid, rho_wall=c.rho_wall, limiters=c.limiters,
+                       delta_median=c.delta_median, delta_ehrenfest=c.delta_ehrenfest, k_max=c.k_max,
+                       median_mode=c.median_mode, equilibrium=oracle.EQ_ENTROPIC)
+    return g, oc
+
+
+@pytest.mark.parametrize("kernel,lattice", [(lbm.KERNEL_FUSED, lbm.D2Q9), (lbm.KERNEL_TILED, lbm.D2Q9),
+                                            (lbm.KERNEL_AUTO, lbm.D1Q3)])
+def test_fp32_entropic_one_step_against_oracle(kernel, lattice):
+    """One FP32 step from the stored FP32 state: populations within the FP32 bar
+    (2e-5 relative), identical Ehrenfests' set (FP64 keys with entropic f* on both
+    sides), counts equal, dS statistics within 1e-4 (FP32 sums of FP32 terms)."""
+    if lattice == lbm.D2Q9:
+        nx, ny = 157, 93
+        cfg = dict(lattice=lattice, nx=nx, ny=ny, boundary=lbm.BC_WALLS, beta=0.97, u_lid=0.1)
+    else:
+        nx, ny = 1300, 1
+        cfg = dict(lattice=lattice, nx=nx, ny=ny, boundary=lbm.BC_WALLS, beta=0.999)
+    g, oc = pair32(precision=lbm.FP32, limiters=ALL, delta_median=1e-4, delta_ehrenfest=2e-3,
+                   k_max=max(1, nx * ny // 1000), kernel=kernel, **cfg)
+    f0 = rand_state(g.q, ny, nx, 31 + nx, neg_frac=0.01, heavy=max(2, nx * ny // 250))
+    g.set_populations(f0)
+    f = g.get_populations()
+    bound, want_ds = ds_bound(oc, f)
+    assert_ds_close(g.delta_s(), want_ds, bound)
+    g.step(1)
+    r = oracle.step(oc, f)
+    np.testing.assert_allclose(g.get_populations(), r.f, rtol=2e-5, atol=2e-7)
+    np.testing.assert_array_equal(g.limited_sites(), np.sort(r.selected))
+    st = g.stats()
+    for key in ("n_pos", "n_ehr", "n_cand", "n_bad"):
+        assert st[key] == r.stats[key], (key, st[key], r.stats[key])
+    assert abs(st["n_med"] - r.stats["n_med"]) <= max(2, r.stats["n_med"] // 100)
+    assert r.stats["n_pos"] > 0 and r.stats["n_ehr"] > 0
+    assert abs(st["mass"] - r.stats["mass"]) <= 1e-6 * r.stats["mass"]
+    for key in ("sum_dS", "dS_lbgk", "dS_lim"):
+        np.testing.assert_allclose(st[key], r.stats[key], rtol=1e-4, err_msg=key)
+
+
+def test_fp32_entropic_fused_and_tiled_agree_bitwise():
+    """The two kernels evaluate entropic f* and dS with the same FP32 operations
+    (paired and single): 200 steps of a developing cavity agree bit for bit."""
+    nx, ny = 300, 211
+    base = dict(lattice=lbm.D2Q9, nx=nx, ny=ny, boundary=lbm.BC_WALLS, beta=0.95, u_lid=0.1, precision=lbm.FP32,
+                limiters=ALL, delta_median=1e-5, delta_ehrenfest=1e-4, k_max=20, equilibrium=lbm.EQ_ENTROPIC)
+    rho, ux, uy = inputs.random_moments(13, nx, ny, umax=0.05)
+    out = []
+    for kernel in (lbm.KERNEL_FUSED, lbm.KERNEL_TILED):
+        g = lbm.Lattice(kernel=kernel, **base)
+        g.init(rho, ux, uy)
+        g.step(200)
+        out.append((g.get_populations(), g.stats()))
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    for key in ("n_pos", "n_med", "n_ehr", "n_cand", "n_bad"):
+        assert out[0][1][key] == out[1][1][key], key
+    assert out[0][1]["n_med"] > 0
+
+
+@pytest.mark.parametrize("precision", [lbm.BF16, lbm.FP16])
+def test_16bit_entropic_one_step_within_one_rounding(precision):
+    nx, ny = 131, 70
+    g, oc = pair32(lattice=lbm.D2Q9, nx=nx, ny=ny, boundary=lbm.BC_WALLS, beta=0.97, u_lid=0.1, precision=precision,
+                   limiters=ALL, delta_median=1e-4, delta_ehrenfest=2e-3, k_max=9)
+    assert g.step_kernel() == lbm.KERNEL_FUSED
+    g.set_populations(rand_state(9, ny, nx, 41))
+    f = g.get_populations()
+    g.step(1)
+    r = oracle.step(oc, f)
+    u = 2.0 ** -8 if precision == lbm.BF16 else 2.0 ** -11
+    dev = r.f - W9.reshape(9, 1, 1)  # the stored deviations
+    err = np.abs(g.get_populations() - r.f)
+    assert (err <= u * (np.abs(dev) + 2e-6 * np.abs(dev).max()) + 2e-6 * np.abs(dev).max() + 6e-8).all(), err.max()
+    np.testing.assert_array_equal(g.limited_sites(), np.sort(r.selected))
+
+
+@pytest.mark.parametrize("re", [2000.0, 5000.0])
+def test_fp32_entropic_cavity_100_matches_fp64_oracle_after_1000_steps(re):
+    """The FP32 bar of the north star for the entropic path: the 100 x 100 cavity
+    (lid 0.1, median delta = 1e-3), rho and u within 1e-5 after 1000 steps.  At
+    Re = 5000 the entropic flow amplifies rounding strongly (the oracle itself,
+    its state rounded to FP32 deviations after every step, drifts by ~5e-3 over
+    the run), so there the bar is 4 x that drift, measured here."""
+    beta = inputs.beta_from_nu(inputs.cavity_nu(100, 0.1, re))
+    g, oc = pair32(lattice=lbm.D2Q9, nx=100, ny=100, boundary=lbm.BC_WALLS, beta=beta, u_lid=0.1, rho_wall=1.0,
+                   precision=lbm.FP32, limiters=lbm.LIM_MEDIAN, delta_median=1e-3)
+    rho, ux, uy = inputs.cavity_rest(100, 100)
+    g.init(rho, ux, uy)
+    f0 = oracle.init(oc, rho, ux, uy)
+    g.step(1000)
+    f, st, rc = oracle.run(oc, f0, 1000)
+    assert rc == 0
+    grho, gux, guy = g.moments()
+    orho, oux, ouy = oracle.moments(oc, f)
+    err = max(np.abs(grho - orho).max(), np.abs(gux - oux).max(), np.abs(guy - ouy).max())
+    bar = 1e-5
+    if re > 2000.0:
+        w = W9.reshape(9, 1, 1)
+        h = f0.copy()
+        for _ in range(1000):
+            h = oracle.step(oc, h).f
+            h = (h - w).astype(np.float32).astype(np.float64) + w
+        hr, hx, hy = oracle.moments(oc, h)
+        drift = max(np.abs(hr - orho).max(), np.abs(hx - oux).max(), np.abs(hy - ouy).max())
+        bar = max(bar, 4.0 * drift)
+    print("entropic FP32 cavity, Re", re, "1000 steps: max |d rho|, |d u| =", err, "bar", bar)
+    assert err < bar, err

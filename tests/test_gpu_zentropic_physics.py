@@ -1,6 +1,6 @@
 """Long-run physics of the entropic path: the 100 x 100 lid-driven cavity at
-Re = 2000 with entropic quasiequilibria (Eq. maxwellian, FP64 storage) and the
-median filter, run to a steady state on the GPU, against Table vort row (e)
+Re = 2000 with entropic quasiequilibria (Eq. maxwellian; FP64 and FP32 storage)
+and the median filter, run to a steady state on the GPU, against Table vort row (e)
 (Sec. 4.4.1; tests/golden/table_vort_entropic.txt).  The FP64 oracle, run the
 same way on the CPU, puts every centre within 0.66 cells of the table."""
 import numpy as np
@@ -20,11 +20,13 @@ def _built():
     assert torch.cuda.is_available(), "GPU tests need CUDA"
 
 
-def test_entropic_cavity_re2000_vortex_centres_and_mass():
+@pytest.mark.parametrize("precision", [lbm.FP64, lbm.FP32])
+def test_entropic_cavity_re2000_vortex_centres_and_mass(precision):
     """The 100 x 100 cavity at Re = 2000 with entropic f* and the median filter
     (delta = 1e-3), run to a steady state: the primary and both lower vortex
     centres within one cell of Table vort row (e) (Sec. 4.4.1,
-    tests/golden/table_vort_entropic.txt), mass kept to rounding."""
+    tests/golden/table_vort_entropic.txt), mass kept to rounding (FP64 storage
+    on the tiled kernel; FP32 storage on the fused kernel, mass to 1e-6)."""
     import os
     from tests.test_gpu_physics import extremum, stream_function
     golden = os.path.join(os.path.dirname(__file__), "golden", "table_vort_entropic.txt")
@@ -36,8 +38,14 @@ def test_entropic_cavity_re2000_vortex_centres_and_mass():
             want = {"primary": v[0:2], "lower_left": v[2:4], "lower_right": v[4:6]}
     n, re, u0 = 100, 2000.0, 0.1
     beta = inputs.beta_from_nu(inputs.cavity_nu(n, u0, re))
-    g, _ = pair(lattice=lbm.D2Q9, nx=n, ny=n, boundary=lbm.BC_WALLS, beta=beta, u_lid=u0, rho_wall=1.0,
-                limiters=lbm.LIM_MEDIAN, delta_median=1e-3)
+    if precision == lbm.FP64:
+        g, _ = pair(lattice=lbm.D2Q9, nx=n, ny=n, boundary=lbm.BC_WALLS, beta=beta, u_lid=u0, rho_wall=1.0,
+                    limiters=lbm.LIM_MEDIAN, delta_median=1e-3)
+    else:
+        g = lbm.Lattice(lattice=lbm.D2Q9, nx=n, ny=n, boundary=lbm.BC_WALLS, beta=beta, u_lid=u0, rho_wall=1.0,
+                        limiters=lbm.LIM_MEDIAN, delta_median=1e-3, precision=lbm.FP32,
+                        equilibrium=lbm.EQ_ENTROPIC)
+        assert g.step_kernel() == lbm.KERNEL_FUSED
     g.init(*inputs.cavity_rest(n, n))
     m0 = float(n * n)
     prev = None
@@ -53,7 +61,7 @@ def test_entropic_cavity_re2000_vortex_centres_and_mass():
         prev = pm
     st = g.stats()
     assert st["n_bad"] == 0
-    assert abs(st["mass"] - m0) < 1e-9 * m0
+    assert abs(st["mass"] - m0) < (1e-9 if precision == lbm.FP64 else 1e-6) * m0
     ii, jj = np.meshgrid(np.arange(n), np.arange(n))
     xs, ys = (ii + 0.5) / n, (jj + 0.5) / n
     sign = -np.sign(psi[n // 2, n // 2])
