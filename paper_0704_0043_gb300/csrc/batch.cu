@@ -151,6 +151,7 @@ lbm_status rebuild(lbm_batch *b)
                 FinalArgs F{ctx_final_params(c, 1, lim, blocks), dst};
                 F.p.src = src;
                 F.p.fixed = 1;  // one work item per warp in batched launches: no counter to clear
+                F.p.partials = ctx_fx_rows(c);  // the fused kernel's accumulator rows
                 b->h_fin9[k].push_back(F);
                 if (k == 0)
                     for (int lb = 0; lb < blocks; ++lb)

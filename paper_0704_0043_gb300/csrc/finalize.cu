@@ -95,6 +95,40 @@ __device__ double fx_to_double(unsigned __int128 x)
     return (neg ? -d : d) * 5.42101086242752217003726400434970855712890625e-20;  // 2^-64
 }
 
+// The digit of a radix-selection pass: hist[d] counts the keys with digit d
+// among those still in play, and the rem-th of them is wanted, counting from
+// the top digit down (desc) or from digit 0 up.  Threads 0..255 scan the
+// counts with warp shuffles (integer sums, so the same on every run) and the
+// block picks the digit with __syncthreads_count; every thread of the block
+// must call this.  Writes the digit to *digit and the rank left within it to
+// *rem_left.
+__device__ void pick_digit(const unsigned *hist, long long rem, bool desc, unsigned long long *part,
+                           unsigned long long *digit, long long *rem_left)
+{
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    unsigned long long c = 0;
+    if (t < 256) {
+        c = hist[desc ? 255 - t : t];  // position t of the scan order
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, c, o);
+            if (lane >= o) c += y;
+        }
+        if (lane == 31) part[w] = c;
+    }
+    __syncthreads();
+    if (t < 256)
+        for (int j = 0; j < w; ++j) c += part[j];
+    // c = inclusive count up to scan position t; the wanted digit is the first
+    // position whose inclusive count reaches rem
+    const int before = __syncthreads_count(t < 256 && (long long)c < rem);
+    if (t == before && t < 256) {
+        *digit = (unsigned long long)(desc ? 255 - t : t);
+        *rem_left = rem - ((long long)c - (long long)hist[desc ? 255 - t : t]);
+    }
+    __syncthreads();
+}
+
 // BATCHED: block b finishes instance b of `table`; otherwise the single (p0, f0).
 template <int Q, typename S, bool BATCHED>
 __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, S *__restrict__ f0,
@@ -121,6 +155,7 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, 
     __shared__ int s_site[kCap];
     __shared__ int s_idx[kCap];
     __shared__ unsigned hist[256];
+    __shared__ unsigned long long s_part[8], s_digit;
     __shared__ unsigned long long s_prefix;
     __shared__ long long s_rem, s_step, s_rec;
     __shared__ int s_n, s_nsel, s_valid;
@@ -262,7 +297,30 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, 
         unsigned long long kv = 0;  // threshold dS pattern
         int site_thr = 0x7fffffff;
         const bool take_all = (long long)n_valid <= k;
-        if (!take_all) {
+        // few candidates (held in shared memory, at most one per thread): each
+        // thread ranks its own by counting the keys that beat it (larger dS, or
+        // equal dS at a lower site) -- one pass instead of the digit passes
+        const bool by_rank = !take_all && small && n <= kFinThreads;
+        if (by_rank) {
+            bool chosen = false;
+            if (t < n) {
+                const unsigned long long u = key_bits(s_key[t]);
+                const int st = s_site[t];
+                long long rank = 0;
+                if ((long long)u > 0) {
+                    for (int j = 0; j < n; ++j) {
+                        const unsigned long long v = key_bits(s_key[j]);
+                        rank += (long long)v > 0 && (v > u || (v == u && s_site[j] < st));
+                    }
+                    chosen = rank < k;
+                }
+            }
+            if (chosen) {
+                const int j = atomicAdd(&s_nsel, 1);
+                if (j < p.sel_cap) p.sel[j] = t;
+            }
+        }
+        if (!take_all && !by_rank) {
             unsigned long long prefix = 0, mask = 0;
             long long rem = k;
             for (int shift = 56; shift >= 0; shift -= 8) {
@@ -274,19 +332,8 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, 
                     if ((long long)u > 0 && (u & mask) == prefix) atomicAdd(&hist[(u >> shift) & 255u], 1u);
                 }
                 __syncthreads();
-                if (t == 0) {
-                    long long cum = 0;
-                    for (int d = 255; d >= 0; --d) {
-                        if (cum + (long long)hist[d] >= rem) {
-                            s_prefix = prefix | ((unsigned long long)d << shift);
-                            s_rem = rem - cum;
-                            break;
-                        }
-                        cum += hist[d];
-                    }
-                }
-                __syncthreads();
-                prefix = s_prefix;
+                pick_digit(hist, rem, true, s_part, &s_digit, &s_rem);
+                prefix = prefix | (s_digit << shift);
                 rem = s_rem;
                 mask |= 255ull << shift;
                 __syncthreads();
@@ -304,19 +351,8 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, 
                         atomicAdd(&hist[(s >> shift) & 255u], 1u);
                 }
                 __syncthreads();
-                if (t == 0) {
-                    long long cum = 0;
-                    for (int d = 0; d < 256; ++d) {
-                        if (cum + (long long)hist[d] >= rem) {
-                            s_prefix = (unsigned long long)(sprefix | ((unsigned)d << shift));
-                            s_rem = rem - cum;
-                            break;
-                        }
-                        cum += hist[d];
-                    }
-                }
-                __syncthreads();
-                sprefix = (unsigned)s_prefix;
+                pick_digit(hist, rem, false, s_part, &s_digit, &s_rem);
+                sprefix = sprefix | ((unsigned)s_digit << shift);
                 rem = s_rem;
                 smask |= 255u << shift;
                 __syncthreads();
@@ -324,7 +360,7 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, 
             site_thr = (int)sprefix;
         }
         // compaction of the chosen candidates (indices into the candidate list)
-        for (int i = t; i < n; i += kFinThreads) {
+        for (int i = t; i < n && !by_rank; i += kFinThreads) {
             const double key = key_of(i);
             const unsigned long long u = key_bits(key);
             const bool chosen = (long long)u > 0 && (take_all || u > kv || (u == kv && site_of(i) <= site_thr));

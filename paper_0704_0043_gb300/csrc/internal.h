@@ -50,6 +50,12 @@ struct EntState {
 // Sticky device status bits.
 enum : unsigned { kStatNonfinite = 1u, kStatTimeout = 2u, kStatCandOverflow = 4u };
 
+// Block rows of the tiled kernel are summed in chunks of kChunkRows by the
+// last block of each chunk to finish (fixed order within the chunk); the tail
+// kernel reduces the chunk rows.
+constexpr int kChunkRows = 256;
+__host__ __device__ inline int chunks_for(int blocks) { return (blocks + kChunkRows - 1) / kChunkRows; }
+
 // Per-block partial sums written by the step kernels, reduced in a fixed
 // order by the finalise kernel.
 enum { P_MASS = 0, P_SUM_DS, P_SUM_IN, P_DS_LIM, P_NPOS, P_NMED, P_NBAD, P_NSTAT };
@@ -113,7 +119,10 @@ struct StepParams {
     Cand *cand;
     int *cand_count;
     int cand_cap;
-    double *partials;          // [blocks][P_NSTAT] doubles; fused kernel: [kFxRows][kFxWords] fixed-point accumulators
+    double *partials;          // tiled kernel: [blocks][P_NSTAT] doubles
+    double *partials2;         // tiled kernel: [chunks][P_NSTAT] sums of kChunkRows block rows each
+    unsigned long long *fx_rows;  // fused kernel: [kFxRows][kFxWords] fixed-point accumulators (own region)
+    unsigned *chunk_cnt;       // tiled kernel: blocks of each chunk done this launch (reset by its last block)
     unsigned *status;
     int *work;                 // fused kernel: counter of work items handed out (nullptr: one item per warp)
     double *ds_out;            // optional FP64 dS(f') field (nx * ny) or nullptr
@@ -265,6 +274,7 @@ struct lbm_ctx {
     int sel_cap = 0;
     double *partials = nullptr;
     int partial_rows = 0;
+    unsigned *chunk_cnt = nullptr;  // tiled kernel: per-chunk block counters
     unsigned *status = nullptr;
     lbm::DevStats *ring = nullptr;
     int ring_len = 1;
@@ -305,6 +315,8 @@ StepParams cfg_step_params(const lbm_config &g, int q, int pitch, long long plan
 FinalParams cfg_final_params(const lbm_config &g, const StepParams &p, int collide, unsigned limiters, int nblocks);
 // Per-step parameters of a context (collide = 0 for a limiter pass).
 StepParams ctx_step_params(lbm_ctx *c, int collide, unsigned limiters);
+// The fused kernel's accumulator rows of a context (the tail's partials when fixed = 1).
+double *ctx_fx_rows(lbm_ctx *c);
 FinalParams ctx_final_params(lbm_ctx *c, int collide, unsigned limiters, int nblocks);
 bool ctx_uses_fused(const lbm_ctx *c);
 }  // namespace lbm

@@ -665,13 +665,15 @@ __device__ __forceinline__ float ent_term1(float d, float fs)
 {
     const float f = __fadd_rn(fs, d);
     if (!(f >= 0.f)) return f < 0.f ? __int_as_float(0x7f800000) : f;  // +inf, or NaN through
-    const float z = __fdiv_rn(d, __fadd_rn(__fadd_rn(fs, fs), d));
+    // the two quotients of the series by the hardware reciprocal (relative error
+    // below 2^-22): they scale a term of dS, not a population
+    const float z = __fmul_rn(d, rcp_approx(__fadd_rn(__fadd_rn(fs, fs), d)));
     if (fabsf(z) < 0.1f) {
         const float w = __fmul_rn(z, z);
         const float odd = __fmaf_rn(w, __fmaf_rn(w, 1.0f / 7.0f, 1.0f / 5.0f), 1.0f / 3.0f);
         const float even = __fmaf_rn(w, __fmaf_rn(w, __fmaf_rn(w, 1.0f / 7.0f, 1.0f / 5.0f), 1.0f / 3.0f), 1.0f);
         const float P = __fmaf_rn(z, odd, even);
-        return __fmul_rn(fs, __fdiv_rn(__fmul_rn(__fmul_rn(2.f, w), P), __fsub_rn(1.f, z)));
+        return __fmul_rn(fs, __fmul_rn(__fmul_rn(__fmul_rn(2.f, w), P), rcp_approx(__fsub_rn(1.f, z))));
     }
     if (f == 0.f) return fs;
     return __fsub_rn(__fmul_rn(f, logf(__fdiv_rn(f, fs))), d);
@@ -688,15 +690,33 @@ __device__ __forceinline__ float rel_entropy_dev(const float d[Q], const float f
     return s;
 }
 
-// The paired form for the fused kernel: the same operations per component.
+// ent_term1 for the two sites a lane of the fused kernel carries: the series
+// branch with paired instructions when both sites take it (the common case),
+// else site by site; the same operations per component, so the same bits.
+__device__ __forceinline__ float2 ent_term2(float2 d, float2 fs)
+{
+    using O = F2;
+    const float2 f = O::add(fs, d);
+    const float2 den = O::add(O::add(fs, fs), d);
+    const float2 z = O::mul(d, make_float2(rcp_approx(den.x), rcp_approx(den.y)));
+    if (f.x >= 0.f && f.y >= 0.f && fabsf(z.x) < 0.1f && fabsf(z.y) < 0.1f) {
+        const float2 w = O::mul(z, z);
+        const float2 odd = O::fma(w, O::fma(w, O::s(1.0f / 7.0f), O::s(1.0f / 5.0f)), O::s(1.0f / 3.0f));
+        const float2 even =
+            O::fma(w, O::fma(w, O::fma(w, O::s(1.0f / 7.0f), O::s(1.0f / 5.0f)), O::s(1.0f / 3.0f)), O::s(1.0f));
+        const float2 P = O::fma(z, odd, even);
+        const float2 om = O::sub(O::s(1.f), z);
+        return O::mul(fs, O::mul(O::mul(O::mul(O::s(2.f), w), P), make_float2(rcp_approx(om.x), rcp_approx(om.y))));
+    }
+    return make_float2(ent_term1(d.x, fs.x), ent_term1(d.y, fs.y));
+}
+
+// The paired form of rel_entropy_dev<9> for the fused kernel.
 __device__ __forceinline__ float2 rel_entropy9_x(const float2 d[9], const float2 fsa[9])
 {
     float2 s = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        s.x = __fadd_rn(s.x, ent_term1(d[k].x, fsa[k].x));
-        s.y = __fadd_rn(s.y, ent_term1(d[k].y, fsa[k].y));
-    }
+    for (int k = 0; k < 9; ++k) s = F2::add(s, ent_term2(d[k], fsa[k]));
     return s;
 }
 

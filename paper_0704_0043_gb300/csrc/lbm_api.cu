@@ -66,12 +66,6 @@ bool fused_applies(const lbm_config &c)
            c.kernel != LBM_KERNEL_TILED && fused_d2q9_fits((long long)c.ny * row_pitch(c.nx));
 }
 
-int tiled_blocks(const lbm_config &c)
-{
-    if (c.lattice == LBM_D2Q9) return ((c.nx + 29) / 30) * ((c.ny + 5) / 6);
-    return (c.nx + 253) / 254;
-}
-
 std::string validate(const lbm_config *c)
 {
     if (!c) return "config is NULL";
@@ -122,6 +116,7 @@ std::string validate(const lbm_config *c)
 }
 
 size_t ens_bytes() { return (2 * (size_t)kEnsBlocks + 4) * sizeof(double); }
+size_t fx_bytes() { return (size_t)kFxRows * kFxWords * sizeof(unsigned long long); }
 
 struct Sizes {
     int q, pitch;
@@ -131,7 +126,7 @@ struct Sizes {
     int64_t total() const
     {
         return (int64_t)(2 * field + cand + sel + partials + ring + ens_bytes() + ent + 64 * sizeof(long long) +
-                         4096);
+                         (size_t)chunks_for(rows) * sizeof(unsigned) + 4096);
     }
 };
 
@@ -148,10 +143,9 @@ Sizes sizes_for(const lbm_config &c)
     z.cand = (size_t)z.cand_cap * sizeof(Cand);
     z.sel_cap = (int)std::max<long long>(1, std::min<long long>(c.k_max, n));
     z.sel = (size_t)z.sel_cap * sizeof(int);
-    z.rows = tiled_blocks(c);
-    z.partials = (size_t)z.rows * P_NSTAT * sizeof(double);
-    if (fused_applies(c))
-        z.partials = std::max(z.partials, (size_t)kFxRows * kFxWords * sizeof(unsigned long long));
+    // [fused accumulator rows][tiled block rows][chunk rows]
+    z.rows = tiled_blocks_for(z.q, c.nx, c.ny);
+    z.partials = fx_bytes() + (size_t)(z.rows + chunks_for(z.rows)) * P_NSTAT * sizeof(double);
     z.ring_len = std::max(1, c.stats_history);
     z.ring = (size_t)z.ring_len * sizeof(DevStats);
     // Eq. EntThresh: the pass's dS field (compute precision) and the solve's state
@@ -207,7 +201,10 @@ StepParams step_params(lbm_ctx *c, int collide, unsigned limiters)
     p.cand = c->cand;
     p.cand_count = c->counts;
     p.cand_cap = c->cand_cap;
-    p.partials = c->partials;
+    p.fx_rows = reinterpret_cast<unsigned long long *>(c->partials);
+    p.partials = c->partials + fx_bytes() / sizeof(double);
+    p.partials2 = p.partials + (size_t)c->partial_rows * P_NSTAT;
+    p.chunk_cnt = c->chunk_cnt;
     p.status = c->status;
     p.work = c->counts + 2;
     p.ens = c->ens + 2 * kEnsBlocks;
@@ -219,8 +216,9 @@ StepParams step_params(lbm_ctx *c, int collide, unsigned limiters)
 FinalParams final_params(lbm_ctx *c, int collide, unsigned limiters, int nblocks)
 {
     const StepParams p = step_params(c, collide, limiters);
-    FinalParams f = cfg_final_params(c->cfg, p, collide, limiters, nblocks);
-    f.partials = c->partials;
+    // the tiled kernel's chunk rows (the fused path points the tail at its accumulator rows)
+    FinalParams f = cfg_final_params(c->cfg, p, collide, limiters, chunks_for(nblocks));
+    f.partials = p.partials2;
     f.cand = c->cand;
     f.cand_count = c->counts;
     f.cand_cap = c->cand_cap;
@@ -301,6 +299,7 @@ lbm_status run_pass(lbm_ctx *c, int collide, unsigned limiters)
     if ((ms = mark(c)) != LBM_OK) return ms;
     FinalParams f = final_params(c, collide, limiters, nblocks);
     f.fixed = fused ? 1 : 0;
+    if (fused) f.partials = c->partials;  // the fixed-point accumulator rows
     f.work = fused ? c->counts + 2 : nullptr;
     e = with_storage(c->cfg.precision, [&](auto tag) -> cudaError_t {
         using S = STORAGE_T;
@@ -331,7 +330,7 @@ lbm_status reset_counters(lbm_ctx *c)
     CK(c, cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->stream));
     CK(c, cudaMemsetAsync(c->counts, 0, 4 * sizeof(int), c->stream));
     if (fused_applies(c->cfg))  // the fused kernel's fixed-point accumulators
-        CK(c, cudaMemsetAsync(c->partials, 0, (size_t)kFxRows * kFxWords * sizeof(unsigned long long), c->stream));
+        CK(c, cudaMemsetAsync(c->partials, 0, fx_bytes(), c->stream));
     CK(c, cudaMemsetAsync(c->ring, 0, (size_t)c->ring_len * sizeof(DevStats), c->stream));
     return LBM_OK;
 }
@@ -390,7 +389,7 @@ void free_all(lbm_ctx *c)
     if (c->gstream) cudaStreamDestroy(c->gstream);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     c->events.clear();
-    void *ptrs[] = {c->buf[0], c->buf[1], c->cand, c->counts, c->sel, c->partials,
+    void *ptrs[] = {c->buf[0], c->buf[1], c->cand, c->counts, c->sel, c->partials, c->chunk_cnt,
                     c->status, c->ring, c->counters, c->stage, c->ens, c->probe, c->ent_field, c->ent};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -494,6 +493,7 @@ FinalParams ctx_final_params(lbm_ctx *c, int collide, unsigned limiters, int nbl
     return final_params(c, collide, limiters, nblocks);
 }
 bool ctx_uses_fused(const lbm_ctx *c) { return fused_applies(c->cfg); }
+double *ctx_fx_rows(lbm_ctx *c) { return c->partials; }
 }  // namespace lbm
 
 extern "C" {
@@ -571,6 +571,7 @@ lbm_status lbm_create(const lbm_config *cfg, void *cuda_stream, lbm_ctx **out)
     alloc((void **)&c->counts, 4 * sizeof(int));
     alloc((void **)&c->sel, z.sel);
     alloc((void **)&c->partials, z.partials);
+    alloc((void **)&c->chunk_cnt, (size_t)chunks_for(z.rows) * sizeof(unsigned));
     alloc((void **)&c->status, sizeof(unsigned));
     alloc((void **)&c->ring, z.ring);
     alloc((void **)&c->counters, 2 * sizeof(long long));

@@ -33,9 +33,10 @@ unsigned char *g_scratch_addr[kMaxDevices] = {nullptr};
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 struct Layout {
-    size_t counters, status, counts, ring, partials, sel, cand, total;
+    size_t counters, status, counts, chunk_cnt, ring, partials, partials2, sel, cand, total;
 };
 
+// Everything before `ring` is cleared by each call.
 Layout layout_for(long long sites, int rows, long long k_max, bool ehrenfest)
 {
     Layout L{};
@@ -46,10 +47,14 @@ Layout layout_for(long long sites, int rows, long long k_max, bool ehrenfest)
     off = align_up(off + sizeof(unsigned), 256);
     L.counts = off;
     off = align_up(off + 2 * sizeof(int), 256);
+    L.chunk_cnt = off;
+    off = align_up(off + (size_t)chunks_for(rows) * sizeof(unsigned), 256);
     L.ring = off;
     off = align_up(off + sizeof(DevStats), 256);
     L.partials = off;
     off = align_up(off + (size_t)rows * P_NSTAT * sizeof(double), 256);
+    L.partials2 = off;
+    off = align_up(off + (size_t)chunks_for(rows) * P_NSTAT * sizeof(double), 256);
     const long long sel = k_max < sites ? k_max : sites;
     L.sel = off;
     off = align_up(off + (size_t)(sel > 1 ? sel : 1) * sizeof(int), 256);
@@ -135,7 +140,8 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_config *cfg, const double *f_in
     unsigned char *base = g_scratch_addr[dev];
     cudaStream_t s = (cudaStream_t)cuda_stream;
 
-    // Everything that must start at zero: counters, status, candidate counts.
+    // Everything that must start at zero: counters, status, candidate counts,
+    // the tiled kernel's chunk counters.
     if ((e = cudaMemsetAsync(base, 0, L.ring, s)) != cudaSuccess) return cuda_error(e, "cudaMemsetAsync");
 
     // The kernels address element (k, y, x) at k * plane + y * pitch + kLead + x;
@@ -146,6 +152,9 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_config *cfg, const double *f_in
     p.cand_count = (int *)(base + L.counts);
     p.cand_cap = ehr ? (int)sites : 1;
     p.partials = (double *)(base + L.partials);
+    p.partials2 = (double *)(base + L.partials2);
+    p.chunk_cnt = (unsigned *)(base + L.chunk_cnt);
+    p.fx_rows = nullptr;
     p.status = (unsigned *)(base + L.status);
     p.work = nullptr;
     p.ens = nullptr;
@@ -156,10 +165,10 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_config *cfg, const double *f_in
     if (nblocks != rows)
         return set_thread_error(LBM_ERR_CUDA, "lbm_step_noalloc: block count differs from the scratch layout");
 
-    FinalParams f = cfg_final_params(*cfg, p, 1, cfg->limiters, nblocks);
+    FinalParams f = cfg_final_params(*cfg, p, 1, cfg->limiters, chunks_for(nblocks));
     f.fixed = 0;
     f.work = nullptr;
-    f.partials = p.partials;
+    f.partials = p.partials2;
     f.cand = p.cand;
     f.cand_count = p.cand_count;
     f.cand_cap = p.cand_cap;

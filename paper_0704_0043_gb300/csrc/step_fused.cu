@@ -744,7 +744,7 @@ __global__ void __launch_bounds__(kThreads, (BATCHED || ENT) ? 3 : kBlocksPerSM)
     // 128-bit sum as two 64-bit adds with the carry passed on); the tail
     // kernel reads the rows and clears them for the next step
     if (t < kFxWords) {
-        unsigned long long *row = reinterpret_cast<unsigned long long *>(p.partials) + (long long)(bid % kFxRows) * kFxWords;
+        unsigned long long *row = p.fx_rows + (long long)(bid % kFxRows) * kFxWords;
         if (t < 4) {
             unsigned __int128 v = 0;
 #pragma unroll

@@ -21,7 +21,8 @@ namespace lbm {
 namespace {
 
 constexpr int kTX = 32, kTY = 8;  // D2Q9 tile of computed sites; (kTX-2) x (kTY-2) finished
-constexpr int kT1 = 256;          // D1Q3 tile; kT1 - 2 finished
+constexpr int kT1 = 64;           // D1Q3 tile; kT1 - 2 finished (small tiles: a short tube spreads over
+                                  // many SMs; GB300's FP64 pipe is narrow per SM)
 
 __device__ __forceinline__ long long fidx(long long plane, int pitch, int k, int y, int x)
 {
@@ -577,10 +578,33 @@ __global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const S *__r
         }
     }
     __syncthreads();
+    const int bid = by * gx + bx;
     if (lin < P_NSTAT) {
         double v = 0.0;
         for (int w = 0; w < (BX * BY) / 32; ++w) v += sred[w][lin];
-        p.partials[((long long)by * gx + bx) * P_NSTAT + lin] = v;
+        p.partials[(long long)bid * P_NSTAT + lin] = v;
+    }
+    // The last block of each chunk of kChunkRows blocks to finish sums the
+    // chunk's rows in row order (a ticket, no waiting): the tail then reads one
+    // row per chunk, and the sums are the same whichever block comes last.
+    __shared__ int s_last;
+    const int nblk = BATCHED ? sA.blocks : (int)(gridDim.x * gridDim.y);
+    const int chunk = bid / kChunkRows;
+    const int rows = min(kChunkRows, nblk - chunk * kChunkRows);
+    __threadfence();
+    __syncthreads();
+    if (lin == 0) s_last = atomicAdd(p.chunk_cnt + chunk, 1u) == (unsigned)(rows - 1);
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        const double *base = p.partials + (long long)chunk * kChunkRows * P_NSTAT;
+        for (int stat = warp; stat < P_NSTAT; stat += (BX * BY) / 32) {
+            double v = 0.0;
+            for (int r = lane; r < rows; r += 32) v += __ldcg(base + (long long)r * P_NSTAT + stat);
+            v = warp_sum(v);
+            if (lane == 0) p.partials2[(long long)chunk * P_NSTAT + stat] = v;
+        }
+        if (lin == 0) p.chunk_cnt[chunk] = 0u;  // for the next launch
     }
 }
 

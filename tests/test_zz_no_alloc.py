@@ -37,7 +37,7 @@ def _case(name):
         f0 = inputs.random_populations(78, 9, 45, 70, W9, 0.15, neg_frac=0.01)
         return cfg, f0
     if name == "tube":
-        # D1Q3 rows are 254-site tiles: 1000 sites give four tiles and a ragged tail
+        # D1Q3 tiles finish 62 sites each: 1000 sites give 17 tiles, the last one ragged
         cfg = dict(lattice=lbm.D1Q3, nx=1000, ny=1, boundary=lbm.BC_WALLS, precision=lbm.FP64,
                    beta=0.99, limiters=ALL, delta_median=1e-5, delta_ehrenfest=1e-4, k_max=4)
         f0 = inputs.random_populations(79, 3, 1, 1000, W3, 0.1, neg_frac=0.005)
