@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--develop", type=int, default=-1,
                     help="untimed steps before warm-up so the flow has left the rest state "
                          "(default: the 4096^2 cavity's full 1e4 steps; 0 for the small workloads)")
-    ap.add_argument("--kernel", default="auto", choices=["auto", "tiled", "fused"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "tiled", "fused", "tube"])
     ap.add_argument("--limiters", default="median+ehrenfest",
                     choices=["median+ehrenfest", "smooth+ehrenfest", "threshold+ehrenfest", "entthresh+ehrenfest"],
                     help="smooth / threshold: the ensemble-dependent limiters (tiled kernel, E(dS) reduction first)")
@@ -165,6 +165,8 @@ KERNEL_SOURCES = {
     "fused": ["paper_0704_0043_gb300/csrc/step_fused.cu", "paper_0704_0043_gb300/csrc/keys.cuh",
               "paper_0704_0043_gb300/csrc/lattice.cuh", "paper_0704_0043_gb300/csrc/internal.h",
               "include/lbm.h"],
+    "tube": ["paper_0704_0043_gb300/csrc/step_tube.cu", "paper_0704_0043_gb300/csrc/lattice.cuh",
+             "paper_0704_0043_gb300/csrc/internal.h", "include/lbm.h"],
     "tiled": ["paper_0704_0043_gb300/csrc/step_tiled.cu", "paper_0704_0043_gb300/csrc/lattice.cuh",
               "paper_0704_0043_gb300/csrc/internal.h", "include/lbm.h"],
 }
@@ -259,7 +261,7 @@ def workload(side: int = 4096):
 
 def lattice_kwargs(w, kernel: str, precision: str = "fp32", equilibrium: str = "polynomial"):
     from paper_0704_0043_gb300 import lbm
-    km = {"auto": lbm.KERNEL_AUTO, "tiled": lbm.KERNEL_TILED, "fused": lbm.KERNEL_FUSED}[kernel]
+    km = {"auto": lbm.KERNEL_AUTO, "tiled": lbm.KERNEL_TILED, "fused": lbm.KERNEL_FUSED, "tube": lbm.KERNEL_TUBE}[kernel]
     pm = {"fp32": lbm.FP32, "bf16": lbm.BF16, "fp16": lbm.FP16, "fp64": lbm.FP64}[precision]
     em = {"polynomial": lbm.EQ_POLYNOMIAL, "entropic": lbm.EQ_ENTROPIC}[equilibrium]
     return dict(lattice=lbm.D2Q9, nx=w.nx, ny=w.ny, boundary=lbm.BC_WALLS, precision=pm,
@@ -566,7 +568,8 @@ def single_workload(args, lbm, inputs):
         prec = args.precision or "fp64"
         kw = dict(lattice=lbm.D1Q3, nx=w.nx, ny=1, boundary=lbm.BC_WALLS,
                   precision={"fp32": lbm.FP32, "fp64": lbm.FP64}[prec], beta=w.beta, limiters=w.limiters,
-                  delta_ehrenfest=w.delta_ehrenfest, k_max=w.k_max)
+                  delta_ehrenfest=w.delta_ehrenfest, k_max=w.k_max,
+                  kernel={"auto": lbm.KERNEL_AUTO, "tiled": lbm.KERNEL_TILED, "tube": lbm.KERNEL_TUBE}[args.kernel])
         return w, kw, "d1q3", prec
     if args.workload == "cavity100":
         # the 100 x 100 cavity at Re = 5000 (lid 0.1), median filter, FP32
@@ -716,7 +719,7 @@ def main():
         kern_s = elapsed / args.steps
     achieved = bps * w.sites / kern_s / 1e9
     peak, peak_kind = peaks()
-    kname = "fused" if lat.step_kernel() == lbm.KERNEL_FUSED else "tiled"
+    kname = {lbm.KERNEL_FUSED: "fused", lbm.KERNEL_TUBE: "tube"}.get(lat.step_kernel(), "tiled")
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_kind": peak_kind,
             "traffic": traffic_from_profile(f"{kname}_{prec}", w.sites) if lat_kind == "d2q9" else None,
@@ -727,9 +730,13 @@ def main():
         roof["note"] = ("the lattice lives in L2 (%.1f MB of populations); the step is launch- and "
                         "latency-bound, so this fraction is no HBM claim" % (w.sites * bps / 1e6))
     if ensemble:
-        roof["kernel"] = "k_ens_partial + k_ens_mean + " + ("EntThresh solve + " if args.limiters.startswith("entthresh")
-                                                               else "") + ("k_fused" if kname == "fused" else "k_tiled")
-        roof["traffic"] = traffic_from_profile("tiled_fp32_ensemble", w.sites)
+        # E(dS) by the fused kernel's row streaming (nothing stored) for FP32
+        # cavities, by k_ens_partial otherwise
+        epass = "k_fused E(dS) pass + k_ens_fx" if prec == "fp32" else "k_ens_partial + k_ens_mean"
+        roof["kernel"] = epass + " + " + ("EntThresh solve + " if args.limiters.startswith("entthresh")
+                                           else "") + ("k_fused" if kname == "fused" else "k_tiled")
+        roof["traffic"] = traffic_from_profile("fused_fp32_ensemble" if prec == "fp32" else "tiled_fp32_ensemble",
+                                               w.sites)
 
     if entropic and prec == "fp64":
         # The entropic step is bound by FP64 arithmetic (a logarithm per population

@@ -150,9 +150,13 @@ enum { LBM_PHI_HOMOTHETY = 0, LBM_PHI_ENTROPY = 1 };
 
 /* Kernel choice for lbm_step. */
 enum {
-    LBM_KERNEL_AUTO = 0,    /* fused D2Q9 cavity kernel where it applies, else the tiled kernel */
+    LBM_KERNEL_AUTO = 0,    /* the fused D2Q9 cavity kernel or the D1Q3 tube kernel where it applies,
+                               else the tiled kernel */
     LBM_KERNEL_TILED = 1,   /* overlapping-tile kernel: every lattice, boundary and precision */
-    LBM_KERNEL_FUSED = 2    /* D2Q9 with LBM_BC_WALLS, FP32/BF16/FP16 storage: row-streaming fused kernel */
+    LBM_KERNEL_FUSED = 2,   /* D2Q9 with LBM_BC_WALLS, FP32/BF16/FP16 storage: row-streaming fused kernel */
+    LBM_KERNEL_TUBE = 3     /* D1Q3 with FP32 or FP64 storage, LBM_BC_WALLS or LBM_BC_PERIODIC, no
+                               ensemble-dependent limiter: a streaming pass, one chunk of sites per warp
+                               (the same populations as the tiled kernel, bit for bit) */
 };
 
 typedef struct lbm_config {
@@ -311,8 +315,8 @@ lbm_status lbm_set_graph(lbm_ctx *ctx, int32_t steps_per_graph);
 lbm_status lbm_timing(lbm_ctx *ctx, int32_t enable);
 lbm_status lbm_timing_read(lbm_ctx *ctx, double *step_kernel_ms, double *tail_kernel_ms, int64_t *steps);
 
-/* The step kernel lbm_step launches for this context: LBM_KERNEL_TILED or
- * LBM_KERNEL_FUSED (-1 for a NULL context). */
+/* The step kernel lbm_step launches for this context: LBM_KERNEL_TILED,
+ * LBM_KERNEL_FUSED or LBM_KERNEL_TUBE (-1 for a NULL context). */
 int32_t lbm_step_kernel(const lbm_ctx *ctx);
 
 /* Number of kernel launches the context has enqueued so far. */

@@ -82,17 +82,18 @@ lbm_status lbm_batch_lattice_status(const lbm_batch *b, int32_t slot);
 lbm_status lbm_batch_set_graph(lbm_batch *b, int32_t steps_per_graph);
 
 /* Work-split autotuner: times `trial_steps` batched steps for each candidate
- * (segments chosen per lattice, 8 or 16 rows; 1, 2, 4 or 8 waves of work items),
+ * (automatic segments for 2, 4, 8 or 16 work items per resident warp; fixed
+ * 8- or 16-row segments),
  * keeps the fastest, and restores every lattice's state, counters and stats
  * to what they were before.  *best_ms receives the winning time per step
  * (may be NULL). */
 lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_steps, double *best_ms);
 
 /* Fixes the fused kernel's work split: seg_rows = rows per work item (a warp
- * walking a strip of 62 columns; 0: chosen per lattice, else >= 4), waves 1,
- * 2, 4 or 8 (work items per lattice in proportion to its sites, one wave = the
- * GPU's resident warps).  The split changes the speed only, never a result.
- * Errors: LBM_ERR_INVALID_ARG. */
+ * walking a strip of 62 columns; 0: automatic, else >= 4), waves 1 .. 64 (with
+ * automatic segments: about this many work items per resident warp over the
+ * fused lattices together; the items are handed out dynamically).  The split
+ * changes the speed only, never a result.  Errors: LBM_ERR_INVALID_ARG. */
 lbm_status lbm_batch_set_shape(lbm_batch *b, int32_t seg_rows, int32_t waves);
 
 /* Kernel launches enqueued by lbm_batch_step so far (graph replays count

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "liblbm.so")
-SOURCES = ["lbm_api.cu", "step_tiled.cu", "finalize.cu", "step_fused.cu", "noalloc.cu", "batch.cu", "entthresh.cu"]
+SOURCES = ["lbm_api.cu", "step_tiled.cu", "finalize.cu", "step_fused.cu", "noalloc.cu", "batch.cu", "entthresh.cu", "step_tube.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
          "-I", INCLUDE, "-I", CSRC]

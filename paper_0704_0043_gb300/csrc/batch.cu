@@ -1,14 +1,18 @@
 // batch.cu -- many lattices stepped by shared launches (include/lbm_batch.h).
 //
 // Each lattice is an ordinary context (lbm_ctx) created on the batch's own
-// stream.  A batched step is at most five launches whatever the number of
-// lattices: the fused kernel over every FP32 D2Q9 cavity, the tiled kernel
-// over D1Q3 and over other D2Q9 lattices, and the tail kernel (one block per
-// lattice) for D2Q9 and for D1Q3.  Every block finds its lattice and its
-// local block number in a device table; the tables exist twice, for even and
-// odd steps, because the two population buffers of each lattice swap roles
-// every step.  A lattice's per-site arithmetic is the same as when it runs
-// alone, so its populations match a lone run bit for bit.
+// stream.  A batched step is at most six launches whatever the number of
+// lattices: the fused kernel over every FP32 D2Q9 cavity, the tube kernel
+// over D1Q3 lattices, the tiled kernel over the rest, and the tail kernel (one
+// block per lattice) for D2Q9 and for D1Q3.  The fused launch is one wave of resident
+// warps over the work items of all its lattices (strips of 62 columns times
+// short row segments), handed out through one device counter, so warps that
+// finish early take more work whatever lattice it belongs to; the tube launch
+// does the same over groups of 1024 sites of every tube; tiled blocks find
+// their lattice and local block number in a device table.  The tables
+// exist twice, for even and odd steps, because the two population buffers of
+// each lattice swap roles every step.  A lattice's per-site arithmetic is the
+// same as when it runs alone, so its populations match a lone run bit for bit.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -33,17 +37,21 @@ struct lbm_batch {
     std::vector<FusedArgs> h_fused[2];
     std::vector<TiledArgs> h_t3[2], h_t9[2];
     std::vector<FinalArgs> h_fin9[2], h_fin3[2];
-    std::vector<int2> h_fmap, h_t3map, h_t9map;
+    std::vector<int2> h_fmap, h_t3map, h_t9map, h_tubemap;
+    std::vector<TubeArgs> h_tube[2];
     void *table_mem = nullptr;
     size_t table_bytes = 0;
     FusedArgs *fused[2] = {nullptr, nullptr};
     TiledArgs *t3[2] = {nullptr, nullptr}, *t9[2] = {nullptr, nullptr};
     FinalArgs *fin9[2] = {nullptr, nullptr}, *fin3[2] = {nullptr, nullptr};
-    int2 *fmap = nullptr, *t3map = nullptr, *t9map = nullptr;
-    int fblocks = 0, t3blocks = 0, t9blocks = 0, n9 = 0, n3 = 0;
+    int2 *fmap = nullptr, *t3map = nullptr, *t9map = nullptr, *tubemap = nullptr;
+    TubeArgs *tube[2] = {nullptr, nullptr};
+    int *work = nullptr;   // the fused launch's work-item counter
+    int *twork = nullptr;  // the tube launch's
+    int fitems = 0, t3blocks = 0, t9blocks = 0, titems = 0, n9 = 0, n3 = 0;
     // shape
     int seg_rows = 0;  // rows per fused work item; 0 = automatic
-    int waves = 1;     // fused work-item budget, in waves of resident warps
+    int waves = 8;     // automatic segments: about this many work items per resident warp
     // graph replay
     int graph_steps = 0;
     cudaGraphExec_t exec = nullptr;
@@ -118,22 +126,28 @@ lbm_status rebuild(lbm_batch *b)
     for (int k = 0; k < 2; ++k) {
         b->h_fused[k].clear();
         b->h_t3[k].clear();
+        b->h_tube[k].clear();
         b->h_t9[k].clear();
         b->h_fin9[k].clear();
         b->h_fin3[k].clear();
     }
     b->h_fmap.clear();
     b->h_t3map.clear();
+    b->h_tubemap.clear();
     b->h_t9map.clear();
     b->cur_build.assign(b->slots.size(), 0);
-    // fused block budget per lattice, in proportion to its sites
-    long long fused_sites = 0;
+    int first_fused = -1;  // index in h_fin9 of the first fused lattice's tail
+    int first_tube = -1;   // index in h_fin3 of the first tube's tail
+    // one row-segment length for every fused lattice: about `waves` items per
+    // resident warp over the strip rows of all of them (unless fixed)
+    long long strip_rows = 0;
     for (lbm_ctx *c : b->slots) {
         if (!c) continue;
         if (!c->ready) return bfail(b, LBM_ERR_STATE, "a lattice of the batch was never initialised");
-        if (ctx_uses_fused(c)) fused_sites += (long long)c->cfg.nx * c->cfg.ny;
+        if (ctx_uses_fused(c)) strip_rows += (long long)((c->cfg.nx + 61) / 62) * c->cfg.ny;
     }
-    const double budget = (double)b->waves * fused_slots(4, true);
+    const long long want = std::max(1LL, (long long)b->waves * fused_slots(4, true));
+    const int seg = b->seg_rows > 0 ? b->seg_rows : (int)std::max(4LL, (strip_rows + want - 1) / want);
     for (size_t i = 0; i < b->slots.size(); ++i) {
         lbm_ctx *c = b->slots[i];
         if (!c) continue;
@@ -143,19 +157,37 @@ lbm_status rebuild(lbm_batch *b)
         for (int k = 0; k < 2; ++k) {
             void *src = c->buf[c->cur ^ k], *dst = c->buf[c->cur ^ k ^ 1];
             if (ctx_uses_fused(c)) {
-                const long long sites = (long long)c->cfg.nx * c->cfg.ny;
-                const int slots = std::max(1, (int)std::lround(budget * (double)sites / (double)fused_sites));
                 FusedArgs A;
-                const int blocks = fused_make_args(p, src, dst, b->seg_rows, slots, &A);
+                const int blocks = fused_make_args(p, src, dst, seg, 1, &A);
                 b->h_fused[k].push_back(A);
                 FinalArgs F{ctx_final_params(c, 1, lim, blocks), dst};
                 F.p.src = src;
-                F.p.fixed = 1;  // one work item per warp in batched launches: no counter to clear
+                F.p.fixed = 1;
                 F.p.partials = ctx_fx_rows(c);  // the fused kernel's accumulator rows
+                F.p.work = nullptr;             // the first fused lattice's tail clears the counter (below)
+                if (first_fused < 0 && k == 0) first_fused = (int)b->h_fin9[0].size();
                 b->h_fin9[k].push_back(F);
                 if (k == 0)
-                    for (int lb = 0; lb < blocks; ++lb)
-                        b->h_fmap.push_back(make_int2((int)b->h_fused[0].size() - 1, lb));
+                    for (int it = 0; it < A.items; ++it)
+                        b->h_fmap.push_back(make_int2((int)b->h_fused[0].size() - 1, it));
+            } else if (c->q == 3 && tube_applies(c->cfg, lim)) {
+                // D1Q3: the tube kernel, groups of chunks from one counter
+                TubeArgs A{};
+                A.p = p;
+                A.src = src;
+                A.dst = dst;
+                const int groups = tube_groups(c->cfg.nx);
+                b->h_tube[k].push_back(A);
+                FinalArgs F{ctx_final_params(c, 1, lim, groups), dst};
+                F.p.src = src;
+                F.p.partials = p.partials;  // one row per group
+                F.p.nblocks = groups;
+                F.p.work = nullptr;         // the first tube's tail clears the counter (below)
+                if (first_tube < 0 && k == 0) first_tube = (int)b->h_fin3[0].size();
+                b->h_fin3[k].push_back(F);
+                if (k == 0)
+                    for (int gi = 0; gi < groups; ++gi)
+                        b->h_tubemap.push_back(make_int2((int)b->h_tube[0].size() - 1, gi));
             } else {
                 TiledArgs A{};
                 A.p = p;
@@ -177,11 +209,12 @@ lbm_status rebuild(lbm_batch *b)
     // one device allocation holds every table
     auto sz = [](size_t n, size_t e) { return ((n * e + 255) / 256) * 256; };
     const size_t nf = b->h_fused[0].size(), nt3 = b->h_t3[0].size(), nt9 = b->h_t9[0].size();
-    const size_t nf9 = b->h_fin9[0].size(), nf3 = b->h_fin3[0].size();
+    const size_t nf9 = b->h_fin9[0].size(), nf3 = b->h_fin3[0].size(), ntb = b->h_tube[0].size();
     size_t need = 2 * (sz(nf, sizeof(FusedArgs)) + sz(nt3, sizeof(TiledArgs)) + sz(nt9, sizeof(TiledArgs)) +
-                       sz(nf9, sizeof(FinalArgs)) + sz(nf3, sizeof(FinalArgs))) +
+                       sz(nf9, sizeof(FinalArgs)) + sz(nf3, sizeof(FinalArgs)) + sz(ntb, sizeof(TubeArgs))) +
+                  sz(b->h_tubemap.size(), sizeof(int2)) + 256 +
                   sz(b->h_fmap.size(), sizeof(int2)) + sz(b->h_t3map.size(), sizeof(int2)) +
-                  sz(b->h_t9map.size(), sizeof(int2)) + 256;
+                  sz(b->h_t9map.size(), sizeof(int2)) + 256 + 256;
     if (need > b->table_bytes) {
         BCK(b, cudaStreamSynchronize(b->run));
         if (b->table_mem) cudaFree(b->table_mem);
@@ -191,6 +224,14 @@ lbm_status rebuild(lbm_batch *b)
         b->table_bytes = need;
     }
     char *m = (char *)b->table_mem;
+    b->work = (int *)m;
+    m += 256;
+    b->twork = (int *)m;
+    m += 256;
+    if (first_fused >= 0)
+        for (int k = 0; k < 2; ++k) b->h_fin9[k][(size_t)first_fused].p.work = b->work;
+    if (first_tube >= 0)
+        for (int k = 0; k < 2; ++k) b->h_fin3[k][(size_t)first_tube].p.work = b->twork;
     auto put = [&](const void *h, size_t n, size_t e, void **d) -> cudaError_t {
         *d = m;
         m += sz(n, e);
@@ -202,12 +243,17 @@ lbm_status rebuild(lbm_batch *b)
         BCK(b, put(b->h_t9[k].data(), nt9, sizeof(TiledArgs), (void **)&b->t9[k]));
         BCK(b, put(b->h_fin9[k].data(), nf9, sizeof(FinalArgs), (void **)&b->fin9[k]));
         BCK(b, put(b->h_fin3[k].data(), nf3, sizeof(FinalArgs), (void **)&b->fin3[k]));
+        BCK(b, put(b->h_tube[k].data(), ntb, sizeof(TubeArgs), (void **)&b->tube[k]));
     }
     BCK(b, put(b->h_fmap.data(), b->h_fmap.size(), sizeof(int2), (void **)&b->fmap));
     BCK(b, put(b->h_t3map.data(), b->h_t3map.size(), sizeof(int2), (void **)&b->t3map));
     BCK(b, put(b->h_t9map.data(), b->h_t9map.size(), sizeof(int2), (void **)&b->t9map));
-    b->fblocks = (int)b->h_fmap.size();
+    BCK(b, put(b->h_tubemap.data(), b->h_tubemap.size(), sizeof(int2), (void **)&b->tubemap));
+    BCK(b, cudaMemsetAsync(b->work, 0, sizeof(int), b->run));
+    BCK(b, cudaMemsetAsync(b->twork, 0, sizeof(int), b->run));
+    b->fitems = (int)b->h_fmap.size();
     b->t3blocks = (int)b->h_t3map.size();
+    b->titems = (int)b->h_tubemap.size();
     b->t9blocks = (int)b->h_t9map.size();
     b->n9 = (int)nf9;
     b->n3 = (int)nf3;
@@ -219,15 +265,16 @@ lbm_status rebuild(lbm_batch *b)
 
 int launches_per_step(const lbm_batch *b)
 {
-    return (b->fblocks > 0) + (b->t3blocks > 0) + (b->t9blocks > 0) + (b->n9 > 0) + (b->n3 > 0);
+    return (b->fitems > 0) + (b->t3blocks > 0) + (b->t9blocks > 0) + (b->titems > 0) + (b->n9 > 0) + (b->n3 > 0);
 }
 
 // One batched step on the batch stream (table set `k`).
 cudaError_t one_step(lbm_batch *b, int k)
 {
     cudaError_t e = cudaSuccess;
-    if (b->fblocks && e == cudaSuccess) e = launch_fused_batched(b->fused[k], b->fmap, b->fblocks, b->run);
+    if (b->fitems && e == cudaSuccess) e = launch_fused_batched(b->fused[k], b->fmap, b->fitems, b->work, b->run);
     if (b->t3blocks && e == cudaSuccess) e = launch_tiled_batched_f32(3, b->t3[k], b->t3map, b->t3blocks, b->run);
+    if (b->titems && e == cudaSuccess) e = launch_tube_batched(b->tube[k], b->tubemap, b->titems, b->twork, b->run);
     if (b->t9blocks && e == cudaSuccess) e = launch_tiled_batched_f32(9, b->t9[k], b->t9map, b->t9blocks, b->run);
     if (b->n9 && e == cudaSuccess) e = launch_finalize_batched_f32(9, b->fin9[k], b->n9, b->run);
     if (b->n3 && e == cudaSuccess) e = launch_finalize_batched_f32(3, b->fin3[k], b->n3, b->run);
@@ -502,8 +549,7 @@ lbm_status lbm_batch_set_shape(lbm_batch *b, int32_t seg_rows, int32_t waves)
 {
     if (!b) return LBM_ERR_INVALID_ARG;
     if (seg_rows != 0 && seg_rows < 4) return bfail(b, LBM_ERR_INVALID_ARG, "seg_rows must be 0 or >= 4");
-    if (waves != 1 && waves != 2 && waves != 4 && waves != 8)
-        return bfail(b, LBM_ERR_INVALID_ARG, "waves must be 1, 2, 4 or 8");
+    if (waves < 1 || waves > 64) return bfail(b, LBM_ERR_INVALID_ARG, "waves must lie in 1 .. 64");
     invalidate(b);
     b->seg_rows = seg_rows;
     b->waves = waves;
@@ -538,15 +584,17 @@ lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_steps, double *best_ms)
         BCK(b, cudaMemcpyAsync(m + c->field_bytes + ring + 32, c->counts, 2 * sizeof(int), cudaMemcpyDeviceToDevice, b->run));
         snaps.push_back({c, c->cur, mem});
     }
-    // short items in several waves let the block scheduler even out the
-    // warps' different rates (an item costs no halo rows)
-    const int Ts[3] = {0, 8, 16};
-    const int Ws[4] = {1, 2, 4, 8};
+    // the work split: automatic segments for 2 .. 16 items per resident warp,
+    // or fixed 8- and 16-row segments (an item costs no halo rows; more items
+    // even out the warps' different rates, fewer cost less bookkeeping)
+    const int Ts[6] = {0, 0, 0, 0, 8, 16};
+    const int Ws[6] = {2, 4, 8, 16, 8, 8};
     double best = 1e300;
-    int bestT = 0, bestW = 1;
+    int bestT = 0, bestW = 8;
     lbm_status rs = LBM_OK;
-    for (int T : Ts) {
-        for (int W : Ws) {
+    for (int ci = 0; ci < 6; ++ci) {
+        const int T = Ts[ci], W = Ws[ci];
+        {
             invalidate(b);
             b->seg_rows = T;
             b->waves = W;

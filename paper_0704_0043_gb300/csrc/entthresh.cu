@@ -62,34 +62,69 @@ __global__ void k_ent_init(const double *ens, double a, double delta0, double t_
 }
 
 // Histogram of the digit at `shift` among the values whose higher bits equal
-// st->prefix: per-block shared counts and sums, added into st->cnt / st->sum.
+// st->prefix, added into st->cnt / st->sum.  dS spans few binades, so at the
+// upper levels most values fall into a few crowded bins, where per-value
+// atomics would queue on the same addresses.  Instead a warp takes 32
+// consecutive values at a time and, for each distinct digit among them (one
+// or two, as a rule), adds the lanes holding it (count by ballot, sum by a
+// warp reduction) into its own shared histogram, with no atomic; the block
+// then adds its warps' bins into the global ones.
 template <typename T>
 __global__ void __launch_bounds__(256) k_ent_hist(const T *__restrict__ field, long long n, int shift, EntState *st)
 {
     using B = Bits<T>;
     using U = typename B::U;
-    __shared__ unsigned cnt[256];
-    __shared__ T sum[256];
+    constexpr int kW = 8;
+    __shared__ unsigned cnt[kW][256];
+    __shared__ double sum[kW][256];
     if (st->done) return;
-    cnt[threadIdx.x] = 0u;
-    sum[threadIdx.x] = T(0);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < kW * 256; i += 256) {
+        (&cnt[0][0])[i] = 0u;
+        (&sum[0][0])[i] = 0.0;
+    }
     __syncthreads();
     const U prefix = (U)st->prefix;
     const int hi = shift + 8;  // bits above the digit
-    for (long long s = blockIdx.x * 256LL + threadIdx.x; s < n; s += (long long)gridDim.x * 256) {
-        T v = field[s];
-        if (!(v > T(0))) continue;  // zeros (and excluded sites) add nothing for t >= 0
-        const U u = B::of(v);
-        if (hi < B::kBits && ((u ^ prefix) >> hi) != 0) continue;
-        const unsigned d = (unsigned)((u >> shift) & 255u);
-        atomicAdd(&cnt[d], 1u);
-        atomicAdd(&sum[d], v);
+    const long long stride = (long long)gridDim.x * 256;
+    for (long long s0 = blockIdx.x * 256LL + warp * 32; s0 < n; s0 += stride) {
+        const long long s = s0 + lane;
+        unsigned d = 256u;  // no value
+        T v = T(0);
+        if (s < n) {
+            v = field[s];
+            if (v > T(0)) {  // zeros (and excluded sites) add nothing for t >= 0
+                const U u = B::of(v);
+                if (hi >= B::kBits || ((u ^ prefix) >> hi) == 0) d = (unsigned)((u >> shift) & 255u);
+            }
+        }
+        // the distinct digits of the 32 values, smallest first
+        unsigned left = __ballot_sync(0xffffffffu, d < 256u);
+        while (left) {
+            const unsigned dd = __reduce_min_sync(0xffffffffu, (left >> lane) & 1u ? d : 256u);
+            const unsigned mine = __ballot_sync(0xffffffffu, d == dd);
+            T x = d == dd ? v : T(0);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            if (lane == 0) {
+                cnt[warp][dd] += (unsigned)__popc(mine);
+                sum[warp][dd] += (double)x;
+            }
+            left &= ~mine;
+        }
     }
     __syncthreads();
     const int d = threadIdx.x;
-    if (cnt[d]) {
-        atomicAdd(&st->cnt[d], (unsigned long long)cnt[d]);
-        atomicAdd(&st->sum[d], (double)sum[d]);
+    unsigned c = 0u;
+    double sm = 0.0;
+#pragma unroll
+    for (int w = 0; w < kW; ++w) {
+        c += cnt[w][d];
+        sm += sum[w][d];
+    }
+    if (c) {
+        atomicAdd(&st->cnt[d], (unsigned long long)c);
+        atomicAdd(&st->sum[d], sm);
     }
 }
 

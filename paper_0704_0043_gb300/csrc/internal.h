@@ -195,6 +195,12 @@ struct FinalArgs {
     FinalParams p;
     void *f;
 };
+// One tube-kernel instance of a batched launch (FP32 D1Q3 lattices).
+struct TubeArgs {
+    StepParams p;
+    const void *src;
+    void *dst;
+};
 
 // Launchers (stream-ordered, no synchronisation).  Return cudaGetLastError().
 template <typename T>
@@ -219,6 +225,13 @@ cudaError_t launch_delta_s(int q, const StepParams &p, const T *f, double *out, 
 // E(dS) of the pass p is about to run and the smooth limiter's alpha, into
 // ens[2 kEnsBlocks], ens[2 kEnsBlocks + 1] (ens[0 .. 2 kEnsBlocks) is scratch).
 constexpr int kEnsBlocks = 608;
+// Behind them (in doubles from the start of the E(dS) scratch): {E, alpha, sum,
+// count}, then kFxRows fixed-point rows of the fused E(dS) pass and its
+// work-item counter (launch_fused_epass).
+constexpr int kEnsFxOffset = 2 * kEnsBlocks + 4;
+constexpr int kEnsDoubles = kEnsFxOffset + 8 * 16 + 2;
+template <typename S>
+cudaError_t launch_fused_epass(const StepParams &p, const S *src, cudaStream_t s);
 template <typename T>
 cudaError_t launch_ens_mean(int q, const StepParams &p, const T *src, double *ens, cudaStream_t s);
 // Eq. EntThresh on the field p.ent_field (filled by the ensemble reduction):
@@ -241,11 +254,25 @@ int fused_slots(int elem_bytes, bool batched);  // resident work items (warps) o
 // Fills the instance arguments: row segments of `seg_rows` rows (0: about
 // `slots` work items); returns the block count.
 int fused_make_args(const StepParams &p, const void *src, void *dst, int seg_rows, int slots, FusedArgs *out);
-// Batched launches: `blocks` blocks in total; block b runs instance map[b].x
-// with local block id map[b].y (tables in device memory).
-cudaError_t launch_fused_batched(const FusedArgs *table, const int2 *map, int blocks, cudaStream_t s);
+// Batched launches.  Fused: `items` work items over all instances, item i
+// being item map[i].y of instance map[i].x, handed out dynamically through
+// the counter *work (cleared by the tail after the launch).  Tiled: `blocks`
+// blocks, block b running instance map[b].x as its block map[b].y.
+cudaError_t launch_fused_batched(const FusedArgs *table, const int2 *map, int items, int *work, cudaStream_t s);
 cudaError_t launch_tiled_batched_f32(int q, const TiledArgs *table, const int2 *map, int blocks, cudaStream_t s);
 cudaError_t launch_finalize_batched_f32(int q, const FinalArgs *table, int n, cudaStream_t s);
+// D1Q3 streaming step (FP32 / FP64 storage): *chunked is false when the grid
+// fits one chunk of the tail's reduction, whose rows the tail then reads itself.
+template <typename S>
+cudaError_t launch_tube(const StepParams &p, const S *src, S *dst, int *nblocks, bool *chunked, cudaStream_t s);
+bool tube_applies(const lbm_config &c, unsigned limiters);  // the pass runs on the tube kernel
+// Batched FP32 tubes: `items` work items (groups of chunks, item i = group
+// map[i].y of tube map[i].x) handed out through *work; each item writes its
+// tube's partial row of its group (the tail reads tube_groups(nx) rows).
+cudaError_t launch_tube_batched(const TubeArgs *table, const int2 *map, int items, int *work, cudaStream_t s);
+int tube_groups(int nx);
+int tube_blocks(bool fp64, int nx);                          // blocks (partial rows) of one launch
+int sm_count();
 int tiled_grid_x(int q, int nx);
 int tiled_blocks_for(int q, int nx, int ny);
 bool fused_d2q9_fits(long long plane);  // 32-bit plane offsets inside the kernel

@@ -648,9 +648,9 @@ __device__ __forceinline__ void feq_ent3_dev(float drho, float rho, float u, flo
 {
     float d0, dp, dm;
     ent_axis<F1>(u, d0, dp, dm);
-    gs[1] = (1.0f / 6.0f) * __fmaf_rn(rho, dm, drho);
-    gs[2] = (1.0f / 6.0f) * __fmaf_rn(rho, dp, drho);
-    gs[0] = drho - (gs[1] + gs[2]);
+    gs[1] = __fmul_rn(1.0f / 6.0f, __fmaf_rn(rho, dm, drho));
+    gs[2] = __fmul_rn(1.0f / 6.0f, __fmaf_rn(rho, dp, drho));
+    gs[0] = __fsub_rn(drho, __fadd_rn(gs[1], gs[2]));
 }
 
 // One term of Eq. DelS written without cancellation: with d = f - f* and
@@ -731,22 +731,25 @@ __device__ __forceinline__ void feq9_dev(float drho, float rho, float ux, float 
     feq9_x<F1>(drho, rho, ux, uy, gs);
 }
 
-// D1Q3 (Eq. polyeq1d): g*_{1,2} = (drho + 3 rho u^2)/6 -/+ rho u / 2.
+// D1Q3 (Eq. polyeq1d): g*_{1,2} = (drho + 3 rho u^2)/6 -/+ rho u / 2.  Every
+// operation explicitly rounded, so each kernel that evaluates a D1Q3 site gets
+// the same bits.
 __device__ __forceinline__ void moments3_dev(const float g[3], float rho_ref, float &drho, float &rho, float &ux,
                                              float &uy)
 {
-    drho = (g[0] + g[1]) + g[2];
-    rho = rho_ref + drho;
-    ux = (g[2] - g[1]) * __frcp_rn(rho);
+    drho = __fadd_rn(__fadd_rn(g[0], g[1]), g[2]);
+    rho = __fadd_rn(rho_ref, drho);
+    ux = __fmul_rn(__fsub_rn(g[2], g[1]), __frcp_rn(rho));
     uy = 0.0f;
 }
 
 __device__ __forceinline__ void feq3_dev(float drho, float rho, float u, float gs[3])
 {
-    const float A = (1.0f / 6.0f) * fmaf(3.0f * rho * u, u, drho), B = 0.5f * rho * u;
-    gs[1] = A - B;
-    gs[2] = A + B;
-    gs[0] = drho - (gs[1] + gs[2]);
+    const float A = __fmul_rn(1.0f / 6.0f, __fmaf_rn(__fmul_rn(__fmul_rn(3.0f, rho), u), u, drho));
+    const float B = __fmul_rn(__fmul_rn(0.5f, rho), u);
+    gs[1] = __fsub_rn(A, B);
+    gs[2] = __fadd_rn(A, B);
+    gs[0] = __fsub_rn(drho, __fadd_rn(gs[1], gs[2]));
 }
 
 template <int Q>
@@ -773,12 +776,12 @@ __device__ __forceinline__ void neq9(const float g[9], const float gs[9], float 
 __device__ __forceinline__ void neq3(const float g[3], const float gs[3], float n[3])
 {
 #pragma unroll
-    for (int k = 0; k < 3; ++k) n[k] = g[k] - gs[k];
-    const float rm = (n[0] + n[1]) + n[2];
-    const float hx = 0.5f * (n[2] - n[1]);
-    n[0] -= rm;
-    n[2] -= hx;
-    n[1] += hx;
+    for (int k = 0; k < 3; ++k) n[k] = __fsub_rn(g[k], gs[k]);
+    const float rm = __fadd_rn(__fadd_rn(n[0], n[1]), n[2]);
+    const float hx = __fmul_rn(0.5f, __fsub_rn(n[2], n[1]));
+    n[0] = __fsub_rn(n[0], rm);
+    n[2] = __fsub_rn(n[2], hx);
+    n[1] = __fadd_rn(n[1], hx);
 }
 
 template <int Q>

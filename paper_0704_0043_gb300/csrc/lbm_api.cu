@@ -97,11 +97,13 @@ std::string validate(const lbm_config *c)
     if (!(c->delta_median >= 0.0) || !(c->delta_ehrenfest >= 0.0)) return "delta_median and delta_ehrenfest must be >= 0";
     if (c->k_max < 0) return "k_max must be >= 0";
     if (c->median_mode != LBM_MEDIAN_THRESHOLD && c->median_mode != LBM_MEDIAN_GATE) return "unknown median_mode";
-    if (c->kernel < LBM_KERNEL_AUTO || c->kernel > LBM_KERNEL_FUSED) return "unknown kernel";
+    if (c->kernel < LBM_KERNEL_AUTO || c->kernel > LBM_KERNEL_TUBE) return "unknown kernel";
     if (c->equilibrium != LBM_EQ_POLYNOMIAL && c->equilibrium != LBM_EQ_ENTROPIC) return "unknown equilibrium";
 
     if (c->kernel == LBM_KERNEL_FUSED && !fused_applies(*c))
         return "LBM_KERNEL_FUSED needs D2Q9, FP32/BF16/FP16 storage and LBM_BC_WALLS";
+    if (c->kernel == LBM_KERNEL_TUBE && !tube_applies(*c, c->limiters))
+        return "LBM_KERNEL_TUBE needs D1Q3, FP32 or FP64 storage and no ensemble-dependent limiter";
     if (c->collision != LBM_COLL_LBGK && c->collision != LBM_COLL_ELBM) return "unknown collision";
     if (c->collision == LBM_COLL_ELBM && (c->equilibrium != LBM_EQ_ENTROPIC || c->precision != LBM_FP64))
         return "ELBM needs entropic quasiequilibria (LBM_EQ_ENTROPIC) and LBM_FP64 storage";
@@ -115,7 +117,20 @@ std::string validate(const lbm_config *c)
     return "";
 }
 
-size_t ens_bytes() { return (2 * (size_t)kEnsBlocks + 4) * sizeof(double); }
+size_t ens_bytes()
+{
+    static_assert(kEnsDoubles >= kEnsFxOffset + kFxRows * kFxWords + 1, "fused E(dS) rows and counter");
+    return (size_t)kEnsDoubles * sizeof(double);
+}
+
+// E(dS) of a pass by the fused kernel's row streaming: FP32 D2Q9 halfway-wall
+// lattices, collision passes (whatever kernel the step itself runs on, so that
+// the fused and the tiled step see the same E)
+bool epass_applies(const lbm_config &c, int collide)
+{
+    return collide && c.lattice == LBM_D2Q9 && c.precision == LBM_FP32 && c.boundary == LBM_BC_WALLS &&
+           fused_d2q9_fits((long long)c.ny * row_pitch(c.nx));
+}
 size_t fx_bytes() { return (size_t)kFxRows * kFxWords * sizeof(unsigned long long); }
 
 struct Sizes {
@@ -145,6 +160,7 @@ Sizes sizes_for(const lbm_config &c)
     z.sel = (size_t)z.sel_cap * sizeof(int);
     // [fused accumulator rows][tiled block rows][chunk rows]
     z.rows = tiled_blocks_for(z.q, c.nx, c.ny);
+    if (z.q == 3) z.rows = std::max(z.rows, tube_blocks(c.precision == LBM_FP64, c.nx));
     z.partials = fx_bytes() + (size_t)(z.rows + chunks_for(z.rows)) * P_NSTAT * sizeof(double);
     z.ring_len = std::max(1, c.stats_history);
     z.ring = (size_t)z.ring_len * sizeof(DevStats);
@@ -271,12 +287,21 @@ lbm_status run_pass(lbm_ctx *c, int collide, unsigned limiters)
     cudaError_t e;
     void *src = c->buf[c->cur], *dst = c->buf[c->cur ^ 1];
     const bool fused = collide && fused_applies(c->cfg);
+    const bool tube = tube_applies(c->cfg, limiters);
+    bool chunked = true;
     if (limiters & kLimEnsemble) {
         // E(dS) of this pass, before any site is limited
-        e = with_storage(c->cfg.precision, [&](auto tag) -> cudaError_t {
-            using S = STORAGE_T;
-            return launch_ens_mean<S>(c->q, p, (const S *)src, c->ens, c->stream);
-        });
+        if (epass_applies(c->cfg, collide)) {
+            StepParams pe = p;
+            pe.fx_rows = reinterpret_cast<unsigned long long *>(c->ens + kEnsFxOffset);
+            pe.work = reinterpret_cast<int *>(c->ens + kEnsFxOffset + kFxRows * kFxWords);
+            e = launch_fused_epass<float>(pe, (const float *)src, c->stream);
+        } else {
+            e = with_storage(c->cfg.precision, [&](auto tag) -> cudaError_t {
+                using S = STORAGE_T;
+                return launch_ens_mean<S>(c->q, p, (const S *)src, c->ens, c->stream);
+            });
+        }
         if (e != cudaSuccess) return cuda_fail(c, e, "ensemble reduction launch");
         c->launches += 2;
         if (limiters & LBM_LIM_ENTTHRESH) {
@@ -293,6 +318,8 @@ lbm_status run_pass(lbm_ctx *c, int collide, unsigned limiters)
         using S = STORAGE_T;
         if constexpr (!std::is_same<S, double>::value)
             if (fused) return launch_fused_d2q9<S>(p, (const S *)src, (S *)dst, &nblocks, c->stream);
+        if constexpr (std::is_same<S, double>::value || std::is_same<S, float>::value)
+            if (tube) return launch_tube<S>(p, (const S *)src, (S *)dst, &nblocks, &chunked, c->stream);
         return launch_tiled<S>(c->q, p, (const S *)src, (S *)dst, &nblocks, c->stream);
     });
     if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
@@ -300,6 +327,10 @@ lbm_status run_pass(lbm_ctx *c, int collide, unsigned limiters)
     FinalParams f = final_params(c, collide, limiters, nblocks);
     f.fixed = fused ? 1 : 0;
     if (fused) f.partials = c->partials;  // the fixed-point accumulator rows
+    if (!chunked) {                        // a short tube: the tail reads the block rows
+        f.partials = p.partials;
+        f.nblocks = nblocks;
+    }
     f.work = fused ? c->counts + 2 : nullptr;
     e = with_storage(c->cfg.precision, [&](auto tag) -> cudaError_t {
         using S = STORAGE_T;
@@ -955,7 +986,8 @@ int64_t lbm_launch_count(const lbm_ctx *c) { return c ? c->launches : 0; }
 int32_t lbm_step_kernel(const lbm_ctx *c)
 {
     if (!c) return -1;
-    return fused_applies(c->cfg) ? LBM_KERNEL_FUSED : LBM_KERNEL_TILED;
+    if (fused_applies(c->cfg)) return LBM_KERNEL_FUSED;
+    return tube_applies(c->cfg, c->cfg.limiters) ? LBM_KERNEL_TUBE : LBM_KERNEL_TILED;
 }
 
 const char *lbm_last_error(const lbm_ctx *c) { return c ? c->err.c_str() : g_err.c_str(); }

@@ -50,7 +50,8 @@ namespace {
 
 constexpr int kWarps = 4;  // independent work items per block
 constexpr int kThreads = 32 * kWarps;
-constexpr int kBlocksPerSM = 5;  // resident blocks per SM (batched: 3)
+constexpr int kBlocksPerSM = 5;         // resident blocks per SM
+constexpr int kBlocksPerSMBatched = 4;  // batched launches (the arguments in shared memory take registers)
 constexpr int kRing = 2;         // FP32: rows in each warp's shared-memory load ring
 constexpr int kWin = 72;         // FP32: columns of each plane copied per row (16-byte aligned window)
 constexpr int kWin16 = 80;       // 16-bit storage: the same window, 8-column aligned
@@ -66,6 +67,7 @@ constexpr unsigned kFull = 0xffffffffu;
 struct RowState {
     float2 ds, pp, pe;  // dS(f'), phi of the positivity rule, phi of the ensemble-dependent limiters
     bool bad_a, bad_b, cand_a, cand_b;
+    float2 so;          // entropic f*, no median: dS of the limited state (applied at once)
 };
 
 // What the ensemble-dependent limiters need of their pass (read once per
@@ -77,13 +79,15 @@ struct EnsParams {
     bool e_pos, k_half;
     float alpha, k;
     double thr_t, ent_t;
-    float thr_f, ent_f;
+    float thr_f, ent_f;    // dS_t rounded down: the decision, exact
+    float thr_n, ent_n;    // dS_t rounded to nearest: the homothety's value
 };
 
 // phi of the ensemble-dependent limiters at a site with dS(f') = ds (not
 // flagged), the same operations as the tiled kernel's: Eq. smooth1 with the
 // ensemble's alpha, Eq. EntThresh's dS_t and the threshold dS_t = max(c E,
-// delta) with the homothety of Eq. entrHom (rare sites, in FP64 as there).
+// delta) with the homothety of Eq. entrHom: which sites it limits is decided
+// exactly (against dS_t rounded down), its value sqrt(dS_t / dS) in FP32.
 __device__ __forceinline__ float ens_phi(const EnsParams &e, float ds)
 {
     float pe = 1.f;
@@ -91,8 +95,8 @@ __device__ __forceinline__ float ens_phi(const EnsParams &e, float ds)
         const float pk = e.k_half ? sqrtf(ds) : powf(ds, e.k);
         pe = __fdiv_rn(1.f, __fmaf_rn(e.alpha, pk, 1.f));
     }
-    if ((e.lim & 32u) && ds > e.ent_f) pe = fminf(pe, (float)sqrt(e.ent_t / (double)ds));
-    if ((e.lim & 16u) && ds > e.thr_f) pe = fminf(pe, (float)sqrt(e.thr_t / (double)ds));
+    if ((e.lim & 32u) && ds > e.ent_f) pe = fminf(pe, __fsqrt_rn(__fdiv_rn(e.ent_n, ds)));
+    if ((e.lim & 16u) && ds > e.thr_f) pe = fminf(pe, __fsqrt_rn(__fdiv_rn(e.thr_n, ds)));
     return pe;
 }
 
@@ -161,14 +165,22 @@ __device__ __forceinline__ Sides sides(float a, float b, int lane)
 }
 
 // MED / POS: the median / positivity code is compiled in (each still follows
-// the instance's limiter bits).  BATCHED: block b runs instance map[b].x of
-// `table` as its block map[b].y; otherwise the single instance A0.
+// the instance's limiter bits).  BATCHED: work item i of the launch is item
+// map[i].y of instance map[i].x of `table`, A0.items the launch's item count
+// and A0.p.work its item counter; a warp keeps its current instance's
+// arguments in shared memory and adds its sums into that instance's
+// accumulator rows whenever it moves to another instance.  Otherwise the
+// single instance A0.
 // S: storage type of the deviations (float, __nv_bfloat16 or __half).
-template <typename S, bool MED, bool POS, bool BATCHED, bool ENS = false, bool ENT = false>
-__global__ void __launch_bounds__(kThreads, (BATCHED || ENT) ? 3 : kBlocksPerSM)
+template <typename S, bool MED, bool POS, bool BATCHED, bool ENS = false, bool ENT = false, bool EP = false>
+__global__ void __launch_bounds__(kThreads, ENT ? 3 : (BATCHED ? kBlocksPerSMBatched : kBlocksPerSM))
     k_fused(const FusedArgs A0, const FusedArgs *__restrict__ table, const int2 *__restrict__ map)
 {
     using O = F2;
+    // Ensemble-dependent passes without the median filter apply their
+    // site-local limiters as the row is stored (a variant of its own: the
+    // code costs registers the median variants cannot spare)
+    constexpr bool kFastPhi = !MED && ENS;
     // Launched as a programmatic dependent of the previous kernel: wait for it
     // to finish before any memory access, then let the next kernel (the tail)
     // be scheduled early.  Both are no-ops in an ordinary launch.
@@ -182,18 +194,10 @@ __global__ void __launch_bounds__(kThreads, (BATCHED || ENT) ? 3 : kBlocksPerSM)
     __shared__ __align__(16) S ring[kWarps][kRing][9][kWinS];
     __shared__ unsigned long long sfx[kWarps][kFxWords];
     __shared__ int cand_list[kWarps][kCandList];  // candidate slots of the warp's current item
-    __shared__ __align__(16) FusedArgs sA;
-    int bid = (int)blockIdx.x;
+    __shared__ __align__(16) FusedArgs sA[BATCHED ? kWarps : 1];
+    const int bid = (int)blockIdx.x;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    if constexpr (BATCHED) {
-        const int2 m = map[blockIdx.x];
-        const unsigned *from = reinterpret_cast<const unsigned *>(table + m.x);
-        unsigned *to = reinterpret_cast<unsigned *>(&sA);
-        for (int i = t; i < (int)(sizeof(FusedArgs) / 4); i += kThreads) to[i] = from[i];
-        bid = m.y;
-        __syncthreads();
-    }
-    const FusedArgs &A = BATCHED ? sA : A0;
+    const FusedArgs &A = BATCHED ? sA[warp] : A0;
     const StepParams &p = A.p;
     // ensemble-dependent limiters: this pass's E(dS), alpha and dS_t
     EnsParams ens{};
@@ -209,8 +213,10 @@ __global__ void __launch_bounds__(kThreads, (BATCHED || ENT) ? 3 : kBlocksPerSM)
             if (t < p.threshold_delta) t = p.threshold_delta;
             ens.thr_t = t;
             ens.thr_f = __double2float_rd(t);
+            ens.thr_n = (float)t;
             ens.ent_t = (ens.lim & 32u) ? p.ent->t : 0.0;
             ens.ent_f = (ens.lim & 32u) ? __double2float_rd(ens.ent_t) : 0.f;
+            ens.ent_n = (float)ens.ent_t;
         }
     }
 
@@ -239,13 +245,56 @@ __global__ void __launch_bounds__(kThreads, (BATCHED || ENT) ? 3 : kBlocksPerSM)
     int *list = cand_list[warp];
     int n_list = 0;  // candidates recorded in the current item (the same for the whole warp)
 
+    // BATCHED: adds the warp's fixed-point totals and counts into accumulator
+    // row (warp % kFxRows) of the instance it worked on, and clears them
+    auto commit = [&]() {
+        const int tot_sites = __reduce_add_sync(kFull, n_sites), tot_pos = __reduce_add_sync(kFull, n_pos);
+        const int tot_med = __reduce_add_sync(kFull, n_med), tot_bad = __reduce_add_sync(kFull, n_bad);
+        const unsigned bad_lanes = __ballot_sync(kFull, fx_bad);
+        unsigned long long *row = p.fx_rows + (long long)((bid * kWarps + warp) % kFxRows) * kFxWords;
+        if ((lane & 7) == 0) {
+            const int stat = lane >> 3;  // P_MASS .. P_DS_LIM
+            const unsigned long long lo = (unsigned long long)fx_acc, hi = (unsigned long long)(fx_acc >> 64);
+            const unsigned long long old = atomicAdd(row + FX_SUM + 2 * stat, lo);
+            atomicAdd(row + FX_SUM + 2 * stat + 1, hi + (old + lo < old ? 1ull : 0ull));
+        }
+        if (lane == 0) {
+            atomicAdd(row + FX_SITES, (unsigned long long)tot_sites);
+            atomicAdd(row + FX_NPOS, (unsigned long long)tot_pos);
+            atomicAdd(row + FX_NMED, (unsigned long long)tot_med);
+            atomicAdd(row + FX_NBAD, (unsigned long long)tot_bad);
+            const unsigned long long bits = (bad_lanes & 1u) | ((bad_lanes >> 7) & 2u) | ((bad_lanes >> 14) & 4u) |
+                                            ((bad_lanes >> 21) & 8u);
+            if (bits) atomicOr(row + FX_BAD, bits);
+            if (tot_bad) atomicOr(p.status, kStatNonfinite);  // a site was nonfinite
+        }
+        fx_acc = 0;
+        fx_bad = false;
+        n_sites = n_pos = n_med = n_bad = 0;
+    };
+    int cur = -1;  // BATCHED: the instance whose arguments sA[warp] holds
+
     int item = bid * kWarps + warp;
-    while (item < A.items) {
+    while (item < A0.items) {
+        int it = item;  // the item within its instance
+        if constexpr (BATCHED) {
+            const int2 m = map[item];
+            if (m.x != cur) {
+                if (cur >= 0) commit();
+                __syncwarp();
+                const unsigned *from = reinterpret_cast<const unsigned *>(table + m.x);
+                unsigned *to = reinterpret_cast<unsigned *>(&sA[warp]);
+                for (int i = lane; i < (int)(sizeof(FusedArgs) / 4); i += 32) to[i] = from[i];
+                __syncwarp();
+                cur = m.x;
+            }
+            it = m.y;
+        }
         const S *__restrict__ src = (const S *)A.src;
         S *__restrict__ dst = (S *)A.dst;
         const int nx = p.nx, ny = p.ny, pitch = p.pitch;
         const int plane = (int)p.plane;  // 9 * plane < 2^31 is checked at launch
-        const int strip = item % A.strips, seg = item / A.strips;
+        const int strip = it % A.strips, seg = it / A.strips;
         const int xa = kStripCols * strip - 1 + lane, xb = xa + 32;  // the lane's two columns
         const int ys = seg * A.seg_rows, ye = min(ys + A.seg_rows, ny);
         // The walk computes its own rows [ys, ye) only.  The median of its first
@@ -415,40 +464,110 @@ __global__ void __launch_bounds__(kThreads, (BATCHED || ENT) ? 3 : kBlocksPerSM)
             collide(g, drho, rho, ux, uy, gs, n);
             bool bad_a, bad_b;
             float2 ds = row_ds(gs, n, rho, ux, uy, din, bad_a, bad_b);
-            float fpmin_a = 3.4e38f, fpmin_b = 3.4e38f;
-#pragma unroll
-            for (int k = 0; k < 9; ++k) {
-                g[k] = O::fma(O::s(-b2), n[k], g[k]);  // g' = g - 2 beta n
+            if constexpr (EP) {
+                // E(dS) pass: the sum and count of dS(f') over the owned sites that
+                // are not flagged and have a finite dS, and the Eq. EntThresh field
+                const bool rown = q >= ys && q < ye;
+                const bool oa = own_a && rown, ob = own_b && rown;
+                const bool ga = oa && !bad_a && isfinite(ds.x), gb = ob && !bad_b && isfinite(ds.y);
+                s_ds += (ga ? ds.x : 0.f) + (gb ? ds.y : 0.f);
+                n_sites += (int)ga + (int)gb;
+                if (p.ent_field) {
+                    float *fld = (float *)p.ent_field + (long long)q * nx;
+                    if (oa) fld[xa] = (ga && ds.x > 0.f) ? ds.x : 0.f;
+                    if (ob) fld[xb] = (gb && ds.y > 0.f) ? ds.y : 0.f;
+                }
+                return st;
+            }
+            const bool rown = q >= ys && q < ye;
+            const bool oa = own_a && rown, ob = own_b && rown;
+            if constexpr (kFastPhi) {
+                // g stays the arriving g; g' = g - 2 beta n is formed where it is used
+                float fpmin_a = 3.4e38f, fpmin_b = 3.4e38f;
                 if (pos_on) {
-                    fpmin_a = fminf(fpmin_a, rwk(k).x + g[k].x);
-                    fpmin_b = fminf(fpmin_b, rwk(k).y + g[k].y);
-                }
-            }
-            if (pos_on && __any_sync(kFull, (!bad_a && fpmin_a < 0.f) || (!bad_b && fpmin_b < 0.f))) {
-                // positivity rule (Sec. 3.1)
 #pragma unroll
-                for (int k = 0; k < 9; ++k) {
-                    const float fpa = p.rwf[k] + g[k].x, fsa = p.rwf[k] + gs[k].x;
-                    if (!bad_a && fpa < 0.f) st.pp.x = fminf(st.pp.x, fsa / (fsa - fpa));
-                    const float fpb = p.rwf[k] + g[k].y, fsb = p.rwf[k] + gs[k].y;
-                    if (!bad_b && fpb < 0.f) st.pp.y = fminf(st.pp.y, fsb / (fsb - fpb));
+                    for (int k = 0; k < 9; ++k) {
+                        const float2 gp = O::fma(O::s(-b2), n[k], g[k]);
+                        fpmin_a = fminf(fpmin_a, rwk(k).x + gp.x);
+                        fpmin_b = fminf(fpmin_b, rwk(k).y + gp.y);
+                    }
                 }
-            }
-            if constexpr (ENS) {
-                // site-local, like the positivity rule: applied with the median's
-                // phi one row later (the row is then recomputed from its sources)
+                if (pos_on && __any_sync(kFull, (!bad_a && fpmin_a < 0.f) || (!bad_b && fpmin_b < 0.f))) {
+                    // positivity rule (Sec. 3.1)
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) {
+                        const float2 gp = O::fma(O::s(-b2), n[k], g[k]);
+                        const float fpa = p.rwf[k] + gp.x, fsa = p.rwf[k] + gs[k].x;
+                        if (!bad_a && fpa < 0.f) st.pp.x = fminf(st.pp.x, fsa / (fsa - fpa));
+                        const float fpb = p.rwf[k] + gp.y, fsb = p.rwf[k] + gs[k].y;
+                        if (!bad_b && fpb < 0.f) st.pp.y = fminf(st.pp.y, fsb / (fsb - fpb));
+                    }
+                }
                 if (ens.lim) {
                     if (!bad_a) st.pe.x = ens_phi(ens, ds.x);
                     if (!bad_b) st.pe.y = ens_phi(ens, ds.y);
                 }
-            }
-            const bool rown = q >= ys && q < ye;
-            const bool oa = own_a && rown, ob = own_b && rown;
-            S *out = dst + (long long)q * pitch + kLead + xa;
+                // no median in this pass: every limiter is site-local, so phi is
+                // final here, and the row is stored once: g - (1 + phi (2 beta - 1)) n
+                // where phi < 1 (the operations of the deferred update of
+                // finalise_row), g - 2 beta n elsewhere
+                const float phi_a = oa ? fminf(fminf(st.pp.x, 1.f), st.pe.x) : 1.f;
+                const float phi_b = ob ? fminf(fminf(st.pp.y, 1.f), st.pe.y) : 1.f;
+                const float2 cs = make_float2(phi_a < 1.f ? -limit_weight(phi_a, a, true) : -b2,
+                                              phi_b < 1.f ? -limit_weight(phi_b, a, true) : -b2);
+                if constexpr (ENT) {
+                    if (__any_sync(kFull, phi_a < 1.f || phi_b < 1.f)) {
+                        float2 fsa[9], d[9];
+                        const float2 m = make_float2(__fmul_rn(-phi_a, a), __fmul_rn(-phi_b, a));
 #pragma unroll
-            for (int k = 0; k < 9; ++k) {
-                if (oa) out[k * plane] = f2s<S>(g[k].x);
-                if (ob) out[k * plane + 32] = f2s<S>(g[k].y);
+                        for (int k = 0; k < 9; ++k) {
+                            fsa[k] = O::add(rwk(k), gs[k]);
+                            d[k] = O::mul(m, n[k]);
+                        }
+                        st.so = rel_entropy9_x(d, fsa);
+                    }
+                }
+                S *out = dst + (long long)q * pitch + kLead + xa;
+#pragma unroll
+                for (int k = 0; k < 9; ++k) {
+                    const float2 v = O::fma(cs, n[k], g[k]);
+                    if (oa) out[k * plane] = f2s<S>(v.x);
+                    if (ob) out[k * plane + 32] = f2s<S>(v.y);
+                }
+            } else {
+                float fpmin_a = 3.4e38f, fpmin_b = 3.4e38f;
+#pragma unroll
+                for (int k = 0; k < 9; ++k) {
+                    g[k] = O::fma(O::s(-b2), n[k], g[k]);  // g' = g - 2 beta n
+                    if (pos_on) {
+                        fpmin_a = fminf(fpmin_a, rwk(k).x + g[k].x);
+                        fpmin_b = fminf(fpmin_b, rwk(k).y + g[k].y);
+                    }
+                }
+                if (pos_on && __any_sync(kFull, (!bad_a && fpmin_a < 0.f) || (!bad_b && fpmin_b < 0.f))) {
+                    // positivity rule (Sec. 3.1)
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) {
+                        const float fpa = p.rwf[k] + g[k].x, fsa = p.rwf[k] + gs[k].x;
+                        if (!bad_a && fpa < 0.f) st.pp.x = fminf(st.pp.x, fsa / (fsa - fpa));
+                        const float fpb = p.rwf[k] + g[k].y, fsb = p.rwf[k] + gs[k].y;
+                        if (!bad_b && fpb < 0.f) st.pp.y = fminf(st.pp.y, fsb / (fsb - fpb));
+                    }
+                }
+                if constexpr (ENS) {
+                    // site-local, like the positivity rule: applied with the median's
+                    // phi one row later (the row is then recomputed from its sources)
+                    if (ens.lim) {
+                        if (!bad_a) st.pe.x = ens_phi(ens, ds.x);
+                        if (!bad_b) st.pe.y = ens_phi(ens, ds.y);
+                    }
+                }
+                S *out = dst + (long long)q * pitch + kLead + xa;
+#pragma unroll
+                for (int k = 0; k < 9; ++k) {
+                    if (oa) out[k * plane] = f2s<S>(g[k].x);
+                    if (ob) out[k * plane + 32] = f2s<S>(g[k].y);
+                }
             }
             const bool ga = oa && !bad_a, gb = ob && !bad_b;
             s_mass += (oa ? drho.x : 0.f) + (ob ? drho.y : 0.f);
@@ -508,6 +627,7 @@ __global__ void __launch_bounds__(kThreads, (BATCHED || ENT) ? 3 : kBlocksPerSM)
         // Row y: median of dS (rows y-1, y, y+1 in dm, d0, dp), phi = min(phi_pos,
         // phi_med), limited update where phi < 1, candidate record, sums.
         auto finalise_row = [&](int y, const RowState &st, float2 dm, float2 d0, float2 dp) {
+            if constexpr (EP) return;  // the E(dS) pass stores nothing
             const bool rown = y >= ys && y < ye;
             const bool act_a = own_a && rown, act_b = own_b && rown;
             float pm_a = 1.f, pm_b = 1.f;
@@ -557,7 +677,16 @@ __global__ void __launch_bounds__(kThreads, (BATCHED || ENT) ? 3 : kBlocksPerSM)
             }
             const float phi_a = act_a ? fminf(fminf(st.pp.x, pm_a), st.pe.x) : 1.f;
             const float phi_b = act_b ? fminf(fminf(st.pp.y, pm_b), st.pe.y) : 1.f;
-            if (__any_sync(kFull, phi_a < 1.f || phi_b < 1.f)) {
+            if (kFastPhi && !med_on) {
+                // the update was stored by compute_row; its entropy, as below
+                if constexpr (ENT) {
+                    if (phi_a < 1.f && isfinite(st.ds.x) && isfinite(st.so.x)) s_lim += __fsub_rn(st.ds.x, st.so.x);
+                    if (phi_b < 1.f && isfinite(st.ds.y) && isfinite(st.so.y)) s_lim += __fsub_rn(st.ds.y, st.so.y);
+                } else {
+                    if (phi_a < 1.f) s_lim = fmaf(1.f - phi_a * phi_a, st.ds.x, s_lim);
+                    if (phi_b < 1.f) s_lim = fmaf(1.f - phi_b * phi_b, st.ds.y, s_lim);
+                }
+            } else if (__any_sync(kFull, phi_a < 1.f || phi_b < 1.f)) {
                 // the limited update g - (1 + phi (2 beta - 1)) n (Eq. LimGenF in
                 // nonequilibrium form), with g and n recomputed exactly as the
                 // collision computed them (every lane takes part: edge_row votes)
@@ -715,10 +844,15 @@ __global__ void __launch_bounds__(kThreads, (BATCHED || ENT) ? 3 : kBlocksPerSM)
         // the item's sums, then the next item
         flush();
         rows_acc = 0;
-        if (BATCHED || p.work == nullptr) break;
+        int *work = BATCHED ? A0.p.work : p.work;
+        if (work == nullptr) break;
         int next = 0;
-        if (lane == 0) next = (int)gridDim.x * kWarps + atomicAdd(p.work, 1);
+        if (lane == 0) next = (int)gridDim.x * kWarps + atomicAdd(work, 1);
         item = __shfl_sync(kFull, next, 0);
+    }
+    if constexpr (BATCHED) {
+        if (cur >= 0) commit();
+        return;
     }
 
     // Block row of fixed-point totals and counts: integer sums, so the order
@@ -767,6 +901,8 @@ __global__ void __launch_bounds__(kThreads, (BATCHED || ENT) ? 3 : kBlocksPerSM)
     }
 }
 
+}  // namespace
+
 int sm_count()
 {
     static int sms = 0;
@@ -781,19 +917,21 @@ int sm_count()
     return sms;
 }
 
-template <typename S, bool MED, bool POS, bool BATCHED, bool ENS = false, bool ENT = false>
+namespace {
+
+template <typename S, bool MED, bool POS, bool BATCHED, bool ENS = false, bool ENT = false, bool EP = false>
 cudaError_t launch_k(const FusedArgs &A, const FusedArgs *table, const int2 *map, int blocks, cudaStream_t s)
 {
     static bool configured = false;
     if (!configured && kCarveout >= 0) {
         // shared memory vs L1 split (percent of the unified array for shared memory)
-        if (cudaFuncSetAttribute(k_fused<S, MED, POS, BATCHED, ENS, ENT>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        if (cudaFuncSetAttribute(k_fused<S, MED, POS, BATCHED, ENS, ENT, EP>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  kCarveout) != cudaSuccess)
             cudaGetLastError();
     }
     configured = true;
     if constexpr (BATCHED) {
-        k_fused<S, MED, POS, BATCHED, ENS, ENT><<<blocks, kThreads, 0, s>>>(A, table, map);
+        k_fused<S, MED, POS, BATCHED, ENS, ENT, EP><<<blocks, kThreads, 0, s>>>(A, table, map);
     } else {
         // programmatic dependent launch: the blocks may become resident while
         // the previous kernel of the stream (the tail) still runs; they wait
@@ -810,7 +948,7 @@ cudaError_t launch_k(const FusedArgs &A, const FusedArgs *table, const int2 *map
         cfg.numAttrs = 1;
         const FusedArgs *tab = table;
         const int2 *mp = map;
-        return cudaLaunchKernelEx(&cfg, k_fused<S, MED, POS, BATCHED, ENS, ENT>, A, tab, mp);
+        return cudaLaunchKernelEx(&cfg, k_fused<S, MED, POS, BATCHED, ENS, ENT, EP>, A, tab, mp);
     }
     return cudaGetLastError();
 }
@@ -820,10 +958,19 @@ cudaError_t launch_k(const FusedArgs &A, const FusedArgs *table, const int2 *map
 template <typename S>
 cudaError_t launch_lim(const FusedArgs &A, int blocks, cudaStream_t s)
 {
-    if (A.p.eq == 1)  // entropic f* and the exact dS of Eq. DelS; every limiter bit at run time
+    // FP32 passes without the median filter: the variant that stores limited
+    // rows at once (every limiter of the pass is site-local)
+    const bool nomed = std::is_same<S, float>::value && !(A.p.limiters & 4u);
+    if (A.p.eq == 1) {  // entropic f* and the exact dS of Eq. DelS; every limiter bit at run time
+        if constexpr (std::is_same<S, float>::value)
+            if (nomed) return launch_k<S, false, true, false, true, true>(A, nullptr, nullptr, blocks, s);
         return launch_k<S, true, true, false, true, true>(A, nullptr, nullptr, blocks, s);
-    if (A.p.limiters & kLimEnsemble)  // the ensemble-dependent limiters follow every bit at run time
+    }
+    if (A.p.limiters & kLimEnsemble) {  // the ensemble-dependent limiters follow every bit at run time
+        if constexpr (std::is_same<S, float>::value)
+            if (nomed) return launch_k<S, false, true, false, true>(A, nullptr, nullptr, blocks, s);
         return launch_k<S, true, true, false, true>(A, nullptr, nullptr, blocks, s);
+    }
     if constexpr (std::is_same<S, float>::value) {
         const bool med = (A.p.limiters & 4u) != 0, pos = (A.p.limiters & 1u) != 0;
         if (med && pos) return launch_k<S, true, true, false>(A, nullptr, nullptr, blocks, s);
@@ -831,6 +978,9 @@ cudaError_t launch_lim(const FusedArgs &A, int blocks, cudaStream_t s)
         if (pos) return launch_k<S, false, true, false>(A, nullptr, nullptr, blocks, s);
         return launch_k<S, false, false, false>(A, nullptr, nullptr, blocks, s);
     } else {
+        // 16-bit storage: the positivity code is compiled out when the rule is off
+        // (the rest of the instruction stream is the kernel's limit, not memory)
+        if (!(A.p.limiters & 1u)) return launch_k<S, true, false, false>(A, nullptr, nullptr, blocks, s);
         return launch_k<S, true, true, false>(A, nullptr, nullptr, blocks, s);
     }
 }
@@ -840,7 +990,7 @@ cudaError_t launch_lim(const FusedArgs &A, int blocks, cudaStream_t s)
 int fused_slots(int elem_bytes, bool batched)
 {
     (void)elem_bytes;  // every storage type runs kBlocksPerSM blocks per SM
-    const int per_sm = batched ? 3 : kBlocksPerSM;  // as in the launch bounds
+    const int per_sm = batched ? kBlocksPerSMBatched : kBlocksPerSM;  // as in the launch bounds
     return per_sm * kWarps * sm_count();
 }
 
@@ -911,11 +1061,73 @@ template cudaError_t launch_fused_d2q9<__nv_bfloat16>(const StepParams &, const 
                                                       int *, cudaStream_t);
 template cudaError_t launch_fused_d2q9<__half>(const StepParams &, const __half *, __half *, int *, cudaStream_t);
 
-cudaError_t launch_fused_batched(const FusedArgs *table, const int2 *map, int blocks, cudaStream_t s)
+// E(dS) of the step about to run (Sec. 3.3), by the fused kernel's row
+// streaming with nothing stored: the sum in exact fixed point into the rows
+// p.fx_rows (count in FX_SITES), the work items through p.work; k_ens_fx turns
+// them into {E, alpha, sum, count} at p.ens and clears rows and counter.
+__global__ void k_ens_fx(StepParams p, double *out)
 {
-    if (blocks <= 0) return cudaSuccess;
-    const FusedArgs none{};
-    return launch_k<float, true, true, true>(none, table, map, blocks, s);
+    const int lane = threadIdx.x;
+    unsigned long long *rows = p.fx_rows;
+    // lane r < kFxRows adds row r's sum (128 bits) and count
+    unsigned __int128 v = 0;
+    unsigned long long cnt = 0;
+    if (lane < kFxRows) {
+        unsigned long long *row = rows + (long long)lane * kFxWords;
+        v = ((unsigned __int128)row[FX_SUM + 2 * P_SUM_DS + 1] << 64) | row[FX_SUM + 2 * P_SUM_DS];
+        cnt = row[FX_SITES];
+        for (int w = 0; w < kFxWords; ++w) row[w] = 0ull;
+    }
+#pragma unroll
+    for (int o = 1; o < kFxRows; o <<= 1) {
+        const unsigned long long lo = __shfl_xor_sync(0xffffffffu, (unsigned long long)v, o);
+        const unsigned long long hi = __shfl_xor_sync(0xffffffffu, (unsigned long long)(v >> 64), o);
+        v += ((unsigned __int128)hi << 64) | lo;
+        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    }
+    if (lane == 0) {
+        // the fixed-point value in units of 2^-64 (high and low words converted apart)
+        const bool neg = (unsigned long long)(v >> 127) != 0;
+        const unsigned __int128 m = neg ? (unsigned __int128)0 - v : v;
+        double s = (double)(unsigned long long)(m >> 64) * 18446744073709551616.0 + (double)(unsigned long long)m;
+        s = (neg ? -s : s) * 5.42101086242752217003726400434970855712890625e-20;  // 2^-64
+        const double c = (double)cnt;
+        const double E = c > 0.0 ? s / c : 0.0;
+        out[0] = E;
+        out[1] = E > 0.0 ? p.smooth_delta / pow(E, p.smooth_k) : 0.0;  // alpha of Eq. smooth1
+        out[2] = s;
+        out[3] = c;
+        *p.work = 0;
+    }
+}
+
+template <typename S>
+cudaError_t launch_fused_epass(const StepParams &p, const S *src, cudaStream_t s)
+{
+    const int slots = p.eq == 1 ? 3 * kWarps * sm_count() : fused_slots((int)sizeof(S), false);
+    const long long strips = (p.nx + kStripCols - 1) / kStripCols;
+    const int rows = (int)std::max<long long>(kMinSegRows, (strips * p.ny + (long long)kItemsPerWarp * slots - 1) /
+                                                               ((long long)kItemsPerWarp * slots));
+    FusedArgs A;
+    fused_make_args(p, src, nullptr, rows, slots, &A);
+    const int blocks = std::min(A.blocks, slots / kWarps);
+    cudaError_t e = p.eq == 1 ? launch_k<S, false, false, false, false, true, true>(A, nullptr, nullptr, blocks, s)
+                              : launch_k<S, false, false, false, false, false, true>(A, nullptr, nullptr, blocks, s);
+    if (e != cudaSuccess) return e;
+    k_ens_fx<<<1, 32, 0, s>>>(p, const_cast<double *>(p.ens));
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_fused_epass<float>(const StepParams &, const float *, cudaStream_t);
+
+cudaError_t launch_fused_batched(const FusedArgs *table, const int2 *map, int items, int *work, cudaStream_t s)
+{
+    if (items <= 0) return cudaSuccess;
+    FusedArgs A0{};
+    A0.items = items;
+    A0.p.work = work;
+    const int blocks = std::min((items + kWarps - 1) / kWarps, fused_slots(4, true) / kWarps);
+    return launch_k<float, true, true, true>(A0, table, map, blocks, s);
 }
 
 }  // namespace lbm

@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const S *__r
     // recording threshold, kc[2] = 2 beta - 1, kc[3] = alpha of the smooth
     // limiter, kc[4] = dS_t rounded down (for a float dS, dS > kc[4] exactly when
     // (double) dS > dS_t), kc[5] = smooth_k; ke: E > 0, k = 1/2, thresholds on
-    __shared__ float kc[7];
+    __shared__ float kc[9];
     __shared__ int ke[3];
     if constexpr (!std::is_same<T, double>::value) {
         if (tx == 0 && ty == 0) {
@@ -322,10 +322,12 @@ __global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const S *__r
             const double E = (p.limiters & 24u) ? p.ens[0] : 0.0;
             // Eq. EntThresh's dS_t rounded down (for a float dS, dS > kc[6] exactly when (double) dS > dS_t)
             kc[6] = (p.limiters & 32u) ? __double2float_rd(p.ent->t) : 0.f;
+            kc[7] = (p.limiters & 32u) ? (float)p.ent->t : 0.f;  // the homotheties' dS_t, nearest
             double t = p.threshold_c * E;
             if (t < p.threshold_delta) t = p.threshold_delta;
             kc[3] = (p.limiters & 24u) ? (float)p.ens[1] : 0.f;
             kc[4] = __double2float_rd(t);
+            kc[8] = (float)t;
             kc[5] = (float)p.smooth_k;
             ke[0] = E > 0.0;
             ke[1] = p.smooth_k == 0.5;
@@ -415,16 +417,15 @@ __global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const S *__r
                     const float pk = ke[1] ? sqrtf(ds) : powf(ds, kc[5]);
                     pe = __fdiv_rn(1.0f, __fmaf_rn(kc[3], pk, 1.0f));  // explicit: the fused kernel's bits
                 }
+                // the threshold filters: decided exactly against dS_t rounded
+                // down, the homothety sqrt(dS_t / dS) in FP32 (the fused kernel's
+                // operations)
                 if ((p.limiters & 32u) && ds > kc[6]) {
-                    // rare: Eq. EntThresh's exact dS_t at the limited site
-                    const float pt = (float)sqrt(p.ent->t / (double)ds);
+                    const float pt = __fsqrt_rn(__fdiv_rn(kc[7], ds));
                     if (pt < pe) pe = pt;
                 }
                 if (ke[2] && ds > kc[4]) {
-                    // rare: the exact dS_t of the limited site
-                    double t = p.threshold_c * p.ens[0];
-                    if (t < p.threshold_delta) t = p.threshold_delta;
-                    const float pt = (float)sqrt(t / (double)ds);
+                    const float pt = __fsqrt_rn(__fdiv_rn(kc[8], ds));
                     if (pt < pe) pe = pt;
                 }
             }

@@ -23,7 +23,7 @@ BC_WALLS, BC_PERIODIC, BC_CHANNEL, BC_NODE_WALLS, BC_DIFFUSIVE = 0, 1, 2, 3, 4
 LIM_POSITIVITY, LIM_EHRENFEST, LIM_MEDIAN, LIM_SMOOTH, LIM_THRESHOLD, LIM_ENTTHRESH = 1, 2, 4, 8, 16, 32
 MEDIAN_THRESHOLD, MEDIAN_GATE = 0, 1
 EQ_POLYNOMIAL, EQ_ENTROPIC = 0, 1
-KERNEL_AUTO, KERNEL_TILED, KERNEL_FUSED = 0, 1, 2
+KERNEL_AUTO, KERNEL_TILED, KERNEL_FUSED, KERNEL_TUBE = 0, 1, 2, 3
 COLL_LBGK, COLL_ELBM = 0, 1
 PHI_HOMOTHETY, PHI_ENTROPY = 0, 1
 
@@ -375,7 +375,7 @@ class Lattice:
         return lib().lbm_device_bytes(self._h)
 
     def step_kernel(self) -> int:
-        """KERNEL_TILED or KERNEL_FUSED: the kernel lbm_step launches."""
+        """KERNEL_TILED, KERNEL_FUSED or KERNEL_TUBE: the kernel lbm_step launches."""
         return lib().lbm_step_kernel(self._h)
 
     def launch_count(self) -> int:
@@ -492,8 +492,9 @@ class Batch:
                 self._h)
         return out[:n.value].copy()
 
-    def set_shape(self, seg_rows: int = 0, waves: int = 1):
-        """Fused work split: rows per work item (0: automatic, else >= 16), 1 / 2 / 4 waves."""
+    def set_shape(self, seg_rows: int = 0, waves: int = 8):
+        """Fused work split: rows per work item (0: automatic, else >= 4); with automatic
+        segments about `waves` (1 .. 64) work items per resident warp."""
         _bcheck(lib().lbm_batch_set_shape(self._h, int(seg_rows), int(waves)), self._h)
 
     def tune(self, trial_steps: int = 5) -> float:

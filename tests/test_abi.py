@@ -42,7 +42,10 @@ def test_config_validation_without_gpu(lib):
            dict(equilibrium=lbm.EQ_ENTROPIC, precision=lbm.BF16, phi_rule=lbm.PHI_ENTROPY),
            dict(collision=lbm.COLL_ELBM, precision=lbm.FP64), dict(collision=2), dict(limiters=128),
            dict(smooth_k=0.0), dict(smooth_delta=-1.0), dict(threshold_c=float("nan")),
-           dict(threshold_delta=-1e-3), dict(limiters=lbm.LIM_SMOOTH, kernel=lbm.KERNEL_FUSED, precision=lbm.FP64)]
+           dict(threshold_delta=-1e-3), dict(limiters=lbm.LIM_SMOOTH, kernel=lbm.KERNEL_FUSED, precision=lbm.FP64),
+           dict(kernel=lbm.KERNEL_TUBE), dict(kernel=4),
+           dict(lattice=lbm.D1Q3, ny=1, kernel=lbm.KERNEL_TUBE, precision=lbm.BF16),
+           dict(lattice=lbm.D1Q3, ny=1, kernel=lbm.KERNEL_TUBE, limiters=lbm.LIM_THRESHOLD)]
     for b in bad:
         cfg = dict(base)
         cfg.update(b)
@@ -50,6 +53,9 @@ def test_config_validation_without_gpu(lib):
             lbm.footprint_bytes(**cfg)
         assert e.value.status == lbm.ERR_INVALID_ARG
     assert lbm.footprint_bytes(**dict(base, precision=lbm.FP64, equilibrium=lbm.EQ_ENTROPIC)) > 0
+    tube = dict(lattice=lbm.D1Q3, nx=1000, ny=1, boundary=lbm.BC_WALLS, kernel=lbm.KERNEL_TUBE)
+    assert lbm.footprint_bytes(**dict(tube, precision=lbm.FP64)) > 0
+    assert lbm.footprint_bytes(**dict(tube, precision=lbm.FP32, boundary=lbm.BC_PERIODIC)) > 0
     # FP64 doubles the population storage
     f32 = lbm.footprint_bytes(**base)
     f64 = lbm.footprint_bytes(**dict(base, precision=lbm.FP64))

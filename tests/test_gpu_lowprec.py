@@ -27,13 +27,16 @@ UNIT = {lbm.BF16: 2.0 ** -8, lbm.FP16: 2.0 ** -11}
 SUBNORMAL_HALF = {lbm.BF16: 0.0, lbm.FP16: 2.0 ** -25}
 W9 = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
 # Stated error of 1000 steps of the 100 x 100 Re = 5000 cavity (max over the
-# field of |d rho|, |d u|).  The run amplifies a perturbation of the state by
-# about 4e3 over its first 700 steps (the lid corners shed vortices), so the
-# 16-bit rounding (relative 2^-9 / 2^-12 per step) grows to the 1e-2 level at
-# the corners; measured 2.1e-2 (BF16) and 4.8e-2 (FP16).  Away from the lid
-# rows the error is an order of magnitude smaller (RMS bound below).
-LONG_RUN_BOUND = {lbm.BF16: 5e-2, lbm.FP16: 1e-1}
-LONG_RUN_RMS_BOUND = {lbm.BF16: 5e-3, lbm.FP16: 5e-3}
+# field of |d rho|, |d u|, and the field RMS).  The run amplifies a perturbation
+# of the state by about 4e3 over its first 700 steps (the lid corners shed
+# vortices), so the 16-bit rounding (relative 2^-9 / 2^-12 per step) grows to
+# the 1e-2 level at the corners.  Measured: max 2.52e-2 (BF16) and 3.33e-2
+# (FP16), RMS 9.9e-4 and 4.1e-4, relative mass drift -1.5e-6 and -3.8e-8 (the
+# code is deterministic: these are the values of this kernel); the bounds are
+# 1.5 times them.
+LONG_RUN_BOUND = {lbm.BF16: 3.8e-2, lbm.FP16: 5.0e-2}
+LONG_RUN_RMS_BOUND = {lbm.BF16: 1.5e-3, lbm.FP16: 6.2e-4}
+LONG_RUN_MASS_BOUND = {lbm.BF16: 2.2e-6, lbm.FP16: 5.7e-8}
 
 
 @pytest.mark.parametrize("precision", [lbm.BF16, lbm.FP16])
@@ -92,4 +95,4 @@ def test_16bit_cavity_100_error_after_1000_steps(precision):
     assert gs["n_bad"] == 0
     assert max(err) < LONG_RUN_BOUND[precision], err
     assert rms < LONG_RUN_RMS_BOUND[precision], rms
-    assert abs(gs["mass"] - st["mass"]) < 1e-3 * st["mass"]
+    assert abs(gs["mass"] - st["mass"]) < LONG_RUN_MASS_BOUND[precision] * st["mass"]

@@ -190,9 +190,15 @@ def test_fp32_one_step_against_oracle(nx, ny, kernel):
     assert st["n_ehr"] == r.stats["n_ehr"] and st["n_cand"] == r.stats["n_cand"]
     assert abs(st["n_med"] - r.stats["n_med"]) <= max(2, r.stats["n_med"] // 100)
     assert st["n_pos"] == r.stats["n_pos"]
-    assert abs(st["mass"] - r.stats["mass"]) <= 1e-6 * r.stats["mass"]
-    np.testing.assert_allclose(st["sum_dS"], r.stats["sum_dS"], rtol=1e-4)
-    np.testing.assert_allclose(st["dS_lim"], r.stats["dS_lim"], rtol=1e-3)
+    # FP32 statistics against the FP64 oracle (stated bound): every dS term is
+    # within 2^-22 (the hardware reciprocal) + 6 roundings of 2^-24 = 6e-7 of its
+    # FP64 value and the FP32 partial sums add a random-walk rounding well below
+    # that, so the dS sums hold 1e-6 relative (measured worst 2.7e-7, on the 5 x 4
+    # lattice where a few sites carry the sum; 1e-8 to 5e-8 on the larger ones).
+    # The mass sums rho - rho_ref exactly per site: measured worst 3.3e-9.
+    assert abs(st["mass"] - r.stats["mass"]) <= 1e-8 * r.stats["mass"]
+    for key in ("sum_dS", "dS_lbgk", "dS_lim"):
+        np.testing.assert_allclose(st[key], r.stats[key], rtol=1e-6, err_msg=key)
 
 
 @pytest.mark.parametrize("boundary", [lbm.BC_NODE_WALLS, lbm.BC_DIFFUSIVE])
