@@ -84,16 +84,6 @@ __device__ double block_sum0(double v, double *red, bool warp0_only)
     return v;
 }
 
-// Value of a 128-bit two's-complement fixed-point number in units of 2^-64
-// (the fused kernel's sums): the high and low 64-bit magnitudes are converted
-// separately, so the result is the same on every run.
-__device__ double fx_to_double(unsigned __int128 x)
-{
-    const bool neg = (unsigned long long)(x >> 127) != 0;
-    const unsigned __int128 m = neg ? (unsigned __int128)0 - x : x;
-    const double d = (double)(unsigned long long)(m >> 64) * 18446744073709551616.0 + (double)(unsigned long long)m;
-    return (neg ? -d : d) * 5.42101086242752217003726400434970855712890625e-20;  // 2^-64
-}
 
 // The digit of a radix-selection pass: hist[d] counts the keys with digit d
 // among those still in play, and the rem-th of them is wanted, counting from
@@ -208,7 +198,7 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, 
             // (chunk 4) and the nonfinite bits (chunk 6)
             const unsigned long long sites = __shfl_sync(kFull, u0, 4), bits = __shfl_sync(kFull, u0, 6);
             if (lane < 4) {  // FP statistic lane
-                double d = ((bits >> lane) & 1u) ? __longlong_as_double(0x7ff8000000000000LL) : fx_to_double(v);
+                double d = ((bits >> lane) & 1u) ? __longlong_as_double(0x7ff8000000000000LL) : fx_value(v);
                 if (lane == P_MASS) d = Ar<double>::add(d, Ar<double>::mul((double)sites, (double)p.rho_ref));
                 tot[lane] = d;
             } else if (lane == 4) {

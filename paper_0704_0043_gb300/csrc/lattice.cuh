@@ -891,4 +891,41 @@ __device__ __forceinline__ T med9(T a0, T a1, T a2, T b0, T b1, T b2, T c0, T c1
     return med3(lo, mid, hi);
 }
 
+// Adds the FP32 value v exactly to acc, a 128-bit two's-complement fixed-point
+// number in units of 2^-64 (bits of v below 2^-64 are dropped, truncating
+// toward zero).  A nonfinite v, or |v| >= 2^63, sets `bad` instead.
+__device__ __forceinline__ void fx_add(unsigned __int128 &acc, float v, bool &bad)
+{
+    const unsigned u = __float_as_uint(v);
+    const int e = (int)((u >> 23) & 0xffu);  // biased exponent: v = +-m 2^(e - 150)
+    if (e == 0xff) {
+        bad = true;
+        return;
+    }
+    if (e == 0) return;  // zero or subnormal (below 2^-126)
+    const unsigned long long m = (u & 0x7fffffu) | 0x800000u;
+    const int sh = e - 150 + 64;  // v = +-m 2^sh units
+    if (sh >= 104) {
+        bad = true;
+        return;
+    }
+    unsigned __int128 x = 0;
+    if (sh >= 0)
+        x = (unsigned __int128)m << sh;
+    else if (sh > -24)
+        x = (unsigned __int128)(m >> -sh);
+    acc += (u >> 31) ? (unsigned __int128)0 - x : x;
+}
+
+// Value of a 128-bit two's-complement fixed-point number in units of 2^-64:
+// the high and low 64-bit magnitudes are converted separately, so the result
+// is the same on every run.
+__device__ __forceinline__ double fx_value(unsigned __int128 x)
+{
+    const bool neg = (unsigned long long)(x >> 127) != 0;
+    const unsigned __int128 m = neg ? (unsigned __int128)0 - x : x;
+    const double d = (double)(unsigned long long)(m >> 64) * 18446744073709551616.0 + (double)(unsigned long long)m;
+    return (neg ? -d : d) * 5.42101086242752217003726400434970855712890625e-20;  // 2^-64
+}
+
 }  // namespace lbm

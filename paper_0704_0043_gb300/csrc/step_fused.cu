@@ -100,31 +100,6 @@ __device__ __forceinline__ float ens_phi(const EnsParams &e, float ds)
     return pe;
 }
 
-// Adds the FP32 value v exactly to acc, a 128-bit two's-complement fixed-point
-// number in units of 2^-64 (bits of v below 2^-64 are dropped, truncating
-// toward zero).  A nonfinite v, or |v| >= 2^63, sets `bad` instead.
-__device__ __forceinline__ void fx_add(unsigned __int128 &acc, float v, bool &bad)
-{
-    const unsigned u = __float_as_uint(v);
-    const int e = (int)((u >> 23) & 0xffu);  // biased exponent: v = +-m 2^(e - 150)
-    if (e == 0xff) {
-        bad = true;
-        return;
-    }
-    if (e == 0) return;  // zero or subnormal (below 2^-126)
-    const unsigned long long m = (u & 0x7fffffu) | 0x800000u;
-    const int sh = e - 150 + 64;  // v = +-m 2^sh units
-    if (sh >= 104) {
-        bad = true;
-        return;
-    }
-    unsigned __int128 x = 0;
-    if (sh >= 0)
-        x = (unsigned __int128)m << sh;
-    else if (sh > -24)
-        x = (unsigned __int128)(m >> -sh);
-    acc += (u >> 31) ? (unsigned __int128)0 - x : x;
-}
 
 // Sorted column (lo <= mid <= hi) of three values.
 __device__ __forceinline__ void sort3(float a, float b, float c, float &lo, float &mid, float &hi)
@@ -1086,11 +1061,7 @@ __global__ void k_ens_fx(StepParams p, double *out)
         cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
     }
     if (lane == 0) {
-        // the fixed-point value in units of 2^-64 (high and low words converted apart)
-        const bool neg = (unsigned long long)(v >> 127) != 0;
-        const unsigned __int128 m = neg ? (unsigned __int128)0 - v : v;
-        double s = (double)(unsigned long long)(m >> 64) * 18446744073709551616.0 + (double)(unsigned long long)m;
-        s = (neg ? -s : s) * 5.42101086242752217003726400434970855712890625e-20;  // 2^-64
+        const double s = fx_value(v);
         const double c = (double)cnt;
         const double E = c > 0.0 ? s / c : 0.0;
         out[0] = E;

@@ -141,12 +141,26 @@ constexpr int kTubeRing = 3;
 constexpr int kTubeWarps = 8;  // the most warps a block has
 constexpr int kTubeGroup = 8;  // chunks of a batched work item
 // The statistics a warp gathers: FP64 storage sums FP64 terms per lane; FP32
-// storage sums a chunk's FP32 terms per lane, adds the lanes in FP32 and the
-// chunk totals in FP64 (lane 0).
+// storage sums a chunk's FP32 terms per lane, adds the lanes in FP32 (a fixed
+// butterfly that leaves the four totals in lanes 0, 8, 16, 24) and the chunk
+// totals exactly, as 128-bit fixed point (integer instructions: FP64 adds per
+// chunk kept this GPU's FP64 units a third busy).
 struct TubeAcc {
     double t_mass, t_ds, t_in, t_lim;
     int c_pos, c_med, c_bad, c_own;
+    unsigned __int128 fx;  // FP32 storage: lane 0 mass, lane 8 dS, lane 16 dS_in, lane 24 dS_lim
+    bool fx_bad;
 };
+
+// FP32 storage: the four totals of acc (after the walk), in every lane.
+__device__ __forceinline__ void tube_totals(const TubeAcc &acc, double &mass, double &ds, double &din, double &lim)
+{
+    const double v = acc.fx_bad ? __longlong_as_double(0x7ff8000000000000LL) : fx_value(acc.fx);
+    mass = __shfl_sync(0xffffffffu, v, 0);
+    ds = __shfl_sync(0xffffffffu, v, 8);
+    din = __shfl_sync(0xffffffffu, v, 16);
+    lim = __shfl_sync(0xffffffffu, v, 24);
+}
 
 // a ring slot: the three planes of a chunk of 32 V sites, then f_2 left of it
 // and f_1 right of it
@@ -415,19 +429,17 @@ __device__ __forceinline__ void tube_walk(const StepParams &p, const S *__restri
             acc.t_in = A::add(acc.t_in, s_in);
             acc.t_lim = A::add(acc.t_lim, s_lim);
         } else {
+            // butterfly: each level halves the sums a lane carries
+            const bool hi16 = (lane & 16) != 0, hi8 = (lane & 8) != 0;
+            float x0 = hi16 ? s_in : s_mass, x1 = hi16 ? s_lim : s_ds;
+            const float y0 = hi16 ? s_mass : s_in, y1 = hi16 ? s_ds : s_lim;
+            x0 = __fadd_rn(x0, __shfl_xor_sync(0xffffffffu, y0, 16));
+            x1 = __fadd_rn(x1, __shfl_xor_sync(0xffffffffu, y1, 16));
+            float z = hi8 ? x1 : x0;
+            z = __fadd_rn(z, __shfl_xor_sync(0xffffffffu, hi8 ? x0 : x1, 8));
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                s_mass = __fadd_rn(s_mass, __shfl_down_sync(0xffffffffu, s_mass, o));
-                s_ds = __fadd_rn(s_ds, __shfl_down_sync(0xffffffffu, s_ds, o));
-                s_in = __fadd_rn(s_in, __shfl_down_sync(0xffffffffu, s_in, o));
-                s_lim = __fadd_rn(s_lim, __shfl_down_sync(0xffffffffu, s_lim, o));
-            }
-            if (lane == 0) {
-                acc.t_mass += (double)s_mass;
-                acc.t_ds += (double)s_ds;
-                acc.t_in += (double)s_in;
-                acc.t_lim += (double)s_lim;
-            }
+            for (int o = 4; o > 0; o >>= 1) z = __fadd_rn(z, __shfl_xor_sync(0xffffffffu, z, o));
+            if ((lane & 7) == 0) fx_add(acc.fx, z, acc.fx_bad);
         }
     }
     twait<0>();
@@ -455,6 +467,7 @@ __global__ void __launch_bounds__(256, V > 1 ? 2 : 1) k_tube(const StepParams p,
     tube_walk<S, V>(p, src, dst, blockIdx.x * nw + warp, (int)gridDim.x * nw, (p.nx + 32 * V - 1) / (32 * V),
                     ring[warp], klist[warp], &kcount[warp], acc);
     double t_mass = acc.t_mass, t_ds = acc.t_ds, t_in = acc.t_in, t_lim = acc.t_lim;
+    if constexpr (!F64) tube_totals(acc, t_mass, t_ds, t_in, t_lim);
     int c_pos = acc.c_pos, c_med = acc.c_med, c_bad = acc.c_bad, c_own = acc.c_own;
 
     // block partial row: warp sums, then the warps in order; counts as integers
@@ -547,15 +560,17 @@ __global__ void __launch_bounds__(256, 2) k_tube_batched(const TubeArgs *__restr
         TubeAcc acc{};
         tube_walk<S, V>(p, (const S *)sA[warp].src, (S *)sA[warp].dst, c0, 1, c1, ring[warp], klist[warp],
                         &kcount[warp], acc);
-        // FP32 storage: lane 0 holds the sums; the counts are per lane
+        // the item's totals; the counts are per lane
+        double t_mass, t_ds, t_in, t_lim;
+        tube_totals(acc, t_mass, t_ds, t_in, t_lim);
         const int c_pos = __reduce_add_sync(0xffffffffu, acc.c_pos), c_med = __reduce_add_sync(0xffffffffu, acc.c_med);
         const int c_bad = __reduce_add_sync(0xffffffffu, acc.c_bad), c_own = __reduce_add_sync(0xffffffffu, acc.c_own);
         if (lane == 0) {
             double *row = p.partials + (long long)m.y * P_NSTAT;
-            row[P_MASS] = (double)p.rho_ref * (double)c_own + acc.t_mass;
-            row[P_SUM_DS] = acc.t_ds;
-            row[P_SUM_IN] = acc.t_in;
-            row[P_DS_LIM] = acc.t_lim;
+            row[P_MASS] = (double)p.rho_ref * (double)c_own + t_mass;
+            row[P_SUM_DS] = t_ds;
+            row[P_SUM_IN] = t_in;
+            row[P_DS_LIM] = t_lim;
             row[P_NPOS] = (double)c_pos;
             row[P_NMED] = (double)c_med;
             row[P_NBAD] = (double)c_bad;
