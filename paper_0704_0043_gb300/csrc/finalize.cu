@@ -121,7 +121,7 @@ __device__ void pick_digit(const unsigned *hist, long long rem, bool desc, unsig
 
 // BATCHED: block b finishes instance b of `table`; otherwise the single (p0, f0).
 template <int Q, typename S, bool BATCHED>
-__global__ void __launch_bounds__(kFinThreads) k_finalize(const FinalParams p0, S *__restrict__ f0,
+__global__ void __launch_bounds__(kFinThreads, BATCHED ? 2 : 1) k_finalize(const FinalParams p0, S *__restrict__ f0,
                                                           const FinalArgs *__restrict__ table)
 {
     using T = compute_t<S>;
