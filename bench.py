@@ -722,7 +722,7 @@ def main():
     kname = {lbm.KERNEL_FUSED: "fused", lbm.KERNEL_TUBE: "tube"}.get(lat.step_kernel(), "tiled")
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_kind": peak_kind,
-            "traffic": traffic_from_profile(f"{kname}_{prec}", w.sites) if lat_kind == "d2q9" else None,
+            "traffic": traffic_from_profile(f"{kname}_{prec}", w.sites),
             "kernel": kname if timed else "whole step (graph replay)", "kernel_ms": kern_s * 1e3,
             "tail_kernel_ms": tail_ms / max(timed, 1), "timed_launches": timed, "timed_every": every,
             "bytes_per_site": bps}
