@@ -50,8 +50,10 @@ typedef enum {
     LBM_ERR_OOM = 2,         /* device allocation failed */
     LBM_ERR_CUDA = 3,        /* a CUDA runtime call failed (message names it) */
     LBM_ERR_NONFINITE = 4,   /* a site had rho <= 0, f*_k <= 0 or a nonfinite value */
-    LBM_ERR_TIMEOUT = 5,     /* reserved for a bounded device-side wait that gives up; no kernel of
-                                this library waits on another, so no call returns it today */
+    LBM_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up: the grid barrier of the tail that
+                                preselects dense Ehrenfests' candidates (lattices of 2^20 sites or
+                                more, cooperative launch) polls about a second; the pass's results
+                                are then not to be trusted (re-initialise the state) */
     LBM_ERR_STATE = 6        /* call out of order (e.g. step before init) */
 } lbm_status;
 
@@ -96,8 +98,9 @@ enum {
  *   LBM_LIM_THRESHOLD: dS_t = max(threshold_c E, threshold_delta); phi = sqrt(dS_t / dS)
  *     where dS > dS_t (Sec. 3.4, Eq. entrHom, with dS_0 = c E as in Sec. 4.3.2).
  * Every limiter's phi is combined as the minimum, before Ehrenfests' step.  The
- * ensemble limiters (these two and LBM_LIM_ENTTHRESH) run on the tiled kernel (not in
- * batches, not in lbm_step_noalloc). */
+ * ensemble limiters (these two and LBM_LIM_ENTTHRESH) run on the fused kernel where it
+ * applies (the E(dS) pass is then the fused kernel's own row streaming), else on the
+ * tiled kernel; not in batches, not in lbm_step_noalloc. */
 enum { LBM_LIM_POSITIVITY = 1, LBM_LIM_EHRENFEST = 2, LBM_LIM_MEDIAN = 4, LBM_LIM_SMOOTH = 8,
        LBM_LIM_THRESHOLD = 16, LBM_LIM_ENTTHRESH = 32 };
 /* LBM_LIM_ENTTHRESH: the threshold filter with dS_0 from Eq. EntThresh, solved on the
@@ -108,7 +111,7 @@ enum { LBM_LIM_POSITIVITY = 1, LBM_LIM_EHRENFEST = 2, LBM_LIM_MEDIAN = 4, LBM_LI
  *   of LBM_PHI_ENTROPY).  dS_0 is found exactly by a radix descent over the bit patterns
  *   of the dS field (dS_0 = +inf when the right side is 0: nothing is limited); its sums
  *   are added by atomics, so it is reproducible to rounding.  Needs the bit at create
- *   (the field is allocated then); tiled kernel; not in batches or lbm_step_noalloc. */
+ *   (the field is allocated then); not in batches or lbm_step_noalloc. */
 
 /* Median-filter acceptance rule (Sec. 3.5 with the tolerance of Sec. 4.3.2). */
 enum {

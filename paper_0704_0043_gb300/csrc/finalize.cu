@@ -9,10 +9,16 @@
 // 64-bit pattern of dS (positive doubles order like their bit patterns), then
 // four passes over the site index among the candidates tied at the threshold.
 //
-// The kernel is one block and sits between two step launches, so it is built
-// for latency: the candidates arrive with their FP64 keys (the step kernels
-// evaluate them where they find them), up to kCap of them are kept in shared
-// memory, and sums use warp shuffles or exact integer arithmetic.
+// The kernel sits between two step launches, so it is built for latency: the
+// candidates arrive with their FP64 keys (the step kernels evaluate them where
+// they find them), up to kCap of them are kept in shared memory, and sums use
+// warp shuffles or exact integer arithmetic.  One block runs the tail.  When a
+// pass records more candidates than that (a state far from equilibrium), the
+// tail runs as a cooperative grid of one block per SM that first preselects
+// them (dense_select): the FP32 dS recorded with each candidate is within 1/64
+// of its FP64 key, so a radix search over the FP32 values bounds the k-th
+// largest key, and only the candidates near that bound or near delta need
+// their FP64 keys; block 0 then selects among the short list.
 #include <type_traits>
 
 #include "internal.h"
@@ -26,6 +32,7 @@ constexpr int kFinThreads = 512;
 constexpr int kFinWarps = kFinThreads / 32;
 constexpr int kCap = 2048;  // candidates held (and selected sets sorted) in shared memory
 constexpr unsigned kFull = 0xffffffffu;
+constexpr unsigned kSelSpinLimit = 1u << 21;  // grid-barrier polls (about a second) before giving up
 
 __device__ __forceinline__ unsigned long long key_bits(double d) { return (unsigned long long)__double_as_longlong(d); }
 
@@ -119,8 +126,226 @@ __device__ void pick_digit(const unsigned *hist, long long rem, bool desc, unsig
     __syncthreads();
 }
 
+// The geometry of the FP64 key evaluation (D2Q9, FP32 / 16-bit storage).
+__device__ KeyGeom key_geom(const FinalParams &p)
+{
+    KeyGeom kg;
+    kg.nx = p.nx;
+    kg.ny = p.ny;
+    kg.pitch = p.pitch;
+    kg.boundary = p.boundary;
+    kg.plane = p.plane;
+    kg.a = p.a;
+    kg.rw0 = p.rw[0];
+    kg.rw1 = p.rw[1];
+    kg.rw5 = p.rw[5];
+    kg.lid4 = p.lid[4];
+    kg.lid7 = p.lid[7];
+    kg.lid8 = p.lid[8];
+    kg.eq = p.eq;
+    return kg;
+}
+
+// Grid barrier of the cooperative tail: each block adds one arrival to *bar;
+// with `wait` it polls until `target` blocks have arrived.  The poll is
+// bounded: past kSelSpinLimit polls the block sets kStatTimeout in *status and
+// goes on (the pass's results are then not trusted; the host reports
+// LBM_ERR_TIMEOUT).  Every thread of the block calls it; returns whether this
+// block gave up.
+__device__ bool grid_sync(unsigned *bar, unsigned target, bool wait, unsigned *status, int *s_flag)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int gave_up = 0;
+        __threadfence();
+        atomicAdd(bar, 1u);
+        if (wait) {
+            unsigned polls = 0;
+            while (*(volatile unsigned *)bar < target) {
+                if (++polls > kSelSpinLimit) {
+                    gave_up = 1;
+                    atomicOr(status, kStatTimeout);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        *s_flag = gave_up;
+    }
+    __syncthreads();
+    return *s_flag != 0;
+}
+
+// The bin holding the rem-th largest entry (rem >= 1) of a kSelBins-bin
+// histogram in device memory (bin b counts the keys with digit b, larger
+// digits larger keys), and the rank left within that bin.  *s_tot receives the
+// histogram's total; when it is below rem no bin holds the entry and *s_bin
+// is -1.  Thread t scans bins 8t .. 8t+7 from the top; integer sums, so the
+// same on every run.  Every thread of the block calls it.
+__device__ void pick_bin(const unsigned *h, long long rem, long long *s_wpart, int *s_bin, long long *s_rem,
+                         long long *s_tot)
+{
+    constexpr int kPer = kSelBins / kFinThreads;
+    static_assert(kPer * kFinThreads == kSelBins, "whole bins per thread");
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    unsigned c[kPer];
+    long long mine = 0;
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+        c[j] = __ldcg(h + (kSelBins - 1 - (t * kPer + j)));  // written by other blocks' atomics
+        mine += c[j];
+    }
+    long long incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_wpart[w] = incl;
+    if (t == 0) *s_bin = -1;
+    __syncthreads();
+    for (int j = 0; j < w; ++j) incl += s_wpart[j];
+    if (t == kFinThreads - 1) *s_tot = incl;
+    const long long excl = incl - mine;
+    if (excl < rem && rem <= incl) {  // one thread: its bins hold the entry
+        long long acc = excl;
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            if (acc < rem && rem <= acc + c[j]) {
+                *s_bin = kSelBins - 1 - (t * kPer + j);
+                *s_rem = rem - acc;
+            }
+            acc += c[j];
+        }
+    }
+    __syncthreads();
+}
+
+// Device-wide preselection of n > kCap recorded candidates (all blocks of the
+// cooperative tail call it).  R denotes the candidates whose FP32 dS exceeds
+// dhi = delta (1 + 1/64): their FP64 keys exceed delta.  When |R| >= k, the
+// k-th largest FP32 dS in R is at least T, the lower end of its bin after two
+// 12-bit radix levels (bits 30..19, then 18..7, of the FP32 pattern; positive
+// floats order like their patterns), so the k-th largest valid FP64 key is
+// at least T / (1 + 1/64), and a candidate whose key reaches it has FP32 dS of
+// at least T (1 - 1/64) / (1 + 1/64) > T (1 - 1/32) = Tlow.  The list takes
+// every valid candidate with FP32 dS >= Tlow (all valid ones when |R| < k):
+// it holds every candidate of the exact top k, ties at the k-th key included.
+// The valid candidates are counted exactly: a candidate with a key is valid
+// when the key exceeds delta; one without a key is keyed here when it is on
+// the list's side of Tlow or within 1/64 of delta (at or below dhi), and
+// otherwise valid when its FP32 dS exceeds dhi.  Block 0 then reads the list
+// (returns true when it fits in kSelList) and resets the shared state for
+// the next pass; the other blocks return false.  Not inlined: the one-block
+// tail runs from a cold instruction cache every step, and its code stays
+// compact without this rarely taken path.
+template <int Q, typename S>
+__device__ __noinline__ bool dense_select(const FinalParams &p, int n, unsigned *sh, long long *s_wpart, int *s_bin,
+                             long long *s_rem, long long *s_tot, int *s_flag, unsigned *s_acc, unsigned *s_cnt,
+                             unsigned *s_nv)
+{
+    SelState *ss = p.sel_state;
+    const int t = threadIdx.x, lane = t & 31;
+    const unsigned nb = gridDim.x;
+    const int dhi_bits = __float_as_int((float)(p.delta_e * (1.0 + 1.0 / 64.0)));
+    const long long stride = (long long)nb * kFinThreads;
+    const long long base0 = (long long)blockIdx.x * kFinThreads;
+    auto in_r = [&](int u) { return u > dhi_bits && u < 0x7f800000; };  // FP32 dS above dhi (finite)
+
+    // level 1: bits 30..19 of the candidates in R
+    for (int b = t; b < kSelBins; b += kFinThreads) sh[b] = 0;
+    __syncthreads();
+    for (long long i = base0 + t; i < n; i += stride) {
+        const int u = __float_as_int(p.cand[i].ds32);
+        if (in_r(u)) atomicAdd(&sh[u >> 19], 1u);
+    }
+    __syncthreads();
+    for (int b = t; b < kSelBins; b += kFinThreads)
+        if (sh[b]) atomicAdd(&ss->hist1[b], sh[b]);
+    grid_sync(&ss->bar, nb, true, p.status, s_flag);
+
+    // level 2: bits 18..7 within the level-1 bin of the k-th largest
+    pick_bin(ss->hist1, p.k_max, s_wpart, s_bin, s_rem, s_tot);
+    const bool all = *s_tot < p.k_max;  // fewer than k in R: every valid candidate is listed
+    const int b1 = *s_bin;
+    const long long rem1 = *s_rem;
+    for (int b = t; b < kSelBins; b += kFinThreads) sh[b] = 0;
+    __syncthreads();
+    if (!all) {
+        for (long long i = base0 + t; i < n; i += stride) {
+            const int u = __float_as_int(p.cand[i].ds32);
+            if (in_r(u) && (u >> 19) == b1) atomicAdd(&sh[(u >> 7) & (kSelBins - 1)], 1u);
+        }
+        __syncthreads();
+        for (int b = t; b < kSelBins; b += kFinThreads)
+            if (sh[b]) atomicAdd(&ss->hist2[b], sh[b]);
+    }
+    grid_sync(&ss->bar, 2 * nb, true, p.status, s_flag);
+
+    // the bound, the keys, the count and the list
+    int tlow_bits = 0;
+    if (!all) {
+        pick_bin(ss->hist2, rem1, s_wpart, s_bin, s_rem, s_tot);
+        const unsigned ulb = ((unsigned)b1 << 19) | ((unsigned)*s_bin << 7);
+        tlow_bits = __float_as_int(__uint_as_float(ulb) * 0.96875f);
+    }
+    if (t == 0) *s_acc = 0;
+    __syncthreads();
+    constexpr bool kKeyHere = !std::is_same<S, double>::value && Q == 9;  // candidates recorded without a key
+    const KeyGeom kg = key_geom(p);
+    unsigned nv = 0;
+    for (long long base = base0; base < n; base += stride) {  // whole warps per round (warp-aggregated appends)
+        const long long i = base + t;
+        bool valid = false, listed = false;
+        if (i < n) {
+            const Cand c = p.cand[i];
+            const int u = __float_as_int(c.ds32);
+            listed = u >= tlow_bits;
+            double key = c.key;
+            if constexpr (kKeyHere) {
+                if (isnan(key) && (listed || u <= dhi_bits)) {
+                    key = key_dS9_lane<S>(kg, (const S *)p.src, c.site, p.delta_e);
+                    p.cand[i].key = key;
+                }
+            }
+            valid = isnan(key) ? in_r(u) : key > p.delta_e;
+            listed = listed && valid;
+        }
+        const unsigned m = __ballot_sync(kFull, listed);
+        unsigned at = 0;
+        if (lane == 0 && m) at = atomicAdd(&ss->count, (unsigned)__popc(m));
+        at = __shfl_sync(kFull, at, 0) + __popc(m & ((1u << lane) - 1u));
+        if (listed && at < (unsigned)kSelList) ss->list[at] = (int)i;
+        nv += valid;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nv += __shfl_down_sync(kFull, nv, o);
+    if (lane == 0 && nv) atomicAdd(s_acc, nv);
+    __syncthreads();
+    if (t == 0 && *s_acc) atomicAdd(&ss->n_valid, *s_acc);
+    // block 0 waits for every block's list entries and count
+    grid_sync(&ss->bar, 3 * nb, blockIdx.x == 0, p.status, s_flag);
+    if (blockIdx.x != 0) return false;
+    if (t == 0) {
+        *s_cnt = __ldcg(&ss->count);
+        *s_nv = __ldcg(&ss->n_valid);
+        ss->count = 0;
+        ss->n_valid = 0;
+        ss->bar = 0;
+    }
+    for (int b = t; b < kSelBins; b += kFinThreads) {
+        ss->hist1[b] = 0;
+        ss->hist2[b] = 0;
+    }
+    __syncthreads();
+    return *s_cnt <= (unsigned)kSelList;
+}
+
 // BATCHED: block b finishes instance b of `table`; otherwise the single (p0, f0).
-template <int Q, typename S, bool BATCHED>
+// GRID: the cooperative grid of one block per SM (dense candidates are
+// preselected by all blocks; block 0 runs the tail); otherwise one block.
+template <int Q, typename S, bool BATCHED, bool GRID = false>
 __global__ void __launch_bounds__(kFinThreads, BATCHED ? 2 : 1) k_finalize(const FinalParams p0, S *__restrict__ f0,
                                                           const FinalArgs *__restrict__ table)
 {
@@ -129,7 +354,32 @@ __global__ void __launch_bounds__(kFinThreads, BATCHED ? 2 : 1) k_finalize(const
     // finish before any memory access, then let the next step kernel be
     // scheduled early.  Both are no-ops in an ordinary launch.
     asm volatile("griddepcontrol.wait;" ::: "memory");
+    // The next launch may be scheduled now.  In a grid launch it starts only
+    // when every block of this grid has passed this point, i.e. when all of
+    // them are resident, so its blocks cannot keep one of ours from running
+    // (the grid barriers below wait for resident blocks only).
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    __shared__ double s_key[kCap];
+    __shared__ int s_site[kCap];
+    __shared__ int s_idx[kCap];
+    __shared__ long long s_wpart[kFinWarps], s_rem2, s_tot;
+    __shared__ int s_bin, s_flag;
+    __shared__ unsigned s_acc, s_cnt, s_nv;
+    // dense candidates in a grid launch: every block preselects, then block 0
+    // runs the tail over the list (use_list) or, when the list overflowed,
+    // over all candidates; otherwise block 0 alone runs the tail
+    bool use_list = false;
+    if constexpr (GRID) {
+        const int nrec = p0.ehrenfest ? *p0.cand_count : 0;
+        const int n0 = nrec < p0.cand_cap ? nrec : p0.cand_cap;
+        const bool dense = n0 > kCap && p0.sel_state != nullptr && p0.k_max > 0;
+        if (!dense && blockIdx.x != 0) return;
+        if (dense) {
+            use_list = dense_select<Q, S>(p0, n0, reinterpret_cast<unsigned *>(s_key), s_wpart, &s_bin, &s_rem2,
+                                          &s_tot, &s_flag, &s_acc, &s_cnt, &s_nv);
+            if (blockIdx.x != 0) return;
+        }
+    }
     __shared__ __align__(16) FinalArgs sA;
     if constexpr (BATCHED) {
         const unsigned *from = reinterpret_cast<const unsigned *>(table + blockIdx.x);
@@ -141,25 +391,35 @@ __global__ void __launch_bounds__(kFinThreads, BATCHED ? 2 : 1) k_finalize(const
     S *__restrict__ f = BATCHED ? (S *)sA.f : f0;
     __shared__ double red[kFinWarps + 1];
     __shared__ double tot[P_NSTAT];
-    __shared__ double s_key[kCap];
-    __shared__ int s_site[kCap];
-    __shared__ int s_idx[kCap];
     __shared__ unsigned hist[256];
     __shared__ unsigned long long s_part[8], s_digit;
-    __shared__ unsigned long long s_prefix;
     __shared__ long long s_rem, s_step, s_rec;
-    __shared__ int s_n, s_nsel, s_valid;
+    __shared__ int s_nsel, s_valid;
     __shared__ unsigned s_status;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
 
+    // every thread reads the candidate count (one broadcast load) and loads its
+    // first candidate slot at once (any slot below the capacity is readable,
+    // so the load does not wait for the count), and both loads overlap the
+    // reduction of the step's sums; list entry i is candidate cidx(i) (the
+    // preselected list, or all candidates)
+    int n = 0;
+    if (use_list) {
+        n = (int)s_cnt;
+    } else if (p.ehrenfest) {
+        const int nrec = *p.cand_count;
+        n = nrec < p.cand_cap ? nrec : p.cand_cap;
+    }
+    const int *list = use_list ? p.sel_state->list : nullptr;
+    auto cidx = [&](int i) -> int { return use_list ? list[i] : i; };
+    Cand first{};
+    if (!BATCHED && p.ehrenfest && (use_list ? t < n : t < p.cand_cap)) first = p.cand[cidx(t)];
     if (t == 0) {
-        const int nrec = p.ehrenfest ? *p.cand_count : 0;
-        s_n = nrec < p.cand_cap ? nrec : p.cand_cap;
         s_step = p.counters[0];
         s_rec = p.counters[1];
         s_status = *p.status;
         s_nsel = 0;
-        s_valid = 0;
+        s_valid = use_list ? (int)s_nv : 0;
     }
     if (p.fixed) {
         // the fused kernel's kFxRows fixed-point accumulator rows (exact integer
@@ -229,50 +489,43 @@ __global__ void __launch_bounds__(kFinThreads, BATCHED ? 2 : 1) k_finalize(const
     __syncthreads();
     if (!p.fixed && t < P_NSTAT) tot[t] = red[2 * t] + red[2 * t + 1];
     __syncthreads();
-    const int n = s_n;
     const bool small = n <= kCap;  // candidates held in shared memory
     const long long k = p.k_max;
 
     // candidate keys: FP64 dS(f'), written with the candidates by the step
     // kernels (sites at or below the threshold carry -1); the fused kernel
     // leaves NaN where a warp had more candidates than it keys itself, and
-    // those are keyed here, one thread per candidate, with the same operations
+    // those are keyed here, one thread per candidate, with the same operations.
+    // The preselected list holds keyed, valid candidates and their count.
     constexpr bool kLowPrec = !std::is_same<S, double>::value;
-    for (int i = t; i < n; i += kFinThreads) {
-        Cand c = p.cand[i];
-        if constexpr (kLowPrec && Q == 9) {
-            if (isnan(c.key)) {
-                KeyGeom kg;
-                kg.nx = p.nx;
-                kg.ny = p.ny;
-                kg.pitch = p.pitch;
-                kg.boundary = p.boundary;
-                kg.plane = p.plane;
-                kg.a = p.a;
-                kg.rw0 = p.rw[0];
-                kg.rw1 = p.rw[1];
-                kg.rw5 = p.rw[5];
-                kg.lid4 = p.lid[4];
-                kg.lid7 = p.lid[7];
-                kg.lid8 = p.lid[8];
-                kg.eq = p.eq;
-                c.key = key_dS9_lane<S>(kg, (const S *)p.src, c.site, p.delta_e);
-            }
-        }
-        // below the threshold -> -1, so that from here on a key is valid
-        // exactly when its bit pattern is a positive integer (FP64 compares
-        // are slow on this GPU; positive doubles order like their patterns)
-        if (!(c.key > p.delta_e) && c.key != -1.0) c.key = -1.0;
-        if (!small || isnan(p.cand[i].key)) p.cand[i].key = c.key;
-        if (small) {
+    if (use_list) {
+        for (int i = t; i < n && small; i += kFinThreads) {
+            const Cand c = !BATCHED && i == t ? first : p.cand[list[i]];
             s_key[i] = c.key;
             s_site[i] = c.site;
         }
+    } else {
+        for (int i = t; i < n; i += kFinThreads) {
+            Cand c = !BATCHED && i == t ? first : p.cand[i];
+            if constexpr (kLowPrec && Q == 9) {
+                if (isnan(c.key)) c.key = key_dS9_lane<S>(key_geom(p), (const S *)p.src, c.site, p.delta_e);
+            }
+            // below the threshold -> -1, so that from here on a key is valid
+            // exactly when its bit pattern is a positive integer (FP64 compares
+            // are slow on this GPU; positive doubles order like their patterns)
+            if (!(c.key > p.delta_e) && c.key != -1.0) c.key = -1.0;
+            if (small) {
+                s_key[i] = c.key;
+                s_site[i] = c.site;
+            } else {
+                p.cand[i].key = c.key;
+            }
+        }
     }
     __syncthreads();
-    auto key_of = [&](int i) -> double { return small ? s_key[i] : p.cand[i].key; };
-    auto site_of = [&](int i) -> int { return small ? s_site[i] : p.cand[i].site; };
-    {
+    auto key_of = [&](int i) -> double { return small ? s_key[i] : p.cand[cidx(i)].key; };
+    auto site_of = [&](int i) -> int { return small ? s_site[i] : p.cand[cidx(i)].site; };
+    if (!use_list) {
         int nv = 0;
         for (int i = t; i < n; i += kFinThreads) nv += (long long)key_bits(key_of(i)) > 0;
 #pragma unroll
@@ -307,7 +560,8 @@ __global__ void __launch_bounds__(kFinThreads, BATCHED ? 2 : 1) k_finalize(const
             }
             if (chosen) {
                 const int j = atomicAdd(&s_nsel, 1);
-                if (j < p.sel_cap) p.sel[j] = t;
+                if (j < p.sel_cap) p.sel[j] = cidx(t);
+                if (j < kCap) s_idx[j] = t;
             }
         }
         if (!take_all && !by_rank) {
@@ -349,14 +603,16 @@ __global__ void __launch_bounds__(kFinThreads, BATCHED ? 2 : 1) k_finalize(const
             }
             site_thr = (int)sprefix;
         }
-        // compaction of the chosen candidates (indices into the candidate list)
+        // compaction of the chosen candidates: candidate indices in p.sel, list
+        // entries in s_idx (the first kCap)
         for (int i = t; i < n && !by_rank; i += kFinThreads) {
             const double key = key_of(i);
             const unsigned long long u = key_bits(key);
             const bool chosen = (long long)u > 0 && (take_all || u > kv || (u == kv && site_of(i) <= site_thr));
             if (chosen) {
                 const int j = atomicAdd(&s_nsel, 1);
-                if (j < p.sel_cap) p.sel[j] = i;
+                if (j < p.sel_cap) p.sel[j] = cidx(i);
+                if (j < kCap) s_idx[j] = i;
             }
         }
         __syncthreads();
@@ -365,27 +621,35 @@ __global__ void __launch_bounds__(kFinThreads, BATCHED ? 2 : 1) k_finalize(const
         const int nsel = s_nsel;
         const bool sorted = nsel <= kCap;
         if (sorted) {
-            // bitonic sort of the chosen set by site index (padding sorts last);
-            // the candidate arrays are no longer read, so they hold the sort keys
+            // bitonic sort of the chosen set by site index (padding sorts last).
+            // The payload is s_idx (chosen list entries, -1 for padding); the
+            // sort key is the site: read through s_site when the candidates are
+            // held in shared memory, else copied into s_site first (then free)
             int m = 1;
             while (m < nsel) m <<= 1;
             for (int i = t; i < m; i += kFinThreads) {
-                const int ci = i < nsel ? p.sel[i] : -1;
-                s_idx[i] = ci;
-                s_key[i] = (double)(ci >= 0 ? p.cand[ci].site : 0x7fffffff);
+                if (i >= nsel) s_idx[i] = -1;
+                if (!small) s_site[i] = i < nsel ? site_of(s_idx[i]) : 0x7fffffff;
             }
             __syncthreads();
-            for (int i = t; i < m; i += kFinThreads) s_site[i] = (int)s_key[i];
-            __syncthreads();
+            auto skey = [&](int i) -> int {
+                if (!small) return s_site[i];
+                const int li = s_idx[i];
+                return li >= 0 ? s_site[li] : 0x7fffffff;
+            };
             for (int size = 2; size <= m; size <<= 1) {
                 for (int stride = size >> 1; stride > 0; stride >>= 1) {
                     for (int i = t; i < m; i += kFinThreads) {
                         const int j = i ^ stride;
                         if (j > i) {
                             const bool up = (i & size) == 0;
-                            if ((s_site[i] > s_site[j]) == up) {
-                                int a = s_site[i]; s_site[i] = s_site[j]; s_site[j] = a;
-                                a = s_idx[i]; s_idx[i] = s_idx[j]; s_idx[j] = a;
+                            const int ki = skey(i), kj = skey(j);
+                            if ((ki > kj) == up) {
+                                int a = s_idx[i]; s_idx[i] = s_idx[j]; s_idx[j] = a;
+                                if (!small) {
+                                    s_site[i] = kj;
+                                    s_site[j] = ki;
+                                }
                             }
                         }
                     }
@@ -395,9 +659,22 @@ __global__ void __launch_bounds__(kFinThreads, BATCHED ? 2 : 1) k_finalize(const
         }
         // Ehrenfests' step at each chosen site, in site order when sorted
         for (int r = t; r < nsel; r += kFinThreads) {
-            const int ci = sorted ? s_idx[r] : p.sel[r];
-            const Cand c = p.cand[ci];
-            const int x = c.site % p.nx, y = c.site / p.nx;
+            // the chosen candidate's site and key (from shared memory when
+            // sorted) and its phi
+            int site;
+            double key, phi;
+            if (sorted) {
+                const int li = s_idx[r];
+                site = small ? s_site[li] : s_site[r];
+                key = key_of(li);
+                phi = p.cand[cidx(li)].phi;
+            } else {
+                const Cand c = p.cand[p.sel[r]];
+                site = c.site;
+                key = c.key;
+                phi = c.phi;
+            }
+            const int x = site % p.nx, y = site / p.nx;
             T g[Q], fs[Q], rho, ux, uy;
             bool write = true;
             if constexpr (std::is_same<T, float>::value) {
@@ -453,12 +730,12 @@ __global__ void __launch_bounds__(kFinThreads, BATCHED ? 2 : 1) k_finalize(const
 #pragma unroll
                 for (int q = 0; q < Q; ++q) f[fidx(p.plane, p.pitch, q, y, x)] = f2s<S>(fs[q]);
             }
-            if (p.eq != 1) ehr_sum = Ar<double>::add(ehr_sum, Ar<double>::mul(Ar<double>::mul(c.phi, c.phi), c.key));
+            if (p.eq != 1) ehr_sum = Ar<double>::add(ehr_sum, Ar<double>::mul(Ar<double>::mul(phi, phi), key));
         }
         __syncthreads();
         // the chosen sites, as site indices, for lbm_limited_sites
         if (sorted) {
-            for (int r = t; r < nsel; r += kFinThreads) p.sel[r] = s_site[r];
+            for (int r = t; r < nsel; r += kFinThreads) p.sel[r] = small ? s_site[s_idx[r]] : s_site[r];
         } else {
             // unsorted (more than kCap chosen): convert in place, one owner per slot
             for (int r = t; r < nsel; r += kFinThreads) p.sel[r] = p.cand[p.sel[r]].site;
@@ -520,22 +797,47 @@ __global__ void __launch_bounds__(kFinThreads, BATCHED ? 2 : 1) k_finalize(const
 }  // namespace
 
 template <typename T>
-cudaError_t launch_finalize(int q, const FinalParams &p, T *f, cudaStream_t s)
+cudaError_t launch_finalize(int q, const FinalParams &p, T *f, cudaStream_t s, int grid)
 {
-    // programmatic dependent launch (see k_finalize)
+    // programmatic dependent launch (see k_finalize); a grid is a cooperative
+    // launch, so that its blocks are resident together for the grid barrier
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(1);
+    cfg.gridDim = dim3(grid > 1 ? grid : 1);
     cfg.blockDim = dim3(kFinThreads);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
+    attr[1].id = cudaLaunchAttributeCooperative;
+    attr[1].val.cooperative = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = grid > 1 ? 2 : 1;
+    FinalParams pp = p;
+    if (grid <= 1) pp.sel_state = nullptr;
     const FinalArgs *none = nullptr;
-    if (q == 9) return cudaLaunchKernelEx(&cfg, k_finalize<9, T, false>, p, f, none);
-    return cudaLaunchKernelEx(&cfg, k_finalize<3, T, false>, p, f, none);
+    if (grid > 1) {
+        if (q == 9) return cudaLaunchKernelEx(&cfg, k_finalize<9, T, false, true>, pp, f, none);
+        return cudaLaunchKernelEx(&cfg, k_finalize<3, T, false, true>, pp, f, none);
+    }
+    if (q == 9) return cudaLaunchKernelEx(&cfg, k_finalize<9, T, false>, pp, f, none);
+    return cudaLaunchKernelEx(&cfg, k_finalize<3, T, false>, pp, f, none);
+}
+
+template <typename T>
+int finalize_grid(int q)
+{
+    int dev = 0, coop = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
+    const cudaError_t e = q == 9
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_finalize<9, T, false, true>, kFinThreads, 0)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_finalize<3, T, false, true>, kFinThreads, 0);
+    if (e != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        return 0;
+    }
+    return sm_count();
 }
 
 cudaError_t launch_finalize_batched_f32(int q, const FinalArgs *table, int n, cudaStream_t s)
@@ -549,9 +851,13 @@ cudaError_t launch_finalize_batched_f32(int q, const FinalArgs *table, int n, cu
     return cudaGetLastError();
 }
 
-template cudaError_t launch_finalize<float>(int, const FinalParams &, float *, cudaStream_t);
-template cudaError_t launch_finalize<double>(int, const FinalParams &, double *, cudaStream_t);
-template cudaError_t launch_finalize<__nv_bfloat16>(int, const FinalParams &, __nv_bfloat16 *, cudaStream_t);
-template cudaError_t launch_finalize<__half>(int, const FinalParams &, __half *, cudaStream_t);
+template cudaError_t launch_finalize<float>(int, const FinalParams &, float *, cudaStream_t, int);
+template cudaError_t launch_finalize<double>(int, const FinalParams &, double *, cudaStream_t, int);
+template cudaError_t launch_finalize<__nv_bfloat16>(int, const FinalParams &, __nv_bfloat16 *, cudaStream_t, int);
+template cudaError_t launch_finalize<__half>(int, const FinalParams &, __half *, cudaStream_t, int);
+template int finalize_grid<float>(int);
+template int finalize_grid<double>(int);
+template int finalize_grid<__nv_bfloat16>(int);
+template int finalize_grid<__half>(int);
 
 }  // namespace lbm

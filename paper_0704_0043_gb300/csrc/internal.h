@@ -77,12 +77,40 @@ constexpr int kFxWords = 16;
 constexpr int kFxRows = 8;
 enum { FX_SUM = 0, FX_SITES = 8, FX_NPOS, FX_NMED, FX_NBAD, FX_BAD };
 
-// Ehrenfests' candidate: FP64 key dS(f'), phi of the limiter pass, site index.
+// Ehrenfests' candidate: FP64 key dS(f') (NaN: not keyed yet), phi of the
+// limiter pass, site index, and dS(f') in FP32 (the key rounded, or the FP32
+// value the candidate was recorded on; within 1/64 of the key).
 struct Cand {
     double key;
     double phi;
     int32_t site;
-    int32_t pad;
+    float ds32;
+};
+
+// Device-wide preselection of Ehrenfests' candidates: when a pass records
+// more candidates than the tail's block holds in shared memory, the tail runs
+// as a grid of one block per SM.  The grid finds, by two 12-bit radix levels
+// over the FP32 dS bit patterns of the candidates certainly above delta, a
+// lower bound T of the k-th largest; keys in FP64 the candidates with FP32 dS
+// of at least T (1 - 1/32) and those near delta; counts the valid candidates;
+// and hands block 0 the short list of valid candidates at or above the bound,
+// which holds every candidate the exact top-k can take.
+constexpr int kSelBins = 4096;   // bins of one radix level
+// Lattices of at least this many sites get the grid tail.  Its launch costs
+// one to two microseconds per step, a tenth of a smaller lattice's step; on
+// those, one block keys and selects the candidates, about 0.1 us per
+// candidate without a key (a tenth of a second when every site of a 2^20-site
+// lattice is one).
+constexpr long long kSelMinSites = 1ll << 20;
+constexpr int kSelList = 65536;  // the longest list block 0 is handed
+struct SelState {
+    unsigned hist1[kSelBins];  // level 1: bits 30..19 of the FP32 dS pattern
+    unsigned hist2[kSelBins];  // level 2: bits 18..7 within level 1's bin
+    unsigned bar;              // grid barrier: arrivals so far (block 0 resets it)
+    unsigned count;            // list entries (more than kSelList: overflow)
+    unsigned n_valid;          // candidates with dS above delta
+    unsigned pad;
+    int list[kSelList];        // candidate indices
 };
 
 struct DevStats {  // mirrors lbm_step_stats
@@ -170,6 +198,9 @@ struct FinalParams {
     double *probe;
     long long probe_cap;
     int probe_site;
+    // dense candidates: the grid's shared selection state (launches of more
+    // than one block only; nullptr otherwise)
+    SelState *sel_state = nullptr;
 };
 
 // Arguments of one fused-kernel instance (a lattice, its buffers and its
@@ -206,8 +237,15 @@ struct TubeArgs {
 template <typename T>
 cudaError_t launch_tiled(int q, const StepParams &p, const T *src, T *dst, int *nblocks,
                          cudaStream_t s);
+// The tail: one block, or (grid > 1, p.sel_state set) a cooperative grid of
+// `grid` blocks that preselects dense candidates; the launch returns the
+// launch error without a fallback.
 template <typename T>
-cudaError_t launch_finalize(int q, const FinalParams &p, T *f, cudaStream_t s);
+cudaError_t launch_finalize(int q, const FinalParams &p, T *f, cudaStream_t s, int grid = 1);
+// Blocks of the tail's cooperative grid on this device: one per SM (0 when a
+// block does not fit or the device has no cooperative launch).
+template <typename T>
+int finalize_grid(int q);
 // Field kernels take the StepParams of the context for the layout (nx, ny,
 // pitch, plane) and the FP32 storage offsets (rw).
 template <typename T>
@@ -293,6 +331,9 @@ struct lbm_ctx {
     int cur = 0;
     lbm::Cand *cand = nullptr;
     int cand_cap = 0;
+    lbm::SelState *sel_state = nullptr;  // Ehrenfests' limiter: the cooperative tail's selection state
+    int fin_grid = 0;                     // blocks of the cooperative tail (0: one-block tail only)
+    bool capturing = false;               // a graph capture is in progress (one-block tail)
     double *ens = nullptr;  // [kEnsBlocks][2] partial sums and counts of dS, then E(dS), alpha, sum, count
     void *ent_field = nullptr;   // LBM_LIM_ENTTHRESH: the pass's dS field
     lbm::EntState *ent = nullptr;  // LBM_LIM_ENTTHRESH: solve state

@@ -136,11 +136,12 @@ size_t fx_bytes() { return (size_t)kFxRows * kFxWords * sizeof(unsigned long lon
 struct Sizes {
     int q, pitch;
     long long plane;
-    size_t elem, field, cand, sel, partials, ring, ent;
+    size_t elem, field, cand, sel, partials, ring, ent, selstate;
     int cand_cap, sel_cap, rows, ring_len;
     int64_t total() const
     {
-        return (int64_t)(2 * field + cand + sel + partials + ring + ens_bytes() + ent + 64 * sizeof(long long) +
+        return (int64_t)(2 * field + cand + sel + partials + ring + ens_bytes() + ent + selstate +
+                         64 * sizeof(long long) +
                          (size_t)chunks_for(rows) * sizeof(unsigned) + 4096);
     }
 };
@@ -156,6 +157,7 @@ Sizes sizes_for(const lbm_config &c)
     const long long n = (long long)c.nx * c.ny;
     z.cand_cap = (c.limiters & LBM_LIM_EHRENFEST) ? (int)n : 1;
     z.cand = (size_t)z.cand_cap * sizeof(Cand);
+    z.selstate = (c.limiters & LBM_LIM_EHRENFEST) && n >= kSelMinSites ? sizeof(SelState) : 0;
     z.sel_cap = (int)std::max<long long>(1, std::min<long long>(c.k_max, n));
     z.sel = (size_t)z.sel_cap * sizeof(int);
     // [fused accumulator rows][tiled block rows][chunk rows]
@@ -332,9 +334,21 @@ lbm_status run_pass(lbm_ctx *c, int collide, unsigned limiters)
         f.nblocks = nblocks;
     }
     f.work = fused ? c->counts + 2 : nullptr;
+    // the tail: a cooperative grid when the context has one (it preselects
+    // dense Ehrenfests' candidates); a graph capture keeps the one-block tail.
+    // A device that refuses the cooperative launch keeps the one-block tail
+    // from then on.
+    const int grid = (c->sel_state && !c->capturing) ? c->fin_grid : 1;
+    f.sel_state = c->sel_state;
     e = with_storage(c->cfg.precision, [&](auto tag) -> cudaError_t {
         using S = STORAGE_T;
-        return launch_finalize<S>(c->q, f, (S *)dst, c->stream);
+        cudaError_t le = launch_finalize<S>(c->q, f, (S *)dst, c->stream, grid);
+        if (le != cudaSuccess && grid > 1) {
+            cudaGetLastError();
+            c->fin_grid = 0;
+            le = launch_finalize<S>(c->q, f, (S *)dst, c->stream, 1);
+        }
+        return le;
     });
     if (e != cudaSuccess) return cuda_fail(c, e, "finalize kernel launch");
     if ((ms = mark(c)) != LBM_OK) return ms;
@@ -363,6 +377,8 @@ lbm_status reset_counters(lbm_ctx *c)
     if (fused_applies(c->cfg))  // the fused kernel's fixed-point accumulators
         CK(c, cudaMemsetAsync(c->partials, 0, fx_bytes(), c->stream));
     CK(c, cudaMemsetAsync(c->ring, 0, (size_t)c->ring_len * sizeof(DevStats), c->stream));
+    if (c->sel_state)  // histograms, barrier and counts (a timed-out pass may leave them set)
+        CK(c, cudaMemsetAsync(c->sel_state, 0, offsetof(SelState, list), c->stream));
     return LBM_OK;
 }
 
@@ -386,6 +402,7 @@ lbm_status capture_graph(lbm_ctx *c)
     const int start = c->cur;
     cudaStream_t user = c->stream;
     c->stream = c->gstream;
+    c->capturing = true;
     cudaGraph_t g = nullptr;
     const long long launches = c->launches;
     cudaError_t e = cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal);
@@ -396,6 +413,7 @@ lbm_status capture_graph(lbm_ctx *c)
         if (e == cudaSuccess) e = ee;
     }
     c->stream = user;
+    c->capturing = false;
     c->cur = start;
     c->graph_launches = c->launches - launches;
     c->launches = launches;
@@ -421,7 +439,8 @@ void free_all(lbm_ctx *c)
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     c->events.clear();
     void *ptrs[] = {c->buf[0], c->buf[1], c->cand, c->counts, c->sel, c->partials, c->chunk_cnt,
-                    c->status, c->ring, c->counters, c->stage, c->ens, c->probe, c->ent_field, c->ent};
+                    c->status, c->ring, c->counters, c->stage, c->ens, c->probe, c->ent_field, c->ent,
+                    c->sel_state};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -607,6 +626,15 @@ lbm_status lbm_create(const lbm_config *cfg, void *cuda_stream, lbm_ctx **out)
     alloc((void **)&c->ring, z.ring);
     alloc((void **)&c->counters, 2 * sizeof(long long));
     alloc((void **)&c->ens, ens_bytes());
+    if (z.selstate) {
+        alloc((void **)&c->sel_state, z.selstate);
+        switch (c->cfg.precision) {
+        case LBM_FP64: c->fin_grid = finalize_grid<double>(c->q); break;
+        case LBM_FP32: c->fin_grid = finalize_grid<float>(c->q); break;
+        case LBM_BF16: c->fin_grid = finalize_grid<__nv_bfloat16>(c->q); break;
+        default: c->fin_grid = finalize_grid<__half>(c->q);
+        }
+    }
     if (z.ent) {
         alloc(&c->ent_field, z.ent - sizeof(EntState));
         alloc((void **)&c->ent, sizeof(EntState));

@@ -169,6 +169,7 @@ __global__ void __launch_bounds__(kThreads, ENT ? 3 : (BATCHED ? kBlocksPerSMBat
     __shared__ __align__(16) S ring[kWarps][kRing][9][kWinS];
     __shared__ unsigned long long sfx[kWarps][kFxWords];
     __shared__ int cand_list[kWarps][kCandList];  // candidate slots of the warp's current item
+    __shared__ float2 cand_ds[kWarps][2][32];      // FP32 dS of the lanes' candidates, rows of each parity
     __shared__ __align__(16) FusedArgs sA[BATCHED ? kWarps : 1];
     const int bid = (int)blockIdx.x;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
@@ -563,6 +564,10 @@ __global__ void __launch_bounds__(kThreads, ENT ? 3 : (BATCHED ? kBlocksPerSMBat
             // FP64 key decides
             st.cand_a = lim_ehr && !bad_a && oa && ds.x > A.thr_e;
             st.cand_b = lim_ehr && !bad_b && ob && ds.y > A.thr_e;
+            // their FP32 dS for the record one row later (kept in shared memory,
+            // not in registers across the row: row q is recorded after row q + 1
+            // is computed, so rows of each parity have their own slot)
+            if (st.cand_a || st.cand_b) cand_ds[warp][q & 1][lane] = ds;
             st.bad_a = bad_a;
             st.bad_b = bad_b;
             st.ds = ds;
@@ -570,11 +575,12 @@ __global__ void __launch_bounds__(kThreads, ENT ? 3 : (BATCHED ? kBlocksPerSMBat
         };
 
         // Ehrenfests' candidates of row y (flags ca / cb of the lanes' two
-        // columns) are recorded at once without their key (NaN); the warp
-        // keeps their slots in its list and keys them when the item is done,
-        // away from the row loop's registers
+        // columns) are recorded at once without their key (NaN), with their
+        // FP32 dS; the warp keeps their slots in its list and keys them when
+        // the item is done, away from the row loop's registers
         auto record = [&](int y, bool ca, bool cb, float phi_a, float phi_b) {
-            auto put = [&](bool c, int x, float phi) {
+            const float2 ds = cand_ds[warp][y & 1][lane];
+            auto put = [&](bool c, int x, float phi, float ds32) {
                 int slot = -1;
                 if (c) {
                     slot = atomicAdd(p.cand_count, 1);
@@ -583,7 +589,7 @@ __global__ void __launch_bounds__(kThreads, ENT ? 3 : (BATCHED ? kBlocksPerSMBat
                         cd.key = __longlong_as_double(0x7ff8000000000000LL);
                         cd.phi = (double)phi;
                         cd.site = y * nx + x;
-                        cd.pad = 0;
+                        cd.ds32 = ds32;
                         p.cand[slot] = cd;
                     } else {
                         atomicOr(p.status, kStatCandOverflow);
@@ -595,8 +601,8 @@ __global__ void __launch_bounds__(kThreads, ENT ? 3 : (BATCHED ? kBlocksPerSMBat
                 if (slot >= 0 && at < kCandList) list[at] = slot;
                 n_list += __popc(m);
             };
-            put(ca, xa, phi_a);
-            put(cb, xb, phi_b);
+            put(ca, xa, phi_a, ds.x);
+            put(cb, xb, phi_b, ds.y);
         };
 
         // Row y: median of dS (rows y-1, y, y+1 in dm, d0, dp), phi = min(phi_pos,

@@ -528,7 +528,7 @@ __global__ void __launch_bounds__(256) k_tiled(const StepParams p0, const S *__r
                     c.key = key;
                     c.site = y * p.nx + x;
                     c.phi = (double)phi;
-                    c.pad = 0;
+                    c.ds32 = (float)key;
                     p.cand[slot] = c;
                 } else {
                     atomicOr(p.status, kStatCandOverflow);

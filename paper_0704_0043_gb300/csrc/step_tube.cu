@@ -225,7 +225,7 @@ __device__ __forceinline__ void tube_walk(const StepParams &p, const S *__restri
             cd.key = key;
             cd.site = x;
             cd.phi = phi;
-            cd.pad = 0;
+            cd.ds32 = (float)key;
             p.cand[slot] = cd;
         } else {
             atomicOr(p.status, kStatCandOverflow);
