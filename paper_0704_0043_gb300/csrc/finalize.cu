@@ -242,8 +242,8 @@ __device__ void pick_bin(const unsigned *h, long long rem, long long *s_wpart, i
 // compact without this rarely taken path.
 template <int Q, typename S>
 __device__ __noinline__ bool dense_select(const FinalParams &p, int n, unsigned *sh, long long *s_wpart, int *s_bin,
-                             long long *s_rem, long long *s_tot, int *s_flag, unsigned *s_acc, unsigned *s_cnt,
-                             unsigned *s_nv)
+                             long long *s_rem, long long *s_tot, int *s_flag, int *s_qn, unsigned *s_acc,
+                             unsigned *s_cnt, unsigned *s_nv)
 {
     SelState *ss = p.sel_state;
     const int t = threadIdx.x, lane = t & 31;
@@ -254,11 +254,21 @@ __device__ __noinline__ bool dense_select(const FinalParams &p, int n, unsigned 
     auto in_r = [&](int u) { return u > dhi_bits && u < 0x7f800000; };  // FP32 dS above dhi (finite)
 
     // level 1: bits 30..19 of the candidates in R
+    // lanes with the same bin add once (most candidates fall in a few bins)
+    auto count_bin = [&](int bin) {
+        const unsigned peers = __match_any_sync(kFull, bin);
+        if (bin >= 0 && lane == __ffs(peers) - 1) atomicAdd(&sh[bin], (unsigned)__popc(peers));
+    };
     for (int b = t; b < kSelBins; b += kFinThreads) sh[b] = 0;
     __syncthreads();
-    for (long long i = base0 + t; i < n; i += stride) {
-        const int u = __float_as_int(p.cand[i].ds32);
-        if (in_r(u)) atomicAdd(&sh[u >> 19], 1u);
+    for (long long base = base0; base < n; base += stride) {  // whole warps per round
+        const long long i = base + t;
+        int bin = -1;
+        if (i < n) {
+            const int u = __float_as_int(p.cand[i].ds32);
+            if (in_r(u)) bin = u >> 19;
+        }
+        count_bin(bin);
     }
     __syncthreads();
     for (int b = t; b < kSelBins; b += kFinThreads)
@@ -273,9 +283,14 @@ __device__ __noinline__ bool dense_select(const FinalParams &p, int n, unsigned 
     for (int b = t; b < kSelBins; b += kFinThreads) sh[b] = 0;
     __syncthreads();
     if (!all) {
-        for (long long i = base0 + t; i < n; i += stride) {
-            const int u = __float_as_int(p.cand[i].ds32);
-            if (in_r(u) && (u >> 19) == b1) atomicAdd(&sh[(u >> 7) & (kSelBins - 1)], 1u);
+        for (long long base = base0; base < n; base += stride) {
+            const long long i = base + t;
+            int bin = -1;
+            if (i < n) {
+                const int u = __float_as_int(p.cand[i].ds32);
+                if (in_r(u) && (u >> 19) == b1) bin = (u >> 7) & (kSelBins - 1);
+            }
+            count_bin(bin);
         }
         __syncthreads();
         for (int b = t; b < kSelBins; b += kFinThreads)
@@ -290,35 +305,72 @@ __device__ __noinline__ bool dense_select(const FinalParams &p, int n, unsigned 
         const unsigned ulb = ((unsigned)b1 << 19) | ((unsigned)*s_bin << 7);
         tlow_bits = __float_as_int(__uint_as_float(ulb) * 0.96875f);
     }
-    if (t == 0) *s_acc = 0;
+    // Candidates without a key that need one are queued in shared memory (the
+    // histogram is no longer needed) and keyed a block at a time, every lane
+    // busy: FP64 is slow on this GPU, and keying them where they lie would
+    // run most warps' FP64 code for one or two lanes.
+    int *queue = reinterpret_cast<int *>(sh);  // at most 2 kFinThreads - 1 entries
+    if (t == 0) {
+        *s_acc = 0;
+        *s_qn = 0;
+    }
     __syncthreads();
     constexpr bool kKeyHere = !std::is_same<S, double>::value && Q == 9;  // candidates recorded without a key
     const KeyGeom kg = key_geom(p);
     unsigned nv = 0;
-    for (long long base = base0; base < n; base += stride) {  // whole warps per round (warp-aggregated appends)
-        const long long i = base + t;
-        bool valid = false, listed = false;
-        if (i < n) {
-            const Cand c = p.cand[i];
-            const int u = __float_as_int(c.ds32);
-            listed = u >= tlow_bits;
-            double key = c.key;
-            if constexpr (kKeyHere) {
-                if (isnan(key) && (listed || u <= dhi_bits)) {
-                    key = key_dS9_lane<S>(kg, (const S *)p.src, c.site, p.delta_e);
-                    p.cand[i].key = key;
-                }
-            }
-            valid = isnan(key) ? in_r(u) : key > p.delta_e;
-            listed = listed && valid;
-        }
+    // warp-aggregated list append (every lane of the warp calls it)
+    auto append = [&](bool listed, long long i) {
         const unsigned m = __ballot_sync(kFull, listed);
         unsigned at = 0;
         if (lane == 0 && m) at = atomicAdd(&ss->count, (unsigned)__popc(m));
         at = __shfl_sync(kFull, at, 0) + __popc(m & ((1u << lane) - 1u));
         if (listed && at < (unsigned)kSelList) ss->list[at] = (int)i;
+    };
+    // key queue entries from .. from + cnt - 1 (cnt <= kFinThreads), one per thread
+    auto drain = [&](int from, int cnt) {
+        bool listed = false;
+        long long i = -1;
+        if (t < cnt) {
+            i = queue[from + t];
+            const Cand c = p.cand[i];
+            const double key = key_dS9_lane<S>(kg, (const S *)p.src, c.site, p.delta_e);
+            p.cand[i].key = key;
+            const bool valid = key > p.delta_e;
+            nv += valid;
+            listed = valid && __float_as_int(c.ds32) >= tlow_bits;
+        }
+        append(listed, i);
+    };
+    for (long long base = base0; base < n; base += stride) {  // whole blocks per round
+        const long long i = base + t;
+        bool valid = false, listed = false, need = false;
+        if (i < n) {
+            const Cand c = p.cand[i];
+            const int u = __float_as_int(c.ds32);
+            const bool top = u >= tlow_bits;
+            need = kKeyHere && isnan(c.key) && (top || u <= dhi_bits);
+            valid = !need && (isnan(c.key) ? in_r(u) : c.key > p.delta_e);
+            listed = top && valid;
+        }
+        append(listed, i);
         nv += valid;
+        if constexpr (kKeyHere) {
+            const unsigned m = __ballot_sync(kFull, need);
+            int at = 0;
+            if (lane == 0 && m) at = atomicAdd(s_qn, __popc(m));
+            at = __shfl_sync(kFull, at, 0) + __popc(m & ((1u << lane) - 1u));
+            if (need) queue[at] = (int)i;
+            __syncthreads();
+            const int qn = *s_qn;  // the same for the whole block
+            if (qn >= kFinThreads) {
+                drain(qn - kFinThreads, kFinThreads);
+                __syncthreads();  // the entries are read before new ones overwrite them
+                if (t == 0) *s_qn = qn - kFinThreads;
+                __syncthreads();
+            }
+        }
     }
+    if constexpr (kKeyHere) drain(0, *s_qn);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) nv += __shfl_down_sync(kFull, nv, o);
     if (lane == 0 && nv) atomicAdd(s_acc, nv);
@@ -363,7 +415,7 @@ __global__ void __launch_bounds__(kFinThreads, BATCHED ? 2 : 1) k_finalize(const
     __shared__ int s_site[kCap];
     __shared__ int s_idx[kCap];
     __shared__ long long s_wpart[kFinWarps], s_rem2, s_tot;
-    __shared__ int s_bin, s_flag;
+    __shared__ int s_bin, s_flag, s_qn;
     __shared__ unsigned s_acc, s_cnt, s_nv;
     // dense candidates in a grid launch: every block preselects, then block 0
     // runs the tail over the list (use_list) or, when the list overflowed,
@@ -376,7 +428,7 @@ __global__ void __launch_bounds__(kFinThreads, BATCHED ? 2 : 1) k_finalize(const
         if (!dense && blockIdx.x != 0) return;
         if (dense) {
             use_list = dense_select<Q, S>(p0, n0, reinterpret_cast<unsigned *>(s_key), s_wpart, &s_bin, &s_rem2,
-                                          &s_tot, &s_flag, &s_acc, &s_cnt, &s_nv);
+                                          &s_tot, &s_flag, &s_qn, &s_acc, &s_cnt, &s_nv);
             if (blockIdx.x != 0) return;
         }
     }

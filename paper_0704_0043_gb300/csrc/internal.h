@@ -199,8 +199,8 @@ struct FinalParams {
     long long probe_cap;
     int probe_site;
     // dense candidates: the grid's shared selection state (launches of more
-    // than one block only; nullptr otherwise)
-    SelState *sel_state = nullptr;
+    // than one block only; nullptr otherwise; FinalParams{} zeroes it)
+    SelState *sel_state;
 };
 
 // Arguments of one fused-kernel instance (a lattice, its buffers and its

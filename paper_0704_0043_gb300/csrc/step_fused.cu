@@ -789,8 +789,11 @@ __global__ void __launch_bounds__(kThreads, ENT ? 3 : (BATCHED ? kBlocksPerSMBat
         // site is at or below the threshold or cannot be limited).  A few are
         // keyed one at a time by the whole warp (a lane per direction, the
         // shortest latency), more lane-parallel; past kCandList the tail
-        // kernel keys the rest.
-        if (n_list > 0) {  // the same for the whole warp
+        // kernel keys the rest.  An item with more candidates than that on a
+        // lattice with the grid tail keys none: the grid keys only those that
+        // can matter (near the k-th largest or near delta).
+        const bool dense_item = !BATCHED && n_list > kCandList && (long long)nx * ny >= kSelMinSites;
+        if (n_list > 0 && !dense_item) {  // the same for the whole warp
             KeyGeom kg;
             kg.nx = nx;
             kg.ny = ny;
@@ -820,8 +823,8 @@ __global__ void __launch_bounds__(kThreads, ENT ? 3 : (BATCHED ? kBlocksPerSMBat
                 }
             }
             __syncwarp();
-            n_list = 0;
         }
+        n_list = 0;
         // the item's sums, then the next item
         flush();
         rows_acc = 0;
