@@ -107,6 +107,48 @@ __device__ compute_t<S> tube_ds(const StepParams &p, const TubeK &kk, const S *_
     return ds;
 }
 
+// The polynomial FP32 collision of two sites at once: site_collide_dev (eq = 0,
+// after a collision) in paired FP32 instructions (F2), the same explicitly
+// rounded operations in the same order, so each site gets the same bits.
+// Returns f' - rho_ref W (gp), dS(f'), dS(f_in), rho, and whether each site
+// cannot be limited (rho <= 0, some f*_k <= 0, dS not finite).
+__device__ __forceinline__ void tube_pair_eval(const TubeK &kk, float rho_ref, const float *rwf, const float2 g[3],
+                                               float2 gp[3], float2 &ds, float2 &din, float2 &rho, bool &bad_x,
+                                               bool &bad_y)
+{
+    using O = F2;
+    const float2 drho = O::add(O::add(g[0], g[1]), g[2]);
+    rho = O::add(O::s(rho_ref), drho);
+    const float2 u = O::mul(O::sub(g[2], g[1]), O::rcp_rn(rho));
+    const float2 A = O::mul(O::s(1.0f / 6.0f), O::fma(O::mul(O::mul(O::s(3.0f), rho), u), u, drho));
+    const float2 B = O::mul(O::mul(O::s(0.5f), rho), u);
+    float2 gs[3], n[3];
+    gs[1] = O::sub(A, B);
+    gs[2] = O::add(A, B);
+    gs[0] = O::sub(drho, O::add(gs[1], gs[2]));
+#pragma unroll
+    for (int k = 0; k < 3; ++k) n[k] = O::sub(g[k], gs[k]);
+    const float2 rm = O::add(O::add(n[0], n[1]), n[2]);
+    const float2 hx = O::mul(O::s(0.5f), O::sub(n[2], n[1]));
+    n[0] = O::sub(n[0], rm);
+    n[2] = O::sub(n[2], hx);
+    n[1] = O::add(n[1], hx);
+    float2 d = O::s(0.f);
+    float mx = 3.4e38f, my = 3.4e38f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float2 fsa = O::add(O::s(rwf[k]), gs[k]);
+        d = O::fma(O::mul(n[k], n[k]), O::rcp_fast(fsa), d);
+        gp[k] = O::fma(O::s(-kk.b2), n[k], g[k]);
+        mx = fminf(mx, fsa.x);
+        my = fminf(my, fsa.y);
+    }
+    din = d;
+    ds = O::mul(O::s(__fmul_rn(kk.a, kk.a)), d);
+    bad_x = !(rho.x > 0.f) || !(mx > 0.f) || !isfinite(ds.x);
+    bad_y = !(rho.y > 0.f) || !(my > 0.f) || !isfinite(ds.y);
+}
+
 // Asynchronous copy of N = 4, 8 or 16 bytes global -> shared (cp.async; the
 // 16-byte form bypasses L1), and the per-thread group bookkeeping.
 template <int N>
@@ -174,7 +216,7 @@ struct alignas(16) TubeSlot {
 // a1-a9 at every site, the Ehrenfests' candidates, the sums into acc.  `my`:
 // the warp's ring; klist / kcount: the warp's candidate list (FP32 storage).
 // Every lane of the warp takes part.
-template <typename S, int V>
+template <typename S, int V, bool FAST = true>
 __device__ __forceinline__ void tube_walk(const StepParams &p, const S *__restrict__ src, S *__restrict__ dst,
                                           int c0, int stride, int c_end, TubeSlot<S, V> *my, int2 *klist,
                                           int *kcount, TubeAcc &acc)
@@ -257,8 +299,69 @@ __device__ __forceinline__ void tube_walk(const StepParams &p, const S *__restri
         T fin[V][3], fs[V][3], fp[V][3], fa[V][3], ds[V], dsin[V], rho[V];
         float nq[V][3];
         bool bad[V];
+        // FP32, four sites a lane: a lane inside the tube in a colliding
+        // polynomial pass evaluates its sites as two pairs (0, 1), (2, 3) with
+        // paired instructions.  A pair on which no limiter acts (no bad site, no
+        // negative f', no dS above the median filter's delta) is finished here;
+        // the sites of any other pair are evaluated again one by one below
+        T s_mass = T(0), s_ds = T(0), s_in = T(0), s_lim = T(0);
+        bool fastp[2] = {false, false};
+        if constexpr (FAST && !F64 && V == 4) {
+            if (p.collide && p.eq == 0 && xl >= 1 && xl + V <= nx - 1) {
+                // the finished pairs' sums, added pairwise (paired instructions)
+                float2 m2 = F2::s(0.f), d2s = F2::s(0.f), i2s = F2::s(0.f), dmax = F2::s(0.f);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float2 g[3] = {make_float2(v0[2 * h], v0[2 * h + 1]),
+                                         make_float2(v1[2 * h + 1], h == 0 ? v1[2] : r1),
+                                         make_float2(h == 0 ? l2 : v2[1], v2[2 * h])};
+                    float2 gp[3], d2, i2, r2;
+                    bool bx, by;
+                    tube_pair_eval(kk, p.rho_ref, p.rwf, g, gp, d2, i2, r2, bx, by);
+                    bool act = bx || by;
+                    if (p.limiters & 1u) {
+#pragma unroll
+                        for (int k = 0; k < 3; ++k)
+                            act = act || (p.rwf[k] + gp[k].x < 0.f) || (p.rwf[k] + gp[k].y < 0.f);
+                    }
+                    if (p.limiters & 4u) act = act || d2.x > dm || d2.y > dm;
+                    ds[2 * h] = d2.x;
+                    ds[2 * h + 1] = d2.y;
+                    if (act) continue;
+                    // f' stored as one 8-byte vector a plane (xl + 2h is even)
+                    fastp[h] = true;
+                    const int x = xl + 2 * h;
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) *reinterpret_cast<float2 *>(dst + tidx(p, k, x)) = gp[k];
+                    m2 = F2::add(m2, F2::sub(r2, F2::s(p.rho_ref)));  // each term exact
+                    d2s = F2::add(d2s, d2);
+                    i2s = F2::add(i2s, i2);
+                    dmax = make_float2(fmaxf(dmax.x, d2.x), fmaxf(dmax.y, d2.y));
+                }
+                if (fastp[0] || fastp[1]) {
+                    s_mass = __fadd_rn(m2.x, m2.y);
+                    s_ds = __fadd_rn(d2s.x, d2s.y);
+                    s_in = __fadd_rn(i2s.x, i2s.y);
+                    acc.c_own += 2 * ((int)fastp[0] + (int)fastp[1]);
+                    // Ehrenfests' candidates among the finished sites (rare: one
+                    // test a lane), and the dS field when it is asked for
+                    if ((p.limiters & 2u) && fmaxf(dmax.x, dmax.y) > kk.thr_e) {
+#pragma unroll
+                        for (int j = 0; j < V; ++j)
+                            if (fastp[j >> 1] && ds[j] > kk.thr_e)
+                                klist[atomicAdd(kcount, 1)] = make_int2(xl + j, __float_as_int(1.f));
+                    }
+                    if (p.ds_out) {
+#pragma unroll
+                        for (int j = 0; j < V; ++j)
+                            if (fastp[j >> 1]) p.ds_out[xl + j] = (double)ds[j];
+                    }
+                }
+            }
+        }
 #pragma unroll
         for (int j = 0; j < V; ++j) {
+            if (fastp[j >> 1]) continue;
             const int x = xl + j;
             ds[j] = T(0);
             dsin[j] = T(0);
@@ -286,11 +389,10 @@ __device__ __forceinline__ void tube_walk(const StepParams &p, const S *__restri
         const T dl_lane = __shfl_up_sync(0xffffffffu, ds[V - 1], 1);
         const T dr_lane = __shfl_down_sync(0xffffffffu, ds[0], 1);
 
-        T s_mass = T(0), s_ds = T(0), s_in = T(0), s_lim = T(0);
 #pragma unroll
         for (int j = 0; j < V; ++j) {
             const int x = xl + j;
-            if (x >= nx) continue;
+            if (fastp[j >> 1] || x >= nx) continue;
             ++acc.c_own;
             T phi_pos = T(1), phi_med = T(1);
             if (!bad[j]) {
@@ -558,8 +660,8 @@ __global__ void __launch_bounds__(256, 2) k_tube_batched(const TubeArgs *__restr
         const int nch = (p.nx + 32 * V - 1) / (32 * V);
         const int c0 = m.y * kTubeGroup, c1 = min(c0 + kTubeGroup, nch);
         TubeAcc acc{};
-        tube_walk<S, V>(p, (const S *)sA[warp].src, (S *)sA[warp].dst, c0, 1, c1, ring[warp], klist[warp],
-                        &kcount[warp], acc);
+        tube_walk<S, V, false>(p, (const S *)sA[warp].src, (S *)sA[warp].dst, c0, 1, c1, ring[warp], klist[warp],
+                               &kcount[warp], acc);
         // the item's totals; the counts are per lane
         double t_mass, t_ds, t_in, t_lim;
         tube_totals(acc, t_mass, t_ds, t_in, t_lim);
