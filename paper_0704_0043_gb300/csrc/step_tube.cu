@@ -149,6 +149,88 @@ __device__ __forceinline__ void tube_pair_eval(const TubeK &kk, float rho_ref, c
     bad_y = !(rho.y > 0.f) || !(my > 0.f) || !isfinite(ds.y);
 }
 
+// The sums and counts of one site finished by tube_site32.
+struct SiteSums {
+    float mass, ds, din, lim;
+    int bad, pos, med;
+};
+
+// One FP32 site that the paired fast path did not finish (a limiter acts on
+// its pair, its lane holds an end of the tube, or the pass is not a
+// polynomial collision), from its pull f_in: the evaluation, the positivity
+// rule, the three-point median (the neighbours' dS dsl / dsr, or evaluated
+// here for the sites xlo / xro outside the warp's chunk, -1 when given), the
+// limited or free update, its sums, the Ehrenfests' candidate and the dS
+// field.  The operations are those of the tiled kernel's FP32 path.  Not
+// inlined: the site's state stays out of the walk's registers.
+template <typename S>
+__device__ __noinline__ SiteSums tube_site32(const StepParams &p, TubeK kk, const S *__restrict__ src,
+                                             S *__restrict__ dst, int x, float f0, float f1, float f2, float dsl,
+                                             float dsr, int xlo, int xro, int2 *klist, int *kcount)
+{
+    SiteSums r{0.f, 0.f, 0.f, 0.f, 0, 0, 0};
+    const float fin[3] = {f0, f1, f2};
+    float fs[3], fp[3], fa[3], nq[3], ds, dsin, rho;
+    const bool bad = tube_eval<float>(p, kk, fin, fs, fp, fa, nq, ds, dsin, rho, true);
+    const int nx = p.nx;
+    float phi_pos = 1.f, phi_med = 1.f;
+    if (!bad) {
+        if (p.limiters & 1u) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const float fpa = p.rwf[k] + fp[k];  // absolute f'
+                if (fpa < 0.f) phi_pos = fminf(phi_pos, fa[k] / (fa[k] - fpa));
+            }
+        }
+        // three-point median (the two end sites of a closed tube are not
+        // filtered; a periodic tube's end sites wrap around to each other)
+        const bool end = p.boundary == 0 && (x == 0 || x == nx - 1);
+        if ((p.limiters & 4u) && ds > kk.dm && !end) {
+            const float left = xlo >= 0 ? tube_ds<S>(p, kk, src, xlo) : dsl;
+            const float right = xro >= 0 ? tube_ds<S>(p, kk, src, xro) : dsr;
+            phi_med = phi_median<float>(ds, med3(left, ds, right), kk.dm, p.median_mode);
+        }
+    }
+    const float phi = phi_pos < phi_med ? phi_pos : phi_med;
+    if (phi < 1.f) {
+        const float cw = limit_weight(phi, kk.a, p.collide != 0);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) dst[tidx(p, k, x)] = fmaf(-cw, nq[k], fin[k]);
+        if (p.eq == 1) {
+            float dout[3];
+            const float m = p.collide ? __fmul_rn(-phi, kk.a) : phi;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) dout[k] = __fmul_rn(m, nq[k]);
+            const float so = rel_entropy_dev<3>(dout, fa);
+            if (isfinite(ds) && isfinite(so)) r.lim = __fsub_rn(ds, so);
+        } else {
+            r.lim = __fmul_rn(__fsub_rn(1.f, __fmul_rn(phi, phi)), ds);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) dst[tidx(p, k, x)] = f2s<S>(fp[k]);
+    }
+    r.mass = __fsub_rn(rho, p.rho_ref);  // exact
+    if (!bad) {
+        if (p.eq == 1) {
+            if (isfinite(ds)) r.ds = ds;
+            if (isfinite(ds) && isfinite(dsin)) r.din = __fsub_rn(dsin, ds);
+        } else {
+            r.ds = ds;
+            r.din = dsin;
+        }
+    } else {
+        r.bad = 1;
+        atomicOr(p.status, kStatNonfinite);
+    }
+    r.pos = phi_pos < 1.f;
+    r.med = phi_med < 1.f;
+    // Ehrenfests' candidate: near or above the threshold, keyed in FP64 after the chunk
+    if ((p.limiters & 2u) && !bad && ds > kk.thr_e) klist[atomicAdd(kcount, 1)] = make_int2(x, __float_as_int(phi));
+    if (p.ds_out) p.ds_out[x] = (double)ds;
+    return r;
+}
+
 // Asynchronous copy of N = 4, 8 or 16 bytes global -> shared (cp.async; the
 // 16-byte form bypasses L1), and the per-thread group bookkeeping.
 template <int N>
@@ -296,216 +378,289 @@ __device__ __forceinline__ void tube_walk(const StepParams &p, const S *__restri
         const S r1 = lane == 31 ? sl.e[1] : sl.f[1][lane * V + V];
         const S l2 = lane == 0 ? sl.e[0] : sl.f[2][lane * V - 1];
 
-        T fin[V][3], fs[V][3], fp[V][3], fa[V][3], ds[V], dsin[V], rho[V];
-        float nq[V][3];
-        bool bad[V];
-        // FP32, four sites a lane: a lane inside the tube in a colliding
-        // polynomial pass evaluates its sites as two pairs (0, 1), (2, 3) with
-        // paired instructions.  A pair on which no limiter acts (no bad site, no
-        // negative f', no dS above the median filter's delta) is finished here;
-        // the sites of any other pair are evaluated again one by one below
-        T s_mass = T(0), s_ds = T(0), s_in = T(0), s_lim = T(0);
-        bool fastp[2] = {false, false};
-        if constexpr (FAST && !F64 && V == 4) {
-            if (p.collide && p.eq == 0 && xl >= 1 && xl + V <= nx - 1) {
-                // the finished pairs' sums, added pairwise (paired instructions)
-                float2 m2 = F2::s(0.f), d2s = F2::s(0.f), i2s = F2::s(0.f), dmax = F2::s(0.f);
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const float2 g[3] = {make_float2(v0[2 * h], v0[2 * h + 1]),
-                                         make_float2(v1[2 * h + 1], h == 0 ? v1[2] : r1),
-                                         make_float2(h == 0 ? l2 : v2[1], v2[2 * h])};
-                    float2 gp[3], d2, i2, r2;
-                    bool bx, by;
-                    tube_pair_eval(kk, p.rho_ref, p.rwf, g, gp, d2, i2, r2, bx, by);
-                    bool act = bx || by;
-                    if (p.limiters & 1u) {
-#pragma unroll
-                        for (int k = 0; k < 3; ++k)
-                            act = act || (p.rwf[k] + gp[k].x < 0.f) || (p.rwf[k] + gp[k].y < 0.f);
-                    }
-                    if (p.limiters & 4u) act = act || d2.x > dm || d2.y > dm;
-                    ds[2 * h] = d2.x;
-                    ds[2 * h + 1] = d2.y;
-                    if (act) continue;
-                    // f' stored as one 8-byte vector a plane (xl + 2h is even)
-                    fastp[h] = true;
-                    const int x = xl + 2 * h;
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) *reinterpret_cast<float2 *>(dst + tidx(p, k, x)) = gp[k];
-                    m2 = F2::add(m2, F2::sub(r2, F2::s(p.rho_ref)));  // each term exact
-                    d2s = F2::add(d2s, d2);
-                    i2s = F2::add(i2s, i2);
-                    dmax = make_float2(fmaxf(dmax.x, d2.x), fmaxf(dmax.y, d2.y));
-                }
-                if (fastp[0] || fastp[1]) {
-                    s_mass = __fadd_rn(m2.x, m2.y);
-                    s_ds = __fadd_rn(d2s.x, d2s.y);
-                    s_in = __fadd_rn(i2s.x, i2s.y);
-                    acc.c_own += 2 * ((int)fastp[0] + (int)fastp[1]);
-                    // Ehrenfests' candidates among the finished sites (rare: one
-                    // test a lane), and the dS field when it is asked for
-                    if ((p.limiters & 2u) && fmaxf(dmax.x, dmax.y) > kk.thr_e) {
-#pragma unroll
-                        for (int j = 0; j < V; ++j)
-                            if (fastp[j >> 1] && ds[j] > kk.thr_e)
-                                klist[atomicAdd(kcount, 1)] = make_int2(xl + j, __float_as_int(1.f));
-                    }
-                    if (p.ds_out) {
-#pragma unroll
-                        for (int j = 0; j < V; ++j)
-                            if (fastp[j >> 1]) p.ds_out[xl + j] = (double)ds[j];
-                    }
-                }
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < V; ++j) {
-            if (fastp[j >> 1]) continue;
+        // the lane's pull of its site j (free flight with the tube's ends, or
+        // the stored values of a limiter pass)
+        auto build_fin = [&](int j, T f3[3]) {
             const int x = xl + j;
-            ds[j] = T(0);
-            dsin[j] = T(0);
-            rho[j] = T(0);
-            bad[j] = false;
-            if (x >= nx) continue;
             if (p.collide) {
-                fin[j][0] = tload<S, T>(p, v0[j], 0);
-                fin[j][1] = tload<S, T>(p, j + 1 < V ? v1[j + 1] : r1, 1);
-                fin[j][2] = tload<S, T>(p, j > 0 ? v2[j - 1] : l2, 2);
+                f3[0] = tload<S, T>(p, v0[j], 0);
+                f3[1] = tload<S, T>(p, j + 1 < V ? v1[j + 1] : r1, 1);
+                f3[2] = tload<S, T>(p, j > 0 ? v2[j - 1] : l2, 2);
                 if (x == nx - 1)  // right end: reflect or wrap
-                    fin[j][1] = bc_wrap_x(p.boundary) ? tload<S, T>(p, src[tidx(p, 1, 0)], 1) : tload<S, T>(p, v2[j], 2);
+                    f3[1] = bc_wrap_x(p.boundary) ? tload<S, T>(p, src[tidx(p, 1, 0)], 1) : tload<S, T>(p, v2[j], 2);
                 if (x == 0)  // left end
-                    fin[j][2] =
-                        bc_wrap_x(p.boundary) ? tload<S, T>(p, src[tidx(p, 2, nx - 1)], 2) : tload<S, T>(p, v1[j], 1);
+                    f3[2] = bc_wrap_x(p.boundary) ? tload<S, T>(p, src[tidx(p, 2, nx - 1)], 2) : tload<S, T>(p, v1[j], 1);
             } else {
-                fin[j][0] = tload<S, T>(p, v0[j], 0);
-                fin[j][1] = tload<S, T>(p, v1[j], 1);
-                fin[j][2] = tload<S, T>(p, v2[j], 2);
+                f3[0] = tload<S, T>(p, v0[j], 0);
+                f3[1] = tload<S, T>(p, v1[j], 1);
+                f3[2] = tload<S, T>(p, v2[j], 2);
             }
-            bad[j] = tube_eval<T>(p, kk, fin[j], fs[j], fp[j], fa[j], nq[j], ds[j], dsin[j], rho[j], true);
-        }
-
-        // the median's neighbours: dS of the adjacent lanes' edge sites
-        const T dl_lane = __shfl_up_sync(0xffffffffu, ds[V - 1], 1);
-        const T dr_lane = __shfl_down_sync(0xffffffffu, ds[0], 1);
-
+        };
+        T ds[V];
+        T s_mass = T(0), s_ds = T(0), s_in = T(0), s_lim = T(0);
+        if constexpr (!F64 && FAST) {
+            // FP32: a lane inside the tube in a colliding polynomial pass (four sites
+            // a lane) evaluates its sites as two pairs (0, 1), (2, 3) with paired
+            // instructions, and a pair on which no limiter acts (no bad site, no
+            // negative f', no dS above the median filter's delta) is finished here.
+            // Every other site keeps only its dS until the neighbours' dS are known
+            // and is then finished one at a time by tube_site32.
+            bool fastp[2] = {false, false}, paired = false;
+            if constexpr (V == 4) {
+                paired = p.collide && p.eq == 0 && xl >= 1 && xl + V <= nx - 1;
+                if (paired) {
+                    // the finished pairs' sums, added pairwise (paired instructions)
+                    float2 m2 = F2::s(0.f), d2s = F2::s(0.f), i2s = F2::s(0.f), dmax = F2::s(0.f);
 #pragma unroll
-        for (int j = 0; j < V; ++j) {
-            const int x = xl + j;
-            if (fastp[j >> 1] || x >= nx) continue;
-            ++acc.c_own;
-            T phi_pos = T(1), phi_med = T(1);
-            if (!bad[j]) {
-                if (p.limiters & 1u) {
-                    if constexpr (F64) {
-                        phi_pos = phi_positivity<3, T>(fs[j], fp[j]);
-                    } else {
+                    for (int h = 0; h < 2; ++h) {
+                        const float2 g[3] = {make_float2(v0[2 * h], v0[2 * h + 1]),
+                                             make_float2(v1[2 * h + 1], h == 0 ? v1[2] : r1),
+                                             make_float2(h == 0 ? l2 : v2[1], v2[2 * h])};
+                        float2 gp[3], d2, i2, r2;
+                        bool bx, by;
+                        tube_pair_eval(kk, p.rho_ref, p.rwf, g, gp, d2, i2, r2, bx, by);
+                        bool act = bx || by;
+                        if (p.limiters & 1u) {
 #pragma unroll
-                        for (int k = 0; k < 3; ++k) {
-                            const float fpa = p.rwf[k] + fp[j][k];  // absolute f'
-                            if (fpa < 0.f) phi_pos = fminf(phi_pos, fa[j][k] / (fa[j][k] - fpa));
+                            for (int k = 0; k < 3; ++k)
+                                act = act || (p.rwf[k] + gp[k].x < 0.f) || (p.rwf[k] + gp[k].y < 0.f);
+                        }
+                        if (p.limiters & 4u) act = act || d2.x > dm || d2.y > dm;
+                        // a site that cannot be limited has dS = +inf (as tube_eval gives it)
+                        ds[2 * h] = bx ? T(INFINITY) : d2.x;
+                        ds[2 * h + 1] = by ? T(INFINITY) : d2.y;
+                        if (act) continue;
+                        // f' stored as one 8-byte vector a plane (xl + 2h is even)
+                        fastp[h] = true;
+                        const int x = xl + 2 * h;
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) *reinterpret_cast<float2 *>(dst + tidx(p, k, x)) = gp[k];
+                        m2 = F2::add(m2, F2::sub(r2, F2::s(p.rho_ref)));  // each term exact
+                        d2s = F2::add(d2s, d2);
+                        i2s = F2::add(i2s, i2);
+                        dmax = make_float2(fmaxf(dmax.x, d2.x), fmaxf(dmax.y, d2.y));
+                    }
+                    if (fastp[0] || fastp[1]) {
+                        s_mass = __fadd_rn(m2.x, m2.y);
+                        s_ds = __fadd_rn(d2s.x, d2s.y);
+                        s_in = __fadd_rn(i2s.x, i2s.y);
+                        acc.c_own += 2 * ((int)fastp[0] + (int)fastp[1]);
+                        // Ehrenfests' candidates among the finished sites (rare: one
+                        // test a lane), and the dS field when it is asked for
+                        if ((p.limiters & 2u) && fmaxf(dmax.x, dmax.y) > kk.thr_e) {
+#pragma unroll
+                            for (int j = 0; j < V; ++j)
+                                if (fastp[j >> 1] && ds[j] > kk.thr_e)
+                                    klist[atomicAdd(kcount, 1)] = make_int2(xl + j, __float_as_int(1.f));
+                        }
+                        if (p.ds_out) {
+#pragma unroll
+                            for (int j = 0; j < V; ++j)
+                                if (fastp[j >> 1]) p.ds_out[xl + j] = (double)ds[j];
                         }
                     }
                 }
-                // three-point median (the two end sites of a closed tube are not
-                // filtered; a periodic tube's end sites wrap around to each other)
-                const bool end = p.boundary == 0 && (x == 0 || x == nx - 1);
-                if ((p.limiters & 4u) && ds[j] > dm && !end) {
-                    T left, right;
-                    if (x == 0)
-                        left = tube_ds<S>(p, kk, src, nx - 1);
-                    else if (j > 0)
-                        left = ds[j - 1];
-                    else if (lane > 0)
-                        left = dl_lane;
-                    else
-                        left = tube_ds<S>(p, kk, src, x - 1);
-                    if (x == nx - 1)
-                        right = tube_ds<S>(p, kk, src, 0);
-                    else if (j + 1 < V)
-                        right = ds[j + 1];
-                    else if (lane < 31)
-                        right = dr_lane;
-                    else
-                        right = tube_ds<S>(p, kk, src, x + 1);
-                    const T med = med3(left, ds[j], right);
+            }
+            if (!paired) {
+#pragma unroll
+                for (int j = 0; j < V; ++j) {
+                    ds[j] = T(0);
+                    if (xl + j >= nx) continue;
+                    float f3[3], fs3[3], fp3[3], fa3[3], nq3[3], din, r;
+                    build_fin(j, f3);
+                    tube_eval<float>(p, kk, f3, fs3, fp3, fa3, nq3, ds[j], din, r, false);
+                }
+            }
+            // the median's neighbours: dS of the adjacent lanes' edge sites
+            const T dl_lane = __shfl_up_sync(0xffffffffu, ds[V - 1], 1);
+            const T dr_lane = __shfl_down_sync(0xffffffffu, ds[0], 1);
+#pragma unroll
+            for (int j = 0; j < V; ++j) {
+                const int x = xl + j;
+                if (fastp[j >> 1] || x >= nx) continue;
+                float f3[3];
+                build_fin(j, f3);
+                // the neighbours' dS, or the site to evaluate (outside the chunk)
+                int xlo = -1, xro = -1;
+                float dl = 0.f, dr = 0.f;
+                if (x == 0)
+                    xlo = nx - 1;
+                else if (j > 0)
+                    dl = ds[j - 1];
+                else if (lane > 0)
+                    dl = dl_lane;
+                else
+                    xlo = x - 1;
+                if (x == nx - 1)
+                    xro = 0;
+                else if (j + 1 < V)
+                    dr = ds[j + 1];
+                else if (lane < 31)
+                    dr = dr_lane;
+                else
+                    xro = x + 1;
+                const SiteSums r =
+                    tube_site32<S>(p, kk, src, dst, x, f3[0], f3[1], f3[2], dl, dr, xlo, xro, klist, kcount);
+                s_lim = __fadd_rn(s_lim, r.lim);
+                s_mass = __fadd_rn(s_mass, r.mass);
+                s_ds = __fadd_rn(s_ds, r.ds);
+                s_in = __fadd_rn(s_in, r.din);
+                acc.c_own += 1;
+                acc.c_bad += r.bad;
+                acc.c_pos += r.pos;
+                acc.c_med += r.med;
+            }
+        } else {
+            T fin[V][3], fs[V][3], fp[V][3], fa[V][3], dsin[V], rho[V];
+            float nq[V][3];
+            bool bad[V];
+#pragma unroll
+            for (int j = 0; j < V; ++j) {
+                const int x = xl + j;
+                ds[j] = T(0);
+                dsin[j] = T(0);
+                rho[j] = T(0);
+                bad[j] = false;
+                if (x >= nx) continue;
+                if (p.collide) {
+                    fin[j][0] = tload<S, T>(p, v0[j], 0);
+                    fin[j][1] = tload<S, T>(p, j + 1 < V ? v1[j + 1] : r1, 1);
+                    fin[j][2] = tload<S, T>(p, j > 0 ? v2[j - 1] : l2, 2);
+                    if (x == nx - 1)  // right end: reflect or wrap
+                        fin[j][1] = bc_wrap_x(p.boundary) ? tload<S, T>(p, src[tidx(p, 1, 0)], 1) : tload<S, T>(p, v2[j], 2);
+                    if (x == 0)  // left end
+                        fin[j][2] =
+                            bc_wrap_x(p.boundary) ? tload<S, T>(p, src[tidx(p, 2, nx - 1)], 2) : tload<S, T>(p, v1[j], 1);
+                } else {
+                    fin[j][0] = tload<S, T>(p, v0[j], 0);
+                    fin[j][1] = tload<S, T>(p, v1[j], 1);
+                    fin[j][2] = tload<S, T>(p, v2[j], 2);
+                }
+                bad[j] = tube_eval<T>(p, kk, fin[j], fs[j], fp[j], fa[j], nq[j], ds[j], dsin[j], rho[j], true);
+            }
+
+            // the median's neighbours: dS of the adjacent lanes' edge sites
+            const T dl_lane = __shfl_up_sync(0xffffffffu, ds[V - 1], 1);
+            const T dr_lane = __shfl_down_sync(0xffffffffu, ds[0], 1);
+
+#pragma unroll
+            for (int j = 0; j < V; ++j) {
+                const int x = xl + j;
+                if (x >= nx) continue;
+                ++acc.c_own;
+                T phi_pos = T(1), phi_med = T(1);
+                if (!bad[j]) {
+                    if (p.limiters & 1u) {
+                        if constexpr (F64) {
+                            phi_pos = phi_positivity<3, T>(fs[j], fp[j]);
+                        } else {
+#pragma unroll
+                            for (int k = 0; k < 3; ++k) {
+                                const float fpa = p.rwf[k] + fp[j][k];  // absolute f'
+                                if (fpa < 0.f) phi_pos = fminf(phi_pos, fa[j][k] / (fa[j][k] - fpa));
+                            }
+                        }
+                    }
+                    // three-point median (the two end sites of a closed tube are not
+                    // filtered; a periodic tube's end sites wrap around to each other)
+                    const bool end = p.boundary == 0 && (x == 0 || x == nx - 1);
+                    if ((p.limiters & 4u) && ds[j] > dm && !end) {
+                        T left, right;
+                        if (x == 0)
+                            left = tube_ds<S>(p, kk, src, nx - 1);
+                        else if (j > 0)
+                            left = ds[j - 1];
+                        else if (lane > 0)
+                            left = dl_lane;
+                        else
+                            left = tube_ds<S>(p, kk, src, x - 1);
+                        if (x == nx - 1)
+                            right = tube_ds<S>(p, kk, src, 0);
+                        else if (j + 1 < V)
+                            right = ds[j + 1];
+                        else if (lane < 31)
+                            right = dr_lane;
+                        else
+                            right = tube_ds<S>(p, kk, src, x + 1);
+                        const T med = med3(left, ds[j], right);
+                        if constexpr (F64) {
+                            phi_med = (p.phi_rule == 1 && p.eq == 1)
+                                          ? phi_median_entropy<3>(fp[j], fs[j], ds[j], med, dm, p.median_mode)
+                                          : phi_median<T>(ds[j], med, dm, p.median_mode);
+                        } else {
+                            phi_med = phi_median<T>(ds[j], med, dm, p.median_mode);
+                        }
+                    }
+                }
+                const T phi = phi_pos < phi_med ? phi_pos : phi_med;
+                T lim = T(0);
+                if (phi < T(1)) {
                     if constexpr (F64) {
-                        phi_med = (p.phi_rule == 1 && p.eq == 1)
-                                      ? phi_median_entropy<3>(fp[j], fs[j], ds[j], med, dm, p.median_mode)
-                                      : phi_median<T>(ds[j], med, dm, p.median_mode);
-                    } else {
-                        phi_med = phi_median<T>(ds[j], med, dm, p.median_mode);
-                    }
-                }
-            }
-            const T phi = phi_pos < phi_med ? phi_pos : phi_med;
-            T lim = T(0);
-            if (phi < T(1)) {
-                if constexpr (F64) {
-                    double fo[3];
+                        double fo[3];
 #pragma unroll
-                    for (int k = 0; k < 3; ++k) {
-                        fo[k] = A::add(fs[j][k], A::mul(phi, A::sub(fp[j][k], fs[j][k])));
-                        dst[tidx(p, k, x)] = fo[k];
+                        for (int k = 0; k < 3; ++k) {
+                            fo[k] = A::add(fs[j][k], A::mul(phi, A::sub(fp[j][k], fs[j][k])));
+                            dst[tidx(p, k, x)] = fo[k];
+                        }
+                        if (p.eq == 1) {
+                            const double dout = rel_entropy<3>(fo, fs[j]);
+                            if (isfinite(ds[j]) && isfinite(dout)) lim = A::sub(ds[j], dout);
+                        } else {
+                            lim = A::mul(A::sub(1.0, A::mul(phi, phi)), ds[j]);
+                        }
+                    } else {
+                        const float cw = limit_weight(phi, kk.a, p.collide != 0);
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) dst[tidx(p, k, x)] = fmaf(-cw, nq[j][k], fin[j][k]);
+                        if (p.eq == 1) {
+                            float dout[3];
+                            const float m = p.collide ? __fmul_rn(-phi, kk.a) : phi;
+#pragma unroll
+                            for (int k = 0; k < 3; ++k) dout[k] = __fmul_rn(m, nq[j][k]);
+                            const float so = rel_entropy_dev<3>(dout, fa[j]);
+                            if (isfinite(ds[j]) && isfinite(so)) lim = __fsub_rn(ds[j], so);
+                        } else {
+                            lim = __fmul_rn(__fsub_rn(1.f, __fmul_rn(phi, phi)), ds[j]);
+                        }
                     }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) dst[tidx(p, k, x)] = f2s<S>(fp[j][k]);
+                }
+                s_lim = A::add(s_lim, lim);
+                if constexpr (F64)
+                    s_mass = A::add(s_mass, rho[j]);
+                else
+                    s_mass = __fadd_rn(s_mass, __fsub_rn(rho[j], p.rho_ref));  // each term exact
+                if (!bad[j]) {
+                    T tds = T(0), tin = T(0);
                     if (p.eq == 1) {
-                        const double dout = rel_entropy<3>(fo, fs[j]);
-                        if (isfinite(ds[j]) && isfinite(dout)) lim = A::sub(ds[j], dout);
+                        if (isfinite(ds[j])) tds = ds[j];
+                        if (isfinite(ds[j]) && isfinite(dsin[j])) tin = A::sub(dsin[j], ds[j]);
                     } else {
-                        lim = A::mul(A::sub(1.0, A::mul(phi, phi)), ds[j]);
+                        tds = ds[j];
+                        tin = dsin[j];
                     }
+                    s_ds = A::add(s_ds, tds);
+                    s_in = A::add(s_in, tin);
                 } else {
-                    const float cw = limit_weight(phi, kk.a, p.collide != 0);
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) dst[tidx(p, k, x)] = fmaf(-cw, nq[j][k], fin[j][k]);
-                    if (p.eq == 1) {
-                        float dout[3];
-                        const float m = p.collide ? __fmul_rn(-phi, kk.a) : phi;
-#pragma unroll
-                        for (int k = 0; k < 3; ++k) dout[k] = __fmul_rn(m, nq[j][k]);
-                        const float so = rel_entropy_dev<3>(dout, fa[j]);
-                        if (isfinite(ds[j]) && isfinite(so)) lim = __fsub_rn(ds[j], so);
+                    ++acc.c_bad;
+                    atomicOr(p.status, kStatNonfinite);
+                }
+                acc.c_pos += phi_pos < T(1);
+                acc.c_med += phi_med < T(1);
+                if ((p.limiters & 2u) && !bad[j]) {
+                    // Ehrenfests' candidates on an FP64 dS(f').  FP64 storage: ds itself.
+                    // FP32 storage: sites near and above the threshold go to the warp's list
+                    // and are keyed after the chunk, a lane each (below)
+                    if constexpr (F64) {
+                        if (ds[j] > p.delta_e) record(x, ds[j], (double)phi);
                     } else {
-                        lim = __fmul_rn(__fsub_rn(1.f, __fmul_rn(phi, phi)), ds[j]);
+                        if (ds[j] > kk.thr_e) klist[atomicAdd(kcount, 1)] = make_int2(x, __float_as_int(phi));
                     }
                 }
-            } else {
-#pragma unroll
-                for (int k = 0; k < 3; ++k) dst[tidx(p, k, x)] = f2s<S>(fp[j][k]);
+                if (p.ds_out) p.ds_out[x] = (double)ds[j];
             }
-            s_lim = A::add(s_lim, lim);
-            if constexpr (F64)
-                s_mass = A::add(s_mass, rho[j]);
-            else
-                s_mass = __fadd_rn(s_mass, __fsub_rn(rho[j], p.rho_ref));  // each term exact
-            if (!bad[j]) {
-                T tds = T(0), tin = T(0);
-                if (p.eq == 1) {
-                    if (isfinite(ds[j])) tds = ds[j];
-                    if (isfinite(ds[j]) && isfinite(dsin[j])) tin = A::sub(dsin[j], ds[j]);
-                } else {
-                    tds = ds[j];
-                    tin = dsin[j];
-                }
-                s_ds = A::add(s_ds, tds);
-                s_in = A::add(s_in, tin);
-            } else {
-                ++acc.c_bad;
-                atomicOr(p.status, kStatNonfinite);
-            }
-            acc.c_pos += phi_pos < T(1);
-            acc.c_med += phi_med < T(1);
-            if ((p.limiters & 2u) && !bad[j]) {
-                // Ehrenfests' candidates on an FP64 dS(f').  FP64 storage: ds itself.
-                // FP32 storage: sites near and above the threshold go to the warp's list
-                // and are keyed after the chunk, a lane each (below)
-                if constexpr (F64) {
-                    if (ds[j] > p.delta_e) record(x, ds[j], (double)phi);
-                } else {
-                    if (ds[j] > kk.thr_e) klist[atomicAdd(kcount, 1)] = make_int2(x, __float_as_int(phi));
-                }
-            }
-            if (p.ds_out) p.ds_out[x] = (double)ds[j];
         }
         if constexpr (!F64) {
             __syncwarp();
@@ -548,8 +703,8 @@ __device__ __forceinline__ void tube_walk(const StepParams &p, const S *__restri
 }
 
 template <typename S, int V>
-__global__ void __launch_bounds__(256, V > 1 ? 2 : 1) k_tube(const StepParams p, const S *__restrict__ src,
-                                                               S *__restrict__ dst, int chunked)
+__global__ void __launch_bounds__(256, V > 1 ? 2 : 1)
+    k_tube(const __grid_constant__ StepParams p, const S *__restrict__ src, S *__restrict__ dst, int chunked)
 {
     constexpr bool F64 = std::is_same<compute_t<S>, double>::value;
     __shared__ TubeSlot<S, V> ring[kTubeWarps][kTubeRing];
