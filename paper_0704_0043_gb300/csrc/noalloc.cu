@@ -207,6 +207,8 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_config *cfg, const double *f_in
     }
     if (status & kStatNonfinite)
         return set_thread_error(LBM_ERR_NONFINITE, "lbm_step_noalloc: a site had rho <= 0, f*_k <= 0 or a nonfinite value");
+    if (status & kStatTimeout)  // no kernel of this path waits today; kept in step with the context path
+        return set_thread_error(LBM_ERR_TIMEOUT, "lbm_step_noalloc: a bounded device wait gave up");
     if (status & kStatCandOverflow)
         return set_thread_error(LBM_ERR_CUDA, "lbm_step_noalloc: Ehrenfests' candidate buffer overflowed");
     return LBM_OK;
