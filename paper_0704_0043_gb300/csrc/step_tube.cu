@@ -20,7 +20,11 @@
 //   * FP64 storage is bound by this GPU's FP64 units, which take a warp's FP64
 //     instruction in 64 cycles whatever the number of active lanes: a short
 //     tube runs one site per lane (V = 1) and one warp per block, so its warps
-//     land on separate SM sub-partitions and the step lasts one site's chain.
+//     land on separate SM sub-partitions and the step lasts one site's chain;
+//   * FP32 storage with four sites a lane evaluates them as two pairs with the
+//     paired FP32 instructions and finishes a pair at once when no limiter
+//     acts on it; any other site is finished by an out-of-line function, so
+//     the walk's registers hold only what the common case needs.
 // Ensemble-dependent limiters and 16-bit storage stay on the tiled kernel.
 #include <type_traits>
 
